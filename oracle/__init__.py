@@ -1,0 +1,28 @@
+"""CPU oracle of the TTIE hot path.
+
+TEST INFRASTRUCTURE ONLY.  Plain, slow FP64 (and exact rational) restatement
+of "Differentiable 3D Triangle-Triangle Intersection Energy" used to check the
+CUDA path.  Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline
+leg of ``bench.py`` may import it; the library never does, and it shares no
+code with the CUDA kernels.
+
+Parity status of each function:
+  pair_dual.c oracle_pair    pinned: closed-form pairs (Eq. 1-2), central
+                             finite differences, invariances
+  exact.active_exact         pinned: independent separating-axis brute force
+                             on integer-grid triangle pairs
+  pair_dual.c filtered_side  pinned: agrees with exact signs on random and
+                             near-degenerate inputs
+  gradient / hessian_*       pinned: FD of T, closed-form eigenvalues (§1.1),
+                             sympy derivation of the dropped Eq. 4 terms
+  assemble / newton_solve    pinned: dense recomputation, direct solve
+                             residual; the Newton trajectory itself is
+                             parity-unpinned (only the certified end state is
+                             compared)
+"""
+from .ttie_oracle import (build_oracle, candidate_pairs, partners_of, evaluate,  # noqa: F401
+                          eval_pairs_f64, filtered_sides, gradient, hessian_parts,
+                          hessian_inexact, hessian_psd, clamp_psd, assemble, pair_dofs,
+                          blocks_to_dense, newton_direction, newton_solve, certify, energy,
+                          NewtonParams, PairEval)
+from . import exact  # noqa: F401

@@ -1,0 +1,409 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Nothing here compares the oracle with itself: every check uses a closed form
+(Eq. 1-4 on hand-built pairs, the eigenvalues stated in §1.1), an independent
+exact predicate (separating axes), finite differences, invariances, or a
+brute-force recomputation.
+"""
+import json
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle as O
+import ttie_inputs as ti
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ----------------------------------------------------------------- closed form (Eq. 1, 2)
+def test_closed_form_pairs():
+    spec = json.load(open(os.path.join(GOLDEN, "closed_form_pairs.json")))
+    for c in spec["cases"]:
+        m = ti.closed_form_pair(c["a0"], c["a1"], c["b0"], c["b1"], c["h"])
+        ev = O.evaluate(m.x, m.tri, np.array([[0, 1]]))
+        assert bool(ev.active[0]) == c["active"], c["name"]
+        assert ev.T[0] == pytest.approx(c["T"], rel=1e-12, abs=1e-15), c["name"]
+        if c["active"]:
+            lo_a, hi_a = sorted([c["a0"], c["a1"]])
+            lo_b, hi_b = sorted([c["b0"], c["b1"]])
+            # D points along -x here, so (t_c^0, t_c^1) = -(b, a) of the x-axis intervals
+            assert ev.tc[0, 0] * ev.tc[0, 1] == pytest.approx((lo_a - hi_b) * (hi_a - lo_b), rel=1e-12)
+            # Sum of the four t about their mean is zero (origin A cancels); |I_c| is the sum of lengths
+            assert ev.tc[0, 1] - ev.tc[0, 0] == pytest.approx((hi_a - lo_a) + (hi_b - lo_b), rel=1e-12)
+
+
+def test_appendix_half_scale():
+    """The appendix's listing returns (t_a^0 - t_b^1)/2; tc_scale=0.5 reproduces it, T/16."""
+    m = ti.closed_form_pair(-0.2, 0.5, 0.1, 0.9)
+    e1 = O.evaluate(m.x, m.tri, np.array([[0, 1]]), tc_scale=1.0)
+    e2 = O.evaluate(m.x, m.tri, np.array([[0, 1]]), tc_scale=0.5)
+    assert np.allclose(e2.tc, 0.5 * e1.tc)
+    assert e2.T[0] == pytest.approx(e1.T[0] / 16)
+
+
+def test_vertex_on_plane_case():
+    """Signs (+,-,0): the cut segment runs from the on-plane vertex to the opposite edge."""
+    h = 0.5
+    # A in z=0, cut by y=0 in [-0.25, 0.5]
+    A = [[0.0, -h, 0.0], [-0.5, h, 0.0], [1.0, h, 0.0]]
+    # B in y=0 with one vertex on z=0 at x=0.75, others at z=+h (x=0) and z=-h (x=0.5):
+    # its cut by z=0 is [0.25, 0.75]
+    B = [[0.75, 0.0, 0.0], [0.0, 0.0, h], [0.5, 0.0, -h]]
+    x = np.array(A + B)
+    tri = np.array([[0, 1, 2], [3, 4, 5]], np.int32)
+    ev = O.evaluate(x, tri, np.array([[0, 1]]))
+    assert ev.active[0]
+    assert ev.T[0] == pytest.approx(((-0.25 - 0.75) * (0.5 - 0.25)) ** 2, rel=1e-12)
+    assert list(ev.sides64[0, :3]).count(0) == 1
+
+
+# ----------------------------------------------------------------- exact predicate vs separating axes
+def _sat_active(A, B):
+    """Independent characterisation: the pair is intersecting iff no plane weakly separates the
+    two triangles, i.e. their relative interiors meet and they are not coplanar.  The candidate
+    axes (face normals, edge x edge) contain a facet normal of A (+) (-B), so checking them is
+    complete.  Exact integer / rational arithmetic."""
+    def sub(a, b):
+        return [a[k] - b[k] for k in range(3)]
+
+    def cross(a, b):
+        return [a[1] * b[2] - a[2] * b[1], a[2] * b[0] - a[0] * b[2], a[0] * b[1] - a[1] * b[0]]
+
+    def dot(a, b):
+        return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]
+    ea = [sub(A[(k + 1) % 3], A[k]) for k in range(3)]
+    eb = [sub(B[(k + 1) % 3], B[k]) for k in range(3)]
+    axes = [cross(ea[0], ea[1]), cross(eb[0], eb[1])] + [cross(e, f) for e in ea for f in eb]
+    for k in axes:
+        if k == [0, 0, 0]:
+            continue
+        pa = [dot(k, p) for p in A]
+        pb = [dot(k, p) for p in B]
+        if max(pa) <= min(pb) or max(pb) <= min(pa):
+            return False
+    return True
+
+
+@pytest.mark.parametrize("grid,seed", [(1, 0), (2, 1), (3, 2), (4, 3), (6, 4)])
+def test_exact_matches_separating_axes_on_grid(grid, seed):
+    m = ti.snapped_soup(90, seed, grid)
+    pairs = np.array([(i, j) for i in range(m.F) for j in range(i + 1, m.F)], np.int64)
+    act = O.exact.active_exact(m.x, m.tri, pairs)
+    xi = m.x.astype(np.int64)
+    ref = np.array([_sat_active([list(xi[v]) for v in m.tri[i]], [list(xi[v]) for v in m.tri[j]])
+                    for i, j in pairs])
+    assert np.array_equal(act, ref)
+    # the grid makes every kind of case occur
+    assert ref.sum() > 0 and (~ref).sum() > 0
+
+
+def test_exact_matches_separating_axes_random():
+    m = ti.triangle_soup(120, 11, size=0.5)
+    pairs = np.array([(i, j) for i in range(m.F) for j in range(i + 1, m.F)], np.int64)
+    act = O.exact.active_exact(m.x, m.tri, pairs, prefilter=O.filtered_sides(m.x, m.tri, pairs))
+    xf = [[tuple(Fraction(float(c)) for c in v) for v in m.x[t]] for t in m.tri]
+    ref = np.array([_sat_active([list(p) for p in xf[i]], [list(p) for p in xf[j]]) for i, j in pairs])
+    assert np.array_equal(act, ref)
+    assert ref.sum() > 50
+
+
+def test_fp64_overlap_agrees_on_generic_pairs():
+    """Away from degeneracies the listing's FP64 comparisons give the exact answer."""
+    m = ti.triangle_soup(200, 5, size=0.5)
+    pairs = np.array([(i, j) for i in range(m.F) for j in range(i + 1, m.F)], np.int64)
+    ev = O.evaluate(m.x, m.tri, pairs)
+    assert np.array_equal(ev.active, (ev.flags64 & 4) != 0)
+
+
+# ----------------------------------------------------------------- certified side filter
+def _exact_side(P, q):
+    P = [[Fraction(float(c)) for c in p] for p in P]
+    q = [Fraction(float(c)) for c in q]
+    e1 = [P[1][k] - P[0][k] for k in range(3)]
+    e2 = [P[2][k] - P[0][k] for k in range(3)]
+    f = [q[k] - P[0][k] for k in range(3)]
+    n = [e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]]
+    d = n[0] * f[0] + n[1] * f[1] + n[2] * f[2]
+    return (d > 0) - (d < 0)
+
+
+def test_side_filter_never_wrong():
+    rng = np.random.default_rng(7)
+    base = ti.snapped_soup(150, 8, 3)
+    # near-degenerate: integer grid plus perturbations of a few ulps
+    x = base.x + rng.integers(-2, 3, base.x.shape) * np.ldexp(1.0, -50)
+    x32 = (base.x + rng.normal(0, 1e-7, base.x.shape)).astype(np.float32).astype(np.float64)
+    for xx in (base.x, x, x32):
+        pairs = np.array([(i, j) for i in range(0, base.F, 3) for j in range(i + 1, base.F, 2)], np.int64)
+        fs = O.filtered_sides(xx, base.tri, pairs)
+        n_certain = 0
+        for p, (i, j) in enumerate(pairs):
+            A, B = xx[base.tri[i]], xx[base.tri[j]]
+            ex = [_exact_side(A, b) for b in B] + [_exact_side(B, a) for a in A]
+            for k in range(6):
+                if fs[p, k] != 2:
+                    n_certain += 1
+                    assert fs[p, k] == ex[k]
+        assert n_certain > 0
+
+
+# ----------------------------------------------------------------- derivatives (Eq. 3, 4)
+def _generic_active_pairs(seed=3, n=200, margin=0.05):
+    m = ti.triangle_soup(n, seed, size=0.5)
+    pairs = np.array([(i, j) for i in range(m.F) for j in range(i + 1, m.F)], np.int64)
+    ev = O.evaluate(m.x, m.tri, pairs)
+    keep = []
+    for p in np.nonzero(ev.active)[0]:
+        a, b = ev.tc[p]
+        if min(abs(a), abs(b)) < margin:
+            continue
+        keep.append(p)
+    return m, pairs[keep]
+
+
+def _tc_at(m, pair, loc):
+    x = m.x.copy()
+    x[m.tri[pair[0]]] = loc[:9].reshape(3, 3)
+    x[m.tri[pair[1]]] = loc[9:].reshape(3, 3)
+    tc, dtc, _, fl = O.eval_pairs_f64(x, m.tri, pair[None, :])
+    return tc[0], dtc[0], fl[0]
+
+
+def _loc(m, pair):
+    return np.concatenate([m.x[m.tri[pair[0]]].ravel(), m.x[m.tri[pair[1]]].ravel()])
+
+
+def test_dual_gradient_matches_central_differences():
+    m, pairs = _generic_active_pairs()
+    assert len(pairs) >= 20
+    h = 1e-6
+    for pair in pairs[:40]:
+        loc = _loc(m, pair)
+        tc, dtc, fl = _tc_at(m, pair, loc)
+        fd = np.zeros((2, 18))
+        ok = True
+        for k in range(18):
+            e = np.zeros(18)
+            e[k] = h
+            tp, _, flp = _tc_at(m, pair, loc + e)
+            tm, _, flm = _tc_at(m, pair, loc - e)
+            ok &= (flp == fl) and (flm == fl)
+            fd[:, k] = (tp - tm) / (2 * h)
+        if not ok:
+            continue
+        assert np.allclose(dtc, fd, rtol=1e-5, atol=1e-7 * np.abs(dtc).max())
+
+
+def _T_and_g(m, pair, loc):
+    x = m.x.copy()
+    x[m.tri[pair[0]]] = loc[:9].reshape(3, 3)
+    x[m.tri[pair[1]]] = loc[9:].reshape(3, 3)
+    ev = O.evaluate(x, m.tri, pair[None, :])
+    return ev.T[0], O.gradient(ev)[0], ev
+
+
+def test_eq3_gradient_is_gradient_of_T():
+    m, pairs = _generic_active_pairs(seed=4)
+    h = 1e-6
+    for pair in pairs[:25]:
+        loc = _loc(m, pair)
+        T, g, _ = _T_and_g(m, pair, loc)
+        fd = np.array([(_T_and_g(m, pair, loc + h * np.eye(18)[k])[0] -
+                        _T_and_g(m, pair, loc - h * np.eye(18)[k])[0]) / (2 * h) for k in range(18)])
+        assert np.allclose(g, fd, rtol=1e-5, atol=1e-8 * np.abs(g).max())
+
+
+def test_eq4_is_exact_hessian_minus_dropped_terms():
+    """Eq. 4 equals the exact Hessian of (ab)^2 minus 2ab(b d2a + a d2b) (§1.1, "ignoring the
+    asymmetric part"); exact Hessian and d2a, d2b from central differences of the gradients."""
+    m, pairs = _generic_active_pairs(seed=6)
+    h = 1e-5
+    for pair in pairs[:10]:
+        loc = _loc(m, pair)
+        T, g, ev = _T_and_g(m, pair, loc)
+        a, b = ev.tc[0]
+        Hfd = np.zeros((18, 18))
+        d2a = np.zeros((18, 18))
+        d2b = np.zeros((18, 18))
+        for k in range(18):
+            e = h * np.eye(18)[k]
+            _, gp, evp = _T_and_g(m, pair, loc + e)
+            _, gm, evm = _T_and_g(m, pair, loc - e)
+            Hfd[:, k] = (gp - gm) / (2 * h)
+            d2a[:, k] = (evp.dtc[0, 0] - evm.dtc[0, 0]) / (2 * h)
+            d2b[:, k] = (evp.dtc[0, 1] - evm.dtc[0, 1]) / (2 * h)
+        Hin = O.hessian_inexact(ev)[0]
+        dropped = 2 * a * b * (b * d2a + a * d2b)
+        scale = np.abs(Hfd).max()
+        assert np.allclose(Hin, Hfd - dropped, atol=2e-5 * scale)
+
+
+def test_eq4_symbolic_expansion():
+    """sympy: Hessian of (a b)^2 = Eq. 4 + 2ab(b Hess a + a Hess b) for generic a(x), b(x)."""
+    sp = pytest.importorskip("sympy")
+    xs = sp.symbols("x0:3")
+    a = sp.Function("a")(*xs)
+    b = sp.Function("b")(*xs)
+    T = (a * b) ** 2
+    u = sp.Matrix([sp.diff(a, v) for v in xs])
+    w = sp.Matrix([sp.diff(b, v) for v in xs])
+    H = sp.hessian(T, xs)
+    eq4 = 2 * b ** 2 * u * u.T + 2 * a ** 2 * w * w.T + 4 * a * b * (w * u.T + u * w.T)
+    dropped = 2 * a * b * (b * sp.hessian(a, xs) + a * sp.hessian(b, xs))
+    assert sp.simplify(H - eq4 - dropped) == sp.zeros(3, 3)
+
+
+# ----------------------------------------------------------------- eigen-analysis (§1.1)
+def test_eigenanalysis_closed_forms():
+    m, pairs = _generic_active_pairs(seed=8)
+    ev = O.evaluate(m.x, m.tri, pairs)
+    p1, p2, p3 = O.hessian_parts(ev)
+    a, b = ev.tc[:, 0], ev.tc[:, 1]
+    u, v = ev.dtc[:, 0], ev.dtc[:, 1]
+    for k in range(len(pairs)):
+        w1 = np.linalg.eigvalsh(p1[k])
+        w2 = np.linalg.eigvalsh(p2[k])
+        # part 1 and part 2: a single non-zero eigenvalue 2 b^2 |du|^2, 2 a^2 |dv|^2
+        assert w1[-1] == pytest.approx(2 * b[k] ** 2 * u[k] @ u[k], rel=1e-10)
+        assert w2[-1] == pytest.approx(2 * a[k] ** 2 * v[k] @ v[k], rel=1e-10)
+        assert np.abs(w1[:-1]).max() < 1e-10 * w1[-1]
+        # part 3: trace is the paper's 8ab du.dv; its two eigenvalues 4ab(u.v +- |u||v|)
+        assert np.trace(p3[k]) == pytest.approx(8 * a[k] * b[k] * u[k] @ v[k], rel=1e-10)
+        w3 = np.linalg.eigvalsh(p3[k])
+        nu, nv = np.linalg.norm(u[k]), np.linalg.norm(v[k])
+        lo, hi = sorted([4 * a[k] * b[k] * (u[k] @ v[k] + nu * nv), 4 * a[k] * b[k] * (u[k] @ v[k] - nu * nv)])
+        assert w3[0] == pytest.approx(lo, rel=1e-9) and w3[-1] == pytest.approx(hi, rel=1e-9)
+
+
+def test_psd_projection_properties():
+    m, pairs = _generic_active_pairs(seed=9)
+    ev = O.evaluate(m.x, m.tri, pairs)
+    Hp = O.hessian_psd(ev, "per_part")
+    p3 = O.hessian_parts(ev)[2]
+    a, b = ev.tc[:, 0], ev.tc[:, 1]
+    u, v = ev.dtc[:, 0], ev.dtc[:, 1]
+    for k in range(len(pairs)):
+        H = Hp[k]
+        assert np.allclose(H, H.T, atol=1e-14 * np.abs(H).max())
+        w = np.linalg.eigvalsh(H)
+        assert w[0] >= -1e-12 * w[-1]
+        assert np.sum(w > 1e-10 * w[-1]) <= 2                       # rank <= 2
+        for ax in range(3):                                           # translations are null
+            t = np.zeros(18)
+            t[ax::3] = 1.0
+            assert np.abs(H @ t).max() <= 1e-9 * np.abs(H).max()
+        # clamped part 3 = 2|ab||u||v| (u^ - v^)(u^ - v^)^T (its non-negative eigenpair)
+        nu, nv = np.linalg.norm(u[k]), np.linalg.norm(v[k])
+        wv = u[k] / nu - v[k] / nv
+        closed = 2 * abs(a[k] * b[k]) * nu * nv * np.outer(wv, wv)
+        assert np.allclose(O.clamp_psd(p3[k:k + 1])[0], closed, atol=1e-10 * np.abs(closed).max())
+
+
+# ----------------------------------------------------------------- invariances
+def test_invariances():
+    m, pairs = _generic_active_pairs(seed=10)
+    rng = np.random.default_rng(0)
+    R = ti.random_rotation(rng)
+    t = rng.normal(size=3)
+    for pair in pairs[:30]:
+        x = m.x
+        ev = O.evaluate(x, m.tri, pair[None, :])
+        T0 = ev.T[0]
+        # swap the triangles
+        assert O.evaluate(x, m.tri, pair[::-1][None, :]).T[0] == pytest.approx(T0, rel=1e-9)
+        # cyclic and odd permutations of a triangle's vertices
+        for perm in ([1, 2, 0], [2, 0, 1], [0, 2, 1], [1, 0, 2]):
+            tri2 = m.tri.copy()
+            tri2[pair[0]] = m.tri[pair[0]][perm]
+            assert O.evaluate(x, tri2, pair[None, :]).T[0] == pytest.approx(T0, rel=1e-9)
+        # rigid motion and reflection
+        assert O.evaluate(x @ R.T + t, m.tri, pair[None, :]).T[0] == pytest.approx(T0, rel=1e-8)
+        assert O.evaluate(x * np.array([-1, 1, 1]), m.tri, pair[None, :]).T[0] == pytest.approx(T0, rel=1e-9)
+        # scaling: T is homogeneous of degree 4
+        assert O.evaluate(2.5 * x, m.tri, pair[None, :]).T[0] == pytest.approx(2.5 ** 4 * T0, rel=1e-9)
+        # per-pair gradient: zero net force and zero net torque
+        g = O.gradient(ev)[0].reshape(6, 3)
+        X = np.concatenate([x[m.tri[pair[0]]], x[m.tri[pair[1]]]])
+        sc = np.abs(g).max() * (1 + np.abs(X).max())
+        assert np.abs(g.sum(0)).max() < 1e-10 * sc
+        assert np.abs(np.cross(X, g).sum(0)).max() < 1e-10 * sc
+
+
+# ----------------------------------------------------------------- pairs, assembly, solve
+def test_candidate_pairs_brute_force_loops():
+    m = ti.cloth(9, seed=2)
+    lo, hi = m.x[m.tri].min(1), m.x[m.tri].max(1)
+    ref = []
+    for i in range(m.F):
+        for j in range(i + 1, m.F):
+            if set(m.tri[i]) & set(m.tri[j]):
+                continue
+            if all(lo[i][k] <= hi[j][k] and lo[j][k] <= hi[i][k] for k in range(3)):
+                ref.append((i, j))
+    got = O.candidate_pairs(m.x, m.tri)
+    assert [tuple(p) for p in got] == ref
+    for i in (0, 7, 50):
+        row = sorted([j for (a, j) in ref if a == i] + [a for (a, j) in ref if j == i])
+        assert list(O.partners_of(m.x, m.tri, i)) == row
+
+
+def test_pair_modes():
+    m = ti.two_icospheres()
+    inter = O.candidate_pairs(m.x, m.tri, m.group, "inter", aabb=False)
+    assert len(inter) == 320 * 320
+    assert np.all(m.group[inter[:, 0]] != m.group[inter[:, 1]])
+    inst = O.candidate_pairs(m.x, m.tri, m.group, "instance")
+    assert np.all(m.group[inst[:, 0]] == m.group[inst[:, 1]])
+
+
+def test_assembly_matches_dense_scatter():
+    m = ti.cloth(12, seed=21)
+    pairs = O.candidate_pairs(m.x, m.tri)
+    ev = O.evaluate(m.x, m.tri, pairs)
+    assert ev.active.sum() > 3
+    grad, blocks = O.assemble(m.tri, ev, m.V)
+    g = O.gradient(ev)
+    H = O.hessian_psd(ev)
+    Gd = np.zeros(3 * m.V)
+    Hd = np.zeros((3 * m.V, 3 * m.V))
+    dof = O.pair_dofs(m.tri, ev.pairs)
+    for p in range(len(pairs)):
+        idx = (3 * dof[p][:, None] + np.arange(3)[None, :]).ravel()
+        Gd[idx] += g[p]
+        Hd[np.ix_(idx, idx)] += H[p]
+    assert np.allclose(grad.ravel(), Gd)
+    M = O.blocks_to_dense(blocks, np.arange(m.V))
+    assert np.allclose(M, Hd)
+    pattern = {(int(r), int(c)) for p in np.nonzero(ev.active)[0] for r in dof[p] for c in dof[p]}
+    assert set(blocks) == pattern
+
+
+def test_newton_direction_solves_system():
+    m = ti.cloth(12, seed=21)
+    prm = O.NewtonParams()
+    E, n, grad, d, verts = O.newton_direction(m.x, m.tri, None, prm)
+    assert n > 0 and E > 0
+    pairs = O.candidate_pairs(m.x, m.tri)
+    ev = O.evaluate(m.x, m.tri, pairs)
+    _, blocks = O.assemble(m.tri, ev, m.V)
+    H = O.blocks_to_dense(blocks, verts)
+    mu = prm.mu_rel * np.mean(np.diag(H))
+    r = (H + mu * np.eye(len(H))) @ d[verts].ravel() + grad[verts].ravel()
+    assert np.linalg.norm(r) <= 1e-9 * np.linalg.norm(grad)
+    assert np.sum(grad * d) < 0   # descent direction
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("case", ["spheres_shallow", "cloth_mild"])
+def test_newton_solve_reaches_intersection_free(case):
+    if case == "spheres_shallow":
+        m, mode = ti.two_icospheres(offset=(1.95, 0.0, 0.0)), "inter"
+    else:
+        m, mode = ti.cloth(16, seed=2, shear=0.05), "self"
+    assert O.certify(m.x, m.tri, m.group, mode) > 0
+    x, it, ok = O.newton_solve(m.x, m.tri, m.group, O.NewtonParams(newton_max_it=30, mode=mode))
+    assert ok
+    assert O.certify(x, m.tri, m.group, mode) == 0
