@@ -1,0 +1,236 @@
+/*
+ * ttie.h -- C ABI of the GB300 triangle-triangle intersection energy (TTIE) library.
+ *
+ * The library evaluates, for a triangle mesh, the energy of "Differentiable 3D
+ * Triangle-Triangle Intersection Energy" (arXiv 2606.06511) and drives the mesh
+ * towards an intersection-free state with an inexact Newton method:
+ *
+ *   ttie_build_bvh    broad phase: candidate triangle pairs (LBVH or brute force)
+ *   ttie_eval_pairs   narrow phase + energy: Möller reduction to the intervals
+ *                     I_a, I_b, the Minkowski interval I_c (Eq. 1), the energy
+ *                     T = (t_c^0 t_c^1)^2 (Eq. 2), its gradient (Eq. 3) and the
+ *                     inexact Hessian (Eq. 4) made PSD by its eigen-analysis (§1.1)
+ *   ttie_assemble     3x3 block-CSR Hessian and per-vertex gradient
+ *   ttie_newton_step  one inexact Newton iteration (PCG + backtracking line search)
+ *   ttie_solve        Newton iterations until no pair intersects
+ *
+ * Conventions for every call:
+ *   - Pointers named d_* are CUDA device pointers on the context's device;
+ *     pointers without the prefix are host pointers.  Caller-owned buffers are
+ *     only borrowed for the duration of the call.
+ *   - All work is enqueued on the context's stream.  Calls that return host
+ *     values synchronise that stream.
+ *   - Every call returns a ttie_status.  Arguments are checked before anything
+ *     is launched; on error nothing of the caller's memory has been written
+ *     unless stated.  ttie_last_error(ctx) describes the last failure.
+ *   - Nothing aborts, traps or waits without a bound.
+ *   - A context is not thread-safe; use one per host thread.
+ */
+#ifndef TTIE_H
+#define TTIE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    TTIE_OK = 0,
+    TTIE_ERR_INVALID = 1,        /* bad argument (null pointer, size, index out of range) */
+    TTIE_ERR_CUDA = 2,           /* a CUDA runtime call failed */
+    TTIE_ERR_OOM = 3,            /* a device allocation failed */
+    TTIE_ERR_CAPACITY = 4,       /* a bounded internal structure overflowed (BVH stack) */
+    TTIE_ERR_NONFINITE = 5,      /* NaN or Inf in positions, energy or solver residual */
+    TTIE_ERR_NOT_CONVERGED = 6,  /* iteration limit reached */
+    TTIE_ERR_STATE = 7           /* calls made out of order (e.g. eval before build) */
+} ttie_status;
+
+/* Arithmetic of the per-pair evaluation.
+ * TTIE_F32: positions float32, FP32 evaluation; every sign that decides the
+ *           intersection test is certified (FP32 filter -> FP64 -> exact).
+ * TTIE_F64: positions float64, FP64 evaluation, same certified signs.        */
+typedef enum { TTIE_F32 = 0, TTIE_F64 = 1 } ttie_precision;
+
+/* Which triangle pairs are considered.  Topologically adjacent pairs (sharing a
+ * vertex index) are always excluded (§1).                                    */
+typedef enum {
+    TTIE_PAIRS_SELF = 0,         /* every non-adjacent pair i<j                   */
+    TTIE_PAIRS_INTER_GROUP = 1,  /* only pairs with group[i] != group[j]          */
+    TTIE_PAIRS_INTRA_GROUP = 2   /* only pairs with group[i] == group[j]          */
+} ttie_pair_mode;
+
+/* OR-ed into pair_mode: enumerate every pair of the mode instead of the LBVH
+ * candidates (no bounding-box test). */
+#define TTIE_PAIRS_BRUTE 4
+
+/* PSD projection of the Eq. 4 Hessian (eigen-analysis of §1.1).
+ * PER_PART:   parts 1 and 2 kept, part 3 keeps its non-negative eigenpair.
+ * DROP_CROSS: parts 1 and 2 only.                                            */
+typedef enum { TTIE_PSD_PER_PART = 0, TTIE_PSD_DROP_CROSS = 1 } ttie_psd_mode;
+
+typedef struct {
+    int precision;        /* ttie_precision                                        */
+    int pair_mode;        /* ttie_pair_mode, optionally | TTIE_PAIRS_BRUTE          */
+    int psd_mode;         /* ttie_psd_mode                                         */
+    double tc_scale;      /* t_c = tc_scale * (Eq. 1); 1.0 = Eq. 1, 0.5 = appendix */
+    double mu_rel;        /* Newton regulariser: mu = mu_rel * mean diag(H+)       */
+    double pcg_rtol;      /* PCG stops at |r| <= pcg_rtol |r0|                     */
+    int pcg_max_it;
+    int newton_max_it;
+    int ls_max_halvings;  /* line search tries 1+push_eta, 1, 1/2, ... 2^-this      */
+    double armijo_c;
+    double push_eta;      /* first trial step 1 + push_eta (overshoot past touching) */
+    int exact_only;       /* test switch: decide every sign with exact arithmetic  */
+    int profile;          /* record per-stage GPU times in ttie_step_info          */
+} ttie_params;
+
+typedef struct ttie_ctx ttie_ctx;
+
+/* Fills *p with the defaults: F32, SELF, PER_PART, tc_scale 1, mu_rel 1e-3,
+ * pcg_rtol 1e-3, pcg_max_it 200, newton_max_it 200, ls_max_halvings 20,
+ * armijo_c 1e-4, push_eta 0.5, exact_only 0, profile 0. */
+void ttie_default_params(ttie_params *p);
+
+/* Creates a context on the current CUDA device.  stream: a cudaStream_t or NULL
+ * for the legacy default stream.  The context owns every internal buffer (pair
+ * lists, BVH, BSR, solver vectors); they grow on demand. */
+ttie_status ttie_create(ttie_ctx **out, const ttie_params *p, void *stream);
+void ttie_destroy(ttie_ctx *ctx);
+/* Message of the last failed call on ctx (never NULL; valid until the next call). */
+const char *ttie_last_error(const ttie_ctx *ctx);
+ttie_status ttie_set_params(ttie_ctx *ctx, const ttie_params *p);
+
+/*
+ * Broad phase (§1.2 uses a spatial structure "to eliminate redundant
+ * computations"; this library uses an LBVH).
+ *   d_x      V x x_stride positions (float for F32, double for F64), x_stride 3 or 4
+ *   d_tri    F x 3 int32 vertex indices in [0, V)
+ *   d_group  F int32 group ids in [0, 2^20) or NULL (required by the group modes)
+ *   n_candidates (host out) number of candidate pairs: non-adjacent pairs i<j of
+ *            the pair mode whose closed axis-aligned bounding boxes overlap
+ *            (every pair of the mode with TTIE_PAIRS_BRUTE).
+ * Records the topology (tri, group, V) in the context for the calls below.
+ * Errors: INVALID (sizes, indices), NONFINITE (positions), CAPACITY, OOM, CUDA. */
+ttie_status ttie_build_bvh(ttie_ctx *ctx, const void *d_x, int64_t V, int x_stride,
+                           const int32_t *d_tri, int64_t F, const int32_t *d_group,
+                           int64_t *n_candidates);
+
+/* Evaluation flags. */
+#define TTIE_EVAL_E 1u   /* energy sum T (Eq. 2)                                  */
+#define TTIE_EVAL_G 2u   /* gradient (Eq. 3), scattered per vertex                 */
+#define TTIE_EVAL_H 4u   /* per-pair PSD Hessian factors (Eq. 4, §1.1) for ttie_assemble */
+
+/*
+ * Narrow phase and energy over the candidates of the last ttie_build_bvh, at
+ * positions d_x (same V, stride and dtype as the build; may differ in value).
+ *   energy   (host out, nullable) sum over intersecting pairs of T, FP64 sum
+ *   n_active (host out, nullable) number of intersecting pairs: both triangles
+ *            straddle the other's plane and 0 lies strictly inside I_c (§1)
+ *   d_grad   (device out, nullable) V x 3 gradient of the energy (same dtype as
+ *            the positions); rows of vertices in no intersecting pair are zero.
+ * Errors: STATE (no build), INVALID, NONFINITE, OOM, CUDA.
+ */
+ttie_status ttie_eval_pairs(ttie_ctx *ctx, const void *d_x, unsigned what, double *energy,
+                            int64_t *n_active, void *d_grad);
+
+/* Device views into context memory, valid until the next mutating call. */
+typedef struct {
+    int64_t n_rows;              /* active vertices (in at least one intersecting pair) */
+    int64_t nnzb;                /* stored 3x3 blocks                                    */
+    const int32_t *row_ptr;      /* n_rows + 1                                          */
+    const int32_t *col_idx;      /* nnzb, compact row ids, ascending within a row        */
+    const void *val;             /* nnzb x 9, row-major 3x3 blocks of H+ (positions' dtype) */
+    const int32_t *vertex_of_row;/* n_rows, ascending global vertex ids                  */
+    const void *grad;            /* n_rows x 3 assembled gradient (positions' dtype)      */
+} ttie_bsr_view;
+
+/*
+ * Assembles the PSD Hessian H+ and the gradient of the last ttie_eval_pairs
+ * (which must have included TTIE_EVAL_H) over the active vertices.  The block
+ * pattern is the union of the 6x6 vertex blocks of the intersecting pairs; the
+ * sums run in a fixed order (sorted keys), so the result is deterministic.
+ * Errors: STATE, OOM, CUDA.
+ */
+ttie_status ttie_assemble(ttie_ctx *ctx, ttie_bsr_view *out);
+
+/* Copies the last assembled system into caller-owned device buffers sized from the
+ * ttie_assemble view: row_ptr n_rows + 1, col_idx nnzb, val nnzb x 9,
+ * vertex_of_row n_rows, grad n_rows x 3.  Any pointer may be NULL.
+ * Errors: STATE (nothing assembled), CUDA. */
+ttie_status ttie_copy_bsr(ttie_ctx *ctx, int32_t *d_row_ptr, int32_t *d_col_idx, void *d_val,
+                         int32_t *d_vertex_of_row, void *d_grad);
+
+/*
+ * Preconditioned conjugate gradients on the last assembled system:
+ * (H+ + mu I) d = rhs with mu = mu_rel * mean diag(H+), block-Jacobi (3x3)
+ * preconditioner, FP64 dot products.  d_rhs, d_out: n_rows x 3 device arrays
+ * of the positions' dtype.  Stops at |r| <= rtol |rhs| or max_it iterations.
+ * iters, rel_residual: host outs (nullable).
+ */
+ttie_status ttie_pcg(ttie_ctx *ctx, const void *d_rhs, void *d_out, double rtol, int max_it,
+                     int *iters, double *rel_residual);
+
+typedef struct {
+    int64_t n_candidates;        /* candidate pairs at x                              */
+    int64_t n_active;            /* intersecting pairs at x                           */
+    int64_t n_rows, nnzb;        /* assembled system size                             */
+    double energy;               /* E(x)                                               */
+    double energy_new;           /* E at the accepted point                           */
+    int64_t n_active_new;        /* intersecting pairs at the accepted point          */
+    double alpha;                /* accepted step length                               */
+    double grad_dot_dir;         /* g . d                                              */
+    int pcg_iters;
+    double pcg_rel_residual;
+    int ls_trials;               /* trial steps evaluated                              */
+    int64_t n_candidates_swept;  /* candidates of the line-search sweep [x, x+a_max d] */
+    float ms_build, ms_eval, ms_assemble, ms_pcg, ms_line_search;  /* if params.profile */
+} ttie_step_info;
+
+/*
+ * One inexact Newton iteration on the mesh recorded by ttie_build_bvh:
+ * candidates and evaluation at x, assembly, PCG for d, then a backtracking line
+ * search over the trial steps 1+push_eta, 1, 1/2, ... on candidates from the
+ * boxes swept between x and x + (1+push_eta) d; a trial is accepted when it
+ * meets Armijo's condition or leaves no intersecting pair.  d_x_inout is
+ * updated in place (unchanged when x has no intersecting pair).
+ */
+ttie_status ttie_newton_step(ttie_ctx *ctx, void *d_x_inout, ttie_step_info *info);
+
+typedef struct {
+    int iterations;
+    int converged;               /* 1 when the final x has no intersecting pair        */
+    int64_t n_active_initial, n_active_final;
+    double energy_initial, energy_final;
+    double seconds;              /* wall time of the solve                              */
+} ttie_solve_info;
+
+/* Newton iterations until no pair intersects or params.newton_max_it.
+ * Returns NOT_CONVERGED (with d_x_inout holding the last iterate) at the limit. */
+ttie_status ttie_solve(ttie_ctx *ctx, void *d_x_inout, ttie_solve_info *info);
+
+/* ---- inspection (tests, tools) ------------------------------------------------ */
+
+/* Copies the candidate pairs of the last build (n x 2 int32, i<j, deterministic
+ * order) into d_out (capacity pairs).  *n receives the count. */
+ttie_status ttie_get_candidates(ttie_ctx *ctx, int32_t *d_out, int64_t capacity, int64_t *n);
+
+/* Copies the intersecting pairs of the last ttie_eval_pairs in candidate order:
+ * d_pairs n x 2 int32 (nullable); d_tc n x 2 (t_c^0, t_c^1) and d_dtc n x 36
+ * (gradients of t_c^0 then t_c^1 w.r.t. [A0 A1 A2 B0 B1 B2], A = first triangle)
+ * in the positions' dtype, both nullable (require TTIE_EVAL_G or TTIE_EVAL_H). */
+ttie_status ttie_get_active(ttie_ctx *ctx, int32_t *d_pairs, void *d_tc, void *d_dtc,
+                            int64_t capacity, int64_t *n);
+
+/* Copies the last Newton direction (V x 3, positions' dtype) into d_out. */
+ttie_status ttie_get_direction(ttie_ctx *ctx, void *d_out);
+
+/* Counters of the last ttie_eval_pairs: pair signs decided by the FP32 filter,
+ * by FP64, and by exact arithmetic (host out array of 3). */
+ttie_status ttie_get_filter_stats(ttie_ctx *ctx, int64_t *out3);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TTIE_H */

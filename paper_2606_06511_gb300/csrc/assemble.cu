@@ -1,0 +1,514 @@
+// Assembly of the PSD Hessian and gradient into 3x3 block CSR, and the PCG solve.
+//
+// Per intersecting pair with a = t_c^0, b = t_c^1, u = grad a, v = grad b:
+//   gradient (Eq. 3)      g  = 2ab (b u + a v)
+//   Hessian (Eq. 4)       H  = 2b^2 uu' + 2a^2 vv' + 4ab (vu' + uv')
+// Eigen-analysis (§1.1): parts 1 and 2 are PSD; part 3 = 4ab(uv' + vu') has the
+// eigenpairs 4ab(u.v +- |u||v|) on u^ +- v^, and on an intersecting pair (ab < 0)
+// only 4ab(u.v - |u||v|) >= 0 survives the projection.  So
+//   H+ = z1 z1' + z2 z2' + z3 z3',  z1 = sqrt2 |b| u,  z2 = sqrt2 |a| v,
+//   z3 = sqrt(2 |ab| |u||v|) (u^ - v^)          (z3 = 0 for DROP_CROSS)
+// and no 18x18 eigen-solve is needed.
+//
+// Assembly: 36 vertex-block keys (row, col) per pair, a stable radix sort, and
+// one thread per distinct key summing its run in sorted order, so both the
+// pattern and the values are deterministic.
+#include "common.cuh"
+
+namespace ttie {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kFacStride = 40;   // [a, b, grad a (18), grad b (18), pad 2]
+constexpr int kZStride = 72;     // [z1 (18), z2 (18), z3 (18), g (18)]
+
+template <typename T>
+__device__ __forceinline__ T block_sum(T v) {
+    __shared__ T sh[32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    T r = T(0);
+    if (w == 0) {
+        r = lane < (int)(blockDim.x >> 5) ? sh[lane] : T(0);
+#pragma unroll
+        for (int o = 16; o; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+    }
+    __syncthreads();
+    return r;
+}
+
+// Deterministic grid sums of N values; the last block to finish runs `fin` on the totals.
+template <int N, typename Fin>
+__device__ __forceinline__ void grid_sums(const double (&v)[N], double *partials, unsigned int *ticket, Fin fin) {
+    __shared__ bool last;
+    double b[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) b[i] = block_sum(v[i]);
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int i = 0; i < N; ++i) partials[(size_t)i * gridDim.x + blockIdx.x] = b[i];
+        __threadfence();
+        last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (last) {
+        double tot[N];
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            double s = 0.0;
+            for (unsigned j = threadIdx.x; j < gridDim.x; j += blockDim.x) s += __ldcg(&partials[(size_t)i * gridDim.x + j]);
+            tot[i] = block_sum(s);
+        }
+        if (threadIdx.x == 0) {
+            fin(tot);
+            *ticket = 0u;
+        }
+    }
+}
+
+__global__ void k_mark_vertices(const int4 *__restrict__ tri4, const int2 *__restrict__ pairs,
+                                const uint32_t *__restrict__ active, const DevScalars *ds, uint32_t *__restrict__ vflag) {
+    const unsigned long long n = ds->n_active;
+    for (unsigned long long k = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; k < n;
+         k += (unsigned long long)gridDim.x * blockDim.x) {
+        int2 pr = pairs[active[k]];
+        int4 a = tri4[pr.x], b = tri4[pr.y];
+        vflag[a.x] = 1; vflag[a.y] = 1; vflag[a.z] = 1;
+        vflag[b.x] = 1; vflag[b.y] = 1; vflag[b.z] = 1;
+    }
+}
+
+__global__ void k_row_vertex(const uint32_t *__restrict__ vflag, const unsigned long long *__restrict__ vrow, int64_t V,
+                             int32_t *__restrict__ row_vertex, DevScalars *ds) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < V; v += (int64_t)gridDim.x * blockDim.x)
+        if (vflag[v]) row_vertex[vrow[v]] = (int32_t)v;
+    if (blockIdx.x == 0 && threadIdx.x == 0) ds->n_rows = vrow[V];
+}
+
+// PSD factors z1, z2, z3 and the gradient of each intersecting pair; trace of H+.
+template <typename T>
+__global__ void k_factors(const T *__restrict__ fac, int psd_mode, T *__restrict__ z, double *partials, DevScalars *ds) {
+    const unsigned long long n = ds->n_active;
+    double tr = 0.0;
+    for (unsigned long long k = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; k < n;
+         k += (unsigned long long)gridDim.x * blockDim.x) {
+        const T *r = fac + k * kFacStride;
+        const T a = r[0], b = r[1];
+        T uu = 0, vv = 0;
+#pragma unroll
+        for (int i = 0; i < 18; ++i) { uu += r[2 + i] * r[2 + i]; vv += r[20 + i] * r[20 + i]; }
+        const T nu = sqrt(uu), nv = sqrt(vv);
+        const T c1 = sqrt(T(2)) * fabs(b), c2 = sqrt(T(2)) * fabs(a);
+        T c3 = T(0), iu = T(0), iv = T(0);
+        if (psd_mode == TTIE_PSD_PER_PART && nu > T(0) && nv > T(0)) {
+            c3 = sqrt(T(2) * fabs(a * b) * nu * nv);
+            iu = T(1) / nu;
+            iv = T(1) / nv;
+        }
+        T *o = z + k * kZStride;
+        double t = 0.0;
+#pragma unroll
+        for (int i = 0; i < 18; ++i) {
+            const T u = r[2 + i], v = r[20 + i];
+            const T z1 = c1 * u, z2 = c2 * v, z3 = c3 * (u * iu - v * iv);
+            o[i] = z1;
+            o[18 + i] = z2;
+            o[36 + i] = z3;
+            o[54 + i] = T(2) * a * b * (b * u + a * v);
+            t += (double)z1 * z1 + (double)z2 * z2 + (double)z3 * z3;
+        }
+        tr += t;
+    }
+    double v[1] = {tr};
+    grid_sums<1>(v, partials, &ds->done_counter[1], [&](const double *tot) { ds->trace = tot[0]; });
+}
+
+__device__ __forceinline__ int vid(int4 a, int4 b, int r) {
+    return r == 0 ? a.x : r == 1 ? a.y : r == 2 ? a.z : r == 3 ? b.x : r == 4 ? b.y : b.z;
+}
+
+__global__ void k_block_keys(const int4 *__restrict__ tri4, const int2 *__restrict__ pairs,
+                             const uint32_t *__restrict__ active, const unsigned long long *__restrict__ vrow,
+                             const DevScalars *ds, unsigned long long *__restrict__ key, uint32_t *__restrict__ val) {
+    const unsigned long long n = ds->n_active, nr = ds->n_rows;
+    for (unsigned long long k = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; k < n;
+         k += (unsigned long long)gridDim.x * blockDim.x) {
+        int2 pr = pairs[active[k]];
+        int4 a = tri4[pr.x], b = tri4[pr.y];
+        unsigned long long row[6];
+#pragma unroll
+        for (int r = 0; r < 6; ++r) row[r] = vrow[vid(a, b, r)];
+#pragma unroll
+        for (int r = 0; r < 6; ++r)
+#pragma unroll
+            for (int c = 0; c < 6; ++c) {
+                key[k * 36 + r * 6 + c] = row[r] * nr + row[c];
+                val[k * 36 + r * 6 + c] = (uint32_t)(k * 36 + r * 6 + c);
+            }
+    }
+}
+
+__global__ void k_run_flags(const unsigned long long *__restrict__ key, int64_t n, uint32_t *__restrict__ flag) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        flag[i] = (i == 0 || key[i] != key[i - 1]) ? 1u : 0u;
+}
+
+__global__ void k_run_starts(const uint32_t *__restrict__ flag, const unsigned long long *__restrict__ pos, int64_t n,
+                             uint32_t *__restrict__ run_start, DevScalars *ds) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        if (flag[i]) run_start[pos[i]] = (uint32_t)i;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        const unsigned long long nb = pos[n];
+        run_start[nb] = (uint32_t)n;
+        ds->nnzb = nb;
+    }
+}
+
+// One thread per stored block: pattern, then the sum over its run in sorted order.
+template <typename T>
+__global__ void k_block_values(const unsigned long long *__restrict__ key, const uint32_t *__restrict__ val,
+                               const uint32_t *__restrict__ run_start, const T *__restrict__ z, const DevScalars *ds,
+                               int32_t *__restrict__ row_ptr, int32_t *__restrict__ col_idx, T *__restrict__ bval,
+                               T *__restrict__ grad_rows, const int32_t *__restrict__ row_vertex,
+                               T *__restrict__ grad_full) {
+    const unsigned long long nb = ds->nnzb, nr = ds->n_rows;
+    for (unsigned long long bi = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; bi < nb;
+         bi += (unsigned long long)gridDim.x * blockDim.x) {
+        const uint32_t s = run_start[bi], e = run_start[bi + 1];
+        const unsigned long long kk = key[s];
+        const unsigned long long row = kk / nr, col = kk - row * nr;
+        col_idx[bi] = (int32_t)col;
+        if (bi == 0 || key[run_start[bi - 1]] / nr != row) row_ptr[row] = (int32_t)bi;
+        if (bi == nb - 1) row_ptr[nr] = (int32_t)nb;
+        T m[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) m[i] = T(0);
+        T g0 = 0, g1 = 0, g2 = 0;
+        for (uint32_t i = s; i < e; ++i) {
+            const uint32_t v = val[i];
+            const uint32_t pk = v / 36, rc = v - pk * 36, r = rc / 6, c = rc - r * 6;
+            const T *zp = z + (size_t)pk * kZStride;
+#pragma unroll
+            for (int t = 0; t < 3; ++t) {
+                const T *zt = zp + 18 * t;
+                const T x0 = zt[3 * r], x1 = zt[3 * r + 1], x2 = zt[3 * r + 2];
+                const T y0 = zt[3 * c], y1 = zt[3 * c + 1], y2 = zt[3 * c + 2];
+                m[0] += x0 * y0; m[1] += x0 * y1; m[2] += x0 * y2;
+                m[3] += x1 * y0; m[4] += x1 * y1; m[5] += x1 * y2;
+                m[6] += x2 * y0; m[7] += x2 * y1; m[8] += x2 * y2;
+            }
+            if (row == col) {
+                g0 += zp[54 + 3 * r]; g1 += zp[54 + 3 * r + 1]; g2 += zp[54 + 3 * r + 2];
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 9; ++i) bval[bi * 9 + i] = m[i];
+        if (row == col) {
+            grad_rows[row * 3] = g0; grad_rows[row * 3 + 1] = g1; grad_rows[row * 3 + 2] = g2;
+            if (grad_full) {
+                const int64_t v = row_vertex[row];
+                grad_full[v * 3] = g0; grad_full[v * 3 + 1] = g1; grad_full[v * 3 + 2] = g2;
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------- PCG
+template <typename T>
+__device__ __forceinline__ void inv3(const T *m, T mu, T *o) {
+    const double a = (double)m[0] + mu, b = m[1], c = m[2], d = m[3], e = (double)m[4] + mu, f = m[5], g = m[6], h = m[7],
+                 i = (double)m[8] + mu;
+    const double A = e * i - f * h, B = -(d * i - f * g), C = d * h - e * g;
+    const double det = a * A + b * B + c * C;
+    const double id = det != 0.0 ? 1.0 / det : 0.0;
+    o[0] = (T)(A * id); o[1] = (T)(-(b * i - c * h) * id); o[2] = (T)((b * f - c * e) * id);
+    o[3] = (T)(B * id); o[4] = (T)((a * i - c * g) * id); o[5] = (T)(-(a * f - c * d) * id);
+    o[6] = (T)(C * id); o[7] = (T)(-(a * h - b * g) * id); o[8] = (T)((a * e - b * d) * id);
+}
+
+template <typename T>
+__global__ void k_pcg_setup(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col_idx,
+                            const T *__restrict__ bval, double mu_rel, T *__restrict__ dinv, const T *__restrict__ rhs,
+                            T *__restrict__ x, T *__restrict__ r, T *__restrict__ z, T *__restrict__ p, double *partials,
+                            DevScalars *ds) {
+    const unsigned long long nr = ds->n_rows;
+    const T mu = (T)(nr ? mu_rel * ds->trace / (3.0 * (double)nr) : 0.0);
+    double rz = 0.0, rr = 0.0;
+    for (unsigned long long row = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; row < nr;
+         row += (unsigned long long)gridDim.x * blockDim.x) {
+        const T zero9[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+        const T *diag = zero9;
+        for (int b = row_ptr[row]; b < row_ptr[row + 1]; ++b)
+            if ((unsigned long long)col_idx[b] == row) { diag = bval + (size_t)b * 9; break; }
+        T di[9];
+        inv3(diag, mu, di);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) dinv[row * 9 + i] = di[i];
+        const T r0 = rhs[row * 3], r1 = rhs[row * 3 + 1], r2 = rhs[row * 3 + 2];
+        const T z0 = di[0] * r0 + di[1] * r1 + di[2] * r2, z1 = di[3] * r0 + di[4] * r1 + di[5] * r2,
+                z2 = di[6] * r0 + di[7] * r1 + di[8] * r2;
+        x[row * 3] = 0; x[row * 3 + 1] = 0; x[row * 3 + 2] = 0;
+        r[row * 3] = r0; r[row * 3 + 1] = r1; r[row * 3 + 2] = r2;
+        z[row * 3] = z0; z[row * 3 + 1] = z1; z[row * 3 + 2] = z2;
+        p[row * 3] = z0; p[row * 3 + 1] = z1; p[row * 3 + 2] = z2;
+        rz += (double)r0 * z0 + (double)r1 * z1 + (double)r2 * z2;
+        rr += (double)r0 * r0 + (double)r1 * r1 + (double)r2 * r2;
+    }
+    double v[2] = {rz, rr};
+    grid_sums<2>(v, partials, &ds->done_counter[2], [&](const double *t) {
+        ds->mu = (double)mu;
+        ds->red[0] = t[0];   // r.z
+        ds->red[1] = t[1];   // r0.r0
+        ds->red[4] = t[1];   // r.r
+        ds->pcg_iters = 0;
+        ds->pcg_done = (t[1] == 0.0) ? 1 : 0;
+    });
+}
+
+// q = (H + mu I) p and p.q
+template <typename T>
+__global__ void k_pcg_spmv(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col_idx,
+                           const T *__restrict__ bval, const T *__restrict__ p, T *__restrict__ q, double *partials,
+                           DevScalars *ds) {
+    if (ds->pcg_done) return;
+    const unsigned long long nr = ds->n_rows;
+    const T mu = (T)ds->mu;
+    double pq = 0.0;
+    for (unsigned long long row = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; row < nr;
+         row += (unsigned long long)gridDim.x * blockDim.x) {
+        T y0 = mu * p[row * 3], y1 = mu * p[row * 3 + 1], y2 = mu * p[row * 3 + 2];
+        for (int b = row_ptr[row]; b < row_ptr[row + 1]; ++b) {
+            const T *m = bval + (size_t)b * 9;
+            const int c = col_idx[b];
+            const T p0 = p[c * 3], p1 = p[c * 3 + 1], p2 = p[c * 3 + 2];
+            y0 += m[0] * p0 + m[1] * p1 + m[2] * p2;
+            y1 += m[3] * p0 + m[4] * p1 + m[5] * p2;
+            y2 += m[6] * p0 + m[7] * p1 + m[8] * p2;
+        }
+        q[row * 3] = y0; q[row * 3 + 1] = y1; q[row * 3 + 2] = y2;
+        pq += (double)p[row * 3] * y0 + (double)p[row * 3 + 1] * y1 + (double)p[row * 3 + 2] * y2;
+    }
+    double v[1] = {pq};
+    grid_sums<1>(v, partials, &ds->done_counter[3], [&](const double *t) { ds->red[2] = t[0]; });
+}
+
+// x += alpha p, r -= alpha q, z = M r; r.z and r.r; then beta and the stopping test.
+template <typename T>
+__global__ void k_pcg_update(const T *__restrict__ dinv, const T *__restrict__ p, const T *__restrict__ q, T *__restrict__ x,
+                             T *__restrict__ r, T *__restrict__ z, double rtol2, double *partials, DevScalars *ds) {
+    if (ds->pcg_done) return;
+    const unsigned long long nr = ds->n_rows;
+    const double pq = ds->red[2];
+    const T alpha = (T)(pq != 0.0 ? ds->red[0] / pq : 0.0);
+    double rz = 0.0, rr = 0.0;
+    for (unsigned long long row = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; row < nr;
+         row += (unsigned long long)gridDim.x * blockDim.x) {
+        T rv[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            x[row * 3 + i] += alpha * p[row * 3 + i];
+            rv[i] = r[row * 3 + i] - alpha * q[row * 3 + i];
+            r[row * 3 + i] = rv[i];
+        }
+        const T *di = dinv + row * 9;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            const T zi = di[3 * i] * rv[0] + di[3 * i + 1] * rv[1] + di[3 * i + 2] * rv[2];
+            z[row * 3 + i] = zi;
+            rz += (double)rv[i] * zi;
+            rr += (double)rv[i] * rv[i];
+        }
+    }
+    double v[2] = {rz, rr};
+    grid_sums<2>(v, partials, &ds->done_counter[4], [&](const double *t) {
+        const double rz_old = ds->red[0];
+        ds->red[3] = rz_old != 0.0 ? t[0] / rz_old : 0.0;   // beta
+        ds->red[0] = t[0];
+        ds->red[4] = t[1];
+        ds->pcg_iters += 1;
+        if (t[1] <= rtol2 * ds->red[1] || !(pq > 0.0) || !isfinite(t[1])) ds->pcg_done = 1;
+    });
+}
+
+template <typename T>
+__global__ void k_pcg_dir(const T *__restrict__ z, T *__restrict__ p, const DevScalars *ds) {
+    if (ds->pcg_done) return;
+    const unsigned long long n3 = ds->n_rows * 3;
+    const T beta = (T)ds->red[3];
+    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n3;
+         i += (unsigned long long)gridDim.x * blockDim.x)
+        p[i] = z[i] + beta * p[i];
+}
+
+template <typename T>
+__global__ void k_axpy_positions(const vec4_t<T> *__restrict__ x, const T *__restrict__ d, T alpha, int64_t V,
+                                 vec4_t<T> *__restrict__ out) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < V; v += (int64_t)gridDim.x * blockDim.x) {
+        vec4_t<T> a = x[v];
+        a.x += alpha * d[v * 3]; a.y += alpha * d[v * 3 + 1]; a.z += alpha * d[v * 3 + 2];
+        out[v] = a;
+    }
+}
+
+template <typename T>
+__global__ void k_scatter_rows(const T *__restrict__ d_rows, const int32_t *__restrict__ row_vertex, const DevScalars *ds,
+                               T *__restrict__ d_full) {
+    const unsigned long long nr = ds->n_rows;
+    for (unsigned long long r = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; r < nr;
+         r += (unsigned long long)gridDim.x * blockDim.x) {
+        const int64_t v = row_vertex[r];
+        d_full[v * 3] = d_rows[r * 3]; d_full[v * 3 + 1] = d_rows[r * 3 + 1]; d_full[v * 3 + 2] = d_rows[r * 3 + 2];
+    }
+}
+
+template <typename T>
+__global__ void k_update_positions(T *__restrict__ x, int stride, const T *__restrict__ d, T alpha, int64_t V) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < V; v += (int64_t)gridDim.x * blockDim.x) {
+        x[v * stride] += alpha * d[v * 3];
+        x[v * stride + 1] += alpha * d[v * 3 + 1];
+        x[v * stride + 2] += alpha * d[v * 3 + 2];
+    }
+}
+
+int bits_for(unsigned long long v) {
+    int b = 0;
+    while (b < 64 && (v >> b) != 0ull) ++b;
+    return b;
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t assemble_system(Ctx &c, T *grad_full) {
+    const int64_t n_act = c.n_active;
+    const int64_t V = c.V;
+    TTIE_CUDA_TRY(ensure(c, c.vflag, (size_t)V * 4));
+    TTIE_CUDA_TRY(ensure(c, c.vrow, (size_t)(V + 1) * 8));
+    TTIE_CUDA_TRY(cudaMemsetAsync(c.vflag.p, 0, (size_t)V * 4, c.stream));
+    const int4 *tri4 = (const int4 *)c.tri4.p;
+    const int2 *pairs = (const int2 *)c.cand.p;
+    const uint32_t *active = (const uint32_t *)c.active.p;
+    const unsigned gA = grid_for(n_act, kThreads);
+    k_mark_vertices<<<gA, kThreads, 0, c.stream>>>(tri4, pairs, active, c.ds, (uint32_t *)c.vflag.p);
+    TTIE_CUDA_TRY(scan_u32_u64(c, (const uint32_t *)c.vflag.p, (unsigned long long *)c.vrow.p, V));
+    TTIE_CUDA_TRY(ensure(c, c.row_vertex, (size_t)(V > 0 ? V : 1) * 4));
+    k_row_vertex<<<grid_for(V, kThreads), kThreads, 0, c.stream>>>((const uint32_t *)c.vflag.p,
+                                                                  (const unsigned long long *)c.vrow.p, V,
+                                                                  (int32_t *)c.row_vertex.p, c.ds);
+    TTIE_CUDA_TRY(ensure(c, c.zfac, (size_t)(n_act > 0 ? n_act : 1) * kZStride * sizeof(T)));
+    TTIE_CUDA_TRY(ensure(c, c.partials, (size_t)kNumSMs * 16 * 4 * sizeof(double)));
+    k_factors<T><<<grid_for(n_act, 128, kNumSMs * 8), 128, 0, c.stream>>>((const T *)c.fac.p, c.prm.psd_mode,
+                                                                        (T *)c.zfac.p, (double *)c.partials.p, c.ds);
+    const int64_t nk = n_act * 36;
+    TTIE_CUDA_TRY(ensure(c, c.bkey, (size_t)(nk > 0 ? nk : 1) * 8));
+    TTIE_CUDA_TRY(ensure(c, c.bkey2, (size_t)(nk > 0 ? nk : 1) * 8));
+    TTIE_CUDA_TRY(ensure(c, c.bval, (size_t)(nk > 0 ? nk : 1) * 4));
+    TTIE_CUDA_TRY(ensure(c, c.bval2, (size_t)(nk > 0 ? nk : 1) * 4));
+    TTIE_CUDA_TRY(ensure(c, c.bflag, (size_t)(nk > 0 ? nk : 1) * 4));
+    TTIE_CUDA_TRY(ensure(c, c.run_start, (size_t)(nk + 1) * 8));
+    // the row count decides the key width: one sync
+    TTIE_CUDA_TRY(cudaMemcpyAsync(&c.hs->n_rows, &c.ds->n_rows, 8, cudaMemcpyDeviceToHost, c.stream));
+    TTIE_CUDA_TRY(cudaStreamSynchronize(c.stream));
+    const int64_t nr = (int64_t)c.hs->n_rows;
+    c.n_rows = nr;
+    k_block_keys<<<gA, kThreads, 0, c.stream>>>(tri4, pairs, active, (const unsigned long long *)c.vrow.p, c.ds,
+                                                (unsigned long long *)c.bkey.p, (uint32_t *)c.bval.p);
+    TTIE_CUDA_TRY(cudaGetLastError());
+    const int kbits = bits_for((unsigned long long)nr * (unsigned long long)nr);
+    TTIE_CUDA_TRY(radix_sort(c, (unsigned long long *)c.bkey.p, (uint32_t *)c.bval.p, (unsigned long long *)c.bkey2.p,
+                             (uint32_t *)c.bval2.p, nk, kbits));
+    // run boundaries: flags -> positions (bkey2 reused as the u64 scan output)
+    k_run_flags<<<grid_for(nk, kThreads), kThreads, 0, c.stream>>>((const unsigned long long *)c.bkey.p, nk,
+                                                                  (uint32_t *)c.bflag.p);
+    TTIE_CUDA_TRY(ensure(c, c.gtmp, (size_t)(nk + 1) * 8));
+    TTIE_CUDA_TRY(scan_u32_u64(c, (const uint32_t *)c.bflag.p, (unsigned long long *)c.gtmp.p, nk));
+    k_run_starts<<<grid_for(nk, kThreads), kThreads, 0, c.stream>>>((const uint32_t *)c.bflag.p,
+                                                                   (const unsigned long long *)c.gtmp.p, nk,
+                                                                   (uint32_t *)c.run_start.p, c.ds);
+    TTIE_CUDA_TRY(cudaMemcpyAsync(&c.hs->nnzb, &c.ds->nnzb, 8, cudaMemcpyDeviceToHost, c.stream));
+    TTIE_CUDA_TRY(cudaStreamSynchronize(c.stream));
+    const int64_t nnzb = nk > 0 ? (int64_t)c.hs->nnzb : 0;
+    c.nnzb = nnzb;
+    TTIE_CUDA_TRY(ensure(c, c.row_ptr, (size_t)(nr + 1) * 4));
+    TTIE_CUDA_TRY(ensure(c, c.col_idx, (size_t)(nnzb > 0 ? nnzb : 1) * 4));
+    TTIE_CUDA_TRY(ensure(c, c.bsr_val, (size_t)(nnzb > 0 ? nnzb : 1) * 9 * sizeof(T)));
+    TTIE_CUDA_TRY(ensure(c, c.rhs, (size_t)(nr > 0 ? nr : 1) * 3 * sizeof(T)));
+    if (grad_full) TTIE_CUDA_TRY(cudaMemsetAsync(grad_full, 0, (size_t)V * 3 * sizeof(T), c.stream));
+    if (nk == 0) {
+        TTIE_CUDA_TRY(cudaMemsetAsync(c.row_ptr.p, 0, 4, c.stream));
+        return cudaGetLastError();
+    }
+    k_block_values<T><<<grid_for(nnzb, 128, kNumSMs * 16), 128, 0, c.stream>>>(
+        (const unsigned long long *)c.bkey.p, (const uint32_t *)c.bval.p, (const uint32_t *)c.run_start.p,
+        (const T *)c.zfac.p, c.ds, (int32_t *)c.row_ptr.p, (int32_t *)c.col_idx.p, (T *)c.bsr_val.p, (T *)c.rhs.p,
+        (const int32_t *)c.row_vertex.p, grad_full);
+    return cudaGetLastError();
+}
+template cudaError_t assemble_system<float>(Ctx &, float *);
+template cudaError_t assemble_system<double>(Ctx &, double *);
+
+template <typename T>
+cudaError_t pcg_solve(Ctx &c, const T *rhs, T *out, double rtol, int max_it) {
+    const int64_t nr = c.n_rows;
+    TTIE_CUDA_TRY(ensure(c, c.dinv, (size_t)(nr > 0 ? nr : 1) * 9 * sizeof(T)));
+    TTIE_CUDA_TRY(ensure(c, c.pcg_r, (size_t)(nr > 0 ? nr : 1) * 3 * sizeof(T)));
+    TTIE_CUDA_TRY(ensure(c, c.pcg_z, (size_t)(nr > 0 ? nr : 1) * 3 * sizeof(T)));
+    TTIE_CUDA_TRY(ensure(c, c.pcg_p, (size_t)(nr > 0 ? nr : 1) * 3 * sizeof(T)));
+    TTIE_CUDA_TRY(ensure(c, c.pcg_q, (size_t)(nr > 0 ? nr : 1) * 3 * sizeof(T)));
+    TTIE_CUDA_TRY(ensure(c, c.partials, (size_t)kNumSMs * 16 * 4 * sizeof(double)));
+    double *part = (double *)c.partials.p;
+    const unsigned g = grid_for(nr, kThreads, kNumSMs * 4);
+    k_pcg_setup<T><<<g, kThreads, 0, c.stream>>>((const int32_t *)c.row_ptr.p, (const int32_t *)c.col_idx.p,
+                                                 (const T *)c.bsr_val.p, c.prm.mu_rel, (T *)c.dinv.p, rhs, out,
+                                                 (T *)c.pcg_r.p, (T *)c.pcg_z.p, (T *)c.pcg_p.p, part, c.ds);
+    TTIE_CUDA_TRY(cudaGetLastError());
+    const double rtol2 = rtol * rtol;
+    for (int it = 0; it < max_it; ++it) {
+        k_pcg_spmv<T><<<g, kThreads, 0, c.stream>>>((const int32_t *)c.row_ptr.p, (const int32_t *)c.col_idx.p,
+                                                    (const T *)c.bsr_val.p, (const T *)c.pcg_p.p, (T *)c.pcg_q.p, part,
+                                                    c.ds);
+        k_pcg_update<T><<<g, kThreads, 0, c.stream>>>((const T *)c.dinv.p, (const T *)c.pcg_p.p, (const T *)c.pcg_q.p, out,
+                                                      (T *)c.pcg_r.p, (T *)c.pcg_z.p, rtol2, part, c.ds);
+        k_pcg_dir<T><<<g, kThreads, 0, c.stream>>>((const T *)c.pcg_z.p, (T *)c.pcg_p.p, c.ds);
+        if ((it & 15) == 15) {
+            TTIE_CUDA_TRY(cudaMemcpyAsync(&c.hs->pcg_done, &c.ds->pcg_done, 4, cudaMemcpyDeviceToHost, c.stream));
+            TTIE_CUDA_TRY(cudaStreamSynchronize(c.stream));
+            if (c.hs->pcg_done) break;
+        }
+    }
+    return cudaGetLastError();
+}
+template cudaError_t pcg_solve<float>(Ctx &, const float *, float *, double, int);
+template cudaError_t pcg_solve<double>(Ctx &, const double *, double *, double, int);
+
+template <typename T>
+cudaError_t axpy_positions(Ctx &c, const vec4_t<T> *x, const T *d, T alpha, vec4_t<T> *out) {
+    k_axpy_positions<T><<<grid_for(c.V, kThreads), kThreads, 0, c.stream>>>(x, d, alpha, c.V, out);
+    return cudaGetLastError();
+}
+template cudaError_t axpy_positions<float>(Ctx &, const float4 *, const float *, float, float4 *);
+template cudaError_t axpy_positions<double>(Ctx &, const dvec4 *, const double *, double, dvec4 *);
+
+template <typename T>
+cudaError_t scatter_direction(Ctx &c, const T *d_rows, T *d_full) {
+    TTIE_CUDA_TRY(cudaMemsetAsync(d_full, 0, (size_t)c.V * 3 * sizeof(T), c.stream));
+    k_scatter_rows<T><<<grid_for(c.n_rows, kThreads), kThreads, 0, c.stream>>>(d_rows, (const int32_t *)c.row_vertex.p,
+                                                                              c.ds, d_full);
+    return cudaGetLastError();
+}
+template cudaError_t scatter_direction<float>(Ctx &, const float *, float *);
+template cudaError_t scatter_direction<double>(Ctx &, const double *, double *);
+
+template <typename T>
+cudaError_t update_positions(Ctx &c, T *x, int stride, const T *d_full, T alpha) {
+    k_update_positions<T><<<grid_for(c.V, kThreads), kThreads, 0, c.stream>>>(x, stride, d_full, alpha, c.V);
+    return cudaGetLastError();
+}
+template cudaError_t update_positions<float>(Ctx &, float *, int, const float *, float);
+template cudaError_t update_positions<double>(Ctx &, double *, int, const double *, double);
+
+}  // namespace ttie

@@ -1,0 +1,463 @@
+// Broad phase: candidate triangle pairs whose closed bounding boxes overlap.
+//
+// §1.2 accelerates the pair tests with a spatial structure that "eliminates
+// redundant computations" (spatial hashing there).  Here: a linear BVH built
+// from 63-bit Morton codes (Karras' radix-tree construction), refitted
+// bottom-up, then traversed once per leaf to count and once to write, so the
+// pair list comes out in a deterministic order without a global sort.
+// Topologically adjacent pairs (a shared vertex index, §1) are dropped.
+#include "common.cuh"
+
+namespace ttie {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kStack = 96;
+
+__device__ __forceinline__ unsigned long long ordered_bits(double v) {
+    unsigned long long u = (unsigned long long)__double_as_longlong(v);
+    return (u >> 63) ? ~u : (u | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double from_ordered(unsigned long long u) {
+    u = (u >> 63) ? (u & 0x7fffffffffffffffull) : ~u;
+    return __longlong_as_double((long long)u);
+}
+
+template <typename T> __device__ __forceinline__ bool finite3(T a, T b, T c) { return isfinite(a) && isfinite(b) && isfinite(c); }
+
+template <typename T>
+__global__ void k_pack_positions(const T *__restrict__ x, int stride, int64_t V, vec4_t<T> *__restrict__ out,
+                                 DevScalars *ds) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < V; i += (int64_t)gridDim.x * blockDim.x) {
+        T a = x[i * stride], b = x[i * stride + 1], c = x[i * stride + 2];
+        vec4_t<T> v;
+        v.x = a; v.y = b; v.z = c; v.w = T(0);
+        out[i] = v;
+        if (!finite3(a, b, c)) atomicOr(&ds->err, ERR_NONFINITE);
+    }
+}
+
+__global__ void k_pack_topology(const int32_t *__restrict__ tri, const int32_t *__restrict__ grp_in, int64_t F,
+                                int64_t V, int4 *__restrict__ tri4, int32_t *__restrict__ grp, DevScalars *ds) {
+    for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < F; f += (int64_t)gridDim.x * blockDim.x) {
+        int a = tri[3 * f], b = tri[3 * f + 1], c = tri[3 * f + 2];
+        if (a < 0 || b < 0 || c < 0 || a >= V || b >= V || c >= V) {
+            atomicOr(&ds->err, ERR_BAD_INDEX);
+            a = b = c = 0;
+        }
+        tri4[f] = make_int4(a, b, c, 0);
+        if (grp_in) {
+            int g = grp_in[f];
+            if (g < 0 || g >= (1 << 20)) {
+                atomicOr(&ds->err, ERR_BAD_INDEX);
+                g = 0;
+            }
+            grp[f] = g;
+            atomicMax(&ds->max_group, g);
+        }
+    }
+}
+
+__global__ void k_init_bounds(DevScalars *ds) {
+    if (threadIdx.x < 3) {
+        ds->bounds_lo[threadIdx.x] = ~0ull;
+        ds->bounds_hi[threadIdx.x] = 0ull;
+    }
+}
+
+template <typename T> __device__ __forceinline__ T tmin(T a, T b) { return a < b ? a : b; }
+template <typename T> __device__ __forceinline__ T tmax(T a, T b) { return a > b ? a : b; }
+
+// Box of each triangle (over the vertices at x0 and, when x1 is given, also at x1:
+// the box swept by a straight-line motion) and the scene bounds of the box centres.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_tri_boxes(const vec4_t<T> *__restrict__ x0, const vec4_t<T> *__restrict__ x1,
+                                                        const int4 *__restrict__ tri4, int64_t F, Box<T> *__restrict__ box,
+                                                        DevScalars *ds) {
+    double clo[3] = {1e300, 1e300, 1e300}, chi[3] = {-1e300, -1e300, -1e300};
+    for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < F; f += (int64_t)gridDim.x * blockDim.x) {
+        int4 t = tri4[f];
+        vec4_t<T> a = x0[t.x], b = x0[t.y], c = x0[t.z];
+        Box<T> bx;
+        bx.lo.x = tmin(a.x, tmin(b.x, c.x)); bx.lo.y = tmin(a.y, tmin(b.y, c.y)); bx.lo.z = tmin(a.z, tmin(b.z, c.z));
+        bx.hi.x = tmax(a.x, tmax(b.x, c.x)); bx.hi.y = tmax(a.y, tmax(b.y, c.y)); bx.hi.z = tmax(a.z, tmax(b.z, c.z));
+        if (x1) {
+            a = x1[t.x]; b = x1[t.y]; c = x1[t.z];
+            bx.lo.x = tmin(bx.lo.x, tmin(a.x, tmin(b.x, c.x)));
+            bx.lo.y = tmin(bx.lo.y, tmin(a.y, tmin(b.y, c.y)));
+            bx.lo.z = tmin(bx.lo.z, tmin(a.z, tmin(b.z, c.z)));
+            bx.hi.x = tmax(bx.hi.x, tmax(a.x, tmax(b.x, c.x)));
+            bx.hi.y = tmax(bx.hi.y, tmax(a.y, tmax(b.y, c.y)));
+            bx.hi.z = tmax(bx.hi.z, tmax(a.z, tmax(b.z, c.z)));
+        }
+        bx.lo.w = T(0);
+        bx.hi.w = T(0);
+        box[f] = bx;
+        double cx = 0.5 * ((double)bx.lo.x + (double)bx.hi.x), cy = 0.5 * ((double)bx.lo.y + (double)bx.hi.y),
+               cz = 0.5 * ((double)bx.lo.z + (double)bx.hi.z);
+        clo[0] = fmin(clo[0], cx); clo[1] = fmin(clo[1], cy); clo[2] = fmin(clo[2], cz);
+        chi[0] = fmax(chi[0], cx); chi[1] = fmax(chi[1], cy); chi[2] = fmax(chi[2], cz);
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        for (int o = 16; o; o >>= 1) {
+            clo[k] = fmin(clo[k], __shfl_xor_sync(0xffffffffu, clo[k], o));
+            chi[k] = fmax(chi[k], __shfl_xor_sync(0xffffffffu, chi[k], o));
+        }
+    }
+    if ((threadIdx.x & 31) == 0 && clo[0] <= chi[0]) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            atomicMin(&ds->bounds_lo[k], ordered_bits(clo[k]));
+            atomicMax(&ds->bounds_hi[k], ordered_bits(chi[k]));
+        }
+    }
+}
+
+__device__ __forceinline__ unsigned long long spread3(unsigned long long v) {
+    // insert two zero bits between the low 21 bits of v
+    v &= 0x1fffffull;
+    v = (v | v << 32) & 0x1f00000000ffffull;
+    v = (v | v << 16) & 0x1f0000ff0000ffull;
+    v = (v | v << 8) & 0x100f00f00f00f00full;
+    v = (v | v << 4) & 0x10c30c30c30c30c3ull;
+    v = (v | v << 2) & 0x1249249249249249ull;
+    return v;
+}
+
+template <typename T>
+__global__ void k_morton(const Box<T> *__restrict__ box, int64_t F, const int32_t *__restrict__ grp, int group_bits,
+                         const DevScalars *ds, unsigned long long *__restrict__ key, uint32_t *__restrict__ perm) {
+    const int b = (63 - group_bits) / 3;
+    const double scale = (double)((1ull << b) - 1);
+    double lo[3], ext[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        lo[k] = from_ordered(ds->bounds_lo[k]);
+        double hi = from_ordered(ds->bounds_hi[k]);
+        ext[k] = hi > lo[k] ? hi - lo[k] : 1.0;
+    }
+    for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < F; f += (int64_t)gridDim.x * blockDim.x) {
+        Box<T> bx = box[f];
+        double c[3] = {0.5 * ((double)bx.lo.x + (double)bx.hi.x), 0.5 * ((double)bx.lo.y + (double)bx.hi.y),
+                       0.5 * ((double)bx.lo.z + (double)bx.hi.z)};
+        unsigned long long q[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            double u = (c[k] - lo[k]) / ext[k];
+            u = fmin(fmax(u, 0.0), 1.0);
+            q[k] = (unsigned long long)(u * scale);
+        }
+        unsigned long long m = (spread3(q[0]) << 2) | (spread3(q[1]) << 1) | spread3(q[2]);
+        if (group_bits) m |= (unsigned long long)grp[f] << (3 * b);
+        key[f] = m;
+        perm[f] = (uint32_t)f;
+    }
+}
+
+__global__ void k_leaf_group(const uint32_t *__restrict__ perm, const int32_t *__restrict__ grp, int64_t n,
+                             int32_t *__restrict__ leaf_group) {
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x)
+        leaf_group[s] = grp[perm[s]];
+}
+
+__global__ void k_group_ranges(const int32_t *__restrict__ lg, int64_t n, int2 *__restrict__ range) {
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x) {
+        int g = lg[s];
+        if (s == 0 || lg[s - 1] != g) range[g].x = (int)s;
+        if (s == n - 1 || lg[s + 1] != g) range[g].y = (int)s;
+    }
+}
+
+__global__ void k_fill_int2(int2 *p, int64_t n, int2 v) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) p[i] = v;
+}
+
+// Length of the common prefix of sorted keys i and j; ties broken by the index.
+__device__ __forceinline__ int delta(const unsigned long long *__restrict__ k, int n, int i, int j) {
+    if (j < 0 || j >= n) return -1;
+    unsigned long long a = k[i], b = k[j];
+    if (a == b) return 64 + __clz((unsigned)(i ^ j));
+    return __clzll(a ^ b);
+}
+
+// Internal node i of the radix tree over n sorted keys (Karras 2012).  Leaves are nodes
+// n-1 .. 2n-2; the root is internal node 0.
+__global__ void k_karras(const unsigned long long *__restrict__ key, int n, int2 *__restrict__ child,
+                         int *__restrict__ parent, int2 *__restrict__ range) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n - 1; i += gridDim.x * blockDim.x) {
+        const int d = (delta(key, n, i, i + 1) - delta(key, n, i, i - 1)) >= 0 ? 1 : -1;
+        const int dmin = delta(key, n, i, i - d);
+        int lmax = 2;
+        while (delta(key, n, i, i + lmax * d) > dmin) lmax <<= 1;
+        int l = 0;
+        for (int t = lmax >> 1; t >= 1; t >>= 1)
+            if (delta(key, n, i, i + (l + t) * d) > dmin) l += t;
+        const int j = i + l * d;
+        const int dnode = delta(key, n, i, j);
+        int s = 0, t = l;
+        do {
+            t = (t + 1) >> 1;
+            if (delta(key, n, i, i + (s + t) * d) > dnode) s += t;
+        } while (t > 1);
+        const int gamma = i + s * d + (d < 0 ? -1 : 0);
+        const int lo = min(i, j), hi = max(i, j);
+        const int left = (lo == gamma) ? (n - 1 + gamma) : gamma;
+        const int right = (hi == gamma + 1) ? (n - 1 + gamma + 1) : gamma + 1;
+        child[i] = make_int2(left, right);
+        parent[left] = i;
+        parent[right] = i;
+        range[i] = make_int2(lo, hi);
+        if (i == 0) parent[0] = -1;
+    }
+}
+
+template <typename T>
+__global__ void k_leaf_boxes(const Box<T> *__restrict__ tbox, const uint32_t *__restrict__ perm, int n,
+                             Box<T> *__restrict__ node_box, int2 *__restrict__ range) {
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
+        node_box[n - 1 + s] = tbox[perm[s]];
+        range[n - 1 + s] = make_int2(s, s);
+    }
+}
+
+template <typename T> __device__ __forceinline__ vec4_t<T> ld_cg(const vec4_t<T> *p);
+template <> __device__ __forceinline__ float4 ld_cg<float>(const float4 *p) { return __ldcg(p); }
+template <> __device__ __forceinline__ dvec4 ld_cg<double>(const dvec4 *p) {
+    const double2 *q = reinterpret_cast<const double2 *>(p);
+    double2 a = __ldcg(q), b = __ldcg(q + 1);
+    dvec4 r;
+    r.x = a.x; r.y = a.y; r.z = b.x; r.w = b.y;
+    return r;
+}
+
+// Bottom-up refit: the second child to arrive at a node writes its box and moves up.
+template <typename T>
+__global__ void k_refit(int n, const int *__restrict__ parent, const int2 *__restrict__ child, Box<T> *node_box,
+                        unsigned int *visit, DevScalars *ds) {
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
+        int node = parent[n - 1 + s];
+        for (int level = 0; node >= 0; ++level) {
+            if (level > 2 * kStack) {   // deeper than any valid tree: malformed, stop
+                atomicOr(&ds->err, ERR_STACK);
+                break;
+            }
+            __threadfence();
+            if (atomicAdd(&visit[node], 1u) == 0u) break;
+            int2 ch = child[node];
+            vec4_t<T> alo = ld_cg<T>(&node_box[ch.x].lo), ahi = ld_cg<T>(&node_box[ch.x].hi);
+            vec4_t<T> blo = ld_cg<T>(&node_box[ch.y].lo), bhi = ld_cg<T>(&node_box[ch.y].hi);
+            Box<T> u;
+            u.lo.x = tmin(alo.x, blo.x); u.lo.y = tmin(alo.y, blo.y); u.lo.z = tmin(alo.z, blo.z); u.lo.w = T(0);
+            u.hi.x = tmax(ahi.x, bhi.x); u.hi.y = tmax(ahi.y, bhi.y); u.hi.z = tmax(ahi.z, bhi.z); u.hi.w = T(0);
+            node_box[node] = u;
+            node = parent[node];
+        }
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ bool overlap(const vec4_t<T> &alo, const vec4_t<T> &ahi, const vec4_t<T> &blo,
+                                        const vec4_t<T> &bhi) {
+    return alo.x <= bhi.x && blo.x <= ahi.x && alo.y <= bhi.y && blo.y <= ahi.y && alo.z <= bhi.z && blo.z <= ahi.z;
+}
+
+__device__ __forceinline__ bool share_vertex(int4 a, int4 b) {
+    return a.x == b.x || a.x == b.y || a.x == b.z || a.y == b.x || a.y == b.y || a.y == b.z || a.z == b.x ||
+           a.z == b.y || a.z == b.z;
+}
+
+// One thread per leaf s: every leaf s' > s in the pair-mode window whose box overlaps.
+template <typename T, bool kWrite>
+__global__ void __launch_bounds__(kThreads) k_traverse(int n, const int2 *__restrict__ child, const int2 *__restrict__ range,
+                                                       const Box<T> *__restrict__ node_box,
+                                                       const uint32_t *__restrict__ perm, const int4 *__restrict__ tri4,
+                                                       const int32_t *__restrict__ leaf_group,
+                                                       const int2 *__restrict__ group_range, int mode,
+                                                       uint32_t *__restrict__ count,
+                                                       const unsigned long long *__restrict__ offset,
+                                                       int2 *__restrict__ pairs, DevScalars *ds) {
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
+        int lo = s + 1, hi = n - 1;
+        if (mode == TTIE_PAIRS_INTRA_GROUP) {
+            hi = group_range[leaf_group[s]].y;
+        } else if (mode == TTIE_PAIRS_INTER_GROUP) {
+            lo = max(lo, group_range[leaf_group[s]].y + 1);
+        }
+        uint32_t cnt = 0;
+        unsigned long long out = kWrite ? offset[s] : 0ull;
+        if (lo <= hi) {
+            const uint32_t qi = perm[s];
+            const int4 tq = tri4[qi];
+            const Box<T> qb = node_box[n - 1 + s];
+            int stack[kStack];
+            int sp = 0;
+            stack[sp++] = 0;
+            while (sp > 0) {
+                const int node = stack[--sp];
+                const int2 r = range[node];
+                if (r.y < lo || r.x > hi) continue;
+                const Box<T> nb = node_box[node];
+                if (!overlap<T>(qb.lo, qb.hi, nb.lo, nb.hi)) continue;
+                if (node >= n - 1) {
+                    const uint32_t tj = perm[node - (n - 1)];
+                    if (share_vertex(tq, tri4[tj])) continue;
+                    if (kWrite) {
+                        pairs[out + cnt] = make_int2((int)min(qi, tj), (int)max(qi, tj));
+                    }
+                    ++cnt;
+                } else {
+                    if (sp + 2 > kStack) {
+                        atomicOr(&ds->err, ERR_STACK);
+                        sp = 0;
+                        break;
+                    }
+                    const int2 ch = child[node];
+                    stack[sp++] = ch.y;
+                    stack[sp++] = ch.x;
+                }
+            }
+        }
+        if (!kWrite) count[s] = cnt;
+    }
+}
+
+// Brute force: every pair i<j of the mode sharing no vertex (no box test).
+template <bool kWrite>
+__global__ void k_brute(int n, const int4 *__restrict__ tri4, const int32_t *__restrict__ grp, int mode,
+                        uint32_t *__restrict__ count, const unsigned long long *__restrict__ offset,
+                        int2 *__restrict__ pairs) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int4 ti = tri4[i];
+        const int gi = grp ? grp[i] : 0;
+        uint32_t cnt = 0;
+        unsigned long long out = kWrite ? offset[i] : 0ull;
+        for (int j = i + 1; j < n; ++j) {
+            if (mode == TTIE_PAIRS_INTER_GROUP && grp[j] == gi) continue;
+            if (mode == TTIE_PAIRS_INTRA_GROUP && grp[j] != gi) continue;
+            if (share_vertex(ti, tri4[j])) continue;
+            if (kWrite) pairs[out + cnt] = make_int2(i, j);
+            ++cnt;
+        }
+        if (!kWrite) count[i] = cnt;
+    }
+}
+
+}  // namespace
+
+template <typename T> cudaError_t pack_positions(Ctx &c, const T *x, int stride, vec4_t<T> *out) {
+    k_pack_positions<T><<<grid_for(c.V, kThreads), kThreads, 0, c.stream>>>(x, stride, c.V, out, c.ds);
+    return cudaGetLastError();
+}
+template cudaError_t pack_positions<float>(Ctx &, const float *, int, float4 *);
+template cudaError_t pack_positions<double>(Ctx &, const double *, int, dvec4 *);
+
+cudaError_t pack_topology(Ctx &c, const int32_t *tri, const int32_t *group) {
+    TTIE_CUDA_TRY(ensure(c, c.tri4, (size_t)c.F * sizeof(int4)));
+    if (group) TTIE_CUDA_TRY(ensure(c, c.grp, (size_t)c.F * sizeof(int32_t)));
+    k_pack_topology<<<grid_for(c.F, kThreads), kThreads, 0, c.stream>>>(tri, group, c.F, c.V, (int4 *)c.tri4.p,
+                                                                      (int32_t *)c.grp.p, c.ds);
+    return cudaGetLastError();
+}
+
+static int mode_of(const Ctx &c) { return c.prm.pair_mode & 3; }
+
+template <typename T>
+cudaError_t build_candidates(Ctx &c, const vec4_t<T> *x0, const vec4_t<T> *x1, Buf &out_pairs, int64_t *n_out) {
+    const int n = (int)c.F;
+    const int mode = mode_of(c);
+    *n_out = 0;
+    if (n < 2) return cudaSuccess;
+    TTIE_CUDA_TRY(ensure(c, c.tbox, (size_t)n * sizeof(Box<T>)));
+    TTIE_CUDA_TRY(ensure(c, c.mkey, (size_t)n * 8));
+    TTIE_CUDA_TRY(ensure(c, c.mkey2, (size_t)n * 8));
+    TTIE_CUDA_TRY(ensure(c, c.perm, (size_t)n * 4));
+    TTIE_CUDA_TRY(ensure(c, c.perm2, (size_t)n * 4));
+    TTIE_CUDA_TRY(ensure(c, c.node_box, (size_t)(2 * n - 1) * sizeof(Box<T>)));
+    TTIE_CUDA_TRY(ensure(c, c.node_child, (size_t)(n - 1) * sizeof(int2)));
+    TTIE_CUDA_TRY(ensure(c, c.node_parent, (size_t)(2 * n - 1) * sizeof(int)));
+    TTIE_CUDA_TRY(ensure(c, c.node_range, (size_t)(2 * n - 1) * sizeof(int2)));
+    TTIE_CUDA_TRY(ensure(c, c.visit, (size_t)(n - 1) * sizeof(unsigned int)));
+    TTIE_CUDA_TRY(ensure(c, c.cand_cnt, (size_t)n * 4));
+    TTIE_CUDA_TRY(ensure(c, c.cand_off, (size_t)(n + 1) * 8));
+    const bool grouped = mode != TTIE_PAIRS_SELF;
+    if (grouped) {
+        TTIE_CUDA_TRY(ensure(c, c.leaf_group, (size_t)n * 4));
+        TTIE_CUDA_TRY(ensure(c, c.group_range, (size_t)c.n_groups * sizeof(int2)));
+    }
+    Box<T> *tbox = (Box<T> *)c.tbox.p;
+    auto *key = (unsigned long long *)c.mkey.p;
+    auto *perm = (uint32_t *)c.perm.p;
+    const unsigned g = grid_for(n, kThreads);
+
+    k_init_bounds<<<1, 32, 0, c.stream>>>(c.ds);
+    k_tri_boxes<T><<<g, kThreads, 0, c.stream>>>(x0, x1, (const int4 *)c.tri4.p, n, tbox, c.ds);
+    const int gbits = grouped ? c.group_bits : 0;
+    k_morton<T><<<g, kThreads, 0, c.stream>>>(tbox, n, (const int32_t *)c.grp.p, gbits, c.ds, key, perm);
+    TTIE_CUDA_TRY(cudaGetLastError());
+    const int key_bits = 3 * ((63 - gbits) / 3) + gbits;
+    TTIE_CUDA_TRY(radix_sort(c, key, perm, (unsigned long long *)c.mkey2.p, (uint32_t *)c.perm2.p, n, key_bits));
+    if (grouped) {
+        k_leaf_group<<<g, kThreads, 0, c.stream>>>(perm, (const int32_t *)c.grp.p, n, (int32_t *)c.leaf_group.p);
+        k_fill_int2<<<grid_for(c.n_groups, kThreads), kThreads, 0, c.stream>>>((int2 *)c.group_range.p, c.n_groups,
+                                                                              make_int2(1, 0));
+        k_group_ranges<<<g, kThreads, 0, c.stream>>>((const int32_t *)c.leaf_group.p, n, (int2 *)c.group_range.p);
+    }
+    int2 *child = (int2 *)c.node_child.p;
+    int *parent = (int *)c.node_parent.p;
+    int2 *range = (int2 *)c.node_range.p;
+    Box<T> *nbox = (Box<T> *)c.node_box.p;
+    k_karras<<<grid_for(n - 1, kThreads), kThreads, 0, c.stream>>>(key, n, child, parent, range);
+    k_leaf_boxes<T><<<g, kThreads, 0, c.stream>>>(tbox, perm, n, nbox, range);
+    TTIE_CUDA_TRY(cudaMemsetAsync(c.visit.p, 0, (size_t)(n - 1) * sizeof(unsigned int), c.stream));
+    k_refit<T><<<g, kThreads, 0, c.stream>>>(n, parent, child, nbox, (unsigned int *)c.visit.p, c.ds);
+    auto *cnt = (uint32_t *)c.cand_cnt.p;
+    auto *off = (unsigned long long *)c.cand_off.p;
+    k_traverse<T, false><<<g, kThreads, 0, c.stream>>>(n, child, range, nbox, perm, (const int4 *)c.tri4.p,
+                                                       (const int32_t *)c.leaf_group.p, (const int2 *)c.group_range.p,
+                                                       mode, cnt, nullptr, nullptr, c.ds);
+    TTIE_CUDA_TRY(cudaGetLastError());
+    TTIE_CUDA_TRY(scan_u32_u64(c, cnt, off, n));
+    unsigned long long total = 0;
+    TTIE_CUDA_TRY(cudaMemcpyAsync(&c.hs->n_cand, off + n, 8, cudaMemcpyDeviceToHost, c.stream));
+    TTIE_CUDA_TRY(cudaStreamSynchronize(c.stream));
+    total = c.hs->n_cand;
+    TTIE_CUDA_TRY(ensure(c, out_pairs, (size_t)(total > 0 ? total : 1) * sizeof(int2)));
+    if (total > 0)
+        k_traverse<T, true><<<g, kThreads, 0, c.stream>>>(n, child, range, nbox, perm, (const int4 *)c.tri4.p,
+                                                          (const int32_t *)c.leaf_group.p,
+                                                          (const int2 *)c.group_range.p, mode, nullptr, off,
+                                                          (int2 *)out_pairs.p, c.ds);
+    *n_out = (int64_t)total;
+    return cudaGetLastError();
+}
+template cudaError_t build_candidates<float>(Ctx &, const float4 *, const float4 *, Buf &, int64_t *);
+template cudaError_t build_candidates<double>(Ctx &, const dvec4 *, const dvec4 *, Buf &, int64_t *);
+
+cudaError_t brute_candidates(Ctx &c, Buf &out_pairs, int64_t *n_out) {
+    const int n = (int)c.F;
+    const int mode = mode_of(c);
+    *n_out = 0;
+    if (n < 2) return cudaSuccess;
+    TTIE_CUDA_TRY(ensure(c, c.cand_cnt, (size_t)n * 4));
+    TTIE_CUDA_TRY(ensure(c, c.cand_off, (size_t)(n + 1) * 8));
+    auto *cnt = (uint32_t *)c.cand_cnt.p;
+    auto *off = (unsigned long long *)c.cand_off.p;
+    const unsigned g = grid_for(n, 128);
+    k_brute<false><<<g, 128, 0, c.stream>>>(n, (const int4 *)c.tri4.p, (const int32_t *)c.grp.p, mode, cnt, nullptr,
+                                            nullptr);
+    TTIE_CUDA_TRY(cudaGetLastError());
+    TTIE_CUDA_TRY(scan_u32_u64(c, cnt, off, n));
+    TTIE_CUDA_TRY(cudaMemcpyAsync(&c.hs->n_cand, off + n, 8, cudaMemcpyDeviceToHost, c.stream));
+    TTIE_CUDA_TRY(cudaStreamSynchronize(c.stream));
+    unsigned long long total = c.hs->n_cand;
+    TTIE_CUDA_TRY(ensure(c, out_pairs, (size_t)(total > 0 ? total : 1) * sizeof(int2)));
+    if (total > 0)
+        k_brute<true><<<g, 128, 0, c.stream>>>(n, (const int4 *)c.tri4.p, (const int32_t *)c.grp.p, mode, nullptr,
+                                               off, (int2 *)out_pairs.p);
+    *n_out = (int64_t)total;
+    return cudaGetLastError();
+}
+
+}  // namespace ttie

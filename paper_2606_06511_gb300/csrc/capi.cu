@@ -1,0 +1,614 @@
+// C ABI of libttie: argument checks, context memory, and the order of the stages.
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstring>
+#include <new>
+
+#include "common.cuh"
+
+namespace ttie {
+
+cudaError_t ensure(Ctx &c, Buf &b, size_t bytes) {
+    (void)c;
+    if (b.bytes >= bytes) return cudaSuccess;
+    if (b.p) {
+        cudaError_t e = cudaFree(b.p);   // waits for pending work that may still use it
+        b.p = nullptr;
+        b.bytes = 0;
+        if (e != cudaSuccess) return e;
+    }
+    const size_t nb = bytes + bytes / 4 + 256;
+    cudaError_t e = cudaMalloc(&b.p, nb);
+    if (e != cudaSuccess) {
+        b.p = nullptr;
+        return e;
+    }
+    b.bytes = nb;
+    return cudaSuccess;
+}
+
+template <typename T> cudaError_t dot_rows(Ctx &c, const T *a, const T *b, int64_t n3, double *out_dev);
+
+namespace {
+
+constexpr int kThreads = 256;
+
+template <typename T>
+__global__ void k_copy_neg(const T *__restrict__ a, T *__restrict__ b, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) b[i] = -a[i];
+}
+
+template <typename T>
+__global__ void k_dot(const T *__restrict__ a, const T *__restrict__ b, int64_t n, double *out) {
+    __shared__ double sh[32];
+    double s = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        s += (double)a[i] * (double)b[i];
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+        *out = t;   // single block: deterministic
+    }
+}
+
+__global__ void k_gather_active(const int2 *__restrict__ cand, const uint32_t *__restrict__ active, int64_t n,
+                                int2 *__restrict__ out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = cand[active[i]];
+}
+
+template <typename T>
+__global__ void k_split_fac(const T *__restrict__ fac, int64_t n, T *__restrict__ tc, T *__restrict__ dtc) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const T *r = fac + i * 40;
+        if (tc) { tc[2 * i] = r[0]; tc[2 * i + 1] = r[1]; }
+        if (dtc)
+            for (int k = 0; k < 36; ++k) dtc[36 * i + k] = r[2 + k];
+    }
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t dot_rows(Ctx &c, const T *a, const T *b, int64_t n3, double *out_dev) {
+    k_dot<T><<<1, 1024, 0, c.stream>>>(a, b, n3, out_dev);
+    return cudaGetLastError();
+}
+
+}  // namespace ttie
+
+using namespace ttie;
+
+struct ttie_ctx {
+    Ctx c;
+};
+
+static ttie_status set_err(Ctx &c, ttie_status s, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    c.err = buf;
+    return s;
+}
+
+static ttie_status cuda_err(Ctx &c, cudaError_t e, const char *where) {
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return set_err(c, TTIE_ERR_OOM, "%s: device allocation failed", where);
+    }
+    return set_err(c, TTIE_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+#define CK(expr, where)                                      \
+    do {                                                     \
+        cudaError_t _e = (expr);                             \
+        if (_e != cudaSuccess) return cuda_err(c, _e, where); \
+    } while (0)
+
+static ttie_status check_params(Ctx &c, const ttie_params *p) {
+    if (!p) return set_err(c, TTIE_ERR_INVALID, "params is NULL");
+    if (p->precision != TTIE_F32 && p->precision != TTIE_F64) return set_err(c, TTIE_ERR_INVALID, "precision");
+    const int m = p->pair_mode & 3;
+    if (m == 3 || (p->pair_mode & ~7)) return set_err(c, TTIE_ERR_INVALID, "pair_mode");
+    if (p->psd_mode != TTIE_PSD_PER_PART && p->psd_mode != TTIE_PSD_DROP_CROSS)
+        return set_err(c, TTIE_ERR_INVALID, "psd_mode");
+    if (!(p->tc_scale > 0.0) || !(p->mu_rel >= 0.0) || !(p->pcg_rtol > 0.0) || p->pcg_max_it < 1 ||
+        p->newton_max_it < 0 || p->ls_max_halvings < 0 || p->ls_max_halvings > 60 || !(p->armijo_c >= 0.0) ||
+        !(p->push_eta >= 0.0))
+        return set_err(c, TTIE_ERR_INVALID, "numeric parameter out of range");
+    return TTIE_OK;
+}
+
+extern "C" {
+
+void ttie_default_params(ttie_params *p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof *p);
+    p->precision = TTIE_F32;
+    p->pair_mode = TTIE_PAIRS_SELF;
+    p->psd_mode = TTIE_PSD_PER_PART;
+    p->tc_scale = 1.0;
+    p->mu_rel = 1e-3;
+    p->pcg_rtol = 1e-3;
+    p->pcg_max_it = 200;
+    p->newton_max_it = 200;
+    p->ls_max_halvings = 20;
+    p->armijo_c = 1e-4;
+    p->push_eta = 0.5;
+}
+
+ttie_status ttie_create(ttie_ctx **out, const ttie_params *p, void *stream) {
+    if (!out) return TTIE_ERR_INVALID;
+    *out = nullptr;
+    ttie_ctx *h = new (std::nothrow) ttie_ctx;
+    if (!h) return TTIE_ERR_OOM;
+    Ctx &c = h->c;
+    ttie_params def;
+    ttie_default_params(&def);
+    if (check_params(c, p ? p : &def) != TTIE_OK) {
+        delete h;
+        return TTIE_ERR_INVALID;
+    }
+    c.prm = p ? *p : def;
+    c.stream = (cudaStream_t)stream;
+    cudaError_t e = cudaGetDevice(&c.device);
+    if (e == cudaSuccess) e = cudaMalloc(&c.ds, sizeof(DevScalars));
+    if (e == cudaSuccess) e = cudaMallocHost(&c.hs, sizeof(DevScalars));
+    if (e == cudaSuccess) e = cudaMemsetAsync(c.ds, 0, sizeof(DevScalars), c.stream);
+    for (int i = 0; i < 12 && e == cudaSuccess; ++i) e = cudaEventCreate(&c.ev[i]);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
+    if (e != cudaSuccess) {
+        ttie_status s = e == cudaErrorMemoryAllocation ? TTIE_ERR_OOM : TTIE_ERR_CUDA;
+        cudaGetLastError();
+        ttie_destroy(h);
+        return s;
+    }
+    std::memset(c.hs, 0, sizeof(DevScalars));
+    *out = h;
+    return TTIE_OK;
+}
+
+void ttie_destroy(ttie_ctx *h) {
+    if (!h) return;
+    Ctx &c = h->c;
+    if (c.stream || c.ds) cudaStreamSynchronize(c.stream);
+#define TTIE_FREE_BUF(name) if (c.name.p) cudaFree(c.name.p);
+    TTIE_BUFS(TTIE_FREE_BUF)
+#undef TTIE_FREE_BUF
+    if (c.ds) cudaFree(c.ds);
+    if (c.hs) cudaFreeHost(c.hs);
+    for (int i = 0; i < 12; ++i)
+        if (c.ev[i]) cudaEventDestroy(c.ev[i]);
+    delete h;
+}
+
+const char *ttie_last_error(const ttie_ctx *h) {
+    if (!h) return "null context";
+    return h->c.err.c_str();
+}
+
+ttie_status ttie_set_params(ttie_ctx *h, const ttie_params *p) {
+    if (!h) return TTIE_ERR_INVALID;
+    Ctx &c = h->c;
+    ttie_status s = check_params(c, p);
+    if (s != TTIE_OK) return s;
+    if (c.have_mesh && p->precision != c.prm.precision)
+        return set_err(c, TTIE_ERR_STATE, "precision cannot change after ttie_build_bvh");
+    c.prm = *p;
+    return TTIE_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ stage helpers
+static ttie_status read_err(Ctx &c, const char *where) {
+    CK(cudaMemcpyAsync(&c.hs->err, &c.ds->err, sizeof(int), cudaMemcpyDeviceToHost, c.stream), where);
+    CK(cudaStreamSynchronize(c.stream), where);
+    const int e = c.hs->err;
+    if (e) CK(cudaMemsetAsync(&c.ds->err, 0, sizeof(int), c.stream), where);
+    if (e & ERR_BAD_INDEX) return set_err(c, TTIE_ERR_INVALID, "%s: triangle or group index out of range", where);
+    if (e & ERR_NONFINITE) return set_err(c, TTIE_ERR_NONFINITE, "%s: non-finite vertex position", where);
+    if (e & ERR_STACK) return set_err(c, TTIE_ERR_CAPACITY, "%s: BVH traversal stack overflow", where);
+    return TTIE_OK;
+}
+
+template <typename T>
+static ttie_status build_impl(Ctx &c, const T *x, const int32_t *tri, const int32_t *group, int64_t *n_cand) {
+    c.have_cand = c.have_eval = c.have_bsr = c.have_dir = false;
+    CK(cudaMemsetAsync(&c.ds->max_group, 0, sizeof(int), c.stream), "build");
+    CK(pack_topology(c, tri, group), "build: topology");
+    CK(ensure(c, c.xp, (size_t)(c.V > 0 ? c.V : 1) * sizeof(vec4_t<T>)), "build");
+    CK(pack_positions<T>(c, x, c.x_stride, (vec4_t<T> *)c.xp.p), "build: positions");
+    ttie_status s = read_err(c, "ttie_build_bvh");
+    if (s != TTIE_OK) return s;
+    c.have_group = group != nullptr;
+    c.n_groups = 1;
+    c.group_bits = 0;
+    if (group) {
+        CK(cudaMemcpyAsync(&c.hs->max_group, &c.ds->max_group, sizeof(int), cudaMemcpyDeviceToHost, c.stream), "build");
+        CK(cudaStreamSynchronize(c.stream), "build");
+        c.n_groups = c.hs->max_group + 1;
+        while ((1 << c.group_bits) < c.n_groups) ++c.group_bits;
+        if (c.group_bits == 0) c.group_bits = 1;
+    }
+    c.have_mesh = true;
+    int64_t n = 0;
+    if (c.prm.pair_mode & TTIE_PAIRS_BRUTE)
+        CK(brute_candidates(c, c.cand, &n), "build: brute-force pairs");
+    else
+        CK(build_candidates<T>(c, (const vec4_t<T> *)c.xp.p, nullptr, c.cand, &n), "build: LBVH");
+    s = read_err(c, "ttie_build_bvh");
+    if (s != TTIE_OK) return s;
+    c.n_cand = n;
+    c.have_cand = true;
+    if (n_cand) *n_cand = n;
+    return TTIE_OK;
+}
+
+template <typename T>
+static ttie_status eval_impl(Ctx &c, const T *x, unsigned what, double *energy, int64_t *n_active, T *grad) {
+    c.have_eval = c.have_bsr = false;
+    CK(pack_positions<T>(c, x, c.x_stride, (vec4_t<T> *)c.xp.p), "eval: positions");
+    ttie_status s = read_err(c, "ttie_eval_pairs");
+    if (s != TTIE_OK) return s;
+    CK(eval_candidates<T>(c, (const vec4_t<T> *)c.xp.p, (const int2 *)c.cand.p, c.n_cand, what), "eval");
+    c.have_eval = true;
+    c.eval_what = what;
+    if (grad) {
+        CK(assemble_system<T>(c, grad), "eval: gradient");
+        c.have_bsr = true;
+    }
+    CK(cudaMemcpyAsync(&c.hs->energy, &c.ds->energy, sizeof(double), cudaMemcpyDeviceToHost, c.stream), "eval");
+    CK(cudaStreamSynchronize(c.stream), "eval");
+    if (!std::isfinite(c.hs->energy)) return set_err(c, TTIE_ERR_NONFINITE, "ttie_eval_pairs: energy is not finite");
+    if (energy) *energy = c.hs->energy;
+    if (n_active) *n_active = c.n_active;
+    return TTIE_OK;
+}
+
+// Energy and intersecting-pair count at positions xt over the given candidate list.
+template <typename T>
+static ttie_status energy_at(Ctx &c, const vec4_t<T> *xt, const int2 *pairs, int64_t n, double *E, int64_t *n_act) {
+    CK(eval_candidates<T>(c, xt, pairs, n, TTIE_EVAL_E), "line search");
+    CK(cudaMemcpyAsync(&c.hs->energy, &c.ds->energy, sizeof(double), cudaMemcpyDeviceToHost, c.stream), "line search");
+    CK(cudaStreamSynchronize(c.stream), "line search");
+    *E = c.hs->energy;
+    *n_act = c.n_active;
+    return TTIE_OK;
+}
+
+static float ms_between(Ctx &c, int a, int b) {
+    float ms = 0.f;
+    if (c.prm.profile) cudaEventElapsedTime(&ms, c.ev[a], c.ev[b]);
+    return ms;
+}
+
+static void mark(Ctx &c, int i) {
+    if (c.prm.profile) cudaEventRecord(c.ev[i], c.stream);
+}
+
+template <typename T> static cudaError_t negate_copy(Ctx &c, const T *a, T *b, int64_t n) {
+    ttie::k_copy_neg<T><<<grid_for(n, 256), 256, 0, c.stream>>>(a, b, n);
+    return cudaGetLastError();
+}
+
+template <typename T>
+static ttie_status newton_impl(Ctx &c, T *x, ttie_step_info *info) {
+    ttie_step_info inf;
+    std::memset(&inf, 0, sizeof inf);
+    c.have_dir = false;
+    mark(c, 0);
+    // candidates and evaluation at x
+    CK(pack_positions<T>(c, x, c.x_stride, (vec4_t<T> *)c.xp.p), "newton: positions");
+    ttie_status s = read_err(c, "ttie_newton_step");
+    if (s != TTIE_OK) return s;
+    int64_t n = 0;
+    if (c.prm.pair_mode & TTIE_PAIRS_BRUTE)
+        CK(brute_candidates(c, c.cand, &n), "newton: pairs");
+    else
+        CK(build_candidates<T>(c, (const vec4_t<T> *)c.xp.p, nullptr, c.cand, &n), "newton: LBVH");
+    c.n_cand = n;
+    c.have_cand = true;
+    inf.n_candidates = n;
+    mark(c, 1);
+    CK(eval_candidates<T>(c, (const vec4_t<T> *)c.xp.p, (const int2 *)c.cand.p, n, TTIE_EVAL_E | TTIE_EVAL_H), "newton: eval");
+    c.have_eval = true;
+    c.eval_what = TTIE_EVAL_E | TTIE_EVAL_H;
+    CK(cudaMemcpyAsync(&c.hs->energy, &c.ds->energy, sizeof(double), cudaMemcpyDeviceToHost, c.stream), "newton");
+    CK(cudaStreamSynchronize(c.stream), "newton");
+    const double E = c.hs->energy;
+    inf.energy = E;
+    inf.n_active = c.n_active;
+    mark(c, 2);
+    if (!std::isfinite(E)) return set_err(c, TTIE_ERR_NONFINITE, "ttie_newton_step: energy is not finite");
+    if (c.n_active == 0) {
+        inf.energy_new = E;
+        mark(c, 3); mark(c, 4); mark(c, 5);
+        if (c.prm.profile) cudaEventSynchronize(c.ev[5]);
+        inf.ms_build = ms_between(c, 0, 1);
+        inf.ms_eval = ms_between(c, 1, 2);
+        if (info) *info = inf;
+        return TTIE_OK;
+    }
+    // assembly and PCG for (H+ + mu I) d = -g
+    CK(assemble_system<T>(c, nullptr), "newton: assembly");
+    c.have_bsr = true;
+    inf.n_rows = c.n_rows;
+    inf.nnzb = c.nnzb;
+    mark(c, 3);
+    const int64_t n3 = c.n_rows * 3;
+    CK(ensure(c, c.pcg_x, (size_t)(n3 > 0 ? n3 : 1) * sizeof(T)), "newton");
+    CK(ensure(c, c.xsave, (size_t)(n3 > 0 ? n3 : 1) * sizeof(T)), "newton");
+    CK(negate_copy(c, (const T *)c.rhs.p, (T *)c.xsave.p, n3), "newton");
+    CK(pcg_solve<T>(c, (const T *)c.xsave.p, (T *)c.pcg_x.p, c.prm.pcg_rtol, c.prm.pcg_max_it), "newton: PCG");
+    CK(dot_rows<T>(c, (const T *)c.rhs.p, (const T *)c.pcg_x.p, n3, &c.ds->red[6]), "newton");
+    CK(ensure(c, c.dir, (size_t)c.V * 3 * sizeof(T)), "newton");
+    CK(scatter_direction<T>(c, (const T *)c.pcg_x.p, (T *)c.dir.p), "newton");
+    c.have_dir = true;
+    CK(cudaMemcpyAsync(c.hs, c.ds, sizeof(DevScalars), cudaMemcpyDeviceToHost, c.stream), "newton");
+    CK(cudaStreamSynchronize(c.stream), "newton");
+    const double gd = c.hs->red[6];
+    inf.grad_dot_dir = gd;
+    inf.pcg_iters = c.hs->pcg_iters;
+    inf.pcg_rel_residual = c.hs->red[1] > 0.0 ? std::sqrt(c.hs->red[4] / c.hs->red[1]) : 0.0;
+    mark(c, 4);
+    // line search on candidates from the boxes swept between x and x + a_max d
+    const double a_max = 1.0 + c.prm.push_eta;
+    CK(ensure(c, c.xq, (size_t)c.V * sizeof(vec4_t<T>)), "newton");
+    CK(ensure(c, c.xt, (size_t)c.V * sizeof(vec4_t<T>)), "newton");
+    CK(axpy_positions<T>(c, (const vec4_t<T> *)c.xp.p, (const T *)c.dir.p, (T)a_max, (vec4_t<T> *)c.xq.p), "newton");
+    int64_t ns = 0;
+    if (c.prm.pair_mode & TTIE_PAIRS_BRUTE) {
+        ns = c.n_cand;
+        CK(ensure(c, c.sweep_cand, (size_t)(ns > 0 ? ns : 1) * sizeof(int2)), "newton");
+        CK(cudaMemcpyAsync(c.sweep_cand.p, c.cand.p, (size_t)ns * sizeof(int2), cudaMemcpyDeviceToDevice, c.stream), "newton");
+    } else {
+        CK(build_candidates<T>(c, (const vec4_t<T> *)c.xp.p, (const vec4_t<T> *)c.xq.p, c.sweep_cand, &ns), "newton: sweep");
+    }
+    s = read_err(c, "ttie_newton_step");
+    if (s != TTIE_OK) return s;
+    inf.n_candidates_swept = ns;
+    double alpha = 0.0, E_new = E;
+    int64_t n_new = c.n_active;
+    int trials = 0;
+    bool accepted = false;
+    for (int k = -1; k <= c.prm.ls_max_halvings; ++k) {
+        const double a = k < 0 ? a_max : std::ldexp(1.0, -k);
+        if (k < 0 && !(a_max > 1.0)) continue;
+        CK(axpy_positions<T>(c, (const vec4_t<T> *)c.xp.p, (const T *)c.dir.p, (T)a, (vec4_t<T> *)c.xt.p), "newton");
+        double Et = 0.0;
+        int64_t nt = 0;
+        s = energy_at<T>(c, (const vec4_t<T> *)c.xt.p, (const int2 *)c.sweep_cand.p, ns, &Et, &nt);
+        if (s != TTIE_OK) return s;
+        ++trials;
+        alpha = a;
+        E_new = Et;
+        n_new = nt;
+        if (nt == 0 || Et <= E + c.prm.armijo_c * a * gd) {
+            accepted = true;
+            break;
+        }
+    }
+    (void)accepted;   // the last (smallest) trial is taken when none is accepted
+    CK(update_positions<T>(c, x, c.x_stride, (const T *)c.dir.p, (T)alpha), "newton: update");
+    c.have_eval = false;   // the last evaluation ran on the line-search candidates
+    mark(c, 5);
+    CK(cudaStreamSynchronize(c.stream), "newton");
+    inf.alpha = alpha;
+    inf.energy_new = E_new;
+    inf.n_active_new = n_new;
+    inf.ls_trials = trials;
+    inf.ms_build = ms_between(c, 0, 1);
+    inf.ms_eval = ms_between(c, 1, 2);
+    inf.ms_assemble = ms_between(c, 2, 3);
+    inf.ms_pcg = ms_between(c, 3, 4);
+    inf.ms_line_search = ms_between(c, 4, 5);
+    if (info) *info = inf;
+    return TTIE_OK;
+}
+
+extern "C" {
+
+ttie_status ttie_build_bvh(ttie_ctx *h, const void *d_x, int64_t V, int x_stride, const int32_t *d_tri, int64_t F,
+                           const int32_t *d_group, int64_t *n_candidates) {
+    if (!h) return TTIE_ERR_INVALID;
+    Ctx &c = h->c;
+    if (!d_x || (!d_tri && F > 0)) return set_err(c, TTIE_ERR_INVALID, "ttie_build_bvh: null pointer");
+    if (V < 1 || V > (int64_t)INT32_MAX) return set_err(c, TTIE_ERR_INVALID, "ttie_build_bvh: V out of range");
+    if (F < 0 || F > (int64_t)INT32_MAX / 2) return set_err(c, TTIE_ERR_INVALID, "ttie_build_bvh: F out of range");
+    if (x_stride != 3 && x_stride != 4) return set_err(c, TTIE_ERR_INVALID, "ttie_build_bvh: x_stride must be 3 or 4");
+    const int mode = c.prm.pair_mode & 3;
+    if (mode != TTIE_PAIRS_SELF && !d_group)
+        return set_err(c, TTIE_ERR_INVALID, "ttie_build_bvh: the group pair modes need d_group");
+    c.V = V;
+    c.F = F;
+    c.x_stride = x_stride;
+    c.have_mesh = false;
+    if (c.prm.precision == TTIE_F64) return build_impl<double>(c, (const double *)d_x, d_tri, d_group, n_candidates);
+    return build_impl<float>(c, (const float *)d_x, d_tri, d_group, n_candidates);
+}
+
+ttie_status ttie_eval_pairs(ttie_ctx *h, const void *d_x, unsigned what, double *energy, int64_t *n_active, void *d_grad) {
+    if (!h) return TTIE_ERR_INVALID;
+    Ctx &c = h->c;
+    if (!c.have_cand) return set_err(c, TTIE_ERR_STATE, "ttie_eval_pairs: call ttie_build_bvh first");
+    if (!d_x) return set_err(c, TTIE_ERR_INVALID, "ttie_eval_pairs: null positions");
+    if (what & ~7u) return set_err(c, TTIE_ERR_INVALID, "ttie_eval_pairs: unknown flags");
+    if (d_grad && !(what & TTIE_EVAL_G)) return set_err(c, TTIE_ERR_INVALID, "ttie_eval_pairs: d_grad needs TTIE_EVAL_G");
+    if (c.prm.precision == TTIE_F64)
+        return eval_impl<double>(c, (const double *)d_x, what, energy, n_active, (double *)d_grad);
+    return eval_impl<float>(c, (const float *)d_x, what, energy, n_active, (float *)d_grad);
+}
+
+ttie_status ttie_assemble(ttie_ctx *h, ttie_bsr_view *out) {
+    if (!h) return TTIE_ERR_INVALID;
+    Ctx &c = h->c;
+    if (!out) return set_err(c, TTIE_ERR_INVALID, "ttie_assemble: null output");
+    if (!c.have_eval || !(c.eval_what & (TTIE_EVAL_H | TTIE_EVAL_G)))
+        return set_err(c, TTIE_ERR_STATE, "ttie_assemble: needs a ttie_eval_pairs with TTIE_EVAL_H");
+    if (!c.have_bsr) {
+        cudaError_t e = c.prm.precision == TTIE_F64 ? assemble_system<double>(c, nullptr) : assemble_system<float>(c, nullptr);
+        if (e != cudaSuccess) return cuda_err(c, e, "ttie_assemble");
+        c.have_bsr = true;
+    }
+    CK(cudaStreamSynchronize(c.stream), "ttie_assemble");
+    out->n_rows = c.n_rows;
+    out->nnzb = c.nnzb;
+    out->row_ptr = (const int32_t *)c.row_ptr.p;
+    out->col_idx = (const int32_t *)c.col_idx.p;
+    out->val = c.bsr_val.p;
+    out->vertex_of_row = (const int32_t *)c.row_vertex.p;
+    out->grad = c.rhs.p;
+    return TTIE_OK;
+}
+
+ttie_status ttie_copy_bsr(ttie_ctx *h, int32_t *d_row_ptr, int32_t *d_col_idx, void *d_val, int32_t *d_vertex_of_row,
+                         void *d_grad) {
+    if (!h) return TTIE_ERR_INVALID;
+    Ctx &c = h->c;
+    if (!c.have_bsr) return set_err(c, TTIE_ERR_STATE, "ttie_copy_bsr: call ttie_assemble first");
+    const size_t es = c.prm.precision == TTIE_F64 ? 8 : 4;
+    const cudaMemcpyKind k = cudaMemcpyDeviceToDevice;
+    if (d_row_ptr) CK(cudaMemcpyAsync(d_row_ptr, c.row_ptr.p, (size_t)(c.n_rows + 1) * 4, k, c.stream), "ttie_copy_bsr");
+    if (d_col_idx && c.nnzb) CK(cudaMemcpyAsync(d_col_idx, c.col_idx.p, (size_t)c.nnzb * 4, k, c.stream), "ttie_copy_bsr");
+    if (d_val && c.nnzb) CK(cudaMemcpyAsync(d_val, c.bsr_val.p, (size_t)c.nnzb * 9 * es, k, c.stream), "ttie_copy_bsr");
+    if (d_vertex_of_row && c.n_rows)
+        CK(cudaMemcpyAsync(d_vertex_of_row, c.row_vertex.p, (size_t)c.n_rows * 4, k, c.stream), "ttie_copy_bsr");
+    if (d_grad && c.n_rows) CK(cudaMemcpyAsync(d_grad, c.rhs.p, (size_t)c.n_rows * 3 * es, k, c.stream), "ttie_copy_bsr");
+    CK(cudaStreamSynchronize(c.stream), "ttie_copy_bsr");
+    return TTIE_OK;
+}
+
+ttie_status ttie_pcg(ttie_ctx *h, const void *d_rhs, void *d_out, double rtol, int max_it, int *iters, double *rel_residual) {
+    if (!h) return TTIE_ERR_INVALID;
+    Ctx &c = h->c;
+    if (!c.have_bsr) return set_err(c, TTIE_ERR_STATE, "ttie_pcg: call ttie_assemble first");
+    if (!d_rhs || !d_out || !(rtol > 0.0) || max_it < 1) return set_err(c, TTIE_ERR_INVALID, "ttie_pcg: arguments");
+    cudaError_t e = c.prm.precision == TTIE_F64
+                        ? pcg_solve<double>(c, (const double *)d_rhs, (double *)d_out, rtol, max_it)
+                        : pcg_solve<float>(c, (const float *)d_rhs, (float *)d_out, rtol, max_it);
+    if (e != cudaSuccess) return cuda_err(c, e, "ttie_pcg");
+    CK(cudaMemcpyAsync(c.hs, c.ds, sizeof(DevScalars), cudaMemcpyDeviceToHost, c.stream), "ttie_pcg");
+    CK(cudaStreamSynchronize(c.stream), "ttie_pcg");
+    if (iters) *iters = c.hs->pcg_iters;
+    const double rel = c.hs->red[1] > 0.0 ? std::sqrt(c.hs->red[4] / c.hs->red[1]) : 0.0;
+    if (rel_residual) *rel_residual = rel;
+    if (!std::isfinite(rel)) return set_err(c, TTIE_ERR_NONFINITE, "ttie_pcg: residual is not finite");
+    return TTIE_OK;
+}
+
+ttie_status ttie_newton_step(ttie_ctx *h, void *d_x_inout, ttie_step_info *info) {
+    if (!h) return TTIE_ERR_INVALID;
+    Ctx &c = h->c;
+    if (!c.have_mesh) return set_err(c, TTIE_ERR_STATE, "ttie_newton_step: call ttie_build_bvh first");
+    if (!d_x_inout) return set_err(c, TTIE_ERR_INVALID, "ttie_newton_step: null positions");
+    if (c.prm.precision == TTIE_F64) return newton_impl<double>(c, (double *)d_x_inout, info);
+    return newton_impl<float>(c, (float *)d_x_inout, info);
+}
+
+ttie_status ttie_solve(ttie_ctx *h, void *d_x_inout, ttie_solve_info *info) {
+    if (!h) return TTIE_ERR_INVALID;
+    Ctx &c = h->c;
+    if (!c.have_mesh) return set_err(c, TTIE_ERR_STATE, "ttie_solve: call ttie_build_bvh first");
+    if (!d_x_inout) return set_err(c, TTIE_ERR_INVALID, "ttie_solve: null positions");
+    ttie_solve_info inf;
+    std::memset(&inf, 0, sizeof inf);
+    const auto t0 = std::chrono::steady_clock::now();
+    ttie_status s = TTIE_OK;
+    int it = 0;
+    for (;; ++it) {
+        ttie_step_info st;
+        s = ttie_newton_step(h, d_x_inout, &st);
+        if (s != TTIE_OK) break;
+        if (it == 0) {
+            inf.energy_initial = st.energy;
+            inf.n_active_initial = st.n_active;
+        }
+        inf.energy_final = st.energy;
+        inf.n_active_final = st.n_active;
+        if (st.n_active == 0) {
+            inf.converged = 1;
+            break;
+        }
+        if (it >= c.prm.newton_max_it) {
+            s = set_err(c, TTIE_ERR_NOT_CONVERGED, "ttie_solve: %d iterations, %lld pairs still intersect", it,
+                        (long long)st.n_active);
+            break;
+        }
+    }
+    inf.iterations = it;
+    inf.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (info) *info = inf;
+    return s;
+}
+
+ttie_status ttie_get_candidates(ttie_ctx *h, int32_t *d_out, int64_t capacity, int64_t *n) {
+    if (!h) return TTIE_ERR_INVALID;
+    Ctx &c = h->c;
+    if (!c.have_cand) return set_err(c, TTIE_ERR_STATE, "ttie_get_candidates: no candidates");
+    if (n) *n = c.n_cand;
+    if (!d_out) return TTIE_OK;
+    if (capacity < c.n_cand) return set_err(c, TTIE_ERR_INVALID, "ttie_get_candidates: capacity %lld < %lld",
+                                            (long long)capacity, (long long)c.n_cand);
+    if (c.n_cand) CK(cudaMemcpyAsync(d_out, c.cand.p, (size_t)c.n_cand * sizeof(int2), cudaMemcpyDeviceToDevice, c.stream), "get");
+    CK(cudaStreamSynchronize(c.stream), "ttie_get_candidates");
+    return TTIE_OK;
+}
+
+ttie_status ttie_get_active(ttie_ctx *h, int32_t *d_pairs, void *d_tc, void *d_dtc, int64_t capacity, int64_t *n) {
+    if (!h) return TTIE_ERR_INVALID;
+    Ctx &c = h->c;
+    if (!c.have_eval) return set_err(c, TTIE_ERR_STATE, "ttie_get_active: no evaluation");
+    if (n) *n = c.n_active;
+    if (!d_pairs && !d_tc && !d_dtc) return TTIE_OK;
+    if (capacity < c.n_active) return set_err(c, TTIE_ERR_INVALID, "ttie_get_active: capacity too small");
+    if ((d_tc || d_dtc) && !(c.eval_what & (TTIE_EVAL_G | TTIE_EVAL_H)))
+        return set_err(c, TTIE_ERR_STATE, "ttie_get_active: t_c and gradients need TTIE_EVAL_G or TTIE_EVAL_H");
+    const int64_t na = c.n_active;
+    if (na > 0) {
+        if (d_pairs)
+            k_gather_active<<<grid_for(na, kThreads), kThreads, 0, c.stream>>>((const int2 *)c.cand.p,
+                                                                              (const uint32_t *)c.active.p, na,
+                                                                              (int2 *)d_pairs);
+        if (d_tc || d_dtc) {
+            if (c.prm.precision == TTIE_F64)
+                k_split_fac<double><<<grid_for(na, kThreads), kThreads, 0, c.stream>>>((const double *)c.fac.p, na,
+                                                                                      (double *)d_tc, (double *)d_dtc);
+            else
+                k_split_fac<float><<<grid_for(na, kThreads), kThreads, 0, c.stream>>>((const float *)c.fac.p, na,
+                                                                                     (float *)d_tc, (float *)d_dtc);
+        }
+        CK(cudaGetLastError(), "ttie_get_active");
+    }
+    CK(cudaStreamSynchronize(c.stream), "ttie_get_active");
+    return TTIE_OK;
+}
+
+ttie_status ttie_get_direction(ttie_ctx *h, void *d_out) {
+    if (!h) return TTIE_ERR_INVALID;
+    Ctx &c = h->c;
+    if (!c.have_dir) return set_err(c, TTIE_ERR_STATE, "ttie_get_direction: no Newton direction");
+    if (!d_out) return set_err(c, TTIE_ERR_INVALID, "ttie_get_direction: null output");
+    const size_t es = c.prm.precision == TTIE_F64 ? 8 : 4;
+    CK(cudaMemcpyAsync(d_out, c.dir.p, (size_t)c.V * 3 * es, cudaMemcpyDeviceToDevice, c.stream), "ttie_get_direction");
+    CK(cudaStreamSynchronize(c.stream), "ttie_get_direction");
+    return TTIE_OK;
+}
+
+ttie_status ttie_get_filter_stats(ttie_ctx *h, int64_t *out3) {
+    if (!h) return TTIE_ERR_INVALID;
+    Ctx &c = h->c;
+    if (!out3) return set_err(c, TTIE_ERR_INVALID, "ttie_get_filter_stats: null output");
+    CK(cudaMemcpyAsync(c.hs->filter_stats, c.ds->filter_stats, 3 * 8, cudaMemcpyDeviceToHost, c.stream), "stats");
+    CK(cudaStreamSynchronize(c.stream), "stats");
+    for (int i = 0; i < 3; ++i) out3[i] = (int64_t)c.hs->filter_stats[i];
+    return TTIE_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,165 @@
+// Internal declarations shared by the translation units of libttie.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <string>
+
+#include "ttie.h"
+
+namespace ttie {
+
+// ------------------------------------------------------------------ vector types
+struct alignas(32) dvec4 { double x, y, z, w; };
+
+template <typename T> struct vec4_of;
+template <> struct vec4_of<float> { typedef float4 type; };
+template <> struct vec4_of<double> { typedef dvec4 type; };
+template <typename T> using vec4_t = typename vec4_of<T>::type;
+
+template <typename T> struct v3 { T x, y, z; };
+
+template <typename T> __host__ __device__ __forceinline__ v3<T> mk(T x, T y, T z) { return {x, y, z}; }
+template <typename T> __host__ __device__ __forceinline__ v3<T> xyz(const vec4_t<T> &a) { return {a.x, a.y, a.z}; }
+template <typename T> __host__ __device__ __forceinline__ v3<T> operator+(v3<T> a, v3<T> b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
+template <typename T> __host__ __device__ __forceinline__ v3<T> operator-(v3<T> a, v3<T> b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+template <typename T> __host__ __device__ __forceinline__ v3<T> operator*(T s, v3<T> a) { return {s * a.x, s * a.y, s * a.z}; }
+template <typename T> __host__ __device__ __forceinline__ T dot(v3<T> a, v3<T> b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+template <typename T> __host__ __device__ __forceinline__ v3<T> cross(v3<T> a, v3<T> b) {
+    return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+template <typename T> __host__ __device__ __forceinline__ v3<T> vabs(v3<T> a) { return {fabs(a.x), fabs(a.y), fabs(a.z)}; }
+// |a| x |b| componentwise "absolute cross product": the permanent of the cross product
+template <typename T> __host__ __device__ __forceinline__ v3<T> abs_cross(v3<T> a, v3<T> b) {
+    return {fabs(a.y * b.z) + fabs(a.z * b.y), fabs(a.z * b.x) + fabs(a.x * b.z), fabs(a.x * b.y) + fabs(a.y * b.x)};
+}
+
+template <typename T> struct Box { vec4_t<T> lo, hi; };
+
+// ------------------------------------------------------------------ device scalars
+// One small block of device memory holding counters and reduction results; it is
+// copied to a pinned host mirror when the host needs a value.
+enum ErrBits : int {
+    ERR_NONFINITE = 1,      // NaN / Inf in positions
+    ERR_BAD_INDEX = 2,      // triangle index outside [0, V) or group outside [0, 2^20)
+    ERR_STACK = 4,          // traversal stack overflow
+    ERR_DEFER = 8,          // exact-resolve list overflow
+};
+
+struct DevScalars {
+    unsigned long long n_cand;
+    unsigned long long n_active;
+    unsigned long long n_defer;
+    unsigned long long n_rows;
+    unsigned long long nnzb;
+    unsigned long long n_groups_seen;
+    unsigned long long filter_stats[3];   // signs decided by FP32 filter, FP64 filter, exact
+    int err;
+    int max_group;
+    unsigned int done_counter[8];         // "last block" reduction tickets
+    unsigned long long bounds_lo[3];      // scene bounds as order-preserving integers
+    unsigned long long bounds_hi[3];
+    double energy;
+    double trace;                          // sum of diag(H+) over active DOFs
+    double mu;
+    double red[8];                         // PCG scalars
+    int pcg_done;
+    int pcg_iters;
+};
+
+// ------------------------------------------------------------------ buffers
+struct Buf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+struct Ctx;
+cudaError_t ensure(Ctx &c, Buf &b, size_t bytes);   // grow-only, contents not kept
+
+#define TTIE_BUFS(X)                                                                       \
+    X(tri4) X(grp) X(xp) X(xq) X(tbox) X(mkey) X(mkey2) X(perm) X(perm2) X(sort_cnt)       \
+    X(node_box) X(node_child) X(node_parent) X(node_range) X(visit) X(leaf_group)          \
+    X(group_range) X(cand_cnt) X(cand_off) X(cand) X(scan_tmp) X(act_bits) X(word_off)     \
+    X(defer) X(active) X(fac) X(partials) X(vflag) X(vrow) X(row_vertex) X(bkey) X(bkey2)   \
+    X(bval) X(bval2) X(bflag) X(run_start) X(row_ptr) X(col_idx) X(bsr_val) X(rhs)         \
+    X(zfac) X(dinv) X(pcg_x) X(pcg_r) X(pcg_z) X(pcg_p) X(pcg_q) X(dir) X(xt) X(gtmp)      \
+    X(xsave) X(sweep_cand)
+
+struct Ctx {
+    ttie_params prm;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    std::string err;
+    // topology recorded by ttie_build_bvh
+    bool have_mesh = false;
+    int64_t V = 0, F = 0;
+    int x_stride = 3;
+    bool have_group = false;
+    int n_groups = 1;
+    int group_bits = 0;
+    // state of the last calls
+    bool have_cand = false;
+    int64_t n_cand = 0;
+    bool have_eval = false;
+    unsigned eval_what = 0;
+    int64_t n_active = 0;
+    bool have_bsr = false;
+    int64_t n_rows = 0, nnzb = 0;
+    bool have_dir = false;
+    int64_t defer_cap = 0;
+    // memory
+    DevScalars *ds = nullptr;     // device
+    DevScalars *hs = nullptr;     // pinned host mirror
+#define TTIE_DECL_BUF(name) Buf name;
+    TTIE_BUFS(TTIE_DECL_BUF)
+#undef TTIE_DECL_BUF
+    cudaEvent_t ev[12] = {};
+};
+
+// ------------------------------------------------------------------ launch helpers
+constexpr int kNumSMs = 152;
+inline unsigned grid_for(int64_t n, int threads, int64_t cap = 152 * 16) {
+    int64_t g = (n + threads - 1) / threads;
+    if (g < 1) g = 1;
+    if (g > cap) g = cap;
+    return (unsigned)g;
+}
+
+// ------------------------------------------------------------------ primitives (sort_scan.cu)
+// Exclusive scan of n uint32 counts into uint64 offsets; out[n] = total.
+cudaError_t scan_u32_u64(Ctx &c, const uint32_t *in, unsigned long long *out, int64_t n);
+// Stable LSD radix sort of (key, value) by the low `bits` bits of key.  The result is
+// left in keys/vals; keys2/vals2 are scratch of the same size.
+cudaError_t radix_sort(Ctx &c, unsigned long long *keys, uint32_t *vals, unsigned long long *keys2,
+                       uint32_t *vals2, int64_t n, int bits);
+
+// ------------------------------------------------------------------ broad phase (bvh.cu)
+template <typename T> cudaError_t pack_positions(Ctx &c, const T *x, int stride, vec4_t<T> *out);
+cudaError_t pack_topology(Ctx &c, const int32_t *tri, const int32_t *group);
+template <typename T> cudaError_t build_candidates(Ctx &c, const vec4_t<T> *x0, const vec4_t<T> *x1,
+                                                   Buf &out_pairs, int64_t *n_out);
+cudaError_t brute_candidates(Ctx &c, Buf &out_pairs, int64_t *n_out);
+
+// ------------------------------------------------------------------ narrow phase (pair_eval.cu)
+// what: TTIE_EVAL_* bits.  Classifies the n candidate pairs at x, compacts the
+// intersecting ones (ctx.active), and with G|H writes their t_c and gradients (ctx.fac).
+// Energy lands in ds->energy, count in ds->n_active.
+template <typename T> cudaError_t eval_candidates(Ctx &c, const vec4_t<T> *x, const int2 *pairs, int64_t n,
+                                                  unsigned what);
+
+// ------------------------------------------------------------------ assembly / solve (assemble.cu)
+template <typename T> cudaError_t assemble_system(Ctx &c, T *grad_out_V3);
+template <typename T> cudaError_t pcg_solve(Ctx &c, const T *rhs, T *out, double rtol, int max_it);
+template <typename T> cudaError_t axpy_positions(Ctx &c, const vec4_t<T> *x, const T *d, T alpha, vec4_t<T> *out);
+template <typename T> cudaError_t scatter_direction(Ctx &c, const T *d_rows, T *d_full);
+template <typename T> cudaError_t update_positions(Ctx &c, T *x, int stride, const T *d_full, T alpha);
+
+}  // namespace ttie
+
+#define TTIE_CUDA_TRY(expr)                              \
+    do {                                                 \
+        cudaError_t _e = (expr);                         \
+        if (_e != cudaSuccess) return _e;                \
+    } while (0)

@@ -1,0 +1,110 @@
+// Exact sign of a 3x3 orientation determinant with floating-point expansions.
+//
+// Method: Shewchuk, "Adaptive Precision Floating-Point Arithmetic and Fast Robust
+// Geometric Predicates" (1997): TWO-SUM, TWO-PRODUCT (here through fma),
+// EXPANSION-SUM and SCALE-EXPANSION produce a non-overlapping expansion whose
+// largest non-zero component has the sign of the exact value.  Written for this
+// library; used only by the kernel that settles signs the floating-point
+// filters could not certify.  Exact for inputs whose products neither
+// overflow nor underflow (always the case for float32 inputs held in doubles).
+#pragma once
+
+namespace ttie {
+namespace exact {
+
+__device__ __forceinline__ void two_sum(double a, double b, double &x, double &y) {
+    x = a + b;
+    double bv = x - a;
+    double av = x - bv;
+    y = (a - av) + (b - bv);
+}
+
+// requires |a| >= |b| or a == 0
+__device__ __forceinline__ void fast_two_sum(double a, double b, double &x, double &y) {
+    x = a + b;
+    y = b - (x - a);
+}
+
+__device__ __forceinline__ void two_prod(double a, double b, double &x, double &y) {
+    x = a * b;
+    y = fma(a, b, -x);
+}
+
+// h[0 .. m+n) = e[0 .. m) + f[0 .. n); every f component is grown into the running sum.
+__device__ __forceinline__ int expansion_sum(int m, const double *e, int n, const double *f, double *h) {
+    for (int i = 0; i < m; ++i) h[i] = e[i];
+    for (int j = 0; j < n; ++j) {
+        double q = f[j];
+        for (int i = j; i < j + m; ++i) {
+            double lo;
+            two_sum(q, h[i], q, lo);
+            h[i] = lo;
+        }
+        h[j + m] = q;
+    }
+    return m + n;
+}
+
+// h[0 .. 2m) = b * e[0 .. m)
+__device__ __forceinline__ int scale_expansion(int m, const double *e, double b, double *h) {
+    double q, t, tt;
+    two_prod(e[0], b, q, h[0]);
+    for (int i = 1; i < m; ++i) {
+        two_prod(e[i], b, tt, t);
+        two_sum(q, t, q, h[2 * i - 1]);
+        fast_two_sum(tt, q, q, h[2 * i]);
+    }
+    h[2 * m - 1] = q;
+    return 2 * m;
+}
+
+__device__ __forceinline__ int expansion_sign(int m, const double *e) {
+    for (int i = m - 1; i >= 0; --i) {
+        if (e[i] > 0.0) return 1;
+        if (e[i] < 0.0) return -1;
+    }
+    return 0;
+}
+
+// px*qy - qx*py as a 4-component expansion
+__device__ __forceinline__ void minor2(double px, double py, double qx, double qy, double *h) {
+    double a[2], b[2];
+    two_prod(px, qy, a[1], a[0]);
+    two_prod(qx, py, b[1], b[0]);
+    b[0] = -b[0];
+    b[1] = -b[1];
+    expansion_sum(2, a, 2, b, h);
+}
+
+// det [[px py 1] [qx qy 1] [rx ry 1]] = m(p,q) + m(q,r) + m(r,p): 12 components
+__device__ __forceinline__ void det3xy1(const double *p, const double *q, const double *r, double *h) {
+    double m1[4], m2[4], m3[4], s[8];
+    minor2(p[0], p[1], q[0], q[1], m1);
+    minor2(q[0], q[1], r[0], r[1], m2);
+    minor2(r[0], r[1], p[0], p[1], m3);
+    expansion_sum(4, m1, 4, m2, s);
+    expansion_sum(8, s, 4, m3, h);
+}
+
+// Sign of det[b - a, c - a, d - a] (positive when d lies on the side of the plane
+// (a, b, c) that the normal (b - a) x (c - a) points to).
+// The 4x4 determinant with rows (x, y, z, 1) of a, b, c, d, expanded along z, equals
+// -det[b - a, c - a, d - a].
+__device__ __noinline__ int orient3d_exact(const double *a, const double *b, const double *c, const double *d) {
+    double t12[12], s24a[24], s24b[24], s48a[48], s48b[48], s96[96];
+    det3xy1(b, c, d, t12);
+    scale_expansion(12, t12, a[2], s24a);
+    det3xy1(a, c, d, t12);
+    scale_expansion(12, t12, -b[2], s24b);
+    expansion_sum(24, s24a, 24, s24b, s48a);
+    det3xy1(a, b, d, t12);
+    scale_expansion(12, t12, c[2], s24a);
+    det3xy1(a, b, c, t12);
+    scale_expansion(12, t12, -d[2], s24b);
+    expansion_sum(24, s24a, 24, s24b, s48b);
+    expansion_sum(48, s48a, 48, s48b, s96);
+    return -expansion_sign(96, s96);
+}
+
+}  // namespace exact
+}  // namespace ttie

@@ -1,0 +1,506 @@
+// Narrow phase and energy (§1, Eq. 1-3, Appendix A).
+//
+// 1. k_classify: one thread per candidate pair.  The pair intersects iff each
+//    triangle has vertices strictly on both sides of the other's plane and the
+//    open intervals I_a, I_b on the intersection line overlap (0 inside I_c).
+//    Every sign of that test is certified: an FP32 determinant with a forward
+//    error bound, then FP64 with its bound; signs neither can certify send the
+//    pair to k_resolve (exact expansions).  The interval comparison is recast
+//    as orientation signs: with p1 the vertex of A alone on its side of plane B
+//    and q1 the vertex of B alone on its side of plane A, the endpoint on edge
+//    (p1, p_u) and the endpoint on edge (q1, q_v) compare as
+//        sign(t_v - t_u) = -s_p s_q sign det[p_u - p1, q_v - q1, q1 - p1]
+//    (s_p, s_q the sides of p1 and q1), and the intervals overlap openly iff
+//    these four signs include both a positive and a negative one.
+// 2. k_compact: intersecting pairs in candidate order.
+// 3. k_derivs: t_c^0, t_c^1 (Eq. 1), T (Eq. 2) and the analytic gradients of
+//    t_c^0 and t_c^1 for each intersecting pair (manual chain rule through the
+//    Möller construction, as §1.2 describes), plus the FP64 energy sum.
+#include "common.cuh"
+#include "exact.cuh"
+
+namespace ttie {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+// ---------------------------------------------------------------- certified signs
+// Sign of det[e1, e2, f] = (e1 x e2) . f, given n = e1 x e2 and N = |e1| x |e2|
+// (componentwise absolute cross product).  The rounding error of the computed value
+// is below ~8u times the permanent N.|f| (u: unit roundoff), so a sign is trusted
+// only beyond 1e-6 (FP32, ~17u) or 2e-15 (FP64, ~18u) times the permanent.
+// Returns +1 / -1, or 0 when the filter cannot decide.
+__device__ __forceinline__ int filt_f32(v3<float> n, v3<float> N, v3<float> f) {
+    float d = dot(n, f);
+    float perm = dot(N, vabs(f));
+    if (!(perm > 1e-30f) || !(perm < 1e30f)) return 0;
+    float bound = 1e-6f * perm;
+    return d > bound ? 1 : (d < -bound ? -1 : 0);
+}
+__device__ __forceinline__ int filt_f64(v3<double> n, v3<double> N, v3<double> f) {
+    double d = dot(n, f);
+    double perm = dot(N, vabs(f));
+    if (!(perm > 1e-280) || !(perm < 1e280)) return 0;
+    double bound = 2e-15 * perm;
+    return d > bound ? 1 : (d < -bound ? -1 : 0);
+}
+__device__ __forceinline__ v3<double> to_d(v3<float> a) { return {(double)a.x, (double)a.y, (double)a.z}; }
+__device__ __forceinline__ v3<double> to_d(v3<double> a) { return a; }
+
+// det[p1 - p0, p2 - p0, q - p0] in FP64 from the original coordinates
+template <typename T>
+__device__ __noinline__ int side_f64(v3<T> p0, v3<T> p1, v3<T> p2, v3<T> q) {
+    v3<double> a = to_d(p0), e1 = to_d(p1) - a, e2 = to_d(p2) - a, f = to_d(q) - a;
+    return filt_f64(cross(e1, e2), abs_cross(e1, e2), f);
+}
+
+__device__ __forceinline__ int orient_exact(v3<double> a, v3<double> b, v3<double> c, v3<double> d) {
+    double A[3] = {a.x, a.y, a.z}, B[3] = {b.x, b.y, b.z}, C[3] = {c.x, c.y, c.z}, D[3] = {d.x, d.y, d.z};
+    return exact::orient3d_exact(A, B, C, D);
+}
+
+struct Stats {
+    unsigned long long f32 = 0, f64 = 0, ex = 0;
+};
+
+// Sides of Q's vertices w.r.t. the plane of P: s[k] in {+1, -1}, or 0 if undecided.
+template <typename T>
+__device__ __forceinline__ void sides(const v3<T> P[3], const v3<T> Q[3], int s[3], bool exact_only, Stats &st);
+
+template <>
+__device__ __forceinline__ void sides<float>(const v3<float> P[3], const v3<float> Q[3], int s[3], bool exact_only,
+                                             Stats &st) {
+    v3<float> e1 = P[1] - P[0], e2 = P[2] - P[0];
+    v3<float> n = cross(e1, e2), N = abs_cross(e1, e2);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        s[k] = exact_only ? 0 : filt_f32(n, N, Q[k] - P[0]);
+        if (s[k]) {
+            ++st.f32;
+        } else if (!exact_only) {
+            s[k] = side_f64<float>(P[0], P[1], P[2], Q[k]);
+            if (s[k]) ++st.f64;
+        }
+    }
+}
+template <>
+__device__ __forceinline__ void sides<double>(const v3<double> P[3], const v3<double> Q[3], int s[3], bool exact_only,
+                                              Stats &st) {
+    v3<double> e1 = P[1] - P[0], e2 = P[2] - P[0];
+    v3<double> n = cross(e1, e2), N = abs_cross(e1, e2);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        s[k] = exact_only ? 0 : filt_f64(n, N, Q[k] - P[0]);
+        if (s[k]) ++st.f64;
+    }
+}
+
+// det[pu - p1, qv - q1, q1 - p1]
+template <typename T>
+__device__ __forceinline__ int overlap_sign(v3<T> p1, v3<T> pu, v3<T> q1, v3<T> qv, bool exact_only, Stats &st);
+
+template <>
+__device__ __forceinline__ int overlap_sign<float>(v3<float> p1, v3<float> pu, v3<float> q1, v3<float> qv,
+                                                   bool exact_only, Stats &st) {
+    if (!exact_only) {
+        v3<float> e1 = pu - p1, e2 = qv - q1;
+        int s = filt_f32(cross(e1, e2), abs_cross(e1, e2), q1 - p1);
+        if (s) { ++st.f32; return s; }
+        v3<double> d1 = to_d(pu) - to_d(p1), d2 = to_d(qv) - to_d(q1), f = to_d(q1) - to_d(p1);
+        s = filt_f64(cross(d1, d2), abs_cross(d1, d2), f);
+        if (s) { ++st.f64; return s; }
+    }
+    return 0;
+}
+template <>
+__device__ __forceinline__ int overlap_sign<double>(v3<double> p1, v3<double> pu, v3<double> q1, v3<double> qv,
+                                                    bool exact_only, Stats &st) {
+    if (!exact_only) {
+        v3<double> e1 = pu - p1, e2 = qv - q1;
+        int s = filt_f64(cross(e1, e2), abs_cross(e1, e2), q1 - p1);
+        if (s) { ++st.f64; return s; }
+    }
+    return 0;
+}
+
+// Index of the vertex whose side is unique among three non-zero sides, or -1.
+__device__ __forceinline__ int lone_of(const int s[3]) {
+    if (s[0] == s[1] && s[1] != s[2]) return 2;
+    if (s[0] == s[2] && s[0] != s[1]) return 1;
+    if (s[1] == s[2] && s[0] != s[1]) return 0;
+    return -1;
+}
+
+template <typename T>
+__device__ __forceinline__ void load_pair(const vec4_t<T> *__restrict__ x, const int4 *__restrict__ tri4, int2 pr,
+                                          v3<T> A[3], v3<T> B[3]) {
+    int4 ta = tri4[pr.x], tb = tri4[pr.y];
+    A[0] = xyz<T>(x[ta.x]); A[1] = xyz<T>(x[ta.y]); A[2] = xyz<T>(x[ta.z]);
+    B[0] = xyz<T>(x[tb.x]); B[1] = xyz<T>(x[tb.y]); B[2] = xyz<T>(x[tb.z]);
+}
+
+// 1: intersecting, 0: not, -1: undecided (needs exact arithmetic)
+template <typename T>
+__device__ __forceinline__ int classify(const v3<T> A[3], const v3<T> B[3], bool exact_only, Stats &st) {
+    int sB[3], sA[3];
+    sides<T>(A, B, sB, exact_only, st);
+    if (sB[0] && sB[0] == sB[1] && sB[1] == sB[2]) return 0;   // B on one side of plane A
+    sides<T>(B, A, sA, exact_only, st);
+    if (sA[0] && sA[0] == sA[1] && sA[1] == sA[2]) return 0;
+    if (!(sB[0] && sB[1] && sB[2] && sA[0] && sA[1] && sA[2])) return -1;
+    const int ip = lone_of(sA), iq = lone_of(sB);
+    const int sp = sA[ip], sq = sB[iq];
+    const v3<T> p1 = A[ip], pu = A[(ip + 1) % 3], pw = A[(ip + 2) % 3];
+    const v3<T> q1 = B[iq], qv = B[(iq + 1) % 3], qw = B[(iq + 2) % 3];
+    int d0 = overlap_sign<T>(p1, pu, q1, qv, exact_only, st);
+    int d1 = overlap_sign<T>(p1, pu, q1, qw, exact_only, st);
+    int d2 = overlap_sign<T>(p1, pw, q1, qv, exact_only, st);
+    int d3 = overlap_sign<T>(p1, pw, q1, qw, exact_only, st);
+    if (!(d0 && d1 && d2 && d3)) return -1;
+    const int f = -sp * sq;
+    const int s0 = f * d0, s1 = f * d1, s2 = f * d2, s3 = f * d3;
+    const bool pos = s0 > 0 || s1 > 0 || s2 > 0 || s3 > 0;
+    const bool neg = s0 < 0 || s1 < 0 || s2 < 0 || s3 < 0;
+    return (pos && neg) ? 1 : 0;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_classify(const vec4_t<T> *__restrict__ x, const int4 *__restrict__ tri4,
+                                                       const int2 *__restrict__ pairs, int64_t n, int exact_only,
+                                                       uint32_t *__restrict__ bits, uint32_t *__restrict__ defer,
+                                                       DevScalars *ds) {
+    const int lane = threadIdx.x & 31;
+    const int64_t n_words = (n + 31) / 32;
+    const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t n_warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    Stats st;
+    for (int64_t w = warp0; w < n_words; w += n_warps) {
+        const int64_t p = w * 32 + lane;
+        int r = 0;
+        if (p < n) {
+            v3<T> A[3], B[3];
+            load_pair<T>(x, tri4, pairs[p], A, B);
+            r = classify<T>(A, B, exact_only != 0, st);
+        }
+        const unsigned act = __ballot_sync(0xffffffffu, r == 1);
+        const unsigned und = __ballot_sync(0xffffffffu, r == -1);
+        if (lane == 0) bits[w] = act;
+        if (und) {
+            unsigned long long base = 0;
+            if (lane == 0) base = atomicAdd(&ds->n_defer, (unsigned long long)__popc(und));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (r == -1) defer[base + __popc(und & ((1u << lane) - 1u))] = (uint32_t)p;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        st.f32 += __shfl_xor_sync(0xffffffffu, st.f32, o);
+        st.f64 += __shfl_xor_sync(0xffffffffu, st.f64, o);
+    }
+    if (lane == 0 && (st.f32 | st.f64)) {
+        atomicAdd(&ds->filter_stats[0], st.f32);
+        atomicAdd(&ds->filter_stats[1], st.f64);
+    }
+}
+
+// Exact decision of the undecided pairs (§1's criterion with exact signs; a vertex
+// exactly on the plane counts as zero, touching intervals do not overlap).
+template <typename T>
+__global__ void k_resolve(const vec4_t<T> *__restrict__ x, const int4 *__restrict__ tri4, const int2 *__restrict__ pairs,
+                          const uint32_t *__restrict__ defer, uint32_t *__restrict__ bits, DevScalars *ds) {
+    const unsigned long long m = ds->n_defer;
+    unsigned long long cnt = 0;
+    for (unsigned long long k = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; k < m;
+         k += (unsigned long long)gridDim.x * blockDim.x) {
+        const uint32_t p = defer[k];
+        v3<T> A_[3], B_[3];
+        load_pair<T>(x, tri4, pairs[p], A_, B_);
+        v3<double> A[3], B[3];
+        for (int i = 0; i < 3; ++i) { A[i] = to_d(A_[i]); B[i] = to_d(B_[i]); }
+        int sB[3], sA[3];
+        for (int i = 0; i < 3; ++i) sB[i] = orient_exact(A[0], A[1], A[2], B[i]);
+        cnt += 3;
+        int posB = (sB[0] > 0) + (sB[1] > 0) + (sB[2] > 0), negB = (sB[0] < 0) + (sB[1] < 0) + (sB[2] < 0);
+        if (!(posB && negB)) continue;
+        for (int i = 0; i < 3; ++i) sA[i] = orient_exact(B[0], B[1], B[2], A[i]);
+        cnt += 3;
+        int posA = (sA[0] > 0) + (sA[1] > 0) + (sA[2] > 0), negA = (sA[0] < 0) + (sA[1] < 0) + (sA[2] < 0);
+        if (!(posA && negA)) continue;
+        // a vertex whose (non-zero) side is unique
+        int ip = 0, iq = 0;
+        for (int i = 0; i < 3; ++i) {
+            int same = (sA[i] == sA[0]) + (sA[i] == sA[1]) + (sA[i] == sA[2]);
+            if (sA[i] != 0 && same == 1) { ip = i; break; }
+        }
+        for (int i = 0; i < 3; ++i) {
+            int same = (sB[i] == sB[0]) + (sB[i] == sB[1]) + (sB[i] == sB[2]);
+            if (sB[i] != 0 && same == 1) { iq = i; break; }
+        }
+        const int f = -sA[ip] * sB[iq];
+        bool pos = false, neg = false;
+        for (int u = 1; u <= 2; ++u)
+            for (int v = 1; v <= 2; ++v) {
+                // det[pu - p1, qv - q1, q1 - p1] = det[pu - p1, qv - p1, q1 - p1]
+                int s = f * orient_exact(A[ip], A[(ip + u) % 3], B[(iq + v) % 3], B[iq]);
+                pos |= s > 0;
+                neg |= s < 0;
+            }
+        cnt += 4;
+        if (pos && neg) atomicOr(&bits[p >> 5], 1u << (p & 31));
+    }
+    if (cnt) atomicAdd(&ds->filter_stats[2], cnt);
+}
+
+__global__ void k_popc(const uint32_t *__restrict__ bits, int64_t n_words, uint32_t *__restrict__ cnt) {
+    for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < n_words; w += (int64_t)gridDim.x * blockDim.x)
+        cnt[w] = __popc(bits[w]);
+}
+
+__global__ void k_compact(const uint32_t *__restrict__ bits, int64_t n_words, const unsigned long long *__restrict__ off,
+                          uint32_t *__restrict__ active, DevScalars *ds) {
+    for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < n_words; w += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t b = bits[w];
+        unsigned long long o = off[w];
+        while (b) {
+            int i = __ffs(b) - 1;
+            active[o++] = (uint32_t)(w * 32 + i);
+            b &= b - 1;
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) ds->n_active = off[n_words];
+}
+
+// ---------------------------------------------------------------- reductions
+template <typename T>
+__device__ __forceinline__ T block_sum(T v) {
+    __shared__ T sh[32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    T r = T(0);
+    if (w == 0) {
+        r = lane < (int)(blockDim.x >> 5) ? sh[lane] : T(0);
+#pragma unroll
+        for (int o = 16; o; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+    }
+    __syncthreads();
+    return r;   // valid in thread 0
+}
+
+// Deterministic grid sum: block partials, then the last block to finish adds them in order.
+__device__ __forceinline__ void grid_sum(double v, double *partials, unsigned int *ticket, double *out) {
+    __shared__ bool last;
+    double b = block_sum(v);
+    if (threadIdx.x == 0) {
+        partials[blockIdx.x] = b;
+        __threadfence();
+        last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (last) {
+        double s = 0.0;
+        for (unsigned i = threadIdx.x; i < gridDim.x; i += blockDim.x) s += __ldcg(&partials[i]);
+        s = block_sum(s);
+        if (threadIdx.x == 0) {
+            *out = s;
+            *ticket = 0u;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- derivatives
+template <typename T> struct Cut {
+    // Segment endpoint on edge (m, p) of the cut triangle: S = (1 - lam) q_m + lam q_p
+    int m0, p0, m1, p1;
+    T lam0, lam1;
+    v3<T> S0, S1;
+};
+
+// Plane-side values and the cut of triangle Q by the plane of P (values only; the
+// sides were certified during classification, here they only pick the edges).
+template <typename T>
+__device__ __forceinline__ Cut<T> cut_by(const v3<T> P[3], const v3<T> Q[3], v3<T> nP) {
+    T d[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) d[k] = dot(nP, Q[k] - P[0]);
+    const int s0 = d[0] >= T(0), s1 = d[1] >= T(0), s2 = d[2] >= T(0);
+    int m;
+    const int pos = s0 + s1 + s2;
+    if (pos == 1) m = s0 ? 0 : (s1 ? 1 : 2);
+    else if (pos == 2) m = !s0 ? 0 : (!s1 ? 1 : 2);
+    else {   // not straddling in this precision (near-degenerate): farthest vertex
+        T a0 = fabs(d[0]), a1 = fabs(d[1]), a2 = fabs(d[2]);
+        m = (a0 >= a1 && a0 >= a2) ? 0 : (a1 >= a2 ? 1 : 2);
+    }
+    Cut<T> c;
+    const int u = (m + 1) % 3, v = (m + 2) % 3;   // the other two, in increasing order
+    c.m0 = m; c.p0 = u < v ? u : v;
+    c.m1 = m; c.p1 = u < v ? v : u;
+    T den0 = d[m] - d[c.p0], den1 = d[m] - d[c.p1];
+    c.lam0 = den0 != T(0) ? d[m] / den0 : T(0.5);
+    c.lam1 = den1 != T(0) ? d[m] / den1 : T(0.5);
+    c.S0 = Q[m] + c.lam0 * (Q[c.p0] - Q[m]);
+    c.S1 = Q[m] + c.lam1 * (Q[c.p1] - Q[m]);
+    return c;
+}
+
+// g[off_Q + 3v + k] += coefficients of d(D.S)/d(vertex) for the endpoint S on edge (m, p) of
+// Q cut by the plane (P, nP), scaled by w:
+//   q_m: (1 - lam) Pd, q_p: lam Pd with Pd = D + rho nP, rho = -(D.e)/(nP.e), e = q_p - q_m
+//   P_k: rho (S - P_0) x (P_{k+2} - P_{k+1}), and P_0 additionally -rho nP
+template <typename T>
+__device__ __forceinline__ void add_endpoint(T *g, int offQ, int offP, const v3<T> P[3], const v3<T> Q[3], v3<T> nP,
+                                             v3<T> D, int m, int p, T lam, v3<T> S, T w) {
+    const v3<T> e = Q[p] - Q[m];
+    const T ne = dot(nP, e);
+    const T rho = ne != T(0) ? -dot(D, e) / ne : T(0);
+    const v3<T> Pd = D + rho * nP;
+#pragma unroll
+    for (int v = 0; v < 3; ++v) {
+        const T cv = w * ((v == m ? T(1) - lam : T(0)) + (v == p ? lam : T(0)));
+        g[offQ + 3 * v + 0] += cv * Pd.x;
+        g[offQ + 3 * v + 1] += cv * Pd.y;
+        g[offQ + 3 * v + 2] += cv * Pd.z;
+    }
+    const v3<T> c = S - P[0];
+    const T wr = w * rho;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        v3<T> t = cross(c, P[(k + 2) % 3] - P[(k + 1) % 3]);
+        if (k == 0) t = t - nP;
+        g[offP + 3 * k + 0] += wr * t.x;
+        g[offP + 3 * k + 1] += wr * t.y;
+        g[offP + 3 * k + 2] += wr * t.z;
+    }
+}
+
+// g += w * d(D.Delta)/dx through D = (nB x nA)/|nB x nA| with Delta fixed:
+//   c = (Delta - (D.Delta) D)/|w|;  b_k: (nA x c) x (b_{k+2} - b_{k+1});  a_k: (c x nB) x (a_{k+2} - a_{k+1})
+template <typename T>
+__device__ __forceinline__ void add_direction(T *g, const v3<T> A[3], const v3<T> B[3], v3<T> nA, v3<T> nB, v3<T> D,
+                                              T inv_w, v3<T> Delta, T w) {
+    const v3<T> c = (w * inv_w) * (Delta - dot(D, Delta) * D);
+    const v3<T> cb = cross(nA, c), ca = cross(c, nB);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const v3<T> tb = cross(cb, B[(k + 2) % 3] - B[(k + 1) % 3]);
+        const v3<T> ta = cross(ca, A[(k + 2) % 3] - A[(k + 1) % 3]);
+        g[9 + 3 * k + 0] += tb.x; g[9 + 3 * k + 1] += tb.y; g[9 + 3 * k + 2] += tb.z;
+        g[3 * k + 0] += ta.x; g[3 * k + 1] += ta.y; g[3 * k + 2] += ta.z;
+    }
+}
+
+// Output row per intersecting pair: [t_c^0, t_c^1, d t_c^0 (18), d t_c^1 (18), pad 2].
+constexpr int kFacStride = 40;
+
+template <typename T, bool kGrad>
+__global__ void __launch_bounds__(128) k_derivs(const vec4_t<T> *__restrict__ x, const int4 *__restrict__ tri4,
+                                                const int2 *__restrict__ pairs, const uint32_t *__restrict__ active,
+                                                T tc_scale, T *__restrict__ fac, double *partials, DevScalars *ds) {
+    const unsigned long long n_act = ds->n_active;
+    double e_sum = 0.0;
+    for (unsigned long long k = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; k < n_act;
+         k += (unsigned long long)gridDim.x * blockDim.x) {
+        v3<T> A[3], B[3];
+        load_pair<T>(x, tri4, pairs[active[k]], A, B);
+        // local frame at A0: T and its gradient are translation invariant, and small
+        // coordinates keep the cancellations in t_c at the size of the triangles
+        const v3<T> o = A[0];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) { A[i] = A[i] - o; B[i] = B[i] - o; }
+        const v3<T> nA = cross(A[1] - A[0], A[2] - A[0]);
+        const v3<T> nB = cross(B[1] - B[0], B[2] - B[0]);
+        const Cut<T> cB = cut_by<T>(A, B, nA);   // segment on B (plane of A)
+        const Cut<T> cA = cut_by<T>(B, A, nB);   // segment on A (plane of B)
+        const v3<T> wv = cross(nB, nA);
+        const T wn = sqrt(dot(wv, wv));
+        const T inv_w = wn > T(0) ? T(1) / wn : T(0);
+        const v3<T> D = inv_w * wv;
+        const T tA0 = dot(D, cA.S0), tA1 = dot(D, cA.S1), tB0 = dot(D, cB.S0), tB1 = dot(D, cB.S1);
+        const bool a0min = !(tA1 < tA0), b0min = !(tB1 < tB0);
+        const T a = tc_scale * ((a0min ? tA0 : tA1) - (b0min ? tB1 : tB0));
+        const T b = tc_scale * ((a0min ? tA1 : tA0) - (b0min ? tB0 : tB1));
+        e_sum += (double)(a * b) * (double)(a * b);
+        T *row = fac + k * kFacStride;
+        row[0] = a;
+        row[1] = b;
+        if (kGrad) {
+            T ga[18], gb[18];
+#pragma unroll
+            for (int i = 0; i < 18; ++i) { ga[i] = T(0); gb[i] = T(0); }
+            // t_c^0 = s (t_A,min - t_B,max), t_c^1 = s (t_A,max - t_B,min)
+            const int amin_m = a0min ? cA.m0 : cA.m1, amin_p = a0min ? cA.p0 : cA.p1;
+            const int amax_m = a0min ? cA.m1 : cA.m0, amax_p = a0min ? cA.p1 : cA.p0;
+            const T amin_l = a0min ? cA.lam0 : cA.lam1, amax_l = a0min ? cA.lam1 : cA.lam0;
+            const v3<T> amin_S = a0min ? cA.S0 : cA.S1, amax_S = a0min ? cA.S1 : cA.S0;
+            const int bmin_m = b0min ? cB.m0 : cB.m1, bmin_p = b0min ? cB.p0 : cB.p1;
+            const int bmax_m = b0min ? cB.m1 : cB.m0, bmax_p = b0min ? cB.p1 : cB.p0;
+            const T bmin_l = b0min ? cB.lam0 : cB.lam1, bmax_l = b0min ? cB.lam1 : cB.lam0;
+            const v3<T> bmin_S = b0min ? cB.S0 : cB.S1, bmax_S = b0min ? cB.S1 : cB.S0;
+            add_endpoint<T>(ga, 0, 9, B, A, nB, D, amin_m, amin_p, amin_l, amin_S, tc_scale);
+            add_endpoint<T>(ga, 9, 0, A, B, nA, D, bmax_m, bmax_p, bmax_l, bmax_S, -tc_scale);
+            add_direction<T>(ga, A, B, nA, nB, D, inv_w, amin_S - bmax_S, tc_scale);
+            add_endpoint<T>(gb, 0, 9, B, A, nB, D, amax_m, amax_p, amax_l, amax_S, tc_scale);
+            add_endpoint<T>(gb, 9, 0, A, B, nA, D, bmin_m, bmin_p, bmin_l, bmin_S, -tc_scale);
+            add_direction<T>(gb, A, B, nA, nB, D, inv_w, amax_S - bmin_S, tc_scale);
+#pragma unroll
+            for (int i = 0; i < 18; ++i) {
+                row[2 + i] = ga[i];
+                row[20 + i] = gb[i];
+            }
+        }
+    }
+    grid_sum(e_sum, partials, &ds->done_counter[0], &ds->energy);
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t eval_candidates(Ctx &c, const vec4_t<T> *x, const int2 *pairs, int64_t n, unsigned what) {
+    const int64_t n_words = (n + 31) / 32;
+    TTIE_CUDA_TRY(ensure(c, c.act_bits, (size_t)(n_words > 0 ? n_words : 1) * 4));
+    TTIE_CUDA_TRY(ensure(c, c.word_off, (size_t)(n_words + 1) * 8));
+    TTIE_CUDA_TRY(ensure(c, c.defer, (size_t)(n > 0 ? n : 1) * 4));
+    TTIE_CUDA_TRY(ensure(c, c.active, (size_t)(n > 0 ? n : 1) * 4));
+    TTIE_CUDA_TRY(ensure(c, c.partials, (size_t)kNumSMs * 16 * sizeof(double)));
+    TTIE_CUDA_TRY(cudaMemsetAsync(&c.ds->n_defer, 0, 8, c.stream));
+    TTIE_CUDA_TRY(cudaMemsetAsync(&c.ds->filter_stats[0], 0, 3 * 8, c.stream));
+    auto *bits = (uint32_t *)c.act_bits.p;
+    const int4 *tri4 = (const int4 *)c.tri4.p;
+    if (n > 0) {
+        const unsigned g = grid_for(n_words * 32, kThreads, (int64_t)kNumSMs * 8);
+        k_classify<T><<<g, kThreads, 0, c.stream>>>(x, tri4, pairs, n, c.prm.exact_only, bits,
+                                                     (uint32_t *)c.defer.p, c.ds);
+        k_resolve<T><<<kNumSMs * 4, 64, 0, c.stream>>>(x, tri4, pairs, (const uint32_t *)c.defer.p, bits, c.ds);
+        TTIE_CUDA_TRY(ensure(c, c.gtmp, (size_t)(n_words > 0 ? n_words : 1) * 4));
+        k_popc<<<grid_for(n_words, kThreads), kThreads, 0, c.stream>>>(bits, n_words, (uint32_t *)c.gtmp.p);
+        TTIE_CUDA_TRY(scan_u32_u64(c, (const uint32_t *)c.gtmp.p, (unsigned long long *)c.word_off.p, n_words));
+        k_compact<<<grid_for(n_words, kThreads), kThreads, 0, c.stream>>>(
+            bits, n_words, (const unsigned long long *)c.word_off.p, (uint32_t *)c.active.p, c.ds);
+    } else {
+        TTIE_CUDA_TRY(cudaMemsetAsync(&c.ds->n_active, 0, 8, c.stream));
+    }
+    TTIE_CUDA_TRY(cudaGetLastError());
+    const bool grad = (what & (TTIE_EVAL_G | TTIE_EVAL_H)) != 0;
+    // read the count (one sync) so the per-pair rows are sized by the active set
+    TTIE_CUDA_TRY(cudaMemcpyAsync(&c.hs->n_active, &c.ds->n_active, 8, cudaMemcpyDeviceToHost, c.stream));
+    TTIE_CUDA_TRY(cudaStreamSynchronize(c.stream));
+    const int64_t n_act = (int64_t)c.hs->n_active;
+    TTIE_CUDA_TRY(ensure(c, c.fac, (size_t)(n_act > 0 ? n_act : 1) * kFacStride * sizeof(T)));
+    const unsigned gd = grid_for(n_act, 128, (int64_t)kNumSMs * 8);
+    if (grad)
+        k_derivs<T, true><<<gd, 128, 0, c.stream>>>(x, tri4, pairs, (const uint32_t *)c.active.p, (T)c.prm.tc_scale,
+                                                     (T *)c.fac.p, (double *)c.partials.p, c.ds);
+    else
+        k_derivs<T, false><<<gd, 128, 0, c.stream>>>(x, tri4, pairs, (const uint32_t *)c.active.p, (T)c.prm.tc_scale,
+                                                      (T *)c.fac.p, (double *)c.partials.p, c.ds);
+    c.n_active = n_act;
+    return cudaGetLastError();
+}
+template cudaError_t eval_candidates<float>(Ctx &, const float4 *, const int2 *, int64_t, unsigned);
+template cudaError_t eval_candidates<double>(Ctx &, const dvec4 *, const int2 *, int64_t, unsigned);
+
+}  // namespace ttie

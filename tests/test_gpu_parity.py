@@ -1,0 +1,280 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Integer results are compared bit-exactly: the candidate pair set (closed box
+overlap, non-adjacent), the intersecting pair set and the block pattern.  FP32
+values are compared with a tolerance derived from the arithmetic (see
+``_cases.fp32_tolerance``); the FP64 form with relative 1e-5 (T) and 1e-4
+(gradients, Hessian blocks) on pairs with min(|t_c^0|, |t_c^1|) > 1e-6 of the
+bounding-box diagonal.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import ttie_inputs as ti
+from _cases import MODE, fp32_tolerance, pair_set, small_cases
+
+pytestmark = pytest.mark.gpu
+
+CASES = small_cases()
+
+
+@pytest.fixture(scope="module")
+def ttie():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2606_06511_gb300 import ttie as t
+    return t
+
+
+def _ctx(ttie, mode, precision=0, brute=False, **kw):
+    pm = MODE[mode] | (ttie.PAIRS_BRUTE if brute else 0)
+    return ttie.Context(precision=precision, pair_mode=pm, **kw)
+
+
+def _dev(m, dtype=torch.float32):
+    x = torch.tensor(m.x, dtype=dtype, device="cuda")
+    tri = torch.tensor(m.tri, dtype=torch.int32, device="cuda")
+    grp = torch.tensor(m.group, dtype=torch.int32, device="cuda")
+    return x, tri, grp
+
+
+_oracle_cache = {}
+
+
+def _oracle(name):
+    if name not in _oracle_cache:
+        m, mode = CASES[name]
+        pairs = O.candidate_pairs(m.x, m.tri, m.group, mode)
+        ev = O.evaluate(m.x, m.tri, pairs)
+        _oracle_cache[name] = (pairs, ev)
+    return _oracle_cache[name]
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_candidates_bit_exact(ttie, name):
+    m, mode = CASES[name]
+    x, tri, grp = _dev(m)
+    ctx = _ctx(ttie, mode)
+    n = ctx.build_bvh(x, tri, grp)
+    got = ctx.get_candidates().cpu().numpy()
+    pairs, _ = _oracle(name)
+    assert n == len(pairs)
+    assert np.all(got[:, 0] < got[:, 1])
+    assert pair_set(got) == pair_set(pairs)
+    # deterministic order
+    ctx.build_bvh(x, tri, grp)
+    assert np.array_equal(ctx.get_candidates().cpu().numpy(), got)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("exact_only", [0, 1])
+def test_active_set_bit_exact(ttie, name, exact_only):
+    m, mode = CASES[name]
+    x, tri, grp = _dev(m)
+    ctx = _ctx(ttie, mode, exact_only=exact_only)
+    ctx.build_bvh(x, tri, grp)
+    E, n_act = ctx.eval_pairs(x, ttie.EVAL_E)
+    pairs, ev = _oracle(name)
+    act_pairs, _, _ = ctx.get_active(with_derivatives=False)
+    assert n_act == int(ev.active.sum())
+    assert pair_set(act_pairs.cpu().numpy()) == pair_set(pairs[ev.active])
+    st = ctx.get_filter_stats()
+    if exact_only:
+        assert st["fp32"] == 0 and st["fp64"] == 0
+
+
+def _match(ctx, pairs, ev):
+    ap, tc, dtc = ctx.get_active()
+    ap = ap.cpu().numpy().astype(np.int64)
+    tc = tc.double().cpu().numpy()
+    dtc = dtc.double().cpu().numpy()
+    idx = {tuple(p): k for k, p in enumerate(pairs.tolist())}
+    k = np.array([idx[tuple(p)] for p in ap.tolist()], dtype=np.int64)
+    return ap, tc, dtc, k
+
+
+def _pair_size(m, pairs):
+    v = np.concatenate([m.x[m.tri[pairs[:, 0]]], m.x[m.tri[pairs[:, 1]]]], axis=1)
+    return (v.max(1) - v.min(1)).max(1)
+
+
+@pytest.mark.parametrize("name", ["cloth40", "spheres_inter", "soup", "tori", "ellipsoids_intra"])
+def test_energy_and_gradient_fp32(ttie, name):
+    m, mode = CASES[name]
+    x, tri, grp = _dev(m)
+    ctx = _ctx(ttie, mode)
+    ctx.build_bvh(x, tri, grp)
+    E, n_act = ctx.eval_pairs(x, ttie.EVAL_E | ttie.EVAL_H)
+    pairs, ev = _oracle(name)
+    ap, tc, dtc, k = _match(ctx, pairs, ev)
+    T_or = ev.T[k]
+    g_or = O.gradient(ev)[k]
+    T_gpu = (tc[:, 0] * tc[:, 1]) ** 2
+    L = _pair_size(m, ap)
+    tol = fp32_tolerance(T_or, g_or, L)
+    bad = np.abs(T_gpu - T_or) > tol
+    assert not bad.any(), (np.abs(T_gpu - T_or)[bad][:5], T_or[bad][:5])
+    assert abs(E - ev.T.sum()) <= 1e-5 * ev.T.sum() + tol.sum()
+    # gradient of T per pair (Eq. 3) from the GPU's t_c and their gradients
+    a, b = tc[:, 0], tc[:, 1]
+    g_gpu = (2 * a * b * b)[:, None] * dtc[:, 0] + (2 * b * a * a)[:, None] * dtc[:, 1]
+    H_or = O.hessian_inexact(O.PairEval(ev.pairs[k], ev.tc[k], ev.dtc[k], ev.sides64[k], ev.flags64[k],
+                                        ev.active[k]))
+    gtol = 1e-4 * np.abs(g_or).max(1, keepdims=True) + 64 * 2.0 ** -24 * L[:, None] * np.abs(H_or).sum(2)
+    well = np.minimum(np.abs(ev.tc[k, 0]), np.abs(ev.tc[k, 1])) > 1e-2 * L
+    assert well.sum() > 0.5 * len(k)
+    bad = (np.abs(g_gpu - g_or) > gtol)[well]
+    assert not bad.any(), np.abs(g_gpu - g_or)[well][bad][:5]
+
+
+@pytest.mark.parametrize("name", ["spheres_inter", "cloth40"])
+def test_fp64_form_meets_relative_tolerances(ttie, name):
+    m, mode = CASES[name]
+    x, tri, grp = _dev(m, torch.float64)
+    ctx = _ctx(ttie, mode, precision=ttie.F64, brute=(name == "spheres_inter"))
+    n = ctx.build_bvh(x, tri, grp)
+    if name == "spheres_inter":
+        assert n == 320 * 320
+    E, n_act = ctx.eval_pairs(x, ttie.EVAL_E | ttie.EVAL_H)
+    pairs, ev = _oracle(name)
+    assert n_act == int(ev.active.sum())
+    ap, tc, dtc, k = _match(ctx, pairs, ev)
+    diag = np.linalg.norm(m.x.max(0) - m.x.min(0))
+    mask = np.minimum(np.abs(ev.tc[k, 0]), np.abs(ev.tc[k, 1])) > 1e-6 * diag
+    T_gpu = (tc[:, 0] * tc[:, 1]) ** 2
+    assert np.allclose(T_gpu[mask], ev.T[k][mask], rtol=1e-5, atol=0)
+    a, b = tc[:, 0], tc[:, 1]
+    g_gpu = (2 * a * b * b)[:, None] * dtc[:, 0] + (2 * b * a * a)[:, None] * dtc[:, 1]
+    g_or = O.gradient(ev)[k]
+    err = np.abs(g_gpu - g_or).max(1) / np.abs(g_or).max(1)
+    assert (err[mask] <= 1e-4).all(), err[mask].max()
+    assert E == pytest.approx(ev.T.sum(), rel=1e-9)
+
+
+@pytest.mark.parametrize("name,precision", [("cloth40", 0), ("tori", 0), ("spheres_inter", 1)])
+def test_assembly_pattern_and_values(ttie, name, precision):
+    m, mode = CASES[name]
+    dt = torch.float64 if precision else torch.float32
+    x, tri, grp = _dev(m, dt)
+    ctx = _ctx(ttie, mode, precision=precision)
+    ctx.build_bvh(x, tri, grp)
+    grad_full = torch.zeros((m.V, 3), dtype=dt, device="cuda")
+    ctx.eval_pairs(x, ttie.EVAL_E | ttie.EVAL_G | ttie.EVAL_H, grad=grad_full)
+    bsr = ctx.assemble()
+    pairs, ev = _oracle(name)
+    grad_or, blocks = O.assemble(m.tri, ev, m.V)
+    rows = bsr.vertex_of_row.cpu().numpy()
+    rp = bsr.row_ptr.cpu().numpy()
+    ci = bsr.col_idx.cpu().numpy()
+    val = bsr.val.double().cpu().numpy()
+    got = {}
+    for r in range(len(rows)):
+        for b in range(rp[r], rp[r + 1]):
+            got[(int(rows[r]), int(rows[ci[b]]))] = val[b]
+    assert set(got) == set(blocks)                      # pattern bit-exact
+    assert np.all(np.diff(rows) > 0)
+    for r in range(len(rows)):                          # columns ascending within a row
+        assert np.all(np.diff(ci[rp[r]:rp[r + 1]]) > 0)
+    scale = max(np.abs(b).max() for b in blocks.values())
+    tol = 1e-4 if precision else 2e-3
+    for key, b in blocks.items():
+        assert np.allclose(got[key], b, rtol=tol, atol=tol * scale), key
+    g = grad_full.double().cpu().numpy()
+    assert np.allclose(g, grad_or, rtol=tol, atol=tol * np.abs(grad_or).max())
+    assert np.allclose(bsr.grad.double().cpu().numpy(), grad_or[rows], rtol=tol, atol=tol * np.abs(grad_or).max())
+    # deterministic
+    ctx.eval_pairs(x, ttie.EVAL_E | ttie.EVAL_H)
+    bsr2 = ctx.assemble()
+    assert torch.equal(bsr2.val, bsr.val) and torch.equal(bsr2.col_idx, bsr.col_idx)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_pcg_matches_direct_solve(ttie, precision):
+    name = "cloth40"
+    m, mode = CASES[name]
+    dt = torch.float64 if precision else torch.float32
+    x, tri, grp = _dev(m, dt)
+    ctx = _ctx(ttie, mode, precision=precision)
+    ctx.build_bvh(x, tri, grp)
+    ctx.eval_pairs(x, ttie.EVAL_E | ttie.EVAL_H)
+    bsr = ctx.assemble()
+    rhs = -bsr.grad
+    d, iters, rel = ctx.pcg(rhs.contiguous(), rtol=1e-7 if precision else 1e-5, max_it=5000)
+    pairs, ev = _oracle(name)
+    _, blocks = O.assemble(m.tri, ev, m.V)
+    rows = bsr.vertex_of_row.cpu().numpy()
+    H = O.blocks_to_dense(blocks, rows)
+    mu = 1e-3 * np.mean(np.diag(H))
+    sol = np.linalg.solve(H + mu * np.eye(len(H)), -bsr.grad.double().cpu().numpy().ravel())
+    dd = d.double().cpu().numpy().ravel()
+    err = np.linalg.norm(dd - sol) / np.linalg.norm(sol)
+    assert err < (1e-5 if precision else 2e-2), (err, iters, rel)
+
+
+def test_newton_step_descends(ttie):
+    m, mode = CASES["cloth40"]
+    x, tri, grp = _dev(m)
+    ctx = _ctx(ttie, mode)
+    ctx.build_bvh(x, tri, grp)
+    info = ctx.newton_step(x)
+    assert info["n_active"] > 0 and info["grad_dot_dir"] < 0
+    assert info["energy_new"] < info["energy"] or info["n_active_new"] == 0
+    assert info["n_candidates_swept"] >= info["n_candidates"]
+    d = ctx.get_direction()
+    assert torch.isfinite(d).all()
+
+
+@pytest.mark.parametrize("case", ["spheres_shallow", "cloth_mild"])
+def test_solve_certified_intersection_free(ttie, case):
+    if case == "spheres_shallow":
+        m, mode = ti.two_icospheres(offset=(1.95, 0.0, 0.0)).as_f32(), "inter"
+    else:
+        m, mode = ti.cloth(16, seed=2, shear=0.05).as_f32(), "self"
+    x, tri, grp = _dev(m)
+    ctx = _ctx(ttie, mode, newton_max_it=40)
+    ctx.build_bvh(x, tri, grp)
+    info = ctx.solve(x)
+    assert info["converged"] == 1, info
+    xf = x.double().cpu().numpy()
+    assert O.certify(xf, m.tri, m.group, mode) == 0
+
+
+def test_errors_are_status_codes(ttie):
+    m, mode = CASES["cloth40"]
+    x, tri, grp = _dev(m)
+    ctx = _ctx(ttie, mode)
+    with pytest.raises(ttie.TTIEError) as e:
+        ctx.eval_pairs(x)
+    assert e.value.status == ttie.TTIE_ERR_STATE
+    bad = tri.clone()
+    bad[5, 1] = m.V + 3
+    with pytest.raises(ttie.TTIEError) as e:
+        ctx.build_bvh(x, bad)
+    assert e.value.status == ttie.TTIE_ERR_INVALID
+    xn = x.clone()
+    xn[7, 2] = float("nan")
+    with pytest.raises(ttie.TTIEError) as e:
+        ctx.build_bvh(xn, tri)
+    assert e.value.status == ttie.TTIE_ERR_NONFINITE
+    ctx.build_bvh(x, tri)
+    with pytest.raises(ttie.TTIEError) as e:
+        ctx.eval_pairs(xn)
+    assert e.value.status == ttie.TTIE_ERR_NONFINITE
+    # the context stays usable after errors
+    ctx.build_bvh(x, tri)
+    E, n = ctx.eval_pairs(x)
+    assert n > 0
+
+
+def test_degenerate_sizes(ttie):
+    ctx = _ctx(ttie, "self")
+    x = torch.tensor([[0, 0, 0], [1, 0, 0], [0, 1, 0]], dtype=torch.float32, device="cuda")
+    tri = torch.tensor([[0, 1, 2]], dtype=torch.int32, device="cuda")
+    assert ctx.build_bvh(x, tri) == 0
+    assert ctx.eval_pairs(x) == (0.0, 0)
+    assert ctx.newton_step(x)["n_active"] == 0
+    tri0 = torch.zeros((0, 3), dtype=torch.int32, device="cuda")
+    assert ctx.build_bvh(x, tri0) == 0
+    assert ctx.eval_pairs(x) == (0.0, 0)
