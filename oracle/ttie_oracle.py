@@ -278,6 +278,7 @@ class NewtonParams:
     ls_max_halvings: int = 20
     newton_max_it: int = 200
     push_eta: float = 0.5         # first trial step 1 + eta (overshoot past touching)
+    max_step: float = 1.0         # largest vertex move per iteration, in mean edge lengths (0: none)
     mode: str = "self"
 
 
@@ -308,7 +309,8 @@ def newton_direction(x, tri, group, prm: NewtonParams):
 
 def newton_solve(x0, tri, group=None, prm: NewtonParams | None = None, log=None):
     """Inexact Newton on E = sum T with a backtracking line search; stops when no pair
-    intersects (decided exactly).
+    intersects (decided exactly).  The direction is scaled so that no vertex moves more
+    than max_step mean edge lengths (of the initial mesh) per iteration.
 
     The minimum T = 0 of a pair is reached at touching, which a Newton iteration on (ab)^2
     only approaches; so every iteration first tries the overshoot step 1 + push_eta, then
@@ -316,12 +318,17 @@ def newton_solve(x0, tri, group=None, prm: NewtonParams | None = None, log=None)
     E(x + a d) <= E(x) + c a g.d or leaves no intersecting pair."""
     prm = prm or NewtonParams()
     x = np.array(x0, dtype=np.float64)
+    edges = np.concatenate([x[tri[:, 1]] - x[tri[:, 0]], x[tri[:, 2]] - x[tri[:, 1]], x[tri[:, 0]] - x[tri[:, 2]]])
+    cap = prm.max_step * float(np.linalg.norm(edges, axis=1).mean())
     for it in range(prm.newton_max_it):
         E, n_act, grad, d, verts = newton_direction(x, tri, group, prm)
         if log is not None:
             log.append((it, E, n_act))
         if n_act == 0:
             return x, it, True
+        dmax = float(np.linalg.norm(d, axis=1).max())
+        if cap > 0 and dmax > cap:
+            d = d * (cap / dmax)
         slope = float(np.sum(grad * d))
         alphas = [1.0 + prm.push_eta] + [0.5 ** k for k in range(prm.ls_max_halvings + 1)]
         for a in alphas:
