@@ -40,7 +40,7 @@ typedef enum {
     TTIE_ERR_INVALID = 1,        /* bad argument (null pointer, size, index out of range) */
     TTIE_ERR_CUDA = 2,           /* a CUDA runtime call failed */
     TTIE_ERR_OOM = 3,            /* a device allocation failed */
-    TTIE_ERR_CAPACITY = 4,       /* a bounded internal structure overflowed (BVH stack) */
+    TTIE_ERR_CAPACITY = 4,       /* a bounded structure overflowed (BVH stack, max_candidates) */
     TTIE_ERR_NONFINITE = 5,      /* NaN or Inf in positions, energy or solver residual */
     TTIE_ERR_NOT_CONVERGED = 6,  /* iteration limit reached */
     TTIE_ERR_STATE = 7           /* calls made out of order (e.g. eval before build) */
@@ -83,13 +83,18 @@ typedef struct {
     double push_eta;      /* first trial step 1 + push_eta (overshoot past touching) */
     int exact_only;       /* test switch: decide every sign with exact arithmetic  */
     int profile;          /* record per-stage GPU times in ttie_step_info          */
+    double max_step;      /* Newton step cap: largest vertex move per iteration, in
+                             mean edge lengths of the mesh (0 = no cap)            */
+    int64_t max_candidates; /* cap on a candidate list (0 = 64 F + 1e6); a larger
+                             list is refused with TTIE_ERR_CAPACITY               */
 } ttie_params;
 
 typedef struct ttie_ctx ttie_ctx;
 
 /* Fills *p with the defaults: F32, SELF, PER_PART, tc_scale 1, mu_rel 1e-3,
  * pcg_rtol 1e-3, pcg_max_it 200, newton_max_it 200, ls_max_halvings 20,
- * armijo_c 1e-4, push_eta 0.5, exact_only 0, profile 0. */
+ * armijo_c 1e-4, push_eta 0.5, exact_only 0, profile 0, max_step 1,
+ * max_candidates 0. */
 void ttie_default_params(ttie_params *p);
 
 /* Creates a context on the current CUDA device.  stream: a cudaStream_t or NULL

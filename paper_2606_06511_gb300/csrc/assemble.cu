@@ -303,7 +303,10 @@ __global__ void k_pcg_update(const T *__restrict__ dinv, const T *__restrict__ p
     if (ds->pcg_done) return;
     const unsigned long long nr = ds->n_rows;
     const double pq = ds->red[2];
-    const T alpha = (T)(pq != 0.0 ? ds->red[0] / pq : 0.0);
+    // breakdown (p.q <= 0 from rounding on a near-singular system): no update, except at the
+    // first iteration, where x = p = M^-1 r0 (the preconditioned gradient step) is kept
+    const bool ok = pq > 0.0 && isfinite(pq);
+    const T alpha = (T)(ok ? ds->red[0] / pq : (ds->pcg_iters == 0 ? 1.0 : 0.0));
     double rz = 0.0, rr = 0.0;
     for (unsigned long long row = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; row < nr;
          row += (unsigned long long)gridDim.x * blockDim.x) {
@@ -330,7 +333,7 @@ __global__ void k_pcg_update(const T *__restrict__ dinv, const T *__restrict__ p
         ds->red[0] = t[0];
         ds->red[4] = t[1];
         ds->pcg_iters += 1;
-        if (t[1] <= rtol2 * ds->red[1] || !(pq > 0.0) || !isfinite(t[1])) ds->pcg_done = 1;
+        if (t[1] <= rtol2 * ds->red[1] || !ok || !isfinite(t[1])) ds->pcg_done = 1;
     });
 }
 

@@ -364,7 +364,8 @@ cudaError_t pack_topology(Ctx &c, const int32_t *tri, const int32_t *group) {
 static int mode_of(const Ctx &c) { return c.prm.pair_mode & 3; }
 
 template <typename T>
-cudaError_t build_candidates(Ctx &c, const vec4_t<T> *x0, const vec4_t<T> *x1, Buf &out_pairs, int64_t *n_out) {
+cudaError_t build_candidates(Ctx &c, const vec4_t<T> *x0, const vec4_t<T> *x1, Buf &out_pairs, int64_t *n_out,
+                             int64_t cap) {
     const int n = (int)c.F;
     const int mode = mode_of(c);
     *n_out = 0;
@@ -423,6 +424,10 @@ cudaError_t build_candidates(Ctx &c, const vec4_t<T> *x0, const vec4_t<T> *x1, B
     TTIE_CUDA_TRY(cudaMemcpyAsync(&c.hs->n_cand, off + n, 8, cudaMemcpyDeviceToHost, c.stream));
     TTIE_CUDA_TRY(cudaStreamSynchronize(c.stream));
     total = c.hs->n_cand;
+    if ((int64_t)total > cap) {
+        *n_out = (int64_t)total;
+        return cudaSuccess;
+    }
     TTIE_CUDA_TRY(ensure(c, out_pairs, (size_t)(total > 0 ? total : 1) * sizeof(int2)));
     if (total > 0)
         k_traverse<T, true><<<g, kThreads, 0, c.stream>>>(n, child, range, nbox, perm, (const int4 *)c.tri4.p,
@@ -432,8 +437,38 @@ cudaError_t build_candidates(Ctx &c, const vec4_t<T> *x0, const vec4_t<T> *x1, B
     *n_out = (int64_t)total;
     return cudaGetLastError();
 }
-template cudaError_t build_candidates<float>(Ctx &, const float4 *, const float4 *, Buf &, int64_t *);
-template cudaError_t build_candidates<double>(Ctx &, const dvec4 *, const dvec4 *, Buf &, int64_t *);
+template cudaError_t build_candidates<float>(Ctx &, const float4 *, const float4 *, Buf &, int64_t *, int64_t);
+template cudaError_t build_candidates<double>(Ctx &, const dvec4 *, const dvec4 *, Buf &, int64_t *, int64_t);
+
+namespace {
+template <typename T>
+__global__ void k_edge_sum(const vec4_t<T> *__restrict__ x, const int4 *__restrict__ tri4, int64_t F, double *out) {
+    __shared__ double sh[32];
+    double s = 0.0;
+    for (int64_t f = threadIdx.x; f < F; f += blockDim.x) {
+        const int4 t = tri4[f];
+        const v3<T> a = xyz<T>(x[t.x]), b = xyz<T>(x[t.y]), c = xyz<T>(x[t.z]);
+        const v3<T> e0 = b - a, e1 = c - b, e2 = a - c;
+        s += sqrt((double)dot(e0, e0)) + sqrt((double)dot(e1, e1)) + sqrt((double)dot(e2, e2));
+    }
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+        *out = F > 0 ? t / (3.0 * (double)F) : 0.0;
+    }
+}
+}  // namespace
+
+// Mean edge length over all triangles (one block: a fixed summation order).
+template <typename T> cudaError_t mean_edge_length(Ctx &c, const vec4_t<T> *x, double *out_dev) {
+    k_edge_sum<T><<<1, 1024, 0, c.stream>>>(x, (const int4 *)c.tri4.p, c.F, out_dev);
+    return cudaGetLastError();
+}
+template cudaError_t mean_edge_length<float>(Ctx &, const float4 *, double *);
+template cudaError_t mean_edge_length<double>(Ctx &, const dvec4 *, double *);
 
 cudaError_t brute_candidates(Ctx &c, Buf &out_pairs, int64_t *n_out) {
     const int n = (int)c.F;

@@ -28,7 +28,6 @@ cudaError_t ensure(Ctx &c, Buf &b, size_t bytes) {
     return cudaSuccess;
 }
 
-template <typename T> cudaError_t dot_rows(Ctx &c, const T *a, const T *b, int64_t n3, double *out_dev);
 
 namespace {
 
@@ -39,20 +38,40 @@ __global__ void k_copy_neg(const T *__restrict__ a, T *__restrict__ b, int64_t n
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) b[i] = -a[i];
 }
 
+// g.d (FP64) and the largest vertex displacement |d_r| over the rows; one block, so the
+// summation order is fixed.
 template <typename T>
-__global__ void k_dot(const T *__restrict__ a, const T *__restrict__ b, int64_t n, double *out) {
-    __shared__ double sh[32];
-    double s = 0.0;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        s += (double)a[i] * (double)b[i];
-    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+__global__ void k_dir_stats(const T *__restrict__ g, const T *__restrict__ d, int64_t n_rows, double *out) {
+    __shared__ double sh_s[32], sh_m[32];
+    double s = 0.0, m = 0.0;
+    for (int64_t r = threadIdx.x; r < n_rows; r += blockDim.x) {
+        const double d0 = d[3 * r], d1 = d[3 * r + 1], d2 = d[3 * r + 2];
+        s += (double)g[3 * r] * d0 + (double)g[3 * r + 1] * d1 + (double)g[3 * r + 2] * d2;
+        m = fmax(m, d0 * d0 + d1 * d1 + d2 * d2);
+    }
+    for (int o = 16; o; o >>= 1) {
+        s += __shfl_xor_sync(0xffffffffu, s, o);
+        m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        sh_s[threadIdx.x >> 5] = s;
+        sh_m[threadIdx.x >> 5] = m;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
-        *out = t;   // single block: deterministic
+        double ts = 0.0, tm = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            ts += sh_s[w];
+            tm = fmax(tm, sh_m[w]);
+        }
+        out[0] = ts;
+        out[1] = sqrt(tm);
     }
+}
+
+template <typename T> __global__ void k_scale(T *a, int64_t n, double s) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        a[i] = (T)(a[i] * s);
 }
 
 __global__ void k_gather_active(const int2 *__restrict__ cand, const uint32_t *__restrict__ active, int64_t n,
@@ -74,8 +93,13 @@ __global__ void k_split_fac(const T *__restrict__ fac, int64_t n, T *__restrict_
 }  // namespace
 
 template <typename T>
-cudaError_t dot_rows(Ctx &c, const T *a, const T *b, int64_t n3, double *out_dev) {
-    k_dot<T><<<1, 1024, 0, c.stream>>>(a, b, n3, out_dev);
+cudaError_t dir_stats(Ctx &c, const T *g, const T *d, int64_t n_rows, double *out_dev) {
+    k_dir_stats<T><<<1, 1024, 0, c.stream>>>(g, d, n_rows, out_dev);
+    return cudaGetLastError();
+}
+
+template <typename T> cudaError_t scale(Ctx &c, T *a, int64_t n, double s) {
+    k_scale<T><<<grid_for(n, kThreads), kThreads, 0, c.stream>>>(a, n, s);
     return cudaGetLastError();
 }
 
@@ -120,7 +144,7 @@ static ttie_status check_params(Ctx &c, const ttie_params *p) {
         return set_err(c, TTIE_ERR_INVALID, "psd_mode");
     if (!(p->tc_scale > 0.0) || !(p->mu_rel >= 0.0) || !(p->pcg_rtol > 0.0) || p->pcg_max_it < 1 ||
         p->newton_max_it < 0 || p->ls_max_halvings < 0 || p->ls_max_halvings > 60 || !(p->armijo_c >= 0.0) ||
-        !(p->push_eta >= 0.0))
+        !(p->push_eta >= 0.0) || !(p->max_step >= 0.0) || p->max_candidates < 0)
         return set_err(c, TTIE_ERR_INVALID, "numeric parameter out of range");
     return TTIE_OK;
 }
@@ -141,6 +165,8 @@ void ttie_default_params(ttie_params *p) {
     p->ls_max_halvings = 20;
     p->armijo_c = 1e-4;
     p->push_eta = 0.5;
+    p->max_step = 1.0;
+    p->max_candidates = 0;
 }
 
 ttie_status ttie_create(ttie_ctx **out, const ttie_params *p, void *stream) {
@@ -207,6 +233,10 @@ ttie_status ttie_set_params(ttie_ctx *h, const ttie_params *p) {
 }  // extern "C"
 
 // ------------------------------------------------------------------ stage helpers
+static int64_t cand_cap(const Ctx &c) {
+    return c.prm.max_candidates > 0 ? c.prm.max_candidates : 64 * c.F + 1000000;
+}
+
 static ttie_status read_err(Ctx &c, const char *where) {
     CK(cudaMemcpyAsync(&c.hs->err, &c.ds->err, sizeof(int), cudaMemcpyDeviceToHost, c.stream), where);
     CK(cudaStreamSynchronize(c.stream), where);
@@ -239,12 +269,19 @@ static ttie_status build_impl(Ctx &c, const T *x, const int32_t *tri, const int3
     }
     c.have_mesh = true;
     int64_t n = 0;
+    CK(mean_edge_length<T>(c, (const vec4_t<T> *)c.xp.p, &c.ds->red[7]), "build");
+    CK(cudaMemcpyAsync(&c.hs->red[7], &c.ds->red[7], sizeof(double), cudaMemcpyDeviceToHost, c.stream), "build");
+    CK(cudaStreamSynchronize(c.stream), "build");
+    c.mean_edge = c.hs->red[7];
     if (c.prm.pair_mode & TTIE_PAIRS_BRUTE)
         CK(brute_candidates(c, c.cand, &n), "build: brute-force pairs");
     else
-        CK(build_candidates<T>(c, (const vec4_t<T> *)c.xp.p, nullptr, c.cand, &n), "build: LBVH");
+        CK(build_candidates<T>(c, (const vec4_t<T> *)c.xp.p, nullptr, c.cand, &n, cand_cap(c)), "build: LBVH");
     s = read_err(c, "ttie_build_bvh");
     if (s != TTIE_OK) return s;
+    if (n > cand_cap(c))
+        return set_err(c, TTIE_ERR_CAPACITY, "ttie_build_bvh: %lld candidate pairs exceed max_candidates %lld",
+                       (long long)n, (long long)cand_cap(c));
     c.n_cand = n;
     c.have_cand = true;
     if (n_cand) *n_cand = n;
@@ -312,7 +349,12 @@ static ttie_status newton_impl(Ctx &c, T *x, ttie_step_info *info) {
     if (c.prm.pair_mode & TTIE_PAIRS_BRUTE)
         CK(brute_candidates(c, c.cand, &n), "newton: pairs");
     else
-        CK(build_candidates<T>(c, (const vec4_t<T> *)c.xp.p, nullptr, c.cand, &n), "newton: LBVH");
+        CK(build_candidates<T>(c, (const vec4_t<T> *)c.xp.p, nullptr, c.cand, &n, cand_cap(c)), "newton: LBVH");
+    if (n > cand_cap(c)) {
+        c.have_cand = false;
+        return set_err(c, TTIE_ERR_CAPACITY, "ttie_newton_step: %lld candidate pairs exceed max_candidates %lld",
+                       (long long)n, (long long)cand_cap(c));
+    }
     c.n_cand = n;
     c.have_cand = true;
     inf.n_candidates = n;
@@ -347,29 +389,46 @@ static ttie_status newton_impl(Ctx &c, T *x, ttie_step_info *info) {
     CK(ensure(c, c.xsave, (size_t)(n3 > 0 ? n3 : 1) * sizeof(T)), "newton");
     CK(negate_copy(c, (const T *)c.rhs.p, (T *)c.xsave.p, n3), "newton");
     CK(pcg_solve<T>(c, (const T *)c.xsave.p, (T *)c.pcg_x.p, c.prm.pcg_rtol, c.prm.pcg_max_it), "newton: PCG");
-    CK(dot_rows<T>(c, (const T *)c.rhs.p, (const T *)c.pcg_x.p, n3, &c.ds->red[6]), "newton");
+    CK(dir_stats<T>(c, (const T *)c.rhs.p, (const T *)c.pcg_x.p, c.n_rows, &c.ds->red[5]), "newton");
+    CK(cudaMemcpyAsync(c.hs, c.ds, sizeof(DevScalars), cudaMemcpyDeviceToHost, c.stream), "newton");
+    CK(cudaStreamSynchronize(c.stream), "newton");
+    double gd = c.hs->red[5];
+    const double dmax = c.hs->red[6];
+    if (!std::isfinite(gd) || !std::isfinite(dmax))
+        return set_err(c, TTIE_ERR_NONFINITE, "ttie_newton_step: Newton direction is not finite");
+    const double cap = c.prm.max_step * c.mean_edge;
+    if (cap > 0.0 && dmax > cap) {   // step cap: no vertex moves more than max_step mean edges
+        CK(scale<T>(c, (T *)c.pcg_x.p, n3, cap / dmax), "newton");
+        gd *= cap / dmax;
+    }
     CK(ensure(c, c.dir, (size_t)c.V * 3 * sizeof(T)), "newton");
     CK(scatter_direction<T>(c, (const T *)c.pcg_x.p, (T *)c.dir.p), "newton");
     c.have_dir = true;
-    CK(cudaMemcpyAsync(c.hs, c.ds, sizeof(DevScalars), cudaMemcpyDeviceToHost, c.stream), "newton");
-    CK(cudaStreamSynchronize(c.stream), "newton");
-    const double gd = c.hs->red[6];
     inf.grad_dot_dir = gd;
     inf.pcg_iters = c.hs->pcg_iters;
     inf.pcg_rel_residual = c.hs->red[1] > 0.0 ? std::sqrt(c.hs->red[4] / c.hs->red[1]) : 0.0;
     mark(c, 4);
     // line search on candidates from the boxes swept between x and x + a_max d
-    const double a_max = 1.0 + c.prm.push_eta;
+    double a_max = 1.0 + c.prm.push_eta;
     CK(ensure(c, c.xq, (size_t)c.V * sizeof(vec4_t<T>)), "newton");
     CK(ensure(c, c.xt, (size_t)c.V * sizeof(vec4_t<T>)), "newton");
-    CK(axpy_positions<T>(c, (const vec4_t<T> *)c.xp.p, (const T *)c.dir.p, (T)a_max, (vec4_t<T> *)c.xq.p), "newton");
     int64_t ns = 0;
     if (c.prm.pair_mode & TTIE_PAIRS_BRUTE) {
         ns = c.n_cand;
         CK(ensure(c, c.sweep_cand, (size_t)(ns > 0 ? ns : 1) * sizeof(int2)), "newton");
         CK(cudaMemcpyAsync(c.sweep_cand.p, c.cand.p, (size_t)ns * sizeof(int2), cudaMemcpyDeviceToDevice, c.stream), "newton");
     } else {
-        CK(build_candidates<T>(c, (const vec4_t<T> *)c.xp.p, (const vec4_t<T> *)c.xq.p, c.sweep_cand, &ns), "newton: sweep");
+        // a swept list beyond the cap shrinks the largest trial step until it fits
+        for (int tries = 0;; ++tries) {
+            CK(axpy_positions<T>(c, (const vec4_t<T> *)c.xp.p, (const T *)c.dir.p, (T)a_max, (vec4_t<T> *)c.xq.p), "newton");
+            CK(build_candidates<T>(c, (const vec4_t<T> *)c.xp.p, (const vec4_t<T> *)c.xq.p, c.sweep_cand, &ns,
+                                   cand_cap(c)), "newton: sweep");
+            if (ns <= cand_cap(c)) break;
+            if (tries >= 12)
+                return set_err(c, TTIE_ERR_CAPACITY, "ttie_newton_step: swept candidates %lld exceed max_candidates",
+                               (long long)ns);
+            a_max *= 0.5;
+        }
     }
     s = read_err(c, "ttie_newton_step");
     if (s != TTIE_OK) return s;
@@ -381,6 +440,7 @@ static ttie_status newton_impl(Ctx &c, T *x, ttie_step_info *info) {
     for (int k = -1; k <= c.prm.ls_max_halvings; ++k) {
         const double a = k < 0 ? a_max : std::ldexp(1.0, -k);
         if (k < 0 && !(a_max > 1.0)) continue;
+        if (a > a_max) continue;   // beyond the swept range
         CK(axpy_positions<T>(c, (const vec4_t<T> *)c.xp.p, (const T *)c.dir.p, (T)a, (vec4_t<T> *)c.xt.p), "newton");
         double Et = 0.0;
         int64_t nt = 0;

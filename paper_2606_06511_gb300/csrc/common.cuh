@@ -108,7 +108,7 @@ struct Ctx {
     bool have_bsr = false;
     int64_t n_rows = 0, nnzb = 0;
     bool have_dir = false;
-    int64_t defer_cap = 0;
+    double mean_edge = 0.0;   // mean edge length at the last ttie_build_bvh
     // memory
     DevScalars *ds = nullptr;     // device
     DevScalars *hs = nullptr;     // pinned host mirror
@@ -138,9 +138,12 @@ cudaError_t radix_sort(Ctx &c, unsigned long long *keys, uint32_t *vals, unsigne
 // ------------------------------------------------------------------ broad phase (bvh.cu)
 template <typename T> cudaError_t pack_positions(Ctx &c, const T *x, int stride, vec4_t<T> *out);
 cudaError_t pack_topology(Ctx &c, const int32_t *tri, const int32_t *group);
+// Candidate pairs whose boxes (over x0, or swept from x0 to x1) overlap.  When the count
+// exceeds `cap` nothing is written and *n_out receives the count.
 template <typename T> cudaError_t build_candidates(Ctx &c, const vec4_t<T> *x0, const vec4_t<T> *x1,
-                                                   Buf &out_pairs, int64_t *n_out);
+                                                   Buf &out_pairs, int64_t *n_out, int64_t cap);
 cudaError_t brute_candidates(Ctx &c, Buf &out_pairs, int64_t *n_out);
+template <typename T> cudaError_t mean_edge_length(Ctx &c, const vec4_t<T> *x, double *out_dev);
 
 // ------------------------------------------------------------------ narrow phase (pair_eval.cu)
 // what: TTIE_EVAL_* bits.  Classifies the n candidate pairs at x, compacts the

@@ -86,11 +86,43 @@ __device__ __forceinline__ void det3xy1(const double *p, const double *q, const 
     expansion_sum(8, s, 4, m3, h);
 }
 
+__device__ __forceinline__ void two_diff(double a, double b, double &x, double &y) {
+    x = a - b;
+    double bv = a - x;
+    double av = x + bv;
+    y = (a - av) + (bv - b);
+}
+
+// Sign of det[e1, e2, f] = e1 . (e2 x f) for exactly known entries: 24 components.
+__device__ __noinline__ int det3_exact(const double *e1, const double *e2, const double *f) {
+    double mx[4], my[4], mz[4], a[8], b[8], c[8], s16[16], s24[24];
+    minor2(e2[1], e2[2], f[1], f[2], mx);   // e2y fz - fy e2z
+    minor2(e2[2], e2[0], f[2], f[0], my);   // e2z fx - fz e2x
+    minor2(e2[0], e2[1], f[0], f[1], mz);   // e2x fy - fx e2y
+    scale_expansion(4, mx, e1[0], a);
+    scale_expansion(4, my, e1[1], b);
+    scale_expansion(4, mz, e1[2], c);
+    expansion_sum(8, a, 8, b, s16);
+    expansion_sum(16, s16, 8, c, s24);
+    return expansion_sign(24, s24);
+}
+
 // Sign of det[b - a, c - a, d - a] (positive when d lies on the side of the plane
-// (a, b, c) that the normal (b - a) x (c - a) points to).
-// The 4x4 determinant with rows (x, y, z, 1) of a, b, c, d, expanded along z, equals
-// -det[b - a, c - a, d - a].
+// (a, b, c) that the normal (b - a) x (c - a) points to).  When the nine coordinate
+// differences are exact doubles (always the case for float32 inputs of similar
+// magnitude) the 3x3 determinant of the differences is expanded directly; otherwise
+// the 4x4 determinant with rows (x, y, z, 1) of a, b, c, d, which expanded along z
+// equals -det[b - a, c - a, d - a].
 __device__ __noinline__ int orient3d_exact(const double *a, const double *b, const double *c, const double *d) {
+    double e1[3], e2[3], f[3], r1, r2, r3;
+    bool exact_diff = true;
+    for (int k = 0; k < 3; ++k) {
+        two_diff(b[k], a[k], e1[k], r1);
+        two_diff(c[k], a[k], e2[k], r2);
+        two_diff(d[k], a[k], f[k], r3);
+        exact_diff &= (r1 == 0.0) && (r2 == 0.0) && (r3 == 0.0);
+    }
+    if (exact_diff) return det3_exact(e1, e2, f);
     double t12[12], s24a[24], s24b[24], s48a[48], s48b[48], s96[96];
     det3xy1(b, c, d, t12);
     scale_expansion(12, t12, a[2], s24a);

@@ -26,33 +26,47 @@ namespace {
 constexpr int kThreads = 256;
 
 // ---------------------------------------------------------------- certified signs
+// Every sign below is +1, -1, 0 (certified zero) or kUndec (not certified).
+constexpr int kUndec = 2;
+
 // Sign of det[e1, e2, f] = (e1 x e2) . f, given n = e1 x e2 and N = |e1| x |e2|
 // (componentwise absolute cross product).  The rounding error of the computed value
 // is below ~8u times the permanent N.|f| (u: unit roundoff), so a sign is trusted
 // only beyond 1e-6 (FP32, ~17u) or 2e-15 (FP64, ~18u) times the permanent.
-// Returns +1 / -1, or 0 when the filter cannot decide.
 __device__ __forceinline__ int filt_f32(v3<float> n, v3<float> N, v3<float> f) {
     float d = dot(n, f);
     float perm = dot(N, vabs(f));
-    if (!(perm > 1e-30f) || !(perm < 1e30f)) return 0;
+    if (!(perm > 1e-30f) || !(perm < 1e30f)) return kUndec;
     float bound = 1e-6f * perm;
-    return d > bound ? 1 : (d < -bound ? -1 : 0);
+    return d > bound ? 1 : (d < -bound ? -1 : kUndec);
 }
 __device__ __forceinline__ int filt_f64(v3<double> n, v3<double> N, v3<double> f) {
     double d = dot(n, f);
     double perm = dot(N, vabs(f));
-    if (!(perm > 1e-280) || !(perm < 1e280)) return 0;
+    if (!(perm > 1e-280) || !(perm < 1e280)) return kUndec;
     double bound = 2e-15 * perm;
-    return d > bound ? 1 : (d < -bound ? -1 : 0);
+    return d > bound ? 1 : (d < -bound ? -1 : kUndec);
 }
 __device__ __forceinline__ v3<double> to_d(v3<float> a) { return {(double)a.x, (double)a.y, (double)a.z}; }
 __device__ __forceinline__ v3<double> to_d(v3<double> a) { return a; }
 
-// det[p1 - p0, p2 - p0, q - p0] in FP64 from the original coordinates
-template <typename T>
-__device__ __noinline__ int side_f64(v3<T> p0, v3<T> p1, v3<T> p2, v3<T> q) {
-    v3<double> a = to_d(p0), e1 = to_d(p1) - a, e2 = to_d(p2) - a, f = to_d(q) - a;
-    return filt_f64(cross(e1, e2), abs_cross(e1, e2), f);
+// det[e1, e2, f] is exactly zero when each of its six terms e1_i e2_j f_k has a factor
+// that is exactly zero (a difference of floating-point numbers is exactly zero only
+// when they are equal).  Aligned meshes (a grid keeping one coordinate exact) produce
+// such determinants at every crossing of two sheets.
+__device__ __forceinline__ bool structural_zero(v3<double> a, v3<double> b, v3<double> f) {
+    const bool ax = a.x == 0.0, ay = a.y == 0.0, az = a.z == 0.0;
+    const bool bx = b.x == 0.0, by = b.y == 0.0, bz = b.z == 0.0;
+    const bool fx = f.x == 0.0, fy = f.y == 0.0, fz = f.z == 0.0;
+    return (ax || by || fz) && (ax || bz || fy) && (ay || bx || fz) && (ay || bz || fx) && (az || bx || fy) &&
+           (az || by || fx);
+}
+
+// FP64 stage: filter, then the structural-zero certificate.
+__device__ __noinline__ int det_sign_f64(v3<double> e1, v3<double> e2, v3<double> f) {
+    const int s = filt_f64(cross(e1, e2), abs_cross(e1, e2), f);
+    if (s != kUndec) return s;
+    return structural_zero(e1, e2, f) ? 0 : kUndec;
 }
 
 __device__ __forceinline__ int orient_exact(v3<double> a, v3<double> b, v3<double> c, v3<double> d) {
@@ -64,73 +78,51 @@ struct Stats {
     unsigned long long f32 = 0, f64 = 0, ex = 0;
 };
 
-// Sides of Q's vertices w.r.t. the plane of P: s[k] in {+1, -1}, or 0 if undecided.
-template <typename T>
-__device__ __forceinline__ void sides(const v3<T> P[3], const v3<T> Q[3], int s[3], bool exact_only, Stats &st);
-
-template <>
-__device__ __forceinline__ void sides<float>(const v3<float> P[3], const v3<float> Q[3], int s[3], bool exact_only,
-                                             Stats &st) {
-    v3<float> e1 = P[1] - P[0], e2 = P[2] - P[0];
-    v3<float> n = cross(e1, e2), N = abs_cross(e1, e2);
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        s[k] = exact_only ? 0 : filt_f32(n, N, Q[k] - P[0]);
-        if (s[k]) {
-            ++st.f32;
-        } else if (!exact_only) {
-            s[k] = side_f64<float>(P[0], P[1], P[2], Q[k]);
-            if (s[k]) ++st.f64;
+// Sign providers.  side(P0, P1, P2, q) = sign det[P1-P0, P2-P0, q-P0] (side of q w.r.t. the
+// plane of P); over(p1, pu, q1, qv) = sign det[pu-p1, qv-q1, q1-p1].
+template <typename T> struct Filtered {
+    bool exact_only;
+    Stats &st;
+    __device__ __forceinline__ int side(v3<T> P0, v3<T> P1, v3<T> P2, v3<T> q) {
+        if (exact_only) return kUndec;
+        int s = kUndec;
+        if (sizeof(T) == 4) {
+            const v3<T> e1 = P1 - P0, e2 = P2 - P0, f = q - P0;
+            s = filt_f32(to_f(cross(e1, e2)), to_f(abs_cross(e1, e2)), to_f(f));
+            if (s != kUndec) { ++st.f32; return s; }
         }
+        const v3<double> a = to_d(P0);
+        s = det_sign_f64(to_d(P1) - a, to_d(P2) - a, to_d(q) - a);
+        if (s != kUndec) ++st.f64;
+        return s;
     }
-}
-template <>
-__device__ __forceinline__ void sides<double>(const v3<double> P[3], const v3<double> Q[3], int s[3], bool exact_only,
-                                              Stats &st) {
-    v3<double> e1 = P[1] - P[0], e2 = P[2] - P[0];
-    v3<double> n = cross(e1, e2), N = abs_cross(e1, e2);
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        s[k] = exact_only ? 0 : filt_f64(n, N, Q[k] - P[0]);
-        if (s[k]) ++st.f64;
+    __device__ __forceinline__ int over(v3<T> p1, v3<T> pu, v3<T> q1, v3<T> qv) {
+        if (exact_only) return kUndec;
+        int s = kUndec;
+        if (sizeof(T) == 4) {
+            const v3<T> e1 = pu - p1, e2 = qv - q1;
+            s = filt_f32(to_f(cross(e1, e2)), to_f(abs_cross(e1, e2)), to_f(q1 - p1));
+            if (s != kUndec) { ++st.f32; return s; }
+        }
+        s = det_sign_f64(to_d(pu) - to_d(p1), to_d(qv) - to_d(q1), to_d(q1) - to_d(p1));
+        if (s != kUndec) ++st.f64;
+        return s;
     }
-}
+    __device__ __forceinline__ static v3<float> to_f(v3<T> a) { return {(float)a.x, (float)a.y, (float)a.z}; }
+};
 
-// det[pu - p1, qv - q1, q1 - p1]
-template <typename T>
-__device__ __forceinline__ int overlap_sign(v3<T> p1, v3<T> pu, v3<T> q1, v3<T> qv, bool exact_only, Stats &st);
-
-template <>
-__device__ __forceinline__ int overlap_sign<float>(v3<float> p1, v3<float> pu, v3<float> q1, v3<float> qv,
-                                                   bool exact_only, Stats &st) {
-    if (!exact_only) {
-        v3<float> e1 = pu - p1, e2 = qv - q1;
-        int s = filt_f32(cross(e1, e2), abs_cross(e1, e2), q1 - p1);
-        if (s) { ++st.f32; return s; }
-        v3<double> d1 = to_d(pu) - to_d(p1), d2 = to_d(qv) - to_d(q1), f = to_d(q1) - to_d(p1);
-        s = filt_f64(cross(d1, d2), abs_cross(d1, d2), f);
-        if (s) { ++st.f64; return s; }
+struct Exact {
+    Stats &st;
+    template <typename T> __device__ int side(v3<T> P0, v3<T> P1, v3<T> P2, v3<T> q) {
+        ++st.ex;
+        return orient_exact(to_d(P0), to_d(P1), to_d(P2), to_d(q));
     }
-    return 0;
-}
-template <>
-__device__ __forceinline__ int overlap_sign<double>(v3<double> p1, v3<double> pu, v3<double> q1, v3<double> qv,
-                                                    bool exact_only, Stats &st) {
-    if (!exact_only) {
-        v3<double> e1 = pu - p1, e2 = qv - q1;
-        int s = filt_f64(cross(e1, e2), abs_cross(e1, e2), q1 - p1);
-        if (s) { ++st.f64; return s; }
+    // det[pu - p1, qv - q1, q1 - p1] = det[pu - p1, qv - p1, q1 - p1]
+    template <typename T> __device__ int over(v3<T> p1, v3<T> pu, v3<T> q1, v3<T> qv) {
+        ++st.ex;
+        return orient_exact(to_d(p1), to_d(pu), to_d(qv), to_d(q1));
     }
-    return 0;
-}
-
-// Index of the vertex whose side is unique among three non-zero sides, or -1.
-__device__ __forceinline__ int lone_of(const int s[3]) {
-    if (s[0] == s[1] && s[1] != s[2]) return 2;
-    if (s[0] == s[2] && s[0] != s[1]) return 1;
-    if (s[1] == s[2] && s[0] != s[1]) return 0;
-    return -1;
-}
+};
 
 template <typename T>
 __device__ __forceinline__ void load_pair(const vec4_t<T> *__restrict__ x, const int4 *__restrict__ tri4, int2 pr,
@@ -140,29 +132,51 @@ __device__ __forceinline__ void load_pair(const vec4_t<T> *__restrict__ x, const
     B[0] = xyz<T>(x[tb.x]); B[1] = xyz<T>(x[tb.y]); B[2] = xyz<T>(x[tb.z]);
 }
 
-// 1: intersecting, 0: not, -1: undecided (needs exact arithmetic)
-template <typename T>
-__device__ __forceinline__ int classify(const v3<T> A[3], const v3<T> B[3], bool exact_only, Stats &st) {
+// First vertex whose side is non-zero and shared by no other vertex.
+__device__ __forceinline__ int lone_of(const int s[3]) {
+    for (int i = 0; i < 3; ++i) {
+        const int same = (s[i] == s[0]) + (s[i] == s[1]) + (s[i] == s[2]);
+        if (s[i] != 0 && same == 1) return i;
+    }
+    return 0;
+}
+
+// 1: intersecting, 0: not, -1: undecided (some deciding sign not certified).
+template <typename T, typename Signs>
+__device__ __forceinline__ int classify(const v3<T> A[3], const v3<T> B[3], Signs &sg) {
     int sB[3], sA[3];
-    sides<T>(A, B, sB, exact_only, st);
-    if (sB[0] && sB[0] == sB[1] && sB[1] == sB[2]) return 0;   // B on one side of plane A
-    sides<T>(B, A, sA, exact_only, st);
-    if (sA[0] && sA[0] == sA[1] && sA[1] == sA[2]) return 0;
-    if (!(sB[0] && sB[1] && sB[2] && sA[0] && sA[1] && sA[2])) return -1;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) sB[k] = sg.side(A[0], A[1], A[2], B[k]);
+    int pos = (sB[0] == 1) + (sB[1] == 1) + (sB[2] == 1);
+    int neg = (sB[0] == -1) + (sB[1] == -1) + (sB[2] == -1);
+    const int undB = (sB[0] == kUndec) + (sB[1] == kUndec) + (sB[2] == kUndec);
+    if (!(pos + undB >= 1 && neg + undB >= 1)) return 0;   // B cannot straddle plane A
+#pragma unroll
+    for (int k = 0; k < 3; ++k) sA[k] = sg.side(B[0], B[1], B[2], A[k]);
+    pos = (sA[0] == 1) + (sA[1] == 1) + (sA[2] == 1);
+    neg = (sA[0] == -1) + (sA[1] == -1) + (sA[2] == -1);
+    const int undA = (sA[0] == kUndec) + (sA[1] == kUndec) + (sA[2] == kUndec);
+    if (!(pos + undA >= 1 && neg + undA >= 1)) return 0;
+    if (undA || undB) return -1;
+    // both straddle: compare the interval endpoints through orientation signs
     const int ip = lone_of(sA), iq = lone_of(sB);
-    const int sp = sA[ip], sq = sB[iq];
+    const int f = -sA[ip] * sB[iq];
     const v3<T> p1 = A[ip], pu = A[(ip + 1) % 3], pw = A[(ip + 2) % 3];
     const v3<T> q1 = B[iq], qv = B[(iq + 1) % 3], qw = B[(iq + 2) % 3];
-    int d0 = overlap_sign<T>(p1, pu, q1, qv, exact_only, st);
-    int d1 = overlap_sign<T>(p1, pu, q1, qw, exact_only, st);
-    int d2 = overlap_sign<T>(p1, pw, q1, qv, exact_only, st);
-    int d3 = overlap_sign<T>(p1, pw, q1, qw, exact_only, st);
-    if (!(d0 && d1 && d2 && d3)) return -1;
-    const int f = -sp * sq;
-    const int s0 = f * d0, s1 = f * d1, s2 = f * d2, s3 = f * d3;
-    const bool pos = s0 > 0 || s1 > 0 || s2 > 0 || s3 > 0;
-    const bool neg = s0 < 0 || s1 < 0 || s2 < 0 || s3 < 0;
-    return (pos && neg) ? 1 : 0;
+    int s[4];
+    s[0] = sg.over(p1, pu, q1, qv);
+    s[1] = sg.over(p1, pu, q1, qw);
+    s[2] = sg.over(p1, pw, q1, qv);
+    s[3] = sg.over(p1, pw, q1, qw);
+    bool any_pos = false, any_neg = false, und = false;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        if (s[k] == kUndec) { und = true; continue; }
+        any_pos |= f * s[k] > 0;
+        any_neg |= f * s[k] < 0;
+    }
+    if (any_pos && any_neg) return 1;
+    return und ? -1 : 0;
 }
 
 template <typename T>
@@ -175,13 +189,14 @@ __global__ void __launch_bounds__(kThreads) k_classify(const vec4_t<T> *__restri
     const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t n_warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     Stats st;
+    Filtered<T> sg{exact_only != 0, st};
     for (int64_t w = warp0; w < n_words; w += n_warps) {
         const int64_t p = w * 32 + lane;
         int r = 0;
         if (p < n) {
             v3<T> A[3], B[3];
             load_pair<T>(x, tri4, pairs[p], A, B);
-            r = classify<T>(A, B, exact_only != 0, st);
+            r = classify<T>(A, B, sg);
         }
         const unsigned act = __ballot_sync(0xffffffffu, r == 1);
         const unsigned und = __ballot_sync(0xffffffffu, r == -1);
@@ -204,52 +219,23 @@ __global__ void __launch_bounds__(kThreads) k_classify(const vec4_t<T> *__restri
     }
 }
 
-// Exact decision of the undecided pairs (§1's criterion with exact signs; a vertex
-// exactly on the plane counts as zero, touching intervals do not overlap).
+// Exact decision of the undecided pairs: the same test with every sign from exact
+// expansion arithmetic (a vertex exactly on a plane counts as zero, touching
+// intervals do not overlap).
 template <typename T>
 __global__ void k_resolve(const vec4_t<T> *__restrict__ x, const int4 *__restrict__ tri4, const int2 *__restrict__ pairs,
                           const uint32_t *__restrict__ defer, uint32_t *__restrict__ bits, DevScalars *ds) {
     const unsigned long long m = ds->n_defer;
-    unsigned long long cnt = 0;
+    Stats st;
+    Exact sg{st};
     for (unsigned long long k = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; k < m;
          k += (unsigned long long)gridDim.x * blockDim.x) {
         const uint32_t p = defer[k];
-        v3<T> A_[3], B_[3];
-        load_pair<T>(x, tri4, pairs[p], A_, B_);
-        v3<double> A[3], B[3];
-        for (int i = 0; i < 3; ++i) { A[i] = to_d(A_[i]); B[i] = to_d(B_[i]); }
-        int sB[3], sA[3];
-        for (int i = 0; i < 3; ++i) sB[i] = orient_exact(A[0], A[1], A[2], B[i]);
-        cnt += 3;
-        int posB = (sB[0] > 0) + (sB[1] > 0) + (sB[2] > 0), negB = (sB[0] < 0) + (sB[1] < 0) + (sB[2] < 0);
-        if (!(posB && negB)) continue;
-        for (int i = 0; i < 3; ++i) sA[i] = orient_exact(B[0], B[1], B[2], A[i]);
-        cnt += 3;
-        int posA = (sA[0] > 0) + (sA[1] > 0) + (sA[2] > 0), negA = (sA[0] < 0) + (sA[1] < 0) + (sA[2] < 0);
-        if (!(posA && negA)) continue;
-        // a vertex whose (non-zero) side is unique
-        int ip = 0, iq = 0;
-        for (int i = 0; i < 3; ++i) {
-            int same = (sA[i] == sA[0]) + (sA[i] == sA[1]) + (sA[i] == sA[2]);
-            if (sA[i] != 0 && same == 1) { ip = i; break; }
-        }
-        for (int i = 0; i < 3; ++i) {
-            int same = (sB[i] == sB[0]) + (sB[i] == sB[1]) + (sB[i] == sB[2]);
-            if (sB[i] != 0 && same == 1) { iq = i; break; }
-        }
-        const int f = -sA[ip] * sB[iq];
-        bool pos = false, neg = false;
-        for (int u = 1; u <= 2; ++u)
-            for (int v = 1; v <= 2; ++v) {
-                // det[pu - p1, qv - q1, q1 - p1] = det[pu - p1, qv - p1, q1 - p1]
-                int s = f * orient_exact(A[ip], A[(ip + u) % 3], B[(iq + v) % 3], B[iq]);
-                pos |= s > 0;
-                neg |= s < 0;
-            }
-        cnt += 4;
-        if (pos && neg) atomicOr(&bits[p >> 5], 1u << (p & 31));
+        v3<T> A[3], B[3];
+        load_pair<T>(x, tri4, pairs[p], A, B);
+        if (classify<T>(A, B, sg) == 1) atomicOr(&bits[p >> 5], 1u << (p & 31));
     }
-    if (cnt) atomicAdd(&ds->filter_stats[2], cnt);
+    if (st.ex) atomicAdd(&ds->filter_stats[2], st.ex);
 }
 
 __global__ void k_popc(const uint32_t *__restrict__ bits, int64_t n_words, uint32_t *__restrict__ cnt) {
