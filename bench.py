@@ -1,0 +1,327 @@
+#!/usr/bin/env python3
+"""Throughput of the TTIE hot path on one GB300 (or N independent replicas).
+
+A step is one full inexact-Newton iteration of the library on the workload's
+initial state: LBVH candidates, certified narrow phase, energy / gradient /
+PSD Hessian of every intersecting pair, block-CSR assembly, PCG, and the
+line search with its swept-box candidates.  ``value`` is candidate pairs
+through that step per second (whole job), inputs resident in HBM.  ``e2e`` is
+the same metric through the public API with the positions copied host->device
+before and device->host after every step.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+``--impl reference`` times the CPU oracle (the program the CUDA path is
+checked against) on a bounded sample of the same workload.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "TTIE pair evals/s (E+grad+PSD Hess+assembly); seconds to intersection-free"
+UNIT = "pair evals/s"
+L2_FLUSH_BYTES = 256 << 20   # larger than the 129 MB L2
+
+
+def workload(name):
+    import ttie_inputs as ti
+    if name == "cloth256":
+        return ti.cloth(256, seed=2).as_f32(), 0, (
+            "cloth 256x256 vertices (130,050 triangles) on [0,1]^2, z = 8 seeded sinusoids "
+            "(A~U[0.05,0.3], k~U[2,12]), x += 0.4*g(x,y) with g an independent 8-sinusoid field "
+            "(folds that cross themselves); self pairs, LBVH; float32")
+    if name == "cloth256_literal":
+        return ti.cloth(256, seed=2, crossing=False).as_f32(), 0, (
+            "cloth 256x256 (130,050 triangles), x += 0.4*z shear (intersection-free by construction)")
+    if name == "noisy_sphere":
+        return ti.noisy_sphere(9, seed=5).as_f32(), 0, (
+            "octahedral sphere level 9 (2,097,152 triangles) displaced by 0.15*(N1,N2,N3) value noise")
+    raise SystemExit("unknown workload %s" % name)
+
+
+def oracle_sample(m, n_side):
+    """The workload restricted to the first n_side x n_side grid vertices (cloth) or the first
+    triangles (others): what the oracle can process in seconds."""
+    import numpy as np
+    import ttie_inputs as ti
+    if m.V == 256 * 256:
+        ij = np.arange(m.V)
+        keep_v = ((ij % 256) < n_side) & ((ij // 256) < n_side)
+        keep_t = keep_v[m.tri].all(axis=1)
+    else:
+        keep_t = np.zeros(m.F, bool)
+        keep_t[: n_side * n_side * 2] = True
+    tri = m.tri[keep_t]
+    used = np.unique(tri)
+    remap = -np.ones(m.V, np.int64)
+    remap[used] = np.arange(len(used))
+    return ti.Mesh(m.x[used], remap[tri].astype(np.int32), m.group[keep_t])
+
+
+def oracle_step(sub):
+    """One pass of the oracle over the sample: brute-force candidates, per-pair evaluation
+    (duals + exact test), gradient, PSD Hessian and assembly.  Returns candidate pairs."""
+    import oracle as O
+    pairs = O.candidate_pairs(sub.x, sub.tri)
+    ev = O.evaluate(sub.x, sub.tri, pairs)
+    O.assemble(sub.tri, ev, sub.V)
+    return len(pairs)
+
+
+class Clocks:
+    """nvidia-smi samples during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [v.strip() for v in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+def run_reference(args, rank, world):
+    """CPU oracle arm: rank 0 only."""
+    if rank != 0:
+        return
+    m, _, desc = workload(args.workload)
+    sub = oracle_sample(m, 24)
+    for _ in range(args.warmup):
+        oracle_step(sub)
+    t0 = time.perf_counter()
+    n = 0
+    for _ in range(args.steps):
+        n += oracle_step(sub)
+    dt = time.perf_counter() - t0
+    v = n / dt
+    sample = "oracle on a 24x24-vertex patch of the workload (%d triangles, %d candidate pairs per step)" % (
+        sub.F, n // max(args.steps, 1))
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * dt / max(args.steps, 1), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": desc, "sample": sample},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def cpu_baseline(m, seconds_target=15.0):
+    """Oracle throughput on a bounded sample (patch of the workload), single core."""
+    sub = oracle_sample(m, 80)
+    t0 = time.perf_counter()
+    n, reps = 0, 0
+    while True:
+        n += oracle_step(sub)
+        reps += 1
+        if time.perf_counter() - t0 > seconds_target or reps >= 4:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "oracle on an 80x80-vertex patch of the workload (%d triangles, %d candidate pairs) x %d, "
+                      "%.1f s" % (sub.F, n // reps, reps, dt)}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="cloth256")
+    ap.add_argument("--no-solve", action="store_true", help="skip the time-to-intersection-free run")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    import torch.distributed as dist
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2606_06511_gb300 import ttie
+
+    m, precision, desc = workload(args.workload)
+    dt = torch.float32 if precision == 0 else torch.float64
+    x0 = torch.tensor(m.x, dtype=dt, device="cuda")
+    tri = torch.tensor(m.tri, dtype=torch.int32, device="cuda")
+    x = x0.clone()
+    ctx = ttie.Context(precision=precision, profile=1)
+    ctx.build_bvh(x0, tri)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        x.copy_(x0)
+        info = ctx.newton_step(x)
+    barrier()
+    clocks = Clocks(local)
+    clocks.start()
+    launches0 = ctx.get_launch_count()
+    total_ms, pairs, active = 0.0, 0, 0
+    stage = {"build": 0.0, "eval": 0.0, "assemble": 0.0, "pcg": 0.0, "line_search": 0.0}
+    kern = {"classify": 0.0, "pcg": 0.0}
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    infos = []
+    for _ in range(args.steps):
+        x.copy_(x0)
+        flush.zero_()
+        ev0.record(stream)
+        info = ctx.newton_step(x)
+        ev1.record(stream)
+        ev1.synchronize()
+        total_ms += ev0.elapsed_time(ev1)
+        pairs += info["n_candidates"]
+        active += info["n_active"]
+        for k in stage:
+            stage[k] += info["ms_" + k]
+        kern["classify"] += info["ms_classify"]
+        kern["pcg"] += info["ms_pcg_kernel"]
+        infos.append(info)
+    launches = ctx.get_launch_count() - launches0
+    barrier()
+    clk = clocks.stop()
+    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+    p = torch.tensor([float(pairs)], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(p, op=dist.ReduceOp.SUM)
+    total_s = t.item() / 1e3
+    value = p.item() / total_s
+
+    # end to end through the public API with host buffers
+    xh0 = x0.cpu().pin_memory()
+    xh = torch.empty_like(xh0).pin_memory()
+    e2e_ms, e2e_pairs = 0.0, 0
+    for i in range(args.warmup + max(3, args.steps // 2)):
+        flush.zero_()
+        ev0.record(stream)
+        x.copy_(xh0, non_blocking=True)
+        info = ctx.newton_step(x)
+        xh.copy_(x, non_blocking=True)
+        ev1.record(stream)
+        ev1.synchronize()
+        if i >= args.warmup:
+            e2e_ms += ev0.elapsed_time(ev1)
+            e2e_pairs += info["n_candidates"]
+    e2e_bytes = x0.numel() * x0.element_size()
+
+    # roofline of the dominant kernel: the narrow-phase classification, 104 algorithmic bytes
+    # per candidate (pair ids 8 B + 2 x (indices 12 B + coordinates 36 B)); see the design doc
+    peaks = measured_peaks()
+    hbm = peaks.get("hbm_gbs")
+    k_ms = kern["classify"] / args.steps
+    n_cand = infos[-1]["n_candidates"]
+    achieved = 104.0 * n_cand / (k_ms * 1e-3) / 1e9 if k_ms > 0 else None
+    roofline = {"kernel": "k_classify", "bound": "hbm", "achieved": achieved,
+                "peak": hbm if hbm else 6800.0, "unit": "GB/s",
+                "peak_source": "measured" if hbm else "fallback",
+                "frac": (achieved / (hbm if hbm else 6800.0)) if achieved else None,
+                "traffic": None, "ms_per_launch": k_ms}
+
+    solve = None
+    if not args.no_solve and rank == 0:
+        xs = x0.clone()
+        ctx.set_params(newton_max_it=100)
+        torch.cuda.synchronize()
+        s = ctx.solve(xs)
+        solve = {"converged": bool(s["converged"]), "iterations": s["iterations"], "seconds": s["seconds"],
+                 "n_active_initial": s["n_active_initial"], "n_active_final": s["n_active_final"],
+                 "energy_initial": s["energy_initial"], "energy_final": s["energy_final"],
+                 "newton_max_it": 100}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(m)
+
+    if rank == 0:
+        last = infos[-1]
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if precision == 0 else "f64",
+            "data": "synthetic",
+            "config": {"workload": desc, "triangles": m.F, "vertices": m.V,
+                       "candidates_per_step": last["n_candidates"], "intersecting_per_step": last["n_active"],
+                       "swept_candidates_per_step": last["n_candidates_swept"],
+                       "line_search_trials": last["ls_trials"], "pcg_iters": last["pcg_iters"],
+                       "bsr_rows": last["n_rows"], "bsr_blocks": last["nnzb"],
+                       "l2": "flushed (256 MiB write) before every timed step",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "stage_ms_per_step": {k: v / args.steps for k, v in stage.items()},
+            "active_pairs_per_s": active / (total_ms / 1e3),
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_pairs / (e2e_ms / 1e3) if e2e_ms > 0 else None, "unit": UNIT,
+                    "h2d_bytes_per_step": e2e_bytes, "d2h_bytes_per_step": e2e_bytes},
+            "gpu_launches": launches,
+            "gpu_launches_per_step": launches / args.steps,
+            "clocks": clk,
+            "time_to_intersection_free": solve,
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

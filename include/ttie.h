@@ -190,6 +190,8 @@ typedef struct {
     int ls_trials;               /* trial steps evaluated                              */
     int64_t n_candidates_swept;  /* candidates of the line-search sweep [x, x+a_max d] */
     float ms_build, ms_eval, ms_assemble, ms_pcg, ms_line_search;  /* if params.profile */
+    float ms_classify;           /* classification kernel of the evaluation at x (profile) */
+    float ms_pcg_kernel;         /* persistent PCG kernel (profile)                          */
 } ttie_step_info;
 
 /*
@@ -233,6 +235,9 @@ ttie_status ttie_get_direction(ttie_ctx *ctx, void *d_out);
 /* Counters of the last ttie_eval_pairs: pair signs decided by the FP32 filter,
  * by FP64, and by exact arithmetic (host out array of 3). */
 ttie_status ttie_get_filter_stats(ttie_ctx *ctx, int64_t *out3);
+
+/* Number of CUDA kernels the context has launched since ttie_create (host out). */
+ttie_status ttie_get_launch_count(ttie_ctx *ctx, int64_t *n);
 
 #ifdef __cplusplus
 }

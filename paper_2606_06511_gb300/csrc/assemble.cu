@@ -269,82 +269,212 @@ __global__ void k_pcg_setup(const int32_t *__restrict__ row_ptr, const int32_t *
     });
 }
 
-// q = (H + mu I) p and p.q
+// ---------------------------------------------------------------- persistent PCG
+// All PCG iterations in one cooperative launch (every block resident).  Blocks meet at
+// a grid barrier three times per iteration; each wait is bounded and, when it runs out,
+// sets ERR_BARRIER and the kernel returns.  Reductions: block partials, then every block
+// sums all partials in the same order, so all blocks take the same decisions and the
+// result does not depend on timing.
+constexpr long long kBarrierSpins = 50000000;   // with ~32-64 ns sleeps: a few seconds
+
+constexpr int kBarGroups = 16;
+
+// Two-level barrier: blocks arrive on one of 16 group counters (separate cache lines),
+// the last of each group on the root counter, the last of all bumps the generation the
+// others poll.  Same-address atomics are the cost of a grid barrier (they serialise, and
+// more so across the two dies), so each counter sees at most ~G/16 or 16 arrivals.
+__device__ __forceinline__ bool grid_barrier(DevScalars *ds) {
+    __syncthreads();
+    __shared__ int failed;
+    if (threadIdx.x == 0) {
+        volatile unsigned int *gen = &ds->bar_gen;
+        const unsigned int g = *gen;
+        const unsigned int G = gridDim.x;
+        const unsigned int ng = G < kBarGroups ? G : kBarGroups;
+        const unsigned int grp = blockIdx.x % ng;
+        const unsigned int gsize = G / ng + (grp < G % ng ? 1u : 0u);
+        __threadfence();
+        failed = 0;
+        bool release = false;
+        if (atomicAdd(&ds->bar_group[grp][0], 1u) == gsize - 1) {
+            ds->bar_group[grp][0] = 0u;
+            __threadfence();
+            if (atomicAdd(&ds->bar_count, 1u) == ng - 1) {
+                ds->bar_count = 0u;
+                __threadfence();
+                atomicAdd(&ds->bar_gen, 1u);
+                release = true;
+            }
+        }
+        if (!release) {
+            long long spins = 0;
+            while (*gen == g) {
+                if (++spins > kBarrierSpins) {
+                    atomicOr(&ds->err, ERR_BARRIER);
+                    failed = 1;
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+        __threadfence();
+        if (*(volatile int *)&ds->err & ERR_BARRIER) failed = 1;
+    }
+    __syncthreads();
+    return failed == 0;
+}
+
+// Sum of per-block values v[0..N) over the grid; identical in every block.
+template <int N>
+__device__ __forceinline__ bool grid_allreduce(double (&v)[N], double *part, DevScalars *ds) {
+    __shared__ double tot[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        const double b = block_sum(v[i]);
+        if (threadIdx.x == 0) part[(size_t)i * gridDim.x + blockIdx.x] = b;
+    }
+    if (!grid_barrier(ds)) return false;
+    if (threadIdx.x < 32) {
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            double s = 0.0;
+            for (unsigned j = threadIdx.x; j < gridDim.x; j += 32) s += __ldcg(&part[(size_t)i * gridDim.x + j]);
+#pragma unroll
+            for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            if (threadIdx.x == 0) tot[i] = s;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < N; ++i) v[i] = tot[i];
+    __syncthreads();
+    return true;
+}
+
+template <typename T> struct PcgArgs {
+    const int32_t *row_ptr;
+    const int32_t *col_idx;
+    const T *bval;
+    const T *dinv;
+    T *x, *r, *z, *p, *q;
+    double *partA, *partB;
+    double rtol2;
+    int max_it;
+    DevScalars *ds;
+};
+
+// 8 consecutive lanes share a row in the product w = (H + mu I) z: each takes every 8th
+// block of the row and the partial products are summed by shuffles.  Lane 0 of the group
+// owns the row in the vector updates, so x, r, z, p, q of a row are written by one thread
+// only; z of other rows is read through L2 (__ldcg) after the barrier that follows its
+// update.  With w = A z, the search direction's product follows from q = A p = w + beta q,
+// so an iteration needs two grid reductions (p.q, then r.z and r.r) and no third barrier.
+constexpr int kLanesPerRow = 8;
+constexpr int kPcgThreads = 1024;
+
 template <typename T>
-__global__ void k_pcg_spmv(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col_idx,
-                           const T *__restrict__ bval, const T *__restrict__ p, T *__restrict__ q, double *partials,
-                           DevScalars *ds) {
+__device__ __forceinline__ void spmv_row(const PcgArgs<T> &a, unsigned long long row, int sub, unsigned gmask, T mu,
+                                         T &y0, T &y1, T &y2) {
+    const int b0 = a.row_ptr[row], b1 = a.row_ptr[row + 1];
+    y0 = 0; y1 = 0; y2 = 0;
+    for (int b = b0 + sub; b < b1; b += kLanesPerRow) {
+        const T *m = a.bval + (size_t)b * 9;
+        const int c = a.col_idx[b];
+        const T c0 = __ldcg(&a.z[c * 3]), c1 = __ldcg(&a.z[c * 3 + 1]), c2 = __ldcg(&a.z[c * 3 + 2]);
+        y0 += m[0] * c0 + m[1] * c1 + m[2] * c2;
+        y1 += m[3] * c0 + m[4] * c1 + m[5] * c2;
+        y2 += m[6] * c0 + m[7] * c1 + m[8] * c2;
+    }
+#pragma unroll
+    for (int o = kLanesPerRow / 2; o; o >>= 1) {
+        y0 += __shfl_xor_sync(gmask, y0, o, kLanesPerRow);
+        y1 += __shfl_xor_sync(gmask, y1, o, kLanesPerRow);
+        y2 += __shfl_xor_sync(gmask, y2, o, kLanesPerRow);
+    }
+    y0 += mu * a.z[row * 3]; y1 += mu * a.z[row * 3 + 1]; y2 += mu * a.z[row * 3 + 2];
+}
+
+// p = z + beta p, q = A z + beta q (p = z, q = A z when first: p and q hold nothing yet),
+// returns the row's p.q
+template <typename T>
+__device__ __forceinline__ double direction_phase(const PcgArgs<T> &a, unsigned long long nr, unsigned long long group,
+                                                  unsigned long long n_groups, int sub, unsigned gmask, T mu, T beta,
+                                                  bool first) {
+    double pq = 0.0;
+    for (unsigned long long row = group; row < nr; row += n_groups) {
+        T w0, w1, w2;
+        spmv_row(a, row, sub, gmask, mu, w0, w1, w2);
+        if (sub == 0) {
+            const T w[3] = {w0, w1, w2};
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                const T pi = first ? a.z[row * 3 + i] : a.z[row * 3 + i] + beta * a.p[row * 3 + i];
+                const T qi = first ? w[i] : w[i] + beta * a.q[row * 3 + i];
+                a.p[row * 3 + i] = pi;
+                a.q[row * 3 + i] = qi;
+                pq += (double)pi * qi;
+            }
+        }
+    }
+    return pq;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kPcgThreads) k_pcg_persistent(PcgArgs<T> a) {
+    DevScalars *ds = a.ds;
     if (ds->pcg_done) return;
     const unsigned long long nr = ds->n_rows;
     const T mu = (T)ds->mu;
-    double pq = 0.0;
-    for (unsigned long long row = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; row < nr;
-         row += (unsigned long long)gridDim.x * blockDim.x) {
-        T y0 = mu * p[row * 3], y1 = mu * p[row * 3 + 1], y2 = mu * p[row * 3 + 2];
-        for (int b = row_ptr[row]; b < row_ptr[row + 1]; ++b) {
-            const T *m = bval + (size_t)b * 9;
-            const int c = col_idx[b];
-            const T p0 = p[c * 3], p1 = p[c * 3 + 1], p2 = p[c * 3 + 2];
-            y0 += m[0] * p0 + m[1] * p1 + m[2] * p2;
-            y1 += m[3] * p0 + m[4] * p1 + m[5] * p2;
-            y2 += m[6] * p0 + m[7] * p1 + m[8] * p2;
-        }
-        q[row * 3] = y0; q[row * 3 + 1] = y1; q[row * 3 + 2] = y2;
-        pq += (double)p[row * 3] * y0 + (double)p[row * 3 + 1] * y1 + (double)p[row * 3 + 2] * y2;
-    }
-    double v[1] = {pq};
-    grid_sums<1>(v, partials, &ds->done_counter[3], [&](const double *t) { ds->red[2] = t[0]; });
-}
-
-// x += alpha p, r -= alpha q, z = M r; r.z and r.r; then beta and the stopping test.
-template <typename T>
-__global__ void k_pcg_update(const T *__restrict__ dinv, const T *__restrict__ p, const T *__restrict__ q, T *__restrict__ x,
-                             T *__restrict__ r, T *__restrict__ z, double rtol2, double *partials, DevScalars *ds) {
-    if (ds->pcg_done) return;
-    const unsigned long long nr = ds->n_rows;
-    const double pq = ds->red[2];
-    // breakdown (p.q <= 0 from rounding on a near-singular system): no update, except at the
-    // first iteration, where x = p = M^-1 r0 (the preconditioned gradient step) is kept
-    const bool ok = pq > 0.0 && isfinite(pq);
-    const T alpha = (T)(ok ? ds->red[0] / pq : (ds->pcg_iters == 0 ? 1.0 : 0.0));
-    double rz = 0.0, rr = 0.0;
-    for (unsigned long long row = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; row < nr;
-         row += (unsigned long long)gridDim.x * blockDim.x) {
-        T rv[3];
+    const double rr0 = ds->red[1];
+    double rz = ds->red[0], rr = rr0;
+    const int lane = threadIdx.x & 31, sub = lane & (kLanesPerRow - 1);
+    const unsigned gmask = 0xffu << (lane & ~(kLanesPerRow - 1));
+    const unsigned long long group = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) / kLanesPerRow;
+    const unsigned long long n_groups = (unsigned long long)gridDim.x * blockDim.x / kLanesPerRow;
+    // p = z, q = A z (z comes from the setup kernel, an earlier launch)
+    double v1[1] = {direction_phase(a, nr, group, n_groups, sub, gmask, mu, T(0), true)};
+    if (!grid_allreduce<1>(v1, a.partA, ds)) return;
+    int it = 0;
+    for (; it < a.max_it; ++it) {
+        const double pq = v1[0];
+        const bool ok = pq > 0.0 && isfinite(pq);
+        // breakdown at the first iteration keeps x = p = M^-1 r0 (preconditioned gradient)
+        const T alpha = (T)(ok ? rz / pq : (it == 0 ? 1.0 : 0.0));
+        double v2[2] = {0.0, 0.0};
+        if (sub == 0) {
+            for (unsigned long long row = group; row < nr; row += n_groups) {
+                T rv[3];
 #pragma unroll
-        for (int i = 0; i < 3; ++i) {
-            x[row * 3 + i] += alpha * p[row * 3 + i];
-            rv[i] = r[row * 3 + i] - alpha * q[row * 3 + i];
-            r[row * 3 + i] = rv[i];
-        }
-        const T *di = dinv + row * 9;
+                for (int i = 0; i < 3; ++i) {
+                    a.x[row * 3 + i] += alpha * a.p[row * 3 + i];
+                    rv[i] = a.r[row * 3 + i] - alpha * a.q[row * 3 + i];
+                    a.r[row * 3 + i] = rv[i];
+                }
+                const T *di = a.dinv + row * 9;
 #pragma unroll
-        for (int i = 0; i < 3; ++i) {
-            const T zi = di[3 * i] * rv[0] + di[3 * i + 1] * rv[1] + di[3 * i + 2] * rv[2];
-            z[row * 3 + i] = zi;
-            rz += (double)rv[i] * zi;
-            rr += (double)rv[i] * rv[i];
+                for (int i = 0; i < 3; ++i) {
+                    const T zi = di[3 * i] * rv[0] + di[3 * i + 1] * rv[1] + di[3 * i + 2] * rv[2];
+                    a.z[row * 3 + i] = zi;
+                    v2[0] += (double)rv[i] * zi;
+                    v2[1] += (double)rv[i] * rv[i];
+                }
+            }
         }
+        if (!grid_allreduce<2>(v2, a.partB, ds)) return;
+        if (!ok) { ++it; break; }
+        const double beta = rz != 0.0 ? v2[0] / rz : 0.0;
+        rz = v2[0];
+        rr = v2[1];
+        if (rr <= a.rtol2 * rr0 || !isfinite(rr)) { ++it; break; }
+        v1[0] = direction_phase(a, nr, group, n_groups, sub, gmask, mu, (T)beta, false);
+        if (!grid_allreduce<1>(v1, a.partA, ds)) return;
     }
-    double v[2] = {rz, rr};
-    grid_sums<2>(v, partials, &ds->done_counter[4], [&](const double *t) {
-        const double rz_old = ds->red[0];
-        ds->red[3] = rz_old != 0.0 ? t[0] / rz_old : 0.0;   // beta
-        ds->red[0] = t[0];
-        ds->red[4] = t[1];
-        ds->pcg_iters += 1;
-        if (t[1] <= rtol2 * ds->red[1] || !ok || !isfinite(t[1])) ds->pcg_done = 1;
-    });
-}
-
-template <typename T>
-__global__ void k_pcg_dir(const T *__restrict__ z, T *__restrict__ p, const DevScalars *ds) {
-    if (ds->pcg_done) return;
-    const unsigned long long n3 = ds->n_rows * 3;
-    const T beta = (T)ds->red[3];
-    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n3;
-         i += (unsigned long long)gridDim.x * blockDim.x)
-        p[i] = z[i] + beta * p[i];
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        ds->pcg_iters = it;
+        ds->red[0] = rz;
+        ds->red[4] = rr;
+        ds->pcg_done = 1;
+    }
 }
 
 template <typename T>
@@ -377,6 +507,24 @@ __global__ void k_update_positions(T *__restrict__ x, int stride, const T *__res
     }
 }
 
+// g.d and max_r |d_r| of a Newton direction: deterministic sum, order-free max.
+template <typename T>
+__global__ void k_dir_stats(const T *__restrict__ g, const T *__restrict__ d, double *partials, DevScalars *ds,
+                            double *out) {
+    const unsigned long long nr = ds->n_rows;
+    double s = 0.0, m = 0.0;
+    for (unsigned long long r = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; r < nr;
+         r += (unsigned long long)gridDim.x * blockDim.x) {
+        const double d0 = d[3 * r], d1 = d[3 * r + 1], d2 = d[3 * r + 2];
+        s += (double)g[3 * r] * d0 + (double)g[3 * r + 1] * d1 + (double)g[3 * r + 2] * d2;
+        m = fmax(m, d0 * d0 + d1 * d1 + d2 * d2);
+    }
+    for (int o = 16; o; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0 && m > 0.0) atomicMax((unsigned long long *)&out[1], (unsigned long long)__double_as_longlong(m));
+    double v[1] = {s};
+    grid_sums<1>(v, partials, &ds->done_counter[5], [&](const double *t) { out[0] = t[0]; });
+}
+
 int bits_for(unsigned long long v) {
     int b = 0;
     while (b < 64 && (v >> b) != 0ull) ++b;
@@ -396,15 +544,15 @@ cudaError_t assemble_system(Ctx &c, T *grad_full) {
     const int2 *pairs = (const int2 *)c.cand.p;
     const uint32_t *active = (const uint32_t *)c.active.p;
     const unsigned gA = grid_for(n_act, kThreads);
-    k_mark_vertices<<<gA, kThreads, 0, c.stream>>>(tri4, pairs, active, c.ds, (uint32_t *)c.vflag.p);
+    launch(c, k_mark_vertices, dim3(gA), dim3(kThreads), tri4, pairs, active, c.ds, (uint32_t *)c.vflag.p);
     TTIE_CUDA_TRY(scan_u32_u64(c, (const uint32_t *)c.vflag.p, (unsigned long long *)c.vrow.p, V));
     TTIE_CUDA_TRY(ensure(c, c.row_vertex, (size_t)(V > 0 ? V : 1) * 4));
-    k_row_vertex<<<grid_for(V, kThreads), kThreads, 0, c.stream>>>((const uint32_t *)c.vflag.p,
+    launch(c, k_row_vertex, dim3(grid_for(V, kThreads)), dim3(kThreads), (const uint32_t *)c.vflag.p,
                                                                   (const unsigned long long *)c.vrow.p, V,
                                                                   (int32_t *)c.row_vertex.p, c.ds);
     TTIE_CUDA_TRY(ensure(c, c.zfac, (size_t)(n_act > 0 ? n_act : 1) * kZStride * sizeof(T)));
     TTIE_CUDA_TRY(ensure(c, c.partials, (size_t)kNumSMs * 16 * 4 * sizeof(double)));
-    k_factors<T><<<grid_for(n_act, 128, kNumSMs * 8), 128, 0, c.stream>>>((const T *)c.fac.p, c.prm.psd_mode,
+    launch(c, k_factors<T>, dim3(grid_for(n_act, 128, kNumSMs * 8)), dim3(128), (const T *)c.fac.p, c.prm.psd_mode,
                                                                         (T *)c.zfac.p, (double *)c.partials.p, c.ds);
     const int64_t nk = n_act * 36;
     TTIE_CUDA_TRY(ensure(c, c.bkey, (size_t)(nk > 0 ? nk : 1) * 8));
@@ -418,18 +566,18 @@ cudaError_t assemble_system(Ctx &c, T *grad_full) {
     TTIE_CUDA_TRY(cudaStreamSynchronize(c.stream));
     const int64_t nr = (int64_t)c.hs->n_rows;
     c.n_rows = nr;
-    k_block_keys<<<gA, kThreads, 0, c.stream>>>(tri4, pairs, active, (const unsigned long long *)c.vrow.p, c.ds,
+    launch(c, k_block_keys, dim3(gA), dim3(kThreads), tri4, pairs, active, (const unsigned long long *)c.vrow.p, c.ds,
                                                 (unsigned long long *)c.bkey.p, (uint32_t *)c.bval.p);
     TTIE_CUDA_TRY(cudaGetLastError());
     const int kbits = bits_for((unsigned long long)nr * (unsigned long long)nr);
     TTIE_CUDA_TRY(radix_sort(c, (unsigned long long *)c.bkey.p, (uint32_t *)c.bval.p, (unsigned long long *)c.bkey2.p,
                              (uint32_t *)c.bval2.p, nk, kbits));
     // run boundaries: flags -> positions (bkey2 reused as the u64 scan output)
-    k_run_flags<<<grid_for(nk, kThreads), kThreads, 0, c.stream>>>((const unsigned long long *)c.bkey.p, nk,
+    launch(c, k_run_flags, dim3(grid_for(nk, kThreads)), dim3(kThreads), (const unsigned long long *)c.bkey.p, nk,
                                                                   (uint32_t *)c.bflag.p);
     TTIE_CUDA_TRY(ensure(c, c.gtmp, (size_t)(nk + 1) * 8));
     TTIE_CUDA_TRY(scan_u32_u64(c, (const uint32_t *)c.bflag.p, (unsigned long long *)c.gtmp.p, nk));
-    k_run_starts<<<grid_for(nk, kThreads), kThreads, 0, c.stream>>>((const uint32_t *)c.bflag.p,
+    launch(c, k_run_starts, dim3(grid_for(nk, kThreads)), dim3(kThreads), (const uint32_t *)c.bflag.p,
                                                                    (const unsigned long long *)c.gtmp.p, nk,
                                                                    (uint32_t *)c.run_start.p, c.ds);
     TTIE_CUDA_TRY(cudaMemcpyAsync(&c.hs->nnzb, &c.ds->nnzb, 8, cudaMemcpyDeviceToHost, c.stream));
@@ -445,7 +593,7 @@ cudaError_t assemble_system(Ctx &c, T *grad_full) {
         TTIE_CUDA_TRY(cudaMemsetAsync(c.row_ptr.p, 0, 4, c.stream));
         return cudaGetLastError();
     }
-    k_block_values<T><<<grid_for(nnzb, 128, kNumSMs * 16), 128, 0, c.stream>>>(
+    launch(c, k_block_values<T>, dim3(grid_for(nnzb, 128, kNumSMs * 16)), dim3(128), 
         (const unsigned long long *)c.bkey.p, (const uint32_t *)c.bval.p, (const uint32_t *)c.run_start.p,
         (const T *)c.zfac.p, c.ds, (int32_t *)c.row_ptr.p, (int32_t *)c.col_idx.p, (T *)c.bsr_val.p, (T *)c.rhs.p,
         (const int32_t *)c.row_vertex.p, grad_full);
@@ -465,24 +613,40 @@ cudaError_t pcg_solve(Ctx &c, const T *rhs, T *out, double rtol, int max_it) {
     TTIE_CUDA_TRY(ensure(c, c.partials, (size_t)kNumSMs * 16 * 4 * sizeof(double)));
     double *part = (double *)c.partials.p;
     const unsigned g = grid_for(nr, kThreads, kNumSMs * 4);
-    k_pcg_setup<T><<<g, kThreads, 0, c.stream>>>((const int32_t *)c.row_ptr.p, (const int32_t *)c.col_idx.p,
+    TTIE_CUDA_TRY(cudaMemsetAsync(&c.ds->bar_count, 0, sizeof(unsigned int) * (2 + 16 * 32), c.stream));
+    launch(c, k_pcg_setup<T>, dim3(g), dim3(kThreads), (const int32_t *)c.row_ptr.p, (const int32_t *)c.col_idx.p,
                                                  (const T *)c.bsr_val.p, c.prm.mu_rel, (T *)c.dinv.p, rhs, out,
                                                  (T *)c.pcg_r.p, (T *)c.pcg_z.p, (T *)c.pcg_p.p, part, c.ds);
     TTIE_CUDA_TRY(cudaGetLastError());
-    const double rtol2 = rtol * rtol;
-    for (int it = 0; it < max_it; ++it) {
-        k_pcg_spmv<T><<<g, kThreads, 0, c.stream>>>((const int32_t *)c.row_ptr.p, (const int32_t *)c.col_idx.p,
-                                                    (const T *)c.bsr_val.p, (const T *)c.pcg_p.p, (T *)c.pcg_q.p, part,
-                                                    c.ds);
-        k_pcg_update<T><<<g, kThreads, 0, c.stream>>>((const T *)c.dinv.p, (const T *)c.pcg_p.p, (const T *)c.pcg_q.p, out,
-                                                      (T *)c.pcg_r.p, (T *)c.pcg_z.p, rtol2, part, c.ds);
-        k_pcg_dir<T><<<g, kThreads, 0, c.stream>>>((const T *)c.pcg_z.p, (T *)c.pcg_p.p, c.ds);
-        if ((it & 15) == 15) {
-            TTIE_CUDA_TRY(cudaMemcpyAsync(&c.hs->pcg_done, &c.ds->pcg_done, 4, cudaMemcpyDeviceToHost, c.stream));
-            TTIE_CUDA_TRY(cudaStreamSynchronize(c.stream));
-            if (c.hs->pcg_done) break;
-        }
-    }
+    PcgArgs<T> args;
+    args.row_ptr = (const int32_t *)c.row_ptr.p;
+    args.col_idx = (const int32_t *)c.col_idx.p;
+    args.bval = (const T *)c.bsr_val.p;
+    args.dinv = (const T *)c.dinv.p;
+    args.x = out;
+    args.r = (T *)c.pcg_r.p;
+    args.z = (T *)c.pcg_z.p;
+    args.p = (T *)c.pcg_p.p;
+    args.q = (T *)c.pcg_q.p;
+    args.partA = part;
+    args.partB = part + 2 * kNumSMs * 8;
+    args.rtol2 = rtol * rtol;
+    args.max_it = max_it;
+    args.ds = c.ds;
+    int per_sm = 0;
+    TTIE_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg_persistent<T>, kPcgThreads, 0));
+    if (per_sm < 1) per_sm = 1;
+    const int sms = c.num_sms > 0 ? c.num_sms : kNumSMs;
+    // one block per SM at most: fewer arrivals per grid barrier
+    int64_t blocks = (nr * kLanesPerRow + kPcgThreads - 1) / kPcgThreads;
+    if (blocks > (int64_t)sms) blocks = sms;
+    if (blocks < 1) blocks = 1;
+    void *kargs[] = {&args};
+    ++c.n_launch;
+    if (c.prm.profile) cudaEventRecord(c.ev[8], c.stream);
+    TTIE_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)k_pcg_persistent<T>, dim3((unsigned)blocks), dim3(kPcgThreads),
+                                              kargs, 0, c.stream));
+    if (c.prm.profile) cudaEventRecord(c.ev[9], c.stream);
     return cudaGetLastError();
 }
 template cudaError_t pcg_solve<float>(Ctx &, const float *, float *, double, int);
@@ -490,7 +654,7 @@ template cudaError_t pcg_solve<double>(Ctx &, const double *, double *, double, 
 
 template <typename T>
 cudaError_t axpy_positions(Ctx &c, const vec4_t<T> *x, const T *d, T alpha, vec4_t<T> *out) {
-    k_axpy_positions<T><<<grid_for(c.V, kThreads), kThreads, 0, c.stream>>>(x, d, alpha, c.V, out);
+    launch(c, k_axpy_positions<T>, dim3(grid_for(c.V, kThreads)), dim3(kThreads), x, d, alpha, c.V, out);
     return cudaGetLastError();
 }
 template cudaError_t axpy_positions<float>(Ctx &, const float4 *, const float *, float, float4 *);
@@ -499,7 +663,7 @@ template cudaError_t axpy_positions<double>(Ctx &, const dvec4 *, const double *
 template <typename T>
 cudaError_t scatter_direction(Ctx &c, const T *d_rows, T *d_full) {
     TTIE_CUDA_TRY(cudaMemsetAsync(d_full, 0, (size_t)c.V * 3 * sizeof(T), c.stream));
-    k_scatter_rows<T><<<grid_for(c.n_rows, kThreads), kThreads, 0, c.stream>>>(d_rows, (const int32_t *)c.row_vertex.p,
+    launch(c, k_scatter_rows<T>, dim3(grid_for(c.n_rows, kThreads)), dim3(kThreads), d_rows, (const int32_t *)c.row_vertex.p,
                                                                               c.ds, d_full);
     return cudaGetLastError();
 }
@@ -508,10 +672,22 @@ template cudaError_t scatter_direction<double>(Ctx &, const double *, double *);
 
 template <typename T>
 cudaError_t update_positions(Ctx &c, T *x, int stride, const T *d_full, T alpha) {
-    k_update_positions<T><<<grid_for(c.V, kThreads), kThreads, 0, c.stream>>>(x, stride, d_full, alpha, c.V);
+    launch(c, k_update_positions<T>, dim3(grid_for(c.V, kThreads)), dim3(kThreads), x, stride, d_full, alpha, c.V);
     return cudaGetLastError();
 }
 template cudaError_t update_positions<float>(Ctx &, float *, int, const float *, float);
 template cudaError_t update_positions<double>(Ctx &, double *, int, const double *, double);
+
+// out_dev[0] = g.d, out_dev[1] = max_r |d_r| (d given per assembled row)
+template <typename T> cudaError_t direction_stats(Ctx &c, const T *g, const T *d, double *out_dev) {
+    TTIE_CUDA_TRY(cudaMemsetAsync(out_dev, 0, 2 * sizeof(double), c.stream));
+    launch(c, k_dir_stats<T>, dim3(grid_for(c.n_rows, kThreads, kNumSMs * 4)), dim3(kThreads), g, d,
+           (double *)c.partials.p, c.ds, out_dev);
+    TTIE_CUDA_TRY(cudaGetLastError());
+    // the max was accumulated on the squared norm
+    return cudaSuccess;
+}
+template cudaError_t direction_stats<float>(Ctx &, const float *, const float *, double *);
+template cudaError_t direction_stats<double>(Ctx &, const double *, const double *, double *);
 
 }  // namespace ttie

@@ -347,7 +347,7 @@ __global__ void k_brute(int n, const int4 *__restrict__ tri4, const int32_t *__r
 }  // namespace
 
 template <typename T> cudaError_t pack_positions(Ctx &c, const T *x, int stride, vec4_t<T> *out) {
-    k_pack_positions<T><<<grid_for(c.V, kThreads), kThreads, 0, c.stream>>>(x, stride, c.V, out, c.ds);
+    launch(c, k_pack_positions<T>, dim3(grid_for(c.V, kThreads)), dim3(kThreads), x, stride, c.V, out, c.ds);
     return cudaGetLastError();
 }
 template cudaError_t pack_positions<float>(Ctx &, const float *, int, float4 *);
@@ -356,7 +356,7 @@ template cudaError_t pack_positions<double>(Ctx &, const double *, int, dvec4 *)
 cudaError_t pack_topology(Ctx &c, const int32_t *tri, const int32_t *group) {
     TTIE_CUDA_TRY(ensure(c, c.tri4, (size_t)c.F * sizeof(int4)));
     if (group) TTIE_CUDA_TRY(ensure(c, c.grp, (size_t)c.F * sizeof(int32_t)));
-    k_pack_topology<<<grid_for(c.F, kThreads), kThreads, 0, c.stream>>>(tri, group, c.F, c.V, (int4 *)c.tri4.p,
+    launch(c, k_pack_topology, dim3(grid_for(c.F, kThreads)), dim3(kThreads), tri, group, c.F, c.V, (int4 *)c.tri4.p,
                                                                       (int32_t *)c.grp.p, c.ds);
     return cudaGetLastError();
 }
@@ -392,30 +392,30 @@ cudaError_t build_candidates(Ctx &c, const vec4_t<T> *x0, const vec4_t<T> *x1, B
     auto *perm = (uint32_t *)c.perm.p;
     const unsigned g = grid_for(n, kThreads);
 
-    k_init_bounds<<<1, 32, 0, c.stream>>>(c.ds);
-    k_tri_boxes<T><<<g, kThreads, 0, c.stream>>>(x0, x1, (const int4 *)c.tri4.p, n, tbox, c.ds);
+    launch(c, k_init_bounds, dim3(1), dim3(32), c.ds);
+    launch(c, k_tri_boxes<T>, dim3(g), dim3(kThreads), x0, x1, (const int4 *)c.tri4.p, n, tbox, c.ds);
     const int gbits = grouped ? c.group_bits : 0;
-    k_morton<T><<<g, kThreads, 0, c.stream>>>(tbox, n, (const int32_t *)c.grp.p, gbits, c.ds, key, perm);
+    launch(c, k_morton<T>, dim3(g), dim3(kThreads), tbox, n, (const int32_t *)c.grp.p, gbits, c.ds, key, perm);
     TTIE_CUDA_TRY(cudaGetLastError());
     const int key_bits = 3 * ((63 - gbits) / 3) + gbits;
     TTIE_CUDA_TRY(radix_sort(c, key, perm, (unsigned long long *)c.mkey2.p, (uint32_t *)c.perm2.p, n, key_bits));
     if (grouped) {
-        k_leaf_group<<<g, kThreads, 0, c.stream>>>(perm, (const int32_t *)c.grp.p, n, (int32_t *)c.leaf_group.p);
-        k_fill_int2<<<grid_for(c.n_groups, kThreads), kThreads, 0, c.stream>>>((int2 *)c.group_range.p, c.n_groups,
+        launch(c, k_leaf_group, dim3(g), dim3(kThreads), perm, (const int32_t *)c.grp.p, n, (int32_t *)c.leaf_group.p);
+        launch(c, k_fill_int2, dim3(grid_for(c.n_groups, kThreads)), dim3(kThreads), (int2 *)c.group_range.p, c.n_groups,
                                                                               make_int2(1, 0));
-        k_group_ranges<<<g, kThreads, 0, c.stream>>>((const int32_t *)c.leaf_group.p, n, (int2 *)c.group_range.p);
+        launch(c, k_group_ranges, dim3(g), dim3(kThreads), (const int32_t *)c.leaf_group.p, n, (int2 *)c.group_range.p);
     }
     int2 *child = (int2 *)c.node_child.p;
     int *parent = (int *)c.node_parent.p;
     int2 *range = (int2 *)c.node_range.p;
     Box<T> *nbox = (Box<T> *)c.node_box.p;
-    k_karras<<<grid_for(n - 1, kThreads), kThreads, 0, c.stream>>>(key, n, child, parent, range);
-    k_leaf_boxes<T><<<g, kThreads, 0, c.stream>>>(tbox, perm, n, nbox, range);
+    launch(c, k_karras, dim3(grid_for(n - 1, kThreads)), dim3(kThreads), key, n, child, parent, range);
+    launch(c, k_leaf_boxes<T>, dim3(g), dim3(kThreads), tbox, perm, n, nbox, range);
     TTIE_CUDA_TRY(cudaMemsetAsync(c.visit.p, 0, (size_t)(n - 1) * sizeof(unsigned int), c.stream));
-    k_refit<T><<<g, kThreads, 0, c.stream>>>(n, parent, child, nbox, (unsigned int *)c.visit.p, c.ds);
+    launch(c, k_refit<T>, dim3(g), dim3(kThreads), n, parent, child, nbox, (unsigned int *)c.visit.p, c.ds);
     auto *cnt = (uint32_t *)c.cand_cnt.p;
     auto *off = (unsigned long long *)c.cand_off.p;
-    k_traverse<T, false><<<g, kThreads, 0, c.stream>>>(n, child, range, nbox, perm, (const int4 *)c.tri4.p,
+    launch(c, k_traverse<T, false>, dim3(g), dim3(kThreads), n, child, range, nbox, perm, (const int4 *)c.tri4.p,
                                                        (const int32_t *)c.leaf_group.p, (const int2 *)c.group_range.p,
                                                        mode, cnt, nullptr, nullptr, c.ds);
     TTIE_CUDA_TRY(cudaGetLastError());
@@ -430,7 +430,7 @@ cudaError_t build_candidates(Ctx &c, const vec4_t<T> *x0, const vec4_t<T> *x1, B
     }
     TTIE_CUDA_TRY(ensure(c, out_pairs, (size_t)(total > 0 ? total : 1) * sizeof(int2)));
     if (total > 0)
-        k_traverse<T, true><<<g, kThreads, 0, c.stream>>>(n, child, range, nbox, perm, (const int4 *)c.tri4.p,
+        launch(c, k_traverse<T, true>, dim3(g), dim3(kThreads), n, child, range, nbox, perm, (const int4 *)c.tri4.p,
                                                           (const int32_t *)c.leaf_group.p,
                                                           (const int2 *)c.group_range.p, mode, nullptr, off,
                                                           (int2 *)out_pairs.p, c.ds);
@@ -441,11 +441,13 @@ template cudaError_t build_candidates<float>(Ctx &, const float4 *, const float4
 template cudaError_t build_candidates<double>(Ctx &, const dvec4 *, const dvec4 *, Buf &, int64_t *, int64_t);
 
 namespace {
+// Per-block sums of edge lengths, then one block adds the block sums in order.
 template <typename T>
-__global__ void k_edge_sum(const vec4_t<T> *__restrict__ x, const int4 *__restrict__ tri4, int64_t F, double *out) {
+__global__ void k_edge_sum(const vec4_t<T> *__restrict__ x, const int4 *__restrict__ tri4, int64_t F,
+                           double *partials) {
     __shared__ double sh[32];
     double s = 0.0;
-    for (int64_t f = threadIdx.x; f < F; f += blockDim.x) {
+    for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < F; f += (int64_t)gridDim.x * blockDim.x) {
         const int4 t = tri4[f];
         const v3<T> a = xyz<T>(x[t.x]), b = xyz<T>(x[t.y]), c = xyz<T>(x[t.z]);
         const v3<T> e0 = b - a, e1 = c - b, e2 = a - c;
@@ -457,14 +459,24 @@ __global__ void k_edge_sum(const vec4_t<T> *__restrict__ x, const int4 *__restri
     if (threadIdx.x == 0) {
         double t = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+        partials[blockIdx.x] = t;
+    }
+}
+__global__ void k_edge_mean(const double *partials, int n, int64_t F, double *out) {
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int i = 0; i < n; ++i) t += partials[i];
         *out = F > 0 ? t / (3.0 * (double)F) : 0.0;
     }
 }
 }  // namespace
 
-// Mean edge length over all triangles (one block: a fixed summation order).
+// Mean edge length over all triangles (fixed summation order).
 template <typename T> cudaError_t mean_edge_length(Ctx &c, const vec4_t<T> *x, double *out_dev) {
-    k_edge_sum<T><<<1, 1024, 0, c.stream>>>(x, (const int4 *)c.tri4.p, c.F, out_dev);
+    TTIE_CUDA_TRY(ensure(c, c.partials, (size_t)kNumSMs * 16 * 4 * sizeof(double)));
+    const unsigned g = grid_for(c.F, kThreads, kNumSMs * 4);
+    launch(c, k_edge_sum<T>, dim3(g), dim3(kThreads), x, (const int4 *)c.tri4.p, c.F, (double *)c.partials.p);
+    launch(c, k_edge_mean, dim3(1), dim3(32), (const double *)c.partials.p, (int)g, c.F, out_dev);
     return cudaGetLastError();
 }
 template cudaError_t mean_edge_length<float>(Ctx &, const float4 *, double *);
@@ -480,7 +492,7 @@ cudaError_t brute_candidates(Ctx &c, Buf &out_pairs, int64_t *n_out) {
     auto *cnt = (uint32_t *)c.cand_cnt.p;
     auto *off = (unsigned long long *)c.cand_off.p;
     const unsigned g = grid_for(n, 128);
-    k_brute<false><<<g, 128, 0, c.stream>>>(n, (const int4 *)c.tri4.p, (const int32_t *)c.grp.p, mode, cnt, nullptr,
+    launch(c, k_brute<false>, dim3(g), dim3(128), n, (const int4 *)c.tri4.p, (const int32_t *)c.grp.p, mode, cnt, nullptr,
                                             nullptr);
     TTIE_CUDA_TRY(cudaGetLastError());
     TTIE_CUDA_TRY(scan_u32_u64(c, cnt, off, n));
@@ -489,7 +501,7 @@ cudaError_t brute_candidates(Ctx &c, Buf &out_pairs, int64_t *n_out) {
     unsigned long long total = c.hs->n_cand;
     TTIE_CUDA_TRY(ensure(c, out_pairs, (size_t)(total > 0 ? total : 1) * sizeof(int2)));
     if (total > 0)
-        k_brute<true><<<g, 128, 0, c.stream>>>(n, (const int4 *)c.tri4.p, (const int32_t *)c.grp.p, mode, nullptr,
+        launch(c, k_brute<true>, dim3(g), dim3(128), n, (const int4 *)c.tri4.p, (const int32_t *)c.grp.p, mode, nullptr,
                                                off, (int2 *)out_pairs.p);
     *n_out = (int64_t)total;
     return cudaGetLastError();

@@ -38,37 +38,6 @@ __global__ void k_copy_neg(const T *__restrict__ a, T *__restrict__ b, int64_t n
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) b[i] = -a[i];
 }
 
-// g.d (FP64) and the largest vertex displacement |d_r| over the rows; one block, so the
-// summation order is fixed.
-template <typename T>
-__global__ void k_dir_stats(const T *__restrict__ g, const T *__restrict__ d, int64_t n_rows, double *out) {
-    __shared__ double sh_s[32], sh_m[32];
-    double s = 0.0, m = 0.0;
-    for (int64_t r = threadIdx.x; r < n_rows; r += blockDim.x) {
-        const double d0 = d[3 * r], d1 = d[3 * r + 1], d2 = d[3 * r + 2];
-        s += (double)g[3 * r] * d0 + (double)g[3 * r + 1] * d1 + (double)g[3 * r + 2] * d2;
-        m = fmax(m, d0 * d0 + d1 * d1 + d2 * d2);
-    }
-    for (int o = 16; o; o >>= 1) {
-        s += __shfl_xor_sync(0xffffffffu, s, o);
-        m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-    }
-    if ((threadIdx.x & 31) == 0) {
-        sh_s[threadIdx.x >> 5] = s;
-        sh_m[threadIdx.x >> 5] = m;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double ts = 0.0, tm = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-            ts += sh_s[w];
-            tm = fmax(tm, sh_m[w]);
-        }
-        out[0] = ts;
-        out[1] = sqrt(tm);
-    }
-}
-
 template <typename T> __global__ void k_scale(T *a, int64_t n, double s) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         a[i] = (T)(a[i] * s);
@@ -92,14 +61,8 @@ __global__ void k_split_fac(const T *__restrict__ fac, int64_t n, T *__restrict_
 
 }  // namespace
 
-template <typename T>
-cudaError_t dir_stats(Ctx &c, const T *g, const T *d, int64_t n_rows, double *out_dev) {
-    k_dir_stats<T><<<1, 1024, 0, c.stream>>>(g, d, n_rows, out_dev);
-    return cudaGetLastError();
-}
-
 template <typename T> cudaError_t scale(Ctx &c, T *a, int64_t n, double s) {
-    k_scale<T><<<grid_for(n, kThreads), kThreads, 0, c.stream>>>(a, n, s);
+    launch(c, k_scale<T>, dim3(grid_for(n, kThreads)), dim3(kThreads), a, n, s);
     return cudaGetLastError();
 }
 
@@ -184,6 +147,7 @@ ttie_status ttie_create(ttie_ctx **out, const ttie_params *p, void *stream) {
     c.prm = p ? *p : def;
     c.stream = (cudaStream_t)stream;
     cudaError_t e = cudaGetDevice(&c.device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c.num_sms, cudaDevAttrMultiProcessorCount, c.device);
     if (e == cudaSuccess) e = cudaMalloc(&c.ds, sizeof(DevScalars));
     if (e == cudaSuccess) e = cudaMallocHost(&c.hs, sizeof(DevScalars));
     if (e == cudaSuccess) e = cudaMemsetAsync(c.ds, 0, sizeof(DevScalars), c.stream);
@@ -245,6 +209,7 @@ static ttie_status read_err(Ctx &c, const char *where) {
     if (e & ERR_BAD_INDEX) return set_err(c, TTIE_ERR_INVALID, "%s: triangle or group index out of range", where);
     if (e & ERR_NONFINITE) return set_err(c, TTIE_ERR_NONFINITE, "%s: non-finite vertex position", where);
     if (e & ERR_STACK) return set_err(c, TTIE_ERR_CAPACITY, "%s: BVH traversal stack overflow", where);
+    if (e & ERR_BARRIER) return set_err(c, TTIE_ERR_CUDA, "%s: PCG grid barrier timed out", where);
     return TTIE_OK;
 }
 
@@ -331,7 +296,7 @@ static void mark(Ctx &c, int i) {
 }
 
 template <typename T> static cudaError_t negate_copy(Ctx &c, const T *a, T *b, int64_t n) {
-    ttie::k_copy_neg<T><<<grid_for(n, 256), 256, 0, c.stream>>>(a, b, n);
+    launch(c, ttie::k_copy_neg<T>, dim3(grid_for(n, 256)), dim3(256), a, b, n);
     return cudaGetLastError();
 }
 
@@ -359,7 +324,9 @@ static ttie_status newton_impl(Ctx &c, T *x, ttie_step_info *info) {
     c.have_cand = true;
     inf.n_candidates = n;
     mark(c, 1);
+    c.time_kernels = c.prm.profile != 0;
     CK(eval_candidates<T>(c, (const vec4_t<T> *)c.xp.p, (const int2 *)c.cand.p, n, TTIE_EVAL_E | TTIE_EVAL_H), "newton: eval");
+    c.time_kernels = false;
     c.have_eval = true;
     c.eval_what = TTIE_EVAL_E | TTIE_EVAL_H;
     CK(cudaMemcpyAsync(&c.hs->energy, &c.ds->energy, sizeof(double), cudaMemcpyDeviceToHost, c.stream), "newton");
@@ -375,6 +342,7 @@ static ttie_status newton_impl(Ctx &c, T *x, ttie_step_info *info) {
         if (c.prm.profile) cudaEventSynchronize(c.ev[5]);
         inf.ms_build = ms_between(c, 0, 1);
         inf.ms_eval = ms_between(c, 1, 2);
+        inf.ms_classify = c.n_cand > 0 ? ms_between(c, 6, 7) : 0.f;
         if (info) *info = inf;
         return TTIE_OK;
     }
@@ -389,11 +357,13 @@ static ttie_status newton_impl(Ctx &c, T *x, ttie_step_info *info) {
     CK(ensure(c, c.xsave, (size_t)(n3 > 0 ? n3 : 1) * sizeof(T)), "newton");
     CK(negate_copy(c, (const T *)c.rhs.p, (T *)c.xsave.p, n3), "newton");
     CK(pcg_solve<T>(c, (const T *)c.xsave.p, (T *)c.pcg_x.p, c.prm.pcg_rtol, c.prm.pcg_max_it), "newton: PCG");
-    CK(dir_stats<T>(c, (const T *)c.rhs.p, (const T *)c.pcg_x.p, c.n_rows, &c.ds->red[5]), "newton");
+    s = read_err(c, "ttie_newton_step");
+    if (s != TTIE_OK) return s;
+    CK(direction_stats<T>(c, (const T *)c.rhs.p, (const T *)c.pcg_x.p, &c.ds->red[5]), "newton");
     CK(cudaMemcpyAsync(c.hs, c.ds, sizeof(DevScalars), cudaMemcpyDeviceToHost, c.stream), "newton");
     CK(cudaStreamSynchronize(c.stream), "newton");
     double gd = c.hs->red[5];
-    const double dmax = c.hs->red[6];
+    const double dmax = std::sqrt(c.hs->red[6]);
     if (!std::isfinite(gd) || !std::isfinite(dmax))
         return set_err(c, TTIE_ERR_NONFINITE, "ttie_newton_step: Newton direction is not finite");
     const double cap = c.prm.max_step * c.mean_edge;
@@ -469,6 +439,8 @@ static ttie_status newton_impl(Ctx &c, T *x, ttie_step_info *info) {
     inf.ms_assemble = ms_between(c, 2, 3);
     inf.ms_pcg = ms_between(c, 3, 4);
     inf.ms_line_search = ms_between(c, 4, 5);
+    inf.ms_classify = c.n_cand > 0 ? ms_between(c, 6, 7) : 0.f;
+    inf.ms_pcg_kernel = ms_between(c, 8, 9);
     if (info) *info = inf;
     return TTIE_OK;
 }
@@ -554,6 +526,8 @@ ttie_status ttie_pcg(ttie_ctx *h, const void *d_rhs, void *d_out, double rtol, i
                         ? pcg_solve<double>(c, (const double *)d_rhs, (double *)d_out, rtol, max_it)
                         : pcg_solve<float>(c, (const float *)d_rhs, (float *)d_out, rtol, max_it);
     if (e != cudaSuccess) return cuda_err(c, e, "ttie_pcg");
+    ttie_status st = read_err(c, "ttie_pcg");
+    if (st != TTIE_OK) return st;
     CK(cudaMemcpyAsync(c.hs, c.ds, sizeof(DevScalars), cudaMemcpyDeviceToHost, c.stream), "ttie_pcg");
     CK(cudaStreamSynchronize(c.stream), "ttie_pcg");
     if (iters) *iters = c.hs->pcg_iters;
@@ -633,15 +607,15 @@ ttie_status ttie_get_active(ttie_ctx *h, int32_t *d_pairs, void *d_tc, void *d_d
     const int64_t na = c.n_active;
     if (na > 0) {
         if (d_pairs)
-            k_gather_active<<<grid_for(na, kThreads), kThreads, 0, c.stream>>>((const int2 *)c.cand.p,
+            launch(c, k_gather_active, dim3(grid_for(na, kThreads)), dim3(kThreads), (const int2 *)c.cand.p,
                                                                               (const uint32_t *)c.active.p, na,
                                                                               (int2 *)d_pairs);
         if (d_tc || d_dtc) {
             if (c.prm.precision == TTIE_F64)
-                k_split_fac<double><<<grid_for(na, kThreads), kThreads, 0, c.stream>>>((const double *)c.fac.p, na,
+                launch(c, k_split_fac<double>, dim3(grid_for(na, kThreads)), dim3(kThreads), (const double *)c.fac.p, na,
                                                                                       (double *)d_tc, (double *)d_dtc);
             else
-                k_split_fac<float><<<grid_for(na, kThreads), kThreads, 0, c.stream>>>((const float *)c.fac.p, na,
+                launch(c, k_split_fac<float>, dim3(grid_for(na, kThreads)), dim3(kThreads), (const float *)c.fac.p, na,
                                                                                      (float *)d_tc, (float *)d_dtc);
         }
         CK(cudaGetLastError(), "ttie_get_active");
@@ -668,6 +642,12 @@ ttie_status ttie_get_filter_stats(ttie_ctx *h, int64_t *out3) {
     CK(cudaMemcpyAsync(c.hs->filter_stats, c.ds->filter_stats, 3 * 8, cudaMemcpyDeviceToHost, c.stream), "stats");
     CK(cudaStreamSynchronize(c.stream), "stats");
     for (int i = 0; i < 3; ++i) out3[i] = (int64_t)c.hs->filter_stats[i];
+    return TTIE_OK;
+}
+
+ttie_status ttie_get_launch_count(ttie_ctx *h, int64_t *n) {
+    if (!h || !n) return TTIE_ERR_INVALID;
+    *n = (int64_t)h->c.n_launch;
     return TTIE_OK;
 }
 

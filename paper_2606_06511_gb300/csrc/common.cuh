@@ -46,6 +46,7 @@ enum ErrBits : int {
     ERR_BAD_INDEX = 2,      // triangle index outside [0, V) or group outside [0, 2^20)
     ERR_STACK = 4,          // traversal stack overflow
     ERR_DEFER = 8,          // exact-resolve list overflow
+    ERR_BARRIER = 16,       // a grid barrier wait ran out of its iteration limit
 };
 
 struct DevScalars {
@@ -67,6 +68,9 @@ struct DevScalars {
     double red[8];                         // PCG scalars
     int pcg_done;
     int pcg_iters;
+    unsigned int bar_count;                // grid barrier of the persistent PCG kernel: root
+    unsigned int bar_gen;                  // counter and generation; group counters below,
+    unsigned int bar_group[16][32];        // one 128-byte line each
 };
 
 // ------------------------------------------------------------------ buffers
@@ -116,7 +120,18 @@ struct Ctx {
     TTIE_BUFS(TTIE_DECL_BUF)
 #undef TTIE_DECL_BUF
     cudaEvent_t ev[12] = {};
+    int num_sms = 0;
+    unsigned long long n_launch = 0;   // kernels launched through this context
+    bool time_kernels = false;         // profile: events around the classification / PCG kernels
 };
+
+// Every kernel of the library is launched through this helper on the context's
+// stream, which also counts the launches.
+template <typename... KArgs, typename... Args>
+inline void launch(Ctx &c, void (*kernel)(KArgs...), dim3 grid, dim3 block, Args &&...args) {
+    ++c.n_launch;
+    kernel<<<grid, block, 0, c.stream>>>(static_cast<KArgs>(args)...);
+}
 
 // ------------------------------------------------------------------ launch helpers
 constexpr int kNumSMs = 152;
@@ -155,6 +170,8 @@ template <typename T> cudaError_t eval_candidates(Ctx &c, const vec4_t<T> *x, co
 // ------------------------------------------------------------------ assembly / solve (assemble.cu)
 template <typename T> cudaError_t assemble_system(Ctx &c, T *grad_out_V3);
 template <typename T> cudaError_t pcg_solve(Ctx &c, const T *rhs, T *out, double rtol, int max_it);
+// out_dev[0] = g.d, out_dev[1] = max over rows of |d_r|^2 (rows of the assembled system)
+template <typename T> cudaError_t direction_stats(Ctx &c, const T *g, const T *d, double *out_dev);
 template <typename T> cudaError_t axpy_positions(Ctx &c, const vec4_t<T> *x, const T *d, T alpha, vec4_t<T> *out);
 template <typename T> cudaError_t scatter_direction(Ctx &c, const T *d_rows, T *d_full);
 template <typename T> cudaError_t update_positions(Ctx &c, T *x, int stride, const T *d_full, T alpha);

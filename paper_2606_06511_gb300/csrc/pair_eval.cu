@@ -458,13 +458,15 @@ cudaError_t eval_candidates(Ctx &c, const vec4_t<T> *x, const int2 *pairs, int64
     const int4 *tri4 = (const int4 *)c.tri4.p;
     if (n > 0) {
         const unsigned g = grid_for(n_words * 32, kThreads, (int64_t)kNumSMs * 8);
-        k_classify<T><<<g, kThreads, 0, c.stream>>>(x, tri4, pairs, n, c.prm.exact_only, bits,
+        if (c.time_kernels) cudaEventRecord(c.ev[6], c.stream);
+        launch(c, k_classify<T>, dim3(g), dim3(kThreads), x, tri4, pairs, n, c.prm.exact_only, bits,
                                                      (uint32_t *)c.defer.p, c.ds);
-        k_resolve<T><<<kNumSMs * 4, 64, 0, c.stream>>>(x, tri4, pairs, (const uint32_t *)c.defer.p, bits, c.ds);
+        if (c.time_kernels) cudaEventRecord(c.ev[7], c.stream);
+        launch(c, k_resolve<T>, dim3(kNumSMs * 4), dim3(64), x, tri4, pairs, (const uint32_t *)c.defer.p, bits, c.ds);
         TTIE_CUDA_TRY(ensure(c, c.gtmp, (size_t)(n_words > 0 ? n_words : 1) * 4));
-        k_popc<<<grid_for(n_words, kThreads), kThreads, 0, c.stream>>>(bits, n_words, (uint32_t *)c.gtmp.p);
+        launch(c, k_popc, dim3(grid_for(n_words, kThreads)), dim3(kThreads), bits, n_words, (uint32_t *)c.gtmp.p);
         TTIE_CUDA_TRY(scan_u32_u64(c, (const uint32_t *)c.gtmp.p, (unsigned long long *)c.word_off.p, n_words));
-        k_compact<<<grid_for(n_words, kThreads), kThreads, 0, c.stream>>>(
+        launch(c, k_compact, dim3(grid_for(n_words, kThreads)), dim3(kThreads), 
             bits, n_words, (const unsigned long long *)c.word_off.p, (uint32_t *)c.active.p, c.ds);
     } else {
         TTIE_CUDA_TRY(cudaMemsetAsync(&c.ds->n_active, 0, 8, c.stream));
@@ -478,10 +480,10 @@ cudaError_t eval_candidates(Ctx &c, const vec4_t<T> *x, const int2 *pairs, int64
     TTIE_CUDA_TRY(ensure(c, c.fac, (size_t)(n_act > 0 ? n_act : 1) * kFacStride * sizeof(T)));
     const unsigned gd = grid_for(n_act, 128, (int64_t)kNumSMs * 8);
     if (grad)
-        k_derivs<T, true><<<gd, 128, 0, c.stream>>>(x, tri4, pairs, (const uint32_t *)c.active.p, (T)c.prm.tc_scale,
+        launch(c, k_derivs<T, true>, dim3(gd), dim3(128), x, tri4, pairs, (const uint32_t *)c.active.p, (T)c.prm.tc_scale,
                                                      (T *)c.fac.p, (double *)c.partials.p, c.ds);
     else
-        k_derivs<T, false><<<gd, 128, 0, c.stream>>>(x, tri4, pairs, (const uint32_t *)c.active.p, (T)c.prm.tc_scale,
+        launch(c, k_derivs<T, false>, dim3(gd), dim3(128), x, tri4, pairs, (const uint32_t *)c.active.p, (T)c.prm.tc_scale,
                                                       (T *)c.fac.p, (double *)c.partials.p, c.ds);
     c.n_active = n_act;
     return cudaGetLastError();

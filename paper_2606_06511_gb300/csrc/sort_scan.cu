@@ -174,9 +174,9 @@ cudaError_t scan_u32_u64(Ctx &c, const uint32_t *in, unsigned long long *out, in
     if (n_tiles < 1) n_tiles = 1;
     TTIE_CUDA_TRY(ensure(c, c.scan_tmp, (size_t)(n_tiles + 1) * sizeof(unsigned long long)));
     auto *ts = (unsigned long long *)c.scan_tmp.p;
-    k_tile_sums<<<(unsigned)n_tiles, kThreads, 0, c.stream>>>(in, n, ts);
-    k_scan_tile_sums<<<1, 1024, 0, c.stream>>>(ts, n_tiles);
-    k_scan_tiles<<<(unsigned)n_tiles, kThreads, 0, c.stream>>>(in, n, ts, n_tiles, out);
+    launch(c, k_tile_sums, dim3((unsigned)n_tiles), dim3(kThreads), in, n, ts);
+    launch(c, k_scan_tile_sums, dim3(1), dim3(1024), ts, n_tiles);
+    launch(c, k_scan_tiles, dim3((unsigned)n_tiles), dim3(kThreads), in, n, ts, n_tiles, out);
     return cudaGetLastError();
 }
 
@@ -192,9 +192,9 @@ cudaError_t radix_sort(Ctx &c, unsigned long long *keys, uint32_t *vals, unsigne
     uint32_t *va = vals, *vb = vals2;
     int passes = 0;
     for (int shift = 0; shift < bits; shift += kRadixBits, ++passes) {
-        k_radix_hist<<<(unsigned)n_tiles, kThreads, 0, c.stream>>>(ka, n, shift, n_tiles, cnt);
+        launch(c, k_radix_hist, dim3((unsigned)n_tiles), dim3(kThreads), ka, n, shift, n_tiles, cnt);
         TTIE_CUDA_TRY(scan_u32_u64(c, cnt, off, n_cnt));
-        k_radix_scatter<<<(unsigned)n_tiles, kThreads, 0, c.stream>>>(ka, va, kb, vb, n, shift, n_tiles, off);
+        launch(c, k_radix_scatter, dim3((unsigned)n_tiles), dim3(kThreads), ka, va, kb, vb, n, shift, n_tiles, off);
         TTIE_CUDA_TRY(cudaGetLastError());
         unsigned long long *tk = ka; ka = kb; kb = tk;
         uint32_t *tv = va; va = vb; vb = tv;

@@ -56,7 +56,8 @@ class StepInfo(ctypes.Structure):
                 ("n_active_new", ctypes.c_int64), ("alpha", ctypes.c_double), ("grad_dot_dir", ctypes.c_double),
                 ("pcg_iters", ctypes.c_int), ("pcg_rel_residual", ctypes.c_double), ("ls_trials", ctypes.c_int),
                 ("n_candidates_swept", ctypes.c_int64), ("ms_build", ctypes.c_float), ("ms_eval", ctypes.c_float),
-                ("ms_assemble", ctypes.c_float), ("ms_pcg", ctypes.c_float), ("ms_line_search", ctypes.c_float)]
+                ("ms_assemble", ctypes.c_float), ("ms_pcg", ctypes.c_float), ("ms_line_search", ctypes.c_float),
+                ("ms_classify", ctypes.c_float), ("ms_pcg_kernel", ctypes.c_float)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -95,6 +96,7 @@ _SIGS = {
                                        ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]),
     "ttie_get_direction": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "ttie_get_filter_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)]),
+    "ttie_get_launch_count": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)]),
 }
 
 
@@ -271,3 +273,8 @@ class Context:
         arr = (ctypes.c_int64 * 3)()
         self._chk(self.lib.ttie_get_filter_stats(self.h, arr))
         return {"fp32": arr[0], "fp64": arr[1], "exact": arr[2]}
+
+    def get_launch_count(self) -> int:
+        n = ctypes.c_int64()
+        self._chk(self.lib.ttie_get_launch_count(self.h, ctypes.byref(n)))
+        return n.value
