@@ -236,6 +236,39 @@ ttie_status ttie_get_direction(ttie_ctx *ctx, void *d_out);
  * by FP64, and by exact arithmetic (host out array of 3). */
 ttie_status ttie_get_filter_stats(ttie_ctx *ctx, int64_t *out3);
 
+/* ---- solve without allocating -------------------------------------------------- */
+
+/* Largest system ttie_pcg_static accepts (rows of 3x3 blocks). */
+#define TTIE_PCG_STATIC_MAX_ROWS 16384
+
+/*
+ * The block-Jacobi PCG solve of ttie_pcg, (H + mu I) d = rhs on a 3x3 block-CSR matrix
+ * (layout as ttie_bsr_view: row_ptr n_rows + 1, col_idx nnzb ascending per row, val
+ * nnzb x 9 row-major, float32), for callers that cannot allocate device memory: a host
+ * whose device-memory budget is planned up front (a plugin or embedded runtime that
+ * hands out no cudaMalloc), or a loop that cannot afford the device-wide
+ * synchronisation an allocation implies.  It needs no context and allocates nothing:
+ * no cudaMalloc, cudaFree or allocating library call.  The paper has no counterpart;
+ * this is a service of the library.
+ *
+ * All inputs and the output d_out (n_rows x 3) are the caller's device buffers.  The
+ * work vectors live in one static device array sized for TTIE_PCG_STATIC_MAX_ROWS rows
+ * (about 1.4 MB), which every GPU that loads the library holds until the process exits.
+ * n_rows beyond that limit is refused with TTIE_ERR_INVALID before any work.
+ *
+ * The first call on a device looks up the array's device address (once per device, with
+ * that device current); make that first call before any stream capture begins.  Every
+ * call reuses the same array and clears the parts that must start at zero; two calls
+ * whose work overlaps on the GPU (other streams, other host threads, the same device)
+ * race on it, so serialise them.  Work is enqueued on `stream` (NULL: legacy default
+ * stream) and the call synchronises it before returning iters and rel_residual (host
+ * outs, nullable).  Errors: INVALID, CUDA (also when the solver's bounded grid-barrier
+ * wait runs out), NONFINITE.
+ */
+ttie_status ttie_pcg_static(const int32_t *d_row_ptr, const int32_t *d_col_idx, const float *d_val,
+                            int64_t n_rows, double mu, const float *d_rhs, float *d_out, double rtol,
+                            int max_it, void *stream, int *iters, double *rel_residual);
+
 /* Number of CUDA kernels the context has launched since ttie_create (host out). */
 ttie_status ttie_get_launch_count(ttie_ctx *ctx, int64_t *n);
 

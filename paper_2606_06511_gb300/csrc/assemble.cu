@@ -690,4 +690,38 @@ template <typename T> cudaError_t direction_stats(Ctx &c, const T *g, const T *d
 template cudaError_t direction_stats<float>(Ctx &, const float *, const float *, double *);
 template cudaError_t direction_stats<double>(Ctx &, const double *, const double *, double *);
 
+// PCG on explicit buffers (no context): the setup and persistent kernels above, on
+// caller-provided work vectors and state.  ds must hold n_rows and trace (mu = mu_rel *
+// trace / (3 n_rows)) with its counters, tickets and barrier words zeroed.
+cudaError_t pcg_run_raw(cudaStream_t stream, int num_sms, const int32_t *row_ptr, const int32_t *col_idx,
+                        const float *bval, int64_t n_rows, double mu_rel, const float *rhs, float *out, float *dinv,
+                        float *r, float *z, float *p, float *q, double *partials, DevScalars *ds, double rtol,
+                        int max_it) {
+    const unsigned g = grid_for(n_rows, kThreads, kNumSMs * 4);
+    k_pcg_setup<float><<<g, kThreads, 0, stream>>>(row_ptr, col_idx, bval, mu_rel, dinv, rhs, out, r, z, p, partials,
+                                                   ds);
+    TTIE_CUDA_TRY(cudaGetLastError());
+    PcgArgs<float> args;
+    args.row_ptr = row_ptr;
+    args.col_idx = col_idx;
+    args.bval = bval;
+    args.dinv = dinv;
+    args.x = out;
+    args.r = r;
+    args.z = z;
+    args.p = p;
+    args.q = q;
+    args.partA = partials;
+    args.partB = partials + 2 * kNumSMs * 8;
+    args.rtol2 = rtol * rtol;
+    args.max_it = max_it;
+    args.ds = ds;
+    int blocks = (int)((n_rows * kLanesPerRow + kPcgThreads - 1) / kPcgThreads);
+    if (blocks > num_sms) blocks = num_sms;
+    if (blocks < 1) blocks = 1;
+    void *kargs[] = {&args};
+    return cudaLaunchCooperativeKernel((const void *)k_pcg_persistent<float>, dim3((unsigned)blocks),
+                                       dim3(kPcgThreads), kargs, 0, stream);
+}
+
 }  // namespace ttie
