@@ -477,6 +477,134 @@ __global__ void __launch_bounds__(kPcgThreads) k_pcg_persistent(PcgArgs<T> a) {
     }
 }
 
+// ---------------------------------------------------------------- PCG, block-resident rows
+// Each block owns the contiguous rows [row0, row0 + nrow) for the whole solve.  Their x,
+// r, z, p, q, the inverse diagonal blocks, the row offsets and, when they fit, the matrix
+// rows live in shared memory, so the vector updates never leave the SM.  Only z, which
+// the product reads across rows, is also written to global memory (read back through
+// L2 by other blocks after the barrier that follows the update).  Same iteration, same
+// reductions and decisions as k_pcg_persistent.
+constexpr int kResidentSmem = 200 * 1024;   // dynamic shared memory per block
+
+template <typename T>
+__device__ __forceinline__ double resident_direction(const PcgArgs<T> &a, const int *srp, const T *sval,
+                                                     const int *scol, bool cached, int b_begin, long long row0,
+                                                     int nrow, const T *sz, T *sp, T *sq, T mu, T beta, bool first) {
+    const int lane = threadIdx.x & 31, sub = lane & (kLanesPerRow - 1);
+    const unsigned gmask = 0xffu << (lane & ~(kLanesPerRow - 1));
+    double pq = 0.0;
+    for (int lr = threadIdx.x / kLanesPerRow; lr < nrow; lr += kPcgThreads / kLanesPerRow) {
+        T y0 = 0, y1 = 0, y2 = 0;
+        for (int b = srp[lr] + sub; b < srp[lr + 1]; b += kLanesPerRow) {
+            const T *m = cached ? sval + (size_t)b * 9 : a.bval + (size_t)(b_begin + b) * 9;
+            const int c = cached ? scol[b] : a.col_idx[b_begin + b];
+            const T c0 = __ldcg(&a.z[c * 3]), c1 = __ldcg(&a.z[c * 3 + 1]), c2 = __ldcg(&a.z[c * 3 + 2]);
+            y0 += m[0] * c0 + m[1] * c1 + m[2] * c2;
+            y1 += m[3] * c0 + m[4] * c1 + m[5] * c2;
+            y2 += m[6] * c0 + m[7] * c1 + m[8] * c2;
+        }
+#pragma unroll
+        for (int o = kLanesPerRow / 2; o; o >>= 1) {
+            y0 += __shfl_xor_sync(gmask, y0, o, kLanesPerRow);
+            y1 += __shfl_xor_sync(gmask, y1, o, kLanesPerRow);
+            y2 += __shfl_xor_sync(gmask, y2, o, kLanesPerRow);
+        }
+        if (sub == 0) {
+            const T w[3] = {y0 + mu * sz[lr * 3], y1 + mu * sz[lr * 3 + 1], y2 + mu * sz[lr * 3 + 2]};
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                const T pi = first ? sz[lr * 3 + i] : sz[lr * 3 + i] + beta * sp[lr * 3 + i];
+                const T qi = first ? w[i] : w[i] + beta * sq[lr * 3 + i];
+                sp[lr * 3 + i] = pi;
+                sq[lr * 3 + i] = qi;
+                pq += (double)pi * qi;
+            }
+        }
+    }
+    (void)row0;
+    return pq;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kPcgThreads) k_pcg_resident(PcgArgs<T> a, int rows_per_block, int smem_bytes) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    DevScalars *ds = a.ds;
+    if (ds->pcg_done) return;
+    const long long nr = (long long)ds->n_rows;
+    const int R = rows_per_block;
+    const long long row0 = (long long)blockIdx.x * R;
+    const int nrow = (int)max(0LL, min((long long)R, nr - row0));
+    T *sx = (T *)smem, *sr = sx + 3 * R, *sz = sr + 3 * R, *sp = sz + 3 * R, *sq = sp + 3 * R, *sdi = sq + 3 * R;
+    int *srp = (int *)(sdi + 9 * R);
+    const size_t vec_bytes = ((size_t)R * 24 * sizeof(T) + (size_t)(R + 1) * sizeof(int) + 15) / 16 * 16;
+    const int b_begin = nrow ? a.row_ptr[row0] : 0;
+    const int nnz = nrow ? a.row_ptr[row0 + nrow] - b_begin : 0;
+    const bool cached = vec_bytes + (size_t)nnz * (9 * sizeof(T) + sizeof(int)) <= (size_t)smem_bytes;
+    T *sval = (T *)(smem + vec_bytes);
+    int *scol = (int *)(sval + (size_t)9 * nnz);
+    // load the block's rows (x = 0, r, z = M^-1 r, p = z and M^-1 from the setup kernel)
+    for (int i = threadIdx.x; i < 3 * nrow; i += blockDim.x) {
+        sx[i] = a.x[row0 * 3 + i];
+        sr[i] = a.r[row0 * 3 + i];
+        sz[i] = a.z[row0 * 3 + i];
+        sp[i] = a.p[row0 * 3 + i];
+    }
+    for (int i = threadIdx.x; i < 9 * nrow; i += blockDim.x) sdi[i] = a.dinv[row0 * 9 + i];
+    for (int i = threadIdx.x; i <= nrow; i += blockDim.x) srp[i] = a.row_ptr[row0 + i] - b_begin;
+    if (cached) {
+        for (int i = threadIdx.x; i < 9 * nnz; i += blockDim.x) sval[i] = a.bval[(size_t)b_begin * 9 + i];
+        for (int i = threadIdx.x; i < nnz; i += blockDim.x) scol[i] = a.col_idx[b_begin + i];
+    }
+    __syncthreads();
+    const T mu = (T)ds->mu;
+    const double rr0 = ds->red[1];
+    double rz = ds->red[0], rr = rr0;
+    double v1[1] = {resident_direction(a, srp, sval, scol, cached, b_begin, row0, nrow, sz, sp, sq, mu, T(0), true)};
+    if (!grid_allreduce<1>(v1, a.partA, ds)) return;
+    int it = 0;
+    for (; it < a.max_it; ++it) {
+        const double pq = v1[0];
+        const bool ok = pq > 0.0 && isfinite(pq);
+        // breakdown at the first iteration keeps x = p = M^-1 r0 (preconditioned gradient)
+        const T alpha = (T)(ok ? rz / pq : (it == 0 ? 1.0 : 0.0));
+        double v2[2] = {0.0, 0.0};
+        for (int lr = threadIdx.x; lr < nrow; lr += blockDim.x) {
+            T rv[3];
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                sx[lr * 3 + i] += alpha * sp[lr * 3 + i];
+                rv[i] = sr[lr * 3 + i] - alpha * sq[lr * 3 + i];
+                sr[lr * 3 + i] = rv[i];
+            }
+            const T *di = sdi + lr * 9;
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                const T zi = di[3 * i] * rv[0] + di[3 * i + 1] * rv[1] + di[3 * i + 2] * rv[2];
+                sz[lr * 3 + i] = zi;
+                a.z[(row0 + lr) * 3 + i] = zi;
+                v2[0] += (double)rv[i] * zi;
+                v2[1] += (double)rv[i] * rv[i];
+            }
+        }
+        if (!grid_allreduce<2>(v2, a.partB, ds)) return;
+        if (!ok) { ++it; break; }
+        const double beta = rz != 0.0 ? v2[0] / rz : 0.0;
+        rz = v2[0];
+        rr = v2[1];
+        if (rr <= a.rtol2 * rr0 || !isfinite(rr)) { ++it; break; }
+        v1[0] = resident_direction(a, srp, sval, scol, cached, b_begin, row0, nrow, sz, sp, sq, mu, (T)beta, false);
+        if (!grid_allreduce<1>(v1, a.partA, ds)) return;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 3 * nrow; i += blockDim.x) a.x[row0 * 3 + i] = sx[i];
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        ds->pcg_iters = it;
+        ds->red[0] = rz;
+        ds->red[4] = rr;
+        ds->pcg_done = 1;
+    }
+}
+
 template <typename T>
 __global__ void k_axpy_positions(const vec4_t<T> *__restrict__ x, const T *__restrict__ d, T alpha, int64_t V,
                                  vec4_t<T> *__restrict__ out) {
@@ -633,19 +761,29 @@ cudaError_t pcg_solve(Ctx &c, const T *rhs, T *out, double rtol, int max_it) {
     args.rtol2 = rtol * rtol;
     args.max_it = max_it;
     args.ds = c.ds;
-    int per_sm = 0;
-    TTIE_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg_persistent<T>, kPcgThreads, 0));
-    if (per_sm < 1) per_sm = 1;
     const int sms = c.num_sms > 0 ? c.num_sms : kNumSMs;
     // one block per SM at most: fewer arrivals per grid barrier
     int64_t blocks = (nr * kLanesPerRow + kPcgThreads - 1) / kPcgThreads;
     if (blocks > (int64_t)sms) blocks = sms;
     if (blocks < 1) blocks = 1;
-    void *kargs[] = {&args};
+    // rows resident in shared memory when a block's vectors fit; else the global-memory kernel
+    const int64_t rows_per_block = (nr + blocks - 1) / blocks;
+    const size_t vec_bytes = ((size_t)rows_per_block * 24 * sizeof(T) + (size_t)(rows_per_block + 1) * 4 + 15) / 16 * 16;
+    const bool resident = vec_bytes <= (size_t)kResidentSmem;
     ++c.n_launch;
     if (c.prm.profile) cudaEventRecord(c.ev[8], c.stream);
-    TTIE_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)k_pcg_persistent<T>, dim3((unsigned)blocks), dim3(kPcgThreads),
-                                              kargs, 0, c.stream));
+    if (resident) {
+        TTIE_CUDA_TRY(cudaFuncSetAttribute((const void *)k_pcg_resident<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           kResidentSmem));
+        int rpb = (int)rows_per_block, smem = kResidentSmem;
+        void *kargs[] = {&args, &rpb, &smem};
+        TTIE_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)k_pcg_resident<T>, dim3((unsigned)blocks),
+                                                  dim3(kPcgThreads), kargs, (size_t)kResidentSmem, c.stream));
+    } else {
+        void *kargs[] = {&args};
+        TTIE_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)k_pcg_persistent<T>, dim3((unsigned)blocks),
+                                                  dim3(kPcgThreads), kargs, 0, c.stream));
+    }
     if (c.prm.profile) cudaEventRecord(c.ev[9], c.stream);
     return cudaGetLastError();
 }
