@@ -25,8 +25,10 @@ def nvcc() -> str:
 
 
 def flags(extra=()):
+    # TTIE_BUILD_CHECKS=1 builds the self-checking variant (bounds checks, a sync after every launch)
+    checks = ["-DTTIE_CHECKS"] if os.environ.get("TTIE_BUILD_CHECKS") == "1" else []
     return ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include"),
-                   "-I", SRC] + list(extra)
+                   "-I", SRC] + checks + list(extra)
 
 
 def _stamp():
@@ -35,6 +37,7 @@ def _stamp():
 
 
 def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:
+    force = force or os.environ.get("TTIE_BUILD_CHECKS") == "1"
     if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _stamp() and not ptxas_info:
         return LIB
     os.makedirs(OUT_DIR, exist_ok=True)

@@ -144,6 +144,9 @@ __global__ void k_block_keys(const int4 *__restrict__ tri4, const int2 *__restri
         for (int r = 0; r < 6; ++r) row[r] = vrow[vid(a, b, r)];
 #pragma unroll
         for (int r = 0; r < 6; ++r)
+            if (TTIE_BAD((DevScalars *)ds, row[r] < nr, 11, row[r])) row[r] = 0;
+#pragma unroll
+        for (int r = 0; r < 6; ++r)
 #pragma unroll
             for (int c = 0; c < 6; ++c) {
                 key[k * 36 + r * 6 + c] = row[r] * nr + row[c];
@@ -179,8 +182,10 @@ __global__ void k_block_values(const unsigned long long *__restrict__ key, const
     for (unsigned long long bi = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; bi < nb;
          bi += (unsigned long long)gridDim.x * blockDim.x) {
         const uint32_t s = run_start[bi], e = run_start[bi + 1];
+        if (TTIE_BAD((DevScalars *)ds, s < e && e <= ds->n_active * 36, 21, ((long long)s << 32) | e)) continue;
         const unsigned long long kk = key[s];
         const unsigned long long row = kk / nr, col = kk - row * nr;
+        if (TTIE_BAD((DevScalars *)ds, row < nr, 22, row)) continue;
         col_idx[bi] = (int32_t)col;
         if (bi == 0 || key[run_start[bi - 1]] / nr != row) row_ptr[row] = (int32_t)bi;
         if (bi == nb - 1) row_ptr[nr] = (int32_t)nb;
@@ -191,6 +196,7 @@ __global__ void k_block_values(const unsigned long long *__restrict__ key, const
         for (uint32_t i = s; i < e; ++i) {
             const uint32_t v = val[i];
             const uint32_t pk = v / 36, rc = v - pk * 36, r = rc / 6, c = rc - r * 6;
+            if (TTIE_BAD((DevScalars *)ds, pk < ds->n_active, 23, pk)) continue;
             const T *zp = z + (size_t)pk * kZStride;
 #pragma unroll
             for (int t = 0; t < 3; ++t) {
@@ -242,6 +248,9 @@ __global__ void k_pcg_setup(const int32_t *__restrict__ row_ptr, const int32_t *
          row += (unsigned long long)gridDim.x * blockDim.x) {
         const T zero9[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
         const T *diag = zero9;
+        if (TTIE_BAD(ds, row_ptr[row] <= row_ptr[row + 1] && (unsigned long long)row_ptr[row + 1] <= ds->nnzb, 31,
+                     row))
+            continue;
         for (int b = row_ptr[row]; b < row_ptr[row + 1]; ++b)
             if ((unsigned long long)col_idx[b] == row) { diag = bval + (size_t)b * 9; break; }
         T di[9];
@@ -275,80 +284,72 @@ __global__ void k_pcg_setup(const int32_t *__restrict__ row_ptr, const int32_t *
 // sets ERR_BARRIER and the kernel returns.  Reductions: block partials, then every block
 // sums all partials in the same order, so all blocks take the same decisions and the
 // result does not depend on timing.
-constexpr long long kBarrierSpins = 50000000;   // with ~32-64 ns sleeps: a few seconds
+constexpr long long kBarrierSpins = 50000000;   // with ~20-40 ns sleeps: a few seconds
 
-constexpr int kBarGroups = 16;
-
-// Two-level barrier: blocks arrive on one of 16 group counters (separate cache lines),
-// the last of each group on the root counter, the last of all bumps the generation the
-// others poll.  Same-address atomics are the cost of a grid barrier (they serialise, and
-// more so across the two dies), so each counter sees at most ~G/16 or 16 arrivals.
-__device__ __forceinline__ bool grid_barrier(DevScalars *ds) {
-    __syncthreads();
-    __shared__ int failed;
-    if (threadIdx.x == 0) {
-        volatile unsigned int *gen = &ds->bar_gen;
-        const unsigned int g = *gen;
-        const unsigned int G = gridDim.x;
-        const unsigned int ng = G < kBarGroups ? G : kBarGroups;
-        const unsigned int grp = blockIdx.x % ng;
-        const unsigned int gsize = G / ng + (grp < G % ng ? 1u : 0u);
-        __threadfence();
-        failed = 0;
-        bool release = false;
-        if (atomicAdd(&ds->bar_group[grp][0], 1u) == gsize - 1) {
-            ds->bar_group[grp][0] = 0u;
-            __threadfence();
-            if (atomicAdd(&ds->bar_count, 1u) == ng - 1) {
-                ds->bar_count = 0u;
-                __threadfence();
-                atomicAdd(&ds->bar_gen, 1u);
-                release = true;
-            }
-        }
-        if (!release) {
-            long long spins = 0;
-            while (*gen == g) {
-                if (++spins > kBarrierSpins) {
-                    atomicOr(&ds->err, ERR_BARRIER);
-                    failed = 1;
-                    break;
-                }
-                __nanosleep(32);
-            }
-        }
-        __threadfence();
-        if (*(volatile int *)&ds->err & ERR_BARRIER) failed = 1;
-    }
-    __syncthreads();
-    return failed == 0;
-}
-
-// Sum of per-block values v[0..N) over the grid; identical in every block.
+// Sum of per-block values v[0..N) over the grid, identical in every block, fused with a
+// grid barrier.  Each block writes its partial sums and arrives on one counter; the last
+// block to arrive adds all partials in block order (a fixed order, so the result does not
+// depend on timing), publishes the totals and bumps the generation the others poll; they
+// then read the totals.  Waits are bounded (kBarrierSpins); on timeout ERR_BARRIER is set
+// and false returned.  part holds N x gridDim.x partials followed by N totals.
 template <int N>
 __device__ __forceinline__ bool grid_allreduce(double (&v)[N], double *part, DevScalars *ds) {
     __shared__ double tot[N];
+    __shared__ int s_last, s_fail;
+    __shared__ unsigned s_gen;
+    const unsigned G = gridDim.x;
+    double b[N];
 #pragma unroll
-    for (int i = 0; i < N; ++i) {
-        const double b = block_sum(v[i]);
-        if (threadIdx.x == 0) part[(size_t)i * gridDim.x + blockIdx.x] = b;
+    for (int i = 0; i < N; ++i) b[i] = block_sum(v[i]);
+    if (threadIdx.x == 0) {
+        s_fail = 0;
+        s_gen = *(volatile unsigned int *)&ds->bar_gen;   // before arriving: the release bumps it
+#pragma unroll
+        for (int i = 0; i < N; ++i) part[(size_t)i * G + blockIdx.x] = b[i];
+        __threadfence();
+        s_last = atomicAdd(&ds->bar_count, 1u) == G - 1;
     }
-    if (!grid_barrier(ds)) return false;
+    __syncthreads();
     if (threadIdx.x < 32) {
+        const unsigned g = s_gen;
+        if (s_last) {
+            __threadfence();
 #pragma unroll
-        for (int i = 0; i < N; ++i) {
-            double s = 0.0;
-            for (unsigned j = threadIdx.x; j < gridDim.x; j += 32) s += __ldcg(&part[(size_t)i * gridDim.x + j]);
+            for (int i = 0; i < N; ++i) {
+                double s = 0.0;
+                for (unsigned j = threadIdx.x; j < G; j += 32) s += __ldcg(&part[(size_t)i * G + j]);
 #pragma unroll
-            for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-            if (threadIdx.x == 0) tot[i] = s;
+                for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+                tot[i] = s;
+            }
+            if (threadIdx.x == 0) {
+#pragma unroll
+                for (int i = 0; i < N; ++i) part[(size_t)N * G + i] = tot[i];
+                ds->bar_count = 0u;
+                __threadfence();
+                atomicAdd(&ds->bar_gen, 1u);
+            }
+        } else if (threadIdx.x == 0) {
+            long long spins = 0;
+            while (*(volatile unsigned int *)&ds->bar_gen == g) {
+                if (++spins > kBarrierSpins) {
+                    atomicOr(&ds->err, ERR_BARRIER);
+                    s_fail = 1;
+                    break;
+                }
+                __nanosleep(20);
+            }
+            __threadfence();
+#pragma unroll
+            for (int i = 0; i < N; ++i) tot[i] = __ldcg(&part[(size_t)N * G + i]);
         }
     }
     __syncthreads();
+    const bool ok = s_fail == 0;
 #pragma unroll
     for (int i = 0; i < N; ++i) v[i] = tot[i];
     __syncthreads();
-    return true;
+    return ok;
 }
 
 template <typename T> struct PcgArgs {
@@ -378,8 +379,10 @@ __device__ __forceinline__ void spmv_row(const PcgArgs<T> &a, unsigned long long
     const int b0 = a.row_ptr[row], b1 = a.row_ptr[row + 1];
     y0 = 0; y1 = 0; y2 = 0;
     for (int b = b0 + sub; b < b1; b += kLanesPerRow) {
+        if (TTIE_BAD(a.ds, b >= 0 && (unsigned long long)b < a.ds->nnzb, 51, b)) break;
         const T *m = a.bval + (size_t)b * 9;
         const int c = a.col_idx[b];
+        if (TTIE_BAD(a.ds, c >= 0 && (unsigned long long)c < a.ds->n_rows, 52, c)) break;
         const T c0 = __ldcg(&a.z[c * 3]), c1 = __ldcg(&a.z[c * 3 + 1]), c2 = __ldcg(&a.z[c * 3 + 2]);
         y0 += m[0] * c0 + m[1] * c1 + m[2] * c2;
         y1 += m[3] * c0 + m[4] * c1 + m[5] * c2;
@@ -496,8 +499,10 @@ __device__ __forceinline__ double resident_direction(const PcgArgs<T> &a, const 
     for (int lr = threadIdx.x / kLanesPerRow; lr < nrow; lr += kPcgThreads / kLanesPerRow) {
         T y0 = 0, y1 = 0, y2 = 0;
         for (int b = srp[lr] + sub; b < srp[lr + 1]; b += kLanesPerRow) {
+            if (TTIE_BAD(a.ds, b >= 0 && (unsigned long long)(b_begin + b) < a.ds->nnzb, 41, b)) break;
             const T *m = cached ? sval + (size_t)b * 9 : a.bval + (size_t)(b_begin + b) * 9;
             const int c = cached ? scol[b] : a.col_idx[b_begin + b];
+            if (TTIE_BAD(a.ds, c >= 0 && (unsigned long long)c < a.ds->n_rows, 42, c)) break;
             const T c0 = __ldcg(&a.z[c * 3]), c1 = __ldcg(&a.z[c * 3 + 1]), c2 = __ldcg(&a.z[c * 3 + 2]);
             y0 += m[0] * c0 + m[1] * c1 + m[2] * c2;
             y1 += m[3] * c0 + m[4] * c1 + m[5] * c2;
@@ -550,7 +555,10 @@ __global__ void __launch_bounds__(kPcgThreads) k_pcg_resident(PcgArgs<T> a, int 
         sp[i] = a.p[row0 * 3 + i];
     }
     for (int i = threadIdx.x; i < 9 * nrow; i += blockDim.x) sdi[i] = a.dinv[row0 * 9 + i];
-    for (int i = threadIdx.x; i <= nrow; i += blockDim.x) srp[i] = a.row_ptr[row0 + i] - b_begin;
+    for (int i = threadIdx.x; i <= nrow; i += blockDim.x) {
+        srp[i] = a.row_ptr[row0 + i] - b_begin;
+        if (TTIE_BAD(ds, srp[i] >= 0 && srp[i] <= nnz, 43, srp[i])) srp[i] = 0;
+    }
     if (cached) {
         for (int i = threadIdx.x; i < 9 * nnz; i += blockDim.x) sval[i] = a.bval[(size_t)b_begin * 9 + i];
         for (int i = threadIdx.x; i < nnz; i += blockDim.x) scol[i] = a.col_idx[b_begin + i];
@@ -653,6 +661,22 @@ __global__ void k_dir_stats(const T *__restrict__ g, const T *__restrict__ d, do
     grid_sums<1>(v, partials, &ds->done_counter[5], [&](const double *t) { out[0] = t[0]; });
 }
 
+#ifdef TTIE_CHECKS
+__global__ void k_check_sorted(const unsigned long long *key, int64_t n, DevScalars *ds) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x + 1; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        if (TTIE_BAD(ds, key[i - 1] <= key[i], 71, i)) return;
+}
+__global__ void k_check_runs(const uint32_t *run_start, const unsigned long long *pos, const uint32_t *flag, int64_t n,
+                             DevScalars *ds) {
+    const unsigned long long nb = ds->nnzb;
+    for (unsigned long long k = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; k < nb;
+         k += (unsigned long long)gridDim.x * blockDim.x)
+        if (TTIE_BAD(ds, run_start[k] < run_start[k + 1], 72, k)) return;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x + 1; i <= n; i += (int64_t)gridDim.x * blockDim.x)
+        if (TTIE_BAD(ds, pos[i] == pos[i - 1] + flag[i - 1], 73, i)) return;
+}
+#endif
+
 int bits_for(unsigned long long v) {
     int b = 0;
     while (b < 64 && (v >> b) != 0ull) ++b;
@@ -700,7 +724,10 @@ cudaError_t assemble_system(Ctx &c, T *grad_full) {
     const int kbits = bits_for((unsigned long long)nr * (unsigned long long)nr);
     TTIE_CUDA_TRY(radix_sort(c, (unsigned long long *)c.bkey.p, (uint32_t *)c.bval.p, (unsigned long long *)c.bkey2.p,
                              (uint32_t *)c.bval2.p, nk, kbits));
-    // run boundaries: flags -> positions (bkey2 reused as the u64 scan output)
+#ifdef TTIE_CHECKS
+    launch(c, k_check_sorted, dim3(grid_for(nk, kThreads)), dim3(kThreads), (const unsigned long long *)c.bkey.p, nk, c.ds);
+#endif
+    // run boundaries: flags -> positions
     launch(c, k_run_flags, dim3(grid_for(nk, kThreads)), dim3(kThreads), (const unsigned long long *)c.bkey.p, nk,
                                                                   (uint32_t *)c.bflag.p);
     TTIE_CUDA_TRY(ensure(c, c.gtmp, (size_t)(nk + 1) * 8));
@@ -708,6 +735,10 @@ cudaError_t assemble_system(Ctx &c, T *grad_full) {
     launch(c, k_run_starts, dim3(grid_for(nk, kThreads)), dim3(kThreads), (const uint32_t *)c.bflag.p,
                                                                    (const unsigned long long *)c.gtmp.p, nk,
                                                                    (uint32_t *)c.run_start.p, c.ds);
+#ifdef TTIE_CHECKS
+    launch(c, k_check_runs, dim3(grid_for(nk, kThreads)), dim3(kThreads), (const uint32_t *)c.run_start.p,
+           (const unsigned long long *)c.gtmp.p, (const uint32_t *)c.bflag.p, nk, c.ds);
+#endif
     TTIE_CUDA_TRY(cudaMemcpyAsync(&c.hs->nnzb, &c.ds->nnzb, 8, cudaMemcpyDeviceToHost, c.stream));
     TTIE_CUDA_TRY(cudaStreamSynchronize(c.stream));
     const int64_t nnzb = nk > 0 ? (int64_t)c.hs->nnzb : 0;
@@ -741,7 +772,7 @@ cudaError_t pcg_solve(Ctx &c, const T *rhs, T *out, double rtol, int max_it) {
     TTIE_CUDA_TRY(ensure(c, c.partials, (size_t)kNumSMs * 16 * 4 * sizeof(double)));
     double *part = (double *)c.partials.p;
     const unsigned g = grid_for(nr, kThreads, kNumSMs * 4);
-    TTIE_CUDA_TRY(cudaMemsetAsync(&c.ds->bar_count, 0, sizeof(unsigned int) * (2 + 16 * 32), c.stream));
+    TTIE_CUDA_TRY(cudaMemsetAsync(&c.ds->bar_count, 0, 2 * sizeof(unsigned int), c.stream));
     launch(c, k_pcg_setup<T>, dim3(g), dim3(kThreads), (const int32_t *)c.row_ptr.p, (const int32_t *)c.col_idx.p,
                                                  (const T *)c.bsr_val.p, c.prm.mu_rel, (T *)c.dinv.p, rhs, out,
                                                  (T *)c.pcg_r.p, (T *)c.pcg_z.p, (T *)c.pcg_p.p, part, c.ds);

@@ -304,6 +304,7 @@ __global__ void __launch_bounds__(kThreads) k_traverse(int n, const int2 *__rest
                     const uint32_t tj = perm[node - (n - 1)];
                     if (share_vertex(tq, tri4[tj])) continue;
                     if (kWrite) {
+                        if (TTIE_BAD(ds, out + cnt < offset[s + 1], 61, out + cnt)) continue;
                         pairs[out + cnt] = make_int2((int)min(qi, tj), (int)max(qi, tj));
                     }
                     ++cnt;

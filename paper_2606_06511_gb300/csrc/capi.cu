@@ -210,6 +210,12 @@ static ttie_status read_err(Ctx &c, const char *where) {
     if (e & ERR_NONFINITE) return set_err(c, TTIE_ERR_NONFINITE, "%s: non-finite vertex position", where);
     if (e & ERR_STACK) return set_err(c, TTIE_ERR_CAPACITY, "%s: BVH traversal stack overflow", where);
     if (e & ERR_BARRIER) return set_err(c, TTIE_ERR_CUDA, "%s: PCG grid barrier timed out", where);
+    if (e & ERR_CHECK) {
+        CK(cudaMemcpyAsync(c.hs, c.ds, sizeof(DevScalars), cudaMemcpyDeviceToHost, c.stream), where);
+        CK(cudaStreamSynchronize(c.stream), where);
+        return set_err(c, TTIE_ERR_CAPACITY, "%s: bounds check %d failed (value %lld)", where, c.hs->check_code,
+                       c.hs->check_value);
+    }
     return TTIE_OK;
 }
 

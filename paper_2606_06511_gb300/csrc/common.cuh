@@ -47,6 +47,7 @@ enum ErrBits : int {
     ERR_STACK = 4,          // traversal stack overflow
     ERR_DEFER = 8,          // exact-resolve list overflow
     ERR_BARRIER = 16,       // a grid barrier wait ran out of its iteration limit
+    ERR_CHECK = 32,         // a bounds check of a TTIE_CHECKS build failed (see check_code)
 };
 
 struct DevScalars {
@@ -68,9 +69,10 @@ struct DevScalars {
     double red[8];                         // PCG scalars
     int pcg_done;
     int pcg_iters;
-    unsigned int bar_count;                // grid barrier of the persistent PCG kernel: root
-    unsigned int bar_gen;                  // counter and generation; group counters below,
-    unsigned int bar_group[16][32];        // one 128-byte line each
+    int check_code;                        // first failed bounds check (TTIE_CHECKS builds)
+    long long check_value;                 // the offending index
+    unsigned int bar_count;                // arrivals at the PCG kernels' grid all-reduce
+    unsigned int bar_gen;                  // its generation (bumped on release)
 };
 
 // ------------------------------------------------------------------ buffers
@@ -126,12 +128,30 @@ struct Ctx {
 };
 
 // Every kernel of the library is launched through this helper on the context's
-// stream, which also counts the launches.
+// stream, which also counts the launches.  A TTIE_CHECKS build also synchronises after
+// every launch and reports the kernel's signature when it failed.
 template <typename... KArgs, typename... Args>
 inline void launch(Ctx &c, void (*kernel)(KArgs...), dim3 grid, dim3 block, Args &&...args) {
     ++c.n_launch;
     kernel<<<grid, block, 0, c.stream>>>(static_cast<KArgs>(args)...);
+#ifdef TTIE_CHECKS
+    cudaError_t e = cudaStreamSynchronize(c.stream);
+    if (e != cudaSuccess) fprintf(stderr, "TTIE_CHECKS: launch %llu failed (%s) in %s\n", c.n_launch, cudaGetErrorString(e), __PRETTY_FUNCTION__);
+#endif
 }
+
+// Bounds checks of TTIE_CHECKS builds: record the first failure and let the caller skip the
+// access.  In other builds they compile to nothing.
+#ifdef TTIE_CHECKS
+__device__ __forceinline__ bool ttie_check_fail(DevScalars *ds, int code, long long v) {
+    if (atomicCAS(&ds->check_code, 0, code) == 0) ds->check_value = v;
+    atomicOr(&ds->err, ERR_CHECK);
+    return true;
+}
+#define TTIE_BAD(ds, cond, code, v) (!(cond) && ttie_check_fail((ds), (code), (long long)(v)))
+#else
+#define TTIE_BAD(ds, cond, code, v) false
+#endif
 
 // ------------------------------------------------------------------ launch helpers
 constexpr int kNumSMs = 152;

@@ -25,10 +25,12 @@ __device__ __forceinline__ T warp_inclusive_scan(T v) {
     return v;
 }
 
-// Exclusive block scan of one value per thread; returns the block total in *total.
+// Exclusive block scan of one value per thread (up to 32 warps); returns the block total
+// in *total.
 template <typename T>
 __device__ __forceinline__ T block_exclusive_scan(T v, T *total) {
     __shared__ T warp_tot[32];
+    __shared__ T block_tot;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
     T inc = warp_inclusive_scan(v);
     if (lane == 31) warp_tot[w] = inc;
@@ -37,11 +39,11 @@ __device__ __forceinline__ T block_exclusive_scan(T v, T *total) {
         T t = lane < nw ? warp_tot[lane] : T(0);
         T ti = warp_inclusive_scan(t);
         if (lane < nw) warp_tot[lane] = ti - t;
-        if (lane == nw - 1) warp_tot[31] = ti;
+        if (lane == nw - 1) block_tot = ti;
     }
     __syncthreads();
     T res = warp_tot[w] + inc - v;
-    *total = warp_tot[31];
+    *total = block_tot;
     __syncthreads();
     return res;
 }
