@@ -75,45 +75,56 @@ def oracle_step(sub):
 
 
 class Clocks:
-    """nvidia-smi samples during the timed region."""
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    """nvidia-smi samples (every 50 ms) kept only inside the timed window."""
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, index):
         self.index = index
         self.proc = None
+        self.t0 = self.t1 = None
 
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
 
+    def mark_begin(self):
+        self.t0 = time.time()
+
+    def mark_end(self):
+        self.t1 = time.time()
+
     def stop(self):
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.1)
         self.proc.terminate()
         out, _ = self.proc.communicate(timeout=10)
-        sm, mx, reasons = [], None, set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        import datetime
+        rows = []
         for line in out.strip().splitlines():
             f = [v.strip() for v in line.split(",")]
-            if len(f) < 9:
+            if len(f) < 10:
                 continue
             try:
-                sm.append(float(f[1]))
-                mx = float(f[2])
+                ts = datetime.datetime.strptime(f[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                rows.append((ts, float(f[2]), float(f[3]), f[6:10]))
             except ValueError:
                 continue
-            for n, v in zip(names, f[5:9]):
-                if v.lower().startswith("active"):
-                    reasons.add(n)
-        sm.sort()
-        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
-                "samples": len(sm)}
+        inside = [r for r in rows if self.t0 is not None and self.t0 <= r[0] <= self.t1]
+        if not inside and rows and self.t0 is not None:   # window shorter than the sampling period
+            mid = 0.5 * (self.t0 + self.t1)
+            inside = [min(rows, key=lambda r: abs(r[0] - mid))]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in inside for n, v in zip(names, r[3]) if v.lower().startswith("active")})
+        sm = sorted(r[1] for r in inside)
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": inside[0][2] if inside else None,
+                "reasons": reasons, "samples": len(inside)}
 
 
 def measured_peaks():
@@ -168,7 +179,7 @@ def cpu_baseline(m, seconds_target=15.0):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=60)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="cloth256")
@@ -209,12 +220,13 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
+    clocks = Clocks(local)
+    clocks.start()
     for _ in range(args.warmup):
         x.copy_(x0)
         info = ctx.newton_step(x)
     barrier()
-    clocks = Clocks(local)
-    clocks.start()
+    clocks.mark_begin()
     launches0 = ctx.get_launch_count()
     total_ms, pairs, active = 0.0, 0, 0
     stage = {"build": 0.0, "eval": 0.0, "assemble": 0.0, "pcg": 0.0, "line_search": 0.0}
@@ -238,6 +250,7 @@ def main():
         infos.append(info)
     launches = ctx.get_launch_count() - launches0
     barrier()
+    clocks.mark_end()
     clk = clocks.stop()
     t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
     p = torch.tensor([float(pairs)], dtype=torch.float64, device="cuda")
@@ -264,18 +277,29 @@ def main():
             e2e_pairs += info["n_candidates"]
     e2e_bytes = x0.numel() * x0.element_size()
 
-    # roofline of the dominant kernel: the narrow-phase classification, 104 algorithmic bytes
-    # per candidate (pair ids 8 B + 2 x (indices 12 B + coordinates 36 B)); see the design doc
+    # Rooflines (algorithmic bytes per launch / CUDA-event duration of that launch):
+    # the dominant kernel is the persistent PCG: per iteration the block-CSR matrix
+    # (36 B value + 4 B column per 3x3 block) and 160 B of vector traffic per row
+    # (z read/write, p, q, x, r updates, inverse diagonal block, row offset);
+    # the pair kernel is the narrow-phase classification, 104 B per candidate
+    # (pair ids 8 B + 2 x (indices 12 B + coordinates 36 B)).
     peaks = measured_peaks()
     hbm = peaks.get("hbm_gbs")
+    peak = hbm if hbm else 6800.0
+    last = infos[-1]
+    pcg_ms = kern["pcg"] / args.steps
+    pcg_bytes = last["pcg_iters"] * (40.0 * last["nnzb"] + 160.0 * last["n_rows"])
+    pcg_ach = pcg_bytes / (pcg_ms * 1e-3) / 1e9 if pcg_ms > 0 else None
+    roofline = {"kernel": "k_pcg_resident", "bound": "hbm", "achieved": pcg_ach, "peak": peak, "unit": "GB/s",
+                "peak_source": "measured" if hbm else "fallback", "frac": pcg_ach / peak if pcg_ach else None,
+                "traffic": None, "ms_per_launch": pcg_ms, "algorithmic_bytes_per_launch": pcg_bytes,
+                "share_of_step": pcg_ms / (total_ms / args.steps)}
     k_ms = kern["classify"] / args.steps
-    n_cand = infos[-1]["n_candidates"]
-    achieved = 104.0 * n_cand / (k_ms * 1e-3) / 1e9 if k_ms > 0 else None
-    roofline = {"kernel": "k_classify", "bound": "hbm", "achieved": achieved,
-                "peak": hbm if hbm else 6800.0, "unit": "GB/s",
-                "peak_source": "measured" if hbm else "fallback",
-                "frac": (achieved / (hbm if hbm else 6800.0)) if achieved else None,
-                "traffic": None, "ms_per_launch": k_ms}
+    n_cand = last["n_candidates"]
+    cl_ach = 104.0 * n_cand / (k_ms * 1e-3) / 1e9 if k_ms > 0 else None
+    roofline_pairs = {"kernel": "k_classify", "bound": "hbm", "achieved": cl_ach, "peak": peak, "unit": "GB/s",
+                      "peak_source": "measured" if hbm else "fallback", "frac": cl_ach / peak if cl_ach else None,
+                      "traffic": None, "ms_per_launch": k_ms, "algorithmic_bytes_per_launch": 104.0 * n_cand}
 
     solve = None
     if not args.no_solve and rank == 0:
@@ -293,7 +317,6 @@ def main():
         cpu = cpu_baseline(m)
 
     if rank == 0:
-        last = infos[-1]
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -309,6 +332,7 @@ def main():
             "stage_ms_per_step": {k: v / args.steps for k, v in stage.items()},
             "active_pairs_per_s": active / (total_ms / 1e3),
             "roofline": roofline,
+            "roofline_pair_eval": roofline_pairs,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_pairs / (e2e_ms / 1e3) if e2e_ms > 0 else None, "unit": UNIT,
                     "h2d_bytes_per_step": e2e_bytes, "d2h_bytes_per_step": e2e_bytes},

@@ -1,0 +1,106 @@
+"""Parity at the benchmark's size and launch configuration: the 256x256 crossing cloth
+(130,050 triangles), default parameters.
+
+The oracle cannot enumerate all pairs at this size, so it checks samples it can compute
+one by one (candidate rows of sampled triangles, exact decisions and values of sampled
+pairs) and properties that hold at any size (structure and symmetry of the assembled
+system after several Newton steps, determinism).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import ttie_inputs as ti
+from _cases import fp32_tolerance, pair_set
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def setup():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2606_06511_gb300 import ttie
+    m = ti.cloth(256, seed=2).as_f32()
+    x = torch.tensor(m.x, dtype=torch.float32, device="cuda")
+    tri = torch.tensor(m.tri, dtype=torch.int32, device="cuda")
+    ctx = ttie.Context()
+    return ttie, m, x, tri, ctx
+
+
+def _sample_checks(ttie, m, x, ctx, rng):
+    """Candidate rows, exact decisions and values on samples at positions x."""
+    xn = x.double().cpu().numpy()
+    ctx.build_bvh(x, torch.tensor(m.tri, dtype=torch.int32, device="cuda"))
+    cand = ctx.get_candidates().cpu().numpy().astype(np.int64)
+    E, n_act = ctx.eval_pairs(x, ttie.EVAL_E | ttie.EVAL_H)
+    ap, tc, dtc = ctx.get_active()
+    ap = ap.cpu().numpy().astype(np.int64)
+    active = pair_set(ap)
+    # candidate rows of sampled triangles: bit-exact against brute force
+    for i in rng.choice(m.F, 24, replace=False):
+        got = np.sort(np.concatenate([cand[cand[:, 0] == i, 1], cand[cand[:, 1] == i, 0]]))
+        assert np.array_equal(got, O.partners_of(xn, m.tri, int(i))), i
+    # exact decision on sampled candidates, and every GPU-active pair among them
+    pick = cand[rng.choice(len(cand), min(4000, len(cand)), replace=False)]
+    pick = np.concatenate([pick, ap[rng.choice(len(ap), min(1000, len(ap)), replace=False)]])
+    ev = O.evaluate(xn, m.tri, pick)
+    gpu_flag = np.array([tuple(p) in active for p in pick.tolist()])
+    assert np.array_equal(gpu_flag, ev.active)
+    # T and gradient on the sampled active pairs
+    idx = {tuple(p): k for k, p in enumerate(ap.tolist())}
+    k = np.array([idx[tuple(p)] for p in pick[ev.active].tolist()])
+    tcs = tc.double().cpu().numpy()[k]
+    dts = dtc.double().cpu().numpy()[k]
+    T_gpu = (tcs[:, 0] * tcs[:, 1]) ** 2
+    T_or = ev.T[ev.active]
+    g_or = O.gradient(ev)[ev.active]
+    v = np.concatenate([xn[m.tri[pick[ev.active, 0]]], xn[m.tri[pick[ev.active, 1]]]], axis=1)
+    L = (v.max(1) - v.min(1)).max(1)
+    assert (np.abs(T_gpu - T_or) <= fp32_tolerance(T_or, g_or, L)).all()
+    return E, n_act
+
+
+def test_fullsize_samples_at_start(setup):
+    ttie, m, x, tri, ctx = setup
+    E, n = _sample_checks(ttie, m, x.clone(), ctx, np.random.default_rng(0))
+    assert n > 10000 and np.isfinite(E)
+
+
+def test_fullsize_after_newton_steps(setup):
+    ttie, m, x0, tri, ctx = setup
+    x = x0.clone()
+    ctx.build_bvh(x, tri)
+    for _ in range(4):
+        info = ctx.newton_step(x)
+        assert np.isfinite(info["energy"]) and info["grad_dot_dir"] < 0
+    # more than 2^21 block keys at this state: the assembly's sort and scans span > 1024 tiles
+    _sample_checks(ttie, m, x, ctx, np.random.default_rng(1))
+    ctx.eval_pairs(x, ttie.EVAL_E | ttie.EVAL_H)
+    bsr = ctx.assemble()
+    rp = bsr.row_ptr.cpu().numpy().astype(np.int64)
+    ci = bsr.col_idx.cpu().numpy().astype(np.int64)
+    val = bsr.val.double().cpu().numpy()
+    n, nnzb = len(rp) - 1, len(ci)
+    assert rp[0] == 0 and rp[-1] == nnzb and np.all(np.diff(rp) >= 1)
+    rows = np.repeat(np.arange(n), np.diff(rp))
+    assert np.all((ci >= 0) & (ci < n))
+    assert np.all(np.diff(ci)[np.diff(rows) == 0] > 0)            # sorted, unique per row
+    assert np.all(ci[rp[:-1]] <= np.arange(n)) and np.all(ci[rp[1:] - 1] >= np.arange(n))
+    key = rows * n + ci
+    tkey = ci * n + rows
+    order = np.argsort(key)
+    pos = np.searchsorted(key[order], tkey)
+    assert np.array_equal(key[order][pos], tkey)                     # symmetric pattern
+    tv = val[order][pos]
+    scale = np.abs(val).max()
+    assert np.allclose(val, np.transpose(tv, (0, 2, 1)), atol=1e-5 * scale)   # symmetric values
+    diag = val[rows == ci]
+    w = np.linalg.eigvalsh(0.5 * (diag + np.transpose(diag, (0, 2, 1))))
+    assert (w >= -1e-5 * scale).all()
+    # determinism of the whole assembly
+    ctx.eval_pairs(x, ttie.EVAL_E | ttie.EVAL_H)
+    bsr2 = ctx.assemble()
+    assert torch.equal(bsr2.val, bsr.val) and torch.equal(bsr2.col_idx, bsr.col_idx)
+    assert torch.equal(bsr2.row_ptr, bsr.row_ptr)
