@@ -127,6 +127,19 @@ class Clocks:
                 "reasons": reasons, "samples": len(inside)}
 
 
+def aggregate(total_ms, pairs, world, device):
+    """Whole-job figures over N replica ranks: the slowest rank's time (MAX) and the pairs all
+    ranks processed (SUM).  Returns (seconds, pairs)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+    p = torch.tensor([float(pairs)], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(p, op=dist.ReduceOp.SUM)
+    return t.item() / 1e3, p.item()
+
+
 def measured_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -252,13 +265,8 @@ def main():
     barrier()
     clocks.mark_end()
     clk = clocks.stop()
-    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-    p = torch.tensor([float(pairs)], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dist.all_reduce(p, op=dist.ReduceOp.SUM)
-    total_s = t.item() / 1e3
-    value = p.item() / total_s
+    total_s, all_pairs = aggregate(total_ms, pairs, world, "cuda")
+    value = all_pairs / total_s
 
     # end to end through the public API with host buffers
     xh0 = x0.cpu().pin_memory()

@@ -358,6 +358,7 @@ template <typename T> struct PcgArgs {
     const T *bval;
     const T *dinv;
     T *x, *r, *z, *p, *q;
+    vec4_t<T> *z4;           // z mirrored as one 16/32-byte vector per row (resident kernel)
     double *partA, *partB;
     double rtol2;
     int max_it;
@@ -489,6 +490,23 @@ __global__ void __launch_bounds__(kPcgThreads) k_pcg_persistent(PcgArgs<T> a) {
 // reductions and decisions as k_pcg_persistent.
 constexpr int kResidentSmem = 200 * 1024;   // dynamic shared memory per block
 
+template <typename T> __device__ __forceinline__ vec4_t<T> ldcg4(const vec4_t<T> *p);
+template <> __device__ __forceinline__ float4 ldcg4<float>(const float4 *p) { return __ldcg(p); }
+template <> __device__ __forceinline__ dvec4 ldcg4<double>(const dvec4 *p) {
+    const double2 *q = reinterpret_cast<const double2 *>(p);
+    const double2 a = __ldcg(q), b = __ldcg(q + 1);
+    dvec4 r;
+    r.x = a.x; r.y = a.y; r.z = b.x; r.w = b.y;
+    return r;
+}
+
+template <typename T>
+__device__ __forceinline__ void block_times(const T *m, const vec4_t<T> &v, T &y0, T &y1, T &y2) {
+    y0 += m[0] * v.x + m[1] * v.y + m[2] * v.z;
+    y1 += m[3] * v.x + m[4] * v.y + m[5] * v.z;
+    y2 += m[6] * v.x + m[7] * v.y + m[8] * v.z;
+}
+
 template <typename T>
 __device__ __forceinline__ double resident_direction(const PcgArgs<T> &a, const int *srp, const T *sval,
                                                      const int *scol, bool cached, int b_begin, long long row0,
@@ -498,15 +516,25 @@ __device__ __forceinline__ double resident_direction(const PcgArgs<T> &a, const 
     double pq = 0.0;
     for (int lr = threadIdx.x / kLanesPerRow; lr < nrow; lr += kPcgThreads / kLanesPerRow) {
         T y0 = 0, y1 = 0, y2 = 0;
-        for (int b = srp[lr] + sub; b < srp[lr + 1]; b += kLanesPerRow) {
+        int b = srp[lr] + sub;
+        const int be = srp[lr + 1];
+        if (cached) {
+            // two blocks per step: both gathers in flight before either is used
+            for (; b + kLanesPerRow < be; b += 2 * kLanesPerRow) {
+                const int c0 = scol[b], c1 = scol[b + kLanesPerRow];
+                const vec4_t<T> v0 = ldcg4<T>(&a.z4[c0]), v1 = ldcg4<T>(&a.z4[c1]);
+                block_times(sval + (size_t)b * 9, v0, y0, y1, y2);
+                block_times(sval + (size_t)(b + kLanesPerRow) * 9, v1, y0, y1, y2);
+            }
+            if (b < be) block_times(sval + (size_t)b * 9, ldcg4<T>(&a.z4[scol[b]]), y0, y1, y2);
+            b = be;
+        }
+        for (; b < be; b += kLanesPerRow) {
             if (TTIE_BAD(a.ds, b >= 0 && (unsigned long long)(b_begin + b) < a.ds->nnzb, 41, b)) break;
-            const T *m = cached ? sval + (size_t)b * 9 : a.bval + (size_t)(b_begin + b) * 9;
-            const int c = cached ? scol[b] : a.col_idx[b_begin + b];
+            const T *m = a.bval + (size_t)(b_begin + b) * 9;
+            const int c = a.col_idx[b_begin + b];
             if (TTIE_BAD(a.ds, c >= 0 && (unsigned long long)c < a.ds->n_rows, 42, c)) break;
-            const T c0 = __ldcg(&a.z[c * 3]), c1 = __ldcg(&a.z[c * 3 + 1]), c2 = __ldcg(&a.z[c * 3 + 2]);
-            y0 += m[0] * c0 + m[1] * c1 + m[2] * c2;
-            y1 += m[3] * c0 + m[4] * c1 + m[5] * c2;
-            y2 += m[6] * c0 + m[7] * c1 + m[8] * c2;
+            block_times(m, ldcg4<T>(&a.z4[c]), y0, y1, y2);
         }
 #pragma unroll
         for (int o = kLanesPerRow / 2; o; o >>= 1) {
@@ -564,6 +592,15 @@ __global__ void __launch_bounds__(kPcgThreads) k_pcg_resident(PcgArgs<T> a, int 
         for (int i = threadIdx.x; i < nnz; i += blockDim.x) scol[i] = a.col_idx[b_begin + i];
     }
     __syncthreads();
+    for (int lr = threadIdx.x; lr < nrow; lr += blockDim.x) {   // publish z for the first product
+        vec4_t<T> z4;
+        z4.x = sz[lr * 3]; z4.y = sz[lr * 3 + 1]; z4.z = sz[lr * 3 + 2]; z4.w = T(0);
+        a.z4[row0 + lr] = z4;
+    }
+    {
+        double dummy[1] = {0.0};
+        if (!grid_allreduce<1>(dummy, a.partB, ds)) return;
+    }
     const T mu = (T)ds->mu;
     const double rr0 = ds->red[1];
     double rz = ds->red[0], rr = rr0;
@@ -585,14 +622,18 @@ __global__ void __launch_bounds__(kPcgThreads) k_pcg_resident(PcgArgs<T> a, int 
                 sr[lr * 3 + i] = rv[i];
             }
             const T *di = sdi + lr * 9;
+            T zv[3];
 #pragma unroll
             for (int i = 0; i < 3; ++i) {
                 const T zi = di[3 * i] * rv[0] + di[3 * i + 1] * rv[1] + di[3 * i + 2] * rv[2];
+                zv[i] = zi;
                 sz[lr * 3 + i] = zi;
-                a.z[(row0 + lr) * 3 + i] = zi;
                 v2[0] += (double)rv[i] * zi;
                 v2[1] += (double)rv[i] * rv[i];
             }
+            vec4_t<T> z4;
+            z4.x = zv[0]; z4.y = zv[1]; z4.z = zv[2]; z4.w = T(0);
+            a.z4[row0 + lr] = z4;
         }
         if (!grid_allreduce<2>(v2, a.partB, ds)) return;
         if (!ok) { ++it; break; }
@@ -769,6 +810,7 @@ cudaError_t pcg_solve(Ctx &c, const T *rhs, T *out, double rtol, int max_it) {
     TTIE_CUDA_TRY(ensure(c, c.pcg_z, (size_t)(nr > 0 ? nr : 1) * 3 * sizeof(T)));
     TTIE_CUDA_TRY(ensure(c, c.pcg_p, (size_t)(nr > 0 ? nr : 1) * 3 * sizeof(T)));
     TTIE_CUDA_TRY(ensure(c, c.pcg_q, (size_t)(nr > 0 ? nr : 1) * 3 * sizeof(T)));
+    TTIE_CUDA_TRY(ensure(c, c.pcg_z4, (size_t)(nr > 0 ? nr : 1) * sizeof(vec4_t<T>)));
     TTIE_CUDA_TRY(ensure(c, c.partials, (size_t)kNumSMs * 16 * 4 * sizeof(double)));
     double *part = (double *)c.partials.p;
     const unsigned g = grid_for(nr, kThreads, kNumSMs * 4);
@@ -787,6 +829,7 @@ cudaError_t pcg_solve(Ctx &c, const T *rhs, T *out, double rtol, int max_it) {
     args.z = (T *)c.pcg_z.p;
     args.p = (T *)c.pcg_p.p;
     args.q = (T *)c.pcg_q.p;
+    args.z4 = (vec4_t<T> *)c.pcg_z4.p;
     args.partA = part;
     args.partB = part + 2 * kNumSMs * 8;
     args.rtol2 = rtol * rtol;
@@ -880,6 +923,7 @@ cudaError_t pcg_run_raw(cudaStream_t stream, int num_sms, const int32_t *row_ptr
     args.z = z;
     args.p = p;
     args.q = q;
+    args.z4 = nullptr;   // only the block-resident kernel uses the vector mirror
     args.partA = partials;
     args.partB = partials + 2 * kNumSMs * 8;
     args.rtol2 = rtol * rtol;

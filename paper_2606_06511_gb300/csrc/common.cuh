@@ -91,7 +91,7 @@ cudaError_t ensure(Ctx &c, Buf &b, size_t bytes);   // grow-only, contents not k
     X(defer) X(active) X(fac) X(partials) X(vflag) X(vrow) X(row_vertex) X(bkey) X(bkey2)   \
     X(bval) X(bval2) X(bflag) X(run_start) X(row_ptr) X(col_idx) X(bsr_val) X(rhs)         \
     X(zfac) X(dinv) X(pcg_x) X(pcg_r) X(pcg_z) X(pcg_p) X(pcg_q) X(dir) X(xt) X(gtmp)      \
-    X(xsave) X(sweep_cand)
+    X(xsave) X(sweep_cand) X(pcg_z4)
 
 struct Ctx {
     ttie_params prm;
