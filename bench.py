@@ -26,6 +26,10 @@ sys.path.insert(0, ROOT)
 
 METRIC = "TTIE pair evals/s (E+grad+PSD Hess+assembly); seconds to intersection-free"
 UNIT = "pair evals/s"
+# dram__bytes_read.sum + dram__bytes_write.sum per launch, one ncu capture of the default
+# workload (256x256 crossing cloth, first Newton step) with the kernels as they are now;
+# reported only for that workload.
+NCU_TRAFFIC = {"cloth256": {"k_pcg_resident": 20293376, "k_classify": 8579072}}
 L2_FLUSH_BYTES = 256 << 20   # larger than the 129 MB L2
 
 
@@ -285,7 +289,7 @@ def main():
             e2e_pairs += info["n_candidates"]
     e2e_bytes = x0.numel() * x0.element_size()
 
-    # Rooflines (algorithmic bytes per launch / CUDA-event duration of that launch, DESIGN.md):
+    # Rooflines (algorithmic bytes per launch / CUDA-event duration of that launch):
     # the dominant kernel is the persistent PCG: per iteration the block-CSR matrix
     # (36 B value + 4 B column per 3x3 block) and 160 B of vector traffic per row
     # (z read/write, p, q, x, r updates, inverse diagonal block, row offset);
@@ -300,14 +304,14 @@ def main():
     pcg_ach = pcg_bytes / (pcg_ms * 1e-3) / 1e9 if pcg_ms > 0 else None
     roofline = {"kernel": "k_pcg_resident", "bound": "hbm", "achieved": pcg_ach, "peak": peak, "unit": "GB/s",
                 "peak_source": "measured" if hbm else "fallback", "frac": pcg_ach / peak if pcg_ach else None,
-                "traffic": None, "ms_per_launch": pcg_ms, "algorithmic_bytes_per_launch": pcg_bytes,
+                "traffic": NCU_TRAFFIC.get(args.workload, {}).get("k_pcg_resident"), "ms_per_launch": pcg_ms, "algorithmic_bytes_per_launch": pcg_bytes,
                 "share_of_step": pcg_ms / (total_ms / args.steps)}
     k_ms = kern["classify"] / args.steps
     n_cand = last["n_candidates"]
     cl_ach = 104.0 * n_cand / (k_ms * 1e-3) / 1e9 if k_ms > 0 else None
     roofline_pairs = {"kernel": "k_classify", "bound": "hbm", "achieved": cl_ach, "peak": peak, "unit": "GB/s",
                       "peak_source": "measured" if hbm else "fallback", "frac": cl_ach / peak if cl_ach else None,
-                      "traffic": None, "ms_per_launch": k_ms, "algorithmic_bytes_per_launch": 104.0 * n_cand}
+                      "traffic": NCU_TRAFFIC.get(args.workload, {}).get("k_classify"), "ms_per_launch": k_ms, "algorithmic_bytes_per_launch": 104.0 * n_cand}
 
     solve = None
     if not args.no_solve and rank == 0:

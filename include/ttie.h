@@ -66,8 +66,11 @@ typedef enum {
 
 /* PSD projection of the Eq. 4 Hessian (eigen-analysis of §1.1).
  * PER_PART:   parts 1 and 2 kept, part 3 keeps its non-negative eigenpair.
- * DROP_CROSS: parts 1 and 2 only.                                            */
-typedef enum { TTIE_PSD_PER_PART = 0, TTIE_PSD_DROP_CROSS = 1 } ttie_psd_mode;
+ * DROP_CROSS: parts 1 and 2 only.
+ * WHOLE:      the sum of the three parts with its negative eigenvalue set to
+ *             zero (rank one: Eq. 4 has one positive and one negative
+ *             eigenvalue on every intersecting pair).                       */
+typedef enum { TTIE_PSD_PER_PART = 0, TTIE_PSD_DROP_CROSS = 1, TTIE_PSD_WHOLE = 2 } ttie_psd_mode;
 
 typedef struct {
     int precision;        /* ttie_precision                                        */
@@ -175,6 +178,21 @@ ttie_status ttie_copy_bsr(ttie_ctx *ctx, int32_t *d_row_ptr, int32_t *d_col_idx,
  */
 ttie_status ttie_pcg(ttie_ctx *ctx, const void *d_rhs, void *d_out, double rtol, int max_it,
                      int *iters, double *rel_residual);
+
+/*
+ * Hessian-vector product of the energy at the positions of the last ttie_eval_pairs (which
+ * must have included TTIE_EVAL_G or TTIE_EVAL_H), restricted to its intersecting pairs:
+ *   exact = 1: the full Hessian of sum T (Eq. 2) applied to v, by forward-mode
+ *              differentiation of the per-pair gradient (Eq. 3) along v (dual numbers, the
+ *              way Appendix A obtains derivatives); d_x must be the evaluated positions,
+ *              V x x_stride as given to ttie_build_bvh (borrowed for the call).
+ *   exact = 0: the PSD Hessian H+ (Eq. 4 projected per §1.1) as assembled by ttie_assemble
+ *              (assembled here if needed); d_x is ignored.
+ * d_v, d_out: V x 3 device arrays of the positions' dtype; rows of vertices in no
+ * intersecting pair are zero.  Per-vertex sums run in a fixed order (deterministic).
+ * Errors: STATE, INVALID, NONFINITE, CUDA.
+ */
+ttie_status ttie_hvp(ttie_ctx *ctx, const void *d_x, const void *d_v, void *d_out, int exact);
 
 typedef struct {
     int64_t n_candidates;        /* candidate pairs at x                              */

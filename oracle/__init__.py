@@ -15,6 +15,9 @@ Parity status of each function:
                              near-degenerate inputs
   gradient / hessian_*       pinned: FD of T, closed-form eigenvalues (§1.1),
                              sympy derivation of the dropped Eq. 4 terms
+  hessian_vector_product     pinned: Euler's identity H x = 3 g (T has degree 4),
+                             H (w x x) = w x g (rotation invariance), H 1 = 0
+                             (translation), v.Hv = second difference of E
   assemble / newton_solve    pinned: dense recomputation, direct solve
                              residual; the Newton trajectory itself is
                              parity-unpinned (only the certified end state is
@@ -23,6 +26,7 @@ Parity status of each function:
 from .ttie_oracle import (build_oracle, candidate_pairs, partners_of, evaluate,  # noqa: F401
                           eval_pairs_f64, filtered_sides, gradient, hessian_parts,
                           hessian_inexact, hessian_psd, clamp_psd, assemble, pair_dofs,
-                          blocks_to_dense, newton_direction, newton_solve, certify, energy,
+                          blocks_to_dense, hessian_vector_product, pair_hessian_vector,
+                          newton_direction, newton_solve, certify, energy,
                           NewtonParams, PairEval)
 from . import exact  # noqa: F401

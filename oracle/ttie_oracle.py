@@ -14,6 +14,10 @@ Steps and the passages they follow:
                     (``exact.py``); T (Eq. 2), gradient (Eq. 3), inexact
                     Hessian (Eq. 4), eigen-analysis projection (§1.1).
   assemble          sum of per-pair 18-vectors / 18x18 blocks over vertices.
+  hessian_vector_product  exact Hessian of T (no Eq. 4 terms dropped) times a
+                    direction: derivative of the Eq. 3 gradient along it,
+                    fourth-order central differences at fixed pairs, the
+                    step refined per pair until it lies in one smooth piece.
   newton_solve      inexact Newton with backtracking line search until no pair
                     intersects (abstract, §1.2 "GPU-based inexact Newton").
 
@@ -224,6 +228,68 @@ def hessian_psd(ev: PairEval, mode: str = "per_part") -> np.ndarray:
     else:
         raise ValueError(mode)
     return np.where(ev.active[:, None, None], H, 0.0)
+
+
+def pair_hessian_vector(x, tri, pairs, v, tc_scale: float = 1.0, h: float | None = None,
+                        rtol: float = 1e-7, max_halvings: int = 24) -> np.ndarray:
+    """Exact Hessian of T times v, per listed pair ([P,18]): the derivative of the Eq. 3 pair
+    gradient 2ab(b da + a db) along v, taken at fixed pairs by the fourth-order central
+    difference D(h) = (8(g(h) - g(-h)) - (g(2h) - g(-2h))) / 12h.  This includes the second
+    derivatives of t_c that Eq. 4 drops.
+
+    The pair gradient is smooth only piecewise: the min/max selections of the interval end
+    points and the cut case switch where two values tie.  A step that straddles such a switch
+    gives a meaningless quotient, so each pair's step is halved until D(h) and D(h/2) agree to
+    rtol (relative to the pair's largest entry, floored at 1e-3 of the largest entry over all
+    pairs) plus their rounding, 1e-13 |g| / h; D(h/2) is returned.  h starts at 1e-4 of the mean edge length over max |v|."""
+    x = np.asarray(x, np.float64)
+    v = np.asarray(v, np.float64).reshape(x.shape)
+    pairs = np.asarray(pairs, np.int64).reshape(-1, 2)
+    if h is None:
+        e = x[tri[:, [1, 2, 0]]] - x[tri]
+        vmax = np.abs(v).max()
+        h = 1e-4 * float(np.linalg.norm(e, axis=-1).mean()) / (vmax if vmax > 0 else 1.0)
+
+    def g(sub, t):
+        tc, dtc, _, _ = eval_pairs_f64(x + t * v, tri, sub, tc_scale)
+        a, b = tc[:, 0], tc[:, 1]
+        return (2 * a * b)[:, None] * (b[:, None] * dtc[:, 0] + a[:, None] * dtc[:, 1])
+
+    def D(sub, step):
+        return (8 * (g(sub, step) - g(sub, -step)) - (g(sub, 2 * step) - g(sub, -2 * step))) / (12 * step)
+
+    out = np.zeros((len(pairs), 18))
+    if len(pairs) == 0:
+        return out
+    g0 = np.abs(g(pairs, 0.0)).max(1)       # rounding of D(h) is about eps * |g| / h
+    todo = np.arange(len(pairs))
+    prev = D(pairs, h)
+    floor = None
+    for _ in range(max_halvings):
+        h *= 0.5
+        cur = D(pairs[todo], h)
+        if floor is None:
+            floor = 1e-3 * np.abs(cur).max()
+        scale = np.maximum(np.abs(cur).max(1), floor)
+        ok = np.abs(cur - prev).max(1) <= rtol * scale + 1e-13 * g0[todo] / h
+        out[todo[ok]] = cur[ok]
+        todo, prev = todo[~ok], cur[~ok]
+        if len(todo) == 0:
+            return out
+    raise ArithmeticError("pair_hessian_vector: no converged step for pairs %s" % pairs[todo[:8]].tolist())
+
+
+def hessian_vector_product(x, tri, ev: PairEval, v, tc_scale: float = 1.0, h: float | None = None) -> np.ndarray:
+    """[V,3]: sum over the intersecting pairs of ev of the exact pair Hessian times v."""
+    act = np.nonzero(ev.active)[0]
+    out = np.zeros((np.asarray(x).shape[0], 3))
+    if len(act) == 0:
+        return out
+    hv = pair_hessian_vector(x, tri, ev.pairs[act], v, tc_scale, h)
+    vid = pair_dofs(tri, ev.pairs[act])
+    for r in range(6):
+        np.add.at(out, vid[:, r], hv[:, 3 * r:3 * r + 3])
+    return out
 
 
 # ------------------------------------------------------------------ assembly

@@ -8,7 +8,10 @@
 // only 4ab(u.v - |u||v|) >= 0 survives the projection.  So
 //   H+ = z1 z1' + z2 z2' + z3 z3',  z1 = sqrt2 |b| u,  z2 = sqrt2 |a| v,
 //   z3 = sqrt(2 |ab| |u||v|) (u^ - v^)          (z3 = 0 for DROP_CROSS)
-// and no 18x18 eigen-solve is needed.
+// and no 18x18 eigen-solve is needed.  WHOLE projects the sum instead: H = G M G' with
+// G = [u v] and M = [[2b^2, 4ab], [4ab, 2a^2]] (det M = -12 a^2 b^2 < 0), so with G = QR
+// (Gram-Schmidt) the non-zero spectrum of H is that of the 2x2 S = R M R', which has one
+// positive eigenvalue; H+ = z1 z1' with z1 = sqrt(lambda+) Q e+.
 //
 // Assembly: 36 vertex-block keys (row, col) per pair, a stable radix sort, and
 // one thread per distinct key summing its run in sorted order, so both the
@@ -89,6 +92,42 @@ __global__ void k_row_vertex(const uint32_t *__restrict__ vflag, const unsigned 
     if (blockIdx.x == 0 && threadIdx.x == 0) ds->n_rows = vrow[V];
 }
 
+// Rank-one projection of the whole Eq. 4 Hessian: z = alpha u + beta v.
+template <typename T>
+__device__ __forceinline__ void whole_projection(T a, T b, T uu, T uv, T vv, T &alpha, T &beta) {
+    alpha = beta = T(0);
+    const T m11 = T(2) * b * b, m12 = T(4) * a * b, m22 = T(2) * a * a;
+    if (!(uu > T(0))) {                       // G = [0 v]: H = 2a^2 vv'
+        if (vv > T(0)) beta = sqrt(m22);
+        return;
+    }
+    const T nu = sqrt(uu);
+    const T r12 = uv / nu;                    // R = [[|u|, u.v/|u|], [0, |w|]], w = v - (v.q1) q1
+    const T w2 = vv - r12 * r12;
+    const T r22 = w2 > T(0) ? sqrt(w2) : T(0);
+    // S = R M R'
+    const T s11 = nu * nu * m11 + T(2) * nu * r12 * m12 + r12 * r12 * m22;
+    const T s12 = r22 * (nu * m12 + r12 * m22);
+    const T s22 = r22 * r22 * m22;
+    const T hm = T(0.5) * (s11 + s22), hd = T(0.5) * (s11 - s22);
+    const T lam = hm + sqrt(hd * hd + s12 * s12);
+    if (!(lam > T(0))) return;
+    // eigenvector of the larger eigenvalue: the better conditioned of (s12, lam - s11), (lam - s22, s12)
+    T e1 = s12, e2 = lam - s11;
+    const T f1 = lam - s22, f2 = s12;
+    if (f1 * f1 + f2 * f2 > e1 * e1 + e2 * e2) { e1 = f1; e2 = f2; }
+    const T en = sqrt(e1 * e1 + e2 * e2);
+    if (!(en > T(0))) { alpha = sqrt(lam) / nu; return; }
+    const T c = sqrt(lam) / en;
+    // Q e = e1 u/|u| + e2 (v - (u.v/|u|^2) u)/|w|
+    if (r22 > T(0)) {
+        beta = c * e2 / r22;
+        alpha = c * e1 / nu - beta * uv / uu;
+    } else {
+        alpha = c * e1 / nu;
+    }
+}
+
 // PSD factors z1, z2, z3 and the gradient of each intersecting pair; trace of H+.
 template <typename T>
 __global__ void k_factors(const T *__restrict__ fac, int psd_mode, T *__restrict__ z, double *partials, DevScalars *ds) {
@@ -98,23 +137,30 @@ __global__ void k_factors(const T *__restrict__ fac, int psd_mode, T *__restrict
          k += (unsigned long long)gridDim.x * blockDim.x) {
         const T *r = fac + k * kFacStride;
         const T a = r[0], b = r[1];
-        T uu = 0, vv = 0;
+        T uu = 0, vv = 0, uv = 0;
 #pragma unroll
-        for (int i = 0; i < 18; ++i) { uu += r[2 + i] * r[2 + i]; vv += r[20 + i] * r[20 + i]; }
+        for (int i = 0; i < 18; ++i) {
+            uu += r[2 + i] * r[2 + i];
+            vv += r[20 + i] * r[20 + i];
+            uv += r[2 + i] * r[20 + i];
+        }
         const T nu = sqrt(uu), nv = sqrt(vv);
-        const T c1 = sqrt(T(2)) * fabs(b), c2 = sqrt(T(2)) * fabs(a);
-        T c3 = T(0), iu = T(0), iv = T(0);
+        T c1 = sqrt(T(2)) * fabs(b), c2 = sqrt(T(2)) * fabs(a);
+        T c3 = T(0), iu = T(0), iv = T(0), wa = T(0), wb = T(0);
         if (psd_mode == TTIE_PSD_PER_PART && nu > T(0) && nv > T(0)) {
             c3 = sqrt(T(2) * fabs(a * b) * nu * nv);
             iu = T(1) / nu;
             iv = T(1) / nv;
+        } else if (psd_mode == TTIE_PSD_WHOLE) {
+            whole_projection(a, b, uu, uv, vv, wa, wb);
+            c1 = c2 = T(0);
         }
         T *o = z + k * kZStride;
         double t = 0.0;
 #pragma unroll
         for (int i = 0; i < 18; ++i) {
             const T u = r[2 + i], v = r[20 + i];
-            const T z1 = c1 * u, z2 = c2 * v, z3 = c3 * (u * iu - v * iv);
+            const T z1 = c1 * u + (wa * u + wb * v), z2 = c2 * v, z3 = c3 * (u * iu - v * iv);
             o[i] = z1;
             o[18 + i] = z2;
             o[36 + i] = z3;
@@ -718,6 +764,53 @@ __global__ void k_check_runs(const uint32_t *run_start, const unsigned long long
 }
 #endif
 
+// Sum of per-pair 18-vectors per vertex, over the diagonal block runs of the last
+// assembly (each lists every (pair, vertex) of that vertex once, in sorted order).
+template <typename T>
+__global__ void k_vertex_sums(const unsigned long long *__restrict__ key, const uint32_t *__restrict__ val,
+                              const uint32_t *__restrict__ run_start, const T *__restrict__ h,
+                              const int32_t *__restrict__ row_vertex, const DevScalars *ds, T *__restrict__ out) {
+    const unsigned long long nb = ds->nnzb, nr = ds->n_rows;
+    for (unsigned long long bi = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; bi < nb;
+         bi += (unsigned long long)gridDim.x * blockDim.x) {
+        const uint32_t s = run_start[bi], e = run_start[bi + 1];
+        const unsigned long long kk = key[s];
+        const unsigned long long row = kk / nr, col = kk - row * nr;
+        if (row != col) continue;
+        T g0 = 0, g1 = 0, g2 = 0;
+        for (uint32_t i = s; i < e; ++i) {
+            const uint32_t v = val[i];
+            const uint32_t pk = v / 36, r = (v - pk * 36) / 6;
+            const T *hp = h + (size_t)pk * 18 + 3 * r;
+            g0 += hp[0]; g1 += hp[1]; g2 += hp[2];
+        }
+        const int64_t vx = row_vertex[row];
+        out[vx * 3] = g0; out[vx * 3 + 1] = g1; out[vx * 3 + 2] = g2;
+    }
+}
+
+// out (V x 3) = H+ v on the assembled rows (vertices of intersecting pairs); other rows 0.
+template <typename T>
+__global__ void k_bsr_matvec(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col_idx,
+                             const T *__restrict__ bval, const int32_t *__restrict__ row_vertex,
+                             const T *__restrict__ v, const DevScalars *ds, T *__restrict__ out) {
+    const unsigned long long nr = ds->n_rows;
+    for (unsigned long long row = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; row < nr;
+         row += (unsigned long long)gridDim.x * blockDim.x) {
+        T y0 = 0, y1 = 0, y2 = 0;
+        for (int b = row_ptr[row]; b < row_ptr[row + 1]; ++b) {
+            const T *m = bval + (size_t)b * 9;
+            const int64_t cv = row_vertex[col_idx[b]];
+            const T c0 = v[cv * 3], c1 = v[cv * 3 + 1], c2 = v[cv * 3 + 2];
+            y0 += m[0] * c0 + m[1] * c1 + m[2] * c2;
+            y1 += m[3] * c0 + m[4] * c1 + m[5] * c2;
+            y2 += m[6] * c0 + m[7] * c1 + m[8] * c2;
+        }
+        const int64_t rv = row_vertex[row];
+        out[rv * 3] = y0; out[rv * 3 + 1] = y1; out[rv * 3 + 2] = y2;
+    }
+}
+
 int bits_for(unsigned long long v) {
     int b = 0;
     while (b < 64 && (v >> b) != 0ull) ++b;
@@ -936,5 +1029,25 @@ cudaError_t pcg_run_raw(cudaStream_t stream, int num_sms, const int32_t *row_ptr
     return cudaLaunchCooperativeKernel((const void *)k_pcg_persistent<float>, dim3((unsigned)blocks),
                                        dim3(kPcgThreads), kargs, 0, stream);
 }
+
+template <typename T> cudaError_t vertex_sums(Ctx &c, const T *h, T *out) {
+    TTIE_CUDA_TRY(cudaMemsetAsync(out, 0, (size_t)c.V * 3 * sizeof(T), c.stream));
+    if (c.nnzb == 0) return cudaSuccess;
+    launch(c, k_vertex_sums<T>, dim3(grid_for(c.nnzb, kThreads)), dim3(kThreads), (const unsigned long long *)c.bkey.p,
+           (const uint32_t *)c.bval.p, (const uint32_t *)c.run_start.p, h, (const int32_t *)c.row_vertex.p, c.ds, out);
+    return cudaGetLastError();
+}
+template cudaError_t vertex_sums<float>(Ctx &, const float *, float *);
+template cudaError_t vertex_sums<double>(Ctx &, const double *, double *);
+
+template <typename T> cudaError_t bsr_matvec(Ctx &c, const T *v, T *out) {
+    TTIE_CUDA_TRY(cudaMemsetAsync(out, 0, (size_t)c.V * 3 * sizeof(T), c.stream));
+    if (c.n_rows == 0) return cudaSuccess;
+    launch(c, k_bsr_matvec<T>, dim3(grid_for(c.n_rows, kThreads)), dim3(kThreads), (const int32_t *)c.row_ptr.p,
+           (const int32_t *)c.col_idx.p, (const T *)c.bsr_val.p, (const int32_t *)c.row_vertex.p, v, c.ds, out);
+    return cudaGetLastError();
+}
+template cudaError_t bsr_matvec<float>(Ctx &, const float *, float *);
+template cudaError_t bsr_matvec<double>(Ctx &, const double *, double *);
 
 }  // namespace ttie

@@ -103,7 +103,7 @@ static ttie_status check_params(Ctx &c, const ttie_params *p) {
     if (p->precision != TTIE_F32 && p->precision != TTIE_F64) return set_err(c, TTIE_ERR_INVALID, "precision");
     const int m = p->pair_mode & 3;
     if (m == 3 || (p->pair_mode & ~7)) return set_err(c, TTIE_ERR_INVALID, "pair_mode");
-    if (p->psd_mode != TTIE_PSD_PER_PART && p->psd_mode != TTIE_PSD_DROP_CROSS)
+    if (p->psd_mode != TTIE_PSD_PER_PART && p->psd_mode != TTIE_PSD_DROP_CROSS && p->psd_mode != TTIE_PSD_WHOLE)
         return set_err(c, TTIE_ERR_INVALID, "psd_mode");
     if (!(p->tc_scale > 0.0) || !(p->mu_rel >= 0.0) || !(p->pcg_rtol > 0.0) || p->pcg_max_it < 1 ||
         p->newton_max_it < 0 || p->ls_max_halvings < 0 || p->ls_max_halvings > 60 || !(p->armijo_c >= 0.0) ||
@@ -451,6 +451,26 @@ static ttie_status newton_impl(Ctx &c, T *x, ttie_step_info *info) {
     return TTIE_OK;
 }
 
+template <typename T>
+static ttie_status hvp_impl(Ctx &c, const T *x, const T *v, T *out, int exact) {
+    if (!c.have_bsr) {
+        CK(assemble_system<T>(c, nullptr), "ttie_hvp: assembly");
+        c.have_bsr = true;
+    }
+    if (exact) {
+        CK(pack_positions<T>(c, x, c.x_stride, (vec4_t<T> *)c.xp.p), "ttie_hvp");
+        ttie_status s = read_err(c, "ttie_hvp");
+        if (s != TTIE_OK) return s;
+        CK(ensure(c, c.hbuf, (size_t)(c.n_active > 0 ? c.n_active : 1) * 18 * sizeof(T)), "ttie_hvp");
+        CK(hvp_pairs<T>(c, (const vec4_t<T> *)c.xp.p, v, (T *)c.hbuf.p), "ttie_hvp");
+        CK(vertex_sums<T>(c, (const T *)c.hbuf.p, out), "ttie_hvp");
+    } else {
+        CK(bsr_matvec<T>(c, v, out), "ttie_hvp");
+    }
+    CK(cudaStreamSynchronize(c.stream), "ttie_hvp");
+    return TTIE_OK;
+}
+
 extern "C" {
 
 ttie_status ttie_build_bvh(ttie_ctx *h, const void *d_x, int64_t V, int x_stride, const int32_t *d_tri, int64_t F,
@@ -521,6 +541,17 @@ ttie_status ttie_copy_bsr(ttie_ctx *h, int32_t *d_row_ptr, int32_t *d_col_idx, v
     if (d_grad && c.n_rows) CK(cudaMemcpyAsync(d_grad, c.rhs.p, (size_t)c.n_rows * 3 * es, k, c.stream), "ttie_copy_bsr");
     CK(cudaStreamSynchronize(c.stream), "ttie_copy_bsr");
     return TTIE_OK;
+}
+
+ttie_status ttie_hvp(ttie_ctx *h, const void *d_x, const void *d_v, void *d_out, int exact) {
+    if (!h) return TTIE_ERR_INVALID;
+    Ctx &c = h->c;
+    if (!c.have_eval || !(c.eval_what & (TTIE_EVAL_G | TTIE_EVAL_H)))
+        return set_err(c, TTIE_ERR_STATE, "ttie_hvp: needs a ttie_eval_pairs with TTIE_EVAL_G or TTIE_EVAL_H");
+    if (!d_v || !d_out || (exact && !d_x)) return set_err(c, TTIE_ERR_INVALID, "ttie_hvp: null pointer");
+    if (c.prm.precision == TTIE_F64)
+        return hvp_impl<double>(c, (const double *)d_x, (const double *)d_v, (double *)d_out, exact);
+    return hvp_impl<float>(c, (const float *)d_x, (const float *)d_v, (float *)d_out, exact);
 }
 
 ttie_status ttie_pcg(ttie_ctx *h, const void *d_rhs, void *d_out, double rtol, int max_it, int *iters, double *rel_residual) {

@@ -91,7 +91,7 @@ cudaError_t ensure(Ctx &c, Buf &b, size_t bytes);   // grow-only, contents not k
     X(defer) X(active) X(fac) X(partials) X(vflag) X(vrow) X(row_vertex) X(bkey) X(bkey2)   \
     X(bval) X(bval2) X(bflag) X(run_start) X(row_ptr) X(col_idx) X(bsr_val) X(rhs)         \
     X(zfac) X(dinv) X(pcg_x) X(pcg_r) X(pcg_z) X(pcg_p) X(pcg_q) X(dir) X(xt) X(gtmp)      \
-    X(xsave) X(sweep_cand) X(pcg_z4)
+    X(xsave) X(sweep_cand) X(pcg_z4) X(hbuf)
 
 struct Ctx {
     ttie_params prm;
@@ -190,6 +190,11 @@ template <typename T> cudaError_t eval_candidates(Ctx &c, const vec4_t<T> *x, co
 // ------------------------------------------------------------------ assembly / solve (assemble.cu)
 template <typename T> cudaError_t assemble_system(Ctx &c, T *grad_out_V3);
 template <typename T> cudaError_t pcg_solve(Ctx &c, const T *rhs, T *out, double rtol, int max_it);
+// Hessian-vector products: per-pair exact products (pair_eval.cu), their per-vertex sums over
+// the last assembly's diagonal runs, and the assembled PSD Hessian times v.
+template <typename T> cudaError_t hvp_pairs(Ctx &c, const vec4_t<T> *x, const T *v, T *h);
+template <typename T> cudaError_t vertex_sums(Ctx &c, const T *h, T *out);
+template <typename T> cudaError_t bsr_matvec(Ctx &c, const T *v, T *out);
 // out_dev[0] = g.d, out_dev[1] = max over rows of |d_r|^2 (rows of the assembled system)
 template <typename T> cudaError_t direction_stats(Ctx &c, const T *g, const T *d, double *out_dev);
 template <typename T> cudaError_t axpy_positions(Ctx &c, const vec4_t<T> *x, const T *d, T alpha, vec4_t<T> *out);

@@ -379,8 +379,82 @@ __device__ __forceinline__ void add_direction(T *g, const v3<T> A[3], const v3<T
     }
 }
 
+// Dual number (value, tangent) for forward-mode differentiation; comparisons use values.
+template <typename T> struct Dual {
+    T v, t;
+    __device__ __forceinline__ Dual() {}
+    __device__ __forceinline__ Dual(T a) : v(a), t(T(0)) {}
+    __device__ __forceinline__ Dual(T a, T b) : v(a), t(b) {}
+};
+template <typename T> __device__ __forceinline__ Dual<T> operator+(Dual<T> a, Dual<T> b) { return {a.v + b.v, a.t + b.t}; }
+template <typename T> __device__ __forceinline__ Dual<T> operator-(Dual<T> a, Dual<T> b) { return {a.v - b.v, a.t - b.t}; }
+template <typename T> __device__ __forceinline__ Dual<T> operator-(Dual<T> a) { return {-a.v, -a.t}; }
+template <typename T> __device__ __forceinline__ Dual<T> operator*(Dual<T> a, Dual<T> b) {
+    return {a.v * b.v, a.t * b.v + a.v * b.t};
+}
+template <typename T> __device__ __forceinline__ Dual<T> operator/(Dual<T> a, Dual<T> b) {
+    const T q = a.v / b.v;
+    return {q, (a.t - q * b.t) / b.v};
+}
+template <typename T> __device__ __forceinline__ Dual<T> &operator+=(Dual<T> &a, Dual<T> b) { return a = a + b; }
+template <typename T> __device__ __forceinline__ Dual<T> &operator-=(Dual<T> &a, Dual<T> b) { return a = a - b; }
+template <typename T> __device__ __forceinline__ bool operator<(Dual<T> a, Dual<T> b) { return a.v < b.v; }
+template <typename T> __device__ __forceinline__ bool operator>(Dual<T> a, Dual<T> b) { return a.v > b.v; }
+template <typename T> __device__ __forceinline__ bool operator>=(Dual<T> a, Dual<T> b) { return a.v >= b.v; }
+template <typename T> __device__ __forceinline__ bool operator!=(Dual<T> a, Dual<T> b) { return a.v != b.v; }
+template <typename T> __device__ __forceinline__ Dual<T> sqrt(Dual<T> a) {
+    const T r = sqrt(a.v);
+    return {r, r > T(0) ? a.t / (T(2) * r) : T(0)};
+}
+template <typename T> __device__ __forceinline__ Dual<T> fabs(Dual<T> a) { return a.v < T(0) ? -a : a; }
+using ::sqrt;   // keep the float / double overloads visible next to the dual ones
+using ::fabs;
+
 // Output row per intersecting pair: [t_c^0, t_c^1, d t_c^0 (18), d t_c^1 (18), pad 2].
 constexpr int kFacStride = 40;
+
+// t_c^0, t_c^1 of one intersecting pair and, with kGrad, their gradients (18 each) by the
+// chain rule through the construction above.  S is float, double or a dual number (the
+// exact Hessian-vector product differentiates this function once more in forward mode).
+template <typename S, bool kGrad>
+__device__ __forceinline__ void pair_tc(v3<S> A[3], v3<S> B[3], S tc_scale, S &a, S &b, S *ga, S *gb) {
+    // local frame at A0: T and its gradient are translation invariant, and small
+    // coordinates keep the cancellations in t_c at the size of the triangles
+    const v3<S> o = A[0];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) { A[i] = A[i] - o; B[i] = B[i] - o; }
+    const v3<S> nA = cross(A[1] - A[0], A[2] - A[0]);
+    const v3<S> nB = cross(B[1] - B[0], B[2] - B[0]);
+    const Cut<S> cB = cut_by<S>(A, B, nA);   // segment on B (plane of A)
+    const Cut<S> cA = cut_by<S>(B, A, nB);   // segment on A (plane of B)
+    const v3<S> wv = cross(nB, nA);
+    const S wn = sqrt(dot(wv, wv));
+    const S inv_w = wn > S(0) ? S(1) / wn : S(0);
+    const v3<S> D = inv_w * wv;
+    const S tA0 = dot(D, cA.S0), tA1 = dot(D, cA.S1), tB0 = dot(D, cB.S0), tB1 = dot(D, cB.S1);
+    const bool a0min = !(tA1 < tA0), b0min = !(tB1 < tB0);
+    a = tc_scale * ((a0min ? tA0 : tA1) - (b0min ? tB1 : tB0));
+    b = tc_scale * ((a0min ? tA1 : tA0) - (b0min ? tB0 : tB1));
+    if (kGrad) {
+#pragma unroll
+        for (int i = 0; i < 18; ++i) { ga[i] = S(0); gb[i] = S(0); }
+        // t_c^0 = s (t_A,min - t_B,max), t_c^1 = s (t_A,max - t_B,min)
+        const int amin_m = a0min ? cA.m0 : cA.m1, amin_p = a0min ? cA.p0 : cA.p1;
+        const int amax_m = a0min ? cA.m1 : cA.m0, amax_p = a0min ? cA.p1 : cA.p0;
+        const S amin_l = a0min ? cA.lam0 : cA.lam1, amax_l = a0min ? cA.lam1 : cA.lam0;
+        const v3<S> amin_S = a0min ? cA.S0 : cA.S1, amax_S = a0min ? cA.S1 : cA.S0;
+        const int bmin_m = b0min ? cB.m0 : cB.m1, bmin_p = b0min ? cB.p0 : cB.p1;
+        const int bmax_m = b0min ? cB.m1 : cB.m0, bmax_p = b0min ? cB.p1 : cB.p0;
+        const S bmin_l = b0min ? cB.lam0 : cB.lam1, bmax_l = b0min ? cB.lam1 : cB.lam0;
+        const v3<S> bmin_S = b0min ? cB.S0 : cB.S1, bmax_S = b0min ? cB.S1 : cB.S0;
+        add_endpoint<S>(ga, 0, 9, B, A, nB, D, amin_m, amin_p, amin_l, amin_S, tc_scale);
+        add_endpoint<S>(ga, 9, 0, A, B, nA, D, bmax_m, bmax_p, bmax_l, bmax_S, -tc_scale);
+        add_direction<S>(ga, A, B, nA, nB, D, inv_w, amin_S - bmax_S, tc_scale);
+        add_endpoint<S>(gb, 0, 9, B, A, nB, D, amax_m, amax_p, amax_l, amax_S, tc_scale);
+        add_endpoint<S>(gb, 9, 0, A, B, nA, D, bmin_m, bmin_p, bmin_l, bmin_S, -tc_scale);
+        add_direction<S>(gb, A, B, nA, nB, D, inv_w, amax_S - bmin_S, tc_scale);
+    }
+}
 
 template <typename T, bool kGrad>
 __global__ void __launch_bounds__(128) k_derivs(const vec4_t<T> *__restrict__ x, const int4 *__restrict__ tri4,
@@ -392,46 +466,13 @@ __global__ void __launch_bounds__(128) k_derivs(const vec4_t<T> *__restrict__ x,
          k += (unsigned long long)gridDim.x * blockDim.x) {
         v3<T> A[3], B[3];
         load_pair<T>(x, tri4, pairs[active[k]], A, B);
-        // local frame at A0: T and its gradient are translation invariant, and small
-        // coordinates keep the cancellations in t_c at the size of the triangles
-        const v3<T> o = A[0];
-#pragma unroll
-        for (int i = 0; i < 3; ++i) { A[i] = A[i] - o; B[i] = B[i] - o; }
-        const v3<T> nA = cross(A[1] - A[0], A[2] - A[0]);
-        const v3<T> nB = cross(B[1] - B[0], B[2] - B[0]);
-        const Cut<T> cB = cut_by<T>(A, B, nA);   // segment on B (plane of A)
-        const Cut<T> cA = cut_by<T>(B, A, nB);   // segment on A (plane of B)
-        const v3<T> wv = cross(nB, nA);
-        const T wn = sqrt(dot(wv, wv));
-        const T inv_w = wn > T(0) ? T(1) / wn : T(0);
-        const v3<T> D = inv_w * wv;
-        const T tA0 = dot(D, cA.S0), tA1 = dot(D, cA.S1), tB0 = dot(D, cB.S0), tB1 = dot(D, cB.S1);
-        const bool a0min = !(tA1 < tA0), b0min = !(tB1 < tB0);
-        const T a = tc_scale * ((a0min ? tA0 : tA1) - (b0min ? tB1 : tB0));
-        const T b = tc_scale * ((a0min ? tA1 : tA0) - (b0min ? tB0 : tB1));
+        T a, b, ga[18], gb[18];
+        pair_tc<T, kGrad>(A, B, tc_scale, a, b, ga, gb);
         e_sum += (double)(a * b) * (double)(a * b);
         T *row = fac + k * kFacStride;
         row[0] = a;
         row[1] = b;
         if (kGrad) {
-            T ga[18], gb[18];
-#pragma unroll
-            for (int i = 0; i < 18; ++i) { ga[i] = T(0); gb[i] = T(0); }
-            // t_c^0 = s (t_A,min - t_B,max), t_c^1 = s (t_A,max - t_B,min)
-            const int amin_m = a0min ? cA.m0 : cA.m1, amin_p = a0min ? cA.p0 : cA.p1;
-            const int amax_m = a0min ? cA.m1 : cA.m0, amax_p = a0min ? cA.p1 : cA.p0;
-            const T amin_l = a0min ? cA.lam0 : cA.lam1, amax_l = a0min ? cA.lam1 : cA.lam0;
-            const v3<T> amin_S = a0min ? cA.S0 : cA.S1, amax_S = a0min ? cA.S1 : cA.S0;
-            const int bmin_m = b0min ? cB.m0 : cB.m1, bmin_p = b0min ? cB.p0 : cB.p1;
-            const int bmax_m = b0min ? cB.m1 : cB.m0, bmax_p = b0min ? cB.p1 : cB.p0;
-            const T bmin_l = b0min ? cB.lam0 : cB.lam1, bmax_l = b0min ? cB.lam1 : cB.lam0;
-            const v3<T> bmin_S = b0min ? cB.S0 : cB.S1, bmax_S = b0min ? cB.S1 : cB.S0;
-            add_endpoint<T>(ga, 0, 9, B, A, nB, D, amin_m, amin_p, amin_l, amin_S, tc_scale);
-            add_endpoint<T>(ga, 9, 0, A, B, nA, D, bmax_m, bmax_p, bmax_l, bmax_S, -tc_scale);
-            add_direction<T>(ga, A, B, nA, nB, D, inv_w, amin_S - bmax_S, tc_scale);
-            add_endpoint<T>(gb, 0, 9, B, A, nB, D, amax_m, amax_p, amax_l, amax_S, tc_scale);
-            add_endpoint<T>(gb, 9, 0, A, B, nA, D, bmin_m, bmin_p, bmin_l, bmin_S, -tc_scale);
-            add_direction<T>(gb, A, B, nA, nB, D, inv_w, amax_S - bmin_S, tc_scale);
 #pragma unroll
             for (int i = 0; i < 18; ++i) {
                 row[2 + i] = ga[i];
@@ -440,6 +481,37 @@ __global__ void __launch_bounds__(128) k_derivs(const vec4_t<T> *__restrict__ x,
         }
     }
     grid_sum(e_sum, partials, &ds->done_counter[0], &ds->energy);
+}
+
+// Exact Hessian-vector product per intersecting pair: the pair gradient of Eq. 3,
+// g = 2ab (b grad a + a grad b), evaluated in dual numbers whose tangents are the
+// direction v, gives H_pair v (the full Hessian of T, including the terms Eq. 4 drops).
+template <typename T>
+__global__ void __launch_bounds__(128) k_hvp_pairs(const vec4_t<T> *__restrict__ x, const T *__restrict__ v,
+                                                   const int4 *__restrict__ tri4, const int2 *__restrict__ pairs,
+                                                   const uint32_t *__restrict__ active, T tc_scale,
+                                                   T *__restrict__ h, const DevScalars *ds) {
+    typedef Dual<T> S;
+    const unsigned long long n_act = ds->n_active;
+    for (unsigned long long k = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; k < n_act;
+         k += (unsigned long long)gridDim.x * blockDim.x) {
+        const int2 pr = pairs[active[k]];
+        const int4 ta = tri4[pr.x], tb = tri4[pr.y];
+        const int vid[6] = {ta.x, ta.y, ta.z, tb.x, tb.y, tb.z};
+        v3<S> P[6];
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+            const vec4_t<T> p = x[vid[i]];
+            const T *d = v + 3 * (size_t)vid[i];
+            P[i] = {S(p.x, d[0]), S(p.y, d[1]), S(p.z, d[2])};
+        }
+        v3<S> A[3] = {P[0], P[1], P[2]}, B[3] = {P[3], P[4], P[5]};
+        S a, b, ga[18], gb[18];
+        pair_tc<S, true>(A, B, S(tc_scale), a, b, ga, gb);
+        const S w = S(2) * a * b;
+#pragma unroll
+        for (int i = 0; i < 18; ++i) h[k * 18 + i] = (w * (b * ga[i] + a * gb[i])).t;
+    }
 }
 
 }  // namespace
@@ -490,5 +562,15 @@ cudaError_t eval_candidates(Ctx &c, const vec4_t<T> *x, const int2 *pairs, int64
 }
 template cudaError_t eval_candidates<float>(Ctx &, const float4 *, const int2 *, int64_t, unsigned);
 template cudaError_t eval_candidates<double>(Ctx &, const dvec4 *, const int2 *, int64_t, unsigned);
+
+// Per intersecting pair of the last evaluation: the exact Hessian of T times the direction v
+// (V x 3), 18 values per pair in the order of the pair's vertices.
+template <typename T> cudaError_t hvp_pairs(Ctx &c, const vec4_t<T> *x, const T *v, T *h) {
+    launch(c, k_hvp_pairs<T>, dim3(grid_for(c.n_active, 128, (int64_t)kNumSMs * 8)), dim3(128), x, v,
+           (const int4 *)c.tri4.p, (const int2 *)c.cand.p, (const uint32_t *)c.active.p, (T)c.prm.tc_scale, h, c.ds);
+    return cudaGetLastError();
+}
+template cudaError_t hvp_pairs<float>(Ctx &, const float4 *, const float *, float *);
+template cudaError_t hvp_pairs<double>(Ctx &, const dvec4 *, const double *, double *);
 
 }  // namespace ttie

@@ -25,7 +25,7 @@ TTIE_OK, TTIE_ERR_INVALID, TTIE_ERR_CUDA, TTIE_ERR_OOM, TTIE_ERR_CAPACITY, TTIE_
 STATUS_NAMES = ["OK", "INVALID", "CUDA", "OOM", "CAPACITY", "NONFINITE", "NOT_CONVERGED", "STATE"]
 F32, F64 = 0, 1
 PAIRS_SELF, PAIRS_INTER_GROUP, PAIRS_INTRA_GROUP, PAIRS_BRUTE = 0, 1, 2, 4
-PSD_PER_PART, PSD_DROP_CROSS = 0, 1
+PSD_PER_PART, PSD_DROP_CROSS, PSD_WHOLE = 0, 1, 2
 EVAL_E, EVAL_G, EVAL_H = 1, 2, 4
 
 
@@ -97,6 +97,7 @@ _SIGS = {
     "ttie_get_direction": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "ttie_get_filter_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)]),
     "ttie_get_launch_count": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)]),
+    "ttie_hvp": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
 }
 
 
@@ -162,6 +163,7 @@ class Context:
             raise TTIEError(s, "ttie_create failed")
         self.h = h
         self.V = None
+        self.x_stride = None
 
     def close(self):
         if getattr(self, "h", None):
@@ -173,6 +175,13 @@ class Context:
             self.close()
         except Exception:
             pass
+
+    def _check_x(self, x, name="x"):
+        """Positions after ttie_build_bvh must have its layout: the library reads V x stride."""
+        _check_dev(x, name, self.dtype)
+        if self.V is not None and (x.dim() != 2 or tuple(x.shape) != (self.V, self.x_stride)):
+            raise TTIEError(TTIE_ERR_INVALID, "%s must be [%d,%d] like the mesh given to build_bvh" %
+                            (name, self.V, self.x_stride))
 
     def _chk(self, s):
         if s != TTIE_OK:
@@ -196,11 +205,12 @@ class Context:
         self._chk(self.lib.ttie_build_bvh(self.h, _ptr(x), x.shape[0], x.shape[1], _ptr(tri), tri.shape[0],
                                           _ptr(group), ctypes.byref(n)))
         self.V = x.shape[0]
+        self.x_stride = x.shape[1]
         return n.value
 
     def eval_pairs(self, x: torch.Tensor, what: int = EVAL_E, grad: torch.Tensor | None = None):
         """Returns (energy, n_active); fills ``grad`` ([V,3]) when given (needs EVAL_G)."""
-        _check_dev(x, "x", self.dtype)
+        self._check_x(x)
         if grad is not None:
             _check_dev(grad, "grad", self.dtype)
             if tuple(grad.shape) != (x.shape[0], 3):
@@ -230,14 +240,25 @@ class Context:
         self._chk(self.lib.ttie_pcg(self.h, _ptr(rhs), _ptr(out), rtol, max_it, ctypes.byref(it), ctypes.byref(rr)))
         return out, it.value, rr.value
 
+    def hvp(self, x: torch.Tensor, v: torch.Tensor, exact: bool = True) -> torch.Tensor:
+        """Hessian of the energy (exact, or the assembled PSD H+) times v ([V,3]) at the positions
+        of the last eval_pairs; x must be those positions."""
+        self._check_x(x)
+        _check_dev(v, "v", self.dtype)
+        if tuple(v.shape) != (x.shape[0], 3):
+            raise TTIEError(TTIE_ERR_INVALID, "v must be [V,3]")
+        out = torch.empty_like(v)
+        self._chk(self.lib.ttie_hvp(self.h, _ptr(x), _ptr(v), _ptr(out), 1 if exact else 0))
+        return out
+
     def newton_step(self, x: torch.Tensor) -> dict:
-        _check_dev(x, "x", self.dtype)
+        self._check_x(x)
         info = StepInfo()
         self._chk(self.lib.ttie_newton_step(self.h, _ptr(x), ctypes.byref(info)))
         return info.as_dict()
 
     def solve(self, x: torch.Tensor, raise_on_limit: bool = False) -> dict:
-        _check_dev(x, "x", self.dtype)
+        self._check_x(x)
         info = SolveInfo()
         s = self.lib.ttie_solve(self.h, _ptr(x), ctypes.byref(info))
         if s == TTIE_ERR_NOT_CONVERGED and not raise_on_limit:

@@ -285,3 +285,32 @@ def test_degenerate_sizes(ttie):
     tri0 = torch.zeros((0, 3), dtype=torch.int32, device="cuda")
     assert ctx.build_bvh(x, tri0) == 0
     assert ctx.eval_pairs(x) == (0.0, 0)
+
+
+@pytest.mark.parametrize("name", ["cloth40", "tori", "soup"])
+@pytest.mark.parametrize("psd", ["drop_cross", "whole"])
+def test_assembly_psd_modes(ttie, name, psd):
+    """The other projections of §1.1 against the oracle: parts 1 and 2 only, and the eigenvalue
+    clamp of the whole Eq. 4 Hessian (numpy eigh of the 18x18 sum in the oracle, a 2x2
+    reduction on the GPU)."""
+    m, mode = CASES[name]
+    x, tri, grp = _dev(m, torch.float64)
+    mode_id = {"drop_cross": ttie.PSD_DROP_CROSS, "whole": ttie.PSD_WHOLE}[psd]
+    ctx = _ctx(ttie, mode, precision=1, psd_mode=mode_id)
+    ctx.build_bvh(x, tri, grp)
+    ctx.eval_pairs(x, ttie.EVAL_E | ttie.EVAL_H)
+    bsr = ctx.assemble()
+    pairs, ev = _oracle(name)
+    _, blocks = O.assemble(m.tri, ev, m.V, psd=psd)
+    rows = bsr.vertex_of_row.cpu().numpy()
+    rp = bsr.row_ptr.cpu().numpy()
+    ci = bsr.col_idx.cpu().numpy()
+    val = bsr.val.cpu().numpy()
+    got = {}
+    for r in range(len(rows)):
+        for b in range(rp[r], rp[r + 1]):
+            got[(int(rows[r]), int(rows[ci[b]]))] = val[b]
+    assert set(got) == set(blocks)
+    scale = max(np.abs(b).max() for b in blocks.values())
+    for key, b in blocks.items():
+        assert np.allclose(got[key], b, rtol=1e-4, atol=1e-4 * scale), key

@@ -407,3 +407,85 @@ def test_newton_solve_reaches_intersection_free(case):
     x, it, ok = O.newton_solve(m.x, m.tri, m.group, O.NewtonParams(newton_max_it=30, mode=mode))
     assert ok
     assert O.certify(x, m.tri, m.group, mode) == 0
+
+
+# ----------------------------------------------------------------- exact Hessian-vector product
+def _hvp_case(seed=3):
+    m = ti.triangle_soup(200, seed, size=0.5)
+    pairs = O.candidate_pairs(m.x, m.tri)
+    ev = O.evaluate(m.x, m.tri, pairs)
+    g, _ = O.assemble(m.tri, ev, m.V)
+    return m, ev, g
+
+
+def test_hvp_euler_identity():
+    """T is homogeneous of degree 4 in the positions (t_c are lengths, Eq. 1), so H x = 3 g."""
+    m, ev, g = _hvp_case()
+    assert ev.active.sum() > 20
+    v = m.x - m.x.mean(0)
+    hv = O.hessian_vector_product(m.x, m.tri, ev, v)
+    assert np.allclose(hv, 3 * g, rtol=0, atol=1e-7 * np.abs(g).max())
+
+
+def test_hvp_rotation_and_translation():
+    """T is invariant under rigid motions: H (w x x) = w x g per vertex and H c = 0."""
+    m, ev, g = _hvp_case(seed=5)
+    rng = np.random.default_rng(0)
+    w = rng.normal(size=3)
+    hv = O.hessian_vector_product(m.x, m.tri, ev, np.cross(w, m.x))
+    assert np.allclose(hv, np.cross(w, g), rtol=0, atol=1e-7 * np.abs(g).max() * np.abs(w).max())
+    c = rng.normal(size=3)
+    ht = O.hessian_vector_product(m.x, m.tri, ev, np.tile(c, (m.V, 1)))
+    r = m.x - m.x.mean(0)
+    h_unit = 3 * np.abs(g).max() / np.abs(r).max()      # |H| from Euler's identity, H r = 3 g
+    assert np.abs(ht).max() < 1e-6 * h_unit * np.abs(c).max()
+    # the inexact Hessian of Eq. 4 is not rotation-consistent: the pin tells them apart
+    act = np.nonzero(ev.active)[0]
+    H = O.hessian_inexact(ev)[act]
+    vid = O.pair_dofs(m.tri, ev.pairs[act])
+    u = np.cross(w, m.x)[vid].reshape(len(act), 18)
+    hin = np.zeros_like(m.x)
+    for r in range(6):
+        np.add.at(hin, vid[:, r], np.einsum("pij,pj->pi", H, u)[:, 3 * r:3 * r + 3])
+    assert np.abs(hin - np.cross(w, g)).max() > 1e-3 * np.abs(g).max()
+
+
+def test_hvp_quadratic_form_and_symmetry():
+    """v.Hv is the second difference of E along v (T values only); u.Hv = v.Hu."""
+    m, ev, g = _hvp_case(seed=7)
+    rng = np.random.default_rng(1)
+    v = rng.normal(size=m.x.shape)
+    u = rng.normal(size=m.x.shape)
+    act = ev.pairs[ev.active]
+
+    def E(xx):
+        tc, _, _, _ = O.eval_pairs_f64(xx, m.tri, act)
+        return float(((tc[:, 0] * tc[:, 1]) ** 2).sum())
+
+    eps = 1e-6   # well inside the smooth piece of every pair (the interval end points have kinks)
+    d2 = (E(m.x + eps * v) - 2 * E(m.x) + E(m.x - eps * v)) / eps ** 2
+    hv = O.hessian_vector_product(m.x, m.tri, ev, v)
+    hu = O.hessian_vector_product(m.x, m.tri, ev, u)
+    assert float((v * hv).sum()) == pytest.approx(d2, rel=1e-5)
+    assert float((u * hv).sum()) == pytest.approx(float((v * hu).sum()), rel=1e-5)
+
+
+def test_psd_whole_and_drop_cross_projections():
+    """'whole' is the projection of Eq. 4 onto the PSD cone: H+ is PSD, H+ - H is PSD and
+    H+ (H+ - H) = 0 (complementarity); Eq. 4 has inertia (1, 1, 16), so H+ has rank one.
+    'drop_cross' is parts 1 + 2 exactly."""
+    m, pairs = _generic_active_pairs(seed=9)
+    ev = O.evaluate(m.x, m.tri, pairs)
+    H = O.hessian_inexact(ev)
+    Hw = O.hessian_psd(ev, "whole")
+    p1, p2, _ = O.hessian_parts(ev)
+    assert np.array_equal(O.hessian_psd(ev, "drop_cross"), p1 + p2)
+    for k in range(len(pairs)):
+        s = np.abs(H[k]).max()
+        w = np.linalg.eigvalsh(H[k])
+        assert (w > 1e-9 * s).sum() == 1 and (w < -1e-9 * s).sum() == 1
+        assert np.linalg.eigvalsh(Hw[k]).min() >= -1e-12 * s
+        D = Hw[k] - H[k]
+        assert np.linalg.eigvalsh(D).min() >= -1e-12 * s
+        assert np.abs(Hw[k] @ D).max() <= 1e-10 * s * s
+        assert np.linalg.matrix_rank(Hw[k], tol=1e-9 * s) == 1
