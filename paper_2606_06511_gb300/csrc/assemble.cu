@@ -398,6 +398,12 @@ __device__ __forceinline__ bool grid_allreduce(double (&v)[N], double *part, Dev
     return ok;
 }
 
+// One block's partial sums for the resident PCG's reductions, tagged with the reduction's epoch.
+struct __align__(32) RedSlot {
+    unsigned long long v[3];   // bits of the block's accumulators
+    unsigned long long epoch;
+};
+
 template <typename T> struct PcgArgs {
     const int32_t *row_ptr;
     const int32_t *col_idx;
@@ -406,6 +412,8 @@ template <typename T> struct PcgArgs {
     T *x, *r, *z, *p, *q;
     vec4_t<T> *z4;           // z mirrored as one 16/32-byte vector per row (resident kernel)
     double *partA, *partB;
+    RedSlot *slots;          // resident kernel: 2 x grid epoch-tagged reduction slots
+    unsigned long long *flags;   // resident kernel: per-block publication epochs
     double rtol2;
     int max_it;
     DevScalars *ds;
@@ -528,13 +536,227 @@ __global__ void __launch_bounds__(kPcgThreads) k_pcg_persistent(PcgArgs<T> a) {
 }
 
 // ---------------------------------------------------------------- PCG, block-resident rows
-// Each block owns the contiguous rows [row0, row0 + nrow) for the whole solve.  Their x,
-// r, z, p, q, the inverse diagonal blocks, the row offsets and, when they fit, the matrix
-// rows live in shared memory, so the vector updates never leave the SM.  Only z, which
-// the product reads across rows, is also written to global memory (read back through
-// L2 by other blocks after the barrier that follows the update).  Same iteration, same
-// reductions and decisions as k_pcg_persistent.
-constexpr int kResidentSmem = 200 * 1024;   // dynamic shared memory per block
+// Each block owns the contiguous rows [row0, row0 + nrow) for the whole solve.  Their x, r,
+// u = M^-1 r, p, s = A p, w = A u, the inverse diagonal blocks, the row offsets and, when
+// they fit, the matrix rows and the gathered u of their columns live in shared memory.
+//
+// Iteration (Chronopoulos and Gear's form of preconditioned CG: one reduction per
+// iteration).  With gamma = r.u, delta = w.u:
+//   beta = gamma / gamma_prev,  alpha = gamma / (delta - beta gamma / alpha_prev)
+//   p = u + beta p,  s = w + beta s,  x += alpha p,  r -= alpha s,  u = M^-1 r,  w = A u.
+// The product needs u of other blocks' rows: each block publishes its u (one 16/32-byte
+// vector per row) and then an epoch flag; before the product a block waits only for the
+// flags of the blocks its columns belong to.  The three dot products are summed through
+// per-block slots tagged with an epoch (no atomics): every block reads all slots in the
+// same order, so all blocks take the same decisions.  No block can run a phase ahead of a
+// reader: publishing u for iteration k+1 needs the reduction of iteration k, which needs
+// every block to have finished its product of iteration k.  Slots alternate between two
+// buffers by epoch parity for the same reason.  Every wait is bounded (kBarrierSpins); on
+// timeout ERR_BARRIER is set and the kernel returns.
+constexpr int kResidentSmem = 220 * 1024;   // dynamic shared memory per block
+constexpr int kMaxGridPcg = 256;            // slots per lane in the reduction: 8
+constexpr int kMaxDeps = 256;
+
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long *p, unsigned long long v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// Accumulator of dot products of T vectors and the arithmetic of the CG recurrence.  For FP32
+// vectors it is an unevaluated sum of two floats (hi + lo, about 48 significant bits):
+// products are split exactly with one fma and added with Knuth's two-sum, all at the FP32
+// rate.  GB300 executes FP64 at a small fraction of the FP32 rate (a warp-wide FP64
+// instruction occupies its pipe for tens of cycles), and a block-wide FP64 reduction per
+// iteration costs microseconds.  For FP64 vectors it is a plain double.
+template <typename T> struct Acc;
+template <> struct Acc<double> {
+    double v = 0.0;
+    __device__ __forceinline__ void add_prod(double a, double b) { v = fma(a, b, v); }
+    __device__ __forceinline__ void add(const Acc &o) { v += o.v; }
+    __device__ __forceinline__ Acc shfl_xor(unsigned mask, int o, int width) const {
+        Acc r;
+        r.v = __shfl_xor_sync(mask, v, o, width);
+        return r;
+    }
+    __device__ __forceinline__ unsigned long long bits() const { return (unsigned long long)__double_as_longlong(v); }
+    __device__ __forceinline__ static Acc from_bits(unsigned long long b) {
+        Acc r;
+        r.v = __longlong_as_double((long long)b);
+        return r;
+    }
+    __device__ __forceinline__ Acc times(double b) const { Acc r; r.v = v * b; return r; }
+    __device__ __forceinline__ Acc over(double b) const { Acc r; r.v = v / b; return r; }
+    __device__ __forceinline__ Acc minus(const Acc &o) const { Acc r; r.v = v - o.v; return r; }
+    __device__ __forceinline__ double approx() const { return v; }
+    __device__ __forceinline__ double value() const { return v; }
+};
+template <> struct Acc<float> {
+    float hi = 0.f, lo = 0.f;
+    __device__ __forceinline__ void add_pair(float bh, float bl) {
+        const float s = hi + bh, bb = s - hi;
+        const float e = (hi - (s - bb)) + (bh - bb) + lo + bl;
+        hi = s + e;
+        lo = e - (hi - s);
+    }
+    __device__ __forceinline__ void add_prod(float a, float b) {
+        const float p = a * b;
+        add_pair(p, fmaf(a, b, -p));
+    }
+    __device__ __forceinline__ void add(const Acc &o) { add_pair(o.hi, o.lo); }
+    __device__ __forceinline__ Acc shfl_xor(unsigned mask, int o, int width) const {
+        Acc r;
+        r.hi = __shfl_xor_sync(mask, hi, o, width);
+        r.lo = __shfl_xor_sync(mask, lo, o, width);
+        return r;
+    }
+    __device__ __forceinline__ unsigned long long bits() const {
+        return (unsigned long long)__float_as_uint(hi) | ((unsigned long long)__float_as_uint(lo) << 32);
+    }
+    __device__ __forceinline__ static Acc from_bits(unsigned long long b) {
+        Acc r;
+        r.hi = __uint_as_float((unsigned)b);
+        r.lo = __uint_as_float((unsigned)(b >> 32));
+        return r;
+    }
+    __device__ __forceinline__ Acc times(float b) const {   // (hi + lo) b
+        const float p = hi * b, e = fmaf(hi, b, -p) + lo * b;
+        Acc r;
+        r.hi = p + e;
+        r.lo = e - (r.hi - p);
+        return r;
+    }
+    __device__ __forceinline__ Acc over(float b) const {    // (hi + lo) / b, one correction step
+        const float q1 = hi / b, p = q1 * b, pe = fmaf(q1, b, -p);
+        const float q2 = (((hi - p) - pe) + lo) / b;
+        Acc r;
+        r.hi = q1 + q2;
+        r.lo = q2 - (r.hi - q1);
+        return r;
+    }
+    __device__ __forceinline__ Acc minus(const Acc &o) const {
+        Acc r = *this;
+        r.add_pair(-o.hi, -o.lo);
+        return r;
+    }
+    __device__ __forceinline__ float approx() const { return hi + lo; }
+    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
+// Block sums of N accumulators (warp trees, then warp 0 over the warp totals), valid in warp 0.
+template <int N, typename T>
+__device__ __forceinline__ void block_sums(Acc<T> (&a)[N]) {
+    __shared__ unsigned long long sh[N][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+#pragma unroll
+        for (int o = 16; o; o >>= 1) a[i].add(a[i].shfl_xor(0xffffffffu, o, 32));
+        if (lane == 0) sh[i][w] = a[i].bits();
+    }
+    __syncthreads();
+    if (w == 0) {
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            a[i] = lane < (int)(blockDim.x >> 5) ? Acc<T>::from_bits(sh[i][lane]) : Acc<T>();
+#pragma unroll
+            for (int o = 16; o; o >>= 1) a[i].add(a[i].shfl_xor(0xffffffffu, o, 32));
+        }
+    }
+}
+
+// Grid sums of N <= 3 accumulators through epoch-tagged slots, identical in every block.
+// Warp 0 of each block publishes its block's sums, waits for every slot of epoch e, adds
+// them in slot order, and lane 0 then runs fin(totals) (thread 0 of each block).  Returns
+// false (ERR_BARRIER set) when the wait runs out.
+template <int N, typename T, typename Fin>
+__device__ __forceinline__ bool slot_allreduce(Acc<T> (&a)[N], RedSlot *slots, unsigned long long e, DevScalars *ds,
+                                               Fin fin) {
+    __shared__ int s_fail;
+    const unsigned G = gridDim.x;
+    const int lane = threadIdx.x & 31;
+    block_sums<N, T>(a);
+    RedSlot *buf = slots + (size_t)(e & 1ull) * G;
+    if (threadIdx.x < 32) {
+        if (lane == 0) {
+#pragma unroll
+            for (int i = 0; i < N; ++i) buf[blockIdx.x].v[i] = a[i].bits();
+            __threadfence();
+            st_relaxed_u64(&buf[blockIdx.x].epoch, e);
+        }
+        // every lane polls its (up to 8) slots with all loads in flight, then reads them
+        unsigned ready = 0, want = 0;
+#pragma unroll
+        for (int k = 0; k < kMaxGridPcg / 32; ++k)
+            if (lane + 32u * k < G) want |= 1u << k;
+        long long spins = 0;
+        bool fail = false;
+        while (true) {
+#pragma unroll
+            for (int k = 0; k < kMaxGridPcg / 32; ++k)
+                if ((want & ~ready) >> k & 1u)
+                    if (ld_relaxed_u64(&buf[lane + 32 * k].epoch) >= e) ready |= 1u << k;
+            if (__all_sync(0xffffffffu, ready == want)) break;
+            if (++spins > kBarrierSpins) { fail = true; break; }
+            __nanosleep(20);
+        }
+        __threadfence();
+        Acc<T> s[N];
+#pragma unroll
+        for (int k = 0; k < kMaxGridPcg / 32; ++k)
+            if (want >> k & 1u)
+#pragma unroll
+                for (int i = 0; i < N; ++i) s[i].add(Acc<T>::from_bits(__ldcg(&buf[lane + 32 * k].v[i])));
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+#pragma unroll
+            for (int o = 16; o; o >>= 1) s[i].add(s[i].shfl_xor(0xffffffffu, o, 32));
+        }
+        fail = __any_sync(0xffffffffu, fail);
+        if (lane == 0) {
+            s_fail = fail ? 1 : 0;
+            if (fail) atomicOr(&ds->err, ERR_BARRIER);
+            else fin(s);
+        }
+    }
+    __syncthreads();
+    return s_fail == 0;
+}
+
+// Wait until every block in deps (or every other block when n_dep < 0) has published the
+// epoch e; bounded.
+__device__ __forceinline__ bool wait_flags(const unsigned long long *flags, const int *deps, int n_dep,
+                                           unsigned long long e, DevScalars *ds) {
+    __shared__ int s_fail;
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        const int n = n_dep < 0 ? (int)gridDim.x : n_dep;
+        bool fail = false;
+        for (int j0 = 0; j0 < n && !fail; j0 += 32) {
+            const int j = j0 + lane;
+            const int blk = j < n ? (n_dep < 0 ? j : deps[j]) : -1;
+            bool ok = blk < 0 || blk == (int)blockIdx.x;
+            long long spins = 0;
+            while (true) {
+                if (!ok) ok = ld_relaxed_u64(&flags[blk]) >= e;
+                if (__all_sync(0xffffffffu, ok)) break;
+                if (++spins > kBarrierSpins) { fail = true; break; }
+                __nanosleep(20);
+            }
+            fail = __any_sync(0xffffffffu, fail);
+        }
+        __threadfence();
+        if (lane == 0) {
+            s_fail = fail ? 1 : 0;
+            if (fail) atomicOr(&ds->err, ERR_BARRIER);
+        }
+    }
+    __syncthreads();
+    return s_fail == 0;
+}
 
 template <typename T> __device__ __forceinline__ vec4_t<T> ldcg4(const vec4_t<T> *p);
 template <> __device__ __forceinline__ float4 ldcg4<float>(const float4 *p) { return __ldcg(p); }
@@ -547,40 +769,71 @@ template <> __device__ __forceinline__ dvec4 ldcg4<double>(const dvec4 *p) {
 }
 
 template <typename T>
-__device__ __forceinline__ void block_times(const T *m, const vec4_t<T> &v, T &y0, T &y1, T &y2) {
-    y0 += m[0] * v.x + m[1] * v.y + m[2] * v.z;
-    y1 += m[3] * v.x + m[4] * v.y + m[5] * v.z;
-    y2 += m[6] * v.x + m[7] * v.y + m[8] * v.z;
+__device__ __forceinline__ void block_times(const T *m, T v0, T v1, T v2, T &y0, T &y1, T &y2) {
+    y0 += m[0] * v0 + m[1] * v1 + m[2] * v2;
+    y1 += m[3] * v0 + m[4] * v1 + m[5] * v2;
+    y2 += m[6] * v0 + m[7] * v1 + m[8] * v2;
 }
 
+template <typename T> struct ResidentView {
+    T *x, *r, *u, *p, *s, *w, *di;   // 3 (9 for di) values per local row
+    int *rp;                          // local row offsets (nrow + 1)
+    T *val;                           // matrix rows (9 per block) when cached
+    int *col;                         // their columns when cached
+    T *gu;                            // u at each block's column (3 per block) when gathered
+    bool cached, gathered;
+    int nrow, nnz, b_begin;
+};
+
+// w = (A + mu I) u on the block's rows; returns the rows' w.u
 template <typename T>
-__device__ __forceinline__ double resident_direction(const PcgArgs<T> &a, const int *srp, const T *sval,
-                                                     const int *scol, bool cached, int b_begin, long long row0,
-                                                     int nrow, const T *sz, T *sp, T *sq, T mu, T beta, bool first) {
+__device__ __forceinline__ Acc<T> resident_product(const PcgArgs<T> &a, const ResidentView<T> &v, T mu) {
+    if (v.gathered) {
+        // gather every block's column vector first: all loads of a thread in flight together
+        constexpr int U = 4;
+        for (int j0 = threadIdx.x; j0 < v.nnz; j0 += U * kPcgThreads) {
+            vec4_t<T> g[U];
+#pragma unroll
+            for (int k = 0; k < U; ++k) {
+                const int j = j0 + k * kPcgThreads;
+                if (j < v.nnz) g[k] = ldcg4<T>(&a.z4[v.col[j]]);
+            }
+#pragma unroll
+            for (int k = 0; k < U; ++k) {
+                const int j = j0 + k * kPcgThreads;
+                if (j < v.nnz) { v.gu[3 * j] = g[k].x; v.gu[3 * j + 1] = g[k].y; v.gu[3 * j + 2] = g[k].z; }
+            }
+        }
+        __syncthreads();
+    }
     const int lane = threadIdx.x & 31, sub = lane & (kLanesPerRow - 1);
     const unsigned gmask = 0xffu << (lane & ~(kLanesPerRow - 1));
-    double pq = 0.0;
-    for (int lr = threadIdx.x / kLanesPerRow; lr < nrow; lr += kPcgThreads / kLanesPerRow) {
+    Acc<T> wu;
+    for (int lr = threadIdx.x / kLanesPerRow; lr < v.nrow; lr += kPcgThreads / kLanesPerRow) {
         T y0 = 0, y1 = 0, y2 = 0;
-        int b = srp[lr] + sub;
-        const int be = srp[lr + 1];
-        if (cached) {
-            // two blocks per step: both gathers in flight before either is used
-            for (; b + kLanesPerRow < be; b += 2 * kLanesPerRow) {
-                const int c0 = scol[b], c1 = scol[b + kLanesPerRow];
-                const vec4_t<T> v0 = ldcg4<T>(&a.z4[c0]), v1 = ldcg4<T>(&a.z4[c1]);
-                block_times(sval + (size_t)b * 9, v0, y0, y1, y2);
-                block_times(sval + (size_t)(b + kLanesPerRow) * 9, v1, y0, y1, y2);
+        const int be = v.rp[lr + 1];
+        if (v.gathered) {
+            for (int b = v.rp[lr] + sub; b < be; b += kLanesPerRow)
+                block_times(v.val + (size_t)b * 9, v.gu[3 * b], v.gu[3 * b + 1], v.gu[3 * b + 2], y0, y1, y2);
+        } else if (v.cached) {
+            int b = v.rp[lr] + sub;
+            for (; b + kLanesPerRow < be; b += 2 * kLanesPerRow) {   // two gathers in flight
+                const vec4_t<T> g0 = ldcg4<T>(&a.z4[v.col[b]]), g1 = ldcg4<T>(&a.z4[v.col[b + kLanesPerRow]]);
+                block_times(v.val + (size_t)b * 9, g0.x, g0.y, g0.z, y0, y1, y2);
+                block_times(v.val + (size_t)(b + kLanesPerRow) * 9, g1.x, g1.y, g1.z, y0, y1, y2);
             }
-            if (b < be) block_times(sval + (size_t)b * 9, ldcg4<T>(&a.z4[scol[b]]), y0, y1, y2);
-            b = be;
-        }
-        for (; b < be; b += kLanesPerRow) {
-            if (TTIE_BAD(a.ds, b >= 0 && (unsigned long long)(b_begin + b) < a.ds->nnzb, 41, b)) break;
-            const T *m = a.bval + (size_t)(b_begin + b) * 9;
-            const int c = a.col_idx[b_begin + b];
-            if (TTIE_BAD(a.ds, c >= 0 && (unsigned long long)c < a.ds->n_rows, 42, c)) break;
-            block_times(m, ldcg4<T>(&a.z4[c]), y0, y1, y2);
+            if (b < be) {
+                const vec4_t<T> g0 = ldcg4<T>(&a.z4[v.col[b]]);
+                block_times(v.val + (size_t)b * 9, g0.x, g0.y, g0.z, y0, y1, y2);
+            }
+        } else {
+            for (int b = v.rp[lr] + sub; b < be; b += kLanesPerRow) {
+                if (TTIE_BAD(a.ds, (unsigned long long)(v.b_begin + b) < a.ds->nnzb, 41, b)) break;
+                const int c = a.col_idx[v.b_begin + b];
+                if (TTIE_BAD(a.ds, c >= 0 && (unsigned long long)c < a.ds->n_rows, 42, c)) break;
+                const vec4_t<T> g0 = ldcg4<T>(&a.z4[c]);
+                block_times(a.bval + (size_t)(v.b_begin + b) * 9, g0.x, g0.y, g0.z, y0, y1, y2);
+            }
         }
 #pragma unroll
         for (int o = kLanesPerRow / 2; o; o >>= 1) {
@@ -589,113 +842,188 @@ __device__ __forceinline__ double resident_direction(const PcgArgs<T> &a, const 
             y2 += __shfl_xor_sync(gmask, y2, o, kLanesPerRow);
         }
         if (sub == 0) {
-            const T w[3] = {y0 + mu * sz[lr * 3], y1 + mu * sz[lr * 3 + 1], y2 + mu * sz[lr * 3 + 2]};
-#pragma unroll
-            for (int i = 0; i < 3; ++i) {
-                const T pi = first ? sz[lr * 3 + i] : sz[lr * 3 + i] + beta * sp[lr * 3 + i];
-                const T qi = first ? w[i] : w[i] + beta * sq[lr * 3 + i];
-                sp[lr * 3 + i] = pi;
-                sq[lr * 3 + i] = qi;
-                pq += (double)pi * qi;
-            }
+            const T w0 = y0 + mu * v.u[lr * 3], w1 = y1 + mu * v.u[lr * 3 + 1], w2 = y2 + mu * v.u[lr * 3 + 2];
+            v.w[lr * 3] = w0; v.w[lr * 3 + 1] = w1; v.w[lr * 3 + 2] = w2;
+            wu.add_prod(w0, v.u[lr * 3]);
+            wu.add_prod(w1, v.u[lr * 3 + 1]);
+            wu.add_prod(w2, v.u[lr * 3 + 2]);
         }
     }
-    (void)row0;
-    return pq;
+    return wu;
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kPcgThreads) k_pcg_resident(PcgArgs<T> a, int rows_per_block, int smem_bytes) {
+__global__ void __launch_bounds__(kPcgThreads) k_pcg_resident(PcgArgs<T> a, int rows_per_block, int smem_bytes,
+                                                             unsigned long long epoch0) {
     extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ unsigned s_bits[kMaxGridPcg / 32];
+    __shared__ int s_dep[kMaxDeps];
+    __shared__ int s_ndep;
+    __shared__ T s_alpha, s_beta;
+    __shared__ int s_stop;
     DevScalars *ds = a.ds;
     if (ds->pcg_done) return;
     const long long nr = (long long)ds->n_rows;
     const int R = rows_per_block;
     const long long row0 = (long long)blockIdx.x * R;
-    const int nrow = (int)max(0LL, min((long long)R, nr - row0));
-    T *sx = (T *)smem, *sr = sx + 3 * R, *sz = sr + 3 * R, *sp = sz + 3 * R, *sq = sp + 3 * R, *sdi = sq + 3 * R;
-    int *srp = (int *)(sdi + 9 * R);
-    const size_t vec_bytes = ((size_t)R * 24 * sizeof(T) + (size_t)(R + 1) * sizeof(int) + 15) / 16 * 16;
-    const int b_begin = nrow ? a.row_ptr[row0] : 0;
-    const int nnz = nrow ? a.row_ptr[row0 + nrow] - b_begin : 0;
-    const bool cached = vec_bytes + (size_t)nnz * (9 * sizeof(T) + sizeof(int)) <= (size_t)smem_bytes;
-    T *sval = (T *)(smem + vec_bytes);
-    int *scol = (int *)(sval + (size_t)9 * nnz);
-    // load the block's rows (x = 0, r, z = M^-1 r, p = z and M^-1 from the setup kernel)
-    for (int i = threadIdx.x; i < 3 * nrow; i += blockDim.x) {
-        sx[i] = a.x[row0 * 3 + i];
-        sr[i] = a.r[row0 * 3 + i];
-        sz[i] = a.z[row0 * 3 + i];
-        sp[i] = a.p[row0 * 3 + i];
+    ResidentView<T> v;
+    v.nrow = (int)max(0LL, min((long long)R, nr - row0));
+    v.x = (T *)smem; v.r = v.x + 3 * R; v.u = v.r + 3 * R; v.p = v.u + 3 * R; v.s = v.p + 3 * R; v.w = v.s + 3 * R;
+    v.di = v.w + 3 * R;
+    v.rp = (int *)(v.di + 9 * R);
+    const size_t vec_bytes = ((size_t)R * 27 * sizeof(T) + (size_t)(R + 1) * sizeof(int) + 15) / 16 * 16;
+    v.b_begin = v.nrow ? a.row_ptr[row0] : 0;
+    v.nnz = v.nrow ? a.row_ptr[row0 + v.nrow] - v.b_begin : 0;
+    const size_t mat_bytes = ((size_t)v.nnz * (9 * sizeof(T) + sizeof(int)) + 15) / 16 * 16;
+    v.cached = vec_bytes + mat_bytes <= (size_t)smem_bytes;
+    v.gathered = v.cached && vec_bytes + mat_bytes + (size_t)v.nnz * 3 * sizeof(T) <= (size_t)smem_bytes;
+    v.val = (T *)(smem + vec_bytes);
+    v.col = (int *)(v.val + (size_t)9 * v.nnz);
+    v.gu = (T *)(smem + vec_bytes + mat_bytes);
+    // load the block's rows (x = 0, r, u = M^-1 r and M^-1 from the setup kernel; p = s = 0)
+    for (int i = threadIdx.x; i < 3 * v.nrow; i += blockDim.x) {
+        v.x[i] = a.x[row0 * 3 + i];
+        v.r[i] = a.r[row0 * 3 + i];
+        v.u[i] = a.z[row0 * 3 + i];
+        v.p[i] = T(0);
+        v.s[i] = T(0);
     }
-    for (int i = threadIdx.x; i < 9 * nrow; i += blockDim.x) sdi[i] = a.dinv[row0 * 9 + i];
-    for (int i = threadIdx.x; i <= nrow; i += blockDim.x) {
-        srp[i] = a.row_ptr[row0 + i] - b_begin;
-        if (TTIE_BAD(ds, srp[i] >= 0 && srp[i] <= nnz, 43, srp[i])) srp[i] = 0;
+    for (int i = threadIdx.x; i < 9 * v.nrow; i += blockDim.x) v.di[i] = a.dinv[row0 * 9 + i];
+    for (int i = threadIdx.x; i <= v.nrow; i += blockDim.x) {
+        v.rp[i] = a.row_ptr[row0 + i] - v.b_begin;
+        if (TTIE_BAD(ds, v.rp[i] >= 0 && v.rp[i] <= v.nnz, 43, v.rp[i])) v.rp[i] = 0;
     }
-    if (cached) {
-        for (int i = threadIdx.x; i < 9 * nnz; i += blockDim.x) sval[i] = a.bval[(size_t)b_begin * 9 + i];
-        for (int i = threadIdx.x; i < nnz; i += blockDim.x) scol[i] = a.col_idx[b_begin + i];
+    if (threadIdx.x < kMaxGridPcg / 32) s_bits[threadIdx.x] = 0u;
+    __syncthreads();
+    // the blocks whose rows this block's columns read
+    for (int i = threadIdx.x; i < v.nnz; i += blockDim.x) {
+        int c = a.col_idx[v.b_begin + i];
+        if (TTIE_BAD(ds, c >= 0 && (long long)c < nr, 44, c)) c = 0;
+        if (v.cached) {
+            for (int k = 0; k < 9; ++k) v.val[(size_t)i * 9 + k] = a.bval[(size_t)(v.b_begin + i) * 9 + k];
+            v.col[i] = c;
+        }
+        const int owner = c / R;
+        if (owner != (int)blockIdx.x) atomicOr(&s_bits[owner >> 5], 1u << (owner & 31));
     }
     __syncthreads();
-    for (int lr = threadIdx.x; lr < nrow; lr += blockDim.x) {   // publish z for the first product
+    if (threadIdx.x == 0) {
+        int n = 0;
+        for (int b = 0; b < (int)gridDim.x; ++b)
+            if (s_bits[b >> 5] >> (b & 31) & 1u) {
+                if (n < kMaxDeps) s_dep[n] = b;
+                ++n;
+            }
+        s_ndep = n <= kMaxDeps ? n : -1;
+    }
+    // publish u for the first product
+    for (int lr = threadIdx.x; lr < v.nrow; lr += blockDim.x) {
         vec4_t<T> z4;
-        z4.x = sz[lr * 3]; z4.y = sz[lr * 3 + 1]; z4.z = sz[lr * 3 + 2]; z4.w = T(0);
+        z4.x = v.u[lr * 3]; z4.y = v.u[lr * 3 + 1]; z4.z = v.u[lr * 3 + 2]; z4.w = T(0);
         a.z4[row0 + lr] = z4;
     }
-    {
-        double dummy[1] = {0.0};
-        if (!grid_allreduce<1>(dummy, a.partB, ds)) return;
+    __syncthreads();
+    unsigned long long fe = epoch0 + 1, re = epoch0;
+    if (threadIdx.x == 0) {
+        __threadfence();
+        st_relaxed_u64(&a.flags[blockIdx.x], fe);
     }
     const T mu = (T)ds->mu;
-    const double rr0 = ds->red[1];
-    double rz = ds->red[0], rr = rr0;
-    double v1[1] = {resident_direction(a, srp, sval, scol, cached, b_begin, row0, nrow, sz, sp, sq, mu, T(0), true)};
-    if (!grid_allreduce<1>(v1, a.partA, ds)) return;
+    // local r.u and r.r of the current residual (thread per row)
+    Acc<T> gl, rl;
+    for (int lr = threadIdx.x; lr < v.nrow; lr += blockDim.x)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            gl.add_prod(v.r[lr * 3 + i], v.u[lr * 3 + i]);
+            rl.add_prod(v.r[lr * 3 + i], v.r[lr * 3 + i]);
+        }
+    // the recurrence's scalars, kept and decided by thread 0 of each block (identical inputs,
+    // identical decisions) and broadcast through shared memory
+    Acc<T> gamma, rr;
+    T rr0 = T(0), gamma_prev = T(1), alpha_prev = T(1);
+    const T rtol2 = (T)a.rtol2;
+    bool stop_next = false;
     int it = 0;
-    for (; it < a.max_it; ++it) {
-        const double pq = v1[0];
-        const bool ok = pq > 0.0 && isfinite(pq);
-        // breakdown at the first iteration keeps x = p = M^-1 r0 (preconditioned gradient)
-        const T alpha = (T)(ok ? rz / pq : (it == 0 ? 1.0 : 0.0));
-        double v2[2] = {0.0, 0.0};
-        for (int lr = threadIdx.x; lr < nrow; lr += blockDim.x) {
+    auto decide = [&](const Acc<T> *t) {
+        gamma = t[0];
+        rr = t[2];
+        const T g = gamma.approx(), d = t[1].approx(), r2 = rr.approx();
+        if (it == 0) rr0 = r2;
+        int stop = (stop_next || it >= a.max_it || r2 <= rtol2 * rr0 || !isfinite(r2)) ? 1 : 0;
+        T alpha = T(0), beta = T(0);
+        if (!stop) {
+            bool ok;
+            if (it == 0) {
+                alpha = g / d;
+                ok = d > T(0) && isfinite(alpha);
+            } else {
+                // den = delta - beta gamma / alpha_prev in the accumulator's precision
+                beta = g / gamma_prev;
+                const T den = t[1].minus(gamma.over(alpha_prev).times(beta)).approx();
+                alpha = g / den;
+                ok = den > T(0) && isfinite(alpha);
+            }
+            if (!ok) {
+                if (it > 0) stop = 1;
+                alpha = T(1);      // breakdown at the first step keeps x = M^-1 r0 (preconditioned gradient)
+                beta = T(0);
+                stop_next = true;
+            }
+        }
+        gamma_prev = g;
+        alpha_prev = alpha;
+        s_alpha = alpha;
+        s_beta = beta;
+        s_stop = stop;
+    };
+    while (true) {
+        if (!wait_flags(a.flags, s_dep, s_ndep, fe, ds)) return;
+        Acc<T> red[3] = {gl, resident_product(a, v, mu), rl};
+        if (!slot_allreduce<3, T>(red, a.slots, ++re, ds, decide)) return;
+        if (s_stop) break;
+        const T al = s_alpha, be = s_beta;
+        gl = Acc<T>();
+        rl = Acc<T>();
+        for (int lr = threadIdx.x; lr < v.nrow; lr += blockDim.x) {
             T rv[3];
 #pragma unroll
             for (int i = 0; i < 3; ++i) {
-                sx[lr * 3 + i] += alpha * sp[lr * 3 + i];
-                rv[i] = sr[lr * 3 + i] - alpha * sq[lr * 3 + i];
-                sr[lr * 3 + i] = rv[i];
+                const int k = lr * 3 + i;
+                const T pi = v.u[k] + be * v.p[k];
+                const T si = v.w[k] + be * v.s[k];
+                v.p[k] = pi;
+                v.s[k] = si;
+                v.x[k] += al * pi;
+                rv[i] = v.r[k] - al * si;
+                v.r[k] = rv[i];
             }
-            const T *di = sdi + lr * 9;
+            const T *di = v.di + lr * 9;
+            vec4_t<T> z4;
             T zv[3];
 #pragma unroll
             for (int i = 0; i < 3; ++i) {
-                const T zi = di[3 * i] * rv[0] + di[3 * i + 1] * rv[1] + di[3 * i + 2] * rv[2];
-                zv[i] = zi;
-                sz[lr * 3 + i] = zi;
-                v2[0] += (double)rv[i] * zi;
-                v2[1] += (double)rv[i] * rv[i];
+                zv[i] = di[3 * i] * rv[0] + di[3 * i + 1] * rv[1] + di[3 * i + 2] * rv[2];
+                v.u[lr * 3 + i] = zv[i];
+                gl.add_prod(rv[i], zv[i]);
+                rl.add_prod(rv[i], rv[i]);
             }
-            vec4_t<T> z4;
             z4.x = zv[0]; z4.y = zv[1]; z4.z = zv[2]; z4.w = T(0);
             a.z4[row0 + lr] = z4;
         }
-        if (!grid_allreduce<2>(v2, a.partB, ds)) return;
-        if (!ok) { ++it; break; }
-        const double beta = rz != 0.0 ? v2[0] / rz : 0.0;
-        rz = v2[0];
-        rr = v2[1];
-        if (rr <= a.rtol2 * rr0 || !isfinite(rr)) { ++it; break; }
-        v1[0] = resident_direction(a, srp, sval, scol, cached, b_begin, row0, nrow, sz, sp, sq, mu, (T)beta, false);
-        if (!grid_allreduce<1>(v1, a.partA, ds)) return;
+        ++it;
+        __syncthreads();
+        ++fe;
+        if (threadIdx.x == 0) {
+            __threadfence();
+            st_relaxed_u64(&a.flags[blockIdx.x], fe);
+        }
     }
-    __syncthreads();
-    for (int i = threadIdx.x; i < 3 * nrow; i += blockDim.x) a.x[row0 * 3 + i] = sx[i];
+    for (int i = threadIdx.x; i < 3 * v.nrow; i += blockDim.x) a.x[row0 * 3 + i] = v.x[i];
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         ds->pcg_iters = it;
-        ds->red[0] = rz;
-        ds->red[4] = rr;
+        ds->red[0] = gamma.value();
+        ds->red[1] = (double)rr0;
+        ds->red[4] = rr.value();
         ds->pcg_done = 1;
     }
 }
@@ -929,21 +1257,30 @@ cudaError_t pcg_solve(Ctx &c, const T *rhs, T *out, double rtol, int max_it) {
     args.max_it = max_it;
     args.ds = c.ds;
     const int sms = c.num_sms > 0 ? c.num_sms : kNumSMs;
-    // one block per SM at most: fewer arrivals per grid barrier
+    // one block per SM at most: fewer participants in every reduction
     int64_t blocks = (nr * kLanesPerRow + kPcgThreads - 1) / kPcgThreads;
     if (blocks > (int64_t)sms) blocks = sms;
+    if (blocks > kMaxGridPcg) blocks = kMaxGridPcg;
     if (blocks < 1) blocks = 1;
     // rows resident in shared memory when a block's vectors fit; else the global-memory kernel
     const int64_t rows_per_block = (nr + blocks - 1) / blocks;
-    const size_t vec_bytes = ((size_t)rows_per_block * 24 * sizeof(T) + (size_t)(rows_per_block + 1) * 4 + 15) / 16 * 16;
+    const size_t vec_bytes = ((size_t)rows_per_block * 27 * sizeof(T) + (size_t)(rows_per_block + 1) * 4 + 15) / 16 * 16;
     const bool resident = vec_bytes <= (size_t)kResidentSmem;
+    if (!c.pcg_sync.p) {   // fixed size, zeroed once: epochs only grow over the context's life
+        TTIE_CUDA_TRY(ensure(c, c.pcg_sync, (size_t)kMaxGridPcg * (2 * sizeof(RedSlot) + sizeof(unsigned long long))));
+        TTIE_CUDA_TRY(cudaMemsetAsync(c.pcg_sync.p, 0, c.pcg_sync.bytes, c.stream));
+    }
+    args.slots = (RedSlot *)c.pcg_sync.p;
+    args.flags = (unsigned long long *)((RedSlot *)c.pcg_sync.p + 2 * kMaxGridPcg);
+    c.pcg_epoch += 1ull << 32;
     ++c.n_launch;
     if (c.prm.profile) cudaEventRecord(c.ev[8], c.stream);
     if (resident) {
         TTIE_CUDA_TRY(cudaFuncSetAttribute((const void *)k_pcg_resident<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            kResidentSmem));
         int rpb = (int)rows_per_block, smem = kResidentSmem;
-        void *kargs[] = {&args, &rpb, &smem};
+        unsigned long long e0 = c.pcg_epoch;
+        void *kargs[] = {&args, &rpb, &smem, &e0};
         TTIE_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)k_pcg_resident<T>, dim3((unsigned)blocks),
                                                   dim3(kPcgThreads), kargs, (size_t)kResidentSmem, c.stream));
     } else {

@@ -91,7 +91,7 @@ cudaError_t ensure(Ctx &c, Buf &b, size_t bytes);   // grow-only, contents not k
     X(defer) X(active) X(fac) X(partials) X(vflag) X(vrow) X(row_vertex) X(bkey) X(bkey2)   \
     X(bval) X(bval2) X(bflag) X(run_start) X(row_ptr) X(col_idx) X(bsr_val) X(rhs)         \
     X(zfac) X(dinv) X(pcg_x) X(pcg_r) X(pcg_z) X(pcg_p) X(pcg_q) X(dir) X(xt) X(gtmp)      \
-    X(xsave) X(sweep_cand) X(pcg_z4) X(hbuf)
+    X(xsave) X(sweep_cand) X(pcg_z4) X(hbuf) X(pcg_sync)
 
 struct Ctx {
     ttie_params prm;
@@ -125,6 +125,7 @@ struct Ctx {
     int num_sms = 0;
     unsigned long long n_launch = 0;   // kernels launched through this context
     bool time_kernels = false;         // profile: events around the classification / PCG kernels
+    unsigned long long pcg_epoch = 0;  // resident PCG: epochs of its flags and slots (grow only)
 };
 
 // Every kernel of the library is launched through this helper on the context's
