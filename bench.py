@@ -202,6 +202,7 @@ def main():
     ap.add_argument("--workload", default="cloth256")
     ap.add_argument("--no-solve", action="store_true", help="skip the time-to-intersection-free run")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64-form", action="store_true", help="skip the plain FP64 comparison")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -313,6 +314,36 @@ def main():
                       "peak_source": "measured" if hbm else "fallback", "frac": cl_ach / peak if cl_ach else None,
                       "traffic": NCU_TRAFFIC.get(args.workload, {}).get("k_classify"), "ms_per_launch": k_ms, "algorithmic_bytes_per_launch": 104.0 * n_cand}
 
+    # the plain FP64 form on the same GPU: every stage in double precision (same kernels
+    # instantiated for FP64), a few steps of the same workload
+    fp64 = None
+    if precision == 0 and not args.no_fp64_form and rank == 0:
+        x64_0 = torch.tensor(m.x, dtype=torch.float64, device="cuda")
+        x64 = x64_0.clone()
+        ctx64 = ttie.Context(precision=ttie.F64, profile=1)
+        ctx64.build_bvh(x64_0, tri)
+        n64 = max(3, min(args.steps, 10))
+        for _ in range(args.warmup):
+            x64.copy_(x64_0)
+            ctx64.newton_step(x64)
+        ms64, pairs64, stage64 = 0.0, 0, {k: 0.0 for k in stage}
+        for _ in range(n64):
+            x64.copy_(x64_0)
+            flush.zero_()
+            ev0.record(stream)
+            i64 = ctx64.newton_step(x64)
+            ev1.record(stream)
+            ev1.synchronize()
+            ms64 += ev0.elapsed_time(ev1)
+            pairs64 += i64["n_candidates"]
+            for k in stage64:
+                stage64[k] += i64["ms_" + k]
+        fp64 = {"value": pairs64 / (ms64 / 1e3), "unit": UNIT, "ms_per_step": ms64 / n64, "steps": n64,
+                "dtype": "f64", "pcg_iters": i64["pcg_iters"], "intersecting_per_step": i64["n_active"],
+                "stage_ms_per_step": {k: v / n64 for k, v in stage64.items()},
+                "speedup_of_fp32_form": (ms64 / n64) / (total_ms / args.steps)}
+        ctx64.close()
+
     solve = None
     if not args.no_solve and rank == 0:
         xs = x0.clone()
@@ -346,6 +377,7 @@ def main():
             "roofline": roofline,
             "roofline_pair_eval": roofline_pairs,
             "cpu_baseline": cpu,
+            "fp64_form": fp64,
             "e2e": {"value": e2e_pairs / (e2e_ms / 1e3) if e2e_ms > 0 else None, "unit": UNIT,
                     "h2d_bytes_per_step": e2e_bytes, "d2h_bytes_per_step": e2e_bytes},
             "gpu_launches": launches,

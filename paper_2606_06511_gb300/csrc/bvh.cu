@@ -3,9 +3,14 @@
 // §1.2 accelerates the pair tests with a spatial structure that "eliminates
 // redundant computations" (spatial hashing there).  Here: a linear BVH built
 // from 63-bit Morton codes (Karras' radix-tree construction), refitted
-// bottom-up, then traversed once per leaf to count and once to write, so the
-// pair list comes out in a deterministic order without a global sort.
-// Topologically adjacent pairs (a shared vertex index, §1) are dropped.
+// bottom-up, then traversed without a stack: every node stores its left child
+// and its "rope" (the next node of a depth-first walk once its subtree is done),
+// which in a Karras tree follows from the node's leaf range alone.  One pass
+// counts each leaf's partners and keeps the first kSpill of them; offsets come
+// from a scan, the kept pairs are copied out, and only leaves with more partners
+// are walked again.  The pair list comes out in a deterministic order (leaf
+// order, then depth-first order) without a global sort.  Topologically adjacent
+// pairs (a shared vertex index, §1) are dropped.
 #include "common.cuh"
 
 namespace ttie {
@@ -13,7 +18,8 @@ namespace ttie {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kStack = 96;
+constexpr int kStack = 96;    // bound on the refit's climb (tree depth) before it reports a malformed tree
+constexpr int kSpill = 16;    // partners kept per leaf by the counting pass
 
 __device__ __forceinline__ unsigned long long ordered_bits(double v) {
     unsigned long long u = (unsigned long long)__double_as_longlong(v);
@@ -268,17 +274,48 @@ __device__ __forceinline__ bool share_vertex(int4 a, int4 b) {
            a.z == b.y || a.z == b.z;
 }
 
-// One thread per leaf s: every leaf s' > s in the pair-mode window whose box overlaps.
-template <typename T, bool kWrite>
-__global__ void __launch_bounds__(kThreads) k_traverse(int n, const int2 *__restrict__ child, const int2 *__restrict__ range,
+// Links stored in the unused w lanes of the node boxes: lo.w = left child (-1 for a leaf),
+// hi.w = rope.  A node covering leaves [lo, hi] is followed, once its subtree is done, by the
+// right sibling of its lowest ancestor-or-self that is a left child; that sibling covers a range
+// starting at hi + 1 and is internal node hi + 1 when that node's range starts there (in a
+// Karras tree internal node k has k as one end of its range), else leaf hi + 1.
+template <typename T> __device__ __forceinline__ void set_link(T &w, int v);
+template <> __device__ __forceinline__ void set_link<float>(float &w, int v) { w = __int_as_float(v); }
+template <> __device__ __forceinline__ void set_link<double>(double &w, int v) { w = __longlong_as_double((long long)v); }
+template <typename T> __device__ __forceinline__ int get_link(T w);
+template <> __device__ __forceinline__ int get_link<float>(float w) { return __float_as_int(w); }
+template <> __device__ __forceinline__ int get_link<double>(double w) { return (int)__double_as_longlong(w); }
+
+template <typename T>
+__global__ void k_links(int n, const int2 *__restrict__ child, const int2 *__restrict__ range, Box<T> *node_box) {
+    const int nodes = 2 * n - 1;
+    for (int node = blockIdx.x * blockDim.x + threadIdx.x; node < nodes; node += gridDim.x * blockDim.x) {
+        const int2 r = range[node];
+        int rope = -1;
+        if (r.y < n - 1) {
+            const int k = r.y + 1;
+            rope = (k < n - 1 && range[k].x == k) ? k : n - 1 + k;
+        }
+        set_link<T>(node_box[node].lo.w, node < n - 1 ? child[node].x : -1);
+        set_link<T>(node_box[node].hi.w, rope);
+    }
+}
+
+// One thread per leaf s: every leaf s' > s in the pair-mode window whose box overlaps, in
+// depth-first order.  kPass 0 counts them and keeps the first kSpill in spill[s]; kPass 1
+// writes all of them at offset[s], for the leaves with more than kSpill.
+template <typename T, int kPass>
+__global__ void __launch_bounds__(kThreads) k_traverse(int n, const int2 *__restrict__ range,
                                                        const Box<T> *__restrict__ node_box,
                                                        const uint32_t *__restrict__ perm, const int4 *__restrict__ tri4,
                                                        const int32_t *__restrict__ leaf_group,
                                                        const int2 *__restrict__ group_range, int mode,
                                                        uint32_t *__restrict__ count,
                                                        const unsigned long long *__restrict__ offset,
-                                                       int2 *__restrict__ pairs, DevScalars *ds) {
+                                                       int2 *__restrict__ spill, int2 *__restrict__ pairs,
+                                                       DevScalars *ds) {
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
+        if (kPass == 1 && count[s] <= (uint32_t)kSpill) continue;
         int lo = s + 1, hi = n - 1;
         if (mode == TTIE_PAIRS_INTRA_GROUP) {
             hi = group_range[leaf_group[s]].y;
@@ -286,41 +323,51 @@ __global__ void __launch_bounds__(kThreads) k_traverse(int n, const int2 *__rest
             lo = max(lo, group_range[leaf_group[s]].y + 1);
         }
         uint32_t cnt = 0;
-        unsigned long long out = kWrite ? offset[s] : 0ull;
+        const unsigned long long out = kPass == 1 ? offset[s] : 0ull;
         if (lo <= hi) {
             const uint32_t qi = perm[s];
             const int4 tq = tri4[qi];
             const Box<T> qb = node_box[n - 1 + s];
-            int stack[kStack];
-            int sp = 0;
-            stack[sp++] = 0;
-            while (sp > 0) {
-                const int node = stack[--sp];
-                const int2 r = range[node];
-                if (r.y < lo || r.x > hi) continue;
-                const Box<T> nb = node_box[node];
-                if (!overlap<T>(qb.lo, qb.hi, nb.lo, nb.hi)) continue;
-                if (node >= n - 1) {
-                    const uint32_t tj = perm[node - (n - 1)];
-                    if (share_vertex(tq, tri4[tj])) continue;
-                    if (kWrite) {
-                        if (TTIE_BAD(ds, out + cnt < offset[s + 1], 61, out + cnt)) continue;
-                        pairs[out + cnt] = make_int2((int)min(qi, tj), (int)max(qi, tj));
-                    }
-                    ++cnt;
-                } else {
-                    if (sp + 2 > kStack) {
-                        atomicOr(&ds->err, ERR_STACK);
-                        sp = 0;
-                        break;
-                    }
-                    const int2 ch = child[node];
-                    stack[sp++] = ch.y;
-                    stack[sp++] = ch.x;
+            int node = 0;
+            for (int steps = 0; node >= 0; ++steps) {
+                if (steps > 2 * n) {   // a walk visits every node at most once: malformed links
+                    atomicOr(&ds->err, ERR_STACK);
+                    break;
                 }
+                const Box<T> nb = node_box[node];
+                const int2 r = range[node];
+                int next = get_link<T>(nb.hi.w);
+                if (r.y >= lo && r.x <= hi && overlap<T>(qb.lo, qb.hi, nb.lo, nb.hi)) {
+                    const int left = get_link<T>(nb.lo.w);
+                    if (left >= 0) {
+                        next = left;
+                    } else {
+                        const uint32_t tj = perm[node - (n - 1)];
+                        if (!share_vertex(tq, tri4[tj])) {
+                            const int2 pr = make_int2((int)min(qi, tj), (int)max(qi, tj));
+                            if (kPass == 0) {
+                                if (cnt < (uint32_t)kSpill) spill[(size_t)s * kSpill + cnt] = pr;
+                            } else if (!TTIE_BAD(ds, out + cnt < offset[s + 1], 61, out + cnt)) {
+                                pairs[out + cnt] = pr;
+                            }
+                            ++cnt;
+                        }
+                    }
+                }
+                node = next;
             }
         }
-        if (!kWrite) count[s] = cnt;
+        if (kPass == 0) count[s] = cnt;
+    }
+}
+
+// Copy the kept partners of every leaf to its place in the pair list.
+__global__ void k_spill_copy(int n, const uint32_t *__restrict__ count, const unsigned long long *__restrict__ offset,
+                             const int2 *__restrict__ spill, int2 *__restrict__ pairs) {
+    const long long total = (long long)n * kSpill;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+        const int s = (int)(i / kSpill), k = (int)(i - (long long)s * kSpill);
+        if ((uint32_t)k < min(count[s], (uint32_t)kSpill)) pairs[offset[s] + k] = spill[i];
     }
 }
 
@@ -366,7 +413,7 @@ static int mode_of(const Ctx &c) { return c.prm.pair_mode & 3; }
 
 template <typename T>
 cudaError_t build_candidates(Ctx &c, const vec4_t<T> *x0, const vec4_t<T> *x1, Buf &out_pairs, int64_t *n_out,
-                             int64_t cap) {
+                             int64_t cap, bool refit_only) {
     const int n = (int)c.F;
     const int mode = mode_of(c);
     *n_out = 0;
@@ -393,32 +440,42 @@ cudaError_t build_candidates(Ctx &c, const vec4_t<T> *x0, const vec4_t<T> *x1, B
     auto *perm = (uint32_t *)c.perm.p;
     const unsigned g = grid_for(n, kThreads);
 
-    launch(c, k_init_bounds, dim3(1), dim3(32), c.ds);
-    launch(c, k_tri_boxes<T>, dim3(g), dim3(kThreads), x0, x1, (const int4 *)c.tri4.p, n, tbox, c.ds);
-    const int gbits = grouped ? c.group_bits : 0;
-    launch(c, k_morton<T>, dim3(g), dim3(kThreads), tbox, n, (const int32_t *)c.grp.p, gbits, c.ds, key, perm);
-    TTIE_CUDA_TRY(cudaGetLastError());
-    const int key_bits = 3 * ((63 - gbits) / 3) + gbits;
-    TTIE_CUDA_TRY(radix_sort(c, key, perm, (unsigned long long *)c.mkey2.p, (uint32_t *)c.perm2.p, n, key_bits));
-    if (grouped) {
-        launch(c, k_leaf_group, dim3(g), dim3(kThreads), perm, (const int32_t *)c.grp.p, n, (int32_t *)c.leaf_group.p);
-        launch(c, k_fill_int2, dim3(grid_for(c.n_groups, kThreads)), dim3(kThreads), (int2 *)c.group_range.p, c.n_groups,
-                                                                              make_int2(1, 0));
-        launch(c, k_group_ranges, dim3(g), dim3(kThreads), (const int32_t *)c.leaf_group.p, n, (int2 *)c.group_range.p);
-    }
     int2 *child = (int2 *)c.node_child.p;
     int *parent = (int *)c.node_parent.p;
     int2 *range = (int2 *)c.node_range.p;
     Box<T> *nbox = (Box<T> *)c.node_box.p;
-    launch(c, k_karras, dim3(grid_for(n - 1, kThreads)), dim3(kThreads), key, n, child, parent, range);
+    if (!refit_only) c.tree_leaves = -1;
+    launch(c, k_init_bounds, dim3(1), dim3(32), c.ds);
+    launch(c, k_tri_boxes<T>, dim3(g), dim3(kThreads), x0, x1, (const int4 *)c.tri4.p, n, tbox, c.ds);
+    if (!(refit_only && c.tree_leaves == n)) {
+        const int gbits = grouped ? c.group_bits : 0;
+        launch(c, k_morton<T>, dim3(g), dim3(kThreads), tbox, n, (const int32_t *)c.grp.p, gbits, c.ds, key, perm);
+        TTIE_CUDA_TRY(cudaGetLastError());
+        const int key_bits = 3 * ((63 - gbits) / 3) + gbits;
+        TTIE_CUDA_TRY(radix_sort(c, key, perm, (unsigned long long *)c.mkey2.p, (uint32_t *)c.perm2.p, n, key_bits));
+        if (grouped) {
+            launch(c, k_leaf_group, dim3(g), dim3(kThreads), perm, (const int32_t *)c.grp.p, n, (int32_t *)c.leaf_group.p);
+            launch(c, k_fill_int2, dim3(grid_for(c.n_groups, kThreads)), dim3(kThreads), (int2 *)c.group_range.p,
+                   c.n_groups, make_int2(1, 0));
+            launch(c, k_group_ranges, dim3(g), dim3(kThreads), (const int32_t *)c.leaf_group.p, n,
+                   (int2 *)c.group_range.p);
+        }
+        launch(c, k_karras, dim3(grid_for(n - 1, kThreads)), dim3(kThreads), key, n, child, parent, range);
+        c.tree_leaves = n;
+    }
+    // a refit-only build keeps the hierarchy (and leaf order) of the last full build: any
+    // hierarchy over the new boxes yields the same overlapping pairs
     launch(c, k_leaf_boxes<T>, dim3(g), dim3(kThreads), tbox, perm, n, nbox, range);
     TTIE_CUDA_TRY(cudaMemsetAsync(c.visit.p, 0, (size_t)(n - 1) * sizeof(unsigned int), c.stream));
     launch(c, k_refit<T>, dim3(g), dim3(kThreads), n, parent, child, nbox, (unsigned int *)c.visit.p, c.ds);
+    launch(c, k_links<T>, dim3(grid_for(2 * (int64_t)n - 1, kThreads)), dim3(kThreads), n, (const int2 *)child,
+           (const int2 *)range, nbox);
     auto *cnt = (uint32_t *)c.cand_cnt.p;
     auto *off = (unsigned long long *)c.cand_off.p;
-    launch(c, k_traverse<T, false>, dim3(g), dim3(kThreads), n, child, range, nbox, perm, (const int4 *)c.tri4.p,
-                                                       (const int32_t *)c.leaf_group.p, (const int2 *)c.group_range.p,
-                                                       mode, cnt, nullptr, nullptr, c.ds);
+    TTIE_CUDA_TRY(ensure(c, c.spill, (size_t)n * kSpill * sizeof(int2)));
+    launch(c, k_traverse<T, 0>, dim3(g), dim3(kThreads), n, (const int2 *)range, (const Box<T> *)nbox, (const uint32_t *)perm,
+           (const int4 *)c.tri4.p, (const int32_t *)c.leaf_group.p, (const int2 *)c.group_range.p, mode, cnt,
+           (const unsigned long long *)nullptr, (int2 *)c.spill.p, (int2 *)nullptr, c.ds);
     TTIE_CUDA_TRY(cudaGetLastError());
     TTIE_CUDA_TRY(scan_u32_u64(c, cnt, off, n));
     unsigned long long total = 0;
@@ -430,16 +487,19 @@ cudaError_t build_candidates(Ctx &c, const vec4_t<T> *x0, const vec4_t<T> *x1, B
         return cudaSuccess;
     }
     TTIE_CUDA_TRY(ensure(c, out_pairs, (size_t)(total > 0 ? total : 1) * sizeof(int2)));
-    if (total > 0)
-        launch(c, k_traverse<T, true>, dim3(g), dim3(kThreads), n, child, range, nbox, perm, (const int4 *)c.tri4.p,
-                                                          (const int32_t *)c.leaf_group.p,
-                                                          (const int2 *)c.group_range.p, mode, nullptr, off,
-                                                          (int2 *)out_pairs.p, c.ds);
+    if (total > 0) {
+        launch(c, k_spill_copy, dim3(grid_for((int64_t)n * kSpill, kThreads)), dim3(kThreads), n, (const uint32_t *)cnt,
+               (const unsigned long long *)off, (const int2 *)c.spill.p, (int2 *)out_pairs.p);
+        launch(c, k_traverse<T, 1>, dim3(g), dim3(kThreads), n, (const int2 *)range, (const Box<T> *)nbox,
+               (const uint32_t *)perm, (const int4 *)c.tri4.p, (const int32_t *)c.leaf_group.p,
+               (const int2 *)c.group_range.p, mode, cnt, (const unsigned long long *)off, (int2 *)nullptr,
+               (int2 *)out_pairs.p, c.ds);
+    }
     *n_out = (int64_t)total;
     return cudaGetLastError();
 }
-template cudaError_t build_candidates<float>(Ctx &, const float4 *, const float4 *, Buf &, int64_t *, int64_t);
-template cudaError_t build_candidates<double>(Ctx &, const dvec4 *, const dvec4 *, Buf &, int64_t *, int64_t);
+template cudaError_t build_candidates<float>(Ctx &, const float4 *, const float4 *, Buf &, int64_t *, int64_t, bool);
+template cudaError_t build_candidates<double>(Ctx &, const dvec4 *, const dvec4 *, Buf &, int64_t *, int64_t, bool);
 
 namespace {
 // Per-block sums of edge lengths, then one block adds the block sums in order.

@@ -398,7 +398,7 @@ static ttie_status newton_impl(Ctx &c, T *x, ttie_step_info *info) {
         for (int tries = 0;; ++tries) {
             CK(axpy_positions<T>(c, (const vec4_t<T> *)c.xp.p, (const T *)c.dir.p, (T)a_max, (vec4_t<T> *)c.xq.p), "newton");
             CK(build_candidates<T>(c, (const vec4_t<T> *)c.xp.p, (const vec4_t<T> *)c.xq.p, c.sweep_cand, &ns,
-                                   cand_cap(c)), "newton: sweep");
+                                   cand_cap(c), true), "newton: sweep");
             if (ns <= cand_cap(c)) break;
             if (tries >= 12)
                 return set_err(c, TTIE_ERR_CAPACITY, "ttie_newton_step: swept candidates %lld exceed max_candidates",

@@ -91,7 +91,7 @@ cudaError_t ensure(Ctx &c, Buf &b, size_t bytes);   // grow-only, contents not k
     X(defer) X(active) X(fac) X(partials) X(vflag) X(vrow) X(row_vertex) X(bkey) X(bkey2)   \
     X(bval) X(bval2) X(bflag) X(run_start) X(row_ptr) X(col_idx) X(bsr_val) X(rhs)         \
     X(zfac) X(dinv) X(pcg_x) X(pcg_r) X(pcg_z) X(pcg_p) X(pcg_q) X(dir) X(xt) X(gtmp)      \
-    X(xsave) X(sweep_cand) X(pcg_z4) X(hbuf) X(pcg_sync)
+    X(xsave) X(sweep_cand) X(pcg_z4) X(hbuf) X(pcg_sync) X(spill)
 
 struct Ctx {
     ttie_params prm;
@@ -126,6 +126,7 @@ struct Ctx {
     unsigned long long n_launch = 0;   // kernels launched through this context
     bool time_kernels = false;         // profile: events around the classification / PCG kernels
     unsigned long long pcg_epoch = 0;  // resident PCG: epochs of its flags and slots (grow only)
+    int64_t tree_leaves = -1;          // leaves of the hierarchy in the BVH buffers (-1: none)
 };
 
 // Every kernel of the library is launched through this helper on the context's
@@ -176,8 +177,11 @@ template <typename T> cudaError_t pack_positions(Ctx &c, const T *x, int stride,
 cudaError_t pack_topology(Ctx &c, const int32_t *tri, const int32_t *group);
 // Candidate pairs whose boxes (over x0, or swept from x0 to x1) overlap.  When the count
 // exceeds `cap` nothing is written and *n_out receives the count.
+// refit_only: keep the hierarchy of the last full build of this mesh (the line search's swept
+// boxes reuse the tree built at x) and only refit it to the new boxes.
 template <typename T> cudaError_t build_candidates(Ctx &c, const vec4_t<T> *x0, const vec4_t<T> *x1,
-                                                   Buf &out_pairs, int64_t *n_out, int64_t cap);
+                                                   Buf &out_pairs, int64_t *n_out, int64_t cap,
+                                                   bool refit_only = false);
 cudaError_t brute_candidates(Ctx &c, Buf &out_pairs, int64_t *n_out);
 template <typename T> cudaError_t mean_edge_length(Ctx &c, const vec4_t<T> *x, double *out_dev);
 
