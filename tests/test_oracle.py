@@ -489,3 +489,20 @@ def test_psd_whole_and_drop_cross_projections():
         assert np.linalg.eigvalsh(D).min() >= -1e-12 * s
         assert np.abs(Hw[k] @ D).max() <= 1e-10 * s * s
         assert np.linalg.matrix_rank(Hw[k], tol=1e-9 * s) == 1
+
+
+def test_energy_jumps_at_vertex_face_contact():
+    """Eq. 1-2 measure the overlap of the two intervals on the planes' common line, not a depth:
+    when a vertex of A passes through the interior of B, A's interval is born as a point inside
+    B's interval, so T jumps from 0 to about (half the chord of B)^4 instead of growing from 0.
+    T is smooth inside the intersecting set but not continuous across this part of its border
+    (it is continuous where the intervals separate: t_c^0 or t_c^1 -> 0)."""
+    B = np.array([[-1.0, -1.0, 0.0], [1.5, -1.0, 0.0], [-1.0, 1.5, 0.0]])
+    tri = np.array([[0, 1, 2], [3, 4, 5]])
+    T = {}
+    for eps in [1e-9, 0.0, -1e-9, -1e-6]:
+        A = np.array([[0.0, 0.0, eps], [0.3, 0.1, 1.0], [-0.1, 0.3, 1.0]])
+        ev = O.evaluate(np.concatenate([A, B]), tri, np.array([[0, 1]]))
+        T[eps] = float(ev.T[0])
+    assert T[1e-9] == 0.0 and T[0.0] == 0.0
+    assert T[-1e-9] > 1.0 and T[-1e-6] == pytest.approx(T[-1e-9], rel=1e-5)
