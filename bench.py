@@ -34,30 +34,43 @@ L2_FLUSH_BYTES = 256 << 20   # larger than the 129 MB L2
 
 
 def workload(name):
+    """(mesh, precision, description, pair mode: 0 all pairs, 2 pairs within a group)."""
     import ttie_inputs as ti
     if name == "cloth256":
         return ti.cloth(256, seed=2).as_f32(), 0, (
             "cloth 256x256 vertices (130,050 triangles) on [0,1]^2, z = 8 seeded sinusoids "
             "(A~U[0.05,0.3], k~U[2,12]), x += 0.4*g(x,y) with g an independent 8-sinusoid field "
-            "(folds that cross themselves); self pairs, LBVH; float32")
+            "(folds that cross themselves); self pairs, LBVH; float32"), 0
     if name == "cloth256_literal":
         return ti.cloth(256, seed=2, crossing=False).as_f32(), 0, (
-            "cloth 256x256 (130,050 triangles), x += 0.4*z shear (intersection-free by construction)")
+            "cloth 256x256 (130,050 triangles), x += 0.4*z shear (intersection-free by construction)"), 0
     if name == "noisy_sphere":
         return ti.noisy_sphere(9, seed=5).as_f32(), 0, (
-            "octahedral sphere level 9 (2,097,152 triangles) displaced by 0.15*(N1,N2,N3) value noise")
+            "octahedral sphere level 9 (2,097,152 triangles) displaced by 0.15*(N1,N2,N3) value noise"), 0
+    if name == "ellipsoids512":
+        m, _, _ = ti.ellipsoid_batch(512, seed=4)
+        return m.as_f32(), 0, (
+            "512 independent pairs of lat-long ellipsoids, triangles per mesh log-uniform in [100, 20000], "
+            "semi-axes U[0.5,1.5], random relative rotation, centre offset U[0.3,1] x (sum of mean semi-axes); "
+            "pairs within an instance, each instance solved on its own (per-instance PCG blocks in one launch, "
+            "per-instance line search); float32"), 2
     raise SystemExit("unknown workload %s" % name)
 
 
-def oracle_sample(m, n_side):
-    """The workload restricted to the first n_side x n_side grid vertices (cloth) or the first
-    triangles (others): what the oracle can process in seconds."""
+def oracle_sample(m, n_side, mode=0):
+    """The workload restricted to the first n_side x n_side grid vertices (cloth), to whole
+    instances up to about 2 n_side^2 triangles (batched instances), or to the first triangles
+    (others): what the oracle can process in seconds."""
     import numpy as np
     import ttie_inputs as ti
     if m.V == 256 * 256:
         ij = np.arange(m.V)
         keep_v = ((ij % 256) < n_side) & ((ij // 256) < n_side)
         keep_t = keep_v[m.tri].all(axis=1)
+    elif mode == 2:
+        counts = np.bincount(m.group)
+        upto = max(1, int(np.searchsorted(np.cumsum(counts), 2 * n_side * n_side)))
+        keep_t = m.group < upto
     else:
         keep_t = np.zeros(m.F, bool)
         keep_t[: n_side * n_side * 2] = True
@@ -68,11 +81,11 @@ def oracle_sample(m, n_side):
     return ti.Mesh(m.x[used], remap[tri].astype(np.int32), m.group[keep_t])
 
 
-def oracle_step(sub):
+def oracle_step(sub, mode=0):
     """One pass of the oracle over the sample: brute-force candidates, per-pair evaluation
     (duals + exact test), gradient, PSD Hessian and assembly.  Returns candidate pairs."""
     import oracle as O
-    pairs = O.candidate_pairs(sub.x, sub.tri)
+    pairs = O.candidate_pairs(sub.x, sub.tri, sub.group, "instance" if mode == 2 else "self")
     ev = O.evaluate(sub.x, sub.tri, pairs)
     O.assemble(sub.tri, ev, sub.V)
     return len(pairs)
@@ -155,14 +168,14 @@ def run_reference(args, rank, world):
     """CPU oracle arm: rank 0 only."""
     if rank != 0:
         return
-    m, _, desc = workload(args.workload)
-    sub = oracle_sample(m, 24)
+    m, _, desc, mode = workload(args.workload)
+    sub = oracle_sample(m, 24, mode)
     for _ in range(args.warmup):
-        oracle_step(sub)
+        oracle_step(sub, mode)
     t0 = time.perf_counter()
     n = 0
     for _ in range(args.steps):
-        n += oracle_step(sub)
+        n += oracle_step(sub, mode)
     dt = time.perf_counter() - t0
     v = n / dt
     sample = "oracle on a 24x24-vertex patch of the workload (%d triangles, %d candidate pairs per step)" % (
@@ -177,20 +190,21 @@ def run_reference(args, rank, world):
     }), flush=True)
 
 
-def cpu_baseline(m, seconds_target=15.0):
+def cpu_baseline(m, mode=0, seconds_target=15.0):
     """Oracle throughput on a bounded sample (patch of the workload), single core."""
-    sub = oracle_sample(m, 80)
+    sub = oracle_sample(m, 80, mode)
     t0 = time.perf_counter()
     n, reps = 0, 0
     while True:
-        n += oracle_step(sub)
+        n += oracle_step(sub, mode)
         reps += 1
         if time.perf_counter() - t0 > seconds_target or reps >= 4:
             break
     dt = time.perf_counter() - t0
     return {"value": n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "oracle on an 80x80-vertex patch of the workload (%d triangles, %d candidate pairs) x %d, "
-                      "%.1f s" % (sub.F, n // reps, reps, dt)}
+            "sample": "oracle on a sample of the workload (an 80x80-vertex patch of a grid, or whole instances "
+                      "up to ~12,800 triangles; %d triangles, %d candidate pairs) x %d, %.1f s" % (
+                          sub.F, n // reps, reps, dt)}
 
 
 def main():
@@ -222,13 +236,14 @@ def main():
     __graft_entry__.build()
     from paper_2606_06511_gb300 import ttie
 
-    m, precision, desc = workload(args.workload)
+    m, precision, desc, mode = workload(args.workload)
     dt = torch.float32 if precision == 0 else torch.float64
     x0 = torch.tensor(m.x, dtype=dt, device="cuda")
     tri = torch.tensor(m.tri, dtype=torch.int32, device="cuda")
+    grp = torch.tensor(m.group, dtype=torch.int32, device="cuda") if mode else None
     x = x0.clone()
-    ctx = ttie.Context(precision=precision, profile=1)
-    ctx.build_bvh(x0, tri)
+    ctx = ttie.Context(precision=precision, pair_mode=mode, profile=1)
+    ctx.build_bvh(x0, tri, grp)
     stream = torch.cuda.current_stream()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
@@ -292,7 +307,8 @@ def main():
 
     # Rooflines (algorithmic bytes per launch / CUDA-event duration of that launch):
     # the dominant kernel is the persistent PCG: per iteration the block-CSR matrix
-    # (36 B value + 4 B column per 3x3 block) and 160 B of vector traffic per row
+    # (36 B value + 4 B column per 3x3 block) and 160 B of vector traffic per row, summed over
+    # the iterations each instance ran
     # (z read/write, p, q, x, r updates, inverse diagonal block, row offset);
     # the pair kernel is the narrow-phase classification, 104 B per candidate
     # (pair ids 8 B + 2 x (indices 12 B + coordinates 36 B)).
@@ -301,9 +317,9 @@ def main():
     peak = hbm if hbm else 6800.0
     last = infos[-1]
     pcg_ms = kern["pcg"] / args.steps
-    pcg_bytes = last["pcg_iters"] * (40.0 * last["nnzb"] + 160.0 * last["n_rows"])
+    pcg_bytes = 40.0 * last["pcg_block_iters"] + 160.0 * last["pcg_row_iters"]
     pcg_ach = pcg_bytes / (pcg_ms * 1e-3) / 1e9 if pcg_ms > 0 else None
-    roofline = {"kernel": "k_pcg_resident", "bound": "hbm", "achieved": pcg_ach, "peak": peak, "unit": "GB/s",
+    roofline = {"kernel": "k_pcg_instances" if mode == 2 else "k_pcg_resident", "bound": "hbm", "achieved": pcg_ach, "peak": peak, "unit": "GB/s",
                 "peak_source": "measured" if hbm else "fallback", "frac": pcg_ach / peak if pcg_ach else None,
                 "traffic": NCU_TRAFFIC.get(args.workload, {}).get("k_pcg_resident"), "ms_per_launch": pcg_ms, "algorithmic_bytes_per_launch": pcg_bytes,
                 "share_of_step": pcg_ms / (total_ms / args.steps)}
@@ -320,8 +336,8 @@ def main():
     if precision == 0 and not args.no_fp64_form and rank == 0:
         x64_0 = torch.tensor(m.x, dtype=torch.float64, device="cuda")
         x64 = x64_0.clone()
-        ctx64 = ttie.Context(precision=ttie.F64, profile=1)
-        ctx64.build_bvh(x64_0, tri)
+        ctx64 = ttie.Context(precision=ttie.F64, pair_mode=mode, profile=1)
+        ctx64.build_bvh(x64_0, tri, grp)
         n64 = max(3, min(args.steps, 10))
         for _ in range(args.warmup):
             x64.copy_(x64_0)
@@ -357,7 +373,7 @@ def main():
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(m)
+        cpu = cpu_baseline(m, mode)
 
     if rank == 0:
         line = {

@@ -210,6 +210,8 @@ typedef struct {
     float ms_build, ms_eval, ms_assemble, ms_pcg, ms_line_search;  /* if params.profile */
     float ms_classify;           /* classification kernel of the evaluation at x (profile) */
     float ms_pcg_kernel;         /* persistent PCG kernel (profile)                          */
+    int64_t pcg_block_iters;     /* sum over the PCG iterations of the 3x3 blocks multiplied */
+    int64_t pcg_row_iters;       /* sum over the PCG iterations of the rows updated           */
 } ttie_step_info;
 
 /*
@@ -219,6 +221,17 @@ typedef struct {
  * boxes swept between x and x + (1+push_eta) d; a trial is accepted when it
  * meets Armijo's condition or leaves no intersecting pair.  d_x_inout is
  * updated in place (unchanged when x has no intersecting pair).
+ */
+/*
+ * With pair_mode TTIE_PAIRS_INTRA_GROUP (LBVH) every group is an independent problem and one
+ * call steps all of them at once but independently: one PCG per group (one thread block per
+ * group, in a single launch; mu and the stopping test per group), the step cap per group
+ * (max_step x the group's mean edge length at ttie_build_bvh), and the line search per group
+ * (each group takes the first trial of the shared ladder that meets its own Armijo test or
+ * leaves it without intersecting pairs).  Every vertex must belong to one group and each
+ * group's vertices must be numbered contiguously (else TTIE_ERR_INVALID).  In this mode info
+ * reports alpha = the smallest accepted step, pcg_iters and pcg_rel_residual = the largest
+ * over the groups, grad_dot_dir = the sum over the groups.
  */
 ttie_status ttie_newton_step(ttie_ctx *ctx, void *d_x_inout, ttie_step_info *info);
 

@@ -17,13 +17,13 @@
 // one thread per distinct key summing its run in sorted order, so both the
 // pattern and the values are deterministic.
 #include "common.cuh"
+#include "pcg_common.cuh"
 
 namespace ttie {
 
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kFacStride = 40;   // [a, b, grad a (18), grad b (18), pad 2]
 constexpr int kZStride = 72;     // [z1 (18), z2 (18), z3 (18), g (18)]
 
 template <typename T>
@@ -270,17 +270,6 @@ __global__ void k_block_values(const unsigned long long *__restrict__ key, const
 }
 
 // ---------------------------------------------------------------- PCG
-template <typename T>
-__device__ __forceinline__ void inv3(const T *m, T mu, T *o) {
-    const double a = (double)m[0] + mu, b = m[1], c = m[2], d = m[3], e = (double)m[4] + mu, f = m[5], g = m[6], h = m[7],
-                 i = (double)m[8] + mu;
-    const double A = e * i - f * h, B = -(d * i - f * g), C = d * h - e * g;
-    const double det = a * A + b * B + c * C;
-    const double id = det != 0.0 ? 1.0 / det : 0.0;
-    o[0] = (T)(A * id); o[1] = (T)(-(b * i - c * h) * id); o[2] = (T)((b * f - c * e) * id);
-    o[3] = (T)(B * id); o[4] = (T)((a * i - c * g) * id); o[5] = (T)(-(a * f - c * d) * id);
-    o[6] = (T)(C * id); o[7] = (T)(-(a * h - b * g) * id); o[8] = (T)((a * e - b * d) * id);
-}
 
 template <typename T>
 __global__ void k_pcg_setup(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col_idx,
@@ -564,108 +553,6 @@ __device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long
 }
 __device__ __forceinline__ void st_relaxed_u64(unsigned long long *p, unsigned long long v) {
     asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-
-// Accumulator of dot products of T vectors and the arithmetic of the CG recurrence.  For FP32
-// vectors it is an unevaluated sum of two floats (hi + lo, about 48 significant bits):
-// products are split exactly with one fma and added with Knuth's two-sum, all at the FP32
-// rate.  GB300 executes FP64 at a small fraction of the FP32 rate (a warp-wide FP64
-// instruction occupies its pipe for tens of cycles), and a block-wide FP64 reduction per
-// iteration costs microseconds.  For FP64 vectors it is a plain double.
-template <typename T> struct Acc;
-template <> struct Acc<double> {
-    double v = 0.0;
-    __device__ __forceinline__ void add_prod(double a, double b) { v = fma(a, b, v); }
-    __device__ __forceinline__ void add(const Acc &o) { v += o.v; }
-    __device__ __forceinline__ Acc shfl_xor(unsigned mask, int o, int width) const {
-        Acc r;
-        r.v = __shfl_xor_sync(mask, v, o, width);
-        return r;
-    }
-    __device__ __forceinline__ unsigned long long bits() const { return (unsigned long long)__double_as_longlong(v); }
-    __device__ __forceinline__ static Acc from_bits(unsigned long long b) {
-        Acc r;
-        r.v = __longlong_as_double((long long)b);
-        return r;
-    }
-    __device__ __forceinline__ Acc times(double b) const { Acc r; r.v = v * b; return r; }
-    __device__ __forceinline__ Acc over(double b) const { Acc r; r.v = v / b; return r; }
-    __device__ __forceinline__ Acc minus(const Acc &o) const { Acc r; r.v = v - o.v; return r; }
-    __device__ __forceinline__ double approx() const { return v; }
-    __device__ __forceinline__ double value() const { return v; }
-};
-template <> struct Acc<float> {
-    float hi = 0.f, lo = 0.f;
-    __device__ __forceinline__ void add_pair(float bh, float bl) {
-        const float s = hi + bh, bb = s - hi;
-        const float e = (hi - (s - bb)) + (bh - bb) + lo + bl;
-        hi = s + e;
-        lo = e - (hi - s);
-    }
-    __device__ __forceinline__ void add_prod(float a, float b) {
-        const float p = a * b;
-        add_pair(p, fmaf(a, b, -p));
-    }
-    __device__ __forceinline__ void add(const Acc &o) { add_pair(o.hi, o.lo); }
-    __device__ __forceinline__ Acc shfl_xor(unsigned mask, int o, int width) const {
-        Acc r;
-        r.hi = __shfl_xor_sync(mask, hi, o, width);
-        r.lo = __shfl_xor_sync(mask, lo, o, width);
-        return r;
-    }
-    __device__ __forceinline__ unsigned long long bits() const {
-        return (unsigned long long)__float_as_uint(hi) | ((unsigned long long)__float_as_uint(lo) << 32);
-    }
-    __device__ __forceinline__ static Acc from_bits(unsigned long long b) {
-        Acc r;
-        r.hi = __uint_as_float((unsigned)b);
-        r.lo = __uint_as_float((unsigned)(b >> 32));
-        return r;
-    }
-    __device__ __forceinline__ Acc times(float b) const {   // (hi + lo) b
-        const float p = hi * b, e = fmaf(hi, b, -p) + lo * b;
-        Acc r;
-        r.hi = p + e;
-        r.lo = e - (r.hi - p);
-        return r;
-    }
-    __device__ __forceinline__ Acc over(float b) const {    // (hi + lo) / b, one correction step
-        const float q1 = hi / b, p = q1 * b, pe = fmaf(q1, b, -p);
-        const float q2 = (((hi - p) - pe) + lo) / b;
-        Acc r;
-        r.hi = q1 + q2;
-        r.lo = q2 - (r.hi - q1);
-        return r;
-    }
-    __device__ __forceinline__ Acc minus(const Acc &o) const {
-        Acc r = *this;
-        r.add_pair(-o.hi, -o.lo);
-        return r;
-    }
-    __device__ __forceinline__ float approx() const { return hi + lo; }
-    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
-};
-
-// Block sums of N accumulators (warp trees, then warp 0 over the warp totals), valid in warp 0.
-template <int N, typename T>
-__device__ __forceinline__ void block_sums(Acc<T> (&a)[N]) {
-    __shared__ unsigned long long sh[N][32];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-#pragma unroll
-    for (int i = 0; i < N; ++i) {
-#pragma unroll
-        for (int o = 16; o; o >>= 1) a[i].add(a[i].shfl_xor(0xffffffffu, o, 32));
-        if (lane == 0) sh[i][w] = a[i].bits();
-    }
-    __syncthreads();
-    if (w == 0) {
-#pragma unroll
-        for (int i = 0; i < N; ++i) {
-            a[i] = lane < (int)(blockDim.x >> 5) ? Acc<T>::from_bits(sh[i][lane]) : Acc<T>();
-#pragma unroll
-            for (int o = 16; o; o >>= 1) a[i].add(a[i].shfl_xor(0xffffffffu, o, 32));
-        }
-    }
 }
 
 // Grid sums of N <= 3 accumulators through epoch-tagged slots, identical in every block.

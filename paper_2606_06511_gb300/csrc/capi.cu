@@ -210,6 +210,10 @@ static ttie_status read_err(Ctx &c, const char *where) {
     if (e & ERR_NONFINITE) return set_err(c, TTIE_ERR_NONFINITE, "%s: non-finite vertex position", where);
     if (e & ERR_STACK) return set_err(c, TTIE_ERR_CAPACITY, "%s: BVH traversal stack overflow", where);
     if (e & ERR_BARRIER) return set_err(c, TTIE_ERR_CUDA, "%s: PCG grid barrier timed out", where);
+    if (e & ERR_GROUP)
+        return set_err(c, TTIE_ERR_INVALID,
+                       "%s: batched instances need every vertex in one group and each group's vertices numbered "
+                       "contiguously", where);
     if (e & ERR_CHECK) {
         CK(cudaMemcpyAsync(c.hs, c.ds, sizeof(DevScalars), cudaMemcpyDeviceToHost, c.stream), where);
         CK(cudaStreamSynchronize(c.stream), where);
@@ -217,6 +221,11 @@ static ttie_status read_err(Ctx &c, const char *where) {
                        c.hs->check_value);
     }
     return TTIE_OK;
+}
+
+// Intra-group pairs over an LBVH: every group is an independent problem (instances.cu).
+static bool batched(const Ctx &c) {
+    return (c.prm.pair_mode & 3) == TTIE_PAIRS_INTRA_GROUP && c.have_group && !(c.prm.pair_mode & TTIE_PAIRS_BRUTE);
 }
 
 template <typename T>
@@ -248,6 +257,10 @@ static ttie_status build_impl(Ctx &c, const T *x, const int32_t *tri, const int3
         CK(brute_candidates(c, c.cand, &n), "build: brute-force pairs");
     else
         CK(build_candidates<T>(c, (const vec4_t<T> *)c.xp.p, nullptr, c.cand, &n, cand_cap(c)), "build: LBVH");
+    if (batched(c) && n <= cand_cap(c)) {
+        CK(instance_vertex_groups(c), "build: instances");
+        CK(instance_edges<T>(c, (const vec4_t<T> *)c.xp.p), "build: instances");
+    }
     s = read_err(c, "ttie_build_bvh");
     if (s != TTIE_OK) return s;
     if (n > cand_cap(c))
@@ -306,8 +319,11 @@ template <typename T> static cudaError_t negate_copy(Ctx &c, const T *a, T *b, i
     return cudaGetLastError();
 }
 
+template <typename T> static ttie_status newton_batched(Ctx &c, T *x, ttie_step_info *info);
+
 template <typename T>
 static ttie_status newton_impl(Ctx &c, T *x, ttie_step_info *info) {
+    if (batched(c)) return newton_batched<T>(c, x, info);
     ttie_step_info inf;
     std::memset(&inf, 0, sizeof inf);
     c.have_dir = false;
@@ -383,6 +399,8 @@ static ttie_status newton_impl(Ctx &c, T *x, ttie_step_info *info) {
     inf.grad_dot_dir = gd;
     inf.pcg_iters = c.hs->pcg_iters;
     inf.pcg_rel_residual = c.hs->red[1] > 0.0 ? std::sqrt(c.hs->red[4] / c.hs->red[1]) : 0.0;
+    inf.pcg_block_iters = (int64_t)inf.pcg_iters * c.nnzb;
+    inf.pcg_row_iters = (int64_t)inf.pcg_iters * c.n_rows;
     mark(c, 4);
     // line search on candidates from the boxes swept between x and x + a_max d
     double a_max = 1.0 + c.prm.push_eta;
@@ -439,6 +457,130 @@ static ttie_status newton_impl(Ctx &c, T *x, ttie_step_info *info) {
     inf.alpha = alpha;
     inf.energy_new = E_new;
     inf.n_active_new = n_new;
+    inf.ls_trials = trials;
+    inf.ms_build = ms_between(c, 0, 1);
+    inf.ms_eval = ms_between(c, 1, 2);
+    inf.ms_assemble = ms_between(c, 2, 3);
+    inf.ms_pcg = ms_between(c, 3, 4);
+    inf.ms_line_search = ms_between(c, 4, 5);
+    inf.ms_classify = c.n_cand > 0 ? ms_between(c, 6, 7) : 0.f;
+    inf.ms_pcg_kernel = ms_between(c, 8, 9);
+    if (info) *info = inf;
+    return TTIE_OK;
+}
+
+// One Newton step of every instance at once, each instance on its own (instances.cu): per-
+// instance PCG in one launch, per-instance step cap and line search over a shared ladder of
+// trial steps.
+template <typename T>
+static ttie_status newton_batched(Ctx &c, T *x, ttie_step_info *info) {
+    ttie_step_info inf;
+    std::memset(&inf, 0, sizeof inf);
+    c.have_dir = false;
+    mark(c, 0);
+    CK(pack_positions<T>(c, x, c.x_stride, (vec4_t<T> *)c.xp.p), "newton: positions");
+    ttie_status s = read_err(c, "ttie_newton_step");
+    if (s != TTIE_OK) return s;
+    int64_t n = 0;
+    CK(build_candidates<T>(c, (const vec4_t<T> *)c.xp.p, nullptr, c.cand, &n, cand_cap(c)), "newton: LBVH");
+    if (n > cand_cap(c)) {
+        c.have_cand = false;
+        return set_err(c, TTIE_ERR_CAPACITY, "ttie_newton_step: %lld candidate pairs exceed max_candidates %lld",
+                       (long long)n, (long long)cand_cap(c));
+    }
+    c.n_cand = n;
+    c.have_cand = true;
+    inf.n_candidates = n;
+    mark(c, 1);
+    c.time_kernels = c.prm.profile != 0;
+    CK(eval_candidates<T>(c, (const vec4_t<T> *)c.xp.p, (const int2 *)c.cand.p, n, TTIE_EVAL_E | TTIE_EVAL_H), "newton: eval");
+    c.time_kernels = false;
+    c.have_eval = true;
+    c.eval_what = TTIE_EVAL_E | TTIE_EVAL_H;
+    CK(cudaMemcpyAsync(&c.hs->energy, &c.ds->energy, sizeof(double), cudaMemcpyDeviceToHost, c.stream), "newton");
+    CK(cudaStreamSynchronize(c.stream), "newton");
+    const double E = c.hs->energy;
+    inf.energy = E;
+    inf.n_active = c.n_active;
+    mark(c, 2);
+    if (!std::isfinite(E)) return set_err(c, TTIE_ERR_NONFINITE, "ttie_newton_step: energy is not finite");
+    if (c.n_active == 0) {
+        inf.energy_new = E;
+        mark(c, 3); mark(c, 4); mark(c, 5);
+        if (c.prm.profile) cudaEventSynchronize(c.ev[5]);
+        inf.ms_build = ms_between(c, 0, 1);
+        inf.ms_eval = ms_between(c, 1, 2);
+        inf.ms_classify = c.n_cand > 0 ? ms_between(c, 6, 7) : 0.f;
+        if (info) *info = inf;
+        return TTIE_OK;
+    }
+    // assembly, instance layout and energies at x, per-instance PCG for (H+_i + mu_i I) d_i = -g_i
+    CK(assemble_system<T>(c, nullptr), "newton: assembly");
+    c.have_bsr = true;
+    inf.n_rows = c.n_rows;
+    inf.nnzb = c.nnzb;
+    CK(instance_layout(c), "newton: instances");
+    CK(instance_energies<T>(c, (const int2 *)c.cand.p, 0), "newton: instances");
+    mark(c, 3);
+    const int64_t n3 = c.n_rows * 3;
+    CK(ensure(c, c.pcg_x, (size_t)(n3 > 0 ? n3 : 1) * sizeof(T)), "newton");
+    CK(ensure(c, c.xsave, (size_t)(n3 > 0 ? n3 : 1) * sizeof(T)), "newton");
+    CK(negate_copy(c, (const T *)c.rhs.p, (T *)c.xsave.p, n3), "newton");
+    CK(instance_pcg<T>(c, (const T *)c.xsave.p, (T *)c.pcg_x.p), "newton: PCG");
+    s = read_err(c, "ttie_newton_step");
+    if (s != TTIE_OK) return s;
+    CK(ensure(c, c.dir, (size_t)c.V * 3 * sizeof(T)), "newton");
+    CK(scatter_direction<T>(c, (const T *)c.pcg_x.p, (T *)c.dir.p), "newton");
+    c.have_dir = true;
+    mark(c, 4);
+    // line search: candidates from the boxes swept to the largest trial step (tree of x refitted)
+    double a_max = 1.0 + c.prm.push_eta;
+    CK(ensure(c, c.xq, (size_t)c.V * sizeof(vec4_t<T>)), "newton");
+    CK(ensure(c, c.xt, (size_t)c.V * sizeof(vec4_t<T>)), "newton");
+    int64_t ns = 0;
+    for (int tries = 0;; ++tries) {
+        CK(axpy_positions<T>(c, (const vec4_t<T> *)c.xp.p, (const T *)c.dir.p, (T)a_max, (vec4_t<T> *)c.xq.p), "newton");
+        CK(build_candidates<T>(c, (const vec4_t<T> *)c.xp.p, (const vec4_t<T> *)c.xq.p, c.sweep_cand, &ns, cand_cap(c), true),
+           "newton: sweep");
+        if (ns <= cand_cap(c)) break;
+        if (tries >= 12)
+            return set_err(c, TTIE_ERR_CAPACITY, "ttie_newton_step: swept candidates %lld exceed max_candidates",
+                           (long long)ns);
+        a_max *= 0.5;
+    }
+    inf.n_candidates_swept = ns;
+    CK(instance_ls_init(c), "newton: line search");
+    int trials = 0;
+    for (int k = -1; k <= c.prm.ls_max_halvings; ++k) {
+        const double a = k < 0 ? a_max : std::ldexp(1.0, -k);
+        if (k < 0 && !(a_max > 1.0)) continue;
+        if (a > a_max) continue;   // beyond the swept range
+        CK(axpy_positions<T>(c, (const vec4_t<T> *)c.xp.p, (const T *)c.dir.p, (T)a, (vec4_t<T> *)c.xt.p), "newton");
+        CK(eval_candidates<T>(c, (const vec4_t<T> *)c.xt.p, (const int2 *)c.sweep_cand.p, ns, TTIE_EVAL_E), "line search");
+        CK(instance_energies<T>(c, (const int2 *)c.sweep_cand.p, 1), "line search");
+        CK(instance_ls_accept(c, a, k == c.prm.ls_max_halvings ? 1 : 0, &c.ds->n_pending), "line search");
+        CK(cudaMemcpyAsync(&c.hs->n_pending, &c.ds->n_pending, sizeof(unsigned int), cudaMemcpyDeviceToHost, c.stream),
+           "line search");
+        CK(cudaStreamSynchronize(c.stream), "line search");
+        ++trials;
+        if (c.hs->n_pending == 0) break;
+    }
+    CK(instance_update<T>(c, x, c.x_stride, (const T *)c.dir.p), "newton: update");
+    CK(instance_totals(c, c.ds->batch), "newton");
+    c.have_eval = false;   // the last evaluation ran on the line-search candidates
+    s = read_err(c, "ttie_newton_step");
+    if (s != TTIE_OK) return s;
+    mark(c, 5);
+    CK(cudaMemcpyAsync(c.hs->batch, c.ds->batch, sizeof(c.hs->batch), cudaMemcpyDeviceToHost, c.stream), "newton");
+    CK(cudaStreamSynchronize(c.stream), "newton");
+    inf.energy_new = c.hs->batch[0];
+    inf.n_active_new = (int64_t)c.hs->batch[1];
+    inf.pcg_iters = (int)c.hs->batch[2];
+    inf.pcg_rel_residual = c.hs->batch[3];
+    inf.grad_dot_dir = c.hs->batch[4];
+    inf.alpha = c.hs->batch[5];
+    inf.pcg_block_iters = (int64_t)c.hs->batch[7];
+    inf.pcg_row_iters = (int64_t)c.hs->batch[8];
     inf.ls_trials = trials;
     inf.ms_build = ms_between(c, 0, 1);
     inf.ms_eval = ms_between(c, 1, 2);

@@ -48,6 +48,24 @@ enum ErrBits : int {
     ERR_DEFER = 8,          // exact-resolve list overflow
     ERR_BARRIER = 16,       // a grid barrier wait ran out of its iteration limit
     ERR_CHECK = 32,         // a bounds check of a TTIE_CHECKS build failed (see check_code)
+    ERR_GROUP = 64,         // batched instances: a vertex in two groups, or a group's vertices not contiguous
+};
+
+// Per-pair rows of the evaluation: [a, b, grad a (18), grad b (18), pad 2] (a = t_c^0, b = t_c^1)
+constexpr int kFacStride = 40;
+
+// One instance of a batched solve (intra-group pair mode): its rows of the assembled system,
+// its PCG result, its energies and its line-search state.
+struct Inst {
+    int first, last, count;   // rows [first, last] of the system (contiguous), count of them
+    int iters;                // PCG iterations
+    double rel;               // PCG relative residual
+    double gd;                // g . d after the step cap
+    double e0, et, e_new;     // energy at x, at the current trial, at the accepted step
+    int n0, nt, n_new;        // intersecting pairs at x, at the trial, at the accepted step
+    int seg_lo, seg_hi;       // its range in the active-pair list of the last evaluation
+    int pending;              // line search not yet accepted
+    double alpha;             // accepted step
 };
 
 struct DevScalars {
@@ -73,6 +91,8 @@ struct DevScalars {
     long long check_value;                 // the offending index
     unsigned int bar_count;                // arrivals at the PCG kernels' grid all-reduce
     unsigned int bar_gen;                  // its generation (bumped on release)
+    unsigned int n_pending;                // batched line search: instances still open
+    double batch[10];                      // batched step totals (instance_totals)
 };
 
 // ------------------------------------------------------------------ buffers
@@ -91,7 +111,8 @@ cudaError_t ensure(Ctx &c, Buf &b, size_t bytes);   // grow-only, contents not k
     X(defer) X(active) X(fac) X(partials) X(vflag) X(vrow) X(row_vertex) X(bkey) X(bkey2)   \
     X(bval) X(bval2) X(bflag) X(run_start) X(row_ptr) X(col_idx) X(bsr_val) X(rhs)         \
     X(zfac) X(dinv) X(pcg_x) X(pcg_r) X(pcg_z) X(pcg_p) X(pcg_q) X(dir) X(xt) X(gtmp)      \
-    X(xsave) X(sweep_cand) X(pcg_z4) X(hbuf) X(pcg_sync) X(spill)
+    X(xsave) X(sweep_cand) X(pcg_z4) X(hbuf) X(pcg_sync) X(spill) X(pcg_w) X(vgroup) X(iedge)  \
+    X(inst)
 
 struct Ctx {
     ttie_params prm;
@@ -182,6 +203,17 @@ cudaError_t pack_topology(Ctx &c, const int32_t *tri, const int32_t *group);
 template <typename T> cudaError_t build_candidates(Ctx &c, const vec4_t<T> *x0, const vec4_t<T> *x1,
                                                    Buf &out_pairs, int64_t *n_out, int64_t cap,
                                                    bool refit_only = false);
+
+// batched independent instances (instances.cu)
+cudaError_t instance_vertex_groups(Ctx &c);
+template <typename T> cudaError_t instance_edges(Ctx &c, const vec4_t<T> *x);
+cudaError_t instance_layout(Ctx &c);
+template <typename T> cudaError_t instance_energies(Ctx &c, const int2 *pairs, int at_trial);
+template <typename T> cudaError_t instance_pcg(Ctx &c, const T *rhs, T *out);
+cudaError_t instance_ls_init(Ctx &c);
+cudaError_t instance_ls_accept(Ctx &c, double alpha, int last, unsigned int *d_pending);
+template <typename T> cudaError_t instance_update(Ctx &c, T *x, int stride, const T *d_full);
+cudaError_t instance_totals(Ctx &c, double *d_out);   // 10 values
 cudaError_t brute_candidates(Ctx &c, Buf &out_pairs, int64_t *n_out);
 template <typename T> cudaError_t mean_edge_length(Ctx &c, const vec4_t<T> *x, double *out_dev);
 

@@ -1,0 +1,559 @@
+// Batched independent instances (pair mode TTIE_PAIRS_INTRA_GROUP).
+//
+// When pairs never cross groups, the assembled system is block-diagonal by group and every
+// group is its own problem.  One Newton step then solves them all at once but independently:
+//   * the PCG of every instance runs in one launch, one thread block per instance, with
+//     block-local reductions only (no grid-wide synchronisation), each instance with its
+//     own regulariser mu_i = mu_rel * mean diag(H+_i), its own stopping test and its own
+//     step cap (max_step * the instance's mean edge length);
+//   * the line search walks the same ladder of trial steps for all instances, and each
+//     instance accepts the first trial that meets its own Armijo test (or leaves it without
+//     intersecting pairs); its energy is the sum of T over its own pairs, added in a fixed
+//     order.
+// Layout: every instance's vertices must be numbered contiguously (rows of the block-CSR
+// system are sorted by vertex, so an instance's rows are then a contiguous range); the pair
+// lists come out of the LBVH with group-prefixed Morton keys, so an instance's pairs are a
+// contiguous range of every pair list too.
+#include <climits>
+
+#include "common.cuh"
+#include "pcg_common.cuh"
+
+namespace ttie {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kInstThreads = 256;
+constexpr int kInstLanes = 4;             // lanes sharing a row in the product
+constexpr int kInstSmem = 46 * 1024;      // dynamic shared memory per instance block
+
+__global__ void k_fill_i32(int32_t *p, int64_t n, int32_t v) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) p[i] = v;
+}
+
+// group of every vertex; a vertex used by triangles of two groups is an error
+__global__ void k_vertex_group(const int4 *__restrict__ tri4, const int32_t *__restrict__ grp, int64_t F,
+                               int32_t *vgroup, DevScalars *ds) {
+    for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < F; f += (int64_t)gridDim.x * blockDim.x) {
+        const int4 t = tri4[f];
+        const int g = grp[f];
+        const int v[3] = {t.x, t.y, t.z};
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const int old = atomicCAS(&vgroup[v[k]], -1, g);
+            if (old != -1 && old != g) atomicOr(&ds->err, ERR_GROUP);
+        }
+    }
+}
+
+// mean edge length of every group's triangles (leaves of the group in LBVH order, fixed order)
+template <typename T>
+__global__ void k_group_edges(const vec4_t<T> *__restrict__ x, const int4 *__restrict__ tri4,
+                              const uint32_t *__restrict__ perm, const int2 *__restrict__ group_range, int G,
+                              double *edge) {
+    const int lane = threadIdx.x & 31;
+    for (int g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < G; g += (gridDim.x * blockDim.x) >> 5) {
+        const int2 r = group_range[g];
+        double s = 0.0;
+        for (int i = r.x + lane; i <= r.y; i += 32) {
+            const int4 t = tri4[perm[i]];
+            const v3<T> a = xyz<T>(x[t.x]), b = xyz<T>(x[t.y]), c = xyz<T>(x[t.z]);
+            const v3<T> e0 = b - a, e1 = c - b, e2 = a - c;
+            s += sqrt((double)dot(e0, e0)) + sqrt((double)dot(e1, e1)) + sqrt((double)dot(e2, e2));
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) edge[g] = r.y >= r.x ? s / (3.0 * (r.y - r.x + 1)) : 0.0;
+    }
+}
+
+__global__ void k_inst_init(Inst *inst, int G) {
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x) {
+        Inst I = {};
+        I.first = INT_MAX;
+        I.last = -1;
+        inst[g] = I;
+    }
+}
+
+__global__ void k_inst_rows(const int32_t *__restrict__ row_vertex, const int32_t *__restrict__ vgroup, DevScalars *ds,
+                            int G, Inst *inst) {
+    const long long nr = (long long)ds->n_rows;
+    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < nr; r += (long long)gridDim.x * blockDim.x) {
+        const int g = vgroup[row_vertex[r]];
+        if (TTIE_BAD(ds, g >= 0 && g < G, 81, g)) continue;
+        atomicMin(&inst[g].first, (int)r);
+        atomicMax(&inst[g].last, (int)r);
+        atomicAdd(&inst[g].count, 1);
+    }
+}
+
+__global__ void k_inst_check(Inst *inst, int G, DevScalars *ds) {
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x) {
+        Inst &I = inst[g];
+        if (I.count > 0 && I.last - I.first + 1 != I.count) atomicOr(&ds->err, ERR_GROUP);
+        if (I.count == 0) I.first = 0;
+    }
+}
+
+// Per-instance ranges of the active-pair list of the last evaluation (pairs of a group are
+// contiguous there).
+__global__ void k_inst_segments(const int2 *__restrict__ pairs, const uint32_t *__restrict__ active,
+                                const int32_t *__restrict__ grp, const DevScalars *ds, Inst *inst) {
+    const long long n = (long long)ds->n_active;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+        const int g = grp[pairs[active[k]].x];
+        if (k == 0 || grp[pairs[active[k - 1]].x] != g) inst[g].seg_lo = (int)k;
+        if (k == n - 1 || grp[pairs[active[k + 1]].x] != g) inst[g].seg_hi = (int)(k + 1);
+    }
+}
+
+__global__ void k_inst_clear_segments(Inst *inst, int G) {
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x) {
+        inst[g].seg_lo = 0;
+        inst[g].seg_hi = 0;
+    }
+}
+
+// Energy (sum of T = (a b)^2 over the instance's intersecting pairs, fixed order) and count,
+// one warp per instance; into e0/n0 (at x) or et/nt (at a trial).
+template <typename T>
+__global__ void k_inst_energy(const T *__restrict__ fac, int fac_stride, int G, int at_trial, Inst *inst) {
+    const int lane = threadIdx.x & 31;
+    for (int g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < G; g += (gridDim.x * blockDim.x) >> 5) {
+        const int lo = inst[g].seg_lo, hi = inst[g].seg_hi;
+        double s = 0.0;
+        for (int k = lo + lane; k < hi; k += 32) {
+            const double ab = (double)fac[(size_t)k * fac_stride] * (double)fac[(size_t)k * fac_stride + 1];
+            s += ab * ab;
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) {
+            if (at_trial) {
+                inst[g].et = s;
+                inst[g].nt = hi - lo;
+            } else {
+                inst[g].e0 = s;
+                inst[g].n0 = hi - lo;
+            }
+        }
+    }
+}
+
+template <typename T> struct InstPcgArgs {
+    const int32_t *row_ptr, *col_idx;
+    const T *bval, *rhs;          // rhs = -g on the rows
+    T *x;                         // the direction d on the rows (output)
+    T *r, *u, *p, *s, *w, *dinv;  // row vectors for instances kept in global memory
+    const double *edge;           // mean edge length per instance
+    Inst *inst;
+    double mu_rel, rtol2, max_step;
+    int max_it;
+};
+
+template <typename T> struct InstView {
+    T *x, *r, *u, *p, *s, *w, *di;
+    const T *val;
+    bool resident;
+    int nrow, nnz, r0, b0;
+    int *rp, *col;                // local row offsets and local columns (resident only)
+};
+
+template <typename T>
+__device__ __forceinline__ int inst_rowp(const InstPcgArgs<T> &a, const InstView<T> &v, int i) {
+    return v.resident ? v.rp[i] : a.row_ptr[v.r0 + i] - v.b0;
+}
+template <typename T>
+__device__ __forceinline__ int inst_col(const InstPcgArgs<T> &a, const InstView<T> &v, int b) {
+    return v.resident ? v.col[b] : a.col_idx[v.b0 + b] - v.r0;
+}
+
+// Block sums of N accumulators broadcast to every thread of the block.
+template <int N, typename T>
+__device__ __forceinline__ void block_totals(Acc<T> (&a)[N]) {
+    __shared__ unsigned long long tot[N];
+    block_sums<N, T>(a);
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int i = 0; i < N; ++i) tot[i] = a[i].bits();
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < N; ++i) a[i] = Acc<T>::from_bits(tot[i]);
+    __syncthreads();
+}
+
+// PCG (Chronopoulos-Gear form, as in the grid-wide solver) of one instance per block.
+template <typename T>
+__global__ void __launch_bounds__(kInstThreads) k_pcg_instances(InstPcgArgs<T> a, int smem_bytes) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    Inst *I = a.inst + blockIdx.x;
+    InstView<T> v;
+    v.nrow = I->count;
+    if (v.nrow <= 0) return;
+    v.r0 = I->first;
+    v.b0 = a.row_ptr[v.r0];
+    v.nnz = a.row_ptr[v.r0 + v.nrow] - v.b0;
+    const size_t vec_bytes = ((size_t)v.nrow * 27 * sizeof(T) + (size_t)(v.nrow + 1) * 4 + 15) / 16 * 16;
+    const size_t mat_bytes = (size_t)v.nnz * (9 * sizeof(T) + 4);
+    v.resident = vec_bytes + mat_bytes <= (size_t)smem_bytes;
+    if (v.resident) {
+        v.x = (T *)smem; v.r = v.x + 3 * v.nrow; v.u = v.r + 3 * v.nrow; v.p = v.u + 3 * v.nrow;
+        v.s = v.p + 3 * v.nrow; v.w = v.s + 3 * v.nrow; v.di = v.w + 3 * v.nrow;
+        v.rp = (int *)(v.di + 9 * v.nrow);
+        T *val = (T *)(smem + vec_bytes);
+        v.col = (int *)(val + (size_t)9 * v.nnz);
+        for (int i = threadIdx.x; i < 9 * v.nnz; i += blockDim.x) val[i] = a.bval[(size_t)v.b0 * 9 + i];
+        for (int i = threadIdx.x; i < v.nnz; i += blockDim.x) v.col[i] = a.col_idx[v.b0 + i] - v.r0;
+        for (int i = threadIdx.x; i <= v.nrow; i += blockDim.x) v.rp[i] = a.row_ptr[v.r0 + i] - v.b0;
+        v.val = val;
+    } else {
+        const size_t o = (size_t)v.r0 * 3;
+        v.x = a.x + o; v.r = a.r + o; v.u = a.u + o; v.p = a.p + o; v.s = a.s + o; v.w = a.w + o;
+        v.di = a.dinv + (size_t)v.r0 * 9;
+        v.rp = nullptr;
+        v.col = nullptr;
+        v.val = a.bval + (size_t)v.b0 * 9;
+    }
+    __syncthreads();
+    // mu_i from the instance's own trace, then M^-1, r = rhs, u = M^-1 r, x = p = s = 0
+    Acc<T> tr[1];
+    for (int lr = threadIdx.x; lr < v.nrow; lr += blockDim.x)
+        for (int b = inst_rowp(a, v, lr); b < inst_rowp(a, v, lr + 1); ++b)
+            if (inst_col(a, v, b) == lr) {
+                const T *m = v.val + (size_t)b * 9;
+                tr[0].add_prod(m[0] + m[4] + m[8], T(1));
+                break;
+            }
+    block_totals<1, T>(tr);
+    const T mu = (T)(a.mu_rel * tr[0].value() / (3.0 * v.nrow));
+    Acc<T> red[3];
+    for (int lr = threadIdx.x; lr < v.nrow; lr += blockDim.x) {
+        const T zero9[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+        const T *diag = zero9;
+        for (int b = inst_rowp(a, v, lr); b < inst_rowp(a, v, lr + 1); ++b)
+            if (inst_col(a, v, b) == lr) { diag = v.val + (size_t)b * 9; break; }
+        T di[9];
+        inv3(diag, mu, di);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) v.di[lr * 9 + i] = di[i];
+        const T r0 = a.rhs[(size_t)(v.r0 + lr) * 3], r1 = a.rhs[(size_t)(v.r0 + lr) * 3 + 1],
+                r2 = a.rhs[(size_t)(v.r0 + lr) * 3 + 2];
+        const T u[3] = {di[0] * r0 + di[1] * r1 + di[2] * r2, di[3] * r0 + di[4] * r1 + di[5] * r2,
+                        di[6] * r0 + di[7] * r1 + di[8] * r2};
+        const T rv[3] = {r0, r1, r2};
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            v.x[lr * 3 + i] = T(0);
+            v.r[lr * 3 + i] = rv[i];
+            v.u[lr * 3 + i] = u[i];
+            v.p[lr * 3 + i] = T(0);
+            v.s[lr * 3 + i] = T(0);
+            red[0].add_prod(rv[i], u[i]);
+            red[2].add_prod(rv[i], rv[i]);
+        }
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, sub = lane & (kInstLanes - 1);
+    const unsigned gmask = ((1u << kInstLanes) - 1u) << (lane & ~(kInstLanes - 1));
+    const T rtol2 = (T)a.rtol2;
+    T rr0 = T(0), gamma_prev = T(1), alpha_prev = T(1), rr_last = T(0);
+    bool stop_next = false;
+    int it = 0;
+    while (true) {
+        // w = (A + mu I) u and the rows' w.u
+        for (int lr = threadIdx.x / kInstLanes; lr < v.nrow; lr += kInstThreads / kInstLanes) {
+            T y0 = 0, y1 = 0, y2 = 0;
+            const int be = inst_rowp(a, v, lr + 1);
+            for (int b = inst_rowp(a, v, lr) + sub; b < be; b += kInstLanes) {
+                const int c = inst_col(a, v, b);
+                const T *m = v.val + (size_t)b * 9;
+                const T c0 = v.u[c * 3], c1 = v.u[c * 3 + 1], c2 = v.u[c * 3 + 2];
+                y0 += m[0] * c0 + m[1] * c1 + m[2] * c2;
+                y1 += m[3] * c0 + m[4] * c1 + m[5] * c2;
+                y2 += m[6] * c0 + m[7] * c1 + m[8] * c2;
+            }
+#pragma unroll
+            for (int o = kInstLanes / 2; o; o >>= 1) {
+                y0 += __shfl_xor_sync(gmask, y0, o, kInstLanes);
+                y1 += __shfl_xor_sync(gmask, y1, o, kInstLanes);
+                y2 += __shfl_xor_sync(gmask, y2, o, kInstLanes);
+            }
+            if (sub == 0) {
+                const T w0 = y0 + mu * v.u[lr * 3], w1 = y1 + mu * v.u[lr * 3 + 1], w2 = y2 + mu * v.u[lr * 3 + 2];
+                v.w[lr * 3] = w0; v.w[lr * 3 + 1] = w1; v.w[lr * 3 + 2] = w2;
+                red[1].add_prod(w0, v.u[lr * 3]);
+                red[1].add_prod(w1, v.u[lr * 3 + 1]);
+                red[1].add_prod(w2, v.u[lr * 3 + 2]);
+            }
+        }
+        block_totals<3, T>(red);
+        const T g = red[0].approx(), d = red[1].approx(), r2 = red[2].approx();
+        if (it == 0) rr0 = r2;
+        rr_last = r2;
+        if (stop_next || it >= a.max_it || r2 <= rtol2 * rr0 || !isfinite(r2)) break;
+        T alpha, beta = T(0);
+        bool ok;
+        if (it == 0) {
+            alpha = g / d;
+            ok = d > T(0) && isfinite(alpha);
+        } else {
+            beta = g / gamma_prev;
+            const T den = red[1].minus(red[0].over(alpha_prev).times(beta)).approx();
+            alpha = g / den;
+            ok = den > T(0) && isfinite(alpha);
+        }
+        if (!ok) {
+            if (it > 0) break;
+            alpha = T(1);      // breakdown at the first step keeps x = M^-1 r0 (preconditioned gradient)
+            beta = T(0);
+            stop_next = true;
+        }
+        gamma_prev = g;
+        alpha_prev = alpha;
+        red[0] = Acc<T>();
+        red[1] = Acc<T>();
+        red[2] = Acc<T>();
+        for (int lr = threadIdx.x; lr < v.nrow; lr += blockDim.x) {
+            T rv[3];
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                const int k = lr * 3 + i;
+                const T pi = v.u[k] + beta * v.p[k];
+                const T si = v.w[k] + beta * v.s[k];
+                v.p[k] = pi;
+                v.s[k] = si;
+                v.x[k] += alpha * pi;
+                rv[i] = v.r[k] - alpha * si;
+                v.r[k] = rv[i];
+            }
+            const T *di = v.di + lr * 9;
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                const T zi = di[3 * i] * rv[0] + di[3 * i + 1] * rv[1] + di[3 * i + 2] * rv[2];
+                v.u[lr * 3 + i] = zi;
+                red[0].add_prod(rv[i], zi);
+                red[2].add_prod(rv[i], rv[i]);
+            }
+        }
+        ++it;
+        __syncthreads();
+    }
+    // g.d and max |d_r| of the instance's direction; the step cap; the direction out
+    Acc<T> gd[1];
+    T dm = T(0);
+    for (int lr = threadIdx.x; lr < v.nrow; lr += blockDim.x) {
+        T n2 = T(0);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            const T di = v.x[lr * 3 + i];
+            gd[0].add_prod(-a.rhs[(size_t)(v.r0 + lr) * 3 + i], di);
+            n2 += di * di;
+        }
+        dm = fmax(dm, n2);
+    }
+    __shared__ T s_max[kInstThreads / 32];
+#pragma unroll
+    for (int o = 16; o; o >>= 1) dm = fmax(dm, __shfl_xor_sync(0xffffffffu, dm, o));
+    if (lane == 0) s_max[threadIdx.x >> 5] = dm;
+    block_totals<1, T>(gd);
+    dm = T(0);
+    for (int k = 0; k < kInstThreads / 32; ++k) dm = fmax(dm, s_max[k]);
+    const double dmax = sqrt((double)dm);
+    const double cap = a.max_step * a.edge[blockIdx.x];
+    const double scale = (cap > 0.0 && dmax > cap) ? cap / dmax : 1.0;
+    for (int i = threadIdx.x; i < 3 * v.nrow; i += blockDim.x) {
+        const T di = v.x[i] * (T)scale;
+        a.x[(size_t)v.r0 * 3 + i] = di;
+    }
+    if (threadIdx.x == 0) {
+        I->iters = it;
+        I->rel = rr0 > T(0) ? sqrt((double)rr_last / (double)rr0) : 0.0;
+        I->gd = gd[0].value() * scale;
+    }
+}
+
+// Line search bookkeeping per instance
+__global__ void k_ls_init(Inst *inst, int G) {
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x) {
+        Inst &I = inst[g];
+        I.pending = I.n0 > 0 ? 1 : 0;
+        I.alpha = 0.0;
+        I.e_new = I.e0;
+        I.n_new = I.n0;
+    }
+}
+
+__global__ void k_ls_accept(Inst *inst, int G, double alpha, double armijo_c, int last, unsigned int *n_pending) {
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x) {
+        Inst &I = inst[g];
+        if (!I.pending) continue;
+        if (I.nt == 0 || I.et <= I.e0 + armijo_c * alpha * I.gd || last) {
+            I.alpha = alpha;
+            I.e_new = I.et;
+            I.n_new = I.nt;
+            I.pending = 0;
+        } else {
+            atomicAdd(n_pending, 1u);
+        }
+    }
+}
+
+template <typename T>
+__global__ void k_update_grouped(T *__restrict__ x, int stride, const T *__restrict__ d,
+                                 const int32_t *__restrict__ vgroup, const Inst *__restrict__ inst, int64_t V) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < V; v += (int64_t)gridDim.x * blockDim.x) {
+        const int g = vgroup[v];
+        if (g < 0) continue;
+        const T a = (T)inst[g].alpha;
+        x[v * stride] += a * d[v * 3];
+        x[v * stride + 1] += a * d[v * 3 + 1];
+        x[v * stride + 2] += a * d[v * 3 + 2];
+    }
+}
+
+// Totals of a batched step in fixed order: energy and pairs after the step, largest PCG
+// iteration count and relative residual, sum of g.d, smallest accepted step, instances
+// solved, and the PCG work (iterations x 3x3 blocks, iterations x rows) summed over them.
+__global__ void k_inst_totals(const Inst *inst, int G, const int32_t *row_ptr, double *out) {
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    double e = 0.0, gd = 0.0, rel = 0.0, amin = 1e300, wb = 0.0, wr = 0.0;
+    long long n = 0;
+    int it = 0, solved = 0;
+    for (int g = 0; g < G; ++g) {
+        const Inst &I = inst[g];
+        e += I.e_new;
+        n += I.n_new;
+        if (I.n0 > 0) {
+            gd += I.gd;
+            rel = fmax(rel, I.rel);
+            it = max(it, I.iters);
+            amin = fmin(amin, I.alpha);
+            ++solved;
+        }
+        if (I.count > 0) {
+            wb += (double)I.iters * (row_ptr[I.first + I.count] - row_ptr[I.first]);
+            wr += (double)I.iters * I.count;
+        }
+    }
+    out[7] = wb;
+    out[8] = wr;
+    out[0] = e;
+    out[1] = (double)n;
+    out[2] = (double)it;
+    out[3] = rel;
+    out[4] = gd;
+    out[5] = solved ? amin : 0.0;
+    out[6] = (double)solved;
+}
+
+}  // namespace
+
+cudaError_t instance_vertex_groups(Ctx &c) {
+    TTIE_CUDA_TRY(ensure(c, c.vgroup, (size_t)c.V * 4));
+    launch(c, k_fill_i32, dim3(grid_for(c.V, kThreads)), dim3(kThreads), (int32_t *)c.vgroup.p, c.V, -1);
+    launch(c, k_vertex_group, dim3(grid_for(c.F, kThreads)), dim3(kThreads), (const int4 *)c.tri4.p,
+           (const int32_t *)c.grp.p, c.F, (int32_t *)c.vgroup.p, c.ds);
+    return cudaGetLastError();
+}
+
+template <typename T> cudaError_t instance_edges(Ctx &c, const vec4_t<T> *x) {
+    TTIE_CUDA_TRY(ensure(c, c.iedge, (size_t)(c.n_groups > 0 ? c.n_groups : 1) * sizeof(double)));
+    launch(c, k_group_edges<T>, dim3(grid_for((int64_t)c.n_groups * 32, kThreads)), dim3(kThreads), x,
+           (const int4 *)c.tri4.p, (const uint32_t *)c.perm.p, (const int2 *)c.group_range.p, c.n_groups,
+           (double *)c.iedge.p);
+    return cudaGetLastError();
+}
+template cudaError_t instance_edges<float>(Ctx &, const float4 *);
+template cudaError_t instance_edges<double>(Ctx &, const dvec4 *);
+
+cudaError_t instance_layout(Ctx &c) {
+    const int G = c.n_groups;
+    TTIE_CUDA_TRY(ensure(c, c.inst, (size_t)(G > 0 ? G : 1) * sizeof(Inst)));
+    launch(c, k_inst_init, dim3(grid_for(G, kThreads)), dim3(kThreads), (Inst *)c.inst.p, G);
+    launch(c, k_inst_rows, dim3(grid_for(c.n_rows, kThreads)), dim3(kThreads), (const int32_t *)c.row_vertex.p,
+           (const int32_t *)c.vgroup.p, c.ds, G, (Inst *)c.inst.p);
+    launch(c, k_inst_check, dim3(grid_for(G, kThreads)), dim3(kThreads), (Inst *)c.inst.p, G, c.ds);
+    return cudaGetLastError();
+}
+
+template <typename T> cudaError_t instance_energies(Ctx &c, const int2 *pairs, int at_trial) {
+    const int G = c.n_groups;
+    launch(c, k_inst_clear_segments, dim3(grid_for(G, kThreads)), dim3(kThreads), (Inst *)c.inst.p, G);
+    if (c.n_active > 0)
+        launch(c, k_inst_segments, dim3(grid_for(c.n_active, kThreads)), dim3(kThreads), pairs,
+               (const uint32_t *)c.active.p, (const int32_t *)c.grp.p, (const DevScalars *)c.ds, (Inst *)c.inst.p);
+    launch(c, k_inst_energy<T>, dim3(grid_for((int64_t)G * 32, kThreads)), dim3(kThreads), (const T *)c.fac.p,
+           kFacStride, G, at_trial, (Inst *)c.inst.p);
+    return cudaGetLastError();
+}
+template cudaError_t instance_energies<float>(Ctx &, const int2 *, int);
+template cudaError_t instance_energies<double>(Ctx &, const int2 *, int);
+
+template <typename T> cudaError_t instance_pcg(Ctx &c, const T *rhs, T *out) {
+    const int64_t nr = c.n_rows;
+    const size_t n3 = (size_t)(nr > 0 ? nr : 1) * 3 * sizeof(T);
+    TTIE_CUDA_TRY(ensure(c, c.pcg_r, n3));
+    TTIE_CUDA_TRY(ensure(c, c.pcg_z, n3));
+    TTIE_CUDA_TRY(ensure(c, c.pcg_p, n3));
+    TTIE_CUDA_TRY(ensure(c, c.pcg_q, n3));
+    TTIE_CUDA_TRY(ensure(c, c.pcg_w, n3));
+    TTIE_CUDA_TRY(ensure(c, c.dinv, (size_t)(nr > 0 ? nr : 1) * 9 * sizeof(T)));
+    InstPcgArgs<T> a;
+    a.row_ptr = (const int32_t *)c.row_ptr.p;
+    a.col_idx = (const int32_t *)c.col_idx.p;
+    a.bval = (const T *)c.bsr_val.p;
+    a.rhs = rhs;
+    a.x = out;
+    a.r = (T *)c.pcg_r.p;
+    a.u = (T *)c.pcg_z.p;
+    a.p = (T *)c.pcg_p.p;
+    a.s = (T *)c.pcg_q.p;
+    a.w = (T *)c.pcg_w.p;
+    a.dinv = (T *)c.dinv.p;
+    a.edge = (const double *)c.iedge.p;
+    a.inst = (Inst *)c.inst.p;
+    a.mu_rel = c.prm.mu_rel;
+    a.rtol2 = c.prm.pcg_rtol * c.prm.pcg_rtol;
+    a.max_step = c.prm.max_step;
+    a.max_it = c.prm.pcg_max_it;
+    TTIE_CUDA_TRY(cudaFuncSetAttribute((const void *)k_pcg_instances<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       kInstSmem));
+    ++c.n_launch;
+    if (c.prm.profile) cudaEventRecord(c.ev[8], c.stream);
+    k_pcg_instances<T><<<dim3((unsigned)(c.n_groups > 0 ? c.n_groups : 1)), dim3(kInstThreads), kInstSmem, c.stream>>>(
+        a, kInstSmem);
+    if (c.prm.profile) cudaEventRecord(c.ev[9], c.stream);
+    return cudaGetLastError();
+}
+template cudaError_t instance_pcg<float>(Ctx &, const float *, float *);
+template cudaError_t instance_pcg<double>(Ctx &, const double *, double *);
+
+cudaError_t instance_ls_init(Ctx &c) {
+    launch(c, k_ls_init, dim3(grid_for(c.n_groups, kThreads)), dim3(kThreads), (Inst *)c.inst.p, c.n_groups);
+    return cudaGetLastError();
+}
+
+cudaError_t instance_ls_accept(Ctx &c, double alpha, int last, unsigned int *d_pending) {
+    TTIE_CUDA_TRY(cudaMemsetAsync(d_pending, 0, sizeof(unsigned int), c.stream));
+    launch(c, k_ls_accept, dim3(grid_for(c.n_groups, kThreads)), dim3(kThreads), (Inst *)c.inst.p, c.n_groups, alpha,
+           c.prm.armijo_c, last, d_pending);
+    return cudaGetLastError();
+}
+
+template <typename T> cudaError_t instance_update(Ctx &c, T *x, int stride, const T *d_full) {
+    launch(c, k_update_grouped<T>, dim3(grid_for(c.V, kThreads)), dim3(kThreads), x, stride, d_full,
+           (const int32_t *)c.vgroup.p, (const Inst *)c.inst.p, c.V);
+    return cudaGetLastError();
+}
+template cudaError_t instance_update<float>(Ctx &, float *, int, const float *);
+template cudaError_t instance_update<double>(Ctx &, double *, int, const double *);
+
+cudaError_t instance_totals(Ctx &c, double *d_out) {
+    launch(c, k_inst_totals, dim3(1), dim3(32), (const Inst *)c.inst.p, c.n_groups, (const int32_t *)c.row_ptr.p,
+           d_out);
+    return cudaGetLastError();
+}
+
+}  // namespace ttie

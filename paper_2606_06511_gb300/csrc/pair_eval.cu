@@ -111,14 +111,30 @@ template <typename T> struct Filtered {
     __device__ __forceinline__ static v3<float> to_f(v3<T> a) { return {(float)a.x, (float)a.y, (float)a.z}; }
 };
 
-struct Exact {
+// The undecided pairs' signs: each one through the FP32 and FP64 filters again (certified,
+// so the same decisions), and only the signs neither certifies through exact expansions.
+// With exact_only every sign is exact.
+template <typename T> struct Cascade {
+    bool exact_only;
     Stats &st;
-    template <typename T> __device__ int side(v3<T> P0, v3<T> P1, v3<T> P2, v3<T> q) {
+    __device__ int side(v3<T> P0, v3<T> P1, v3<T> P2, v3<T> q) {
+        if (!exact_only) {
+            Stats none;
+            Filtered<T> f{false, none};
+            const int s = f.side(P0, P1, P2, q);
+            if (s != kUndec) return s;
+        }
         ++st.ex;
         return orient_exact(to_d(P0), to_d(P1), to_d(P2), to_d(q));
     }
     // det[pu - p1, qv - q1, q1 - p1] = det[pu - p1, qv - p1, q1 - p1]
-    template <typename T> __device__ int over(v3<T> p1, v3<T> pu, v3<T> q1, v3<T> qv) {
+    __device__ int over(v3<T> p1, v3<T> pu, v3<T> q1, v3<T> qv) {
+        if (!exact_only) {
+            Stats none;
+            Filtered<T> f{false, none};
+            const int s = f.over(p1, pu, q1, qv);
+            if (s != kUndec) return s;
+        }
         ++st.ex;
         return orient_exact(to_d(p1), to_d(pu), to_d(qv), to_d(q1));
     }
@@ -219,15 +235,16 @@ __global__ void __launch_bounds__(kThreads) k_classify(const vec4_t<T> *__restri
     }
 }
 
-// Exact decision of the undecided pairs: the same test with every sign from exact
-// expansion arithmetic (a vertex exactly on a plane counts as zero, touching
+// Decision of the undecided pairs: the same test, every sign the filters cannot certify
+// from exact expansion arithmetic (a vertex exactly on a plane counts as zero, touching
 // intervals do not overlap).
 template <typename T>
 __global__ void k_resolve(const vec4_t<T> *__restrict__ x, const int4 *__restrict__ tri4, const int2 *__restrict__ pairs,
-                          const uint32_t *__restrict__ defer, uint32_t *__restrict__ bits, DevScalars *ds) {
+                          const uint32_t *__restrict__ defer, int exact_only, uint32_t *__restrict__ bits,
+                          DevScalars *ds) {
     const unsigned long long m = ds->n_defer;
     Stats st;
-    Exact sg{st};
+    Cascade<T> sg{exact_only != 0, st};
     for (unsigned long long k = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; k < m;
          k += (unsigned long long)gridDim.x * blockDim.x) {
         const uint32_t p = defer[k];
@@ -411,7 +428,6 @@ using ::sqrt;   // keep the float / double overloads visible next to the dual on
 using ::fabs;
 
 // Output row per intersecting pair: [t_c^0, t_c^1, d t_c^0 (18), d t_c^1 (18), pad 2].
-constexpr int kFacStride = 40;
 
 // t_c^0, t_c^1 of one intersecting pair and, with kGrad, their gradients (18 each) by the
 // chain rule through the construction above.  S is float, double or a dual number (the
@@ -534,7 +550,8 @@ cudaError_t eval_candidates(Ctx &c, const vec4_t<T> *x, const int2 *pairs, int64
         launch(c, k_classify<T>, dim3(g), dim3(kThreads), x, tri4, pairs, n, c.prm.exact_only, bits,
                                                      (uint32_t *)c.defer.p, c.ds);
         if (c.time_kernels) cudaEventRecord(c.ev[7], c.stream);
-        launch(c, k_resolve<T>, dim3(kNumSMs * 4), dim3(64), x, tri4, pairs, (const uint32_t *)c.defer.p, bits, c.ds);
+        launch(c, k_resolve<T>, dim3(kNumSMs * 4), dim3(64), x, tri4, pairs, (const uint32_t *)c.defer.p,
+               c.prm.exact_only, bits, c.ds);
         TTIE_CUDA_TRY(ensure(c, c.gtmp, (size_t)(n_words > 0 ? n_words : 1) * 4));
         launch(c, k_popc, dim3(grid_for(n_words, kThreads)), dim3(kThreads), bits, n_words, (uint32_t *)c.gtmp.p);
         TTIE_CUDA_TRY(scan_u32_u64(c, (const uint32_t *)c.gtmp.p, (unsigned long long *)c.word_off.p, n_words));

@@ -57,7 +57,8 @@ class StepInfo(ctypes.Structure):
                 ("pcg_iters", ctypes.c_int), ("pcg_rel_residual", ctypes.c_double), ("ls_trials", ctypes.c_int),
                 ("n_candidates_swept", ctypes.c_int64), ("ms_build", ctypes.c_float), ("ms_eval", ctypes.c_float),
                 ("ms_assemble", ctypes.c_float), ("ms_pcg", ctypes.c_float), ("ms_line_search", ctypes.c_float),
-                ("ms_classify", ctypes.c_float), ("ms_pcg_kernel", ctypes.c_float)]
+                ("ms_classify", ctypes.c_float), ("ms_pcg_kernel", ctypes.c_float),
+                ("pcg_block_iters", ctypes.c_int64), ("pcg_row_iters", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
