@@ -90,6 +90,9 @@ typedef struct {
                              mean edge lengths of the mesh (0 = no cap)            */
     int64_t max_candidates; /* cap on a candidate list (0 = 64 F + 1e6); a larger
                              list is refused with TTIE_ERR_CAPACITY               */
+    int inst_threads;     /* batched instances: threads per instance block (128, 256,
+                             512 or 1024); 0 = chosen per size bucket by timing the
+                             candidates on the first step (results do not depend on it) */
 } ttie_params;
 
 typedef struct ttie_ctx ttie_ctx;
@@ -97,7 +100,7 @@ typedef struct ttie_ctx ttie_ctx;
 /* Fills *p with the defaults: F32, SELF, PER_PART, tc_scale 1, mu_rel 1e-3,
  * pcg_rtol 1e-3, pcg_max_it 200, newton_max_it 200, ls_max_halvings 20,
  * armijo_c 1e-4, push_eta 0.5, exact_only 0, profile 0, max_step 1,
- * max_candidates 0. */
+ * max_candidates 0, inst_threads 0. */
 void ttie_default_params(ttie_params *p);
 
 /* Creates a context on the current CUDA device.  stream: a cudaStream_t or NULL

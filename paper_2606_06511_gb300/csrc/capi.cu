@@ -107,7 +107,9 @@ static ttie_status check_params(Ctx &c, const ttie_params *p) {
         return set_err(c, TTIE_ERR_INVALID, "psd_mode");
     if (!(p->tc_scale > 0.0) || !(p->mu_rel >= 0.0) || !(p->pcg_rtol > 0.0) || p->pcg_max_it < 1 ||
         p->newton_max_it < 0 || p->ls_max_halvings < 0 || p->ls_max_halvings > 60 || !(p->armijo_c >= 0.0) ||
-        !(p->push_eta >= 0.0) || !(p->max_step >= 0.0) || p->max_candidates < 0)
+        !(p->push_eta >= 0.0) || !(p->max_step >= 0.0) || p->max_candidates < 0 ||
+        (p->inst_threads != 0 && p->inst_threads != 128 && p->inst_threads != 256 && p->inst_threads != 512 &&
+         p->inst_threads != 1024))
         return set_err(c, TTIE_ERR_INVALID, "numeric parameter out of range");
     return TTIE_OK;
 }
@@ -130,6 +132,7 @@ void ttie_default_params(ttie_params *p) {
     p->push_eta = 0.5;
     p->max_step = 1.0;
     p->max_candidates = 0;
+    p->inst_threads = 0;
 }
 
 ttie_status ttie_create(ttie_ctx **out, const ttie_params *p, void *stream) {
@@ -175,6 +178,10 @@ void ttie_destroy(ttie_ctx *h) {
     if (c.hs) cudaFreeHost(c.hs);
     for (int i = 0; i < 12; ++i)
         if (c.ev[i]) cudaEventDestroy(c.ev[i]);
+    for (int i = 0; i < kInstBuckets; ++i)
+        if (c.aux[i]) cudaStreamDestroy(c.aux[i]);
+    for (int i = 0; i <= kInstBuckets; ++i)
+        if (c.aux_ev[i]) cudaEventDestroy(c.aux_ev[i]);
     delete h;
 }
 
@@ -551,19 +558,24 @@ static ttie_status newton_batched(Ctx &c, T *x, ttie_step_info *info) {
     inf.n_candidates_swept = ns;
     CK(instance_ls_init(c), "newton: line search");
     int trials = 0;
+    // each trial evaluates the candidates of the instances still open (the first trial: all)
+    const int2 *tp = (const int2 *)c.sweep_cand.p;
+    int64_t tn = ns;
     for (int k = -1; k <= c.prm.ls_max_halvings; ++k) {
         const double a = k < 0 ? a_max : std::ldexp(1.0, -k);
         if (k < 0 && !(a_max > 1.0)) continue;
         if (a > a_max) continue;   // beyond the swept range
         CK(axpy_positions<T>(c, (const vec4_t<T> *)c.xp.p, (const T *)c.dir.p, (T)a, (vec4_t<T> *)c.xt.p), "newton");
-        CK(eval_candidates<T>(c, (const vec4_t<T> *)c.xt.p, (const int2 *)c.sweep_cand.p, ns, TTIE_EVAL_E), "line search");
-        CK(instance_energies<T>(c, (const int2 *)c.sweep_cand.p, 1), "line search");
+        CK(eval_candidates<T>(c, (const vec4_t<T> *)c.xt.p, tp, tn, TTIE_EVAL_E), "line search");
+        CK(instance_energies<T>(c, tp, 1), "line search");
         CK(instance_ls_accept(c, a, k == c.prm.ls_max_halvings ? 1 : 0, &c.ds->n_pending), "line search");
         CK(cudaMemcpyAsync(&c.hs->n_pending, &c.ds->n_pending, sizeof(unsigned int), cudaMemcpyDeviceToHost, c.stream),
            "line search");
         CK(cudaStreamSynchronize(c.stream), "line search");
         ++trials;
         if (c.hs->n_pending == 0) break;
+        CK(instance_pending_pairs(c, (const int2 *)c.sweep_cand.p, ns, c.ls_cand, &tn), "line search");
+        tp = (const int2 *)c.ls_cand.p;
     }
     CK(instance_update<T>(c, x, c.x_stride, (const T *)c.dir.p), "newton: update");
     CK(instance_totals(c, c.ds->batch), "newton");

@@ -51,6 +51,8 @@ enum ErrBits : int {
     ERR_GROUP = 64,         // batched instances: a vertex in two groups, or a group's vertices not contiguous
 };
 
+constexpr int kInstBuckets = 4;   // size buckets of the batched PCG
+
 // Per-pair rows of the evaluation: [a, b, grad a (18), grad b (18), pad 2] (a = t_c^0, b = t_c^1)
 constexpr int kFacStride = 40;
 
@@ -58,6 +60,7 @@ constexpr int kFacStride = 40;
 // its PCG result, its energies and its line-search state.
 struct Inst {
     int first, last, count;   // rows [first, last] of the system (contiguous), count of them
+    int nnz;                  // 3x3 blocks of its rows
     int iters;                // PCG iterations
     double rel;               // PCG relative residual
     double gd;                // g . d after the step cap
@@ -112,7 +115,7 @@ cudaError_t ensure(Ctx &c, Buf &b, size_t bytes);   // grow-only, contents not k
     X(bval) X(bval2) X(bflag) X(run_start) X(row_ptr) X(col_idx) X(bsr_val) X(rhs)         \
     X(zfac) X(dinv) X(pcg_x) X(pcg_r) X(pcg_z) X(pcg_p) X(pcg_q) X(dir) X(xt) X(gtmp)      \
     X(xsave) X(sweep_cand) X(pcg_z4) X(hbuf) X(pcg_sync) X(spill) X(pcg_w) X(vgroup) X(iedge)  \
-    X(inst)
+    X(inst) X(ls_cand) X(inst_acc) X(inst_ids)
 
 struct Ctx {
     ttie_params prm;
@@ -143,11 +146,14 @@ struct Ctx {
     TTIE_BUFS(TTIE_DECL_BUF)
 #undef TTIE_DECL_BUF
     cudaEvent_t ev[12] = {};
+    cudaStream_t aux[kInstBuckets] = {};      // batched PCG: one stream per size bucket (lazily made)
+    cudaEvent_t aux_ev[kInstBuckets + 1] = {}; //   fork / join events
     int num_sms = 0;
     unsigned long long n_launch = 0;   // kernels launched through this context
     bool time_kernels = false;         // profile: events around the classification / PCG kernels
     unsigned long long pcg_epoch = 0;  // resident PCG: epochs of its flags and slots (grow only)
     int64_t tree_leaves = -1;          // leaves of the hierarchy in the BVH buffers (-1: none)
+    int inst_tuned[4] = {0, 0, 0, 0};  // batched PCG: block size chosen per size bucket (0: not yet)
 };
 
 // Every kernel of the library is launched through this helper on the context's
@@ -212,6 +218,7 @@ template <typename T> cudaError_t instance_energies(Ctx &c, const int2 *pairs, i
 template <typename T> cudaError_t instance_pcg(Ctx &c, const T *rhs, T *out);
 cudaError_t instance_ls_init(Ctx &c);
 cudaError_t instance_ls_accept(Ctx &c, double alpha, int last, unsigned int *d_pending);
+cudaError_t instance_pending_pairs(Ctx &c, const int2 *pairs, int64_t n, Buf &out, int64_t *n_out);
 template <typename T> cudaError_t instance_update(Ctx &c, T *x, int stride, const T *d_full);
 cudaError_t instance_totals(Ctx &c, double *d_out);   // 10 values
 cudaError_t brute_candidates(Ctx &c, Buf &out_pairs, int64_t *n_out);

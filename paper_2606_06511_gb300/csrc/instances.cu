@@ -14,7 +14,9 @@
 // system are sorted by vertex, so an instance's rows are then a contiguous range); the pair
 // lists come out of the LBVH with group-prefixed Morton keys, so an instance's pairs are a
 // contiguous range of every pair list too.
+#include <algorithm>
 #include <climits>
+#include <vector>
 
 #include "common.cuh"
 #include "pcg_common.cuh"
@@ -24,9 +26,8 @@ namespace ttie {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kInstThreads = 256;
 constexpr int kInstLanes = 4;             // lanes sharing a row in the product
-constexpr int kInstSmem = 46 * 1024;      // dynamic shared memory per instance block
+constexpr int kInstSmemMax = 220 * 1024;  // dynamic shared memory per instance block, at most
 
 __global__ void k_fill_i32(int32_t *p, int64_t n, int32_t v) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) p[i] = v;
@@ -89,11 +90,15 @@ __global__ void k_inst_rows(const int32_t *__restrict__ row_vertex, const int32_
     }
 }
 
-__global__ void k_inst_check(Inst *inst, int G, DevScalars *ds) {
+__global__ void k_inst_check(Inst *inst, int G, const int32_t *__restrict__ row_ptr, DevScalars *ds) {
     for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x) {
         Inst &I = inst[g];
-        if (I.count > 0 && I.last - I.first + 1 != I.count) atomicOr(&ds->err, ERR_GROUP);
+        if (I.count > 0 && I.last - I.first + 1 != I.count) {
+            atomicOr(&ds->err, ERR_GROUP);
+            I.count = 0;   // not solved: the error is reported after the step's kernels
+        }
         if (I.count == 0) I.first = 0;
+        I.nnz = I.count > 0 ? row_ptr[I.first + I.count] - row_ptr[I.first] : 0;
     }
 }
 
@@ -146,15 +151,19 @@ template <typename T> struct InstPcgArgs {
     const int32_t *row_ptr, *col_idx;
     const T *bval, *rhs;          // rhs = -g on the rows
     T *x;                         // the direction d on the rows (output)
-    T *r, *u, *p, *s, *w, *dinv;  // row vectors for instances kept in global memory
+    T *r, *u, *p, *s, *w, *dinv;  // row vectors of instances kept in global memory
+    unsigned long long *acc;      // their row partials: 3 x rows
     const double *edge;           // mean edge length per instance
+    const int32_t *ids;           // the instances of this launch
     Inst *inst;
     double mu_rel, rtol2, max_step;
     int max_it;
+    long long n_rows;
 };
 
 template <typename T> struct InstView {
     T *x, *r, *u, *p, *s, *w, *di;
+    unsigned long long *pg, *pd, *pr;   // per-row partials of r.u, w.u, r.r (accumulator bits)
     const T *val;
     bool resident;
     int nrow, nnz, r0, b0;
@@ -170,66 +179,99 @@ __device__ __forceinline__ int inst_col(const InstPcgArgs<T> &a, const InstView<
     return v.resident ? v.col[b] : a.col_idx[v.b0 + b] - v.r0;
 }
 
-// Block sums of N accumulators broadcast to every thread of the block.
-template <int N, typename T>
-__device__ __forceinline__ void block_totals(Acc<T> (&a)[N]) {
-    __shared__ unsigned long long tot[N];
-    block_sums<N, T>(a);
-    if (threadIdx.x == 0)
+// Sums of N per-row accumulator arrays part[i][0..n) in an order fixed by n alone (not by the
+// block's size): 256 virtual lanes each add rows l, l + 256, ... in order, then warp 0 adds the
+// lanes (lane j: virtual lanes j, j + 32, ..., then a shuffle tree).  Every thread gets the
+// totals.
+template <typename T, int THREADS, int N>
+__device__ __forceinline__ void rows_totals(const unsigned long long *const (&part)[N], int n, Acc<T> (&out)[N]) {
+    constexpr int VL = 256;
+    __shared__ unsigned long long lanes[N][VL];
+    __shared__ unsigned long long total[N];
+    for (int l = threadIdx.x; l < VL; l += THREADS) {
 #pragma unroll
-        for (int i = 0; i < N; ++i) tot[i] = a[i].bits();
+        for (int k = 0; k < N; ++k) {
+            Acc<T> s;
+            for (int i = l; i < n; i += VL) s.add(Acc<T>::from_bits(part[k][i]));
+            lanes[k][l] = s.bits();
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+            Acc<T> s;
+#pragma unroll
+            for (int j = 0; j < VL / 32; ++j) s.add(Acc<T>::from_bits(lanes[k][threadIdx.x + 32 * j]));
+#pragma unroll
+            for (int o = 16; o; o >>= 1) s.add(s.shfl_xor(0xffffffffu, o, 32));
+            if (threadIdx.x == 0) total[k] = s.bits();
+        }
+    }
     __syncthreads();
 #pragma unroll
-    for (int i = 0; i < N; ++i) a[i] = Acc<T>::from_bits(tot[i]);
-    __syncthreads();
+    for (int k = 0; k < N; ++k) out[k] = Acc<T>::from_bits(total[k]);
 }
 
-// PCG (Chronopoulos-Gear form, as in the grid-wide solver) of one instance per block.
-template <typename T>
-__global__ void __launch_bounds__(kInstThreads) k_pcg_instances(InstPcgArgs<T> a, int smem_bytes) {
+template <typename T, int THREADS>
+__device__ __forceinline__ Acc<T> rows_total(const unsigned long long *part, int n) {
+    const unsigned long long *const p[1] = {part};
+    Acc<T> out[1];
+    rows_totals<T, THREADS, 1>(p, n, out);
+    return out[0];
+}
+
+// PCG (Chronopoulos-Gear form, as in the grid-wide solver) of one instance per block.  Each
+// row's product is summed by kInstLanes lanes in a fixed order and every reduction goes
+// through rows_total, so the result does not depend on THREADS (which the tuner picks).
+template <typename T, int THREADS>
+__global__ void __launch_bounds__(THREADS) k_pcg_instances(InstPcgArgs<T> a, int smem_bytes) {
     extern __shared__ __align__(16) unsigned char smem[];
-    Inst *I = a.inst + blockIdx.x;
+    Inst *I = a.inst + a.ids[blockIdx.x];
     InstView<T> v;
     v.nrow = I->count;
     if (v.nrow <= 0) return;
     v.r0 = I->first;
     v.b0 = a.row_ptr[v.r0];
     v.nnz = a.row_ptr[v.r0 + v.nrow] - v.b0;
-    const size_t vec_bytes = ((size_t)v.nrow * 27 * sizeof(T) + (size_t)(v.nrow + 1) * 4 + 15) / 16 * 16;
+    const size_t vec_bytes = ((size_t)v.nrow * (27 * sizeof(T) + 24) + (size_t)(v.nrow + 1) * 4 + 15) / 16 * 16;
     const size_t mat_bytes = (size_t)v.nnz * (9 * sizeof(T) + 4);
     v.resident = vec_bytes + mat_bytes <= (size_t)smem_bytes;
     if (v.resident) {
-        v.x = (T *)smem; v.r = v.x + 3 * v.nrow; v.u = v.r + 3 * v.nrow; v.p = v.u + 3 * v.nrow;
+        v.pg = (unsigned long long *)smem; v.pd = v.pg + v.nrow; v.pr = v.pd + v.nrow;
+        v.x = (T *)(v.pr + v.nrow); v.r = v.x + 3 * v.nrow; v.u = v.r + 3 * v.nrow; v.p = v.u + 3 * v.nrow;
         v.s = v.p + 3 * v.nrow; v.w = v.s + 3 * v.nrow; v.di = v.w + 3 * v.nrow;
         v.rp = (int *)(v.di + 9 * v.nrow);
         T *val = (T *)(smem + vec_bytes);
         v.col = (int *)(val + (size_t)9 * v.nnz);
-        for (int i = threadIdx.x; i < 9 * v.nnz; i += blockDim.x) val[i] = a.bval[(size_t)v.b0 * 9 + i];
-        for (int i = threadIdx.x; i < v.nnz; i += blockDim.x) v.col[i] = a.col_idx[v.b0 + i] - v.r0;
-        for (int i = threadIdx.x; i <= v.nrow; i += blockDim.x) v.rp[i] = a.row_ptr[v.r0 + i] - v.b0;
+        for (int i = threadIdx.x; i < 9 * v.nnz; i += THREADS) val[i] = a.bval[(size_t)v.b0 * 9 + i];
+        for (int i = threadIdx.x; i < v.nnz; i += THREADS) v.col[i] = a.col_idx[v.b0 + i] - v.r0;
+        for (int i = threadIdx.x; i <= v.nrow; i += THREADS) v.rp[i] = a.row_ptr[v.r0 + i] - v.b0;
         v.val = val;
     } else {
         const size_t o = (size_t)v.r0 * 3;
         v.x = a.x + o; v.r = a.r + o; v.u = a.u + o; v.p = a.p + o; v.s = a.s + o; v.w = a.w + o;
         v.di = a.dinv + (size_t)v.r0 * 9;
+        v.pg = a.acc + v.r0; v.pd = a.acc + a.n_rows + v.r0; v.pr = a.acc + 2 * a.n_rows + v.r0;
         v.rp = nullptr;
         v.col = nullptr;
         v.val = a.bval + (size_t)v.b0 * 9;
     }
     __syncthreads();
     // mu_i from the instance's own trace, then M^-1, r = rhs, u = M^-1 r, x = p = s = 0
-    Acc<T> tr[1];
-    for (int lr = threadIdx.x; lr < v.nrow; lr += blockDim.x)
+    for (int lr = threadIdx.x; lr < v.nrow; lr += THREADS) {
+        Acc<T> t;
         for (int b = inst_rowp(a, v, lr); b < inst_rowp(a, v, lr + 1); ++b)
             if (inst_col(a, v, b) == lr) {
                 const T *m = v.val + (size_t)b * 9;
-                tr[0].add_prod(m[0] + m[4] + m[8], T(1));
+                t.add_prod(m[0] + m[4] + m[8], T(1));
                 break;
             }
-    block_totals<1, T>(tr);
-    const T mu = (T)(a.mu_rel * tr[0].value() / (3.0 * v.nrow));
-    Acc<T> red[3];
-    for (int lr = threadIdx.x; lr < v.nrow; lr += blockDim.x) {
+        v.pg[lr] = t.bits();
+    }
+    __syncthreads();
+    const T mu = (T)(a.mu_rel * rows_total<T, THREADS>(v.pg, v.nrow).value() / (3.0 * v.nrow));
+    for (int lr = threadIdx.x; lr < v.nrow; lr += THREADS) {
         const T zero9[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
         const T *diag = zero9;
         for (int b = inst_rowp(a, v, lr); b < inst_rowp(a, v, lr + 1); ++b)
@@ -243,6 +285,7 @@ __global__ void __launch_bounds__(kInstThreads) k_pcg_instances(InstPcgArgs<T> a
         const T u[3] = {di[0] * r0 + di[1] * r1 + di[2] * r2, di[3] * r0 + di[4] * r1 + di[5] * r2,
                         di[6] * r0 + di[7] * r1 + di[8] * r2};
         const T rv[3] = {r0, r1, r2};
+        Acc<T> g, q;
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
             v.x[lr * 3 + i] = T(0);
@@ -250,9 +293,11 @@ __global__ void __launch_bounds__(kInstThreads) k_pcg_instances(InstPcgArgs<T> a
             v.u[lr * 3 + i] = u[i];
             v.p[lr * 3 + i] = T(0);
             v.s[lr * 3 + i] = T(0);
-            red[0].add_prod(rv[i], u[i]);
-            red[2].add_prod(rv[i], rv[i]);
+            g.add_prod(rv[i], u[i]);
+            q.add_prod(rv[i], rv[i]);
         }
+        v.pg[lr] = g.bits();
+        v.pr[lr] = q.bits();
     }
     __syncthreads();
     const int lane = threadIdx.x & 31, sub = lane & (kInstLanes - 1);
@@ -263,7 +308,7 @@ __global__ void __launch_bounds__(kInstThreads) k_pcg_instances(InstPcgArgs<T> a
     int it = 0;
     while (true) {
         // w = (A + mu I) u and the rows' w.u
-        for (int lr = threadIdx.x / kInstLanes; lr < v.nrow; lr += kInstThreads / kInstLanes) {
+        for (int lr = threadIdx.x / kInstLanes; lr < v.nrow; lr += THREADS / kInstLanes) {
             T y0 = 0, y1 = 0, y2 = 0;
             const int be = inst_rowp(a, v, lr + 1);
             for (int b = inst_rowp(a, v, lr) + sub; b < be; b += kInstLanes) {
@@ -283,13 +328,21 @@ __global__ void __launch_bounds__(kInstThreads) k_pcg_instances(InstPcgArgs<T> a
             if (sub == 0) {
                 const T w0 = y0 + mu * v.u[lr * 3], w1 = y1 + mu * v.u[lr * 3 + 1], w2 = y2 + mu * v.u[lr * 3 + 2];
                 v.w[lr * 3] = w0; v.w[lr * 3 + 1] = w1; v.w[lr * 3 + 2] = w2;
-                red[1].add_prod(w0, v.u[lr * 3]);
-                red[1].add_prod(w1, v.u[lr * 3 + 1]);
-                red[1].add_prod(w2, v.u[lr * 3 + 2]);
+                Acc<T> wu;
+                wu.add_prod(w0, v.u[lr * 3]);
+                wu.add_prod(w1, v.u[lr * 3 + 1]);
+                wu.add_prod(w2, v.u[lr * 3 + 2]);
+                v.pd[lr] = wu.bits();
             }
         }
-        block_totals<3, T>(red);
-        const T g = red[0].approx(), d = red[1].approx(), r2 = red[2].approx();
+        __syncthreads();
+        Acc<T> tot[3];
+        {
+            const unsigned long long *const parts[3] = {v.pg, v.pd, v.pr};
+            rows_totals<T, THREADS, 3>(parts, v.nrow, tot);
+        }
+        const Acc<T> gam = tot[0], del = tot[1], rr = tot[2];
+        const T g = gam.approx(), d = del.approx(), r2 = rr.approx();
         if (it == 0) rr0 = r2;
         rr_last = r2;
         if (stop_next || it >= a.max_it || r2 <= rtol2 * rr0 || !isfinite(r2)) break;
@@ -300,7 +353,7 @@ __global__ void __launch_bounds__(kInstThreads) k_pcg_instances(InstPcgArgs<T> a
             ok = d > T(0) && isfinite(alpha);
         } else {
             beta = g / gamma_prev;
-            const T den = red[1].minus(red[0].over(alpha_prev).times(beta)).approx();
+            const T den = del.minus(gam.over(alpha_prev).times(beta)).approx();
             alpha = g / den;
             ok = den > T(0) && isfinite(alpha);
         }
@@ -312,10 +365,7 @@ __global__ void __launch_bounds__(kInstThreads) k_pcg_instances(InstPcgArgs<T> a
         }
         gamma_prev = g;
         alpha_prev = alpha;
-        red[0] = Acc<T>();
-        red[1] = Acc<T>();
-        red[2] = Acc<T>();
-        for (int lr = threadIdx.x; lr < v.nrow; lr += blockDim.x) {
+        for (int lr = threadIdx.x; lr < v.nrow; lr += THREADS) {
             T rv[3];
 #pragma unroll
             for (int i = 0; i < 3; ++i) {
@@ -329,48 +379,53 @@ __global__ void __launch_bounds__(kInstThreads) k_pcg_instances(InstPcgArgs<T> a
                 v.r[k] = rv[i];
             }
             const T *di = v.di + lr * 9;
+            Acc<T> gp, qp;
 #pragma unroll
             for (int i = 0; i < 3; ++i) {
                 const T zi = di[3 * i] * rv[0] + di[3 * i + 1] * rv[1] + di[3 * i + 2] * rv[2];
                 v.u[lr * 3 + i] = zi;
-                red[0].add_prod(rv[i], zi);
-                red[2].add_prod(rv[i], rv[i]);
+                gp.add_prod(rv[i], zi);
+                qp.add_prod(rv[i], rv[i]);
             }
+            v.pg[lr] = gp.bits();
+            v.pr[lr] = qp.bits();
         }
         ++it;
         __syncthreads();
     }
     // g.d and max |d_r| of the instance's direction; the step cap; the direction out
-    Acc<T> gd[1];
     T dm = T(0);
-    for (int lr = threadIdx.x; lr < v.nrow; lr += blockDim.x) {
+    for (int lr = threadIdx.x; lr < v.nrow; lr += THREADS) {
         T n2 = T(0);
+        Acc<T> gd;
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
             const T di = v.x[lr * 3 + i];
-            gd[0].add_prod(-a.rhs[(size_t)(v.r0 + lr) * 3 + i], di);
+            gd.add_prod(-a.rhs[(size_t)(v.r0 + lr) * 3 + i], di);
             n2 += di * di;
         }
+        v.pg[lr] = gd.bits();
         dm = fmax(dm, n2);
     }
-    __shared__ T s_max[kInstThreads / 32];
+    __shared__ T s_max[THREADS / 32];
 #pragma unroll
     for (int o = 16; o; o >>= 1) dm = fmax(dm, __shfl_xor_sync(0xffffffffu, dm, o));
     if (lane == 0) s_max[threadIdx.x >> 5] = dm;
-    block_totals<1, T>(gd);
+    __syncthreads();
+    const Acc<T> gdt = rows_total<T, THREADS>(v.pg, v.nrow);
     dm = T(0);
-    for (int k = 0; k < kInstThreads / 32; ++k) dm = fmax(dm, s_max[k]);
+    for (int k = 0; k < THREADS / 32; ++k) dm = fmax(dm, s_max[k]);
     const double dmax = sqrt((double)dm);
-    const double cap = a.max_step * a.edge[blockIdx.x];
+    const double cap = a.max_step * a.edge[a.ids[blockIdx.x]];
     const double scale = (cap > 0.0 && dmax > cap) ? cap / dmax : 1.0;
-    for (int i = threadIdx.x; i < 3 * v.nrow; i += blockDim.x) {
+    for (int i = threadIdx.x; i < 3 * v.nrow; i += THREADS) {
         const T di = v.x[i] * (T)scale;
         a.x[(size_t)v.r0 * 3 + i] = di;
     }
     if (threadIdx.x == 0) {
         I->iters = it;
         I->rel = rr0 > T(0) ? sqrt((double)rr_last / (double)rr0) : 0.0;
-        I->gd = gd[0].value() * scale;
+        I->gd = gdt.value() * scale;
     }
 }
 
@@ -398,6 +453,18 @@ __global__ void k_ls_accept(Inst *inst, int G, double alpha, double armijo_c, in
             atomicAdd(n_pending, 1u);
         }
     }
+}
+
+// Candidate pairs of the instances whose line search is still open (order kept).
+__global__ void k_pending_flags(const int2 *__restrict__ pairs, int64_t n, const int32_t *__restrict__ grp,
+                                const Inst *__restrict__ inst, uint32_t *__restrict__ flag) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        flag[i] = inst[grp[pairs[i].x]].pending ? 1u : 0u;
+}
+__global__ void k_pending_scatter(const int2 *__restrict__ pairs, int64_t n, const uint32_t *__restrict__ flag,
+                                  const unsigned long long *__restrict__ off, int2 *__restrict__ out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        if (flag[i]) out[off[i]] = pairs[i];
 }
 
 template <typename T>
@@ -474,7 +541,8 @@ cudaError_t instance_layout(Ctx &c) {
     launch(c, k_inst_init, dim3(grid_for(G, kThreads)), dim3(kThreads), (Inst *)c.inst.p, G);
     launch(c, k_inst_rows, dim3(grid_for(c.n_rows, kThreads)), dim3(kThreads), (const int32_t *)c.row_vertex.p,
            (const int32_t *)c.vgroup.p, c.ds, G, (Inst *)c.inst.p);
-    launch(c, k_inst_check, dim3(grid_for(G, kThreads)), dim3(kThreads), (Inst *)c.inst.p, G, c.ds);
+    launch(c, k_inst_check, dim3(grid_for(G, kThreads)), dim3(kThreads), (Inst *)c.inst.p, G,
+           (const int32_t *)c.row_ptr.p, c.ds);
     return cudaGetLastError();
 }
 
@@ -491,8 +559,40 @@ template <typename T> cudaError_t instance_energies(Ctx &c, const int2 *pairs, i
 template cudaError_t instance_energies<float>(Ctx &, const int2 *, int);
 template cudaError_t instance_energies<double>(Ctx &, const int2 *, int);
 
+// Size buckets of the batched PCG (rows per instance: <= 64, <= 512, <= 4096, more) and the
+// block sizes the tuner times for each bucket the first time the context meets it.  Results do
+// not depend on the block size (k_pcg_instances), so the choice only changes the speed.
+constexpr int kBucketRows[kInstBuckets - 1] = {64, 512, 4096};
+constexpr int kTunerThreads[] = {128, 256, 512, 1024};
+
+template <typename T, int THREADS>
+cudaError_t launch_inst(Ctx &c, const InstPcgArgs<T> &a, int n, int smem, cudaStream_t st) {
+    // the dynamic share is at most what the device allows a block beside the kernel's static share
+    cudaFuncAttributes fa;
+    TTIE_CUDA_TRY(cudaFuncGetAttributes(&fa, (const void *)k_pcg_instances<T, THREADS>));
+    int optin = 0;
+    TTIE_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c.device));
+    smem = std::min(smem, (int)(optin - (int)fa.sharedSizeBytes) / 16 * 16);
+    TTIE_CUDA_TRY(cudaFuncSetAttribute((const void *)k_pcg_instances<T, THREADS>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    ++c.n_launch;
+    k_pcg_instances<T, THREADS><<<dim3((unsigned)n), dim3(THREADS), (size_t)smem, st>>>(a, smem);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_inst_threads(Ctx &c, const InstPcgArgs<T> &a, int n, int smem, int threads, cudaStream_t st) {
+    switch (threads) {
+    case 128: return launch_inst<T, 128>(c, a, n, smem, st);
+    case 256: return launch_inst<T, 256>(c, a, n, smem, st);
+    case 512: return launch_inst<T, 512>(c, a, n, smem, st);
+    default: return launch_inst<T, 1024>(c, a, n, smem, st);
+    }
+}
+
 template <typename T> cudaError_t instance_pcg(Ctx &c, const T *rhs, T *out) {
     const int64_t nr = c.n_rows;
+    const int G = c.n_groups;
     const size_t n3 = (size_t)(nr > 0 ? nr : 1) * 3 * sizeof(T);
     TTIE_CUDA_TRY(ensure(c, c.pcg_r, n3));
     TTIE_CUDA_TRY(ensure(c, c.pcg_z, n3));
@@ -500,6 +600,32 @@ template <typename T> cudaError_t instance_pcg(Ctx &c, const T *rhs, T *out) {
     TTIE_CUDA_TRY(ensure(c, c.pcg_q, n3));
     TTIE_CUDA_TRY(ensure(c, c.pcg_w, n3));
     TTIE_CUDA_TRY(ensure(c, c.dinv, (size_t)(nr > 0 ? nr : 1) * 9 * sizeof(T)));
+    TTIE_CUDA_TRY(ensure(c, c.inst_acc, (size_t)(nr > 0 ? nr : 1) * 3 * 8));
+    TTIE_CUDA_TRY(ensure(c, c.inst_ids, (size_t)(G > 0 ? G : 1) * 4));
+    // buckets by size, and the shared memory that keeps a bucket's largest instance resident
+    std::vector<Inst> h(G);
+    TTIE_CUDA_TRY(cudaMemcpyAsync(h.data(), c.inst.p, (size_t)G * sizeof(Inst), cudaMemcpyDeviceToHost, c.stream));
+    TTIE_CUDA_TRY(cudaStreamSynchronize(c.stream));
+    std::vector<int32_t> ids;
+    int start[kInstBuckets + 1] = {0}, smem[kInstBuckets] = {0};
+    for (int b = 0; b < kInstBuckets; ++b) {
+        start[b] = (int)ids.size();
+        for (int g = 0; g < G; ++g) {
+            const int rows = h[g].count;
+            if (rows <= 0) continue;
+            int bb = kInstBuckets - 1;
+            for (int k = 0; k < kInstBuckets - 1; ++k)
+                if (rows <= kBucketRows[k]) { bb = k; break; }
+            if (bb != b) continue;
+            ids.push_back(g);
+            const size_t need = ((size_t)rows * (27 * sizeof(T) + 24) + (size_t)(rows + 1) * 4 + 15) / 16 * 16 +
+                                (size_t)h[g].nnz * (9 * sizeof(T) + 4);
+            smem[b] = (int)std::min<size_t>(std::max<size_t>((size_t)smem[b], (need + 15) / 16 * 16), kInstSmemMax);
+        }
+    }
+    start[kInstBuckets] = (int)ids.size();
+    if (!ids.empty())
+        TTIE_CUDA_TRY(cudaMemcpyAsync(c.inst_ids.p, ids.data(), ids.size() * 4, cudaMemcpyHostToDevice, c.stream));
     InstPcgArgs<T> a;
     a.row_ptr = (const int32_t *)c.row_ptr.p;
     a.col_idx = (const int32_t *)c.col_idx.p;
@@ -512,18 +638,55 @@ template <typename T> cudaError_t instance_pcg(Ctx &c, const T *rhs, T *out) {
     a.s = (T *)c.pcg_q.p;
     a.w = (T *)c.pcg_w.p;
     a.dinv = (T *)c.dinv.p;
+    a.acc = (unsigned long long *)c.inst_acc.p;
     a.edge = (const double *)c.iedge.p;
     a.inst = (Inst *)c.inst.p;
     a.mu_rel = c.prm.mu_rel;
     a.rtol2 = c.prm.pcg_rtol * c.prm.pcg_rtol;
     a.max_step = c.prm.max_step;
     a.max_it = c.prm.pcg_max_it;
-    TTIE_CUDA_TRY(cudaFuncSetAttribute((const void *)k_pcg_instances<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       kInstSmem));
-    ++c.n_launch;
+    a.n_rows = nr;
+    // tuning (first time a bucket is met): every candidate block size timed on the main stream
+    for (int b = 0; b < kInstBuckets; ++b) {
+        const int n = start[b + 1] - start[b];
+        if (n == 0 || c.prm.inst_threads > 0 || c.inst_tuned[b] > 0) continue;
+        a.ids = (const int32_t *)c.inst_ids.p + start[b];
+        cudaEvent_t e0, e1;
+        TTIE_CUDA_TRY(cudaEventCreate(&e0));
+        TTIE_CUDA_TRY(cudaEventCreate(&e1));
+        float best = 0.f;
+        int pick = 0;
+        for (int t : kTunerThreads) {
+            TTIE_CUDA_TRY(cudaEventRecord(e0, c.stream));
+            TTIE_CUDA_TRY(launch_inst_threads<T>(c, a, n, smem[b], t, c.stream));
+            TTIE_CUDA_TRY(cudaEventRecord(e1, c.stream));
+            TTIE_CUDA_TRY(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (pick == 0 || ms < best) { best = ms; pick = t; }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        c.inst_tuned[b] = pick;
+    }
+    // the buckets run side by side, one stream each, forked from and joined to the main stream
+    for (int b = 0; b < kInstBuckets; ++b) {
+        if (!c.aux[b]) TTIE_CUDA_TRY(cudaStreamCreateWithFlags(&c.aux[b], cudaStreamNonBlocking));
+        if (!c.aux_ev[b]) TTIE_CUDA_TRY(cudaEventCreateWithFlags(&c.aux_ev[b], cudaEventDisableTiming));
+    }
+    if (!c.aux_ev[kInstBuckets]) TTIE_CUDA_TRY(cudaEventCreateWithFlags(&c.aux_ev[kInstBuckets], cudaEventDisableTiming));
     if (c.prm.profile) cudaEventRecord(c.ev[8], c.stream);
-    k_pcg_instances<T><<<dim3((unsigned)(c.n_groups > 0 ? c.n_groups : 1)), dim3(kInstThreads), kInstSmem, c.stream>>>(
-        a, kInstSmem);
+    TTIE_CUDA_TRY(cudaEventRecord(c.aux_ev[kInstBuckets], c.stream));
+    for (int b = 0; b < kInstBuckets; ++b) {
+        const int n = start[b + 1] - start[b];
+        if (n == 0) continue;
+        a.ids = (const int32_t *)c.inst_ids.p + start[b];
+        const int threads = c.prm.inst_threads > 0 ? c.prm.inst_threads : c.inst_tuned[b];
+        TTIE_CUDA_TRY(cudaStreamWaitEvent(c.aux[b], c.aux_ev[kInstBuckets], 0));
+        TTIE_CUDA_TRY(launch_inst_threads<T>(c, a, n, smem[b], threads, c.aux[b]));
+        TTIE_CUDA_TRY(cudaEventRecord(c.aux_ev[b], c.aux[b]));
+        TTIE_CUDA_TRY(cudaStreamWaitEvent(c.stream, c.aux_ev[b], 0));
+    }
     if (c.prm.profile) cudaEventRecord(c.ev[9], c.stream);
     return cudaGetLastError();
 }
@@ -539,6 +702,27 @@ cudaError_t instance_ls_accept(Ctx &c, double alpha, int last, unsigned int *d_p
     TTIE_CUDA_TRY(cudaMemsetAsync(d_pending, 0, sizeof(unsigned int), c.stream));
     launch(c, k_ls_accept, dim3(grid_for(c.n_groups, kThreads)), dim3(kThreads), (Inst *)c.inst.p, c.n_groups, alpha,
            c.prm.armijo_c, last, d_pending);
+    return cudaGetLastError();
+}
+
+cudaError_t instance_pending_pairs(Ctx &c, const int2 *pairs, int64_t n, Buf &out, int64_t *n_out) {
+    *n_out = 0;
+    if (n <= 0) return cudaSuccess;
+    TTIE_CUDA_TRY(ensure(c, c.gtmp, (size_t)n * 4));
+    TTIE_CUDA_TRY(ensure(c, c.word_off, (size_t)(n + 1) * 8));
+    auto *flag = (uint32_t *)c.gtmp.p;
+    auto *off = (unsigned long long *)c.word_off.p;
+    launch(c, k_pending_flags, dim3(grid_for(n, kThreads)), dim3(kThreads), pairs, n, (const int32_t *)c.grp.p,
+           (const Inst *)c.inst.p, flag);
+    TTIE_CUDA_TRY(scan_u32_u64(c, flag, off, n));
+    TTIE_CUDA_TRY(cudaMemcpyAsync(&c.hs->n_cand, off + n, 8, cudaMemcpyDeviceToHost, c.stream));
+    TTIE_CUDA_TRY(cudaStreamSynchronize(c.stream));
+    const int64_t m = (int64_t)c.hs->n_cand;
+    TTIE_CUDA_TRY(ensure(c, out, (size_t)(m > 0 ? m : 1) * sizeof(int2)));
+    if (m > 0)
+        launch(c, k_pending_scatter, dim3(grid_for(n, kThreads)), dim3(kThreads), pairs, n, (const uint32_t *)flag,
+               (const unsigned long long *)off, (int2 *)out.p);
+    *n_out = m;
     return cudaGetLastError();
 }
 

@@ -132,3 +132,43 @@ def test_batched_layout_errors(ttie, batch):
     with pytest.raises(ttie.TTIEError) as e:
         ctx.newton_step(x)
     assert e.value.status == ttie.TTIE_ERR_INVALID
+
+
+def test_batched_block_size_does_not_change_results(ttie, batch):
+    """Every reduction of the per-instance PCG runs in an order fixed by the instance alone, so
+    the block size the tuner picks changes the speed, not a bit of the result."""
+    m, vo, to = batch
+    outs = []
+    for t in (128, 512, 1024, 0):
+        x, tri, grp = _dev(m, torch.float32)
+        ctx = ttie.Context(pair_mode=MODE_INTRA, inst_threads=t)
+        ctx.build_bvh(x, tri, grp)
+        for _ in range(2):
+            ctx.newton_step(x)
+        outs.append(x.cpu())
+    for o in outs[1:]:
+        assert torch.equal(o, outs[0])
+
+
+def test_batched_large_instances_in_global_memory(ttie):
+    """Instances too large for one block's shared memory keep their PCG vectors and matrix rows
+    in global memory; the step still equals stepping each instance alone."""
+    m, vo, to = ti.ellipsoid_batch(2, seed=7, f_min=12000, f_max=16000)
+    x, tri, grp = _dev(m, torch.float64)
+    prm = dict(precision=ttie.F64, pcg_rtol=1e-9, pcg_max_it=4000)
+    ctx = ttie.Context(pair_mode=MODE_INTRA, **prm)
+    ctx.build_bvh(x, tri, grp)
+    info = ctx.newton_step(x)
+    # FP64: 244 B per row and 76 B per 3x3 block; an instance needs more than a block's 220 KB
+    assert (info["n_rows"] * 244 + info["nnzb"] * 76) / 2 > 220 * 1024
+    xb = x.cpu().numpy()
+    for k in range(2):
+        mk = _instance(m, vo, to, k)
+        xs, ts, _ = _dev(mk, torch.float64)
+        c1 = ttie.Context(pair_mode=0, **prm)
+        c1.build_bvh(xs, ts)
+        c1.newton_step(xs)
+        step_alone = xs.cpu().numpy() - mk.x
+        step_batch = xb[vo[k]:vo[k + 1]] - m.x[vo[k]:vo[k + 1]]
+        scale = max(np.abs(step_alone).max(), 1e-300)
+        assert np.abs(step_batch - step_alone).max() <= 1e-6 * scale, k
