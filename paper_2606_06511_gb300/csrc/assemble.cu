@@ -741,7 +741,7 @@ __device__ __forceinline__ Acc<T> resident_product(const PcgArgs<T> &a, const Re
 
 template <typename T>
 __global__ void __launch_bounds__(kPcgThreads) k_pcg_resident(PcgArgs<T> a, int rows_per_block, int smem_bytes,
-                                                             unsigned long long epoch0) {
+                                                             unsigned long long epoch0, int lean) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ unsigned s_bits[kMaxGridPcg / 32];
     __shared__ int s_dep[kMaxDeps];
@@ -755,10 +755,21 @@ __global__ void __launch_bounds__(kPcgThreads) k_pcg_resident(PcgArgs<T> a, int 
     const long long row0 = (long long)blockIdx.x * R;
     ResidentView<T> v;
     v.nrow = (int)max(0LL, min((long long)R, nr - row0));
-    v.x = (T *)smem; v.r = v.x + 3 * R; v.u = v.r + 3 * R; v.p = v.u + 3 * R; v.s = v.p + 3 * R; v.w = v.s + 3 * R;
-    v.di = v.w + 3 * R;
-    v.rp = (int *)(v.di + 9 * R);
-    const size_t vec_bytes = ((size_t)R * 27 * sizeof(T) + (size_t)(R + 1) * sizeof(int) + 15) / 16 * 16;
+    // lean: x and the inverse diagonal blocks (read or written once per row and iteration) stay
+    // in global memory so that larger row ranges fit
+    size_t vec_bytes;
+    if (lean) {
+        v.r = (T *)smem; v.u = v.r + 3 * R; v.p = v.u + 3 * R; v.s = v.p + 3 * R; v.w = v.s + 3 * R;
+        v.rp = (int *)(v.w + 3 * R);
+        v.x = a.x + row0 * 3;
+        v.di = (T *)a.dinv + row0 * 9;
+        vec_bytes = ((size_t)R * 15 * sizeof(T) + (size_t)(R + 1) * sizeof(int) + 15) / 16 * 16;
+    } else {
+        v.x = (T *)smem; v.r = v.x + 3 * R; v.u = v.r + 3 * R; v.p = v.u + 3 * R; v.s = v.p + 3 * R; v.w = v.s + 3 * R;
+        v.di = v.w + 3 * R;
+        v.rp = (int *)(v.di + 9 * R);
+        vec_bytes = ((size_t)R * 27 * sizeof(T) + (size_t)(R + 1) * sizeof(int) + 15) / 16 * 16;
+    }
     v.b_begin = v.nrow ? a.row_ptr[row0] : 0;
     v.nnz = v.nrow ? a.row_ptr[row0 + v.nrow] - v.b_begin : 0;
     const size_t mat_bytes = ((size_t)v.nnz * (9 * sizeof(T) + sizeof(int)) + 15) / 16 * 16;
@@ -769,13 +780,14 @@ __global__ void __launch_bounds__(kPcgThreads) k_pcg_resident(PcgArgs<T> a, int 
     v.gu = (T *)(smem + vec_bytes + mat_bytes);
     // load the block's rows (x = 0, r, u = M^-1 r and M^-1 from the setup kernel; p = s = 0)
     for (int i = threadIdx.x; i < 3 * v.nrow; i += blockDim.x) {
-        v.x[i] = a.x[row0 * 3 + i];
+        if (!lean) v.x[i] = a.x[row0 * 3 + i];
         v.r[i] = a.r[row0 * 3 + i];
         v.u[i] = a.z[row0 * 3 + i];
         v.p[i] = T(0);
         v.s[i] = T(0);
     }
-    for (int i = threadIdx.x; i < 9 * v.nrow; i += blockDim.x) v.di[i] = a.dinv[row0 * 9 + i];
+    if (!lean)
+        for (int i = threadIdx.x; i < 9 * v.nrow; i += blockDim.x) v.di[i] = a.dinv[row0 * 9 + i];
     for (int i = threadIdx.x; i <= v.nrow; i += blockDim.x) {
         v.rp[i] = a.row_ptr[row0 + i] - v.b_begin;
         if (TTIE_BAD(ds, v.rp[i] >= 0 && v.rp[i] <= v.nnz, 43, v.rp[i])) v.rp[i] = 0;
@@ -905,7 +917,8 @@ __global__ void __launch_bounds__(kPcgThreads) k_pcg_resident(PcgArgs<T> a, int 
             st_relaxed_u64(&a.flags[blockIdx.x], fe);
         }
     }
-    for (int i = threadIdx.x; i < 3 * v.nrow; i += blockDim.x) a.x[row0 * 3 + i] = v.x[i];
+    if (!lean)
+        for (int i = threadIdx.x; i < 3 * v.nrow; i += blockDim.x) a.x[row0 * 3 + i] = v.x[i];
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         ds->pcg_iters = it;
         ds->red[0] = gamma.value();
@@ -1152,7 +1165,9 @@ cudaError_t pcg_solve(Ctx &c, const T *rhs, T *out, double rtol, int max_it) {
     // rows resident in shared memory when a block's vectors fit; else the global-memory kernel
     const int64_t rows_per_block = (nr + blocks - 1) / blocks;
     const size_t vec_bytes = ((size_t)rows_per_block * 27 * sizeof(T) + (size_t)(rows_per_block + 1) * 4 + 15) / 16 * 16;
-    const bool resident = vec_bytes <= (size_t)kResidentSmem;
+    const size_t lean_bytes = ((size_t)rows_per_block * 15 * sizeof(T) + (size_t)(rows_per_block + 1) * 4 + 15) / 16 * 16;
+    int lean = vec_bytes <= (size_t)kResidentSmem ? 0 : 1;
+    const bool resident = lean_bytes <= (size_t)kResidentSmem;
     if (!c.pcg_sync.p) {   // fixed size, zeroed once: epochs only grow over the context's life
         TTIE_CUDA_TRY(ensure(c, c.pcg_sync, (size_t)kMaxGridPcg * (2 * sizeof(RedSlot) + sizeof(unsigned long long))));
         TTIE_CUDA_TRY(cudaMemsetAsync(c.pcg_sync.p, 0, c.pcg_sync.bytes, c.stream));
@@ -1167,7 +1182,7 @@ cudaError_t pcg_solve(Ctx &c, const T *rhs, T *out, double rtol, int max_it) {
                                            kResidentSmem));
         int rpb = (int)rows_per_block, smem = kResidentSmem;
         unsigned long long e0 = c.pcg_epoch;
-        void *kargs[] = {&args, &rpb, &smem, &e0};
+        void *kargs[] = {&args, &rpb, &smem, &e0, &lean};
         TTIE_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)k_pcg_resident<T>, dim3((unsigned)blocks),
                                                   dim3(kPcgThreads), kargs, (size_t)kResidentSmem, c.stream));
     } else {
