@@ -182,6 +182,7 @@ void ttie_destroy(ttie_ctx *h) {
         if (c.aux[i]) cudaStreamDestroy(c.aux[i]);
     for (int i = 0; i <= kInstBuckets; ++i)
         if (c.aux_ev[i]) cudaEventDestroy(c.aux_ev[i]);
+    if (c.cap_stream) cudaStreamDestroy(c.cap_stream);
     delete h;
 }
 
@@ -558,13 +559,36 @@ static ttie_status newton_batched(Ctx &c, T *x, ttie_step_info *info) {
     inf.n_candidates_swept = ns;
     CK(instance_ls_init(c), "newton: line search");
     int trials = 0;
-    // each trial evaluates the candidates of the instances still open (the first trial: all)
+#ifndef TTIE_CHECKS
+    // every trial (the candidates of the instances still open, trial positions, energies per
+    // instance, acceptance) is one CUDA graph, captured here and replayed with the next step
+    cudaGraphExec_t exec = nullptr;
+    unsigned long long graph_kernels = 0;
+    CK(instance_trial_graph<T>(c, (const vec4_t<T> *)c.xp.p, (const T *)c.dir.p, (vec4_t<T> *)c.xt.p,
+                               (const int2 *)c.sweep_cand.p, ns, &exec, &graph_kernels), "line search: graph");
+    cudaError_t ge = cudaSuccess;
+    for (int k = -1; k <= c.prm.ls_max_halvings; ++k) {
+        const double a = k < 0 ? a_max : std::ldexp(1.0, -k);
+        if (k < 0 && !(a_max > 1.0)) continue;
+        if (a > a_max) continue;   // beyond the swept range
+        c.hs->ls_alpha = a;
+        c.hs->ls_last = k == c.prm.ls_max_halvings ? 1.0 : 0.0;
+        if ((ge = cudaGraphLaunch(exec, c.stream)) != cudaSuccess) break;
+        if ((ge = cudaStreamSynchronize(c.stream)) != cudaSuccess) break;
+        c.n_launch += graph_kernels;
+        ++trials;
+        if (c.hs->n_pending == 0) break;
+    }
+    cudaGraphExecDestroy(exec);
+    CK(ge, "line search: graph replay");
+#else
+    // self-checking builds synchronise after every launch, which a capture does not allow
     const int2 *tp = (const int2 *)c.sweep_cand.p;
     int64_t tn = ns;
     for (int k = -1; k <= c.prm.ls_max_halvings; ++k) {
         const double a = k < 0 ? a_max : std::ldexp(1.0, -k);
         if (k < 0 && !(a_max > 1.0)) continue;
-        if (a > a_max) continue;   // beyond the swept range
+        if (a > a_max) continue;
         CK(axpy_positions<T>(c, (const vec4_t<T> *)c.xp.p, (const T *)c.dir.p, (T)a, (vec4_t<T> *)c.xt.p), "newton");
         CK(eval_candidates<T>(c, (const vec4_t<T> *)c.xt.p, tp, tn, TTIE_EVAL_E), "line search");
         CK(instance_energies<T>(c, tp, 1), "line search");
@@ -577,6 +601,7 @@ static ttie_status newton_batched(Ctx &c, T *x, ttie_step_info *info) {
         CK(instance_pending_pairs(c, (const int2 *)c.sweep_cand.p, ns, c.ls_cand, &tn), "line search");
         tp = (const int2 *)c.ls_cand.p;
     }
+#endif
     CK(instance_update<T>(c, x, c.x_stride, (const T *)c.dir.p), "newton: update");
     CK(instance_totals(c, c.ds->batch), "newton");
     c.have_eval = false;   // the last evaluation ran on the line-search candidates

@@ -95,6 +95,7 @@ struct DevScalars {
     unsigned int bar_count;                // arrivals at the PCG kernels' grid all-reduce
     unsigned int bar_gen;                  // its generation (bumped on release)
     unsigned int n_pending;                // batched line search: instances still open
+    double ls_alpha, ls_last;              // batched line search: trial step, 1 on the last trial
     double batch[10];                      // batched step totals (instance_totals)
 };
 
@@ -115,7 +116,8 @@ cudaError_t ensure(Ctx &c, Buf &b, size_t bytes);   // grow-only, contents not k
     X(bval) X(bval2) X(bflag) X(run_start) X(row_ptr) X(col_idx) X(bsr_val) X(rhs)         \
     X(zfac) X(dinv) X(pcg_x) X(pcg_r) X(pcg_z) X(pcg_p) X(pcg_q) X(dir) X(xt) X(gtmp)      \
     X(xsave) X(sweep_cand) X(pcg_z4) X(hbuf) X(pcg_sync) X(spill) X(pcg_w) X(vgroup) X(iedge)  \
-    X(inst) X(ls_cand) X(inst_acc) X(inst_ids)
+    X(inst) X(ls_cand) X(inst_acc) X(inst_ids) X(ab) X(ls_flag)  \
+    X(ls_off) X(ls_scalars)
 
 struct Ctx {
     ttie_params prm;
@@ -147,6 +149,7 @@ struct Ctx {
 #undef TTIE_DECL_BUF
     cudaEvent_t ev[12] = {};
     cudaStream_t aux[kInstBuckets] = {};      // batched PCG: one stream per size bucket (lazily made)
+    cudaStream_t cap_stream = nullptr;         // stream that graphs are captured on (lazily made)
     cudaEvent_t aux_ev[kInstBuckets + 1] = {}; //   fork / join events
     int num_sms = 0;
     unsigned long long n_launch = 0;   // kernels launched through this context
@@ -219,6 +222,11 @@ template <typename T> cudaError_t instance_pcg(Ctx &c, const T *rhs, T *out);
 cudaError_t instance_ls_init(Ctx &c);
 cudaError_t instance_ls_accept(Ctx &c, double alpha, int last, unsigned int *d_pending);
 cudaError_t instance_pending_pairs(Ctx &c, const int2 *pairs, int64_t n, Buf &out, int64_t *n_out);
+// One line-search trial of every open instance as a CUDA graph (capture once per Newton step,
+// replay per trial after writing the step into the host mirror's ls_alpha / ls_last).
+template <typename T>
+cudaError_t instance_trial_graph(Ctx &c, const vec4_t<T> *xp, const T *dir, vec4_t<T> *xt, const int2 *cand,
+                                 int64_t ns, cudaGraphExec_t *exec, unsigned long long *kernels);
 template <typename T> cudaError_t instance_update(Ctx &c, T *x, int stride, const T *d_full);
 cudaError_t instance_totals(Ctx &c, double *d_out);   // 10 values
 cudaError_t brute_candidates(Ctx &c, Buf &out_pairs, int64_t *n_out);
@@ -230,6 +238,10 @@ template <typename T> cudaError_t mean_edge_length(Ctx &c, const vec4_t<T> *x, d
 // Energy lands in ds->energy, count in ds->n_active.
 template <typename T> cudaError_t eval_candidates(Ctx &c, const vec4_t<T> *x, const int2 *pairs, int64_t n,
                                                   unsigned what);
+template <typename T> cudaError_t prepare_energy_eval(Ctx &c, int64_t n_cap);
+template <typename T>
+cudaError_t energy_eval_nosync(Ctx &c, const vec4_t<T> *x, const int2 *pairs, int64_t n_cap,
+                               const unsigned long long *d_n);
 
 // ------------------------------------------------------------------ assembly / solve (assemble.cu)
 template <typename T> cudaError_t assemble_system(Ctx &c, T *grad_out_V3);

@@ -467,6 +467,35 @@ __global__ void k_pending_scatter(const int2 *__restrict__ pairs, int64_t n, con
         if (flag[i]) out[off[i]] = pairs[i];
 }
 
+// Trial positions x + alpha d with the step read from device memory (graph replays).
+template <typename T>
+__global__ void k_axpy_dev(const vec4_t<T> *__restrict__ x, const T *__restrict__ d, const DevScalars *ds, int64_t V,
+                           vec4_t<T> *__restrict__ out) {
+    const T a = (T)ds->ls_alpha;
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < V; v += (int64_t)gridDim.x * blockDim.x) {
+        vec4_t<T> p = x[v];
+        p.x += a * d[v * 3]; p.y += a * d[v * 3 + 1]; p.z += a * d[v * 3 + 2];
+        out[v] = p;
+    }
+}
+
+__global__ void k_ls_accept_dev(Inst *inst, int G, double armijo_c, DevScalars *ds) {
+    const double alpha = ds->ls_alpha;
+    const bool last = ds->ls_last != 0.0;
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x) {
+        Inst &I = inst[g];
+        if (!I.pending) continue;
+        if (I.nt == 0 || I.et <= I.e0 + armijo_c * alpha * I.gd || last) {
+            I.alpha = alpha;
+            I.e_new = I.et;
+            I.n_new = I.nt;
+            I.pending = 0;
+        } else {
+            atomicAdd(&ds->n_pending, 1u);
+        }
+    }
+}
+
 template <typename T>
 __global__ void k_update_grouped(T *__restrict__ x, int stride, const T *__restrict__ d,
                                  const int32_t *__restrict__ vgroup, const Inst *__restrict__ inst, int64_t V) {
@@ -725,6 +754,73 @@ cudaError_t instance_pending_pairs(Ctx &c, const int2 *pairs, int64_t n, Buf &ou
     *n_out = m;
     return cudaGetLastError();
 }
+
+template <typename T>
+cudaError_t instance_trial_graph(Ctx &c, const vec4_t<T> *xp, const T *dir, vec4_t<T> *xt, const int2 *cand,
+                                 int64_t ns, cudaGraphExec_t *exec, unsigned long long *kernels) {
+    const int G = c.n_groups;
+    // everything sized before the capture: nothing may be allocated inside it
+    TTIE_CUDA_TRY(prepare_energy_eval<T>(c, ns));
+    TTIE_CUDA_TRY(ensure(c, c.ls_flag, (size_t)(ns > 0 ? ns : 1) * 4));
+    TTIE_CUDA_TRY(ensure(c, c.ls_off, (size_t)(ns + 1) * 8));
+    TTIE_CUDA_TRY(ensure(c, c.ls_cand, (size_t)(ns > 0 ? ns : 1) * sizeof(int2)));
+    auto *flag = (uint32_t *)c.ls_flag.p;
+    auto *off = (unsigned long long *)c.ls_off.p;
+    const unsigned long long launches0 = c.n_launch;
+    cudaGraph_t graph = nullptr;
+    // captured on a stream of the context's own (the caller's stream may be the legacy default
+    // stream, which cannot be captured); the graph is then launched on the caller's stream
+    if (!c.cap_stream) TTIE_CUDA_TRY(cudaStreamCreateWithFlags(&c.cap_stream, cudaStreamNonBlocking));
+    const cudaStream_t main_stream = c.stream;
+    c.stream = c.cap_stream;
+    cudaError_t eb = cudaStreamBeginCapture(c.stream, cudaStreamCaptureModeThreadLocal);
+    if (eb != cudaSuccess) {
+        c.stream = main_stream;
+        return eb;
+    }
+    cudaError_t e = cudaSuccess;
+    do {
+        if ((e = cudaMemcpyAsync(&c.ds->ls_alpha, &c.hs->ls_alpha, 2 * sizeof(double), cudaMemcpyHostToDevice,
+                                 c.stream)) != cudaSuccess) break;
+        // the candidates of the instances still open (their count stays on the device)
+        if (ns > 0) {
+            launch(c, k_pending_flags, dim3(grid_for(ns, kThreads)), dim3(kThreads), cand, ns, (const int32_t *)c.grp.p,
+                   (const Inst *)c.inst.p, flag);
+            if ((e = scan_u32_u64(c, (const uint32_t *)flag, off, ns)) != cudaSuccess) break;
+            launch(c, k_pending_scatter, dim3(grid_for(ns, kThreads)), dim3(kThreads), cand, ns, (const uint32_t *)flag,
+                   (const unsigned long long *)off, (int2 *)c.ls_cand.p);
+        }
+        launch(c, k_axpy_dev<T>, dim3(grid_for(c.V, kThreads)), dim3(kThreads), xp, dir, (const DevScalars *)c.ds, c.V,
+               xt);
+        if ((e = energy_eval_nosync<T>(c, xt, (const int2 *)c.ls_cand.p, ns, (const unsigned long long *)off + ns)) !=
+            cudaSuccess)
+            break;
+        launch(c, k_inst_clear_segments, dim3(grid_for(G, kThreads)), dim3(kThreads), (Inst *)c.inst.p, G);
+        if (ns > 0)
+            launch(c, k_inst_segments, dim3(grid_for(ns, kThreads)), dim3(kThreads), (const int2 *)c.ls_cand.p,
+                   (const uint32_t *)c.active.p, (const int32_t *)c.grp.p, (const DevScalars *)c.ds, (Inst *)c.inst.p);
+        launch(c, k_inst_energy<T>, dim3(grid_for((int64_t)G * 32, kThreads)), dim3(kThreads), (const T *)c.ab.p, 2, G, 1,
+               (Inst *)c.inst.p);
+        if ((e = cudaMemsetAsync(&c.ds->n_pending, 0, sizeof(unsigned int), c.stream)) != cudaSuccess) break;
+        launch(c, k_ls_accept_dev, dim3(grid_for(G, kThreads)), dim3(kThreads), (Inst *)c.inst.p, G, c.prm.armijo_c,
+               c.ds);
+        if ((e = cudaMemcpyAsync(&c.hs->n_pending, &c.ds->n_pending, sizeof(unsigned int), cudaMemcpyDeviceToHost,
+                                 c.stream)) != cudaSuccess) break;
+        e = cudaGetLastError();
+    } while (false);
+    const cudaError_t ec = cudaStreamEndCapture(c.stream, &graph);
+    c.stream = main_stream;
+    *kernels = c.n_launch - launches0;
+    c.n_launch = launches0;   // captured, not launched: every replay counts them
+    if (e == cudaSuccess) e = ec;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    return e;
+}
+template cudaError_t instance_trial_graph<float>(Ctx &, const float4 *, const float *, float4 *, const int2 *, int64_t,
+                                                 cudaGraphExec_t *, unsigned long long *);
+template cudaError_t instance_trial_graph<double>(Ctx &, const dvec4 *, const double *, dvec4 *, const int2 *, int64_t,
+                                                  cudaGraphExec_t *, unsigned long long *);
 
 template <typename T> cudaError_t instance_update(Ctx &c, T *x, int stride, const T *d_full) {
     launch(c, k_update_grouped<T>, dim3(grid_for(c.V, kThreads)), dim3(kThreads), x, stride, d_full,

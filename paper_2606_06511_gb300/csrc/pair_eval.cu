@@ -197,11 +197,13 @@ __device__ __forceinline__ int classify(const v3<T> A[3], const v3<T> B[3], Sign
 
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_classify(const vec4_t<T> *__restrict__ x, const int4 *__restrict__ tri4,
-                                                       const int2 *__restrict__ pairs, int64_t n, int exact_only,
+                                                       const int2 *__restrict__ pairs, int64_t n,
+                                                       const unsigned long long *__restrict__ d_n, int exact_only,
                                                        uint32_t *__restrict__ bits, uint32_t *__restrict__ defer,
                                                        DevScalars *ds) {
     const int lane = threadIdx.x & 31;
-    const int64_t n_words = (n + 31) / 32;
+    const int64_t n_words = (n + 31) / 32;   // words of the list's capacity n; pairs at or past *d_n count as 0
+    if (d_n) n = (int64_t)min((unsigned long long)n, *d_n);
     const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t n_warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     Stats st;
@@ -475,7 +477,8 @@ __device__ __forceinline__ void pair_tc(v3<S> A[3], v3<S> B[3], S tc_scale, S &a
 template <typename T, bool kGrad>
 __global__ void __launch_bounds__(128) k_derivs(const vec4_t<T> *__restrict__ x, const int4 *__restrict__ tri4,
                                                 const int2 *__restrict__ pairs, const uint32_t *__restrict__ active,
-                                                T tc_scale, T *__restrict__ fac, double *partials, DevScalars *ds) {
+                                                T tc_scale, T *__restrict__ fac, int stride, double *partials,
+                                                DevScalars *ds) {
     const unsigned long long n_act = ds->n_active;
     double e_sum = 0.0;
     for (unsigned long long k = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; k < n_act;
@@ -485,7 +488,7 @@ __global__ void __launch_bounds__(128) k_derivs(const vec4_t<T> *__restrict__ x,
         T a, b, ga[18], gb[18];
         pair_tc<T, kGrad>(A, B, tc_scale, a, b, ga, gb);
         e_sum += (double)(a * b) * (double)(a * b);
-        T *row = fac + k * kFacStride;
+        T *row = fac + k * stride;
         row[0] = a;
         row[1] = b;
         if (kGrad) {
@@ -547,8 +550,8 @@ cudaError_t eval_candidates(Ctx &c, const vec4_t<T> *x, const int2 *pairs, int64
     if (n > 0) {
         const unsigned g = grid_for(n_words * 32, kThreads, (int64_t)kNumSMs * 8);
         if (c.time_kernels) cudaEventRecord(c.ev[6], c.stream);
-        launch(c, k_classify<T>, dim3(g), dim3(kThreads), x, tri4, pairs, n, c.prm.exact_only, bits,
-                                                     (uint32_t *)c.defer.p, c.ds);
+        launch(c, k_classify<T>, dim3(g), dim3(kThreads), x, tri4, pairs, n, (const unsigned long long *)nullptr,
+               c.prm.exact_only, bits, (uint32_t *)c.defer.p, c.ds);
         if (c.time_kernels) cudaEventRecord(c.ev[7], c.stream);
         launch(c, k_resolve<T>, dim3(kNumSMs * 4), dim3(64), x, tri4, pairs, (const uint32_t *)c.defer.p,
                c.prm.exact_only, bits, c.ds);
@@ -570,15 +573,65 @@ cudaError_t eval_candidates(Ctx &c, const vec4_t<T> *x, const int2 *pairs, int64
     const unsigned gd = grid_for(n_act, 128, (int64_t)kNumSMs * 8);
     if (grad)
         launch(c, k_derivs<T, true>, dim3(gd), dim3(128), x, tri4, pairs, (const uint32_t *)c.active.p, (T)c.prm.tc_scale,
-                                                     (T *)c.fac.p, (double *)c.partials.p, c.ds);
+               (T *)c.fac.p, kFacStride, (double *)c.partials.p, c.ds);
     else
         launch(c, k_derivs<T, false>, dim3(gd), dim3(128), x, tri4, pairs, (const uint32_t *)c.active.p, (T)c.prm.tc_scale,
-                                                      (T *)c.fac.p, (double *)c.partials.p, c.ds);
+               (T *)c.fac.p, kFacStride, (double *)c.partials.p, c.ds);
     c.n_active = n_act;
     return cudaGetLastError();
 }
 template cudaError_t eval_candidates<float>(Ctx &, const float4 *, const int2 *, int64_t, unsigned);
 template cudaError_t eval_candidates<double>(Ctx &, const dvec4 *, const int2 *, int64_t, unsigned);
+
+// Energy and intersecting pairs over a candidate list without reading anything back on the
+// host, so that the sequence can be captured into a CUDA graph: launch sizes follow the
+// list's capacity n_cap, the actual length is *d_n on the device (nullptr: n_cap), and t_c^0,
+// t_c^1 of the intersecting pairs go to ab (2 per pair, room for n_cap).  Results in
+// ds->energy and ds->n_active.  prepare_energy_eval sizes every buffer for n_cap first
+// (nothing may be allocated while a graph is captured).
+template <typename T> cudaError_t prepare_energy_eval(Ctx &c, int64_t n_cap) {
+    const int64_t n_words = (n_cap + 31) / 32;
+    TTIE_CUDA_TRY(ensure(c, c.act_bits, (size_t)(n_words > 0 ? n_words : 1) * 4));
+    TTIE_CUDA_TRY(ensure(c, c.word_off, (size_t)(n_words + 1) * 8));
+    TTIE_CUDA_TRY(ensure(c, c.defer, (size_t)(n_cap > 0 ? n_cap : 1) * 4));
+    TTIE_CUDA_TRY(ensure(c, c.active, (size_t)(n_cap > 0 ? n_cap : 1) * 4));
+    TTIE_CUDA_TRY(ensure(c, c.partials, (size_t)kNumSMs * 16 * sizeof(double)));
+    TTIE_CUDA_TRY(ensure(c, c.gtmp, (size_t)(n_cap > 0 ? n_cap : 1) * 4));
+    TTIE_CUDA_TRY(ensure(c, c.ab, (size_t)(n_cap > 0 ? n_cap : 1) * 2 * sizeof(T)));
+    TTIE_CUDA_TRY(ensure(c, c.scan_tmp, (size_t)((n_cap + 2047) / 2048 + 2) * 8));
+    return cudaSuccess;
+}
+template cudaError_t prepare_energy_eval<float>(Ctx &, int64_t);
+template cudaError_t prepare_energy_eval<double>(Ctx &, int64_t);
+
+template <typename T>
+cudaError_t energy_eval_nosync(Ctx &c, const vec4_t<T> *x, const int2 *pairs, int64_t n_cap,
+                               const unsigned long long *d_n) {
+    const int64_t n_words = (n_cap + 31) / 32;
+    TTIE_CUDA_TRY(cudaMemsetAsync(&c.ds->n_defer, 0, 8, c.stream));
+    TTIE_CUDA_TRY(cudaMemsetAsync(&c.ds->filter_stats[0], 0, 3 * 8, c.stream));
+    auto *bits = (uint32_t *)c.act_bits.p;
+    const int4 *tri4 = (const int4 *)c.tri4.p;
+    if (n_cap > 0) {
+        const unsigned g = grid_for(n_words * 32, kThreads, (int64_t)kNumSMs * 8);
+        launch(c, k_classify<T>, dim3(g), dim3(kThreads), x, tri4, pairs, n_cap, d_n, c.prm.exact_only, bits,
+               (uint32_t *)c.defer.p, c.ds);
+        launch(c, k_resolve<T>, dim3(kNumSMs * 4), dim3(64), x, tri4, pairs, (const uint32_t *)c.defer.p,
+               c.prm.exact_only, bits, c.ds);
+        launch(c, k_popc, dim3(grid_for(n_words, kThreads)), dim3(kThreads), (const uint32_t *)bits, n_words,
+               (uint32_t *)c.gtmp.p);
+        TTIE_CUDA_TRY(scan_u32_u64(c, (const uint32_t *)c.gtmp.p, (unsigned long long *)c.word_off.p, n_words));
+        launch(c, k_compact, dim3(grid_for(n_words, kThreads)), dim3(kThreads), (const uint32_t *)bits, n_words,
+               (const unsigned long long *)c.word_off.p, (uint32_t *)c.active.p, c.ds);
+    } else {
+        TTIE_CUDA_TRY(cudaMemsetAsync(&c.ds->n_active, 0, 8, c.stream));
+    }
+    launch(c, k_derivs<T, false>, dim3(grid_for(n_cap, 128, (int64_t)kNumSMs * 8)), dim3(128), x, tri4, pairs,
+           (const uint32_t *)c.active.p, (T)c.prm.tc_scale, (T *)c.ab.p, 2, (double *)c.partials.p, c.ds);
+    return cudaGetLastError();
+}
+template cudaError_t energy_eval_nosync<float>(Ctx &, const float4 *, const int2 *, int64_t, const unsigned long long *);
+template cudaError_t energy_eval_nosync<double>(Ctx &, const dvec4 *, const int2 *, int64_t, const unsigned long long *);
 
 // Per intersecting pair of the last evaluation: the exact Hessian of T times the direction v
 // (V x 3), 18 values per pair in the order of the pair's vertices.
