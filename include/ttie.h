@@ -197,6 +197,16 @@ ttie_status ttie_pcg(ttie_ctx *ctx, const void *d_rhs, void *d_out, double rtol,
  */
 ttie_status ttie_hvp(ttie_ctx *ctx, const void *d_x, const void *d_v, void *d_out, int exact);
 
+/*
+ * Gradients of t_c^0 and t_c^1 of every intersecting pair of the last ttie_eval_pairs, by
+ * forward-mode dual numbers in FP64 (the route Appendix A takes to the derivatives; an
+ * independent check of the analytic chain rule that ttie_eval_pairs uses).  d_x: the evaluated
+ * positions, V x x_stride as given to ttie_build_bvh.  d_out: n_active x 36 doubles (device),
+ * [d t_c^0 (18), d t_c^1 (18)] per pair in the order of ttie_get_active, coordinates of
+ * [A0 A1 A2 B0 B1 B2].  Errors: STATE (no evaluation), INVALID (null pointer), CUDA.
+ */
+ttie_status ttie_dual_gradients(ttie_ctx *ctx, const void *d_x, double *d_out);
+
 typedef struct {
     int64_t n_candidates;        /* candidate pairs at x                              */
     int64_t n_active;            /* intersecting pairs at x                           */

@@ -733,6 +733,22 @@ ttie_status ttie_hvp(ttie_ctx *h, const void *d_x, const void *d_v, void *d_out,
     return hvp_impl<float>(c, (const float *)d_x, (const float *)d_v, (float *)d_out, exact);
 }
 
+ttie_status ttie_dual_gradients(ttie_ctx *h, const void *d_x, double *d_out) {
+    if (!h) return TTIE_ERR_INVALID;
+    Ctx &c = h->c;
+    if (!c.have_eval) return set_err(c, TTIE_ERR_STATE, "ttie_dual_gradients: needs a ttie_eval_pairs");
+    if (!d_x || !d_out) return set_err(c, TTIE_ERR_INVALID, "ttie_dual_gradients: null pointer");
+    if (c.prm.precision == TTIE_F64) {
+        CK(pack_positions<double>(c, (const double *)d_x, c.x_stride, (dvec4 *)c.xp.p), "ttie_dual_gradients");
+        CK(dual_gradients<double>(c, (const dvec4 *)c.xp.p, d_out), "ttie_dual_gradients");
+    } else {
+        CK(pack_positions<float>(c, (const float *)d_x, c.x_stride, (float4 *)c.xp.p), "ttie_dual_gradients");
+        CK(dual_gradients<float>(c, (const float4 *)c.xp.p, d_out), "ttie_dual_gradients");
+    }
+    CK(cudaStreamSynchronize(c.stream), "ttie_dual_gradients");
+    return read_err(c, "ttie_dual_gradients");
+}
+
 ttie_status ttie_pcg(ttie_ctx *h, const void *d_rhs, void *d_out, double rtol, int max_it, int *iters, double *rel_residual) {
     if (!h) return TTIE_ERR_INVALID;
     Ctx &c = h->c;

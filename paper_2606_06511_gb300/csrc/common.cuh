@@ -249,6 +249,7 @@ template <typename T> cudaError_t pcg_solve(Ctx &c, const T *rhs, T *out, double
 // Hessian-vector products: per-pair exact products (pair_eval.cu), their per-vertex sums over
 // the last assembly's diagonal runs, and the assembled PSD Hessian times v.
 template <typename T> cudaError_t hvp_pairs(Ctx &c, const vec4_t<T> *x, const T *v, T *h);
+template <typename T> cudaError_t dual_gradients(Ctx &c, const vec4_t<T> *x, double *out);
 template <typename T> cudaError_t vertex_sums(Ctx &c, const T *h, T *out);
 template <typename T> cudaError_t bsr_matvec(Ctx &c, const T *v, T *out);
 // out_dev[0] = g.d, out_dev[1] = max over rows of |d_r|^2 (rows of the assembled system)

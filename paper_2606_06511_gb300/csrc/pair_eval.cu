@@ -533,6 +533,43 @@ __global__ void __launch_bounds__(128) k_hvp_pairs(const vec4_t<T> *__restrict__
     }
 }
 
+// The appendix's route to the derivatives, as an independent FP64 check of the analytic
+// chain rule: t_c^0 and t_c^1 of every intersecting pair evaluated in forward-mode dual
+// numbers (FP64 values and tangents), once per coordinate with that coordinate's tangent
+// seeded to 1.  out[k] = [d t_c^0 (18), d t_c^1 (18)] in the pair's vertex order.
+template <typename T>
+__global__ void __launch_bounds__(128) k_dual_gradients(const vec4_t<T> *__restrict__ x, const int4 *__restrict__ tri4,
+                                                        const int2 *__restrict__ pairs,
+                                                        const uint32_t *__restrict__ active, double tc_scale,
+                                                        double *__restrict__ out, const DevScalars *ds) {
+    typedef Dual<double> S;
+    const unsigned long long n_act = ds->n_active;
+    for (unsigned long long k = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; k < n_act;
+         k += (unsigned long long)gridDim.x * blockDim.x) {
+        const int2 pr = pairs[active[k]];
+        const int4 ta = tri4[pr.x], tb = tri4[pr.y];
+        const int vid[6] = {ta.x, ta.y, ta.z, tb.x, tb.y, tb.z};
+        double pv[18];
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+            const vec4_t<T> p = x[vid[i]];
+            pv[3 * i] = (double)p.x; pv[3 * i + 1] = (double)p.y; pv[3 * i + 2] = (double)p.z;
+        }
+        for (int j = 0; j < 18; ++j) {
+            v3<S> P[6];
+#pragma unroll
+            for (int i = 0; i < 6; ++i)
+                P[i] = {S(pv[3 * i], 3 * i == j ? 1.0 : 0.0), S(pv[3 * i + 1], 3 * i + 1 == j ? 1.0 : 0.0),
+                        S(pv[3 * i + 2], 3 * i + 2 == j ? 1.0 : 0.0)};
+            v3<S> A[3] = {P[0], P[1], P[2]}, B[3] = {P[3], P[4], P[5]};
+            S a, b, ga[18], gb[18];
+            pair_tc<S, false>(A, B, S(tc_scale), a, b, ga, gb);
+            out[k * 36 + j] = a.t;
+            out[k * 36 + 18 + j] = b.t;
+        }
+    }
+}
+
 }  // namespace
 
 template <typename T>
@@ -641,6 +678,15 @@ template <typename T> cudaError_t hvp_pairs(Ctx &c, const vec4_t<T> *x, const T 
     return cudaGetLastError();
 }
 template cudaError_t hvp_pairs<float>(Ctx &, const float4 *, const float *, float *);
+
+template <typename T> cudaError_t dual_gradients(Ctx &c, const vec4_t<T> *x, double *out) {
+    launch(c, k_dual_gradients<T>, dim3(grid_for(c.n_active, 128, (int64_t)kNumSMs * 8)), dim3(128), x,
+           (const int4 *)c.tri4.p, (const int2 *)c.cand.p, (const uint32_t *)c.active.p, c.prm.tc_scale, out,
+           (const DevScalars *)c.ds);
+    return cudaGetLastError();
+}
+template cudaError_t dual_gradients<float>(Ctx &, const float4 *, double *);
+template cudaError_t dual_gradients<double>(Ctx &, const dvec4 *, double *);
 template cudaError_t hvp_pairs<double>(Ctx &, const dvec4 *, const double *, double *);
 
 }  // namespace ttie

@@ -100,6 +100,7 @@ _SIGS = {
     "ttie_get_filter_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)]),
     "ttie_get_launch_count": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)]),
     "ttie_hvp": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
+    "ttie_dual_gradients": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
 }
 
 
@@ -252,6 +253,16 @@ class Context:
         out = torch.empty_like(v)
         self._chk(self.lib.ttie_hvp(self.h, _ptr(x), _ptr(v), _ptr(out), 1 if exact else 0))
         return out
+
+    def dual_gradients(self, x: torch.Tensor) -> torch.Tensor:
+        """[n_active, 2, 18] float64 gradients of t_c^0, t_c^1 by forward-mode dual numbers (FP64) at
+        the positions of the last eval_pairs (x must be those positions)."""
+        self._check_x(x)
+        n = ctypes.c_int64()
+        self._chk(self.lib.ttie_get_active(self.h, None, None, None, 0, ctypes.byref(n)))
+        out = torch.empty((max(n.value, 1), 2, 18), dtype=torch.float64, device="cuda")
+        self._chk(self.lib.ttie_dual_gradients(self.h, _ptr(x), _ptr(out)))
+        return out[: n.value]
 
     def newton_step(self, x: torch.Tensor) -> dict:
         self._check_x(x)
