@@ -360,6 +360,24 @@ def main():
                 "speedup_of_fp32_form": (ms64 / n64) / (total_ms / args.steps)}
         ctx64.close()
 
+    # broad phase alone: LBVH against the spatial-hash grid, same candidate set
+    broad = None
+    if rank == 0 and mode != 2:
+        broad = {}
+        for name, flag in (("lbvh", 0), ("hash", ttie.PAIRS_HASH)):
+            cb = ttie.Context(precision=precision, pair_mode=mode | flag)
+            cb.build_bvh(x0, tri, grp)
+            ms = []
+            for _ in range(5):
+                flush.zero_()
+                ev0.record(stream)
+                nb = cb.build_bvh(x0, tri, grp)
+                ev1.record(stream)
+                ev1.synchronize()
+                ms.append(ev0.elapsed_time(ev1))
+            broad[name] = {"ms": sorted(ms)[len(ms) // 2], "candidates": nb}
+            cb.close()
+
     solve = None
     if not args.no_solve and rank == 0:
         xs = x0.clone()
@@ -394,6 +412,7 @@ def main():
             "roofline_pair_eval": roofline_pairs,
             "cpu_baseline": cpu,
             "fp64_form": fp64,
+            "broad_phase_ms": broad,
             "e2e": {"value": e2e_pairs / (e2e_ms / 1e3) if e2e_ms > 0 else None, "unit": UNIT,
                     "h2d_bytes_per_step": e2e_bytes, "d2h_bytes_per_step": e2e_bytes},
             "gpu_launches": launches,

@@ -64,6 +64,11 @@ typedef enum {
  * candidates (no bounding-box test). */
 #define TTIE_PAIRS_BRUTE 4
 
+/* OR-ed into pair_mode: candidates from a uniform spatial hash grid (the broad phase §1.2
+ * names) instead of the LBVH; the same candidate set (closed box overlap, no shared vertex,
+ * i < j), in another deterministic order.  Not used by the batched-instance solve. */
+#define TTIE_PAIRS_HASH 8
+
 /* PSD projection of the Eq. 4 Hessian (eigen-analysis of §1.1).
  * PER_PART:   parts 1 and 2 kept, part 3 keeps its non-negative eigenpair.
  * DROP_CROSS: parts 1 and 2 only.

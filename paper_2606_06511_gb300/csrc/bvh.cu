@@ -447,6 +447,10 @@ cudaError_t build_candidates(Ctx &c, const vec4_t<T> *x0, const vec4_t<T> *x1, B
     if (!refit_only) c.tree_leaves = -1;
     launch(c, k_init_bounds, dim3(1), dim3(32), c.ds);
     launch(c, k_tri_boxes<T>, dim3(g), dim3(kThreads), x0, x1, (const int4 *)c.tri4.p, n, tbox, c.ds);
+    if (c.prm.pair_mode & TTIE_PAIRS_HASH) {   // spatial hashing instead of the LBVH (hash.cu)
+        c.tree_leaves = -1;
+        return hash_candidates<T>(c, (const Box<T> *)tbox, out_pairs, n_out, cap);
+    }
     if (!(refit_only && c.tree_leaves == n)) {
         const int gbits = grouped ? c.group_bits : 0;
         launch(c, k_morton<T>, dim3(g), dim3(kThreads), tbox, n, (const int32_t *)c.grp.p, gbits, c.ds, key, perm);

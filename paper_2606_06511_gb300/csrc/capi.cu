@@ -102,7 +102,8 @@ static ttie_status check_params(Ctx &c, const ttie_params *p) {
     if (!p) return set_err(c, TTIE_ERR_INVALID, "params is NULL");
     if (p->precision != TTIE_F32 && p->precision != TTIE_F64) return set_err(c, TTIE_ERR_INVALID, "precision");
     const int m = p->pair_mode & 3;
-    if (m == 3 || (p->pair_mode & ~7)) return set_err(c, TTIE_ERR_INVALID, "pair_mode");
+    if (m == 3 || (p->pair_mode & ~15) || ((p->pair_mode & TTIE_PAIRS_BRUTE) && (p->pair_mode & TTIE_PAIRS_HASH)))
+        return set_err(c, TTIE_ERR_INVALID, "pair_mode");
     if (p->psd_mode != TTIE_PSD_PER_PART && p->psd_mode != TTIE_PSD_DROP_CROSS && p->psd_mode != TTIE_PSD_WHOLE)
         return set_err(c, TTIE_ERR_INVALID, "psd_mode");
     if (!(p->tc_scale > 0.0) || !(p->mu_rel >= 0.0) || !(p->pcg_rtol > 0.0) || p->pcg_max_it < 1 ||
@@ -216,7 +217,9 @@ static ttie_status read_err(Ctx &c, const char *where) {
     if (e) CK(cudaMemsetAsync(&c.ds->err, 0, sizeof(int), c.stream), where);
     if (e & ERR_BAD_INDEX) return set_err(c, TTIE_ERR_INVALID, "%s: triangle or group index out of range", where);
     if (e & ERR_NONFINITE) return set_err(c, TTIE_ERR_NONFINITE, "%s: non-finite vertex position", where);
-    if (e & ERR_STACK) return set_err(c, TTIE_ERR_CAPACITY, "%s: BVH traversal stack overflow", where);
+    if (e & ERR_STACK)
+        return set_err(c, TTIE_ERR_CAPACITY, "%s: broad-phase capacity exceeded (BVH depth or hash cells per triangle)",
+                       where);
     if (e & ERR_BARRIER) return set_err(c, TTIE_ERR_CUDA, "%s: PCG grid barrier timed out", where);
     if (e & ERR_GROUP)
         return set_err(c, TTIE_ERR_INVALID,
@@ -233,7 +236,8 @@ static ttie_status read_err(Ctx &c, const char *where) {
 
 // Intra-group pairs over an LBVH: every group is an independent problem (instances.cu).
 static bool batched(const Ctx &c) {
-    return (c.prm.pair_mode & 3) == TTIE_PAIRS_INTRA_GROUP && c.have_group && !(c.prm.pair_mode & TTIE_PAIRS_BRUTE);
+    return (c.prm.pair_mode & 3) == TTIE_PAIRS_INTRA_GROUP && c.have_group &&
+           !(c.prm.pair_mode & (TTIE_PAIRS_BRUTE | TTIE_PAIRS_HASH));
 }
 
 template <typename T>

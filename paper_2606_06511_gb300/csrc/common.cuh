@@ -117,7 +117,7 @@ cudaError_t ensure(Ctx &c, Buf &b, size_t bytes);   // grow-only, contents not k
     X(zfac) X(dinv) X(pcg_x) X(pcg_r) X(pcg_z) X(pcg_p) X(pcg_q) X(dir) X(xt) X(gtmp)      \
     X(xsave) X(sweep_cand) X(pcg_z4) X(hbuf) X(pcg_sync) X(spill) X(pcg_w) X(vgroup) X(iedge)  \
     X(inst) X(ls_cand) X(inst_acc) X(inst_ids) X(ab) X(ls_flag)  \
-    X(ls_off) X(ls_scalars)
+    X(ls_off) X(ls_scalars) X(hgrid) X(hkey) X(hkey2) X(hval) X(hval2) X(hcnt) X(hoff)
 
 struct Ctx {
     ttie_params prm;
@@ -209,6 +209,8 @@ cudaError_t pack_topology(Ctx &c, const int32_t *tri, const int32_t *group);
 // exceeds `cap` nothing is written and *n_out receives the count.
 // refit_only: keep the hierarchy of the last full build of this mesh (the line search's swept
 // boxes reuse the tree built at x) and only refit it to the new boxes.
+// spatial-hashing broad phase over the triangle boxes of the last k_tri_boxes (hash.cu)
+template <typename T> cudaError_t hash_candidates(Ctx &c, const Box<T> *box, Buf &out_pairs, int64_t *n_out, int64_t cap);
 template <typename T> cudaError_t build_candidates(Ctx &c, const vec4_t<T> *x0, const vec4_t<T> *x1,
                                                    Buf &out_pairs, int64_t *n_out, int64_t cap,
                                                    bool refit_only = false);

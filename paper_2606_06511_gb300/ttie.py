@@ -24,7 +24,7 @@ TTIE_OK, TTIE_ERR_INVALID, TTIE_ERR_CUDA, TTIE_ERR_OOM, TTIE_ERR_CAPACITY, TTIE_
     TTIE_ERR_NOT_CONVERGED, TTIE_ERR_STATE = range(8)
 STATUS_NAMES = ["OK", "INVALID", "CUDA", "OOM", "CAPACITY", "NONFINITE", "NOT_CONVERGED", "STATE"]
 F32, F64 = 0, 1
-PAIRS_SELF, PAIRS_INTER_GROUP, PAIRS_INTRA_GROUP, PAIRS_BRUTE = 0, 1, 2, 4
+PAIRS_SELF, PAIRS_INTER_GROUP, PAIRS_INTRA_GROUP, PAIRS_BRUTE, PAIRS_HASH = 0, 1, 2, 4, 8
 PSD_PER_PART, PSD_DROP_CROSS, PSD_WHOLE = 0, 1, 2
 EVAL_E, EVAL_G, EVAL_H = 1, 2, 4
 

@@ -314,3 +314,35 @@ def test_assembly_psd_modes(ttie, name, psd):
     scale = max(np.abs(b).max() for b in blocks.values())
     for key, b in blocks.items():
         assert np.allclose(got[key], b, rtol=1e-4, atol=1e-4 * scale), key
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_hash_candidates_bit_exact(ttie, name):
+    """The spatial-hashing broad phase (TTIE_PAIRS_HASH) gives the oracle's candidate set in
+    every pair mode, in a deterministic order, and the same evaluation as the LBVH's list."""
+    m, mode = CASES[name]
+    x, tri, grp = _dev(m)
+    ctx = ttie.Context(pair_mode=MODE[mode] | ttie.PAIRS_HASH)
+    n = ctx.build_bvh(x, tri, grp)
+    got = ctx.get_candidates().cpu().numpy()
+    pairs, ev = _oracle(name)
+    assert n == len(pairs)
+    assert np.all(got[:, 0] < got[:, 1])
+    assert pair_set(got) == pair_set(pairs)
+    ctx.build_bvh(x, tri, grp)
+    assert np.array_equal(ctx.get_candidates().cpu().numpy(), got)
+    E, n_act = ctx.eval_pairs(x, ttie.EVAL_E)
+    assert n_act == int(ev.active.sum())
+    assert E == pytest.approx(float(ev.T.sum()), rel=1e-5, abs=1e-30)
+
+
+def test_hash_candidates_match_lbvh_full_size(ttie):
+    m = ti.cloth(256, seed=2).as_f32()
+    x, tri, grp = _dev(m)
+    sets = []
+    for flag in (0, ttie.PAIRS_HASH):
+        ctx = ttie.Context(pair_mode=flag)
+        ctx.build_bvh(x, tri)
+        c = ctx.get_candidates().cpu().numpy().astype(np.int64)
+        sets.append(np.sort(c[:, 0] * m.F + c[:, 1]))
+    assert len(sets[0]) > 600000 and np.array_equal(sets[0], sets[1])
