@@ -271,11 +271,26 @@ __global__ void k_block_values(const unsigned long long *__restrict__ key, const
 
 // ---------------------------------------------------------------- PCG
 
+// Words that one block publishes to the others carry a tag in their two lowest significand
+// bits (the value is the tagged word itself, on both sides), so a reader that loads a word
+// also learns whether it is the current one: no separate flag or epoch is read first.
+__device__ __forceinline__ float tag_word(float v, unsigned t) { return __uint_as_float((__float_as_uint(v) & ~3u) | t); }
+__device__ __forceinline__ double tag_word(double v, unsigned t) {
+    return __longlong_as_double((long long)(((unsigned long long)__double_as_longlong(v) & ~3ull) | t));
+}
+__device__ __forceinline__ unsigned word_tag(float v) { return __float_as_uint(v) & 3u; }
+__device__ __forceinline__ unsigned word_tag(double v) { return (unsigned)__double_as_longlong(v) & 3u; }
+
+// p = z = M^-1 r0, r = r0, x = 0; r.z and r.r summed.  For the block-resident kernel also the
+// tagged mirror z4 of z (tag 0: the first iteration's vector) and its reduction words cleared
+// (tag 0 never marks a published reduction word).
 template <typename T>
 __global__ void k_pcg_setup(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col_idx,
                             const T *__restrict__ bval, double mu_rel, T *__restrict__ dinv, const T *__restrict__ rhs,
                             T *__restrict__ x, T *__restrict__ r, T *__restrict__ z, T *__restrict__ p, double *partials,
+                            vec4_t<T> *__restrict__ z4, unsigned long long *__restrict__ sync_words, int n_sync_words,
                             DevScalars *ds) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_sync_words; i += gridDim.x * blockDim.x) sync_words[i] = 0ull;
     const unsigned long long nr = ds->n_rows;
     const T mu = (T)(nr ? mu_rel * ds->trace / (3.0 * (double)nr) : 0.0);
     double rz = 0.0, rr = 0.0;
@@ -299,6 +314,11 @@ __global__ void k_pcg_setup(const int32_t *__restrict__ row_ptr, const int32_t *
         r[row * 3] = r0; r[row * 3 + 1] = r1; r[row * 3 + 2] = r2;
         z[row * 3] = z0; z[row * 3 + 1] = z1; z[row * 3 + 2] = z2;
         p[row * 3] = z0; p[row * 3 + 1] = z1; p[row * 3 + 2] = z2;
+        if (z4) {
+            vec4_t<T> t;
+            t.x = tag_word(z0, 0u); t.y = tag_word(z1, 0u); t.z = tag_word(z2, 0u); t.w = T(0);
+            z4[row] = t;
+        }
         rz += (double)r0 * z0 + (double)r1 * z1 + (double)r2 * z2;
         rr += (double)r0 * r0 + (double)r1 * r1 + (double)r2 * r2;
     }
@@ -387,10 +407,10 @@ __device__ __forceinline__ bool grid_allreduce(double (&v)[N], double *part, Dev
     return ok;
 }
 
-// One block's partial sums for the resident PCG's reductions, tagged with the reduction's epoch.
+// One block's partial sums for the resident PCG's reductions: the bits of its accumulators,
+// each word tagged (its lowest bits) with the reduction that wrote it.
 struct __align__(32) RedSlot {
-    unsigned long long v[3];   // bits of the block's accumulators
-    unsigned long long epoch;
+    unsigned long long v[4];   // v[3] unused
 };
 
 template <typename T> struct PcgArgs {
@@ -399,10 +419,9 @@ template <typename T> struct PcgArgs {
     const T *bval;
     const T *dinv;
     T *x, *r, *z, *p, *q;
-    vec4_t<T> *z4;           // z mirrored as one 16/32-byte vector per row (resident kernel)
+    vec4_t<T> *z4;           // z mirrored as one tagged 16/32-byte vector per row (resident kernel)
     double *partA, *partB;
-    RedSlot *slots;          // resident kernel: 2 x grid epoch-tagged reduction slots
-    unsigned long long *flags;   // resident kernel: per-block publication epochs
+    RedSlot *slots;          // resident kernel: 2 x kMaxGridPcg tagged reduction slots
     double rtol2;
     int max_it;
     DevScalars *ds;
@@ -533,126 +552,143 @@ __global__ void __launch_bounds__(kPcgThreads) k_pcg_persistent(PcgArgs<T> a) {
 // iteration).  With gamma = r.u, delta = w.u:
 //   beta = gamma / gamma_prev,  alpha = gamma / (delta - beta gamma / alpha_prev)
 //   p = u + beta p,  s = w + beta s,  x += alpha p,  r -= alpha s,  u = M^-1 r,  w = A u.
-// The product needs u of other blocks' rows: each block publishes its u (one 16/32-byte
-// vector per row) and then an epoch flag; before the product a block waits only for the
-// flags of the blocks its columns belong to.  The three dot products are summed through
-// per-block slots tagged with an epoch (no atomics): every block reads all slots in the
-// same order, so all blocks take the same decisions.  No block can run a phase ahead of a
-// reader: publishing u for iteration k+1 needs the reduction of iteration k, which needs
-// every block to have finished its product of iteration k.  Slots alternate between two
-// buffers by epoch parity for the same reason.  Every wait is bounded (kBarrierSpins); on
-// timeout ERR_BARRIER is set and the kernel returns.
+// The product needs u of other blocks' rows.  Each block publishes its u as one 16/32-byte
+// vector per row whose words carry the iteration's tag (k mod 4); a reader loads the words
+// of its columns and loads again those whose tag is not yet k.  The three dot products are
+// summed through per-block slots whose words carry the reduction's tag (8 + k mod 8); every
+// block reads all slots in the same order, so all blocks take the same decisions.
+//
+// Why the tags cannot be mistaken: u of iteration k is written after reduction k - 1, and a
+// reader reads it after that reduction too, whose publication (release fence, then the
+// words) and completion (the words, then an acquire fence) order every u of iteration k - 1
+// before the reader's loads; no block writes u of iteration k + 1 before reduction k, which
+// needs the reader's product.  So a reader sees the words of iteration k - 1 or k.  Slot
+// buffers alternate by reduction parity: a reader of reduction k sees k - 2 or k.  The setup
+// kernel (an earlier launch) writes u of iteration 0 with tag 0 and clears the slots (tag 0
+// is never a reduction's).  Every wait is bounded; on timeout ERR_BARRIER is set and the
+// kernel returns.
 constexpr int kResidentSmem = 220 * 1024;   // dynamic shared memory per block
 constexpr int kMaxGridPcg = 256;            // slots per lane in the reduction: 8
-constexpr int kMaxDeps = 256;
+constexpr long long kTagSpins = kBarrierSpins / 16;   // reloads of one word (each an L2 round trip)
 
 __device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long *p) {
     unsigned long long v;
-    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p));
     return v;
 }
 __device__ __forceinline__ void st_relaxed_u64(unsigned long long *p, unsigned long long v) {
     asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
+__device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
 
-// Grid sums of N <= 3 accumulators through epoch-tagged slots, identical in every block.
-// Warp 0 of each block publishes its block's sums, waits for every slot of epoch e, adds
-// them in slot order, and lane 0 then runs fin(totals) (thread 0 of each block).  Returns
-// false (ERR_BARRIER set) when the wait runs out.
+// relaxed (coherent, never cached in L1) load of one published row vector
+template <typename T> __device__ __forceinline__ vec4_t<T> ld_row(const vec4_t<T> *p);
+template <> __device__ __forceinline__ float4 ld_row<float>(const float4 *p) {
+    float4 r;
+    asm volatile("ld.relaxed.gpu.global.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w)
+                 : "l"(p));
+    return r;
+}
+template <> __device__ __forceinline__ dvec4 ld_row<double>(const dvec4 *p) {
+    dvec4 r;
+    asm volatile("ld.relaxed.gpu.global.v2.f64 {%0, %1}, [%2];" : "=d"(r.x), "=d"(r.y) : "l"(p));
+    asm volatile("ld.relaxed.gpu.global.f64 %0, [%1];" : "=d"(r.z) : "l"(reinterpret_cast<const double *>(p) + 2));
+    r.w = 0.0;
+    return r;
+}
+template <typename T> __device__ __forceinline__ bool row_tagged(const vec4_t<T> &g, unsigned t) {
+    return (word_tag(g.x) == t) & (word_tag(g.y) == t) & (word_tag(g.z) == t);
+}
+// reload g from p until its words carry tag t; bounded (sets *bad)
+template <typename T>
+__device__ __forceinline__ void settle_row(vec4_t<T> &g, const vec4_t<T> *p, unsigned t, int *bad) {
+    long long spins = 0;
+    while (!row_tagged<T>(g, t)) {
+        if (++spins > kTagSpins || *(volatile int *)bad) { *bad = 1; return; }
+        g = ld_row<T>(p);
+    }
+}
+
+// a reduction word with tag t in the four lowest significand bits of its smaller part
+template <typename T> __device__ __forceinline__ unsigned long long tag_bits(unsigned long long b, unsigned t) {
+    constexpr int s = Acc<T>::kTagShift;
+    return (b & ~(15ull << s)) | ((unsigned long long)t << s);
+}
+template <typename T> __device__ __forceinline__ unsigned bits_tag(unsigned long long b) {
+    return (unsigned)(b >> Acc<T>::kTagShift) & 15u;
+}
+
+// Grid sums of N <= 3 accumulators through tagged slots, identical in every block.  Thread 0
+// publishes its block's sums (tag t = 8 + k mod 8) in buffer k mod 2; warp i < N loads word i
+// of every slot until all carry t and adds them in slot order; thread 0 then runs
+// fin(totals).  A block whose product gave up (*bad) publishes nothing.  Returns false
+// (ERR_BARRIER set) when a wait ran out.
 template <int N, typename T, typename Fin>
-__device__ __forceinline__ bool slot_allreduce(Acc<T> (&a)[N], RedSlot *slots, unsigned long long e, DevScalars *ds,
-                                               Fin fin) {
+__device__ __forceinline__ bool slot_allreduce(Acc<T> (&a)[N], RedSlot *slots, unsigned k, const int *bad,
+                                               DevScalars *ds, Fin fin) {
+    static_assert(N <= 3, "three words per slot");
     __shared__ int s_fail;
+    __shared__ int s_wfail[N];
+    __shared__ unsigned long long s_tot[N];
     const unsigned G = gridDim.x;
-    const int lane = threadIdx.x & 31;
-    block_sums<N, T>(a);
-    RedSlot *buf = slots + (size_t)(e & 1ull) * G;
-    if (threadIdx.x < 32) {
-        if (lane == 0) {
+    const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+    block_sums<N, T>(a);   // its barrier also makes *bad visible
+    RedSlot *buf = slots + (size_t)(k & 1u) * kMaxGridPcg;
+    const unsigned t = 8u | (k & 7u);
+    if (wi < N) {
+        bool fail = *(const volatile int *)bad != 0;
+        if (!fail && threadIdx.x == 0) {
+            fence_acq_rel_gpu();   // release: this block's u (and everything before) ahead of its sums
 #pragma unroll
-            for (int i = 0; i < N; ++i) buf[blockIdx.x].v[i] = a[i].bits();
-            __threadfence();
-            st_relaxed_u64(&buf[blockIdx.x].epoch, e);
+            for (int i = 0; i < N; ++i) st_relaxed_u64(&buf[blockIdx.x].v[i], tag_bits<T>(a[i].bits(), t));
         }
-        // every lane polls its (up to 8) slots with all loads in flight, then reads them
+        // every lane loads its (up to 8) slots' word wi with all loads in flight until they carry t
         unsigned ready = 0, want = 0;
 #pragma unroll
-        for (int k = 0; k < kMaxGridPcg / 32; ++k)
-            if (lane + 32u * k < G) want |= 1u << k;
+        for (int q = 0; q < kMaxGridPcg / 32; ++q)
+            if (lane + 32u * q < G) want |= 1u << q;
+        unsigned long long w[kMaxGridPcg / 32];
         long long spins = 0;
-        bool fail = false;
-        while (true) {
+        while (!fail) {
 #pragma unroll
-            for (int k = 0; k < kMaxGridPcg / 32; ++k)
-                if ((want & ~ready) >> k & 1u)
-                    if (ld_relaxed_u64(&buf[lane + 32 * k].epoch) >= e) ready |= 1u << k;
+            for (int q = 0; q < kMaxGridPcg / 32; ++q)
+                if ((want & ~ready) >> q & 1u) {
+                    w[q] = ld_relaxed_u64(&buf[lane + 32 * q].v[wi]);
+                    if (bits_tag<T>(w[q]) == t) ready |= 1u << q;
+                }
             if (__all_sync(0xffffffffu, ready == want)) break;
             if (++spins > kBarrierSpins) { fail = true; break; }
             __nanosleep(20);
         }
-        __threadfence();
-        Acc<T> s[N];
+        fence_acq_rel_gpu();   // acquire: the next iteration's loads of u follow every block's sums
+        Acc<T> sum;
 #pragma unroll
-        for (int k = 0; k < kMaxGridPcg / 32; ++k)
-            if (want >> k & 1u)
+        for (int q = 0; q < kMaxGridPcg / 32; ++q)
+            if (want >> q & 1u) sum.add(Acc<T>::from_bits(w[q]));
 #pragma unroll
-                for (int i = 0; i < N; ++i) s[i].add(Acc<T>::from_bits(__ldcg(&buf[lane + 32 * k].v[i])));
-#pragma unroll
-        for (int i = 0; i < N; ++i) {
-#pragma unroll
-            for (int o = 16; o; o >>= 1) s[i].add(s[i].shfl_xor(0xffffffffu, o, 32));
-        }
+        for (int o = 16; o; o >>= 1) sum.add(sum.shfl_xor(0xffffffffu, o, 32));
         fail = __any_sync(0xffffffffu, fail);
         if (lane == 0) {
-            s_fail = fail ? 1 : 0;
-            if (fail) atomicOr(&ds->err, ERR_BARRIER);
-            else fin(s);
+            s_tot[wi] = sum.bits();
+            s_wfail[wi] = fail ? 1 : 0;
         }
-    }
-    __syncthreads();
-    return s_fail == 0;
-}
-
-// Wait until every block in deps (or every other block when n_dep < 0) has published the
-// epoch e; bounded.
-__device__ __forceinline__ bool wait_flags(const unsigned long long *flags, const int *deps, int n_dep,
-                                           unsigned long long e, DevScalars *ds) {
-    __shared__ int s_fail;
-    if (threadIdx.x < 32) {
-        const int lane = threadIdx.x;
-        const int n = n_dep < 0 ? (int)gridDim.x : n_dep;
-        bool fail = false;
-        for (int j0 = 0; j0 < n && !fail; j0 += 32) {
-            const int j = j0 + lane;
-            const int blk = j < n ? (n_dep < 0 ? j : deps[j]) : -1;
-            bool ok = blk < 0 || blk == (int)blockIdx.x;
-            long long spins = 0;
-            while (true) {
-                if (!ok) ok = ld_relaxed_u64(&flags[blk]) >= e;
-                if (__all_sync(0xffffffffu, ok)) break;
-                if (++spins > kBarrierSpins) { fail = true; break; }
-                __nanosleep(20);
+        asm volatile("bar.sync 1, %0;" ::"r"(32 * N) : "memory");
+        if (threadIdx.x == 0) {
+            Acc<T> tot[N];
+            bool any = false;
+#pragma unroll
+            for (int i = 0; i < N; ++i) {
+                tot[i] = Acc<T>::from_bits(s_tot[i]);
+                any |= s_wfail[i] != 0;
             }
-            fail = __any_sync(0xffffffffu, fail);
-        }
-        __threadfence();
-        if (lane == 0) {
-            s_fail = fail ? 1 : 0;
-            if (fail) atomicOr(&ds->err, ERR_BARRIER);
+            s_fail = any ? 1 : 0;
+            if (any) atomicOr(&ds->err, ERR_BARRIER);
+            else fin(tot);
         }
     }
     __syncthreads();
     return s_fail == 0;
-}
-
-template <typename T> __device__ __forceinline__ vec4_t<T> ldcg4(const vec4_t<T> *p);
-template <> __device__ __forceinline__ float4 ldcg4<float>(const float4 *p) { return __ldcg(p); }
-template <> __device__ __forceinline__ dvec4 ldcg4<double>(const dvec4 *p) {
-    const double2 *q = reinterpret_cast<const double2 *>(p);
-    const double2 a = __ldcg(q), b = __ldcg(q + 1);
-    dvec4 r;
-    r.x = a.x; r.y = a.y; r.z = b.x; r.w = b.y;
-    return r;
 }
 
 template <typename T>
@@ -672,9 +708,11 @@ template <typename T> struct ResidentView {
     int nrow, nnz, b_begin;
 };
 
-// w = (A + mu I) u on the block's rows; returns the rows' w.u
+// w = (A + mu I) u on the block's rows, u of other rows read from the mirror with tag t;
+// returns the rows' w.u.  A load that never sees tag t sets *bad.
 template <typename T>
-__device__ __forceinline__ Acc<T> resident_product(const PcgArgs<T> &a, const ResidentView<T> &v, T mu) {
+__device__ __forceinline__ Acc<T> resident_product(const PcgArgs<T> &a, const ResidentView<T> &v, T mu, unsigned t,
+                                                   int *bad) {
     if (v.gathered) {
         // gather every block's column vector first: all loads of a thread in flight together
         constexpr int U = 4;
@@ -683,12 +721,15 @@ __device__ __forceinline__ Acc<T> resident_product(const PcgArgs<T> &a, const Re
 #pragma unroll
             for (int k = 0; k < U; ++k) {
                 const int j = j0 + k * kPcgThreads;
-                if (j < v.nnz) g[k] = ldcg4<T>(&a.z4[v.col[j]]);
+                if (j < v.nnz) g[k] = ld_row<T>(&a.z4[v.col[j]]);
             }
 #pragma unroll
             for (int k = 0; k < U; ++k) {
                 const int j = j0 + k * kPcgThreads;
-                if (j < v.nnz) { v.gu[3 * j] = g[k].x; v.gu[3 * j + 1] = g[k].y; v.gu[3 * j + 2] = g[k].z; }
+                if (j < v.nnz) {
+                    settle_row<T>(g[k], &a.z4[v.col[j]], t, bad);
+                    v.gu[3 * j] = g[k].x; v.gu[3 * j + 1] = g[k].y; v.gu[3 * j + 2] = g[k].z;
+                }
             }
         }
         __syncthreads();
@@ -705,12 +746,17 @@ __device__ __forceinline__ Acc<T> resident_product(const PcgArgs<T> &a, const Re
         } else if (v.cached) {
             int b = v.rp[lr] + sub;
             for (; b + kLanesPerRow < be; b += 2 * kLanesPerRow) {   // two gathers in flight
-                const vec4_t<T> g0 = ldcg4<T>(&a.z4[v.col[b]]), g1 = ldcg4<T>(&a.z4[v.col[b + kLanesPerRow]]);
+                const vec4_t<T> *p0 = &a.z4[v.col[b]], *p1 = &a.z4[v.col[b + kLanesPerRow]];
+                vec4_t<T> g0 = ld_row<T>(p0), g1 = ld_row<T>(p1);
+                settle_row<T>(g0, p0, t, bad);
+                settle_row<T>(g1, p1, t, bad);
                 block_times(v.val + (size_t)b * 9, g0.x, g0.y, g0.z, y0, y1, y2);
                 block_times(v.val + (size_t)(b + kLanesPerRow) * 9, g1.x, g1.y, g1.z, y0, y1, y2);
             }
             if (b < be) {
-                const vec4_t<T> g0 = ldcg4<T>(&a.z4[v.col[b]]);
+                const vec4_t<T> *p0 = &a.z4[v.col[b]];
+                vec4_t<T> g0 = ld_row<T>(p0);
+                settle_row<T>(g0, p0, t, bad);
                 block_times(v.val + (size_t)b * 9, g0.x, g0.y, g0.z, y0, y1, y2);
             }
         } else {
@@ -718,7 +764,8 @@ __device__ __forceinline__ Acc<T> resident_product(const PcgArgs<T> &a, const Re
                 if (TTIE_BAD(a.ds, (unsigned long long)(v.b_begin + b) < a.ds->nnzb, 41, b)) break;
                 const int c = a.col_idx[v.b_begin + b];
                 if (TTIE_BAD(a.ds, c >= 0 && (unsigned long long)c < a.ds->n_rows, 42, c)) break;
-                const vec4_t<T> g0 = ldcg4<T>(&a.z4[c]);
+                vec4_t<T> g0 = ld_row<T>(&a.z4[c]);
+                settle_row<T>(g0, &a.z4[c], t, bad);
                 block_times(a.bval + (size_t)(v.b_begin + b) * 9, g0.x, g0.y, g0.z, y0, y1, y2);
             }
         }
@@ -741,13 +788,10 @@ __device__ __forceinline__ Acc<T> resident_product(const PcgArgs<T> &a, const Re
 
 template <typename T>
 __global__ void __launch_bounds__(kPcgThreads) k_pcg_resident(PcgArgs<T> a, int rows_per_block, int smem_bytes,
-                                                             unsigned long long epoch0, int lean) {
+                                                             int lean) {
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ unsigned s_bits[kMaxGridPcg / 32];
-    __shared__ int s_dep[kMaxDeps];
-    __shared__ int s_ndep;
     __shared__ T s_alpha, s_beta;
-    __shared__ int s_stop;
+    __shared__ int s_stop, s_bad;
     DevScalars *ds = a.ds;
     if (ds->pcg_done) return;
     const long long nr = (long long)ds->n_rows;
@@ -778,11 +822,12 @@ __global__ void __launch_bounds__(kPcgThreads) k_pcg_resident(PcgArgs<T> a, int 
     v.val = (T *)(smem + vec_bytes);
     v.col = (int *)(v.val + (size_t)9 * v.nnz);
     v.gu = (T *)(smem + vec_bytes + mat_bytes);
-    // load the block's rows (x = 0, r, u = M^-1 r and M^-1 from the setup kernel; p = s = 0)
+    // load the block's rows (x = 0, r, u = M^-1 r as published with tag 0 by the setup kernel,
+    // M^-1; p = s = 0)
     for (int i = threadIdx.x; i < 3 * v.nrow; i += blockDim.x) {
         if (!lean) v.x[i] = a.x[row0 * 3 + i];
         v.r[i] = a.r[row0 * 3 + i];
-        v.u[i] = a.z[row0 * 3 + i];
+        v.u[i] = reinterpret_cast<const T *>(a.z4 + row0 + i / 3)[i % 3];
         v.p[i] = T(0);
         v.s[i] = T(0);
     }
@@ -792,41 +837,15 @@ __global__ void __launch_bounds__(kPcgThreads) k_pcg_resident(PcgArgs<T> a, int 
         v.rp[i] = a.row_ptr[row0 + i] - v.b_begin;
         if (TTIE_BAD(ds, v.rp[i] >= 0 && v.rp[i] <= v.nnz, 43, v.rp[i])) v.rp[i] = 0;
     }
-    if (threadIdx.x < kMaxGridPcg / 32) s_bits[threadIdx.x] = 0u;
-    __syncthreads();
-    // the blocks whose rows this block's columns read
-    for (int i = threadIdx.x; i < v.nnz; i += blockDim.x) {
-        int c = a.col_idx[v.b_begin + i];
-        if (TTIE_BAD(ds, c >= 0 && (long long)c < nr, 44, c)) c = 0;
-        if (v.cached) {
+    if (v.cached)
+        for (int i = threadIdx.x; i < v.nnz; i += blockDim.x) {
+            int c = a.col_idx[v.b_begin + i];
+            if (TTIE_BAD(ds, c >= 0 && (long long)c < nr, 44, c)) c = 0;
             for (int k = 0; k < 9; ++k) v.val[(size_t)i * 9 + k] = a.bval[(size_t)(v.b_begin + i) * 9 + k];
             v.col[i] = c;
         }
-        const int owner = c / R;
-        if (owner != (int)blockIdx.x) atomicOr(&s_bits[owner >> 5], 1u << (owner & 31));
-    }
+    if (threadIdx.x == 0) s_bad = 0;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        int n = 0;
-        for (int b = 0; b < (int)gridDim.x; ++b)
-            if (s_bits[b >> 5] >> (b & 31) & 1u) {
-                if (n < kMaxDeps) s_dep[n] = b;
-                ++n;
-            }
-        s_ndep = n <= kMaxDeps ? n : -1;
-    }
-    // publish u for the first product
-    for (int lr = threadIdx.x; lr < v.nrow; lr += blockDim.x) {
-        vec4_t<T> z4;
-        z4.x = v.u[lr * 3]; z4.y = v.u[lr * 3 + 1]; z4.z = v.u[lr * 3 + 2]; z4.w = T(0);
-        a.z4[row0 + lr] = z4;
-    }
-    __syncthreads();
-    unsigned long long fe = epoch0 + 1, re = epoch0;
-    if (threadIdx.x == 0) {
-        __threadfence();
-        st_relaxed_u64(&a.flags[blockIdx.x], fe);
-    }
     const T mu = (T)ds->mu;
     // local r.u and r.r of the current residual (thread per row)
     Acc<T> gl, rl;
@@ -876,11 +895,11 @@ __global__ void __launch_bounds__(kPcgThreads) k_pcg_resident(PcgArgs<T> a, int 
         s_stop = stop;
     };
     while (true) {
-        if (!wait_flags(a.flags, s_dep, s_ndep, fe, ds)) return;
-        Acc<T> red[3] = {gl, resident_product(a, v, mu), rl};
-        if (!slot_allreduce<3, T>(red, a.slots, ++re, ds, decide)) return;
+        Acc<T> red[3] = {gl, resident_product(a, v, mu, (unsigned)it & 3u, &s_bad), rl};
+        if (!slot_allreduce<3, T>(red, a.slots, (unsigned)it, &s_bad, ds, decide)) return;
         if (s_stop) break;
         const T al = s_alpha, be = s_beta;
+        const unsigned tn = (unsigned)(it + 1) & 3u;
         gl = Acc<T>();
         rl = Acc<T>();
         for (int lr = threadIdx.x; lr < v.nrow; lr += blockDim.x) {
@@ -901,7 +920,8 @@ __global__ void __launch_bounds__(kPcgThreads) k_pcg_resident(PcgArgs<T> a, int 
             T zv[3];
 #pragma unroll
             for (int i = 0; i < 3; ++i) {
-                zv[i] = di[3 * i] * rv[0] + di[3 * i + 1] * rv[1] + di[3 * i + 2] * rv[2];
+                // the published (tagged) word is the value on every side
+                zv[i] = tag_word(di[3 * i] * rv[0] + di[3 * i + 1] * rv[1] + di[3 * i + 2] * rv[2], tn);
                 v.u[lr * 3 + i] = zv[i];
                 gl.add_prod(rv[i], zv[i]);
                 rl.add_prod(rv[i], rv[i]);
@@ -911,11 +931,6 @@ __global__ void __launch_bounds__(kPcgThreads) k_pcg_resident(PcgArgs<T> a, int 
         }
         ++it;
         __syncthreads();
-        ++fe;
-        if (threadIdx.x == 0) {
-            __threadfence();
-            st_relaxed_u64(&a.flags[blockIdx.x], fe);
-        }
     }
     if (!lean)
         for (int i = threadIdx.x; i < 3 * v.nrow; i += blockDim.x) a.x[row0 * 3 + i] = v.x[i];
@@ -1133,12 +1148,15 @@ cudaError_t pcg_solve(Ctx &c, const T *rhs, T *out, double rtol, int max_it) {
     TTIE_CUDA_TRY(ensure(c, c.pcg_q, (size_t)(nr > 0 ? nr : 1) * 3 * sizeof(T)));
     TTIE_CUDA_TRY(ensure(c, c.pcg_z4, (size_t)(nr > 0 ? nr : 1) * sizeof(vec4_t<T>)));
     TTIE_CUDA_TRY(ensure(c, c.partials, (size_t)kNumSMs * 16 * 4 * sizeof(double)));
+    TTIE_CUDA_TRY(ensure(c, c.pcg_sync, (size_t)kMaxGridPcg * 2 * sizeof(RedSlot)));
     double *part = (double *)c.partials.p;
     const unsigned g = grid_for(nr, kThreads, kNumSMs * 4);
     TTIE_CUDA_TRY(cudaMemsetAsync(&c.ds->bar_count, 0, 2 * sizeof(unsigned int), c.stream));
     launch(c, k_pcg_setup<T>, dim3(g), dim3(kThreads), (const int32_t *)c.row_ptr.p, (const int32_t *)c.col_idx.p,
                                                  (const T *)c.bsr_val.p, c.prm.mu_rel, (T *)c.dinv.p, rhs, out,
-                                                 (T *)c.pcg_r.p, (T *)c.pcg_z.p, (T *)c.pcg_p.p, part, c.ds);
+                                                 (T *)c.pcg_r.p, (T *)c.pcg_z.p, (T *)c.pcg_p.p, part,
+                                                 (vec4_t<T> *)c.pcg_z4.p, (unsigned long long *)c.pcg_sync.p,
+                                                 (int)(c.pcg_sync.bytes / sizeof(unsigned long long)), c.ds);
     TTIE_CUDA_TRY(cudaGetLastError());
     PcgArgs<T> args;
     args.row_ptr = (const int32_t *)c.row_ptr.p;
@@ -1168,21 +1186,14 @@ cudaError_t pcg_solve(Ctx &c, const T *rhs, T *out, double rtol, int max_it) {
     const size_t lean_bytes = ((size_t)rows_per_block * 15 * sizeof(T) + (size_t)(rows_per_block + 1) * 4 + 15) / 16 * 16;
     int lean = vec_bytes <= (size_t)kResidentSmem ? 0 : 1;
     const bool resident = lean_bytes <= (size_t)kResidentSmem;
-    if (!c.pcg_sync.p) {   // fixed size, zeroed once: epochs only grow over the context's life
-        TTIE_CUDA_TRY(ensure(c, c.pcg_sync, (size_t)kMaxGridPcg * (2 * sizeof(RedSlot) + sizeof(unsigned long long))));
-        TTIE_CUDA_TRY(cudaMemsetAsync(c.pcg_sync.p, 0, c.pcg_sync.bytes, c.stream));
-    }
     args.slots = (RedSlot *)c.pcg_sync.p;
-    args.flags = (unsigned long long *)((RedSlot *)c.pcg_sync.p + 2 * kMaxGridPcg);
-    c.pcg_epoch += 1ull << 32;
     ++c.n_launch;
     if (c.prm.profile) cudaEventRecord(c.ev[8], c.stream);
     if (resident) {
         TTIE_CUDA_TRY(cudaFuncSetAttribute((const void *)k_pcg_resident<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            kResidentSmem));
         int rpb = (int)rows_per_block, smem = kResidentSmem;
-        unsigned long long e0 = c.pcg_epoch;
-        void *kargs[] = {&args, &rpb, &smem, &e0, &lean};
+        void *kargs[] = {&args, &rpb, &smem, &lean};
         TTIE_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)k_pcg_resident<T>, dim3((unsigned)blocks),
                                                   dim3(kPcgThreads), kargs, (size_t)kResidentSmem, c.stream));
     } else {
@@ -1243,7 +1254,7 @@ cudaError_t pcg_run_raw(cudaStream_t stream, int num_sms, const int32_t *row_ptr
                         int max_it) {
     const unsigned g = grid_for(n_rows, kThreads, kNumSMs * 4);
     k_pcg_setup<float><<<g, kThreads, 0, stream>>>(row_ptr, col_idx, bval, mu_rel, dinv, rhs, out, r, z, p, partials,
-                                                   ds);
+                                                   nullptr, nullptr, 0, ds);
     TTIE_CUDA_TRY(cudaGetLastError());
     PcgArgs<float> args;
     args.row_ptr = row_ptr;

@@ -154,7 +154,6 @@ struct Ctx {
     int num_sms = 0;
     unsigned long long n_launch = 0;   // kernels launched through this context
     bool time_kernels = false;         // profile: events around the classification / PCG kernels
-    unsigned long long pcg_epoch = 0;  // resident PCG: epochs of its flags and slots (grow only)
     int64_t tree_leaves = -1;          // leaves of the hierarchy in the BVH buffers (-1: none)
     int inst_tuned[4] = {0, 0, 0, 0};  // batched PCG: block size chosen per size bucket (0: not yet)
 };

@@ -13,6 +13,7 @@ namespace ttie {
 // iteration costs microseconds.  For FP64 vectors it is a plain double.
 template <typename T> struct Acc;
 template <> struct Acc<double> {
+    static constexpr int kTagShift = 0;   // a tag in bits() sits in the significand's lowest bits
     double v = 0.0;
     __device__ __forceinline__ void add_prod(double a, double b) { v = fma(a, b, v); }
     __device__ __forceinline__ void add(const Acc &o) { v += o.v; }
@@ -34,6 +35,7 @@ template <> struct Acc<double> {
     __device__ __forceinline__ double value() const { return v; }
 };
 template <> struct Acc<float> {
+    static constexpr int kTagShift = 32;  // a tag in bits() sits in the lowest bits of lo's significand
     float hi = 0.f, lo = 0.f;
     __device__ __forceinline__ void add_pair(float bh, float bl) {
         const float s = hi + bh, bb = s - hi;
