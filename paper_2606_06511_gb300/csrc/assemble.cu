@@ -558,15 +558,16 @@ __global__ void __launch_bounds__(kPcgThreads) k_pcg_persistent(PcgArgs<T> a) {
 // summed through per-block slots whose words carry the reduction's tag (8 + k mod 8); every
 // block reads all slots in the same order, so all blocks take the same decisions.
 //
-// Why the tags cannot be mistaken: u of iteration k is written after reduction k - 1, and a
-// reader reads it after that reduction too, whose publication (release fence, then the
-// words) and completion (the words, then an acquire fence) order every u of iteration k - 1
-// before the reader's loads; no block writes u of iteration k + 1 before reduction k, which
-// needs the reader's product.  So a reader sees the words of iteration k - 1 or k.  Slot
-// buffers alternate by reduction parity: a reader of reduction k sees k - 2 or k.  The setup
-// kernel (an earlier launch) writes u of iteration 0 with tag 0 and clears the slots (tag 0
-// is never a reduction's).  Every wait is bounded; on timeout ERR_BARRIER is set and the
-// kernel returns.
+// Why the tags cannot be mistaken, with no fences: all published words are written and read
+// with relaxed gpu-scope accesses, and a thread reads the same words in every iteration (its
+// columns, its slots).  Coherence per location: having waited for the tag of iteration
+// k - 1 in a word, the same thread's next load of it returns that write or a later one.  No
+// block writes u of iteration k + 1 before it has read the reader's sums of reduction k,
+// which follow the reader's product (a causality cycle otherwise).  So a reader of u sees
+// iteration k - 1 or k; a reader of a slot (buffers alternate by reduction parity) sees
+// reduction k - 2 or k.  The setup kernel (an earlier launch) writes u of iteration 0 with
+// tag 0 and clears the slots (tag 0 is never a reduction's).  Every wait is bounded; on
+// timeout ERR_BARRIER is set and the kernel returns.
 constexpr int kResidentSmem = 220 * 1024;   // dynamic shared memory per block
 constexpr int kMaxGridPcg = 256;            // slots per lane in the reduction: 8
 constexpr long long kTagSpins = kBarrierSpins / 16;   // reloads of one word (each an L2 round trip)
@@ -579,7 +580,6 @@ __device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long
 __device__ __forceinline__ void st_relaxed_u64(unsigned long long *p, unsigned long long v) {
     asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
-__device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
 
 // relaxed (coherent, never cached in L1) load of one published row vector
 template <typename T> __device__ __forceinline__ vec4_t<T> ld_row(const vec4_t<T> *p);
@@ -596,6 +596,15 @@ template <> __device__ __forceinline__ dvec4 ld_row<double>(const dvec4 *p) {
     asm volatile("ld.relaxed.gpu.global.f64 %0, [%1];" : "=d"(r.z) : "l"(reinterpret_cast<const double *>(p) + 2));
     r.w = 0.0;
     return r;
+}
+template <typename T> __device__ __forceinline__ void st_row(vec4_t<T> *p, const vec4_t<T> &v);
+template <> __device__ __forceinline__ void st_row<float>(float4 *p, const float4 &v) {
+    asm volatile("st.relaxed.gpu.global.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w)
+                 : "memory");
+}
+template <> __device__ __forceinline__ void st_row<double>(dvec4 *p, const dvec4 &v) {
+    asm volatile("st.relaxed.gpu.global.v2.f64 [%0], {%1, %2};" ::"l"(p), "d"(v.x), "d"(v.y) : "memory");
+    asm volatile("st.relaxed.gpu.global.f64 [%0], %1;" ::"l"(reinterpret_cast<double *>(p) + 2), "d"(v.z) : "memory");
 }
 template <typename T> __device__ __forceinline__ bool row_tagged(const vec4_t<T> &g, unsigned t) {
     return (word_tag(g.x) == t) & (word_tag(g.y) == t) & (word_tag(g.z) == t);
@@ -619,30 +628,36 @@ template <typename T> __device__ __forceinline__ unsigned bits_tag(unsigned long
     return (unsigned)(b >> Acc<T>::kTagShift) & 15u;
 }
 
-// Grid sums of N <= 3 accumulators through tagged slots, identical in every block.  Thread 0
-// publishes its block's sums (tag t = 8 + k mod 8) in buffer k mod 2; warp i < N loads word i
-// of every slot until all carry t and adds them in slot order; thread 0 then runs
-// fin(totals).  A block whose product gave up (*bad) publishes nothing.  Returns false
-// (ERR_BARRIER set) when a wait ran out.
+// Grid sums of N <= 3 accumulators through tagged slots, identical in every block.  After
+// the warps' partial sums meet in shared memory, warp i < N adds word i over the warps,
+// publishes it with tag t = 8 + k mod 8 in buffer k mod 2, loads word i of every slot until
+// all carry t and adds them in slot order; thread 0 then runs fin(totals).  A block whose
+// product gave up (*bad) publishes nothing.  Returns false (ERR_BARRIER set) when a wait
+// ran out.
 template <int N, typename T, typename Fin>
 __device__ __forceinline__ bool slot_allreduce(Acc<T> (&a)[N], RedSlot *slots, unsigned k, const int *bad,
                                                DevScalars *ds, Fin fin) {
     static_assert(N <= 3, "three words per slot");
     __shared__ int s_fail;
     __shared__ int s_wfail[N];
-    __shared__ unsigned long long s_tot[N];
+    __shared__ unsigned long long s_part[N][32], s_tot[N];
     const unsigned G = gridDim.x;
     const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
-    block_sums<N, T>(a);   // its barrier also makes *bad visible
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+#pragma unroll
+        for (int o = 16; o; o >>= 1) a[i].add(a[i].shfl_xor(0xffffffffu, o, 32));
+        if (lane == 0) s_part[i][wi] = a[i].bits();
+    }
+    __syncthreads();   // also makes *bad visible
     RedSlot *buf = slots + (size_t)(k & 1u) * kMaxGridPcg;
     const unsigned t = 8u | (k & 7u);
     if (wi < N) {
-        bool fail = *(const volatile int *)bad != 0;
-        if (!fail && threadIdx.x == 0) {
-            fence_acq_rel_gpu();   // release: this block's u (and everything before) ahead of its sums
+        Acc<T> mine = lane < (int)(blockDim.x >> 5) ? Acc<T>::from_bits(s_part[wi][lane]) : Acc<T>();
 #pragma unroll
-            for (int i = 0; i < N; ++i) st_relaxed_u64(&buf[blockIdx.x].v[i], tag_bits<T>(a[i].bits(), t));
-        }
+        for (int o = 16; o; o >>= 1) mine.add(mine.shfl_xor(0xffffffffu, o, 32));
+        bool fail = *(const volatile int *)bad != 0;
+        if (!fail && lane == 0) st_relaxed_u64(&buf[blockIdx.x].v[wi], tag_bits<T>(mine.bits(), t));
         // every lane loads its (up to 8) slots' word wi with all loads in flight until they carry t
         unsigned ready = 0, want = 0;
 #pragma unroll
@@ -661,7 +676,6 @@ __device__ __forceinline__ bool slot_allreduce(Acc<T> (&a)[N], RedSlot *slots, u
             if (++spins > kBarrierSpins) { fail = true; break; }
             __nanosleep(20);
         }
-        fence_acq_rel_gpu();   // acquire: the next iteration's loads of u follow every block's sums
         Acc<T> sum;
 #pragma unroll
         for (int q = 0; q < kMaxGridPcg / 32; ++q)
@@ -927,7 +941,7 @@ __global__ void __launch_bounds__(kPcgThreads) k_pcg_resident(PcgArgs<T> a, int 
                 rl.add_prod(rv[i], rv[i]);
             }
             z4.x = zv[0]; z4.y = zv[1]; z4.z = zv[2]; z4.w = T(0);
-            a.z4[row0 + lr] = z4;
+            st_row<T>(&a.z4[row0 + lr], z4);
         }
         ++it;
         __syncthreads();

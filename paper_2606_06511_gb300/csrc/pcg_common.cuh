@@ -1,5 +1,5 @@
 // Shared device helpers of the PCG solvers: the dot-product accumulator (FP32 pairs for
-// FP32 vectors), its block reduction, and the inverse of a regularised 3x3 block.
+// FP32 vectors) and the inverse of a regularised 3x3 block.
 #pragma once
 #include "common.cuh"
 
@@ -86,29 +86,6 @@ template <> struct Acc<float> {
     __device__ __forceinline__ float approx() const { return hi + lo; }
     __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
 };
-
-// Block sums of N accumulators (warp trees, then warp 0 over the warp totals), valid in warp 0.
-template <int N, typename T>
-__device__ __forceinline__ void block_sums(Acc<T> (&a)[N]) {
-    __shared__ unsigned long long sh[N][32];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-#pragma unroll
-    for (int i = 0; i < N; ++i) {
-#pragma unroll
-        for (int o = 16; o; o >>= 1) a[i].add(a[i].shfl_xor(0xffffffffu, o, 32));
-        if (lane == 0) sh[i][w] = a[i].bits();
-    }
-    __syncthreads();
-    if (w == 0) {
-#pragma unroll
-        for (int i = 0; i < N; ++i) {
-            a[i] = lane < (int)(blockDim.x >> 5) ? Acc<T>::from_bits(sh[i][lane]) : Acc<T>();
-#pragma unroll
-            for (int o = 16; o; o >>= 1) a[i].add(a[i].shfl_xor(0xffffffffu, o, 32));
-        }
-    }
-}
-
 
 // Inverse of the 3x3 block m + mu I (row-major), by the adjugate.
 template <typename T>
