@@ -281,16 +281,45 @@ __device__ __forceinline__ double tag_word(double v, unsigned t) {
 __device__ __forceinline__ unsigned word_tag(float v) { return __float_as_uint(v) & 3u; }
 __device__ __forceinline__ unsigned word_tag(double v) { return (unsigned)__double_as_longlong(v) & 3u; }
 
+// Rows of the block-resident PCG's G blocks: part[b] .. part[b + 1], balanced by the work
+// of a block, nnz + row_weight * rows (the first row r whose prefix row_ptr[r] +
+// row_weight * r reaches b / G of the total), then clamped to at most r_cap rows per block
+// (a forward pass bounds each block by its predecessor, a backward pass the tail; r_cap * G
+// >= n_rows makes both feasible).  One block of the setup grid.
+__device__ void resident_partition(const int32_t *__restrict__ row_ptr, long long nr, int G, int r_cap, int row_weight,
+                                   int *__restrict__ part) {
+    const long long total = (long long)row_ptr[nr] + (long long)row_weight * nr;
+    for (int b = threadIdx.x; b <= G; b += blockDim.x) {
+        long long lo = 0, hi = nr;
+        if (b == G) lo = nr;
+        else if (b > 0) {
+            const long long target = total * b / G;
+            while (lo < hi) {
+                const long long mid = (lo + hi) / 2;
+                if ((long long)row_ptr[mid] + (long long)row_weight * mid >= target) hi = mid;
+                else lo = mid + 1;
+            }
+        }
+        part[b] = (int)lo;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int b = 1; b < G; ++b) part[b] = min(max(part[b], part[b - 1]), part[b - 1] + r_cap);
+        for (int b = G - 1; b >= 1; --b) part[b] = max(part[b], part[b + 1] - r_cap);
+    }
+}
+
 // p = z = M^-1 r0, r = r0, x = 0; r.z and r.r summed.  For the block-resident kernel also the
-// tagged mirror z4 of z (tag 0: the first iteration's vector) and its reduction words cleared
-// (tag 0 never marks a published reduction word).
+// tagged mirror z4 of z (tag 0: the first iteration's vector), its reduction words cleared
+// (tag 0 never marks a published reduction word) and its row partition (block 0).
 template <typename T>
 __global__ void k_pcg_setup(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col_idx,
                             const T *__restrict__ bval, double mu_rel, T *__restrict__ dinv, const T *__restrict__ rhs,
                             T *__restrict__ x, T *__restrict__ r, T *__restrict__ z, T *__restrict__ p, double *partials,
                             vec4_t<T> *__restrict__ z4, unsigned long long *__restrict__ sync_words, int n_sync_words,
-                            DevScalars *ds) {
+                            int *__restrict__ part, int part_blocks, int r_cap, int row_weight, DevScalars *ds) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_sync_words; i += gridDim.x * blockDim.x) sync_words[i] = 0ull;
+    if (part && blockIdx.x == 0) resident_partition(row_ptr, (long long)ds->n_rows, part_blocks, r_cap, row_weight, part);
     const unsigned long long nr = ds->n_rows;
     const T mu = (T)(nr ? mu_rel * ds->trace / (3.0 * (double)nr) : 0.0);
     double rz = 0.0, rr = 0.0;
@@ -422,6 +451,7 @@ template <typename T> struct PcgArgs {
     vec4_t<T> *z4;           // z mirrored as one tagged 16/32-byte vector per row (resident kernel)
     double *partA, *partB;
     RedSlot *slots;          // resident kernel: 2 x kMaxGridPcg tagged reduction slots
+    const int *part;         // resident kernel: rows of block b are part[b] .. part[b + 1]
     double rtol2;
     int max_it;
     DevScalars *ds;
@@ -571,6 +601,7 @@ __global__ void __launch_bounds__(kPcgThreads) k_pcg_persistent(PcgArgs<T> a) {
 constexpr int kResidentSmem = 220 * 1024;   // dynamic shared memory per block
 constexpr int kMaxGridPcg = 256;            // slots per lane in the reduction: 8
 constexpr long long kTagSpins = kBarrierSpins / 16;   // reloads of one word (each an L2 round trip)
+constexpr int kRowWeight = 8;   // work of a row in the partition, in matrix blocks (lane-group pass, shuffles, update)
 
 __device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long *p) {
     unsigned long long v;
@@ -729,21 +760,33 @@ __device__ __forceinline__ Acc<T> resident_product(const PcgArgs<T> &a, const Re
                                                    int *bad) {
     if (v.gathered) {
         // gather every block's column vector first: all loads of a thread in flight together
+        // words not yet tagged t are loaded again, all of a thread's together
         constexpr int U = 4;
         for (int j0 = threadIdx.x; j0 < v.nnz; j0 += U * kPcgThreads) {
             vec4_t<T> g[U];
-#pragma unroll
-            for (int k = 0; k < U; ++k) {
-                const int j = j0 + k * kPcgThreads;
-                if (j < v.nnz) g[k] = ld_row<T>(&a.z4[v.col[j]]);
-            }
+            unsigned pend = 0;
 #pragma unroll
             for (int k = 0; k < U; ++k) {
                 const int j = j0 + k * kPcgThreads;
                 if (j < v.nnz) {
-                    settle_row<T>(g[k], &a.z4[v.col[j]], t, bad);
-                    v.gu[3 * j] = g[k].x; v.gu[3 * j + 1] = g[k].y; v.gu[3 * j + 2] = g[k].z;
+                    g[k] = ld_row<T>(&a.z4[v.col[j]]);
+                    pend |= 1u << k;
                 }
+            }
+            long long spins = 0;
+            while (true) {
+#pragma unroll
+                for (int k = 0; k < U; ++k)
+                    if ((pend >> k & 1u) && row_tagged<T>(g[k], t)) {
+                        const int j = j0 + k * kPcgThreads;
+                        v.gu[3 * j] = g[k].x; v.gu[3 * j + 1] = g[k].y; v.gu[3 * j + 2] = g[k].z;
+                        pend &= ~(1u << k);
+                    }
+                if (!pend) break;
+                if (++spins > kTagSpins || *(volatile int *)bad) { *bad = 1; break; }
+#pragma unroll
+                for (int k = 0; k < U; ++k)
+                    if (pend >> k & 1u) g[k] = ld_row<T>(&a.z4[v.col[j0 + k * kPcgThreads]]);
             }
         }
         __syncthreads();
@@ -801,32 +844,38 @@ __device__ __forceinline__ Acc<T> resident_product(const PcgArgs<T> &a, const Re
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kPcgThreads) k_pcg_resident(PcgArgs<T> a, int rows_per_block, int smem_bytes,
-                                                             int lean) {
+__global__ void __launch_bounds__(kPcgThreads) k_pcg_resident(PcgArgs<T> a, int smem_bytes) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ T s_alpha, s_beta;
     __shared__ int s_stop, s_bad;
     DevScalars *ds = a.ds;
     if (ds->pcg_done) return;
     const long long nr = (long long)ds->n_rows;
-    const int R = rows_per_block;
-    const long long row0 = (long long)blockIdx.x * R;
+    const long long row0 = a.part[blockIdx.x];
     ResidentView<T> v;
-    v.nrow = (int)max(0LL, min((long long)R, nr - row0));
+    v.nrow = a.part[blockIdx.x + 1] - (int)row0;
+    const auto vec_size = [](int rows, int per_row) {
+        return ((size_t)rows * per_row * sizeof(T) + (size_t)(rows + 1) * sizeof(int) + 15) / 16 * 16;
+    };
+    if (TTIE_BAD(ds, row0 >= 0 && v.nrow >= 0 && row0 + v.nrow <= nr && vec_size(v.nrow, 15) <= (size_t)smem_bytes, 45,
+                 v.nrow))
+        v.nrow = 0;
+    const int R = v.nrow;
     // lean: x and the inverse diagonal blocks (read or written once per row and iteration) stay
     // in global memory so that larger row ranges fit
+    const bool lean = vec_size(R, 27) > (size_t)smem_bytes;
     size_t vec_bytes;
     if (lean) {
         v.r = (T *)smem; v.u = v.r + 3 * R; v.p = v.u + 3 * R; v.s = v.p + 3 * R; v.w = v.s + 3 * R;
         v.rp = (int *)(v.w + 3 * R);
         v.x = a.x + row0 * 3;
         v.di = (T *)a.dinv + row0 * 9;
-        vec_bytes = ((size_t)R * 15 * sizeof(T) + (size_t)(R + 1) * sizeof(int) + 15) / 16 * 16;
+        vec_bytes = vec_size(R, 15);
     } else {
         v.x = (T *)smem; v.r = v.x + 3 * R; v.u = v.r + 3 * R; v.p = v.u + 3 * R; v.s = v.p + 3 * R; v.w = v.s + 3 * R;
         v.di = v.w + 3 * R;
         v.rp = (int *)(v.di + 9 * R);
-        vec_bytes = ((size_t)R * 27 * sizeof(T) + (size_t)(R + 1) * sizeof(int) + 15) / 16 * 16;
+        vec_bytes = vec_size(R, 27);
     }
     v.b_begin = v.nrow ? a.row_ptr[row0] : 0;
     v.nnz = v.nrow ? a.row_ptr[row0 + v.nrow] - v.b_begin : 0;
@@ -1162,15 +1211,30 @@ cudaError_t pcg_solve(Ctx &c, const T *rhs, T *out, double rtol, int max_it) {
     TTIE_CUDA_TRY(ensure(c, c.pcg_q, (size_t)(nr > 0 ? nr : 1) * 3 * sizeof(T)));
     TTIE_CUDA_TRY(ensure(c, c.pcg_z4, (size_t)(nr > 0 ? nr : 1) * sizeof(vec4_t<T>)));
     TTIE_CUDA_TRY(ensure(c, c.partials, (size_t)kNumSMs * 16 * 4 * sizeof(double)));
-    TTIE_CUDA_TRY(ensure(c, c.pcg_sync, (size_t)kMaxGridPcg * 2 * sizeof(RedSlot)));
+    // reduction slots, then the resident kernel's row partition
+    TTIE_CUDA_TRY(ensure(c, c.pcg_sync, (size_t)kMaxGridPcg * 2 * sizeof(RedSlot) + (kMaxGridPcg + 1) * sizeof(int)));
+    const int sms = c.num_sms > 0 ? c.num_sms : kNumSMs;
+    // one block per SM at most: fewer participants in every reduction
+    int64_t blocks = (nr * kLanesPerRow + kPcgThreads - 1) / kPcgThreads;
+    if (blocks > (int64_t)sms) blocks = sms;
+    if (blocks > kMaxGridPcg) blocks = kMaxGridPcg;
+    if (blocks < 1) blocks = 1;
+    // rows resident in shared memory when every block's vectors fit (lean layout: 15 values
+    // per row); blocks are balanced by nnz + kRowWeight * rows within that cap; else the
+    // global-memory kernel
+    const int64_t r_cap = ((int64_t)kResidentSmem - 4 - 15) / (15 * (int64_t)sizeof(T) + 4);
+    const bool resident = (nr + blocks - 1) / blocks <= r_cap;
+    RedSlot *slots = (RedSlot *)c.pcg_sync.p;
+    int *rpart = (int *)(slots + 2 * kMaxGridPcg);
     double *part = (double *)c.partials.p;
     const unsigned g = grid_for(nr, kThreads, kNumSMs * 4);
     TTIE_CUDA_TRY(cudaMemsetAsync(&c.ds->bar_count, 0, 2 * sizeof(unsigned int), c.stream));
     launch(c, k_pcg_setup<T>, dim3(g), dim3(kThreads), (const int32_t *)c.row_ptr.p, (const int32_t *)c.col_idx.p,
                                                  (const T *)c.bsr_val.p, c.prm.mu_rel, (T *)c.dinv.p, rhs, out,
                                                  (T *)c.pcg_r.p, (T *)c.pcg_z.p, (T *)c.pcg_p.p, part,
-                                                 (vec4_t<T> *)c.pcg_z4.p, (unsigned long long *)c.pcg_sync.p,
-                                                 (int)(c.pcg_sync.bytes / sizeof(unsigned long long)), c.ds);
+                                                 (vec4_t<T> *)c.pcg_z4.p, (unsigned long long *)slots,
+                                                 (int)(2 * kMaxGridPcg * sizeof(RedSlot) / sizeof(unsigned long long)),
+                                                 resident ? rpart : nullptr, (int)blocks, (int)r_cap, kRowWeight, c.ds);
     TTIE_CUDA_TRY(cudaGetLastError());
     PcgArgs<T> args;
     args.row_ptr = (const int32_t *)c.row_ptr.p;
@@ -1188,26 +1252,15 @@ cudaError_t pcg_solve(Ctx &c, const T *rhs, T *out, double rtol, int max_it) {
     args.rtol2 = rtol * rtol;
     args.max_it = max_it;
     args.ds = c.ds;
-    const int sms = c.num_sms > 0 ? c.num_sms : kNumSMs;
-    // one block per SM at most: fewer participants in every reduction
-    int64_t blocks = (nr * kLanesPerRow + kPcgThreads - 1) / kPcgThreads;
-    if (blocks > (int64_t)sms) blocks = sms;
-    if (blocks > kMaxGridPcg) blocks = kMaxGridPcg;
-    if (blocks < 1) blocks = 1;
-    // rows resident in shared memory when a block's vectors fit; else the global-memory kernel
-    const int64_t rows_per_block = (nr + blocks - 1) / blocks;
-    const size_t vec_bytes = ((size_t)rows_per_block * 27 * sizeof(T) + (size_t)(rows_per_block + 1) * 4 + 15) / 16 * 16;
-    const size_t lean_bytes = ((size_t)rows_per_block * 15 * sizeof(T) + (size_t)(rows_per_block + 1) * 4 + 15) / 16 * 16;
-    int lean = vec_bytes <= (size_t)kResidentSmem ? 0 : 1;
-    const bool resident = lean_bytes <= (size_t)kResidentSmem;
-    args.slots = (RedSlot *)c.pcg_sync.p;
+    args.slots = slots;
+    args.part = rpart;
     ++c.n_launch;
     if (c.prm.profile) cudaEventRecord(c.ev[8], c.stream);
     if (resident) {
         TTIE_CUDA_TRY(cudaFuncSetAttribute((const void *)k_pcg_resident<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            kResidentSmem));
-        int rpb = (int)rows_per_block, smem = kResidentSmem;
-        void *kargs[] = {&args, &rpb, &smem, &lean};
+        int smem = kResidentSmem;
+        void *kargs[] = {&args, &smem};
         TTIE_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)k_pcg_resident<T>, dim3((unsigned)blocks),
                                                   dim3(kPcgThreads), kargs, (size_t)kResidentSmem, c.stream));
     } else {
@@ -1268,7 +1321,7 @@ cudaError_t pcg_run_raw(cudaStream_t stream, int num_sms, const int32_t *row_ptr
                         int max_it) {
     const unsigned g = grid_for(n_rows, kThreads, kNumSMs * 4);
     k_pcg_setup<float><<<g, kThreads, 0, stream>>>(row_ptr, col_idx, bval, mu_rel, dinv, rhs, out, r, z, p, partials,
-                                                   nullptr, nullptr, 0, ds);
+                                                   nullptr, nullptr, 0, nullptr, 0, 0, 0, ds);
     TTIE_CUDA_TRY(cudaGetLastError());
     PcgArgs<float> args;
     args.row_ptr = row_ptr;
@@ -1280,7 +1333,9 @@ cudaError_t pcg_run_raw(cudaStream_t stream, int num_sms, const int32_t *row_ptr
     args.z = z;
     args.p = p;
     args.q = q;
-    args.z4 = nullptr;   // only the block-resident kernel uses the vector mirror
+    args.z4 = nullptr;   // only the block-resident kernel uses the vector mirror, slots and partition
+    args.slots = nullptr;
+    args.part = nullptr;
     args.partA = partials;
     args.partB = partials + 2 * kNumSMs * 8;
     args.rtol2 = rtol * rtol;
