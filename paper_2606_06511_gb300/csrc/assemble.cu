@@ -450,7 +450,7 @@ template <typename T> struct PcgArgs {
     T *x, *r, *z, *p, *q;
     vec4_t<T> *z4;           // z mirrored as one tagged 16/32-byte vector per row (resident kernel)
     double *partA, *partB;
-    RedSlot *slots;          // resident kernel: 2 x kMaxGridPcg tagged reduction slots
+    RedSlot *slots;          // resident kernel: 2 x kMaxGridPcg tagged reduction slots, then 2 total slots
     const int *part;         // resident kernel: rows of block b are part[b] .. part[b + 1]
     double rtol2;
     int max_it;
@@ -585,31 +585,38 @@ __global__ void __launch_bounds__(kPcgThreads) k_pcg_persistent(PcgArgs<T> a) {
 // The product needs u of other blocks' rows.  Each block publishes its u as one 16/32-byte
 // vector per row whose words carry the iteration's tag (k mod 4); a reader loads the words
 // of its columns and loads again those whose tag is not yet k.  The three dot products are
-// summed through per-block slots whose words carry the reduction's tag (8 + k mod 8); every
-// block reads all slots in the same order, so all blocks take the same decisions.
+// summed through per-block slots whose words carry the reduction's tag (8 + k mod 8): block
+// 0 adds all slots in a fixed order and publishes the totals, tagged the same way, which
+// every block reads, so all blocks take the same decisions.
 //
 // Why the tags cannot be mistaken, with no fences: all published words are written and read
 // with relaxed gpu-scope accesses, and a thread reads the same words in every iteration (its
 // columns, its slots).  Coherence per location: having waited for the tag of iteration
 // k - 1 in a word, the same thread's next load of it returns that write or a later one.  No
-// block writes u of iteration k + 1 before it has read the reader's sums of reduction k,
-// which follow the reader's product (a causality cycle otherwise).  So a reader of u sees
-// iteration k - 1 or k; a reader of a slot (buffers alternate by reduction parity) sees
-// reduction k - 2 or k.  The setup kernel (an earlier launch) writes u of iteration 0 with
-// tag 0 and clears the slots (tag 0 is never a reduction's).  Every wait is bounded; on
+// block writes u of iteration k + 1 before it has read the totals of reduction k, which
+// follow the reader's sums, which follow its product (a causality cycle otherwise).  So a
+// reader of u sees iteration k - 1 or k.  Slots and totals alternate between two buffers by
+// reduction parity: no block publishes sums of reduction k + 2 before it has read the totals
+// of k + 1, which block 0 publishes after it has read every slot of k + 1 (so after those of
+// k), so block 0 sees reduction k - 2 or k in a slot and every block sees k - 2 or k in the
+// totals.  The setup kernel (an earlier launch) writes u of iteration 0 with tag 0 and
+// clears slots and totals (tag 0 is never a reduction's).  Every wait is bounded; on
 // timeout ERR_BARRIER is set and the kernel returns.
 constexpr int kResidentSmem = 220 * 1024;   // dynamic shared memory per block
-constexpr int kMaxGridPcg = 256;            // slots per lane in the reduction: 8
+constexpr int kMaxGridPcg = 160;            // at least the SM count; slots per lane of the root's poll: 5
 constexpr long long kTagSpins = kBarrierSpins / 16;   // reloads of one word (each an L2 round trip)
 constexpr int kRowWeight = 8;   // work of a row in the partition, in matrix blocks (lane-group pass, shuffles, update)
 
-__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long *p) {
-    unsigned long long v;
-    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p));
-    return v;
-}
 __device__ __forceinline__ void st_relaxed_u64(unsigned long long *p, unsigned long long v) {
     asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// a block's row range that does not fit its layout: recorded as a failed check, rows dropped
+__device__ __forceinline__ void partition_fail(DevScalars *ds, int code) {
+    if (threadIdx.x == 0) {
+        atomicCAS(&ds->check_code, 0, code);
+        atomicOr(&ds->err, ERR_CHECK);
+    }
 }
 
 // relaxed (coherent, never cached in L1) load of one published row vector
@@ -659,19 +666,28 @@ template <typename T> __device__ __forceinline__ unsigned bits_tag(unsigned long
     return (unsigned)(b >> Acc<T>::kTagShift) & 15u;
 }
 
-// Grid sums of N <= 3 accumulators through tagged slots, identical in every block.  After
-// the warps' partial sums meet in shared memory, warp i < N adds word i over the warps,
-// publishes it with tag t = 8 + k mod 8 in buffer k mod 2, loads word i of every slot until
-// all carry t and adds them in slot order; thread 0 then runs fin(totals).  A block whose
-// product gave up (*bad) publishes nothing.  Returns false (ERR_BARRIER set) when a wait
-// ran out.
+// one reduction slot, all four words in one 32-byte load (each word read atomically)
+__device__ __forceinline__ void ld_slot(const RedSlot *p, unsigned long long (&w)[4]) {
+    asm volatile("ld.relaxed.gpu.global.v4.u64 {%0, %1, %2, %3}, [%4];"
+                 : "=l"(w[0]), "=l"(w[1]), "=l"(w[2]), "=l"(w[3])
+                 : "l"(p));
+}
+
+// Grid sums of N <= 3 accumulators, identical in every block, through tagged words (tag
+// t = 8 + k mod 8 for reduction k, buffers by k mod 2).  After the warps' partial sums meet
+// in shared memory, warp i < N adds word i over the warps and publishes it in the block's
+// slot.  Block 0 alone loads all slots (one 32-byte load each) until every word carries t,
+// adds them in slot order and publishes the totals in one slot of their own; every other
+// block polls that one slot.  So each poll round costs the memory system one load per block
+// instead of one per block and slot.  Thread 0 then runs fin(totals).  A block that gave up
+// (*bad) publishes nothing.  Returns false (ERR_BARRIER set) when a wait ran out.
 template <int N, typename T, typename Fin>
 __device__ __forceinline__ bool slot_allreduce(Acc<T> (&a)[N], RedSlot *slots, unsigned k, const int *bad,
                                                DevScalars *ds, Fin fin) {
     static_assert(N <= 3, "three words per slot");
     __shared__ int s_fail;
-    __shared__ int s_wfail[N];
-    __shared__ unsigned long long s_part[N][32], s_tot[N];
+    __shared__ unsigned long long s_part[N][32];
+    __shared__ unsigned long long s_w[kMaxGridPcg][N];
     const unsigned G = gridDim.x;
     const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
 #pragma unroll
@@ -682,54 +698,82 @@ __device__ __forceinline__ bool slot_allreduce(Acc<T> (&a)[N], RedSlot *slots, u
     }
     __syncthreads();   // also makes *bad visible
     RedSlot *buf = slots + (size_t)(k & 1u) * kMaxGridPcg;
+    RedSlot *tot = slots + 2 * kMaxGridPcg + (k & 1u);
     const unsigned t = 8u | (k & 7u);
+    const bool gave_up = *(const volatile int *)bad != 0;
     if (wi < N) {
         Acc<T> mine = lane < (int)(blockDim.x >> 5) ? Acc<T>::from_bits(s_part[wi][lane]) : Acc<T>();
 #pragma unroll
         for (int o = 16; o; o >>= 1) mine.add(mine.shfl_xor(0xffffffffu, o, 32));
-        bool fail = *(const volatile int *)bad != 0;
-        if (!fail && lane == 0) st_relaxed_u64(&buf[blockIdx.x].v[wi], tag_bits<T>(mine.bits(), t));
-        // every lane loads its (up to 8) slots' word wi with all loads in flight until they carry t
-        unsigned ready = 0, want = 0;
-#pragma unroll
-        for (int q = 0; q < kMaxGridPcg / 32; ++q)
-            if (lane + 32u * q < G) want |= 1u << q;
-        unsigned long long w[kMaxGridPcg / 32];
-        long long spins = 0;
-        while (!fail) {
+        if (lane == 0 && !gave_up) st_relaxed_u64(&buf[blockIdx.x].v[wi], tag_bits<T>(mine.bits(), t));
+    }
+    if (wi == 0) {
+        bool fail = gave_up;
+        unsigned long long tw[4];
+        if (blockIdx.x == 0) {
+            // the root: every slot, all loads of a lane in flight together
+            unsigned ready = 0, want = 0;
 #pragma unroll
             for (int q = 0; q < kMaxGridPcg / 32; ++q)
-                if ((want & ~ready) >> q & 1u) {
-                    w[q] = ld_relaxed_u64(&buf[lane + 32 * q].v[wi]);
-                    if (bits_tag<T>(w[q]) == t) ready |= 1u << q;
-                }
-            if (__all_sync(0xffffffffu, ready == want)) break;
-            if (++spins > kBarrierSpins) { fail = true; break; }
-            __nanosleep(20);
-        }
-        Acc<T> sum;
+                if (lane + 32u * q < G) want |= 1u << q;
+            long long spins = 0;
+            while (!fail) {
 #pragma unroll
-        for (int q = 0; q < kMaxGridPcg / 32; ++q)
-            if (want >> q & 1u) sum.add(Acc<T>::from_bits(w[q]));
+                for (int q = 0; q < kMaxGridPcg / 32; ++q)
+                    if ((want & ~ready) >> q & 1u) {
+                        unsigned long long w[4];
+                        ld_slot(&buf[lane + 32 * q], w);
+                        bool ok = true;
 #pragma unroll
-        for (int o = 16; o; o >>= 1) sum.add(sum.shfl_xor(0xffffffffu, o, 32));
-        fail = __any_sync(0xffffffffu, fail);
-        if (lane == 0) {
-            s_tot[wi] = sum.bits();
-            s_wfail[wi] = fail ? 1 : 0;
-        }
-        asm volatile("bar.sync 1, %0;" ::"r"(32 * N) : "memory");
-        if (threadIdx.x == 0) {
-            Acc<T> tot[N];
-            bool any = false;
+                        for (int i = 0; i < N; ++i) ok &= bits_tag<T>(w[i]) == t;
+                        if (ok) {
+#pragma unroll
+                            for (int i = 0; i < N; ++i) s_w[lane + 32 * q][i] = w[i];
+                            ready |= 1u << q;
+                        }
+                    }
+                if (__all_sync(0xffffffffu, ready == want)) break;
+                if (++spins > kBarrierSpins) { fail = true; break; }
+                __nanosleep(20);
+            }
+            fail = __any_sync(0xffffffffu, fail);
+            __syncwarp();
+            Acc<T> sum[N];
+#pragma unroll
+            for (int q = 0; q < kMaxGridPcg / 32; ++q)
+                if (want >> q & 1u)
+#pragma unroll
+                    for (int i = 0; i < N; ++i) sum[i].add(Acc<T>::from_bits(s_w[lane + 32 * q][i]));
 #pragma unroll
             for (int i = 0; i < N; ++i) {
-                tot[i] = Acc<T>::from_bits(s_tot[i]);
-                any |= s_wfail[i] != 0;
+#pragma unroll
+                for (int o = 16; o; o >>= 1) sum[i].add(sum[i].shfl_xor(0xffffffffu, o, 32));
+                tw[i] = tag_bits<T>(sum[i].bits(), t);
             }
-            s_fail = any ? 1 : 0;
-            if (any) atomicOr(&ds->err, ERR_BARRIER);
-            else fin(tot);
+            if (lane == 0 && !fail)
+#pragma unroll
+                for (int i = 0; i < N; ++i) st_relaxed_u64(&tot->v[i], tw[i]);
+        } else if (lane == 0) {
+            long long spins = 0;
+            while (!fail) {
+                ld_slot(tot, tw);
+                bool ok = true;
+#pragma unroll
+                for (int i = 0; i < N; ++i) ok &= bits_tag<T>(tw[i]) == t;
+                if (ok) break;
+                if (++spins > kBarrierSpins) { fail = true; break; }
+                __nanosleep(20);
+            }
+        }
+        if (lane == 0) {
+            s_fail = fail ? 1 : 0;
+            if (fail) atomicOr(&ds->err, ERR_BARRIER);
+            else {
+                Acc<T> tt[N];
+#pragma unroll
+                for (int i = 0; i < N; ++i) tt[i] = Acc<T>::from_bits(tw[i]);
+                fin(tt);
+            }
         }
     }
     __syncthreads();
@@ -857,9 +901,10 @@ __global__ void __launch_bounds__(kPcgThreads) k_pcg_resident(PcgArgs<T> a, int 
     const auto vec_size = [](int rows, int per_row) {
         return ((size_t)rows * per_row * sizeof(T) + (size_t)(rows + 1) * sizeof(int) + 15) / 16 * 16;
     };
-    if (TTIE_BAD(ds, row0 >= 0 && v.nrow >= 0 && row0 + v.nrow <= nr && vec_size(v.nrow, 15) <= (size_t)smem_bytes, 45,
-                 v.nrow))
+    if (!(row0 >= 0 && v.nrow >= 0 && row0 + v.nrow <= nr && vec_size(v.nrow, 15) <= (size_t)smem_bytes)) {
+        partition_fail(ds, 45);   // checked in every build: the rows index shared memory
         v.nrow = 0;
+    }
     const int R = v.nrow;
     // lean: x and the inverse diagonal blocks (read or written once per row and iteration) stay
     // in global memory so that larger row ranges fit
@@ -1212,7 +1257,7 @@ cudaError_t pcg_solve(Ctx &c, const T *rhs, T *out, double rtol, int max_it) {
     TTIE_CUDA_TRY(ensure(c, c.pcg_z4, (size_t)(nr > 0 ? nr : 1) * sizeof(vec4_t<T>)));
     TTIE_CUDA_TRY(ensure(c, c.partials, (size_t)kNumSMs * 16 * 4 * sizeof(double)));
     // reduction slots, then the resident kernel's row partition
-    TTIE_CUDA_TRY(ensure(c, c.pcg_sync, (size_t)kMaxGridPcg * 2 * sizeof(RedSlot) + (kMaxGridPcg + 1) * sizeof(int)));
+    TTIE_CUDA_TRY(ensure(c, c.pcg_sync, (2 * (size_t)kMaxGridPcg + 2) * sizeof(RedSlot) + (kMaxGridPcg + 1) * sizeof(int)));
     const int sms = c.num_sms > 0 ? c.num_sms : kNumSMs;
     // one block per SM at most: fewer participants in every reduction
     int64_t blocks = (nr * kLanesPerRow + kPcgThreads - 1) / kPcgThreads;
@@ -1225,7 +1270,7 @@ cudaError_t pcg_solve(Ctx &c, const T *rhs, T *out, double rtol, int max_it) {
     const int64_t r_cap = ((int64_t)kResidentSmem - 4 - 15) / (15 * (int64_t)sizeof(T) + 4);
     const bool resident = (nr + blocks - 1) / blocks <= r_cap;
     RedSlot *slots = (RedSlot *)c.pcg_sync.p;
-    int *rpart = (int *)(slots + 2 * kMaxGridPcg);
+    int *rpart = (int *)(slots + 2 * kMaxGridPcg + 2);
     double *part = (double *)c.partials.p;
     const unsigned g = grid_for(nr, kThreads, kNumSMs * 4);
     TTIE_CUDA_TRY(cudaMemsetAsync(&c.ds->bar_count, 0, 2 * sizeof(unsigned int), c.stream));
@@ -1233,7 +1278,7 @@ cudaError_t pcg_solve(Ctx &c, const T *rhs, T *out, double rtol, int max_it) {
                                                  (const T *)c.bsr_val.p, c.prm.mu_rel, (T *)c.dinv.p, rhs, out,
                                                  (T *)c.pcg_r.p, (T *)c.pcg_z.p, (T *)c.pcg_p.p, part,
                                                  (vec4_t<T> *)c.pcg_z4.p, (unsigned long long *)slots,
-                                                 (int)(2 * kMaxGridPcg * sizeof(RedSlot) / sizeof(unsigned long long)),
+                                                 (int)((2 * kMaxGridPcg + 2) * sizeof(RedSlot) / sizeof(unsigned long long)),
                                                  resident ? rpart : nullptr, (int)blocks, (int)r_cap, kRowWeight, c.ds);
     TTIE_CUDA_TRY(cudaGetLastError());
     PcgArgs<T> args;
