@@ -22,6 +22,10 @@ Parity status of each function:
                              residual; the Newton trajectory itself is
                              parity-unpinned (only the certified end state is
                              compared)
+  elastic.*                  pinned: spring closed forms, central finite
+                             differences, projected-spectrum closed form,
+                             invariances (the elastic model is a reading: the
+                             paper does not state it)
 """
 from .ttie_oracle import (build_oracle, candidate_pairs, partners_of, evaluate,  # noqa: F401
                           eval_pairs_f64, filtered_sides, gradient, hessian_parts,
@@ -30,3 +34,6 @@ from .ttie_oracle import (build_oracle, candidate_pairs, partners_of, evaluate, 
                           newton_direction, newton_solve, certify, energy,
                           NewtonParams, PairEval)
 from . import exact  # noqa: F401
+from .elastic import (Elastic, mesh_edges, springs_at_rest, elastic_energy, elastic_gradient,  # noqa: F401,E402
+                      spring_hessian, elastic_blocks, elastic_vertices, total_energy,
+                      newton_direction_elastic, quasi_static_solve)

@@ -506,3 +506,121 @@ def test_energy_jumps_at_vertex_face_contact():
         T[eps] = float(ev.T[0])
     assert T[1e-9] == 0.0 and T[0.0] == 0.0
     assert T[-1e-9] > 1.0 and T[-1e-6] == pytest.approx(T[-1e-9], rel=1e-5)
+
+
+# ----------------------------------------------------------------- elastic term (quasi-static simulation)
+def _spring_case(seed=8, anchors=True):
+    m = ti.cloth(6, seed=seed, shear=0.0)
+    rng = np.random.default_rng(seed)
+    el = O.springs_at_rest(m.x, m.tri, k_edge=2.5)
+    x = m.x + 0.05 * rng.standard_normal(m.x.shape)
+    if anchors:
+        el.anchors = np.array([0, 5, 17])
+        el.targets = m.x[el.anchors] + 0.1 * rng.standard_normal((3, 3))
+        el.k_anchor = 0.7
+    return m, el, x
+
+
+def test_spring_closed_form():
+    k, L, dl = 3.0, 0.4, 0.05
+    x = np.array([[0.0, 0.0, 0.0], [L + dl, 0.0, 0.0]])
+    el = O.Elastic(np.array([[0, 1]]), np.array([L]), k)
+    assert O.elastic_energy(x, el) == pytest.approx(0.5 * k * dl * dl, rel=1e-13)
+    g = O.elastic_gradient(x, el)
+    assert np.allclose(g, [[-k * dl, 0, 0], [k * dl, 0, 0]], rtol=1e-13, atol=1e-15)
+    x[1, 0] = L
+    assert O.elastic_energy(x, el) == 0.0 and not O.elastic_gradient(x, el).any()
+    # an anchor: k_a/2 |x - t|^2
+    el = O.Elastic(np.zeros((0, 2), np.int64), np.zeros(0), 0.0, np.array([1]), np.array([[0.0, 0.3, 0.4]]), 2.0)
+    assert O.elastic_energy(x, el) == pytest.approx(0.5 * 2.0 * (L * L + 0.25), rel=1e-13)
+    assert np.allclose(O.elastic_gradient(x, el)[1], 2.0 * (x[1] - [0.0, 0.3, 0.4]))
+
+
+def test_elastic_gradient_central_differences():
+    m, el, x = _spring_case()
+    g = O.elastic_gradient(x, el)
+    h = 1e-6
+    rng = np.random.default_rng(1)
+    for v in rng.choice(m.V, 12, replace=False):
+        for a in range(3):
+            xp, xm = x.copy(), x.copy()
+            xp[v, a] += h
+            xm[v, a] -= h
+            fd = (O.elastic_energy(xp, el) - O.elastic_energy(xm, el)) / (2 * h)
+            assert fd == pytest.approx(g[v, a], rel=1e-6, abs=1e-9)
+
+
+@pytest.mark.parametrize("stretch", [1.3, 0.6])
+def test_spring_hessian_central_differences(stretch):
+    rng = np.random.default_rng(2)
+    xi, n = rng.standard_normal(3), rng.standard_normal(3)
+    L, k = 0.8, 1.7
+    xj = xi + stretch * L * n / np.linalg.norm(n)
+    el = O.Elastic(np.array([[0, 1]]), np.array([L]), k)
+    x = np.stack([xi, xj])
+    H = O.spring_hessian(xi, xj, L, k)
+    h = 1e-6
+    fd = np.zeros((6, 6))
+    for c in range(6):
+        xp, xm = x.copy(), x.copy()
+        xp.ravel()[c] += h
+        xm.ravel()[c] -= h
+        fd[:, c] = (O.elastic_gradient(xp, el) - O.elastic_gradient(xm, el)).ravel() / (2 * h)
+    assert np.allclose(H, fd, rtol=1e-6, atol=1e-7 * k)
+
+
+@pytest.mark.parametrize("stretch", [1.3, 0.6])
+def test_projected_spring_spectrum(stretch):
+    """[[K,-K],[-K,K]] has twice K's eigenvalues and three zeros; K has k along the spring and
+    k (1 - L/l) twice across it, so the projection keeps 2k and 2k max(0, 1 - L/l) (twice)."""
+    rng = np.random.default_rng(3)
+    xi, n = rng.standard_normal(3), rng.standard_normal(3)
+    L, k = 0.8, 1.7
+    xj = xi + stretch * L * n / np.linalg.norm(n)
+    w = np.sort(np.linalg.eigvalsh(O.clamp_psd(O.spring_hessian(xi, xj, L, k)[None])[0]))
+    t = 2 * k * max(0.0, 1 - 1 / stretch)
+    assert np.allclose(w, np.sort([2 * k, t, t, 0, 0, 0]), atol=1e-12 * k)
+
+
+def test_elastic_invariances():
+    m, el, x = _spring_case(anchors=False)
+    E = O.elastic_energy(x, el)
+    assert O.elastic_energy(x + np.array([0.3, -1.0, 2.0]), el) == pytest.approx(E, rel=1e-12)
+    R = ti.random_rotation(np.random.default_rng(4))
+    assert O.elastic_energy(x @ R.T, el) == pytest.approx(E, rel=1e-12)
+    assert np.abs(O.elastic_gradient(x, el).sum(axis=0)).max() <= 1e-12 * np.abs(O.elastic_gradient(x, el)).max()
+
+
+def test_elastic_blocks_quadratic_form():
+    """With every spring stretched the projection changes nothing, so v.Hv is the second central
+    difference of E_el along v; the scatter into vertex blocks is checked by that alone."""
+    m, el, x = _spring_case()
+    x = m.x * 1.2   # every spring stretched by 20 %
+    M = O.blocks_to_dense(O.elastic_blocks(x, el), np.arange(m.V))
+    v = np.random.default_rng(5).standard_normal(x.shape)
+    h = 1e-4
+    d2 = (O.elastic_energy(x + h * v, el) - 2 * O.elastic_energy(x, el) + O.elastic_energy(x - h * v, el)) / (h * h)
+    # E_el is a polynomial of degree 2 in l: fourth-order terms of the difference stay below 1e-6
+    assert v.ravel() @ M @ v.ravel() == pytest.approx(d2, rel=1e-6)
+    assert np.linalg.eigvalsh(O.blocks_to_dense(O.elastic_blocks(_spring_case()[2], el), np.arange(m.V))).min() >= -1e-10
+
+
+def test_newton_direction_elastic_solves_system():
+    m = ti.cloth(12, seed=21)
+    prm = O.NewtonParams()
+    el = O.springs_at_rest(m.x, m.tri, k_edge=1e-3)
+    E, n, grad, d, rows = O.newton_direction_elastic(m.x, m.tri, None, prm, el)
+    assert n > 0
+    pairs = O.candidate_pairs(m.x, m.tri)
+    ev = O.evaluate(m.x, m.tri, pairs)
+    assert E == pytest.approx(float(ev.T.sum()), rel=1e-14)        # springs at rest add nothing
+    g0, blocks = O.assemble(m.tri, ev, m.V)
+    assert np.array_equal(grad, g0)
+    assert len(rows) == m.V                                          # every vertex has a spring
+    for key, b in O.elastic_blocks(m.x, el).items():
+        blocks[key] = blocks[key] + b if key in blocks else b
+    H = O.blocks_to_dense(blocks, rows)
+    mu = prm.mu_rel * np.mean(np.diag(H))
+    r = (H + mu * np.eye(len(H))) @ d[rows].ravel() + grad[rows].ravel()
+    assert np.linalg.norm(r) <= 1e-9 * np.linalg.norm(grad)
+    assert np.sum(grad * d) < 0

@@ -118,6 +118,14 @@ def octasphere(level: int, radius: float = 1.0) -> Mesh:
     return Mesh(x, tri, np.zeros(tri.shape[0], np.int32))
 
 
+def edge_list(tri: np.ndarray) -> np.ndarray:
+    """[E,2] int32 undirected edges (i < j) of a triangle mesh, each once, sorted (topology for
+    the springs of the quasi-static simulation's workloads)."""
+    e = np.concatenate([tri[:, [0, 1]], tri[:, [1, 2]], tri[:, [2, 0]]]).astype(np.int64)
+    e.sort(axis=1)
+    return np.unique(e, axis=0).astype(np.int32)
+
+
 # ---------------------------------------------------------------- grids
 def grid_sheet(n: int):
     """n x n vertex grid on [0,1]^2, every quad split along the same diagonal: F = 2(n-1)^2."""
