@@ -230,7 +230,43 @@ typedef struct {
     float ms_pcg_kernel;         /* persistent PCG kernel (profile)                          */
     int64_t pcg_block_iters;     /* sum over the PCG iterations of the 3x3 blocks multiplied */
     int64_t pcg_row_iters;       /* sum over the PCG iterations of the rows updated           */
+    double energy_elastic;       /* elastic term's part of energy (0 without one)             */
 } ttie_step_info;
+
+/*
+ * Elastic term of the quasi-static simulation (Fig. 2: a simulation with the energy that
+ * evolves from an invalid state to a valid one; the paper does not state its elastic model,
+ * so this is a mass-spring term):
+ *   E_el(x) = sum_e k_edge/2 (|x_i - x_j| - rest_e)^2 + sum_a k_anchor/2 |x_a - target_a|^2.
+ * Once set, ttie_newton_step and ttie_solve minimise E_el + sum T: the gradient and the
+ * PSD-projected Hessian of both terms are assembled into one block-CSR system whose rows are
+ * the vertices of intersecting pairs, springs and anchors (mu from its mean diagonal), and
+ * the line search tests E_el + sum T.  A step at a state with no intersecting pair does
+ * nothing (the state is valid), so ttie_solve stops there as without the term.
+ * ttie_eval_pairs and ttie_assemble stay the pairs' alone.  Not with batched instances
+ * (pair_mode TTIE_PAIRS_INTRA_GROUP over an LBVH).
+ */
+typedef struct {
+    const int32_t *edges;        /* device, n_edges x 2 vertex ids, distinct, each in [0, V) */
+    const void *rest;            /* device, n_edges rest lengths, float or double as the
+                                    context's precision                                    */
+    int64_t n_edges;
+    double k_edge;               /* spring stiffness, >= 0                                  */
+    const int32_t *anchors;      /* device, n_anchors vertex ids in [0, V); NULL if none    */
+    const void *targets;         /* device, n_anchors x 3 anchor points (context precision) */
+    int64_t n_anchors;
+    double k_anchor;             /* anchor stiffness, >= 0                                  */
+} ttie_elastic;
+
+/*
+ * Sets (or, with el NULL or no springs and no anchors, removes) the elastic term for the mesh
+ * of the last ttie_build_bvh.  The arrays are copied into the context during the call (stream
+ * ordered), so the caller's buffers may be reused after it.  Errors: STATE (no mesh built),
+ * INVALID (negative counts or stiffness, null arrays with nonzero counts, a vertex id out of
+ * range or a spring with equal endpoints, batched-instance mode), OOM, CUDA.  A later
+ * ttie_build_bvh with another vertex count removes the term.
+ */
+ttie_status ttie_set_elastic(ttie_ctx *ctx, const ttie_elastic *el);
 
 /*
  * One inexact Newton iteration on the mesh recorded by ttie_build_bvh:

@@ -201,6 +201,131 @@ __global__ void k_block_keys(const int4 *__restrict__ tri4, const int2 *__restri
     }
 }
 
+// ---------------------------------------------------------------- elastic term
+// The quasi-static simulation of Fig. 2 adds an elastic term to sum T; the paper does not
+// state its model, so it is a mass-spring term here: springs k/2 (|x_i - x_j| - L)^2 and
+// anchors k_a/2 |x_v - t_v|^2.  Per spring, with l = |x_i - x_j| and n = (x_i - x_j)/l: the
+// gradient is k (l - L) n on i (minus that on j) and the Hessian [[K, -K], [-K, K]] with
+// K = k (n n' + (1 - L/l)(I - n n')).  Its spectrum is twice K's (k along n, k (1 - L/l)
+// twice across n) and three zeros, so the PSD projection only clamps 1 - L/l at 0:
+// K+ = k (c I + (1 - c) n n'), c = max(0, 1 - L/l).  At l = 0: K+ = k I, gradient 0.  An
+// anchor adds k_a I and k_a (x_v - t_v).  In the assembly a spring contributes four block
+// entries (+K+ on (i,i) and (j,j), -K+ on (i,j) and (j,i)) and an anchor one, after the
+// pairs' 36 per pair, so the same sort and segmented sums merge both patterns.
+constexpr int kElStride = 12;   // per spring: K+ (9, row-major), gradient on i (3)
+
+// Energy of the term at x (and, with sfac, each spring's K+ and gradient, each anchor's
+// gradient, and the term's trace added to ds->trace).
+template <typename T>
+__global__ void k_el_factors(const vec4_t<T> *__restrict__ x, const int2 *__restrict__ edges,
+                             const T *__restrict__ rest, int64_t n_edges, T k, const int32_t *__restrict__ anchors,
+                             const T *__restrict__ targets, int64_t n_anchors, T ka, T *__restrict__ sfac,
+                             T *__restrict__ afac, double *partials, DevScalars *ds) {
+    double en = 0.0, tr = 0.0;
+    const int64_t n = n_edges + n_anchors;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        if (i < n_edges) {
+            const int2 e = edges[i];
+            const vec4_t<T> xi = x[e.x], xj = x[e.y];
+            const T d[3] = {xi.x - xj.x, xi.y - xj.y, xi.z - xj.z};
+            const T l = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+            const T L = rest[i];
+            en += 0.5 * (double)k * ((double)l - (double)L) * ((double)l - (double)L);
+            if (sfac) {
+                T *o = sfac + (size_t)i * kElStride;
+                if (l > T(0)) {
+                    const T nv[3] = {d[0] / l, d[1] / l, d[2] / l};
+                    const T c = max(T(0), T(1) - L / l);
+#pragma unroll
+                    for (int r = 0; r < 3; ++r) {
+#pragma unroll
+                        for (int q = 0; q < 3; ++q) o[3 * r + q] = k * ((r == q ? c : T(0)) + (T(1) - c) * nv[r] * nv[q]);
+                        o[9 + r] = k * (l - L) * nv[r];
+                    }
+                    tr += 2.0 * (double)k * (1.0 + 2.0 * (double)c);
+                } else {
+#pragma unroll
+                    for (int r = 0; r < 9; ++r) o[r] = (r % 4 == 0) ? k : T(0);
+                    o[9] = o[10] = o[11] = T(0);
+                    tr += 6.0 * (double)k;
+                }
+            }
+        } else {
+            const int64_t a = i - n_edges;
+            const vec4_t<T> xv = x[anchors[a]];
+            const T d[3] = {xv.x - targets[3 * a], xv.y - targets[3 * a + 1], xv.z - targets[3 * a + 2]};
+            en += 0.5 * (double)ka * ((double)d[0] * d[0] + (double)d[1] * d[1] + (double)d[2] * d[2]);
+            if (sfac) {
+#pragma unroll
+                for (int r = 0; r < 3; ++r) afac[3 * a + r] = ka * d[r];
+                tr += 3.0 * (double)ka;
+            }
+        }
+    }
+    double v[2] = {en, tr};
+    const bool with_trace = sfac != nullptr;
+    grid_sums<2>(v, partials, &ds->done_counter[6], [&](const double *tot) {
+        ds->el_energy = tot[0];
+        if (with_trace) ds->trace += tot[1];
+    });
+}
+
+// Vertices of springs and anchors are rows of the system.
+__global__ void k_el_mark(const int2 *__restrict__ edges, int64_t n_edges, const int32_t *__restrict__ anchors,
+                          int64_t n_anchors, uint32_t *__restrict__ vflag) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_edges + n_anchors;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        if (i < n_edges) {
+            const int2 e = edges[i];
+            vflag[e.x] = 1;
+            vflag[e.y] = 1;
+        } else {
+            vflag[anchors[i - n_edges]] = 1;
+        }
+    }
+}
+
+// Block entries of springs (4 each) and anchors (1 each) at base + ..., values index themselves.
+__global__ void k_el_keys(const int2 *__restrict__ edges, int64_t n_edges, const int32_t *__restrict__ anchors,
+                          int64_t n_anchors, const unsigned long long *__restrict__ vrow, const DevScalars *ds,
+                          unsigned long long base, unsigned long long *__restrict__ key, uint32_t *__restrict__ val) {
+    const unsigned long long nr = ds->n_rows;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_edges + n_anchors;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        if (i < n_edges) {
+            const int2 e = edges[i];
+            const unsigned long long ri = vrow[e.x], rj = vrow[e.y], o = base + 4 * (unsigned long long)i;
+            key[o] = ri * nr + ri;
+            key[o + 1] = ri * nr + rj;
+            key[o + 2] = rj * nr + ri;
+            key[o + 3] = rj * nr + rj;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) val[o + q] = (uint32_t)(o + q);
+        } else {
+            const unsigned long long r = vrow[anchors[i - n_edges]], o = base + 4 * (unsigned long long)n_edges + (i - n_edges);
+            key[o] = r * nr + r;
+            val[o] = (uint32_t)o;
+        }
+    }
+}
+
+// Spring endpoints distinct and in [0, V), anchors in [0, V).
+__global__ void k_el_check(const int2 *__restrict__ edges, int64_t n_edges, const int32_t *__restrict__ anchors,
+                           int64_t n_anchors, int64_t V, DevScalars *ds) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_edges + n_anchors;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        bool ok;
+        if (i < n_edges) {
+            const int2 e = edges[i];
+            ok = e.x >= 0 && e.x < V && e.y >= 0 && e.y < V && e.x != e.y;
+        } else {
+            const int a = anchors[i - n_edges];
+            ok = a >= 0 && a < V;
+        }
+        if (!ok) atomicOr(&ds->err, ERR_BAD_INDEX);
+    }
+}
+
 __global__ void k_run_flags(const unsigned long long *__restrict__ key, int64_t n, uint32_t *__restrict__ flag) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         flag[i] = (i == 0 || key[i] != key[i - 1]) ? 1u : 0u;
@@ -223,12 +348,13 @@ __global__ void k_block_values(const unsigned long long *__restrict__ key, const
                                const uint32_t *__restrict__ run_start, const T *__restrict__ z, const DevScalars *ds,
                                int32_t *__restrict__ row_ptr, int32_t *__restrict__ col_idx, T *__restrict__ bval,
                                T *__restrict__ grad_rows, const int32_t *__restrict__ row_vertex,
-                               T *__restrict__ grad_full) {
-    const unsigned long long nb = ds->nnzb, nr = ds->n_rows;
+                               T *__restrict__ grad_full, unsigned long long n_entries, const T *__restrict__ sfac,
+                               int64_t n_springs, const T *__restrict__ afac, T ka) {
+    const unsigned long long nb = ds->nnzb, nr = ds->n_rows, n_pair = ds->n_active * 36;
     for (unsigned long long bi = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; bi < nb;
          bi += (unsigned long long)gridDim.x * blockDim.x) {
         const uint32_t s = run_start[bi], e = run_start[bi + 1];
-        if (TTIE_BAD((DevScalars *)ds, s < e && e <= ds->n_active * 36, 21, ((long long)s << 32) | e)) continue;
+        if (TTIE_BAD((DevScalars *)ds, s < e && e <= n_entries, 21, ((long long)s << 32) | e)) continue;
         const unsigned long long kk = key[s];
         const unsigned long long row = kk / nr, col = kk - row * nr;
         if (TTIE_BAD((DevScalars *)ds, row < nr, 22, row)) continue;
@@ -241,6 +367,25 @@ __global__ void k_block_values(const unsigned long long *__restrict__ key, const
         T g0 = 0, g1 = 0, g2 = 0;
         for (uint32_t i = s; i < e; ++i) {
             const uint32_t v = val[i];
+            if (v >= n_pair) {   // elastic entries
+                const unsigned long long w = v - n_pair;
+                if (w < 4ull * (unsigned long long)n_springs) {
+                    const unsigned long long sp = w / 4, q = w - sp * 4;
+                    const T *K = sfac + sp * kElStride;
+                    const T sg = (q == 0 || q == 3) ? T(1) : T(-1);
+#pragma unroll
+                    for (int t = 0; t < 9; ++t) m[t] += sg * K[t];
+                    if (row == col) {   // (i, i): the gradient on i; (j, j): on j, its negative
+                        const T gs = q == 0 ? T(1) : T(-1);
+                        g0 += gs * K[9]; g1 += gs * K[10]; g2 += gs * K[11];
+                    }
+                } else {
+                    const unsigned long long a = w - 4ull * (unsigned long long)n_springs;
+                    m[0] += ka; m[4] += ka; m[8] += ka;
+                    if (row == col) { g0 += afac[3 * a]; g1 += afac[3 * a + 1]; g2 += afac[3 * a + 2]; }
+                }
+                continue;
+            }
             const uint32_t pk = v / 36, rc = v - pk * 36, r = rc / 6, c = rc - r * 6;
             if (TTIE_BAD((DevScalars *)ds, pk < ds->n_active, 23, pk)) continue;
             const T *zp = z + (size_t)pk * kZStride;
@@ -1171,9 +1316,11 @@ int bits_for(unsigned long long v) {
 }  // namespace
 
 template <typename T>
-cudaError_t assemble_system(Ctx &c, T *grad_full) {
+cudaError_t assemble_system(Ctx &c, T *grad_full, bool with_elastic) {
     const int64_t n_act = c.n_active;
     const int64_t V = c.V;
+    const bool el = with_elastic && c.have_elastic;
+    const int64_t n_springs = el ? c.el_n_edges : 0, n_anchors = el ? c.el_n_anchors : 0;
     TTIE_CUDA_TRY(ensure(c, c.vflag, (size_t)V * 4));
     TTIE_CUDA_TRY(ensure(c, c.vrow, (size_t)(V + 1) * 8));
     TTIE_CUDA_TRY(cudaMemsetAsync(c.vflag.p, 0, (size_t)V * 4, c.stream));
@@ -1182,6 +1329,9 @@ cudaError_t assemble_system(Ctx &c, T *grad_full) {
     const uint32_t *active = (const uint32_t *)c.active.p;
     const unsigned gA = grid_for(n_act, kThreads);
     launch(c, k_mark_vertices, dim3(gA), dim3(kThreads), tri4, pairs, active, c.ds, (uint32_t *)c.vflag.p);
+    if (el)
+        launch(c, k_el_mark, dim3(grid_for(n_springs + n_anchors, kThreads)), dim3(kThreads), (const int2 *)c.el_edges.p,
+               n_springs, (const int32_t *)c.el_anchor.p, n_anchors, (uint32_t *)c.vflag.p);
     TTIE_CUDA_TRY(scan_u32_u64(c, (const uint32_t *)c.vflag.p, (unsigned long long *)c.vrow.p, V));
     TTIE_CUDA_TRY(ensure(c, c.row_vertex, (size_t)(V > 0 ? V : 1) * 4));
     launch(c, k_row_vertex, dim3(grid_for(V, kThreads)), dim3(kThreads), (const uint32_t *)c.vflag.p,
@@ -1191,7 +1341,16 @@ cudaError_t assemble_system(Ctx &c, T *grad_full) {
     TTIE_CUDA_TRY(ensure(c, c.partials, (size_t)kNumSMs * 16 * 4 * sizeof(double)));
     launch(c, k_factors<T>, dim3(grid_for(n_act, 128, kNumSMs * 8)), dim3(128), (const T *)c.fac.p, c.prm.psd_mode,
                                                                         (T *)c.zfac.p, (double *)c.partials.p, c.ds);
-    const int64_t nk = n_act * 36;
+    if (el) {   // after k_factors: adds the term's trace to the pairs'
+        TTIE_CUDA_TRY(ensure(c, c.el_sfac, (size_t)(n_springs > 0 ? n_springs : 1) * kElStride * sizeof(T)));
+        TTIE_CUDA_TRY(ensure(c, c.el_afac, (size_t)(n_anchors > 0 ? n_anchors : 1) * 3 * sizeof(T)));
+        launch(c, k_el_factors<T>, dim3(grid_for(n_springs + n_anchors, kThreads, kNumSMs * 4)), dim3(kThreads),
+               (const vec4_t<T> *)c.xp.p, (const int2 *)c.el_edges.p, (const T *)c.el_rest.p, n_springs, (T)c.el_k,
+               (const int32_t *)c.el_anchor.p, (const T *)c.el_target.p, n_anchors, (T)c.el_ka, (T *)c.el_sfac.p,
+               (T *)c.el_afac.p, (double *)c.partials.p, c.ds);
+    }
+    const int64_t nk = n_act * 36 + 4 * n_springs + n_anchors;
+    if (nk >= (int64_t)UINT32_MAX) return cudaErrorInvalidValue;   // entry indices are 32-bit
     TTIE_CUDA_TRY(ensure(c, c.bkey, (size_t)(nk > 0 ? nk : 1) * 8));
     TTIE_CUDA_TRY(ensure(c, c.bkey2, (size_t)(nk > 0 ? nk : 1) * 8));
     TTIE_CUDA_TRY(ensure(c, c.bval, (size_t)(nk > 0 ? nk : 1) * 4));
@@ -1205,6 +1364,10 @@ cudaError_t assemble_system(Ctx &c, T *grad_full) {
     c.n_rows = nr;
     launch(c, k_block_keys, dim3(gA), dim3(kThreads), tri4, pairs, active, (const unsigned long long *)c.vrow.p, c.ds,
                                                 (unsigned long long *)c.bkey.p, (uint32_t *)c.bval.p);
+    if (el)
+        launch(c, k_el_keys, dim3(grid_for(n_springs + n_anchors, kThreads)), dim3(kThreads), (const int2 *)c.el_edges.p,
+               n_springs, (const int32_t *)c.el_anchor.p, n_anchors, (const unsigned long long *)c.vrow.p, c.ds,
+               (unsigned long long)n_act * 36, (unsigned long long *)c.bkey.p, (uint32_t *)c.bval.p);
     TTIE_CUDA_TRY(cudaGetLastError());
     const int kbits = bits_for((unsigned long long)nr * (unsigned long long)nr);
     TTIE_CUDA_TRY(radix_sort(c, (unsigned long long *)c.bkey.p, (uint32_t *)c.bval.p, (unsigned long long *)c.bkey2.p,
@@ -1240,11 +1403,49 @@ cudaError_t assemble_system(Ctx &c, T *grad_full) {
     launch(c, k_block_values<T>, dim3(grid_for(nnzb, 128, kNumSMs * 16)), dim3(128), 
         (const unsigned long long *)c.bkey.p, (const uint32_t *)c.bval.p, (const uint32_t *)c.run_start.p,
         (const T *)c.zfac.p, c.ds, (int32_t *)c.row_ptr.p, (int32_t *)c.col_idx.p, (T *)c.bsr_val.p, (T *)c.rhs.p,
-        (const int32_t *)c.row_vertex.p, grad_full);
+        (const int32_t *)c.row_vertex.p, grad_full, (unsigned long long)nk, (const T *)c.el_sfac.p, n_springs,
+        (const T *)c.el_afac.p, (T)c.el_ka);
     return cudaGetLastError();
 }
-template cudaError_t assemble_system<float>(Ctx &, float *);
-template cudaError_t assemble_system<double>(Ctx &, double *);
+template cudaError_t assemble_system<float>(Ctx &, float *, bool);
+template cudaError_t assemble_system<double>(Ctx &, double *, bool);
+
+// Energy of the elastic term at x into ds->el_energy.
+template <typename T> cudaError_t elastic_energy(Ctx &c, const vec4_t<T> *x) {
+    const int64_t n = c.el_n_edges + c.el_n_anchors;
+    TTIE_CUDA_TRY(ensure(c, c.partials, (size_t)kNumSMs * 16 * 4 * sizeof(double)));
+    launch(c, k_el_factors<T>, dim3(grid_for(n, kThreads, kNumSMs * 4)), dim3(kThreads), x, (const int2 *)c.el_edges.p,
+           (const T *)c.el_rest.p, c.el_n_edges, (T)c.el_k, (const int32_t *)c.el_anchor.p, (const T *)c.el_target.p,
+           c.el_n_anchors, (T)c.el_ka, (T *)nullptr, (T *)nullptr, (double *)c.partials.p, c.ds);
+    return cudaGetLastError();
+}
+template cudaError_t elastic_energy<float>(Ctx &, const float4 *);
+template cudaError_t elastic_energy<double>(Ctx &, const dvec4 *);
+
+// Copies the term's arrays into the context and checks its indices against V (ERR_BAD_INDEX).
+template <typename T> cudaError_t elastic_set(Ctx &c, const ttie_elastic *e) {
+    const int64_t E = e->n_edges, A = e->n_anchors;
+    TTIE_CUDA_TRY(ensure(c, c.el_edges, (size_t)(E > 0 ? E : 1) * sizeof(int2)));
+    TTIE_CUDA_TRY(ensure(c, c.el_rest, (size_t)(E > 0 ? E : 1) * sizeof(T)));
+    TTIE_CUDA_TRY(ensure(c, c.el_anchor, (size_t)(A > 0 ? A : 1) * sizeof(int32_t)));
+    TTIE_CUDA_TRY(ensure(c, c.el_target, (size_t)(A > 0 ? A : 1) * 3 * sizeof(T)));
+    if (E > 0) {
+        TTIE_CUDA_TRY(cudaMemcpyAsync(c.el_edges.p, e->edges, (size_t)E * sizeof(int2), cudaMemcpyDeviceToDevice, c.stream));
+        TTIE_CUDA_TRY(cudaMemcpyAsync(c.el_rest.p, e->rest, (size_t)E * sizeof(T), cudaMemcpyDeviceToDevice, c.stream));
+    }
+    if (A > 0) {
+        TTIE_CUDA_TRY(cudaMemcpyAsync(c.el_anchor.p, e->anchors, (size_t)A * sizeof(int32_t), cudaMemcpyDeviceToDevice,
+                                      c.stream));
+        TTIE_CUDA_TRY(cudaMemcpyAsync(c.el_target.p, e->targets, (size_t)A * 3 * sizeof(T), cudaMemcpyDeviceToDevice,
+                                      c.stream));
+    }
+    if (E + A > 0)
+        launch(c, k_el_check, dim3(grid_for(E + A, kThreads)), dim3(kThreads), (const int2 *)c.el_edges.p, E,
+               (const int32_t *)c.el_anchor.p, A, c.V, c.ds);
+    return cudaGetLastError();
+}
+template cudaError_t elastic_set<float>(Ctx &, const ttie_elastic *);
+template cudaError_t elastic_set<double>(Ctx &, const ttie_elastic *);
 
 template <typename T>
 cudaError_t pcg_solve(Ctx &c, const T *rhs, T *out, double rtol, int max_it) {

@@ -215,7 +215,8 @@ static ttie_status read_err(Ctx &c, const char *where) {
     CK(cudaStreamSynchronize(c.stream), where);
     const int e = c.hs->err;
     if (e) CK(cudaMemsetAsync(&c.ds->err, 0, sizeof(int), c.stream), where);
-    if (e & ERR_BAD_INDEX) return set_err(c, TTIE_ERR_INVALID, "%s: triangle or group index out of range", where);
+    if (e & ERR_BAD_INDEX)
+        return set_err(c, TTIE_ERR_INVALID, "%s: index out of range (triangle, group, spring or anchor)", where);
     if (e & ERR_NONFINITE) return set_err(c, TTIE_ERR_NONFINITE, "%s: non-finite vertex position", where);
     if (e & ERR_STACK)
         return set_err(c, TTIE_ERR_CAPACITY, "%s: broad-phase capacity exceeded (BVH depth or hash cells per triangle)",
@@ -306,13 +307,31 @@ static ttie_status eval_impl(Ctx &c, const T *x, unsigned what, double *energy, 
 }
 
 // Energy and intersecting-pair count at positions xt over the given candidate list.
+// Energy (sum T, plus the elastic term when one is set) and intersecting-pair count at
+// positions xt over the given candidate list.
 template <typename T>
-static ttie_status energy_at(Ctx &c, const vec4_t<T> *xt, const int2 *pairs, int64_t n, double *E, int64_t *n_act) {
+static ttie_status energy_at(Ctx &c, const vec4_t<T> *xt, const int2 *pairs, int64_t n, double *E, int64_t *n_act,
+                             double *E_el = nullptr) {
     CK(eval_candidates<T>(c, xt, pairs, n, TTIE_EVAL_E), "line search");
+    if (c.have_elastic) {
+        CK(elastic_energy<T>(c, xt), "line search: elastic term");
+        CK(cudaMemcpyAsync(&c.hs->el_energy, &c.ds->el_energy, sizeof(double), cudaMemcpyDeviceToHost, c.stream),
+           "line search");
+    }
     CK(cudaMemcpyAsync(&c.hs->energy, &c.ds->energy, sizeof(double), cudaMemcpyDeviceToHost, c.stream), "line search");
     CK(cudaStreamSynchronize(c.stream), "line search");
-    *E = c.hs->energy;
+    const double el = c.have_elastic ? c.hs->el_energy : 0.0;
+    *E = c.hs->energy + el;
+    if (E_el) *E_el = el;
     *n_act = c.n_active;
+    return TTIE_OK;
+}
+
+// The elastic term is usable with the current mesh and precision.
+static ttie_status elastic_ok(Ctx &c, const char *where) {
+    if (!c.have_elastic) return TTIE_OK;
+    if (c.el_prec != c.prm.precision)
+        return set_err(c, TTIE_ERR_STATE, "%s: the elastic term was set for the other precision", where);
     return TTIE_OK;
 }
 
@@ -335,7 +354,15 @@ template <typename T> static ttie_status newton_batched(Ctx &c, T *x, ttie_step_
 
 template <typename T>
 static ttie_status newton_impl(Ctx &c, T *x, ttie_step_info *info) {
-    if (batched(c)) return newton_batched<T>(c, x, info);
+    if (batched(c)) {
+        if (c.have_elastic)
+            return set_err(c, TTIE_ERR_INVALID, "ttie_newton_step: the elastic term is not available with batched instances");
+        return newton_batched<T>(c, x, info);
+    }
+    {
+        const ttie_status se = elastic_ok(c, "ttie_newton_step");
+        if (se != TTIE_OK) return se;
+    }
     ttie_step_info inf;
     std::memset(&inf, 0, sizeof inf);
     c.have_dir = false;
@@ -363,9 +390,15 @@ static ttie_status newton_impl(Ctx &c, T *x, ttie_step_info *info) {
     c.time_kernels = false;
     c.have_eval = true;
     c.eval_what = TTIE_EVAL_E | TTIE_EVAL_H;
+    if (c.have_elastic) {
+        CK(elastic_energy<T>(c, (const vec4_t<T> *)c.xp.p), "newton: elastic term");
+        CK(cudaMemcpyAsync(&c.hs->el_energy, &c.ds->el_energy, sizeof(double), cudaMemcpyDeviceToHost, c.stream),
+           "newton");
+    }
     CK(cudaMemcpyAsync(&c.hs->energy, &c.ds->energy, sizeof(double), cudaMemcpyDeviceToHost, c.stream), "newton");
     CK(cudaStreamSynchronize(c.stream), "newton");
-    const double E = c.hs->energy;
+    inf.energy_elastic = c.have_elastic ? c.hs->el_energy : 0.0;
+    const double E = c.hs->energy + inf.energy_elastic;
     inf.energy = E;
     inf.n_active = c.n_active;
     mark(c, 2);
@@ -380,9 +413,9 @@ static ttie_status newton_impl(Ctx &c, T *x, ttie_step_info *info) {
         if (info) *info = inf;
         return TTIE_OK;
     }
-    // assembly and PCG for (H+ + mu I) d = -g
-    CK(assemble_system<T>(c, nullptr), "newton: assembly");
-    c.have_bsr = true;
+    // assembly (with the elastic term when one is set) and PCG for (H+ + mu I) d = -g
+    CK(assemble_system<T>(c, nullptr, true), "newton: assembly");
+    c.have_bsr = !c.have_elastic;   // ttie_assemble's system is the pairs' alone
     inf.n_rows = c.n_rows;
     inf.nnzb = c.nnzb;
     mark(c, 3);
@@ -667,6 +700,7 @@ ttie_status ttie_build_bvh(ttie_ctx *h, const void *d_x, int64_t V, int x_stride
     const int mode = c.prm.pair_mode & 3;
     if (mode != TTIE_PAIRS_SELF && !d_group)
         return set_err(c, TTIE_ERR_INVALID, "ttie_build_bvh: the group pair modes need d_group");
+    if (c.have_elastic && V != c.el_V) c.have_elastic = false;   // the term was set for another mesh
     c.V = V;
     c.F = F;
     c.x_stride = x_stride;
@@ -770,6 +804,36 @@ ttie_status ttie_pcg(ttie_ctx *h, const void *d_rhs, void *d_out, double rtol, i
     const double rel = c.hs->red[1] > 0.0 ? std::sqrt(c.hs->red[4] / c.hs->red[1]) : 0.0;
     if (rel_residual) *rel_residual = rel;
     if (!std::isfinite(rel)) return set_err(c, TTIE_ERR_NONFINITE, "ttie_pcg: residual is not finite");
+    return TTIE_OK;
+}
+
+ttie_status ttie_set_elastic(ttie_ctx *h, const ttie_elastic *el) {
+    if (!h) return TTIE_ERR_INVALID;
+    Ctx &c = h->c;
+    if (!c.have_mesh) return set_err(c, TTIE_ERR_STATE, "ttie_set_elastic: call ttie_build_bvh first");
+    if (!el || (el->n_edges == 0 && el->n_anchors == 0)) {
+        c.have_elastic = false;
+        return TTIE_OK;
+    }
+    if (el->n_edges < 0 || el->n_anchors < 0 || el->n_edges > (int64_t)INT32_MAX || el->n_anchors > (int64_t)INT32_MAX)
+        return set_err(c, TTIE_ERR_INVALID, "ttie_set_elastic: counts out of range");
+    if (!(el->k_edge >= 0.0) || !(el->k_anchor >= 0.0) || !std::isfinite(el->k_edge) || !std::isfinite(el->k_anchor))
+        return set_err(c, TTIE_ERR_INVALID, "ttie_set_elastic: stiffness must be finite and >= 0");
+    if ((el->n_edges > 0 && (!el->edges || !el->rest)) || (el->n_anchors > 0 && (!el->anchors || !el->targets)))
+        return set_err(c, TTIE_ERR_INVALID, "ttie_set_elastic: null array");
+    if (batched(c))
+        return set_err(c, TTIE_ERR_INVALID, "ttie_set_elastic: the elastic term is not available with batched instances");
+    c.have_elastic = false;
+    CK(c.prm.precision == TTIE_F64 ? elastic_set<double>(c, el) : elastic_set<float>(c, el), "ttie_set_elastic");
+    ttie_status s = read_err(c, "ttie_set_elastic");
+    if (s != TTIE_OK) return s;
+    c.el_n_edges = el->n_edges;
+    c.el_n_anchors = el->n_anchors;
+    c.el_k = el->k_edge;
+    c.el_ka = el->k_anchor;
+    c.el_V = c.V;
+    c.el_prec = c.prm.precision;
+    c.have_elastic = true;
     return TTIE_OK;
 }
 

@@ -97,6 +97,7 @@ struct DevScalars {
     unsigned int n_pending;                // batched line search: instances still open
     double ls_alpha, ls_last;              // batched line search: trial step, 1 on the last trial
     double batch[10];                      // batched step totals (instance_totals)
+    double el_energy;                      // energy of the elastic term at the last evaluation
 };
 
 // ------------------------------------------------------------------ buffers
@@ -116,6 +117,7 @@ cudaError_t ensure(Ctx &c, Buf &b, size_t bytes);   // grow-only, contents not k
     X(bval) X(bval2) X(bflag) X(run_start) X(row_ptr) X(col_idx) X(bsr_val) X(rhs)         \
     X(zfac) X(dinv) X(pcg_x) X(pcg_r) X(pcg_z) X(pcg_p) X(pcg_q) X(dir) X(xt) X(gtmp)      \
     X(xsave) X(sweep_cand) X(pcg_z4) X(hbuf) X(pcg_sync) X(spill) X(pcg_w) X(vgroup) X(iedge)  \
+    X(el_edges) X(el_rest) X(el_anchor) X(el_target) X(el_sfac) X(el_afac)                    \
     X(inst) X(ls_cand) X(inst_acc) X(inst_ids) X(ab) X(ls_flag)  \
     X(ls_off) X(ls_scalars) X(hgrid) X(hkey) X(hkey2) X(hval) X(hval2) X(hcnt) X(hoff)
 
@@ -156,6 +158,11 @@ struct Ctx {
     bool time_kernels = false;         // profile: events around the classification / PCG kernels
     int64_t tree_leaves = -1;          // leaves of the hierarchy in the BVH buffers (-1: none)
     int inst_tuned[4] = {0, 0, 0, 0};  // batched PCG: block size chosen per size bucket (0: not yet)
+    // elastic term of the quasi-static simulation (ttie_set_elastic)
+    bool have_elastic = false;
+    int64_t el_n_edges = 0, el_n_anchors = 0, el_V = -1;
+    int el_prec = 0;
+    double el_k = 0.0, el_ka = 0.0;
 };
 
 // Every kernel of the library is launched through this helper on the context's
@@ -245,7 +252,10 @@ cudaError_t energy_eval_nosync(Ctx &c, const vec4_t<T> *x, const int2 *pairs, in
                                const unsigned long long *d_n);
 
 // ------------------------------------------------------------------ assembly / solve (assemble.cu)
-template <typename T> cudaError_t assemble_system(Ctx &c, T *grad_out_V3);
+// with_elastic: the elastic term (ttie_set_elastic) is added to the pairs' system
+template <typename T> cudaError_t assemble_system(Ctx &c, T *grad_out_V3, bool with_elastic = false);
+template <typename T> cudaError_t elastic_energy(Ctx &c, const vec4_t<T> *x);   // -> ds->el_energy
+template <typename T> cudaError_t elastic_set(Ctx &c, const ttie_elastic *e);
 template <typename T> cudaError_t pcg_solve(Ctx &c, const T *rhs, T *out, double rtol, int max_it);
 // Hessian-vector products: per-pair exact products (pair_eval.cu), their per-vertex sums over
 // the last assembly's diagonal runs, and the assembled PSD Hessian times v.

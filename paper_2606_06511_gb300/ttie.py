@@ -59,10 +59,18 @@ class StepInfo(ctypes.Structure):
                 ("n_candidates_swept", ctypes.c_int64), ("ms_build", ctypes.c_float), ("ms_eval", ctypes.c_float),
                 ("ms_assemble", ctypes.c_float), ("ms_pcg", ctypes.c_float), ("ms_line_search", ctypes.c_float),
                 ("ms_classify", ctypes.c_float), ("ms_pcg_kernel", ctypes.c_float),
-                ("pcg_block_iters", ctypes.c_int64), ("pcg_row_iters", ctypes.c_int64)]
+                ("pcg_block_iters", ctypes.c_int64), ("pcg_row_iters", ctypes.c_int64),
+                ("energy_elastic", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Elastic(ctypes.Structure):
+    """ttie_elastic: springs k_edge/2 (|x_i - x_j| - rest)^2 and anchors k_anchor/2 |x_a - t_a|^2."""
+    _fields_ = [("edges", ctypes.c_void_p), ("rest", ctypes.c_void_p), ("n_edges", ctypes.c_int64),
+                ("k_edge", ctypes.c_double), ("anchors", ctypes.c_void_p), ("targets", ctypes.c_void_p),
+                ("n_anchors", ctypes.c_int64), ("k_anchor", ctypes.c_double)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -101,6 +109,7 @@ _SIGS = {
     "ttie_get_launch_count": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)]),
     "ttie_hvp": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     "ttie_dual_gradients": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "ttie_set_elastic": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Elastic)]),
 }
 
 
@@ -263,6 +272,32 @@ class Context:
         out = torch.empty((max(n.value, 1), 2, 18), dtype=torch.float64, device="cuda")
         self._chk(self.lib.ttie_dual_gradients(self.h, _ptr(x), _ptr(out)))
         return out[: n.value]
+
+    def set_elastic(self, edges: torch.Tensor | None = None, rest: torch.Tensor | None = None, k_edge: float = 0.0,
+                    anchors: torch.Tensor | None = None, targets: torch.Tensor | None = None,
+                    k_anchor: float = 0.0) -> None:
+        """Elastic term of the quasi-static simulation (ttie_set_elastic): springs on edges
+        [E,2] int32 with rest lengths [E] and anchors [A] int32 held at targets [A,3] (both in
+        the context's dtype).  Called with no springs and no anchors it removes the term."""
+        el = Elastic()
+        keep = []
+        if edges is not None and edges.numel():
+            _check_dev(edges, "edges", torch.int32)
+            _check_dev(rest, "rest", self.dtype)
+            if edges.dim() != 2 or edges.shape[1] != 2 or tuple(rest.shape) != (edges.shape[0],):
+                raise TTIEError(TTIE_ERR_INVALID, "edges must be [E,2] and rest [E]")
+            el.edges, el.rest, el.n_edges, el.k_edge = _ptr(edges), _ptr(rest), edges.shape[0], float(k_edge)
+            keep += [edges, rest]
+        if anchors is not None and anchors.numel():
+            _check_dev(anchors, "anchors", torch.int32)
+            _check_dev(targets, "targets", self.dtype)
+            if anchors.dim() != 1 or tuple(targets.shape) != (anchors.shape[0], 3):
+                raise TTIEError(TTIE_ERR_INVALID, "anchors must be [A] and targets [A,3]")
+            el.anchors, el.targets, el.n_anchors, el.k_anchor = _ptr(anchors), _ptr(targets), anchors.shape[0], \
+                float(k_anchor)
+            keep += [anchors, targets]
+        self._chk(self.lib.ttie_set_elastic(self.h, ctypes.byref(el)))
+        del keep   # the context copied the arrays during the call
 
     def newton_step(self, x: torch.Tensor) -> dict:
         self._check_x(x)
