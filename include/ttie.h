@@ -317,8 +317,9 @@ ttie_status ttie_get_active(ttie_ctx *ctx, int32_t *d_pairs, void *d_tc, void *d
 /* Copies the last Newton direction (V x 3, positions' dtype) into d_out. */
 ttie_status ttie_get_direction(ttie_ctx *ctx, void *d_out);
 
-/* Counters of the last ttie_eval_pairs: pair signs decided by the FP32 filter,
- * by FP64, and by exact arithmetic (host out array of 3). */
+/* Counters of the last ttie_eval_pairs (host out array of 3): signs decided by the FP32
+ * filter in the pass over all candidates (FP32 positions), then, in the pass over the pairs
+ * that left a sign undecided, signs decided by the FP64 filter and by exact arithmetic. */
 ttie_status ttie_get_filter_stats(ttie_ctx *ctx, int64_t *out3);
 
 /* ---- solve without allocating -------------------------------------------------- */

@@ -79,8 +79,12 @@ struct Stats {
 };
 
 // Sign providers.  side(P0, P1, P2, q) = sign det[P1-P0, P2-P0, q-P0] (side of q w.r.t. the
-// plane of P); over(p1, pu, q1, qv) = sign det[pu-p1, qv-q1, q1-p1].
-template <typename T> struct Filtered {
+// plane of P); over(p1, pu, q1, qv) = sign det[pu-p1, qv-q1, q1-p1].  kF32Only (FP32
+// positions): a sign the FP32 filter cannot certify is left undecided instead of going to the
+// FP64 filter, so the classification of all candidates never issues FP64 instructions: on
+// GB300 the FP64 pipe runs at a small fraction of the FP32 rate and a warp pays for the
+// FP64 path whenever one of its lanes takes it.  Those pairs go to the resolve pass.
+template <typename T, bool kF32Only = false> struct Filtered {
     bool exact_only;
     Stats &st;
     __device__ __forceinline__ int side(v3<T> P0, v3<T> P1, v3<T> P2, v3<T> q) {
@@ -90,6 +94,7 @@ template <typename T> struct Filtered {
             const v3<T> e1 = P1 - P0, e2 = P2 - P0, f = q - P0;
             s = filt_f32(to_f(cross(e1, e2)), to_f(abs_cross(e1, e2)), to_f(f));
             if (s != kUndec) { ++st.f32; return s; }
+            if (kF32Only) return kUndec;
         }
         const v3<double> a = to_d(P0);
         s = det_sign_f64(to_d(P1) - a, to_d(P2) - a, to_d(q) - a);
@@ -103,6 +108,7 @@ template <typename T> struct Filtered {
             const v3<T> e1 = pu - p1, e2 = qv - q1;
             s = filt_f32(to_f(cross(e1, e2)), to_f(abs_cross(e1, e2)), to_f(q1 - p1));
             if (s != kUndec) { ++st.f32; return s; }
+            if (kF32Only) return kUndec;
         }
         s = det_sign_f64(to_d(pu) - to_d(p1), to_d(qv) - to_d(q1), to_d(q1) - to_d(p1));
         if (s != kUndec) ++st.f64;
@@ -113,15 +119,17 @@ template <typename T> struct Filtered {
 
 // The undecided pairs' signs: each one through the FP32 and FP64 filters again (certified,
 // so the same decisions), and only the signs neither certifies through exact expansions.
-// With exact_only every sign is exact.
+// Counts the signs decided by FP64 and by exact arithmetic (the FP32 ones were counted by the
+// first pass).  With exact_only every sign is exact.
 template <typename T> struct Cascade {
     bool exact_only;
     Stats &st;
     __device__ int side(v3<T> P0, v3<T> P1, v3<T> P2, v3<T> q) {
         if (!exact_only) {
-            Stats none;
-            Filtered<T> f{false, none};
+            Stats inner;
+            Filtered<T> f{false, inner};
             const int s = f.side(P0, P1, P2, q);
+            st.f64 += inner.f64;
             if (s != kUndec) return s;
         }
         ++st.ex;
@@ -130,9 +138,10 @@ template <typename T> struct Cascade {
     // det[pu - p1, qv - q1, q1 - p1] = det[pu - p1, qv - p1, q1 - p1]
     __device__ int over(v3<T> p1, v3<T> pu, v3<T> q1, v3<T> qv) {
         if (!exact_only) {
-            Stats none;
-            Filtered<T> f{false, none};
+            Stats inner;
+            Filtered<T> f{false, inner};
             const int s = f.over(p1, pu, q1, qv);
+            st.f64 += inner.f64;
             if (s != kUndec) return s;
         }
         ++st.ex;
@@ -207,7 +216,7 @@ __global__ void __launch_bounds__(kThreads) k_classify(const vec4_t<T> *__restri
     const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t n_warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     Stats st;
-    Filtered<T> sg{exact_only != 0, st};
+    Filtered<T, true> sg{exact_only != 0, st};
     for (int64_t w = warp0; w < n_words; w += n_warps) {
         const int64_t p = w * 32 + lane;
         int r = 0;
@@ -254,6 +263,7 @@ __global__ void k_resolve(const vec4_t<T> *__restrict__ x, const int4 *__restric
         load_pair<T>(x, tri4, pairs[p], A, B);
         if (classify<T>(A, B, sg) == 1) atomicOr(&bits[p >> 5], 1u << (p & 31));
     }
+    if (st.f64) atomicAdd(&ds->filter_stats[1], st.f64);
     if (st.ex) atomicAdd(&ds->filter_stats[2], st.ex);
 }
 
