@@ -989,30 +989,39 @@ __device__ __forceinline__ Acc<T> resident_product(const PcgArgs<T> &a, const Re
         if (v.gathered) {
             for (int b = v.rp[lr] + sub; b < be; b += kLanesPerRow)
                 block_times(v.val + (size_t)b * 9, v.gu[3 * b], v.gu[3 * b + 1], v.gu[3 * b + 2], y0, y1, y2);
-        } else if (v.cached) {
-            int b = v.rp[lr] + sub;
-            for (; b + kLanesPerRow < be; b += 2 * kLanesPerRow) {   // two gathers in flight
-                const vec4_t<T> *p0 = &a.z4[v.col[b]], *p1 = &a.z4[v.col[b + kLanesPerRow]];
-                vec4_t<T> g0 = ld_row<T>(p0), g1 = ld_row<T>(p1);
-                settle_row<T>(g0, p0, t, bad);
-                settle_row<T>(g1, p1, t, bad);
-                block_times(v.val + (size_t)b * 9, g0.x, g0.y, g0.z, y0, y1, y2);
-                block_times(v.val + (size_t)(b + kLanesPerRow) * 9, g1.x, g1.y, g1.z, y0, y1, y2);
-            }
-            if (b < be) {
-                const vec4_t<T> *p0 = &a.z4[v.col[b]];
-                vec4_t<T> g0 = ld_row<T>(p0);
-                settle_row<T>(g0, p0, t, bad);
-                block_times(v.val + (size_t)b * 9, g0.x, g0.y, g0.z, y0, y1, y2);
-            }
         } else {
-            for (int b = v.rp[lr] + sub; b < be; b += kLanesPerRow) {
-                if (TTIE_BAD(a.ds, (unsigned long long)(v.b_begin + b) < a.ds->nnzb, 41, b)) break;
-                const int c = a.col_idx[v.b_begin + b];
-                if (TTIE_BAD(a.ds, c >= 0 && (unsigned long long)c < a.ds->n_rows, 42, c)) break;
-                vec4_t<T> g0 = ld_row<T>(&a.z4[c]);
-                settle_row<T>(g0, &a.z4[c], t, bad);
-                block_times(a.bval + (size_t)(v.b_begin + b) * 9, g0.x, g0.y, g0.z, y0, y1, y2);
+            // up to four of the lane's blocks at a time: every load in flight before any tag
+            // is checked (a check is a branch on the loaded value)
+            constexpr int U = 4;
+            for (int b0 = v.rp[lr] + sub; b0 < be; b0 += U * kLanesPerRow) {
+                int cc[U];
+#pragma unroll
+                for (int k = 0; k < U; ++k) {
+                    const int b = b0 + k * kLanesPerRow;
+                    cc[k] = -1;
+                    if (b < be) {
+                        if (v.cached) {
+                            cc[k] = v.col[b];
+                        } else {
+                            if (TTIE_BAD(a.ds, (unsigned long long)(v.b_begin + b) < a.ds->nnzb, 41, b)) continue;
+                            const int c = a.col_idx[v.b_begin + b];
+                            if (TTIE_BAD(a.ds, c >= 0 && (unsigned long long)c < a.ds->n_rows, 42, c)) continue;
+                            cc[k] = c;
+                        }
+                    }
+                }
+                vec4_t<T> g[U];
+#pragma unroll
+                for (int k = 0; k < U; ++k)
+                    if (cc[k] >= 0) g[k] = ld_row<T>(&a.z4[cc[k]]);
+#pragma unroll
+                for (int k = 0; k < U; ++k)
+                    if (cc[k] >= 0) {
+                        settle_row<T>(g[k], &a.z4[cc[k]], t, bad);
+                        const int b = b0 + k * kLanesPerRow;
+                        const T *m = v.cached ? v.val + (size_t)b * 9 : a.bval + (size_t)(v.b_begin + b) * 9;
+                        block_times(m, g[k].x, g[k].y, g[k].z, y0, y1, y2);
+                    }
             }
         }
 #pragma unroll

@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <cstddef>
 #include <cstdint>
 #include <cstdio>
 #include <string>
@@ -74,7 +75,8 @@ struct Inst {
 struct DevScalars {
     unsigned long long n_cand;
     unsigned long long n_active;
-    unsigned long long n_defer;
+    unsigned long long n_defer;           // pairs the FP32 pass left undecided
+    unsigned long long n_defer2;          // pairs the FP64 filter left undecided (cleared with n_defer)
     unsigned long long n_rows;
     unsigned long long nnzb;
     unsigned long long n_groups_seen;
@@ -100,6 +102,9 @@ struct DevScalars {
     double el_energy;                      // energy of the elastic term at the last evaluation
 };
 
+static_assert(offsetof(DevScalars, n_defer2) == offsetof(DevScalars, n_defer) + sizeof(unsigned long long),
+              "n_defer and n_defer2 are cleared by one 16-byte memset");
+
 // ------------------------------------------------------------------ buffers
 struct Buf {
     void *p = nullptr;
@@ -117,7 +122,7 @@ cudaError_t ensure(Ctx &c, Buf &b, size_t bytes);   // grow-only, contents not k
     X(bval) X(bval2) X(bflag) X(run_start) X(row_ptr) X(col_idx) X(bsr_val) X(rhs)         \
     X(zfac) X(dinv) X(pcg_x) X(pcg_r) X(pcg_z) X(pcg_p) X(pcg_q) X(dir) X(xt) X(gtmp)      \
     X(xsave) X(sweep_cand) X(pcg_z4) X(hbuf) X(pcg_sync) X(spill) X(pcg_w) X(vgroup) X(iedge)  \
-    X(el_edges) X(el_rest) X(el_anchor) X(el_target) X(el_sfac) X(el_afac)                    \
+    X(el_edges) X(el_rest) X(el_anchor) X(el_target) X(el_sfac) X(el_afac) X(defer2)          \
     X(inst) X(ls_cand) X(inst_acc) X(inst_ids) X(ab) X(ls_flag)  \
     X(ls_off) X(ls_scalars) X(hgrid) X(hkey) X(hkey2) X(hval) X(hval2) X(hcnt) X(hoff)
 

@@ -246,25 +246,47 @@ __global__ void __launch_bounds__(kThreads) k_classify(const vec4_t<T> *__restri
     }
 }
 
-// Decision of the undecided pairs: the same test, every sign the filters cannot certify
-// from exact expansion arithmetic (a vertex exactly on a plane counts as zero, touching
-// intervals do not overlap).
+// Pairs the FP32 pass left undecided, compacted: the test again with the FP32 then FP64
+// filters.  Pairs still undecided go to defer2 for the exact pass, which keeps the
+// registers of the exact expansions (and their low occupancy) off the many pairs that FP64
+// decides.
 template <typename T>
-__global__ void k_resolve(const vec4_t<T> *__restrict__ x, const int4 *__restrict__ tri4, const int2 *__restrict__ pairs,
-                          const uint32_t *__restrict__ defer, int exact_only, uint32_t *__restrict__ bits,
-                          DevScalars *ds) {
+__global__ void k_resolve_f64(const vec4_t<T> *__restrict__ x, const int4 *__restrict__ tri4,
+                              const int2 *__restrict__ pairs, const uint32_t *__restrict__ defer, int exact_only,
+                              uint32_t *__restrict__ bits, uint32_t *__restrict__ defer2, DevScalars *ds) {
     const unsigned long long m = ds->n_defer;
     Stats st;
-    Cascade<T> sg{exact_only != 0, st};
+    Filtered<T> sg{exact_only != 0, st};
     for (unsigned long long k = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; k < m;
          k += (unsigned long long)gridDim.x * blockDim.x) {
         const uint32_t p = defer[k];
         v3<T> A[3], B[3];
         load_pair<T>(x, tri4, pairs[p], A, B);
-        if (classify<T>(A, B, sg) == 1) atomicOr(&bits[p >> 5], 1u << (p & 31));
+        const int r = classify<T>(A, B, sg);
+        if (r == 1) atomicOr(&bits[p >> 5], 1u << (p & 31));
+        else if (r == -1) defer2[atomicAdd(&ds->n_defer2, 1ull)] = p;
     }
     if (st.f64) atomicAdd(&ds->filter_stats[1], st.f64);
-    if (st.ex) atomicAdd(&ds->filter_stats[2], st.ex);
+}
+
+// Decision of the pairs neither filter decided: the same test, every sign the filters
+// cannot certify from exact expansion arithmetic (a vertex exactly on a plane counts as
+// zero, touching intervals do not overlap).
+template <typename T>
+__global__ void k_resolve(const vec4_t<T> *__restrict__ x, const int4 *__restrict__ tri4, const int2 *__restrict__ pairs,
+                          const uint32_t *__restrict__ defer2, int exact_only, uint32_t *__restrict__ bits,
+                          DevScalars *ds) {
+    const unsigned long long m = ds->n_defer2;
+    Stats st;
+    Cascade<T> sg{exact_only != 0, st};
+    for (unsigned long long k = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; k < m;
+         k += (unsigned long long)gridDim.x * blockDim.x) {
+        const uint32_t p = defer2[k];
+        v3<T> A[3], B[3];
+        load_pair<T>(x, tri4, pairs[p], A, B);
+        if (classify<T>(A, B, sg) == 1) atomicOr(&bits[p >> 5], 1u << (p & 31));
+    }
+    if (st.ex) atomicAdd(&ds->filter_stats[2], st.ex);   // its FP64 signs were counted by k_resolve_f64
 }
 
 __global__ void k_popc(const uint32_t *__restrict__ bits, int64_t n_words, uint32_t *__restrict__ cnt) {
@@ -588,9 +610,10 @@ cudaError_t eval_candidates(Ctx &c, const vec4_t<T> *x, const int2 *pairs, int64
     TTIE_CUDA_TRY(ensure(c, c.act_bits, (size_t)(n_words > 0 ? n_words : 1) * 4));
     TTIE_CUDA_TRY(ensure(c, c.word_off, (size_t)(n_words + 1) * 8));
     TTIE_CUDA_TRY(ensure(c, c.defer, (size_t)(n > 0 ? n : 1) * 4));
+    TTIE_CUDA_TRY(ensure(c, c.defer2, (size_t)(n > 0 ? n : 1) * 4));
     TTIE_CUDA_TRY(ensure(c, c.active, (size_t)(n > 0 ? n : 1) * 4));
     TTIE_CUDA_TRY(ensure(c, c.partials, (size_t)kNumSMs * 16 * sizeof(double)));
-    TTIE_CUDA_TRY(cudaMemsetAsync(&c.ds->n_defer, 0, 8, c.stream));
+    TTIE_CUDA_TRY(cudaMemsetAsync(&c.ds->n_defer, 0, 16, c.stream));   // n_defer, n_defer2
     TTIE_CUDA_TRY(cudaMemsetAsync(&c.ds->filter_stats[0], 0, 3 * 8, c.stream));
     auto *bits = (uint32_t *)c.act_bits.p;
     const int4 *tri4 = (const int4 *)c.tri4.p;
@@ -600,7 +623,9 @@ cudaError_t eval_candidates(Ctx &c, const vec4_t<T> *x, const int2 *pairs, int64
         launch(c, k_classify<T>, dim3(g), dim3(kThreads), x, tri4, pairs, n, (const unsigned long long *)nullptr,
                c.prm.exact_only, bits, (uint32_t *)c.defer.p, c.ds);
         if (c.time_kernels) cudaEventRecord(c.ev[7], c.stream);
-        launch(c, k_resolve<T>, dim3(kNumSMs * 4), dim3(64), x, tri4, pairs, (const uint32_t *)c.defer.p,
+        launch(c, k_resolve_f64<T>, dim3(kNumSMs * 8), dim3(128), x, tri4, pairs, (const uint32_t *)c.defer.p,
+               c.prm.exact_only, bits, (uint32_t *)c.defer2.p, c.ds);
+        launch(c, k_resolve<T>, dim3(kNumSMs * 4), dim3(64), x, tri4, pairs, (const uint32_t *)c.defer2.p,
                c.prm.exact_only, bits, c.ds);
         TTIE_CUDA_TRY(ensure(c, c.gtmp, (size_t)(n_words > 0 ? n_words : 1) * 4));
         launch(c, k_popc, dim3(grid_for(n_words, kThreads)), dim3(kThreads), bits, n_words, (uint32_t *)c.gtmp.p);
@@ -641,6 +666,7 @@ template <typename T> cudaError_t prepare_energy_eval(Ctx &c, int64_t n_cap) {
     TTIE_CUDA_TRY(ensure(c, c.act_bits, (size_t)(n_words > 0 ? n_words : 1) * 4));
     TTIE_CUDA_TRY(ensure(c, c.word_off, (size_t)(n_words + 1) * 8));
     TTIE_CUDA_TRY(ensure(c, c.defer, (size_t)(n_cap > 0 ? n_cap : 1) * 4));
+    TTIE_CUDA_TRY(ensure(c, c.defer2, (size_t)(n_cap > 0 ? n_cap : 1) * 4));
     TTIE_CUDA_TRY(ensure(c, c.active, (size_t)(n_cap > 0 ? n_cap : 1) * 4));
     TTIE_CUDA_TRY(ensure(c, c.partials, (size_t)kNumSMs * 16 * sizeof(double)));
     TTIE_CUDA_TRY(ensure(c, c.gtmp, (size_t)(n_cap > 0 ? n_cap : 1) * 4));
@@ -655,7 +681,7 @@ template <typename T>
 cudaError_t energy_eval_nosync(Ctx &c, const vec4_t<T> *x, const int2 *pairs, int64_t n_cap,
                                const unsigned long long *d_n) {
     const int64_t n_words = (n_cap + 31) / 32;
-    TTIE_CUDA_TRY(cudaMemsetAsync(&c.ds->n_defer, 0, 8, c.stream));
+    TTIE_CUDA_TRY(cudaMemsetAsync(&c.ds->n_defer, 0, 16, c.stream));   // n_defer, n_defer2
     TTIE_CUDA_TRY(cudaMemsetAsync(&c.ds->filter_stats[0], 0, 3 * 8, c.stream));
     auto *bits = (uint32_t *)c.act_bits.p;
     const int4 *tri4 = (const int4 *)c.tri4.p;
@@ -663,7 +689,9 @@ cudaError_t energy_eval_nosync(Ctx &c, const vec4_t<T> *x, const int2 *pairs, in
         const unsigned g = grid_for(n_words * 32, kThreads, (int64_t)kNumSMs * 8);
         launch(c, k_classify<T>, dim3(g), dim3(kThreads), x, tri4, pairs, n_cap, d_n, c.prm.exact_only, bits,
                (uint32_t *)c.defer.p, c.ds);
-        launch(c, k_resolve<T>, dim3(kNumSMs * 4), dim3(64), x, tri4, pairs, (const uint32_t *)c.defer.p,
+        launch(c, k_resolve_f64<T>, dim3(kNumSMs * 8), dim3(128), x, tri4, pairs, (const uint32_t *)c.defer.p,
+               c.prm.exact_only, bits, (uint32_t *)c.defer2.p, c.ds);
+        launch(c, k_resolve<T>, dim3(kNumSMs * 4), dim3(64), x, tri4, pairs, (const uint32_t *)c.defer2.p,
                c.prm.exact_only, bits, c.ds);
         launch(c, k_popc, dim3(grid_for(n_words, kThreads)), dim3(kThreads), (const uint32_t *)bits, n_words,
                (uint32_t *)c.gtmp.p);
