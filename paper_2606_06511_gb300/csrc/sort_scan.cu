@@ -116,16 +116,23 @@ __global__ void __launch_bounds__(kThreads) k_radix_hist(const unsigned long lon
 }
 
 // Stable scatter.  Warp w of tile t owns elements [t*kTile + w*32*kItems, +32*kItems) and
-// walks them in rounds of 32 in order, so (warp, round, lane) order is input order.
+// walks them in rounds of 32 in order, so (warp, round, lane) order is input order.  The tile
+// is first reordered by digit in shared memory (same stable order), then written out in that
+// order, so consecutive threads write consecutive positions of one digit's run instead of
+// scattering every element to a different bucket.
 __global__ void __launch_bounds__(kThreads) k_radix_scatter(
     const unsigned long long *__restrict__ kin, const uint32_t *__restrict__ vin,
     unsigned long long *__restrict__ kout, uint32_t *__restrict__ vout, int64_t n, int shift,
     int64_t n_tiles, const unsigned long long *__restrict__ off) {
     __shared__ uint32_t wh[kWarps][kRadix];
+    __shared__ uint32_t dbase[kRadix];            // start of each digit in the reordered tile
+    __shared__ unsigned long long s_key[kTile];
+    __shared__ uint32_t s_val[kTile];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int i = threadIdx.x; i < kWarps * kRadix; i += kThreads) (&wh[0][0])[i] = 0;
     __syncthreads();
-    const int64_t wbase = (int64_t)blockIdx.x * kTile + (int64_t)w * 32 * kItems;
+    const int64_t tbase = (int64_t)blockIdx.x * kTile;
+    const int64_t wbase = tbase + (int64_t)w * 32 * kItems;
     unsigned long long key[kItems];
     uint32_t val[kItems], rank[kItems];
     int dig[kItems];
@@ -146,9 +153,9 @@ __global__ void __launch_bounds__(kThreads) k_radix_scatter(
         __syncwarp();
     }
     __syncthreads();
-    // exclusive prefix over warps per digit
+    // exclusive prefix over warps per digit, then over digits of the tile's counts
     {
-        int d = threadIdx.x;   // kThreads == kRadix
+        const int d = threadIdx.x;   // kThreads == kRadix
         uint32_t run = 0;
 #pragma unroll
         for (int ww = 0; ww < kWarps; ++ww) {
@@ -156,16 +163,27 @@ __global__ void __launch_bounds__(kThreads) k_radix_scatter(
             wh[ww][d] = run;
             run += t;
         }
+        uint32_t tot;
+        dbase[d] = block_exclusive_scan(run, &tot);
     }
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < kItems; ++r) {
-        int d = dig[r];
+        const int d = dig[r];
         if (d < kRadix) {
-            unsigned long long pos = off[(int64_t)d * n_tiles + blockIdx.x] + wh[w][d] + rank[r];
-            kout[pos] = key[r];
-            vout[pos] = val[r];
+            const uint32_t lp = dbase[d] + wh[w][d] + rank[r];
+            s_key[lp] = key[r];
+            s_val[lp] = val[r];
         }
+    }
+    __syncthreads();
+    const int n_valid = (int)min((int64_t)kTile, n - tbase);
+    for (int i = threadIdx.x; i < n_valid; i += kThreads) {
+        const unsigned long long k = s_key[i];
+        const int d = (int)((k >> shift) & (kRadix - 1));
+        const unsigned long long pos = off[(int64_t)d * n_tiles + blockIdx.x] + (uint32_t)(i - dbase[d]);
+        kout[pos] = k;
+        vout[pos] = s_val[i];
     }
 }
 
