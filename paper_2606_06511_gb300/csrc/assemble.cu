@@ -24,7 +24,11 @@ namespace ttie {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kZStride = 72;     // [z1 (18), z2 (18), z3 (18), g (18)]
+// Per intersecting pair, for each of its 6 vertices r: [z1 (3), z2 (3), z3 (3), g (3)] (the
+// rows 3r..3r+2 of the three PSD factors and of the gradient), so a 3x3 block (r, c) reads
+// two contiguous 36-byte runs.
+constexpr int kZStride = 72;
+constexpr int kZVertex = 12;
 
 template <typename T>
 __device__ __forceinline__ T block_sum(T v) {
@@ -161,10 +165,11 @@ __global__ void k_factors(const T *__restrict__ fac, int psd_mode, T *__restrict
         for (int i = 0; i < 18; ++i) {
             const T u = r[2 + i], v = r[20 + i];
             const T z1 = c1 * u + (wa * u + wb * v), z2 = c2 * v, z3 = c3 * (u * iu - v * iv);
-            o[i] = z1;
-            o[18 + i] = z2;
-            o[36 + i] = z3;
-            o[54 + i] = T(2) * a * b * (b * u + a * v);
+            T *ov = o + (i / 3) * kZVertex + i % 3;
+            ov[0] = z1;
+            ov[3] = z2;
+            ov[6] = z3;
+            ov[9] = T(2) * a * b * (b * u + a * v);
             t += (double)z1 * z1 + (double)z2 * z2 + (double)z3 * z3;
         }
         tr += t;
@@ -177,27 +182,23 @@ __device__ __forceinline__ int vid(int4 a, int4 b, int r) {
     return r == 0 ? a.x : r == 1 ? a.y : r == 2 ? a.z : r == 3 ? b.x : r == 4 ? b.y : b.z;
 }
 
+// One thread per block entry (pair k, vertex rows r and c), so the keys and values are written
+// contiguously.
 __global__ void k_block_keys(const int4 *__restrict__ tri4, const int2 *__restrict__ pairs,
                              const uint32_t *__restrict__ active, const unsigned long long *__restrict__ vrow,
                              const DevScalars *ds, unsigned long long *__restrict__ key, uint32_t *__restrict__ val) {
-    const unsigned long long n = ds->n_active, nr = ds->n_rows;
-    for (unsigned long long k = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; k < n;
-         k += (unsigned long long)gridDim.x * blockDim.x) {
-        int2 pr = pairs[active[k]];
-        int4 a = tri4[pr.x], b = tri4[pr.y];
-        unsigned long long row[6];
-#pragma unroll
-        for (int r = 0; r < 6; ++r) row[r] = vrow[vid(a, b, r)];
-#pragma unroll
-        for (int r = 0; r < 6; ++r)
-            if (TTIE_BAD((DevScalars *)ds, row[r] < nr, 11, row[r])) row[r] = 0;
-#pragma unroll
-        for (int r = 0; r < 6; ++r)
-#pragma unroll
-            for (int c = 0; c < 6; ++c) {
-                key[k * 36 + r * 6 + c] = row[r] * nr + row[c];
-                val[k * 36 + r * 6 + c] = (uint32_t)(k * 36 + r * 6 + c);
-            }
+    const unsigned long long n = ds->n_active * 36, nr = ds->n_rows;
+    for (unsigned long long e = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; e < n;
+         e += (unsigned long long)gridDim.x * blockDim.x) {
+        const unsigned long long k = e / 36;
+        const int rc = (int)(e - k * 36), r = rc / 6, c = rc - r * 6;
+        const int2 pr = pairs[active[k]];
+        const int4 a = tri4[pr.x], b = tri4[pr.y];
+        unsigned long long rr = vrow[vid(a, b, r)], cc = vrow[vid(a, b, c)];
+        if (TTIE_BAD((DevScalars *)ds, rr < nr, 11, rr)) rr = 0;
+        if (TTIE_BAD((DevScalars *)ds, cc < nr, 11, cc)) cc = 0;
+        key[e] = rr * nr + cc;
+        val[e] = (uint32_t)e;
     }
 }
 
@@ -388,18 +389,17 @@ __global__ void k_block_values(const unsigned long long *__restrict__ key, const
             }
             const uint32_t pk = v / 36, rc = v - pk * 36, r = rc / 6, c = rc - r * 6;
             if (TTIE_BAD((DevScalars *)ds, pk < ds->n_active, 23, pk)) continue;
-            const T *zp = z + (size_t)pk * kZStride;
+            const T *zr = z + (size_t)pk * kZStride + r * kZVertex, *zc = z + (size_t)pk * kZStride + c * kZVertex;
 #pragma unroll
             for (int t = 0; t < 3; ++t) {
-                const T *zt = zp + 18 * t;
-                const T x0 = zt[3 * r], x1 = zt[3 * r + 1], x2 = zt[3 * r + 2];
-                const T y0 = zt[3 * c], y1 = zt[3 * c + 1], y2 = zt[3 * c + 2];
+                const T x0 = zr[3 * t], x1 = zr[3 * t + 1], x2 = zr[3 * t + 2];
+                const T y0 = zc[3 * t], y1 = zc[3 * t + 1], y2 = zc[3 * t + 2];
                 m[0] += x0 * y0; m[1] += x0 * y1; m[2] += x0 * y2;
                 m[3] += x1 * y0; m[4] += x1 * y1; m[5] += x1 * y2;
                 m[6] += x2 * y0; m[7] += x2 * y1; m[8] += x2 * y2;
             }
             if (row == col) {
-                g0 += zp[54 + 3 * r]; g1 += zp[54 + 3 * r + 1]; g2 += zp[54 + 3 * r + 2];
+                g0 += zr[9]; g1 += zr[10]; g2 += zr[11];
             }
         }
 #pragma unroll
@@ -1349,7 +1349,7 @@ cudaError_t assemble_system(Ctx &c, T *grad_full, bool with_elastic) {
     TTIE_CUDA_TRY(ensure(c, c.zfac, (size_t)(n_act > 0 ? n_act : 1) * kZStride * sizeof(T)));
     TTIE_CUDA_TRY(ensure(c, c.partials, (size_t)kNumSMs * 16 * 4 * sizeof(double)));
     launch(c, k_factors<T>, dim3(grid_for(n_act, 128, kNumSMs * 8)), dim3(128), (const T *)c.fac.p, c.prm.psd_mode,
-                                                                        (T *)c.zfac.p, (double *)c.partials.p, c.ds);
+           (T *)c.zfac.p, (double *)c.partials.p, c.ds);
     if (el) {   // after k_factors: adds the term's trace to the pairs'
         TTIE_CUDA_TRY(ensure(c, c.el_sfac, (size_t)(n_springs > 0 ? n_springs : 1) * kElStride * sizeof(T)));
         TTIE_CUDA_TRY(ensure(c, c.el_afac, (size_t)(n_anchors > 0 ? n_anchors : 1) * 3 * sizeof(T)));
@@ -1371,8 +1371,8 @@ cudaError_t assemble_system(Ctx &c, T *grad_full, bool with_elastic) {
     TTIE_CUDA_TRY(cudaStreamSynchronize(c.stream));
     const int64_t nr = (int64_t)c.hs->n_rows;
     c.n_rows = nr;
-    launch(c, k_block_keys, dim3(gA), dim3(kThreads), tri4, pairs, active, (const unsigned long long *)c.vrow.p, c.ds,
-                                                (unsigned long long *)c.bkey.p, (uint32_t *)c.bval.p);
+    launch(c, k_block_keys, dim3(grid_for(n_act * 36, kThreads)), dim3(kThreads), tri4, pairs, active,
+           (const unsigned long long *)c.vrow.p, c.ds, (unsigned long long *)c.bkey.p, (uint32_t *)c.bval.p);
     if (el)
         launch(c, k_el_keys, dim3(grid_for(n_springs + n_anchors, kThreads)), dim3(kThreads), (const int2 *)c.el_edges.p,
                n_springs, (const int32_t *)c.el_anchor.p, n_anchors, (const unsigned long long *)c.vrow.p, c.ds,
