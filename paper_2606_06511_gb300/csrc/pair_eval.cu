@@ -604,6 +604,18 @@ __global__ void __launch_bounds__(128) k_dual_gradients(const vec4_t<T> *__restr
 
 }  // namespace
 
+// Blocks of k_classify that are resident on the whole GPU at once: one wave of a latency-bound
+// kernel (a second, partial wave would leave SMs idle at its end).
+template <typename T> static int64_t classify_wave(Ctx &c) {
+    static int per_sm = 0;
+    if (per_sm == 0) {
+        int b = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_classify<T>, kThreads, 0) != cudaSuccess || b < 1) b = 1;
+        per_sm = b;
+    }
+    return (int64_t)per_sm * (c.num_sms > 0 ? c.num_sms : kNumSMs);
+}
+
 template <typename T>
 cudaError_t eval_candidates(Ctx &c, const vec4_t<T> *x, const int2 *pairs, int64_t n, unsigned what) {
     const int64_t n_words = (n + 31) / 32;
@@ -618,7 +630,7 @@ cudaError_t eval_candidates(Ctx &c, const vec4_t<T> *x, const int2 *pairs, int64
     auto *bits = (uint32_t *)c.act_bits.p;
     const int4 *tri4 = (const int4 *)c.tri4.p;
     if (n > 0) {
-        const unsigned g = grid_for(n_words * 32, kThreads, (int64_t)kNumSMs * 8);
+        const unsigned g = grid_for(n_words * 32, kThreads, classify_wave<T>(c));
         if (c.time_kernels) cudaEventRecord(c.ev[6], c.stream);
         launch(c, k_classify<T>, dim3(g), dim3(kThreads), x, tri4, pairs, n, (const unsigned long long *)nullptr,
                c.prm.exact_only, bits, (uint32_t *)c.defer.p, c.ds);
@@ -686,7 +698,7 @@ cudaError_t energy_eval_nosync(Ctx &c, const vec4_t<T> *x, const int2 *pairs, in
     auto *bits = (uint32_t *)c.act_bits.p;
     const int4 *tri4 = (const int4 *)c.tri4.p;
     if (n_cap > 0) {
-        const unsigned g = grid_for(n_words * 32, kThreads, (int64_t)kNumSMs * 8);
+        const unsigned g = grid_for(n_words * 32, kThreads, classify_wave<T>(c));
         launch(c, k_classify<T>, dim3(g), dim3(kThreads), x, tri4, pairs, n_cap, d_n, c.prm.exact_only, bits,
                (uint32_t *)c.defer.p, c.ds);
         launch(c, k_resolve_f64<T>, dim3(kNumSMs * 8), dim3(128), x, tri4, pairs, (const uint32_t *)c.defer.p,
