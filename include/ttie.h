@@ -98,6 +98,10 @@ typedef struct {
     int inst_threads;     /* batched instances: threads per instance block (128, 256,
                              512 or 1024); 0 = chosen per size bucket by timing the
                              candidates on the first step (results do not depend on it) */
+    int test_withhold;    /* test switch (0 in use): block 0 of the shared-memory PCG never
+                             publishes its partial sums, so every block's bounded wait for
+                             them runs out (about a second) and the call returns
+                             TTIE_ERR_CUDA with the context still usable               */
 } ttie_params;
 
 typedef struct ttie_ctx ttie_ctx;
@@ -105,7 +109,7 @@ typedef struct ttie_ctx ttie_ctx;
 /* Fills *p with the defaults: F32, SELF, PER_PART, tc_scale 1, mu_rel 1e-3,
  * pcg_rtol 1e-3, pcg_max_it 200, newton_max_it 200, ls_max_halvings 20,
  * armijo_c 1e-4, push_eta 0.5, exact_only 0, profile 0, max_step 1,
- * max_candidates 0, inst_threads 0. */
+ * max_candidates 0, inst_threads 0, test_withhold 0. */
 void ttie_default_params(ttie_params *p);
 
 /* Creates a context on the current CUDA device.  stream: a cudaStream_t or NULL

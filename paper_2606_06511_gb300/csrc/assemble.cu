@@ -513,13 +513,31 @@ __global__ void k_pcg_setup(const int32_t *__restrict__ row_ptr, const int32_t *
 // sets ERR_BARRIER and the kernel returns.  Reductions: block partials, then every block
 // sums all partials in the same order, so all blocks take the same decisions and the
 // result does not depend on timing.
-constexpr long long kBarrierSpins = 50000000;   // with ~20-40 ns sleeps: a few seconds
+// Every wait of the PCG kernels gives up after kWaitNs of elapsed time (the GPU's global
+// timer, read every 64 polls), so a block that never arrives ends the others' waits, and the
+// launch, with ERR_BARRIER in about a second.
+constexpr unsigned long long kWaitNs = 1000000000ull;
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+struct WaitClock {
+    unsigned long long t0 = 0;
+    unsigned polls = 0;
+    __device__ __forceinline__ bool out() {   // true once the wait has run for more than kWaitNs
+        if ((polls++ & 63u) != 0u) return false;
+        const unsigned long long t = global_ns();
+        if (t0 == 0) t0 = t;
+        return t - t0 > kWaitNs;
+    }
+};
 
 // Sum of per-block values v[0..N) over the grid, identical in every block, fused with a
 // grid barrier.  Each block writes its partial sums and arrives on one counter; the last
 // block to arrive adds all partials in block order (a fixed order, so the result does not
 // depend on timing), publishes the totals and bumps the generation the others poll; they
-// then read the totals.  Waits are bounded (kBarrierSpins); on timeout ERR_BARRIER is set
+// then read the totals.  Waits are bounded (kWaitNs); on timeout ERR_BARRIER is set
 // and false returned.  part holds N x gridDim.x partials followed by N totals.
 template <int N>
 __device__ __forceinline__ bool grid_allreduce(double (&v)[N], double *part, DevScalars *ds) {
@@ -559,9 +577,9 @@ __device__ __forceinline__ bool grid_allreduce(double (&v)[N], double *part, Dev
                 atomicAdd(&ds->bar_gen, 1u);
             }
         } else if (threadIdx.x == 0) {
-            long long spins = 0;
+            WaitClock wc;
             while (*(volatile unsigned int *)&ds->bar_gen == g) {
-                if (++spins > kBarrierSpins) {
+                if (wc.out()) {
                     atomicOr(&ds->err, ERR_BARRIER);
                     s_fail = 1;
                     break;
@@ -597,6 +615,7 @@ template <typename T> struct PcgArgs {
     double *partA, *partB;
     RedSlot *slots;          // resident kernel: 2 x kMaxGridPcg tagged reduction slots, then 2 total slots
     const int *part;         // resident kernel: rows of block b are part[b] .. part[b + 1]
+    int withhold;            // test switch: block 0 never publishes its partial sums
     double rtol2;
     int max_it;
     DevScalars *ds;
@@ -749,7 +768,6 @@ __global__ void __launch_bounds__(kPcgThreads) k_pcg_persistent(PcgArgs<T> a) {
 // timeout ERR_BARRIER is set and the kernel returns.
 constexpr int kResidentSmem = 220 * 1024;   // dynamic shared memory per block
 constexpr int kMaxGridPcg = 160;            // at least the SM count; slots per lane of the root's poll: 5
-constexpr long long kTagSpins = kBarrierSpins / 16;   // reloads of one word (each an L2 round trip)
 constexpr int kRowWeight = 8;   // work of a row in the partition, in matrix blocks (lane-group pass, shuffles, update)
 
 __device__ __forceinline__ void st_relaxed_u64(unsigned long long *p, unsigned long long v) {
@@ -795,9 +813,9 @@ template <typename T> __device__ __forceinline__ bool row_tagged(const vec4_t<T>
 // reload g from p until its words carry tag t; bounded (sets *bad)
 template <typename T>
 __device__ __forceinline__ void settle_row(vec4_t<T> &g, const vec4_t<T> *p, unsigned t, int *bad) {
-    long long spins = 0;
+    WaitClock wc;
     while (!row_tagged<T>(g, t)) {
-        if (++spins > kTagSpins || *(volatile int *)bad) { *bad = 1; return; }
+        if (wc.out() || *(volatile int *)bad) { *bad = 1; return; }
         g = ld_row<T>(p);
     }
 }
@@ -825,10 +843,11 @@ __device__ __forceinline__ void ld_slot(const RedSlot *p, unsigned long long (&w
 // adds them in slot order and publishes the totals in one slot of their own; every other
 // block polls that one slot.  So each poll round costs the memory system one load per block
 // instead of one per block and slot.  Thread 0 then runs fin(totals).  A block that gave up
-// (*bad) publishes nothing.  Returns false (ERR_BARRIER set) when a wait ran out.
+// (*bad), or withholds (the failure-path test switch), publishes nothing.  Returns false
+// (ERR_BARRIER set) when a wait ran out.
 template <int N, typename T, typename Fin>
 __device__ __forceinline__ bool slot_allreduce(Acc<T> (&a)[N], RedSlot *slots, unsigned k, const int *bad,
-                                               DevScalars *ds, Fin fin) {
+                                               bool withhold, DevScalars *ds, Fin fin) {
     static_assert(N <= 3, "three words per slot");
     __shared__ int s_fail;
     __shared__ unsigned long long s_part[N][32];
@@ -850,7 +869,7 @@ __device__ __forceinline__ bool slot_allreduce(Acc<T> (&a)[N], RedSlot *slots, u
         Acc<T> mine = lane < (int)(blockDim.x >> 5) ? Acc<T>::from_bits(s_part[wi][lane]) : Acc<T>();
 #pragma unroll
         for (int o = 16; o; o >>= 1) mine.add(mine.shfl_xor(0xffffffffu, o, 32));
-        if (lane == 0 && !gave_up) st_relaxed_u64(&buf[blockIdx.x].v[wi], tag_bits<T>(mine.bits(), t));
+        if (lane == 0 && !gave_up && !withhold) st_relaxed_u64(&buf[blockIdx.x].v[wi], tag_bits<T>(mine.bits(), t));
     }
     if (wi == 0) {
         bool fail = gave_up;
@@ -861,7 +880,7 @@ __device__ __forceinline__ bool slot_allreduce(Acc<T> (&a)[N], RedSlot *slots, u
 #pragma unroll
             for (int q = 0; q < kMaxGridPcg / 32; ++q)
                 if (lane + 32u * q < G) want |= 1u << q;
-            long long spins = 0;
+            WaitClock wc;
             while (!fail) {
 #pragma unroll
                 for (int q = 0; q < kMaxGridPcg / 32; ++q)
@@ -878,7 +897,7 @@ __device__ __forceinline__ bool slot_allreduce(Acc<T> (&a)[N], RedSlot *slots, u
                         }
                     }
                 if (__all_sync(0xffffffffu, ready == want)) break;
-                if (++spins > kBarrierSpins) { fail = true; break; }
+                if (wc.out()) { fail = true; break; }
                 __nanosleep(20);
             }
             fail = __any_sync(0xffffffffu, fail);
@@ -899,14 +918,14 @@ __device__ __forceinline__ bool slot_allreduce(Acc<T> (&a)[N], RedSlot *slots, u
 #pragma unroll
                 for (int i = 0; i < N; ++i) st_relaxed_u64(&tot->v[i], tw[i]);
         } else if (lane == 0) {
-            long long spins = 0;
+            WaitClock wc;
             while (!fail) {
                 ld_slot(tot, tw);
                 bool ok = true;
 #pragma unroll
                 for (int i = 0; i < N; ++i) ok &= bits_tag<T>(tw[i]) == t;
                 if (ok) break;
-                if (++spins > kBarrierSpins) { fail = true; break; }
+                if (wc.out()) { fail = true; break; }
                 __nanosleep(20);
             }
         }
@@ -962,7 +981,7 @@ __device__ __forceinline__ Acc<T> resident_product(const PcgArgs<T> &a, const Re
                     pend |= 1u << k;
                 }
             }
-            long long spins = 0;
+            WaitClock wc;
             while (true) {
 #pragma unroll
                 for (int k = 0; k < U; ++k)
@@ -972,7 +991,7 @@ __device__ __forceinline__ Acc<T> resident_product(const PcgArgs<T> &a, const Re
                         pend &= ~(1u << k);
                     }
                 if (!pend) break;
-                if (++spins > kTagSpins || *(volatile int *)bad) { *bad = 1; break; }
+                if (wc.out() || *(volatile int *)bad) { *bad = 1; break; }
 #pragma unroll
                 for (int k = 0; k < U; ++k)
                     if (pend >> k & 1u) g[k] = ld_row<T>(&a.z4[v.col[j0 + k * kPcgThreads]]);
@@ -1158,7 +1177,7 @@ __global__ void __launch_bounds__(kPcgThreads) k_pcg_resident(PcgArgs<T> a, int 
     };
     while (true) {
         Acc<T> red[3] = {gl, resident_product(a, v, mu, (unsigned)it & 3u, &s_bad), rl};
-        if (!slot_allreduce<3, T>(red, a.slots, (unsigned)it, &s_bad, ds, decide)) return;
+        if (!slot_allreduce<3, T>(red, a.slots, (unsigned)it, &s_bad, a.withhold && blockIdx.x == 0, ds, decide)) return;
         if (s_stop) break;
         const T al = s_alpha, be = s_beta;
         const unsigned tn = (unsigned)(it + 1) & 3u;
@@ -1509,6 +1528,7 @@ cudaError_t pcg_solve(Ctx &c, const T *rhs, T *out, double rtol, int max_it) {
     args.ds = c.ds;
     args.slots = slots;
     args.part = rpart;
+    args.withhold = c.prm.test_withhold;
     ++c.n_launch;
     if (c.prm.profile) cudaEventRecord(c.ev[8], c.stream);
     if (resident) {
@@ -1591,6 +1611,7 @@ cudaError_t pcg_run_raw(cudaStream_t stream, int num_sms, const int32_t *row_ptr
     args.z4 = nullptr;   // only the block-resident kernel uses the vector mirror, slots and partition
     args.slots = nullptr;
     args.part = nullptr;
+    args.withhold = 0;
     args.partA = partials;
     args.partB = partials + 2 * kNumSMs * 8;
     args.rtol2 = rtol * rtol;

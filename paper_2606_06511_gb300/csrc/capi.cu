@@ -110,7 +110,8 @@ static ttie_status check_params(Ctx &c, const ttie_params *p) {
         p->newton_max_it < 0 || p->ls_max_halvings < 0 || p->ls_max_halvings > 60 || !(p->armijo_c >= 0.0) ||
         !(p->push_eta >= 0.0) || !(p->max_step >= 0.0) || p->max_candidates < 0 ||
         (p->inst_threads != 0 && p->inst_threads != 128 && p->inst_threads != 256 && p->inst_threads != 512 &&
-         p->inst_threads != 1024))
+         p->inst_threads != 1024) ||
+        (p->test_withhold != 0 && p->test_withhold != 1))
         return set_err(c, TTIE_ERR_INVALID, "numeric parameter out of range");
     return TTIE_OK;
 }
@@ -134,6 +135,7 @@ void ttie_default_params(ttie_params *p) {
     p->max_step = 1.0;
     p->max_candidates = 0;
     p->inst_threads = 0;
+    p->test_withhold = 0;
 }
 
 ttie_status ttie_create(ttie_ctx **out, const ttie_params *p, void *stream) {

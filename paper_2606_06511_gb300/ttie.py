@@ -42,7 +42,7 @@ class Params(ctypes.Structure):
                 ("pcg_max_it", ctypes.c_int), ("newton_max_it", ctypes.c_int), ("ls_max_halvings", ctypes.c_int),
                 ("armijo_c", ctypes.c_double), ("push_eta", ctypes.c_double), ("exact_only", ctypes.c_int),
                 ("profile", ctypes.c_int), ("max_step", ctypes.c_double), ("max_candidates", ctypes.c_int64),
-                ("inst_threads", ctypes.c_int)]
+                ("inst_threads", ctypes.c_int), ("test_withhold", ctypes.c_int)]
 
 
 class BsrView(ctypes.Structure):

@@ -346,3 +346,27 @@ def test_hash_candidates_match_lbvh_full_size(ttie):
         c = ctx.get_candidates().cpu().numpy().astype(np.int64)
         sets.append(np.sort(c[:, 0] * m.F + c[:, 1]))
     assert len(sets[0]) > 600000 and np.array_equal(sets[0], sets[1])
+
+
+def test_pcg_wait_runs_out_and_context_stays_usable(ttie):
+    """Failure path of the block-resident PCG, without a GPU fault: with the test switch set,
+    block 0 never publishes its partial sums, every block's wait for them runs out after about a
+    second (a bound on elapsed time), the kernel returns and the call reports TTIE_ERR_CUDA; the
+    same context then solves the same system normally."""
+    import time
+    m, mode = CASES["cloth40"]
+    x, tri, grp = _dev(m)
+    ctx = _ctx(ttie, mode)
+    ctx.build_bvh(x, tri, grp)
+    ctx.eval_pairs(x, ttie.EVAL_E | ttie.EVAL_H)
+    bsr = ctx.assemble()
+    rhs = (-bsr.grad).contiguous()
+    ctx.set_params(test_withhold=1)
+    t0 = time.time()
+    with pytest.raises(ttie.TTIEError) as e:
+        ctx.pcg(rhs, rtol=1e-6, max_it=50)
+    assert e.value.status == ttie.TTIE_ERR_CUDA
+    assert time.time() - t0 < 20.0
+    ctx.set_params(test_withhold=0)
+    d, iters, rel = ctx.pcg(rhs, rtol=1e-4, max_it=5000)
+    assert rel <= 1e-4 and torch.isfinite(d).all()
