@@ -508,11 +508,12 @@ __global__ void k_pcg_setup(const int32_t *__restrict__ row_ptr, const int32_t *
 }
 
 // ---------------------------------------------------------------- persistent PCG
-// All PCG iterations in one cooperative launch (every block resident).  Blocks meet at
-// a grid barrier three times per iteration; each wait is bounded and, when it runs out,
-// sets ERR_BARRIER and the kernel returns.  Reductions: block partials, then every block
-// sums all partials in the same order, so all blocks take the same decisions and the
-// result does not depend on timing.
+// All PCG iterations in one cooperative launch (every block resident), for systems whose rows
+// do not fit the block-resident kernels.  Blocks meet at a grid reduction twice per iteration
+// (p.q, then r.z and r.r); each wait is bounded and, when it runs out, sets ERR_BARRIER and
+// the kernel returns.  Reductions: block partials, then the last block to arrive sums them in
+// block order and publishes the totals, so all blocks take the same decisions and the result
+// does not depend on timing.
 // Every wait of the PCG kernels gives up after kWaitNs of elapsed time (the GPU's global
 // timer, read every 64 polls), so a block that never arrives ends the others' waits, and the
 // launch, with ERR_BARRIER in about a second.
