@@ -218,6 +218,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-form", action="store_true", help="skip the plain FP64 comparison")
     ap.add_argument("--no-quasi-static", action="store_true", help="skip the quasi-static simulation run")
+    ap.add_argument("--no-next-rows", action="store_true",
+                    help="skip the timings of the PSD variants, the exact Hessian-vector product and the dual evaluator")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -424,6 +426,48 @@ def main():
               "max_edge_strain": strain, "runs": 5}
         cq.close()
 
+    # the rows beyond the step: a Newton step under each PSD projection of §1.1, the exact
+    # Hessian-vector product and the FP64 dual-number gradient pass, on this workload at x0
+    nxt = None
+    if rank == 0 and not args.no_next_rows and mode != 2:
+        def med(fn, k=5):
+            ts = []
+            for _ in range(k):
+                flush.zero_()
+                ev0.record(stream)
+                r = fn()
+                ev1.record(stream)
+                ev1.synchronize()
+                ts.append(ev0.elapsed_time(ev1))
+            return sorted(ts)[k // 2], r
+        nxt = {"psd_modes": {}}
+        for name, pm in (("per_part", ttie.PSD_PER_PART), ("drop_cross", ttie.PSD_DROP_CROSS),
+                         ("whole", ttie.PSD_WHOLE)):
+            cp = ttie.Context(precision=precision, pair_mode=mode, psd_mode=pm)
+            cp.build_bvh(x0, tri, grp)
+            xs = x0.clone()
+            cp.newton_step(xs)   # warm-up (allocations)
+            def one():
+                xs.copy_(x0)
+                return cp.newton_step(xs)
+            ms, inf = med(one)
+            nxt["psd_modes"][name] = {"ms_per_step": ms, "pcg_iters": inf["pcg_iters"],
+                                      "energy_ratio": inf["energy_new"] / inf["energy"] if inf["energy"] else None,
+                                      "alpha": inf["alpha"]}
+            cp.close()
+        cx = ttie.Context(precision=precision, pair_mode=mode)
+        cx.build_bvh(x0, tri, grp)
+        _, n_act0 = cx.eval_pairs(x0, ttie.EVAL_E | ttie.EVAL_H)
+        vv = torch.randn_like(x0)
+        ms_hx, _ = med(lambda: cx.hvp(x0, vv, exact=True))
+        ms_hp, _ = med(lambda: cx.hvp(x0, vv, exact=False))
+        cx.eval_pairs(x0, ttie.EVAL_E | ttie.EVAL_H)
+        ms_du, _ = med(lambda: cx.dual_gradients(x0))
+        nxt["hvp_exact_ms"] = ms_hx
+        nxt["hvp_psd_ms"] = ms_hp
+        nxt["dual_gradients"] = {"ms": ms_du, "pairs": n_act0, "pairs_per_s": n_act0 / (ms_du / 1e3)}
+        cx.close()
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline(m, mode)
@@ -455,6 +499,7 @@ def main():
             "clocks": clk,
             "time_to_intersection_free": solve,
             "quasi_static": qs,
+            "next_rows": nxt,
         }
         print(json.dumps(line), flush=True)
     ctx.close()
