@@ -334,6 +334,14 @@ def main():
     roofline_pairs = {"kernel": "k_classify", "bound": "hbm", "achieved": cl_ach, "peak": peak, "unit": "GB/s",
                       "peak_source": "measured" if hbm else "fallback", "frac": cl_ach / peak if cl_ach else None,
                       "traffic": NCU_TRAFFIC.get(args.workload, {}).get("k_classify"), "ms_per_launch": k_ms, "algorithmic_bytes_per_launch": 104.0 * n_cand}
+    # the assembly stage as a whole (its sort passes, kernels and two host reads of sizes):
+    # 36 block keys of 8 B and 36 block values of 36 B per intersecting pair
+    asm_ms = stage["assemble"] / args.steps
+    asm_bytes = 1584.0 * last["n_active"]
+    asm_ach = asm_bytes / (asm_ms / 1e3) / 1e9 if asm_ms > 0 else None
+    roofline_asm = {"stage": "assemble", "bound": "hbm", "achieved": asm_ach, "peak": peak, "unit": "GB/s",
+                    "peak_source": "measured" if hbm else "fallback", "frac": asm_ach / peak if asm_ach else None,
+                    "ms_per_step": asm_ms, "algorithmic_bytes_per_step": asm_bytes}
 
     # the plain FP64 form on the same GPU: every stage in double precision (same kernels
     # instantiated for FP64), a few steps of the same workload
@@ -489,6 +497,7 @@ def main():
             "active_pairs_per_s": active / (total_ms / 1e3),
             "roofline": roofline,
             "roofline_pair_eval": roofline_pairs,
+            "roofline_assembly": roofline_asm,
             "cpu_baseline": cpu,
             "fp64_form": fp64,
             "broad_phase_ms": broad,
