@@ -456,7 +456,7 @@ cudaError_t build_candidates(Ctx &c, const vec4_t<T> *x0, const vec4_t<T> *x1, B
         launch(c, k_morton<T>, dim3(g), dim3(kThreads), tbox, n, (const int32_t *)c.grp.p, gbits, c.ds, key, perm);
         TTIE_CUDA_TRY(cudaGetLastError());
         const int key_bits = 3 * ((63 - gbits) / 3) + gbits;
-        TTIE_CUDA_TRY(radix_sort(c, key, perm, (unsigned long long *)c.mkey2.p, (uint32_t *)c.perm2.p, n, key_bits));
+        TTIE_CUDA_TRY(radix_sort_graph(c, key, perm, (unsigned long long *)c.mkey2.p, (uint32_t *)c.perm2.p, n, key_bits));
         if (grouped) {
             launch(c, k_leaf_group, dim3(g), dim3(kThreads), perm, (const int32_t *)c.grp.p, n, (int32_t *)c.leaf_group.p);
             launch(c, k_fill_int2, dim3(grid_for(c.n_groups, kThreads)), dim3(kThreads), (int2 *)c.group_range.p,

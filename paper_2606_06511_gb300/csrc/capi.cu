@@ -185,6 +185,7 @@ void ttie_destroy(ttie_ctx *h) {
         if (c.aux[i]) cudaStreamDestroy(c.aux[i]);
     for (int i = 0; i <= kInstBuckets; ++i)
         if (c.aux_ev[i]) cudaEventDestroy(c.aux_ev[i]);
+    if (c.sort_exec) cudaGraphExecDestroy(c.sort_exec);
     if (c.cap_stream) cudaStreamDestroy(c.cap_stream);
     delete h;
 }

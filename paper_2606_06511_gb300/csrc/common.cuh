@@ -167,6 +167,13 @@ struct Ctx {
     bool have_elastic = false;
     int64_t el_n_edges = 0, el_n_anchors = 0, el_V = -1;
     int el_prec = 0;
+    // the Morton sort of a full LBVH build, captured once as a graph and replayed while its
+    // arguments and scratch buffers stay the same
+    cudaGraphExec_t sort_exec = nullptr;
+    const void *sort_key[7] = {};       // keys, vals, keys2, vals2, count and scan scratch, (n, bits)
+    long long sort_n = -1;
+    int sort_bits = -1;
+    unsigned long long sort_kernels = 0;
     double el_k = 0.0, el_ka = 0.0;
 };
 
@@ -212,6 +219,9 @@ cudaError_t scan_u32_u64(Ctx &c, const uint32_t *in, unsigned long long *out, in
 // left in keys/vals; keys2/vals2 are scratch of the same size.
 cudaError_t radix_sort(Ctx &c, unsigned long long *keys, uint32_t *vals, unsigned long long *keys2,
                        uint32_t *vals2, int64_t n, int bits);
+// The same sort replayed from a graph captured on the first call with these arguments.
+cudaError_t radix_sort_graph(Ctx &c, unsigned long long *keys, uint32_t *vals, unsigned long long *keys2,
+                             uint32_t *vals2, int64_t n, int bits);
 
 // ------------------------------------------------------------------ broad phase (bvh.cu)
 template <typename T> cudaError_t pack_positions(Ctx &c, const T *x, int stride, vec4_t<T> *out);

@@ -227,3 +227,60 @@ cudaError_t radix_sort(Ctx &c, unsigned long long *keys, uint32_t *vals, unsigne
 }
 
 }  // namespace ttie
+
+namespace ttie {
+
+// radix_sort replayed from a graph: 5 launches per 8-bit pass (63-bit Morton keys: 40) become one
+// graph launch.  Captured on the context's capture stream on the first call, and again whenever
+// an argument or a scratch buffer changes (the graph holds their addresses); every buffer is
+// sized before the capture, so nothing is allocated inside it.
+cudaError_t radix_sort_graph(Ctx &c, unsigned long long *keys, uint32_t *vals, unsigned long long *keys2,
+                             uint32_t *vals2, int64_t n, int bits) {
+#ifdef TTIE_CHECKS
+    return radix_sort(c, keys, vals, keys2, vals2, n, bits);   // checked builds synchronise after every launch
+#endif
+    if (n <= 1 || bits <= 0) return cudaSuccess;
+    const int64_t n_tiles = (n + kTile - 1) / kTile;
+    const int64_t n_cnt = n_tiles * kRadix;
+    TTIE_CUDA_TRY(ensure(c, c.sort_cnt, (size_t)n_cnt * sizeof(uint32_t) + (size_t)(n_cnt + 1) * sizeof(unsigned long long)));
+    TTIE_CUDA_TRY(ensure(c, c.scan_tmp, (size_t)((n_cnt + kTile - 1) / kTile + 1) * sizeof(unsigned long long)));
+    const void *key[6] = {keys, vals, keys2, vals2, c.sort_cnt.p, c.scan_tmp.p};
+    bool same = c.sort_exec && c.sort_n == n && c.sort_bits == bits;
+    for (int i = 0; i < 6; ++i) same = same && c.sort_key[i] == key[i];
+    if (!same) {
+        if (c.sort_exec) {
+            cudaGraphExecDestroy(c.sort_exec);
+            c.sort_exec = nullptr;
+        }
+        if (!c.cap_stream) TTIE_CUDA_TRY(cudaStreamCreateWithFlags(&c.cap_stream, cudaStreamNonBlocking));
+        const cudaStream_t main_stream = c.stream;
+        c.stream = c.cap_stream;
+        cudaError_t e = cudaStreamBeginCapture(c.stream, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) {
+            c.stream = main_stream;
+            return e;
+        }
+        const unsigned long long launches0 = c.n_launch;
+        e = radix_sort(c, keys, vals, keys2, vals2, n, bits);
+        cudaGraph_t graph = nullptr;
+        const cudaError_t ec = cudaStreamEndCapture(c.stream, &graph);
+        c.stream = main_stream;
+        c.sort_kernels = c.n_launch - launches0;
+        c.n_launch = launches0;   // captured, not launched: every replay counts them
+        if (e == cudaSuccess) e = ec;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&c.sort_exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            c.sort_exec = nullptr;
+            return e;
+        }
+        for (int i = 0; i < 6; ++i) c.sort_key[i] = key[i];
+        c.sort_n = n;
+        c.sort_bits = bits;
+    }
+    TTIE_CUDA_TRY(cudaGraphLaunch(c.sort_exec, c.stream));
+    c.n_launch += c.sort_kernels;
+    return cudaSuccess;
+}
+
+}  // namespace ttie
