@@ -36,6 +36,8 @@ def test_default_params(lib):
     p = ttie.default_params()
     assert p.precision == ttie.F32 and p.pair_mode == ttie.PAIRS_SELF and p.psd_mode == ttie.PSD_PER_PART
     assert p.tc_scale == 1.0 and p.mu_rel == 1e-3 and p.push_eta == 0.5 and p.exact_only == 0
+    # the fields appended last come back from the library's defaults: the binding's layout matches
+    assert p.max_step == 1.0 and p.max_candidates == 0 and p.inst_threads == 0 and p.test_withhold == 0
 
 
 def test_null_context_is_rejected(lib):
@@ -46,6 +48,7 @@ def test_null_context_is_rejected(lib):
     assert lib.ttie_newton_step(None, None, None) == ttie.TTIE_ERR_INVALID
     assert lib.ttie_last_error(None) == b"null context"
     assert lib.ttie_create(None, None, None) == ttie.TTIE_ERR_INVALID
+    assert lib.ttie_set_elastic(None, None) == ttie.TTIE_ERR_INVALID
 
 
 def test_bad_params_rejected_before_device(lib):
@@ -56,6 +59,10 @@ def test_bad_params_rejected_before_device(lib):
     p = ttie.default_params(pair_mode=3)
     assert lib.ttie_create(ctypes.byref(h), ctypes.byref(p), None) == ttie.TTIE_ERR_INVALID
     p = ttie.default_params(tc_scale=-1.0)
+    assert lib.ttie_create(ctypes.byref(h), ctypes.byref(p), None) == ttie.TTIE_ERR_INVALID
+    p = ttie.default_params(inst_threads=100)
+    assert lib.ttie_create(ctypes.byref(h), ctypes.byref(p), None) == ttie.TTIE_ERR_INVALID
+    p = ttie.default_params(test_withhold=2)
     assert lib.ttie_create(ctypes.byref(h), ctypes.byref(p), None) == ttie.TTIE_ERR_INVALID
 
 
