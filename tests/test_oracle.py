@@ -624,3 +624,15 @@ def test_newton_direction_elastic_solves_system():
     r = (H + mu * np.eye(len(H))) @ d[rows].ravel() + grad[rows].ravel()
     assert np.linalg.norm(r) <= 1e-9 * np.linalg.norm(grad)
     assert np.sum(grad * d) < 0
+
+
+def test_zero_length_spring():
+    """A spring whose ends coincide has no direction: its gradient is 0 and its Hessian block the
+    limit k I of the stretched case along any direction (the energy is k/2 L^2 there)."""
+    k, L = 2.0, 0.3
+    x = np.array([[0.5, -0.2, 1.0], [0.5, -0.2, 1.0]])
+    el = O.Elastic(np.array([[0, 1]]), np.array([L]), k)
+    assert O.elastic_energy(x, el) == pytest.approx(0.5 * k * L * L, rel=1e-14)
+    assert not O.elastic_gradient(x, el).any()
+    H = O.spring_hessian(x[0], x[1], L, k)
+    assert np.array_equal(H[:3, :3], k * np.eye(3)) and np.array_equal(H[:3, 3:], -k * np.eye(3))
