@@ -102,14 +102,31 @@ typedef struct {
                              publishes its partial sums, so every block's bounded wait for
                              them runs out (about a second) and the call returns
                              TTIE_ERR_CUDA with the context still usable               */
+    int pcg_precond;      /* preconditioner of the shared-memory PCG (TTIE_PCG_*); the
+                             global-memory PCG and the batched-instance PCG always use
+                             3x3 block Jacobi                                          */
+    int pcg_cheb_degree;  /* TTIE_PCG_CHEBYSHEV: degree k of the polynomial, 1..8 (0 = 2) */
 } ttie_params;
+
+/* PCG preconditioners.
+ * BLOCK_JACOBI: M^-1 = D^-1, the inverses of the 3x3 diagonal blocks of H+ + mu I.
+ * CHEBYSHEV:    after 6 block-Jacobi iterations, lambda_max of D^-1 (H+ + mu I) is
+ *               estimated from the Lanczos tridiagonal of those iterations' alpha and beta
+ *               (times 1.1), and CG restarts from the current x with M^-1 = p_k(D^-1 A) D^-1,
+ *               the Chebyshev iteration polynomial of degree k on [lambda_max / 10,
+ *               lambda_max]: k extra products per iteration, no extra reduction.  An even k
+ *               keeps M^-1 positive definite whatever the estimate; with an odd k a
+ *               lambda_max above the estimate can make it indefinite, which ends the solve
+ *               at the breakdown test with the iterate so far.                           */
+enum { TTIE_PCG_BLOCK_JACOBI = 0, TTIE_PCG_CHEBYSHEV = 1 };
 
 typedef struct ttie_ctx ttie_ctx;
 
 /* Fills *p with the defaults: F32, SELF, PER_PART, tc_scale 1, mu_rel 1e-3,
  * pcg_rtol 1e-3, pcg_max_it 200, newton_max_it 200, ls_max_halvings 20,
  * armijo_c 1e-4, push_eta 0.5, exact_only 0, profile 0, max_step 1,
- * max_candidates 0, inst_threads 0, test_withhold 0. */
+ * max_candidates 0, inst_threads 0, test_withhold 0, pcg_precond BLOCK_JACOBI,
+ * pcg_cheb_degree 0. */
 void ttie_default_params(ttie_params *p);
 
 /* Creates a context on the current CUDA device.  stream: a cudaStream_t or NULL

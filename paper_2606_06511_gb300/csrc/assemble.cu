@@ -613,6 +613,8 @@ template <typename T> struct PcgArgs {
     const T *dinv;
     T *x, *r, *z, *p, *q;
     vec4_t<T> *z4;           // z mirrored as one tagged 16/32-byte vector per row (resident kernel)
+    vec4_t<T> *z4b;          // resident kernel with the Chebyshev preconditioner: odd publications
+    int cheb_degree;         // degree of the Chebyshev preconditioner (that kernel only)
     double *partA, *partB;
     RedSlot *slots;          // resident kernel: 2 x kMaxGridPcg tagged reduction slots, then 2 total slots
     const int *part;         // resident kernel: rows of block b are part[b] .. part[b + 1]
@@ -958,15 +960,17 @@ template <typename T> struct ResidentView {
     T *val;                           // matrix rows (9 per block) when cached
     int *col;                         // their columns when cached
     T *gu;                            // u at each block's column (3 per block) when gathered
+    T *d, *rr;                        // Chebyshev preconditioner: direction and D^-1 residual (3 each)
     bool cached, gathered;
     int nrow, nnz, b_begin;
 };
 
-// w = (A + mu I) u on the block's rows, u of other rows read from the mirror with tag t;
-// returns the rows' w.u.  A load that never sees tag t sets *bad.
+// w = (A + mu I) u on the block's rows, u of every row read from the published vectors src
+// with tag t (loc: the block's own rows of u, for the shift); returns the rows' w.u.  A load
+// that never sees tag t sets *bad.
 template <typename T>
-__device__ __forceinline__ Acc<T> resident_product(const PcgArgs<T> &a, const ResidentView<T> &v, T mu, unsigned t,
-                                                   int *bad) {
+__device__ __forceinline__ Acc<T> resident_product(const PcgArgs<T> &a, const ResidentView<T> &v,
+                                                   const vec4_t<T> *src, const T *loc, T mu, unsigned t, int *bad) {
     if (v.gathered) {
         // gather every block's column vector first: all loads of a thread in flight together
         // words not yet tagged t are loaded again, all of a thread's together
@@ -978,7 +982,7 @@ __device__ __forceinline__ Acc<T> resident_product(const PcgArgs<T> &a, const Re
             for (int k = 0; k < U; ++k) {
                 const int j = j0 + k * kPcgThreads;
                 if (j < v.nnz) {
-                    g[k] = ld_row<T>(&a.z4[v.col[j]]);
+                    g[k] = ld_row<T>(&src[v.col[j]]);
                     pend |= 1u << k;
                 }
             }
@@ -995,7 +999,7 @@ __device__ __forceinline__ Acc<T> resident_product(const PcgArgs<T> &a, const Re
                 if (wc.out() || *(volatile int *)bad) { *bad = 1; break; }
 #pragma unroll
                 for (int k = 0; k < U; ++k)
-                    if (pend >> k & 1u) g[k] = ld_row<T>(&a.z4[v.col[j0 + k * kPcgThreads]]);
+                    if (pend >> k & 1u) g[k] = ld_row<T>(&src[v.col[j0 + k * kPcgThreads]]);
             }
         }
         __syncthreads();
@@ -1033,11 +1037,11 @@ __device__ __forceinline__ Acc<T> resident_product(const PcgArgs<T> &a, const Re
                 vec4_t<T> g[U];
 #pragma unroll
                 for (int k = 0; k < U; ++k)
-                    if (cc[k] >= 0) g[k] = ld_row<T>(&a.z4[cc[k]]);
+                    if (cc[k] >= 0) g[k] = ld_row<T>(&src[cc[k]]);
 #pragma unroll
                 for (int k = 0; k < U; ++k)
                     if (cc[k] >= 0) {
-                        settle_row<T>(g[k], &a.z4[cc[k]], t, bad);
+                        settle_row<T>(g[k], &src[cc[k]], t, bad);
                         const int b = b0 + k * kLanesPerRow;
                         const T *m = v.cached ? v.val + (size_t)b * 9 : a.bval + (size_t)(v.b_begin + b) * 9;
                         block_times(m, g[k].x, g[k].y, g[k].z, y0, y1, y2);
@@ -1051,17 +1055,80 @@ __device__ __forceinline__ Acc<T> resident_product(const PcgArgs<T> &a, const Re
             y2 += __shfl_xor_sync(gmask, y2, o, kLanesPerRow);
         }
         if (sub == 0) {
-            const T w0 = y0 + mu * v.u[lr * 3], w1 = y1 + mu * v.u[lr * 3 + 1], w2 = y2 + mu * v.u[lr * 3 + 2];
+            const T w0 = y0 + mu * loc[lr * 3], w1 = y1 + mu * loc[lr * 3 + 1], w2 = y2 + mu * loc[lr * 3 + 2];
             v.w[lr * 3] = w0; v.w[lr * 3 + 1] = w1; v.w[lr * 3 + 2] = w2;
-            wu.add_prod(w0, v.u[lr * 3]);
-            wu.add_prod(w1, v.u[lr * 3 + 1]);
-            wu.add_prod(w2, v.u[lr * 3 + 2]);
+            wu.add_prod(w0, loc[lr * 3]);
+            wu.add_prod(w1, loc[lr * 3 + 1]);
+            wu.add_prod(w2, loc[lr * 3 + 2]);
         }
     }
     return wu;
 }
 
+// Chebyshev preconditioner (TTIE_PCG_CHEBYSHEV): block-Jacobi iterations before the estimate
+// of lambda_max(D^-1 A), the margin on that estimate, lambda_max / lambda_min of the interval
+// and the largest degree.
+constexpr int kChebWarm = 6;
+constexpr double kChebSafety = 1.1;
+constexpr double kChebRatio = 10.0;
+constexpr int kChebMaxDeg = 8;
+
+// Eigenvalues below x of the symmetric tridiagonal (diagonal dg, squared off-diagonal e2):
+// the number of negative pivots of its LDL^T factorisation shifted by x (Sturm sequence).
+__device__ __forceinline__ int sturm_below(const double *dg, const double *e2, int m, double x) {
+    int below = 0;
+    double q = 1.0;
+    for (int i = 0; i < m; ++i) {
+        q = dg[i] - x - (i ? e2[i - 1] / q : 0.0);
+        if (q == 0.0) q = 1e-300;
+        below += q < 0.0;
+    }
+    return below;
+}
+
+// From the first kChebWarm CG coefficients (al[j], be[j]: alpha and beta of iteration j; be[0]
+// unused), the Lanczos tridiagonal of D^-1 A: diagonal 1/al[j] + be[j]/al[j-1], off-diagonal
+// sqrt(be[j+1])/al[j].  Its largest eigenvalue (a lower bound of lambda_max, by bisection on
+// the Sturm count from its Gershgorin bound) times kChebSafety is the interval's top; the
+// Chebyshev iteration y = p_k(D^-1 A) D^-1 v on [top / kChebRatio, top] then runs
+//   rr = D^-1 v,  d = rr / theta,  y = d;  for j < k: rr -= D^-1 A d,
+//   d = c1[j] d + c2[j] rr,  y += d
+// with theta, delta the interval's centre and half-width, sigma = theta / delta,
+// rho_0 = 1 / sigma, rho_{j+1} = 1 / (2 sigma - rho_j), c1[j] = rho_{j+1} rho_j and
+// c2[j] = 2 rho_{j+1} / delta.  Same inputs in every block, same coefficients.  False (keep
+// block Jacobi) when a coefficient is not positive and finite.
 template <typename T>
+__device__ __noinline__ bool cheb_coefficients(const double *al, const double *be, int deg, T *c1, T *c2, T *theta_inv) {
+    double dg[kChebWarm], e2[kChebWarm];
+    for (int j = 0; j < kChebWarm; ++j) {
+        if (!(al[j] > 0.0) || !isfinite(al[j]) || (j > 0 && (!(be[j] > 0.0) || !isfinite(be[j])))) return false;
+        dg[j] = 1.0 / al[j] + (j ? be[j] / al[j - 1] : 0.0);
+        if (j > 0) e2[j - 1] = be[j] / (al[j - 1] * al[j - 1]);
+    }
+    double hi = 0.0;
+    for (int i = 0; i < kChebWarm; ++i)
+        hi = fmax(hi, dg[i] + (i ? sqrt(e2[i - 1]) : 0.0) + (i + 1 < kChebWarm ? sqrt(e2[i]) : 0.0));
+    if (!(hi > 0.0) || !isfinite(hi)) return false;
+    double lo = 0.0;
+    for (int s = 0; s < 60; ++s) {
+        const double mid = 0.5 * (lo + hi);
+        if (sturm_below(dg, e2, kChebWarm, mid) < kChebWarm) lo = mid;
+        else hi = mid;
+    }
+    const double top = hi * kChebSafety, bot = top / kChebRatio;
+    const double th = 0.5 * (top + bot), de = 0.5 * (top - bot), sig = th / de;
+    double rho = 1.0 / sig;
+    for (int j = 0; j < deg; ++j) {
+        const double rn = 1.0 / (2.0 * sig - rho);
+        c1[j] = (T)(rn * rho);
+        c2[j] = (T)(2.0 * rn / de);
+        rho = rn;
+    }
+    *theta_inv = (T)(1.0 / th);
+    return true;
+}
+
+template <typename T, bool kCheb>
 __global__ void __launch_bounds__(kPcgThreads) k_pcg_resident(PcgArgs<T> a, int smem_bytes) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ T s_alpha, s_beta;
@@ -1075,14 +1142,17 @@ __global__ void __launch_bounds__(kPcgThreads) k_pcg_resident(PcgArgs<T> a, int 
     const auto vec_size = [](int rows, int per_row) {
         return ((size_t)rows * per_row * sizeof(T) + (size_t)(rows + 1) * sizeof(int) + 15) / 16 * 16;
     };
-    if (!(row0 >= 0 && v.nrow >= 0 && row0 + v.nrow <= nr && vec_size(v.nrow, 15) <= (size_t)smem_bytes)) {
+    // the Chebyshev preconditioner's d and rr, after the other vectors
+    const auto cheb_size = [](int rows) { return kCheb ? ((size_t)rows * 6 * sizeof(T) + 15) / 16 * 16 : (size_t)0; };
+    if (!(row0 >= 0 && v.nrow >= 0 && row0 + v.nrow <= nr &&
+          vec_size(v.nrow, 15) + cheb_size(v.nrow) <= (size_t)smem_bytes)) {
         partition_fail(ds, 45);   // checked in every build: the rows index shared memory
         v.nrow = 0;
     }
     const int R = v.nrow;
     // lean: x and the inverse diagonal blocks (read or written once per row and iteration) stay
     // in global memory so that larger row ranges fit
-    const bool lean = vec_size(R, 27) > (size_t)smem_bytes;
+    const bool lean = vec_size(R, 27) + cheb_size(R) > (size_t)smem_bytes;
     size_t vec_bytes;
     if (lean) {
         v.r = (T *)smem; v.u = v.r + 3 * R; v.p = v.u + 3 * R; v.s = v.p + 3 * R; v.w = v.s + 3 * R;
@@ -1095,6 +1165,11 @@ __global__ void __launch_bounds__(kPcgThreads) k_pcg_resident(PcgArgs<T> a, int 
         v.di = v.w + 3 * R;
         v.rp = (int *)(v.di + 9 * R);
         vec_bytes = vec_size(R, 27);
+    }
+    if constexpr (kCheb) {
+        v.d = (T *)(smem + vec_bytes);
+        v.rr = v.d + 3 * R;
+        vec_bytes += cheb_size(R);
     }
     v.b_begin = v.nrow ? a.row_ptr[row0] : 0;
     v.nnz = v.nrow ? a.row_ptr[row0 + v.nrow] - v.b_begin : 0;
@@ -1144,6 +1219,17 @@ __global__ void __launch_bounds__(kPcgThreads) k_pcg_resident(PcgArgs<T> a, int 
     const T rtol2 = (T)a.rtol2;
     bool stop_next = false;
     int it = 0;
+    // Chebyshev preconditioner: kit counts the iterations since CG (re)started, pub the
+    // published vectors (the setup kernel's u is publication 0).  Publication q goes to z4
+    // when q is even and to z4b when odd, tagged q mod 4: a block publishes q + 1 only after
+    // it has read q of every block it shares a matrix block with, so a reader of q finds q,
+    // q - 2 (other tag) or, first, z4b's zeros (tag 0, never an odd publication's).
+    int kit = 0;
+    unsigned pub = 0;
+    bool cheb_on = false, cheb_tried = false;
+    __shared__ T s_c1[kChebMaxDeg], s_c2[kChebMaxDeg], s_thi;
+    __shared__ double s_al[kChebWarm], s_be[kChebWarm];
+    __shared__ int s_restart;
     auto decide = [&](const Acc<T> *t) {
         gamma = t[0];
         rr = t[2];
@@ -1153,7 +1239,7 @@ __global__ void __launch_bounds__(kPcgThreads) k_pcg_resident(PcgArgs<T> a, int 
         T alpha = T(0), beta = T(0);
         if (!stop) {
             bool ok;
-            if (it == 0) {
+            if ((kCheb ? kit : it) == 0) {
                 alpha = g / d;
                 ok = d > T(0) && isfinite(alpha);
             } else {
@@ -1170,18 +1256,81 @@ __global__ void __launch_bounds__(kPcgThreads) k_pcg_resident(PcgArgs<T> a, int 
                 stop_next = true;
             }
         }
+        if constexpr (kCheb) {
+            // the block-Jacobi iterations' coefficients; after the last of them the Chebyshev
+            // polynomial's, and CG restarts with it (unless they are unusable)
+            s_restart = 0;
+            if (!stop && !stop_next && !cheb_tried && kit < kChebWarm) {
+                s_al[kit] = (double)alpha;
+                s_be[kit] = (double)beta;
+                if (kit == kChebWarm - 1) {
+                    cheb_tried = true;
+                    s_restart = cheb_coefficients<T>(s_al, s_be, a.cheb_degree, s_c1, s_c2, &s_thi) ? 1 : 0;
+                }
+            }
+        }
         gamma_prev = g;
         alpha_prev = alpha;
         s_alpha = alpha;
         s_beta = beta;
         s_stop = stop;
     };
+    // jstep (Chebyshev): 0 when the next product is w = A u of an iteration, j + 1 when it is
+    // the product of the polynomial's j-th direction
+    int jstep = 0;
     while (true) {
-        Acc<T> red[3] = {gl, resident_product(a, v, mu, (unsigned)it & 3u, &s_bad), rl};
+        const bool inner = kCheb && jstep > 0;
+        const vec4_t<T> *src = (kCheb && (pub & 1u)) ? a.z4b : a.z4;
+        const unsigned tu = kCheb ? (pub & 3u) : ((unsigned)it & 3u);
+        const Acc<T> wu = resident_product(a, v, src, inner ? v.d : v.u, mu, tu, &s_bad);
+        if (inner) {
+            // the polynomial's next step: rr -= D^-1 (A + mu I) d, d = c1 d + c2 rr, y += d;
+            // each d but the last published for the next product, then u = y
+            __syncthreads();
+            const int j = jstep - 1;
+            const bool last = j + 1 == a.cheb_degree;
+            const T c1 = s_c1[j], c2 = s_c2[j];
+            const unsigned tq = (pub + 1u) & 3u;
+            vec4_t<T> *dq = ((pub + 1u) & 1u) ? a.z4b : a.z4;
+            for (int lr = threadIdx.x; lr < v.nrow; lr += blockDim.x) {
+                const T *di = v.di + lr * 9;
+                const T w0 = v.w[lr * 3], w1 = v.w[lr * 3 + 1], w2 = v.w[lr * 3 + 2];
+                T o[3];
+#pragma unroll
+                for (int i = 0; i < 3; ++i) {
+                    const int k = lr * 3 + i;
+                    const T rri = v.rr[k] - (di[3 * i] * w0 + di[3 * i + 1] * w1 + di[3 * i + 2] * w2);
+                    v.rr[k] = rri;
+                    const T dn = c1 * v.d[k] + c2 * rri;
+                    if (!last) {
+                        o[i] = tag_word(dn, tq);
+                        v.d[k] = o[i];
+                        v.u[k] += o[i];
+                    } else {
+                        o[i] = tag_word(v.u[k] + dn, tq);
+                        v.u[k] = o[i];
+                        gl.add_prod(v.r[k], o[i]);
+                    }
+                }
+                vec4_t<T> ov;
+                ov.x = o[0]; ov.y = o[1]; ov.z = o[2]; ov.w = T(0);
+                st_row<T>(&dq[row0 + lr], ov);
+            }
+            ++pub;
+            jstep = last ? 0 : jstep + 1;
+            __syncthreads();
+            continue;
+        }
+        Acc<T> red[3] = {gl, wu, rl};
         if (!slot_allreduce<3, T>(red, a.slots, (unsigned)it, &s_bad, a.withhold && blockIdx.x == 0, ds, decide)) return;
         if (s_stop) break;
         const T al = s_alpha, be = s_beta;
-        const unsigned tn = (unsigned)(it + 1) & 3u;
+        // with the Chebyshev preconditioner (from the restart on) the update publishes the
+        // polynomial's first direction d = D^-1 r / theta instead of u
+        const bool cheb_now = kCheb && (cheb_on || s_restart);
+        const T thi = kCheb ? s_thi : T(0);
+        const unsigned tn = kCheb ? ((pub + 1u) & 3u) : ((unsigned)(it + 1) & 3u);
+        vec4_t<T> *dst = (kCheb && ((pub + 1u) & 1u)) ? a.z4b : a.z4;
         gl = Acc<T>();
         rl = Acc<T>();
         for (int lr = threadIdx.x; lr < v.nrow; lr += blockDim.x) {
@@ -1200,19 +1349,42 @@ __global__ void __launch_bounds__(kPcgThreads) k_pcg_resident(PcgArgs<T> a, int 
             const T *di = v.di + lr * 9;
             vec4_t<T> z4;
             T zv[3];
+            if (!cheb_now) {
 #pragma unroll
-            for (int i = 0; i < 3; ++i) {
-                // the published (tagged) word is the value on every side
-                zv[i] = tag_word(di[3 * i] * rv[0] + di[3 * i + 1] * rv[1] + di[3 * i + 2] * rv[2], tn);
-                v.u[lr * 3 + i] = zv[i];
-                gl.add_prod(rv[i], zv[i]);
-                rl.add_prod(rv[i], rv[i]);
+                for (int i = 0; i < 3; ++i) {
+                    // the published (tagged) word is the value on every side
+                    zv[i] = tag_word(di[3 * i] * rv[0] + di[3 * i + 1] * rv[1] + di[3 * i + 2] * rv[2], tn);
+                    v.u[lr * 3 + i] = zv[i];
+                    gl.add_prod(rv[i], zv[i]);
+                    rl.add_prod(rv[i], rv[i]);
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < 3; ++i) {
+                    const int k = lr * 3 + i;
+                    const T q = di[3 * i] * rv[0] + di[3 * i + 1] * rv[1] + di[3 * i + 2] * rv[2];
+                    v.rr[k] = q;
+                    zv[i] = tag_word(q * thi, tn);
+                    v.d[k] = zv[i];
+                    v.u[k] = zv[i];    // y = d
+                    rl.add_prod(rv[i], rv[i]);
+                }
             }
             z4.x = zv[0]; z4.y = zv[1]; z4.z = zv[2]; z4.w = T(0);
-            st_row<T>(&a.z4[row0 + lr], z4);
+            st_row<T>(&dst[row0 + lr], z4);
         }
         ++it;
         __syncthreads();
+        if constexpr (kCheb) {
+            ++pub;
+            if (cheb_now) {
+                kit = cheb_on ? kit + 1 : 0;   // CG restarts with the polynomial
+                cheb_on = true;
+                jstep = 1;
+            } else {
+                ++kit;
+            }
+        }
     }
     if (!lean)
         for (int i = threadIdx.x; i < 3 * v.nrow; i += blockDim.x) a.x[row0 * 3 + i] = v.x[i];
@@ -1497,8 +1669,16 @@ cudaError_t pcg_solve(Ctx &c, const T *rhs, T *out, double rtol, int max_it) {
     // rows resident in shared memory when every block's vectors fit (lean layout: 15 values
     // per row); blocks are balanced by nnz + kRowWeight * rows within that cap; else the
     // global-memory kernel
-    const int64_t r_cap = ((int64_t)kResidentSmem - 4 - 15) / (15 * (int64_t)sizeof(T) + 4);
+    // (the Chebyshev preconditioner keeps 6 more values per row, rounded up separately)
+    const bool cheb = c.prm.pcg_precond == TTIE_PCG_CHEBYSHEV;
+    const int64_t r_cap = cheb ? ((int64_t)kResidentSmem - 4 - 15 - 15) / (21 * (int64_t)sizeof(T) + 4)
+                               : ((int64_t)kResidentSmem - 4 - 15) / (15 * (int64_t)sizeof(T) + 4);
     const bool resident = (nr + blocks - 1) / blocks <= r_cap;
+    if (cheb && resident) {
+        // odd publications; zeros carry tag 0, which no odd publication has
+        TTIE_CUDA_TRY(ensure(c, c.pcg_z4b, (size_t)(nr > 0 ? nr : 1) * sizeof(vec4_t<T>)));
+        TTIE_CUDA_TRY(cudaMemsetAsync(c.pcg_z4b.p, 0, (size_t)(nr > 0 ? nr : 1) * sizeof(vec4_t<T>), c.stream));
+    }
     RedSlot *slots = (RedSlot *)c.pcg_sync.p;
     int *rpart = (int *)(slots + 2 * kMaxGridPcg + 2);
     double *part = (double *)c.partials.p;
@@ -1522,6 +1702,8 @@ cudaError_t pcg_solve(Ctx &c, const T *rhs, T *out, double rtol, int max_it) {
     args.p = (T *)c.pcg_p.p;
     args.q = (T *)c.pcg_q.p;
     args.z4 = (vec4_t<T> *)c.pcg_z4.p;
+    args.z4b = cheb && resident ? (vec4_t<T> *)c.pcg_z4b.p : nullptr;
+    args.cheb_degree = c.prm.pcg_cheb_degree > 0 ? c.prm.pcg_cheb_degree : 2;
     args.partA = part;
     args.partB = part + 2 * kNumSMs * 8;
     args.rtol2 = rtol * rtol;
@@ -1533,12 +1715,12 @@ cudaError_t pcg_solve(Ctx &c, const T *rhs, T *out, double rtol, int max_it) {
     ++c.n_launch;
     if (c.prm.profile) cudaEventRecord(c.ev[8], c.stream);
     if (resident) {
-        TTIE_CUDA_TRY(cudaFuncSetAttribute((const void *)k_pcg_resident<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           kResidentSmem));
+        const void *kern = cheb ? (const void *)k_pcg_resident<T, true> : (const void *)k_pcg_resident<T, false>;
+        TTIE_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kResidentSmem));
         int smem = kResidentSmem;
         void *kargs[] = {&args, &smem};
-        TTIE_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)k_pcg_resident<T>, dim3((unsigned)blocks),
-                                                  dim3(kPcgThreads), kargs, (size_t)kResidentSmem, c.stream));
+        TTIE_CUDA_TRY(cudaLaunchCooperativeKernel(kern, dim3((unsigned)blocks), dim3(kPcgThreads), kargs,
+                                                  (size_t)kResidentSmem, c.stream));
     } else {
         void *kargs[] = {&args};
         TTIE_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)k_pcg_persistent<T>, dim3((unsigned)blocks),

@@ -111,7 +111,9 @@ static ttie_status check_params(Ctx &c, const ttie_params *p) {
         !(p->push_eta >= 0.0) || !(p->max_step >= 0.0) || p->max_candidates < 0 ||
         (p->inst_threads != 0 && p->inst_threads != 128 && p->inst_threads != 256 && p->inst_threads != 512 &&
          p->inst_threads != 1024) ||
-        (p->test_withhold != 0 && p->test_withhold != 1))
+        (p->test_withhold != 0 && p->test_withhold != 1) ||
+        (p->pcg_precond != TTIE_PCG_BLOCK_JACOBI && p->pcg_precond != TTIE_PCG_CHEBYSHEV) ||
+        p->pcg_cheb_degree < 0 || p->pcg_cheb_degree > 8)
         return set_err(c, TTIE_ERR_INVALID, "numeric parameter out of range");
     return TTIE_OK;
 }
@@ -136,6 +138,8 @@ void ttie_default_params(ttie_params *p) {
     p->max_candidates = 0;
     p->inst_threads = 0;
     p->test_withhold = 0;
+    p->pcg_precond = TTIE_PCG_BLOCK_JACOBI;
+    p->pcg_cheb_degree = 0;
 }
 
 ttie_status ttie_create(ttie_ctx **out, const ttie_params *p, void *stream) {
