@@ -106,7 +106,17 @@ typedef struct {
                              global-memory PCG and the batched-instance PCG always use
                              3x3 block Jacobi                                          */
     int pcg_cheb_degree;  /* TTIE_PCG_CHEBYSHEV: degree k of the polynomial, 1..8 (0 = 2) */
+    int assembly_mode;    /* TTIE_ASSEMBLY_*: how the 3x3 block-CSR system is assembled;
+                             both give the same pattern and bit-identical values          */
 } ttie_params;
+
+/* Assembly of the block-CSR system (same result either way: each block is the sum of its
+ * entries in the order pair index, then spring, then anchor).
+ * SORTED_KEYS: every entry's (row, column) key radix-sorted, runs summed.
+ * ROW_BUCKETS: the items of each row (a pair's vertex, a spring end, an anchor) bucketed by
+ *              row; one warp per row orders them, finds the distinct columns and sums each
+ *              column's entries in item order (no global sort; one host read).          */
+enum { TTIE_ASSEMBLY_SORTED_KEYS = 0, TTIE_ASSEMBLY_ROW_BUCKETS = 1 };
 
 /* PCG preconditioners.
  * BLOCK_JACOBI: M^-1 = D^-1, the inverses of the 3x3 diagonal blocks of H+ + mu I.
@@ -126,7 +136,7 @@ typedef struct ttie_ctx ttie_ctx;
  * pcg_rtol 1e-3, pcg_max_it 200, newton_max_it 200, ls_max_halvings 20,
  * armijo_c 1e-4, push_eta 0.5, exact_only 0, profile 0, max_step 1,
  * max_candidates 0, inst_threads 0, test_withhold 0, pcg_precond BLOCK_JACOBI,
- * pcg_cheb_degree 0. */
+ * pcg_cheb_degree 0, assembly_mode SORTED_KEYS. */
 void ttie_default_params(ttie_params *p);
 
 /* Creates a context on the current CUDA device.  stream: a cudaStream_t or NULL

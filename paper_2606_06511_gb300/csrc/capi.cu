@@ -113,7 +113,8 @@ static ttie_status check_params(Ctx &c, const ttie_params *p) {
          p->inst_threads != 1024) ||
         (p->test_withhold != 0 && p->test_withhold != 1) ||
         (p->pcg_precond != TTIE_PCG_BLOCK_JACOBI && p->pcg_precond != TTIE_PCG_CHEBYSHEV) ||
-        p->pcg_cheb_degree < 0 || p->pcg_cheb_degree > 8)
+        p->pcg_cheb_degree < 0 || p->pcg_cheb_degree > 8 ||
+        (p->assembly_mode != TTIE_ASSEMBLY_SORTED_KEYS && p->assembly_mode != TTIE_ASSEMBLY_ROW_BUCKETS))
         return set_err(c, TTIE_ERR_INVALID, "numeric parameter out of range");
     return TTIE_OK;
 }
@@ -140,6 +141,7 @@ void ttie_default_params(ttie_params *p) {
     p->test_withhold = 0;
     p->pcg_precond = TTIE_PCG_BLOCK_JACOBI;
     p->pcg_cheb_degree = 0;
+    p->assembly_mode = TTIE_ASSEMBLY_SORTED_KEYS;
 }
 
 ttie_status ttie_create(ttie_ctx **out, const ttie_params *p, void *stream) {

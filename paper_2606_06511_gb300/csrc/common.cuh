@@ -124,7 +124,8 @@ cudaError_t ensure(Ctx &c, Buf &b, size_t bytes);   // grow-only, contents not k
     X(xsave) X(sweep_cand) X(pcg_z4) X(pcg_z4b) X(hbuf) X(pcg_sync) X(spill) X(pcg_w) X(vgroup) X(iedge)  \
     X(el_edges) X(el_rest) X(el_anchor) X(el_target) X(el_sfac) X(el_afac) X(defer2)          \
     X(inst) X(ls_cand) X(inst_acc) X(inst_ids) X(ab) X(ls_flag)  \
-    X(ls_off) X(ls_scalars) X(hgrid) X(hkey) X(hkey2) X(hval) X(hval2) X(hcnt) X(hoff)
+    X(ls_off) X(ls_scalars) X(hgrid) X(hkey) X(hkey2) X(hval) X(hval2) X(hcnt) X(hoff)   \
+    X(it_cnt) X(it_off) X(it_fill) X(items) X(items2) X(ecol) X(eflag) X(dlist) X(dcnt) X(dptr)
 
 struct Ctx {
     ttie_params prm;
@@ -145,6 +146,7 @@ struct Ctx {
     unsigned eval_what = 0;
     int64_t n_active = 0;
     bool have_bsr = false;
+    bool asm_rows = false;   // the current system came from the row-bucket assembly
     int64_t n_rows = 0, nnzb = 0;
     bool have_dir = false;
     double mean_edge = 0.0;   // mean edge length at the last ttie_build_bvh
