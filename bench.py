@@ -220,6 +220,11 @@ def main():
     ap.add_argument("--no-quasi-static", action="store_true", help="skip the quasi-static simulation run")
     ap.add_argument("--no-next-rows", action="store_true",
                     help="skip the timings of the PSD variants, the exact Hessian-vector product and the dual evaluator")
+    ap.add_argument("--pcg-precond", choices=["block_jacobi", "chebyshev"], default="block_jacobi",
+                    help="preconditioner of the shared-memory PCG")
+    ap.add_argument("--pcg-cheb-degree", type=int, default=0, help="Chebyshev degree (0: the library's default)")
+    ap.add_argument("--assembly", choices=["sorted_keys", "row_buckets"], default="sorted_keys",
+                    help="assembly of the block-CSR system")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -247,7 +252,11 @@ def main():
     tri = torch.tensor(m.tri, dtype=torch.int32, device="cuda")
     grp = torch.tensor(m.group, dtype=torch.int32, device="cuda") if mode else None
     x = x0.clone()
-    ctx = ttie.Context(precision=precision, pair_mode=mode, profile=1)
+    solver = {"pcg_precond": {"block_jacobi": ttie.PCG_BLOCK_JACOBI, "chebyshev": ttie.PCG_CHEBYSHEV}[args.pcg_precond],
+              "pcg_cheb_degree": args.pcg_cheb_degree,
+              "assembly_mode": {"sorted_keys": ttie.ASSEMBLY_SORTED_KEYS,
+                                "row_buckets": ttie.ASSEMBLY_ROW_BUCKETS}[args.assembly]}
+    ctx = ttie.Context(precision=precision, pair_mode=mode, profile=1, **solver)
     ctx.build_bvh(x0, tri, grp)
     stream = torch.cuda.current_stream()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
@@ -349,7 +358,7 @@ def main():
     if precision == 0 and not args.no_fp64_form and rank == 0:
         x64_0 = torch.tensor(m.x, dtype=torch.float64, device="cuda")
         x64 = x64_0.clone()
-        ctx64 = ttie.Context(precision=ttie.F64, pair_mode=mode, profile=1)
+        ctx64 = ttie.Context(precision=ttie.F64, pair_mode=mode, profile=1, **solver)
         ctx64.build_bvh(x64_0, tri, grp)
         n64 = max(3, min(args.steps, 10))
         for _ in range(args.warmup):
@@ -492,6 +501,7 @@ def main():
                        "line_search_trials": last["ls_trials"], "pcg_iters": last["pcg_iters"],
                        "bsr_rows": last["n_rows"], "bsr_blocks": last["nnzb"],
                        "l2": "flushed (256 MiB write) before every timed step",
+                       "pcg_precond": args.pcg_precond, "assembly": args.assembly,
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "stage_ms_per_step": {k: v / args.steps for k, v in stage.items()},
             "active_pairs_per_s": active / (total_ms / 1e3),

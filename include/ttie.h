@@ -259,8 +259,10 @@ typedef struct {
     float ms_build, ms_eval, ms_assemble, ms_pcg, ms_line_search;  /* if params.profile */
     float ms_classify;           /* classification kernel of the evaluation at x (profile) */
     float ms_pcg_kernel;         /* persistent PCG kernel (profile)                          */
-    int64_t pcg_block_iters;     /* sum over the PCG iterations of the 3x3 blocks multiplied */
-    int64_t pcg_row_iters;       /* sum over the PCG iterations of the rows updated           */
+    int64_t pcg_block_iters;     /* sum over the PCG's products of the 3x3 blocks multiplied
+                                    (one product per iteration; k + 1 with the Chebyshev
+                                    preconditioner after its restart)                      */
+    int64_t pcg_row_iters;       /* sum over the PCG's products of the rows updated           */
     double energy_elastic;       /* elastic term's part of energy (0 without one)             */
 } ttie_step_info;
 

@@ -1483,11 +1483,13 @@ __global__ void __launch_bounds__(kPcgThreads) k_pcg_resident(PcgArgs<T> a, int 
     // jstep (Chebyshev): 0 when the next product is w = A u of an iteration, j + 1 when it is
     // the product of the polynomial's j-th direction
     int jstep = 0;
+    unsigned long long n_prod = 0;
     while (true) {
         const bool inner = kCheb && jstep > 0;
         const vec4_t<T> *src = (kCheb && (pub & 1u)) ? a.z4b : a.z4;
         const unsigned tu = kCheb ? (pub & 3u) : ((unsigned)it & 3u);
         const Acc<T> wu = resident_product(a, v, src, inner ? v.d : v.u, mu, tu, &s_bad);
+        if constexpr (kCheb) ++n_prod;
         if (inner) {
             // the polynomial's next step: rr -= D^-1 (A + mu I) d, d = c1 d + c2 rr, y += d;
             // each d but the last published for the next product, then u = y
@@ -1599,6 +1601,7 @@ __global__ void __launch_bounds__(kPcgThreads) k_pcg_resident(PcgArgs<T> a, int 
         ds->red[1] = (double)rr0;
         ds->red[4] = rr.value();
         ds->pcg_done = 1;
+        if constexpr (kCheb) ds->pcg_products = n_prod;
     }
 }
 
@@ -1967,6 +1970,7 @@ cudaError_t pcg_solve(Ctx &c, const T *rhs, T *out, double rtol, int max_it) {
         // odd publications; zeros carry tag 0, which no odd publication has
         TTIE_CUDA_TRY(ensure(c, c.pcg_z4b, (size_t)(nr > 0 ? nr : 1) * sizeof(vec4_t<T>)));
         TTIE_CUDA_TRY(cudaMemsetAsync(c.pcg_z4b.p, 0, (size_t)(nr > 0 ? nr : 1) * sizeof(vec4_t<T>), c.stream));
+        TTIE_CUDA_TRY(cudaMemsetAsync(&c.ds->pcg_products, 0, sizeof(unsigned long long), c.stream));
     }
     RedSlot *slots = (RedSlot *)c.pcg_sync.p;
     int *rpart = (int *)(slots + 2 * kMaxGridPcg + 2);
@@ -1993,6 +1997,7 @@ cudaError_t pcg_solve(Ctx &c, const T *rhs, T *out, double rtol, int max_it) {
     args.z4 = (vec4_t<T> *)c.pcg_z4.p;
     args.z4b = cheb && resident ? (vec4_t<T> *)c.pcg_z4b.p : nullptr;
     args.cheb_degree = c.prm.pcg_cheb_degree > 0 ? c.prm.pcg_cheb_degree : 2;
+    c.pcg_cheb = cheb && resident;
     args.partA = part;
     args.partB = part + 2 * kNumSMs * 8;
     args.rtol2 = rtol * rtol;

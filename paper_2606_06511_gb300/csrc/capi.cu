@@ -453,8 +453,10 @@ static ttie_status newton_impl(Ctx &c, T *x, ttie_step_info *info) {
     inf.grad_dot_dir = gd;
     inf.pcg_iters = c.hs->pcg_iters;
     inf.pcg_rel_residual = c.hs->red[1] > 0.0 ? std::sqrt(c.hs->red[4] / c.hs->red[1]) : 0.0;
-    inf.pcg_block_iters = (int64_t)inf.pcg_iters * c.nnzb;
-    inf.pcg_row_iters = (int64_t)inf.pcg_iters * c.n_rows;
+    // the Chebyshev-preconditioned kernel multiplies k + 1 times per iteration after its restart
+    const int64_t passes = c.pcg_cheb ? (int64_t)c.hs->pcg_products : (int64_t)inf.pcg_iters;
+    inf.pcg_block_iters = passes * c.nnzb;
+    inf.pcg_row_iters = passes * c.n_rows;
     mark(c, 4);
     // line search on candidates from the boxes swept between x and x + a_max d
     double a_max = 1.0 + c.prm.push_eta;

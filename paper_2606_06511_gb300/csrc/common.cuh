@@ -100,6 +100,7 @@ struct DevScalars {
     double ls_alpha, ls_last;              // batched line search: trial step, 1 on the last trial
     double batch[10];                      // batched step totals (instance_totals)
     double el_energy;                      // energy of the elastic term at the last evaluation
+    unsigned long long pcg_products;       // Chebyshev-preconditioned PCG: products computed
 };
 
 static_assert(offsetof(DevScalars, n_defer2) == offsetof(DevScalars, n_defer) + sizeof(unsigned long long),
@@ -147,6 +148,7 @@ struct Ctx {
     int64_t n_active = 0;
     bool have_bsr = false;
     bool asm_rows = false;   // the current system came from the row-bucket assembly
+    bool pcg_cheb = false;   // the last PCG ran the Chebyshev-preconditioned kernel
     int64_t n_rows = 0, nnzb = 0;
     bool have_dir = false;
     double mean_edge = 0.0;   // mean edge length at the last ttie_build_bvh
