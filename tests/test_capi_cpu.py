@@ -31,6 +31,24 @@ def test_every_declared_symbol_is_exported(lib):
         assert hasattr(lib, n), n
 
 
+def test_header_is_plain_c(tmp_path):
+    """The boundary header compiles as strict C99 (and C++17) with every warning an error, so a
+    C caller can use it; every declared entry point is referenced."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    names = declared_functions()
+    src = tmp_path / "use_header.c"
+    src.write_text('#include "ttie.h"\n' + "".join("void (*ref_%s)(void) = (void (*)(void))&%s;\n" % (n, n) for n in names) +
+                   "int main(void) { ttie_params p; ttie_default_params(&p); return p.precision; }\n")
+    for cmd in ([gcc, "-std=c99", "-pedantic"], [gcc, "-x", "c++", "-std=c++17"]):
+        r = subprocess.run(cmd + ["-Wall", "-Wextra", "-Werror", "-I", os.path.join(ROOT, "include"), "-c", str(src),
+                                  "-o", str(tmp_path / "use_header.o")], capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr
+
+
 def test_default_params(lib):
     from paper_2606_06511_gb300 import ttie
     p = ttie.default_params()
