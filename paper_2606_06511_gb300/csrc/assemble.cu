@@ -486,33 +486,47 @@ __global__ void k_row_items(const int4 *__restrict__ tri4, const int2 *__restric
     }
 }
 
-// One warp per row: items in code order (each item's rank among the row's codes, which are
+// One group per row: items in code order (each item's rank among the row's codes, which are
 // distinct), each item's entry columns (6 slots, -1 where an item has fewer), the first entry
 // of each column (no earlier entry in item order has that column) and the distinct columns in
 // ascending order (a first entry's place is the number of first entries with a smaller
-// column).  All of a row's scratch lies in its items' range (x6 for entries).
+// column).  All of a row's scratch lies in its items' range (x6 for entries).  The work per row
+// grows with the square of its entries, so a row with more than kBigItems items goes to a
+// block (kBig: kBigThreads threads) and the others to a warp.
 constexpr int kRowWarps = 4;
-__global__ void __launch_bounds__(32 * kRowWarps)
+constexpr int kBigThreads = 512;
+constexpr unsigned long long kBigItems = 48;
+template <bool kBig> __device__ __forceinline__ void group_sync() {
+    if (kBig) __syncthreads();
+    else __syncwarp();
+}
+
+template <bool kBig>
+__global__ void __launch_bounds__(kBig ? kBigThreads : 32 * kRowWarps)
     k_row_columns(const uint32_t *__restrict__ items, const unsigned long long *__restrict__ off,
                   const int4 *__restrict__ tri4, const int2 *__restrict__ pairs, const uint32_t *__restrict__ active,
                   const unsigned long long *__restrict__ vrow, const int2 *__restrict__ edges, int64_t n_springs,
                   const int32_t *__restrict__ anchors, DevScalars *ds, uint32_t *__restrict__ items2,
                   int32_t *__restrict__ ecol, uint8_t *__restrict__ efirst, int32_t *__restrict__ dlist,
                   uint32_t *__restrict__ dcnt) {
-    const int lane = threadIdx.x & 31;
+    constexpr int G = kBig ? kBigThreads : 32;
+    __shared__ unsigned int s_nd;
+    const int tid = kBig ? (int)threadIdx.x : (int)(threadIdx.x & 31);
     const unsigned long long nr = ds->n_rows, n_pair_items = ds->n_active * 6;
-    const unsigned long long n_warps = (unsigned long long)gridDim.x * kRowWarps;
-    for (unsigned long long row = blockIdx.x * (unsigned long long)kRowWarps + (threadIdx.x >> 5); row < nr;
-         row += n_warps) {
+    const unsigned long long row0 = kBig ? blockIdx.x : blockIdx.x * (unsigned long long)kRowWarps + (threadIdx.x >> 5);
+    const unsigned long long stride = kBig ? gridDim.x : (unsigned long long)gridDim.x * kRowWarps;
+    for (unsigned long long row = row0; row < nr; row += stride) {
         const unsigned long long base = off[row], n = off[row + 1] - base;
-        for (unsigned long long i = lane; i < n; i += 32) {
+        if ((n > kBigItems) != kBig) continue;   // the same for the whole group
+        if (kBig && tid == 0) s_nd = 0;
+        for (unsigned long long i = tid; i < n; i += G) {
             const uint32_t code = items[base + i];
             unsigned long long rank = 0;
             for (unsigned long long j = 0; j < n; ++j) rank += items[base + j] < code;
             if (rank < n) items2[base + rank] = code;
         }
-        __syncwarp();
-        for (unsigned long long i = lane; i < n; i += 32) {
+        group_sync<kBig>();
+        for (unsigned long long i = tid; i < n; i += G) {
             const uint32_t code = items2[base + i];
             int32_t cols[6] = {-1, -1, -1, -1, -1, -1};
             if (code < n_pair_items) {
@@ -531,18 +545,18 @@ __global__ void __launch_bounds__(32 * kRowWarps)
 #pragma unroll
             for (int c = 0; c < 6; ++c) ecol[(base + i) * 6 + c] = cols[c];
         }
-        __syncwarp();
+        group_sync<kBig>();
         const unsigned long long ne = 6 * n;
         int32_t *ec = ecol + base * 6;
-        for (unsigned long long q = lane; q < ne; q += 32) {
+        for (unsigned long long q = tid; q < ne; q += G) {
             const int32_t col = ec[q];
             bool first = col >= 0;
             for (unsigned long long p = 0; p < q && first; ++p) first = ec[p] != col;
             efirst[base * 6 + q] = first ? 1 : 0;
         }
-        __syncwarp();
+        group_sync<kBig>();
         uint32_t nd = 0;
-        for (unsigned long long q = lane; q < ne; q += 32) {
+        for (unsigned long long q = tid; q < ne; q += G) {
             if (!efirst[base * 6 + q]) continue;
             const int32_t col = ec[q];
             unsigned long long place = 0;
@@ -552,35 +566,43 @@ __global__ void __launch_bounds__(32 * kRowWarps)
         }
 #pragma unroll
         for (int o = 16; o; o >>= 1) nd += __shfl_xor_sync(0xffffffffu, nd, o);
-        if (lane == 0) dcnt[row] = nd;
-        __syncwarp();
+        if (kBig) {
+            if ((threadIdx.x & 31) == 0) atomicAdd(&s_nd, nd);
+            __syncthreads();
+            if (tid == 0) dcnt[row] = s_nd;
+        } else if (tid == 0) {
+            dcnt[row] = nd;
+        }
+        group_sync<kBig>();
     }
 }
 
-// One warp per row, a lane per distinct column: the block (row, col) as the sum of its entries
-// in item order, its column index and, on the diagonal, the gradient rows; row_ptr from the
-// scanned distinct counts (dptr[V] = nnzb).
-template <typename T>
-__global__ void __launch_bounds__(32 * kRowWarps)
+// One group per row (as above), a thread per distinct column: the block (row, col) as the sum
+// of its entries in item order, its column index and, on the diagonal, the gradient rows;
+// row_ptr from the scanned distinct counts (dptr[V] = nnzb).
+template <typename T, bool kBig>
+__global__ void __launch_bounds__(kBig ? kBigThreads : 32 * kRowWarps)
     k_row_values(const uint32_t *__restrict__ items2, const unsigned long long *__restrict__ off,
                  const int32_t *__restrict__ ecol, const int32_t *__restrict__ dlist, const uint32_t *__restrict__ dcnt,
                  const unsigned long long *__restrict__ dptr, int64_t V, unsigned long long cap, const T *__restrict__ z,
                  const T *__restrict__ sfac, int64_t n_springs, const T *__restrict__ afac, T ka, DevScalars *ds,
                  int32_t *__restrict__ row_ptr, int32_t *__restrict__ col_idx, T *__restrict__ bval,
                  T *__restrict__ grad_rows, const int32_t *__restrict__ row_vertex, T *__restrict__ grad_full) {
-    const int lane = threadIdx.x & 31;
+    constexpr int G = kBig ? kBigThreads : 32;
+    const int tid = kBig ? (int)threadIdx.x : (int)(threadIdx.x & 31);
     const unsigned long long nr = ds->n_rows, n_pair_items = ds->n_active * 6;
-    const unsigned long long n_warps = (unsigned long long)gridDim.x * kRowWarps;
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    const unsigned long long row0 = kBig ? blockIdx.x : blockIdx.x * (unsigned long long)kRowWarps + (threadIdx.x >> 5);
+    const unsigned long long stride = kBig ? gridDim.x : (unsigned long long)gridDim.x * kRowWarps;
+    if (!kBig && blockIdx.x == 0 && threadIdx.x == 0) {
         ds->nnzb = dptr[V];
         if (nr <= (unsigned long long)V) row_ptr[nr] = (int32_t)dptr[V];
     }
-    for (unsigned long long row = blockIdx.x * (unsigned long long)kRowWarps + (threadIdx.x >> 5); row < nr;
-         row += n_warps) {
+    for (unsigned long long row = row0; row < nr; row += stride) {
         const unsigned long long base = off[row], n = off[row + 1] - base, rp = dptr[row];
+        if ((n > kBigItems) != kBig) continue;
         const uint32_t nd = dcnt[row];
-        if (lane == 0) row_ptr[row] = (int32_t)rp;
-        for (uint32_t d = lane; d < nd && rp + d < cap; d += 32) {
+        if (tid == 0) row_ptr[row] = (int32_t)rp;
+        for (uint32_t d = tid; d < nd && rp + d < cap; d += G) {
             const int32_t col = dlist[base * 6 + d];
             const bool diag = (unsigned long long)col == row;
             T m[9];
@@ -1786,13 +1808,25 @@ static cudaError_t assemble_rows(Ctx &c, T *grad_full, int64_t n_springs, int64_
     TTIE_CUDA_TRY(scan_u32_u64(c, (const uint32_t *)c.it_cnt.p, (unsigned long long *)c.it_off.p, V));
     launch(c, k_row_items<true>, dim3(gI), dim3(kThreads), tri4, pairs, active, vrow, edges, n_springs, anchors,
            n_anchors, c.ds, (uint32_t *)c.it_fill.p, (const unsigned long long *)c.it_off.p, (uint32_t *)c.items.p);
+    // rows of up to kBigItems items: a warp each; larger rows: a block each (the big-row
+    // launches skip the small rows, one load per row)
     const unsigned gR = grid_for((V + kRowWarps - 1) / kRowWarps, 1, kNumSMs * 16);
-    launch(c, k_row_columns, dim3(gR), dim3(32 * kRowWarps), (const uint32_t *)c.items.p,
+    const unsigned gB = grid_for(V, 1, kNumSMs * 2);
+    launch(c, k_row_columns<false>, dim3(gR), dim3(32 * kRowWarps), (const uint32_t *)c.items.p,
+           (const unsigned long long *)c.it_off.p, tri4, pairs, active, vrow, edges, n_springs, anchors, c.ds,
+           (uint32_t *)c.items2.p, (int32_t *)c.ecol.p, (uint8_t *)c.eflag.p, (int32_t *)c.dlist.p,
+           (uint32_t *)c.dcnt.p);
+    launch(c, k_row_columns<true>, dim3(gB), dim3(kBigThreads), (const uint32_t *)c.items.p,
            (const unsigned long long *)c.it_off.p, tri4, pairs, active, vrow, edges, n_springs, anchors, c.ds,
            (uint32_t *)c.items2.p, (int32_t *)c.ecol.p, (uint8_t *)c.eflag.p, (int32_t *)c.dlist.p,
            (uint32_t *)c.dcnt.p);
     TTIE_CUDA_TRY(scan_u32_u64(c, (const uint32_t *)c.dcnt.p, (unsigned long long *)c.dptr.p, V));
-    launch(c, k_row_values<T>, dim3(gR), dim3(32 * kRowWarps), (const uint32_t *)c.items2.p,
+    launch(c, k_row_values<T, false>, dim3(gR), dim3(32 * kRowWarps), (const uint32_t *)c.items2.p,
+           (const unsigned long long *)c.it_off.p, (const int32_t *)c.ecol.p, (const int32_t *)c.dlist.p,
+           (const uint32_t *)c.dcnt.p, (const unsigned long long *)c.dptr.p, V, (unsigned long long)kb, (const T *)c.zfac.p,
+           (const T *)c.el_sfac.p, n_springs, (const T *)c.el_afac.p, (T)c.el_ka, c.ds, (int32_t *)c.row_ptr.p,
+           (int32_t *)c.col_idx.p, (T *)c.bsr_val.p, (T *)c.rhs.p, (const int32_t *)c.row_vertex.p, grad_full);
+    launch(c, k_row_values<T, true>, dim3(gB), dim3(kBigThreads), (const uint32_t *)c.items2.p,
            (const unsigned long long *)c.it_off.p, (const int32_t *)c.ecol.p, (const int32_t *)c.dlist.p,
            (const uint32_t *)c.dcnt.p, (const unsigned long long *)c.dptr.p, V, (unsigned long long)kb, (const T *)c.zfac.p,
            (const T *)c.el_sfac.p, n_springs, (const T *)c.el_afac.p, (T)c.el_ka, c.ds, (int32_t *)c.row_ptr.p,
