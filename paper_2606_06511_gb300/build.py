@@ -13,7 +13,7 @@ ROOT = os.path.dirname(HERE)
 SRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libttie.so")
-UNITS = ["sort_scan.cu", "bvh.cu", "hash.cu", "pair_eval.cu", "assemble.cu", "instances.cu", "capi.cu", "pcg_static.cu"]
+UNITS = ["sort_scan.cu", "bvh.cu", "hash.cu", "pair_eval.cu", "assemble.cu", "pcg.cu", "instances.cu", "capi.cu", "pcg_static.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -270,12 +270,14 @@ template <typename T>
 cudaError_t energy_eval_nosync(Ctx &c, const vec4_t<T> *x, const int2 *pairs, int64_t n_cap,
                                const unsigned long long *d_n);
 
-// ------------------------------------------------------------------ assembly / solve (assemble.cu)
+// ------------------------------------------------------------------ assembly (assemble.cu)
 // with_elastic: the elastic term (ttie_set_elastic) is added to the pairs' system
 template <typename T> cudaError_t assemble_system(Ctx &c, T *grad_out_V3, bool with_elastic = false);
 template <typename T> cudaError_t elastic_energy(Ctx &c, const vec4_t<T> *x);   // -> ds->el_energy
 template <typename T> cudaError_t elastic_set(Ctx &c, const ttie_elastic *e);
+// ------------------------------------------------------------------ solve (pcg.cu)
 template <typename T> cudaError_t pcg_solve(Ctx &c, const T *rhs, T *out, double rtol, int max_it);
+// ------------------------------------------------------------------ (assemble.cu)
 // Hessian-vector products: per-pair exact products (pair_eval.cu), their per-vertex sums over
 // the last assembly's diagonal runs, and the assembled PSD Hessian times v.
 template <typename T> cudaError_t hvp_pairs(Ctx &c, const vec4_t<T> *x, const T *v, T *h);

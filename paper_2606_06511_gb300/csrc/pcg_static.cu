@@ -8,6 +8,7 @@
 #include "common.cuh"
 
 namespace ttie {
+// the setup and persistent PCG kernels on explicit buffers (pcg.cu)
 cudaError_t pcg_run_raw(cudaStream_t stream, int num_sms, const int32_t *row_ptr, const int32_t *col_idx,
                         const float *bval, int64_t n_rows, double mu_rel, const float *rhs, float *out, float *dinv,
                         float *r, float *z, float *p, float *q, double *partials, DevScalars *ds, double rtol,
