@@ -225,6 +225,8 @@ def main():
     ap.add_argument("--pcg-cheb-degree", type=int, default=0, help="Chebyshev degree (0: the library's default)")
     ap.add_argument("--assembly", choices=["sorted_keys", "row_buckets"], default="sorted_keys",
                     help="assembly of the block-CSR system")
+    ap.add_argument("--traversal", choices=["two_walks", "one_walk"], default="two_walks",
+                    help="LBVH traversal")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -255,7 +257,9 @@ def main():
     solver = {"pcg_precond": {"block_jacobi": ttie.PCG_BLOCK_JACOBI, "chebyshev": ttie.PCG_CHEBYSHEV}[args.pcg_precond],
               "pcg_cheb_degree": args.pcg_cheb_degree,
               "assembly_mode": {"sorted_keys": ttie.ASSEMBLY_SORTED_KEYS,
-                                "row_buckets": ttie.ASSEMBLY_ROW_BUCKETS}[args.assembly]}
+                                "row_buckets": ttie.ASSEMBLY_ROW_BUCKETS}[args.assembly],
+              "traversal_mode": {"two_walks": ttie.TRAVERSAL_TWO_WALKS,
+                                 "one_walk": ttie.TRAVERSAL_ONE_WALK}[args.traversal]}
     ctx = ttie.Context(precision=precision, pair_mode=mode, profile=1, **solver)
     ctx.build_bvh(x0, tri, grp)
     stream = torch.cuda.current_stream()
@@ -501,7 +505,7 @@ def main():
                        "line_search_trials": last["ls_trials"], "pcg_iters": last["pcg_iters"],
                        "bsr_rows": last["n_rows"], "bsr_blocks": last["nnzb"],
                        "l2": "flushed (256 MiB write) before every timed step",
-                       "pcg_precond": args.pcg_precond, "assembly": args.assembly,
+                       "pcg_precond": args.pcg_precond, "assembly": args.assembly, "traversal": args.traversal,
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "stage_ms_per_step": {k: v / args.steps for k, v in stage.items()},
             "active_pairs_per_s": active / (total_ms / 1e3),

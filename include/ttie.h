@@ -108,7 +108,18 @@ typedef struct {
     int pcg_cheb_degree;  /* TTIE_PCG_CHEBYSHEV: degree k of the polynomial, 1..8 (0 = 2) */
     int assembly_mode;    /* TTIE_ASSEMBLY_*: how the 3x3 block-CSR system is assembled;
                              both give the same pattern and bit-identical values          */
+    int traversal_mode;   /* TTIE_TRAVERSAL_*: how the LBVH walk lists candidates; both give
+                             the same list in the same order                              */
 } ttie_params;
+
+/* LBVH traversal (one thread per leaf, depth-first walk over rope links).
+ * TWO_WALKS: a counting walk from the root keeps each leaf's first 16 partners; leaves with
+ *            more walk again to write them.
+ * ONE_WALK:  the walk starts after leaf lo - 1 of the leaf's window (its rope) and stops past
+ *            the window; partners past the first 16 go to 32-pair chunks taken from a pool
+ *            and linked per leaf, then copied in walk order.  When the pool is exhausted the
+ *            second walk writes those leaves instead.                                       */
+enum { TTIE_TRAVERSAL_TWO_WALKS = 0, TTIE_TRAVERSAL_ONE_WALK = 1 };
 
 /* Assembly of the block-CSR system (same result either way: each block is the sum of its
  * entries in the order pair index, then spring, then anchor).
@@ -136,7 +147,7 @@ typedef struct ttie_ctx ttie_ctx;
  * pcg_rtol 1e-3, pcg_max_it 200, newton_max_it 200, ls_max_halvings 20,
  * armijo_c 1e-4, push_eta 0.5, exact_only 0, profile 0, max_step 1,
  * max_candidates 0, inst_threads 0, test_withhold 0, pcg_precond BLOCK_JACOBI,
- * pcg_cheb_degree 0, assembly_mode SORTED_KEYS. */
+ * pcg_cheb_degree 0, assembly_mode SORTED_KEYS, traversal_mode TWO_WALKS. */
 void ttie_default_params(ttie_params *p);
 
 /* Creates a context on the current CUDA device.  stream: a cudaStream_t or NULL

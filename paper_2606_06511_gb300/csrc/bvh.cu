@@ -11,6 +11,8 @@
 // are walked again.  The pair list comes out in a deterministic order (leaf
 // order, then depth-first order) without a global sort.  Topologically adjacent
 // pairs (a shared vertex index, §1) are dropped.
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace ttie {
@@ -304,7 +306,15 @@ __global__ void k_links(int n, const int2 *__restrict__ child, const int2 *__res
 // One thread per leaf s: every leaf s' > s in the pair-mode window whose box overlaps, in
 // depth-first order.  kPass 0 counts them and keeps the first kSpill in spill[s]; kPass 1
 // writes all of them at offset[s], for the leaves with more than kSpill.
-template <typename T, int kPass>
+// kOneWalk (counting pass only): the walk starts at the node that follows leaf lo - 1 in
+// depth-first order (its rope) and stops at the first node past hi.  The walk from the root
+// reaches that node before any output, having only descended ancestors of lo - 1 and skipped
+// subtrees below lo, and past it ranges only grow, so the partners and their order are the
+// same.  Partners past the first kSpill go to kChunk-pair chunks taken from the pool by one
+// atomic each and linked per leaf (head[s], next[chunk]); a chunk index past pool_chunks is not
+// written, and the host then runs kPass 1 for the list instead.
+constexpr int kChunk = 32;
+template <typename T, int kPass, bool kOneWalk = false>
 __global__ void __launch_bounds__(kThreads) k_traverse(int n, const int2 *__restrict__ range,
                                                        const Box<T> *__restrict__ node_box,
                                                        const uint32_t *__restrict__ perm, const int4 *__restrict__ tri4,
@@ -313,7 +323,11 @@ __global__ void __launch_bounds__(kThreads) k_traverse(int n, const int2 *__rest
                                                        uint32_t *__restrict__ count,
                                                        const unsigned long long *__restrict__ offset,
                                                        int2 *__restrict__ spill, int2 *__restrict__ pairs,
-                                                       DevScalars *ds) {
+                                                       DevScalars *ds, int2 *__restrict__ pool = nullptr,
+                                                       int *__restrict__ pool_next = nullptr,
+                                                       int *__restrict__ pool_head = nullptr,
+                                                       unsigned long long pool_chunks = 0) {
+    static_assert(!(kOneWalk && kPass != 0), "the one-walk traversal is a counting pass");
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
         if (kPass == 1 && count[s] <= (uint32_t)kSpill) continue;
         int lo = s + 1, hi = n - 1;
@@ -323,12 +337,13 @@ __global__ void __launch_bounds__(kThreads) k_traverse(int n, const int2 *__rest
             lo = max(lo, group_range[leaf_group[s]].y + 1);
         }
         uint32_t cnt = 0;
+        int chunk = -1;
         const unsigned long long out = kPass == 1 ? offset[s] : 0ull;
         if (lo <= hi) {
             const uint32_t qi = perm[s];
             const int4 tq = tri4[qi];
             const Box<T> qb = node_box[n - 1 + s];
-            int node = 0;
+            int node = kOneWalk ? get_link<T>(node_box[n - 1 + lo - 1].hi.w) : 0;
             for (int steps = 0; node >= 0; ++steps) {
                 if (steps > 2 * n) {   // a walk visits every node at most once: malformed links
                     atomicOr(&ds->err, ERR_STACK);
@@ -336,6 +351,7 @@ __global__ void __launch_bounds__(kThreads) k_traverse(int n, const int2 *__rest
                 }
                 const Box<T> nb = node_box[node];
                 const int2 r = range[node];
+                if (kOneWalk && r.x > hi) break;
                 int next = get_link<T>(nb.hi.w);
                 if (r.y >= lo && r.x <= hi && overlap<T>(qb.lo, qb.hi, nb.lo, nb.hi)) {
                     const int left = get_link<T>(nb.lo.w);
@@ -346,7 +362,19 @@ __global__ void __launch_bounds__(kThreads) k_traverse(int n, const int2 *__rest
                         if (!share_vertex(tq, tri4[tj])) {
                             const int2 pr = make_int2((int)min(qi, tj), (int)max(qi, tj));
                             if (kPass == 0) {
-                                if (cnt < (uint32_t)kSpill) spill[(size_t)s * kSpill + cnt] = pr;
+                                if (cnt < (uint32_t)kSpill) {
+                                    spill[(size_t)s * kSpill + cnt] = pr;
+                                } else if (kOneWalk) {
+                                    const uint32_t q = cnt - (uint32_t)kSpill, slot = q & (uint32_t)(kChunk - 1);
+                                    if (slot == 0) {
+                                        const unsigned long long cid = atomicAdd(&ds->ovf_cursor, 1ull);
+                                        const int nc = cid < pool_chunks ? (int)cid : -1;
+                                        if (q == 0) pool_head[s] = nc;
+                                        else if (chunk >= 0) pool_next[chunk] = nc;
+                                        chunk = nc;
+                                    }
+                                    if (chunk >= 0) pool[(size_t)chunk * kChunk + slot] = pr;
+                                }
                             } else if (!TTIE_BAD(ds, out + cnt < offset[s + 1], 61, out + cnt)) {
                                 pairs[out + cnt] = pr;
                             }
@@ -358,6 +386,30 @@ __global__ void __launch_bounds__(kThreads) k_traverse(int n, const int2 *__rest
             }
         }
         if (kPass == 0) count[s] = cnt;
+    }
+}
+
+// One-walk traversal: the partners of each leaf past its first kSpill, from its chunk chain
+// (in walk order) to their place after the kept ones.  Runs only when no chunk index ran past
+// the pool; the copy still stops at a chunk index outside the pool.
+__global__ void k_chunk_copy(int n, const uint32_t *__restrict__ count, const unsigned long long *__restrict__ offset,
+                             const int2 *__restrict__ pool, const int *__restrict__ pool_next,
+                             const int *__restrict__ pool_head, unsigned long long pool_chunks,
+                             int2 *__restrict__ pairs) {
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
+        const uint32_t cnt = count[s];
+        if (cnt <= (uint32_t)kSpill) continue;
+        unsigned long long out = offset[s] + kSpill, end = offset[s + 1];
+        uint32_t rem = cnt - (uint32_t)kSpill;
+        int chunk = pool_head[s];
+        while (rem > 0) {
+            if (chunk < 0 || (unsigned long long)chunk >= pool_chunks) break;
+            const uint32_t take = min(rem, (uint32_t)kChunk);
+            for (uint32_t i = 0; i < take && out + i < end; ++i) pairs[out + i] = pool[(size_t)chunk * kChunk + i];
+            out += take;
+            rem -= take;
+            if (rem > 0) chunk = pool_next[chunk];
+        }
     }
 }
 
@@ -477,15 +529,34 @@ cudaError_t build_candidates(Ctx &c, const vec4_t<T> *x0, const vec4_t<T> *x1, B
     auto *cnt = (uint32_t *)c.cand_cnt.p;
     auto *off = (unsigned long long *)c.cand_off.p;
     TTIE_CUDA_TRY(ensure(c, c.spill, (size_t)n * kSpill * sizeof(int2)));
-    launch(c, k_traverse<T, 0>, dim3(g), dim3(kThreads), n, (const int2 *)range, (const Box<T> *)nbox, (const uint32_t *)perm,
-           (const int4 *)c.tri4.p, (const int32_t *)c.leaf_group.p, (const int2 *)c.group_range.p, mode, cnt,
-           (const unsigned long long *)nullptr, (int2 *)c.spill.p, (int2 *)nullptr, c.ds);
+    const bool one_walk = c.prm.traversal_mode == TTIE_TRAVERSAL_ONE_WALK;
+    // the pool: n / 4 + 1024 chunks, or what the last walk needed (+ 25 %) if more; a walk that
+    // runs past it falls back to the second walk and sizes the next pool
+    const unsigned long long pool_chunks = std::max((unsigned long long)n / 4 + 1024, c.ovf_chunks);
+    if (one_walk) {
+        TTIE_CUDA_TRY(ensure(c, c.ovf_pool, (size_t)pool_chunks * kChunk * sizeof(int2)));
+        TTIE_CUDA_TRY(ensure(c, c.ovf_next, (size_t)pool_chunks * sizeof(int)));
+        TTIE_CUDA_TRY(ensure(c, c.ovf_head, (size_t)n * sizeof(int)));
+        TTIE_CUDA_TRY(cudaMemsetAsync(&c.ds->ovf_cursor, 0, sizeof(unsigned long long), c.stream));
+        launch(c, k_traverse<T, 0, true>, dim3(g), dim3(kThreads), n, (const int2 *)range, (const Box<T> *)nbox,
+               (const uint32_t *)perm, (const int4 *)c.tri4.p, (const int32_t *)c.leaf_group.p,
+               (const int2 *)c.group_range.p, mode, cnt, (const unsigned long long *)nullptr, (int2 *)c.spill.p,
+               (int2 *)nullptr, c.ds, (int2 *)c.ovf_pool.p, (int *)c.ovf_next.p, (int *)c.ovf_head.p, pool_chunks);
+    } else {
+        launch(c, k_traverse<T, 0>, dim3(g), dim3(kThreads), n, (const int2 *)range, (const Box<T> *)nbox,
+               (const uint32_t *)perm, (const int4 *)c.tri4.p, (const int32_t *)c.leaf_group.p,
+               (const int2 *)c.group_range.p, mode, cnt, (const unsigned long long *)nullptr, (int2 *)c.spill.p,
+               (int2 *)nullptr, c.ds, (int2 *)nullptr, (int *)nullptr, (int *)nullptr, 0ull);
+    }
     TTIE_CUDA_TRY(cudaGetLastError());
     TTIE_CUDA_TRY(scan_u32_u64(c, cnt, off, n));
     unsigned long long total = 0;
     TTIE_CUDA_TRY(cudaMemcpyAsync(&c.hs->n_cand, off + n, 8, cudaMemcpyDeviceToHost, c.stream));
+    if (one_walk)
+        TTIE_CUDA_TRY(cudaMemcpyAsync(&c.hs->ovf_cursor, &c.ds->ovf_cursor, 8, cudaMemcpyDeviceToHost, c.stream));
     TTIE_CUDA_TRY(cudaStreamSynchronize(c.stream));
     total = c.hs->n_cand;
+    if (one_walk && c.hs->ovf_cursor > pool_chunks) c.ovf_chunks = c.hs->ovf_cursor + c.hs->ovf_cursor / 4;
     if ((int64_t)total > cap) {
         *n_out = (int64_t)total;
         return cudaSuccess;
@@ -494,10 +565,15 @@ cudaError_t build_candidates(Ctx &c, const vec4_t<T> *x0, const vec4_t<T> *x1, B
     if (total > 0) {
         launch(c, k_spill_copy, dim3(grid_for((int64_t)n * kSpill, kThreads)), dim3(kThreads), n, (const uint32_t *)cnt,
                (const unsigned long long *)off, (const int2 *)c.spill.p, (int2 *)out_pairs.p);
-        launch(c, k_traverse<T, 1>, dim3(g), dim3(kThreads), n, (const int2 *)range, (const Box<T> *)nbox,
-               (const uint32_t *)perm, (const int4 *)c.tri4.p, (const int32_t *)c.leaf_group.p,
-               (const int2 *)c.group_range.p, mode, cnt, (const unsigned long long *)off, (int2 *)nullptr,
-               (int2 *)out_pairs.p, c.ds);
+        if (one_walk && c.hs->ovf_cursor <= pool_chunks)
+            launch(c, k_chunk_copy, dim3(g), dim3(kThreads), n, (const uint32_t *)cnt, (const unsigned long long *)off,
+                   (const int2 *)c.ovf_pool.p, (const int *)c.ovf_next.p, (const int *)c.ovf_head.p, pool_chunks,
+                   (int2 *)out_pairs.p);
+        else
+            launch(c, k_traverse<T, 1>, dim3(g), dim3(kThreads), n, (const int2 *)range, (const Box<T> *)nbox,
+                   (const uint32_t *)perm, (const int4 *)c.tri4.p, (const int32_t *)c.leaf_group.p,
+                   (const int2 *)c.group_range.p, mode, cnt, (const unsigned long long *)off, (int2 *)nullptr,
+                   (int2 *)out_pairs.p, c.ds, (int2 *)nullptr, (int *)nullptr, (int *)nullptr, 0ull);
     }
     *n_out = (int64_t)total;
     return cudaGetLastError();

@@ -114,7 +114,8 @@ static ttie_status check_params(Ctx &c, const ttie_params *p) {
         (p->test_withhold != 0 && p->test_withhold != 1) ||
         (p->pcg_precond != TTIE_PCG_BLOCK_JACOBI && p->pcg_precond != TTIE_PCG_CHEBYSHEV) ||
         p->pcg_cheb_degree < 0 || p->pcg_cheb_degree > 8 ||
-        (p->assembly_mode != TTIE_ASSEMBLY_SORTED_KEYS && p->assembly_mode != TTIE_ASSEMBLY_ROW_BUCKETS))
+        (p->assembly_mode != TTIE_ASSEMBLY_SORTED_KEYS && p->assembly_mode != TTIE_ASSEMBLY_ROW_BUCKETS) ||
+        (p->traversal_mode != TTIE_TRAVERSAL_TWO_WALKS && p->traversal_mode != TTIE_TRAVERSAL_ONE_WALK))
         return set_err(c, TTIE_ERR_INVALID, "numeric parameter out of range");
     return TTIE_OK;
 }
@@ -142,6 +143,7 @@ void ttie_default_params(ttie_params *p) {
     p->pcg_precond = TTIE_PCG_BLOCK_JACOBI;
     p->pcg_cheb_degree = 0;
     p->assembly_mode = TTIE_ASSEMBLY_SORTED_KEYS;
+    p->traversal_mode = TTIE_TRAVERSAL_TWO_WALKS;
 }
 
 ttie_status ttie_create(ttie_ctx **out, const ttie_params *p, void *stream) {

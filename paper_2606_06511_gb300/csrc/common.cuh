@@ -101,6 +101,7 @@ struct DevScalars {
     double batch[10];                      // batched step totals (instance_totals)
     double el_energy;                      // energy of the elastic term at the last evaluation
     unsigned long long pcg_products;       // Chebyshev-preconditioned PCG: products computed
+    unsigned long long ovf_cursor;         // one-walk traversal: overflow chunks taken
 };
 
 static_assert(offsetof(DevScalars, n_defer2) == offsetof(DevScalars, n_defer) + sizeof(unsigned long long),
@@ -126,7 +127,8 @@ cudaError_t ensure(Ctx &c, Buf &b, size_t bytes);   // grow-only, contents not k
     X(el_edges) X(el_rest) X(el_anchor) X(el_target) X(el_sfac) X(el_afac) X(defer2)          \
     X(inst) X(ls_cand) X(inst_acc) X(inst_ids) X(ab) X(ls_flag)  \
     X(ls_off) X(ls_scalars) X(hgrid) X(hkey) X(hkey2) X(hval) X(hval2) X(hcnt) X(hoff)   \
-    X(it_cnt) X(it_off) X(it_fill) X(items) X(items2) X(ecol) X(eflag) X(dlist) X(dcnt) X(dptr)
+    X(it_cnt) X(it_off) X(it_fill) X(items) X(items2) X(ecol) X(eflag) X(dlist) X(dcnt) X(dptr)  \
+    X(ovf_pool) X(ovf_next) X(ovf_head)
 
 struct Ctx {
     ttie_params prm;
@@ -149,6 +151,7 @@ struct Ctx {
     bool have_bsr = false;
     bool asm_rows = false;   // the current system came from the row-bucket assembly
     bool pcg_cheb = false;   // the last PCG ran the Chebyshev-preconditioned kernel
+    unsigned long long ovf_chunks = 0;   // one-walk traversal: chunks the last walk needed, + 25 %
     int64_t n_rows = 0, nnzb = 0;
     bool have_dir = false;
     double mean_edge = 0.0;   // mean edge length at the last ttie_build_bvh

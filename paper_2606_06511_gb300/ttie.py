@@ -28,6 +28,7 @@ PAIRS_SELF, PAIRS_INTER_GROUP, PAIRS_INTRA_GROUP, PAIRS_BRUTE, PAIRS_HASH = 0, 1
 PSD_PER_PART, PSD_DROP_CROSS, PSD_WHOLE = 0, 1, 2
 PCG_BLOCK_JACOBI, PCG_CHEBYSHEV = 0, 1
 ASSEMBLY_SORTED_KEYS, ASSEMBLY_ROW_BUCKETS = 0, 1
+TRAVERSAL_TWO_WALKS, TRAVERSAL_ONE_WALK = 0, 1
 EVAL_E, EVAL_G, EVAL_H = 1, 2, 4
 
 
@@ -45,7 +46,7 @@ class Params(ctypes.Structure):
                 ("armijo_c", ctypes.c_double), ("push_eta", ctypes.c_double), ("exact_only", ctypes.c_int),
                 ("profile", ctypes.c_int), ("max_step", ctypes.c_double), ("max_candidates", ctypes.c_int64),
                 ("inst_threads", ctypes.c_int), ("test_withhold", ctypes.c_int), ("pcg_precond", ctypes.c_int),
-                ("pcg_cheb_degree", ctypes.c_int), ("assembly_mode", ctypes.c_int)]
+                ("pcg_cheb_degree", ctypes.c_int), ("assembly_mode", ctypes.c_int), ("traversal_mode", ctypes.c_int)]
 
 
 class BsrView(ctypes.Structure):

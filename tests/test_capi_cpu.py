@@ -57,7 +57,7 @@ def test_default_params(lib):
     # the fields appended last come back from the library's defaults: the binding's layout matches
     assert p.max_step == 1.0 and p.max_candidates == 0 and p.inst_threads == 0 and p.test_withhold == 0
     assert p.pcg_precond == ttie.PCG_BLOCK_JACOBI and p.pcg_cheb_degree == 0
-    assert p.assembly_mode == ttie.ASSEMBLY_SORTED_KEYS
+    assert p.assembly_mode == ttie.ASSEMBLY_SORTED_KEYS and p.traversal_mode == ttie.TRAVERSAL_TWO_WALKS
 
 
 def test_null_context_is_rejected(lib):
@@ -90,6 +90,8 @@ def test_bad_params_rejected_before_device(lib):
         p = ttie.default_params(pcg_precond=ttie.PCG_CHEBYSHEV, pcg_cheb_degree=deg)
         assert lib.ttie_create(ctypes.byref(h), ctypes.byref(p), None) == ttie.TTIE_ERR_INVALID
     p = ttie.default_params(assembly_mode=2)
+    assert lib.ttie_create(ctypes.byref(h), ctypes.byref(p), None) == ttie.TTIE_ERR_INVALID
+    p = ttie.default_params(traversal_mode=2)
     assert lib.ttie_create(ctypes.byref(h), ctypes.byref(p), None) == ttie.TTIE_ERR_INVALID
 
 
