@@ -859,7 +859,7 @@ __global__ void __launch_bounds__(kPcgThreads) k_pcg_resident(PcgArgs<T> a, int 
             if (!stop && !stop_next && !cheb_tried && kit < kChebWarm) {
                 s_al[kit] = (double)alpha;
                 s_be[kit] = (double)beta;
-                if (kit == kChebWarm - 1) {
+                if (kit == kChebWarm - 1 && it + 1 < a.max_it) {   // an iteration follows the restart
                     cheb_tried = true;
                     s_restart = cheb_coefficients<T>(s_al, s_be, a.cheb_degree, s_c1, s_c2, &s_thi) ? 1 : 0;
                 }
