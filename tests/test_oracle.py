@@ -26,6 +26,9 @@ def test_closed_form_pairs():
         ev = O.evaluate(m.x, m.tri, np.array([[0, 1]]))
         assert bool(ev.active[0]) == c["active"], c["name"]
         assert ev.T[0] == pytest.approx(c["T"], rel=1e-12, abs=1e-15), c["name"]
+        # the FP64 open-interval test agrees (touching ends compare exactly equal: h = 0.5 keeps
+        # every coordinate, crossing and t dyadic)
+        assert bool(ev.flags64[0] & 4) == c["active"], c["name"]
         if c["active"]:
             lo_a, hi_a = sorted([c["a0"], c["a1"]])
             lo_b, hi_b = sorted([c["b0"], c["b1"]])
@@ -33,6 +36,16 @@ def test_closed_form_pairs():
             assert ev.tc[0, 0] * ev.tc[0, 1] == pytest.approx((lo_a - hi_b) * (hi_a - lo_b), rel=1e-12)
             # Sum of the four t about their mean is zero (origin A cancels); |I_c| is the sum of lengths
             assert ev.tc[0, 1] - ev.tc[0, 0] == pytest.approx((hi_a - lo_a) + (hi_b - lo_b), rel=1e-12)
+            # The listing's line direction D = n_B x n_A (its first normal belongs to the second
+            # triangle), by hand for this geometry: n_A = (A1 - A0) x (A2 - A0) = (0, 0, 4h(a0 - a1)),
+            # n_B = (B1 - B0) x (B2 - B0) = (0, 4h(b1 - b0), 0), so n_B x n_A = -16h^2 (b1 - b0)(a1 - a0) x^
+            # and D = sx x^.  The end points of the segments sit at x = a0, a1 and b0, b1, so each
+            # t_c is fixed, not only their product and difference (the opposite direction maps
+            # (t_c^0, t_c^1) to (-t_c^1, -t_c^0)).
+            sx = -np.sign(c["a1"] - c["a0"]) * np.sign(c["b1"] - c["b0"])
+            tA, tB = sorted([sx * c["a0"], sx * c["a1"]]), sorted([sx * c["b0"], sx * c["b1"]])
+            assert ev.tc[0, 0] == pytest.approx(tA[0] - tB[1], rel=1e-12), c["name"]
+            assert ev.tc[0, 1] == pytest.approx(tA[1] - tB[0], rel=1e-12), c["name"]
 
 
 def test_appendix_half_scale():
@@ -300,6 +313,11 @@ def test_psd_projection_properties():
         wv = u[k] / nu - v[k] / nv
         closed = 2 * abs(a[k] * b[k]) * nu * nv * np.outer(wv, wv)
         assert np.allclose(O.clamp_psd(p3[k:k + 1])[0], closed, atol=1e-10 * np.abs(closed).max())
+        # the default projection keeps parts 1 and 2 and that eigenpair of part 3 (per part, §1.1),
+        # not the clamp of the sum, which has rank one: H+ = 2b^2 uu' + 2a^2 vv' + closed, rank 2
+        per_part = 2 * b[k] ** 2 * np.outer(u[k], u[k]) + 2 * a[k] ** 2 * np.outer(v[k], v[k]) + closed
+        assert np.allclose(H, per_part, atol=1e-10 * np.abs(per_part).max())
+        assert np.sum(w > 1e-10 * w[-1]) == 2
 
 
 # ----------------------------------------------------------------- invariances
