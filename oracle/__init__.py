@@ -19,9 +19,10 @@ Parity status of each function:
                              H (w x x) = w x g (rotation invariance), H 1 = 0
                              (translation), v.Hv = second difference of E
   assemble / newton_solve    pinned: dense recomputation, direct solve
-                             residual; the Newton trajectory itself is
-                             parity-unpinned (only the certified end state is
-                             compared)
+                             residual, the line-search rule on a quadratic
+                             whose decisions are known, the step cap; the
+                             Newton trajectory itself is parity-unpinned
+                             (only the certified end state is compared)
   elastic.*                  pinned: spring closed forms, central finite
                              differences, projected-spectrum closed form,
                              invariances (the elastic model is a reading: the
@@ -31,7 +32,8 @@ from .ttie_oracle import (build_oracle, candidate_pairs, partners_of, evaluate, 
                           eval_pairs_f64, filtered_sides, gradient, hessian_parts,
                           hessian_inexact, hessian_psd, clamp_psd, assemble, pair_dofs,
                           blocks_to_dense, hessian_vector_product, pair_hessian_vector,
-                          newton_direction, newton_solve, certify, energy,
+                          newton_direction, newton_solve, line_search, capped_direction,
+                          certify, energy,
                           NewtonParams, PairEval)
 from . import exact  # noqa: F401
 from .elastic import (Elastic, mesh_edges, springs_at_rest, elastic_energy, elastic_gradient,  # noqa: F401,E402

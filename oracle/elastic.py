@@ -24,8 +24,8 @@ from dataclasses import dataclass
 
 import numpy as np
 
-from .ttie_oracle import (NewtonParams, assemble, blocks_to_dense, candidate_pairs, clamp_psd, evaluate,
-                          pair_dofs)
+from .ttie_oracle import (NewtonParams, assemble, blocks_to_dense, candidate_pairs,
+                          capped_direction, clamp_psd, evaluate, line_search, pair_dofs)
 
 
 @dataclass
@@ -166,14 +166,7 @@ def quasi_static_solve(x0, tri, group, prm: NewtonParams, el: Elastic, log=None)
             log.append((it, E, n_act))
         if n_act == 0:
             return x, it, True
-        dmax = float(np.linalg.norm(d, axis=1).max())
-        if cap > 0 and dmax > cap:
-            d = d * (cap / dmax)
-        slope = float(np.sum(grad * d))
-        for a in [1.0 + prm.push_eta] + [0.5 ** k for k in range(prm.ls_max_halvings + 1)]:
-            xt = x + a * d
-            Et, nt = total_energy(xt, tri, group, prm, el)
-            if nt == 0 or Et <= E + prm.armijo_c * a * slope:
-                break
-        x = xt
+        d = capped_direction(d, cap)
+        _, x, _, _ = line_search(x, d, E, float(np.sum(grad * d)),
+                                 lambda xt: total_energy(xt, tri, group, prm, el), prm)
     return x, prm.newton_max_it, False

@@ -373,6 +373,26 @@ def newton_direction(x, tri, group, prm: NewtonParams):
     return E, n_act, grad, d, verts
 
 
+def line_search(x, d, E: float, slope: float, energy_at, prm: NewtonParams):
+    """The backtracking line search of the Newton policy (reading of §1.2's unstated inexact
+    Newton): trial steps 1 + push_eta, then 1, 1/2, ..., 2^-ls_max_halvings; the first trial
+    with Armijo's condition E(x + a d) <= E + c a slope (slope = g.d < 0), or with no
+    intersecting pair, is taken, else the last.  energy_at(xt) -> (E, intersecting pairs).
+    Returns (a, x + a d, E there, intersecting pairs there)."""
+    for a in [1.0 + prm.push_eta] + [0.5 ** k for k in range(prm.ls_max_halvings + 1)]:
+        xt = x + a * d
+        Et, nt = energy_at(xt)
+        if nt == 0 or Et <= E + prm.armijo_c * a * slope:
+            break
+    return a, xt, Et, nt
+
+
+def capped_direction(d, cap: float):
+    """d scaled so that no vertex moves more than cap (0: no cap)."""
+    dmax = float(np.linalg.norm(d, axis=1).max())
+    return d * (cap / dmax) if cap > 0 and dmax > cap else d
+
+
 def newton_solve(x0, tri, group=None, prm: NewtonParams | None = None, log=None):
     """Inexact Newton on E = sum T with a backtracking line search; stops when no pair
     intersects (decided exactly).  The direction is scaled so that no vertex moves more
@@ -392,17 +412,8 @@ def newton_solve(x0, tri, group=None, prm: NewtonParams | None = None, log=None)
             log.append((it, E, n_act))
         if n_act == 0:
             return x, it, True
-        dmax = float(np.linalg.norm(d, axis=1).max())
-        if cap > 0 and dmax > cap:
-            d = d * (cap / dmax)
-        slope = float(np.sum(grad * d))
-        alphas = [1.0 + prm.push_eta] + [0.5 ** k for k in range(prm.ls_max_halvings + 1)]
-        for a in alphas:
-            xt = x + a * d
-            Et, nt = energy(xt, tri, group, prm)
-            if nt == 0 or Et <= E + prm.armijo_c * a * slope:
-                break
-        x = xt
+        d = capped_direction(d, cap)
+        _, x, _, _ = line_search(x, d, E, float(np.sum(grad * d)), lambda xt: energy(xt, tri, group, prm), prm)
     return x, prm.newton_max_it, False
 
 

@@ -368,6 +368,38 @@ def test_candidate_pairs_brute_force_loops():
         assert list(O.partners_of(m.x, m.tri, i)) == row
 
 
+def test_partners_of_rows_in_every_mode():
+    """Brute-force rows (closed boxes, no shared vertex, the mode's group rule) against
+    partners_of in the three pair modes."""
+    m = ti.two_icospheres(offset=(1.6, 0.0, 0.0))
+    lo, hi = m.x[m.tri].min(1), m.x[m.tri].max(1)
+    for mode in ("self", "inter", "instance"):
+        for i in (0, 17, 200, 333, 639):
+            row = []
+            for j in range(m.F):
+                if j == i or set(m.tri[i]) & set(m.tri[j]):
+                    continue
+                if mode == "inter" and m.group[i] == m.group[j]:
+                    continue
+                if mode == "instance" and m.group[i] != m.group[j]:
+                    continue
+                if all(lo[i][k] <= hi[j][k] and lo[j][k] <= hi[i][k] for k in range(3)):
+                    row.append(j)
+            assert list(O.partners_of(m.x, m.tri, i, m.group, mode)) == row, (mode, i)
+
+
+def test_certify_respects_pair_mode():
+    """Two intersecting closed-form pairs, each inside one group, and one pair across groups:
+    the count in each mode is the hand count."""
+    a = ti.closed_form_pair(-0.2, 0.5, 0.1, 0.9)               # intersects (Eq. 1 closed form)
+    x = np.concatenate([a.x, a.x + [10.0, 0.0, 0.0], a.x + [20.0, 0.0, 0.0]])
+    tri = np.concatenate([a.tri, a.tri + 6, a.tri + 12]).astype(np.int32)
+    group = np.array([0, 0, 1, 1, 2, 3], np.int32)
+    assert O.certify(x, tri, group, "self") == 3
+    assert O.certify(x, tri, group, "instance") == 2
+    assert O.certify(x, tri, group, "inter") == 1
+
+
 def test_pair_modes():
     m = ti.two_icospheres()
     inter = O.candidate_pairs(m.x, m.tri, m.group, "inter", aabb=False)
@@ -412,6 +444,47 @@ def test_newton_direction_solves_system():
     r = (H + mu * np.eye(len(H))) @ d[verts].ravel() + grad[verts].ravel()
     assert np.linalg.norm(r) <= 1e-9 * np.linalg.norm(grad)
     assert np.sum(grad * d) < 0   # descent direction
+
+
+def test_line_search_rule():
+    """The policy's line search on E(x) = |x|^2 (one intersecting pair throughout unless stated),
+    decided by hand: trials 1.5, 1, 1/2, ...; Armijo E(x + a d) <= E + c a g.d, or no pair."""
+    prm = O.NewtonParams(armijo_c=1e-4, push_eta=0.5, ls_max_halvings=4)
+    x = np.array([[1.0, 0.0, 0.0]])
+    E, g = 1.0, 2 * x
+    quad = lambda xt: (float(np.sum(xt * xt)), 1)
+    # d = -x: 1.5 lands at -0.5 x, E = 0.25 <= 1 - 1.5e-4 * 2: the overshoot is taken
+    d = -x
+    a, xt, Et, _ = O.line_search(x, d, E, float(np.sum(g * d)), quad, prm)
+    assert a == 1.5 and Et == pytest.approx(0.25)
+    # d = -2x: 1.5 gives E = 4, 1 gives E = 1 (no decrease, rejected), 1/2 gives 0
+    d = -2 * x
+    a, xt, Et, _ = O.line_search(x, d, E, float(np.sum(g * d)), quad, prm)
+    assert a == 0.5 and Et == 0.0
+    # no intersecting pair accepts the first trial whatever its energy
+    a, _, _, nt = O.line_search(x, d, E, float(np.sum(g * d)), lambda xt: (100.0, 0), prm)
+    assert a == 1.5 and nt == 0
+    # nothing acceptable: the last trial, 2^-4, is taken
+    a, _, _, _ = O.line_search(x, x, E, float(np.sum(g * x)), quad, prm)
+    assert a == 0.5 ** 4
+
+
+def test_step_cap_bounds_each_iteration():
+    """No vertex moves more than (1 + push_eta) max_step mean edge lengths in one iteration
+    (the largest trial of the capped direction)."""
+    m = ti.two_icospheres(offset=(1.95, 0.0, 0.0))
+    prm = O.NewtonParams(newton_max_it=1, mode="inter", max_step=0.05)
+    e = np.concatenate([m.x[m.tri[:, 1]] - m.x[m.tri[:, 0]], m.x[m.tri[:, 2]] - m.x[m.tri[:, 1]],
+                        m.x[m.tri[:, 0]] - m.x[m.tri[:, 2]]])
+    cap = prm.max_step * float(np.linalg.norm(e, axis=1).mean())
+    _, _, _, d, _ = O.newton_direction(m.x, m.tri, m.group, prm)
+    assert np.linalg.norm(d, axis=1).max() > cap          # the cap is active here
+    x1, _, _ = O.newton_solve(m.x, m.tri, m.group, prm)
+    moved = np.linalg.norm(x1 - m.x, axis=1).max()
+    assert 0 < moved <= (1 + prm.push_eta) * cap * (1 + 1e-12)
+    dc = O.capped_direction(d, cap)
+    assert np.linalg.norm(dc, axis=1).max() == pytest.approx(cap)
+    assert np.allclose(dc / np.linalg.norm(dc), d / np.linalg.norm(d))
 
 
 @pytest.mark.slow
@@ -642,6 +715,35 @@ def test_newton_direction_elastic_solves_system():
     r = (H + mu * np.eye(len(H))) @ d[rows].ravel() + grad[rows].ravel()
     assert np.linalg.norm(r) <= 1e-9 * np.linalg.norm(grad)
     assert np.sum(grad * d) < 0
+
+
+def test_elastic_system_composition():
+    """The Newton system of E_el + sum T (prestressed springs and anchors, so the elastic part
+    is not zero): its energy is the pairs' sum T plus the elastic energy, and its gradient minus
+    the pairs' assembled gradient is the derivative of the elastic energy, checked by central
+    differences (the elastic term is smooth; T jumps where a vertex crosses a face, so the
+    total is not differenced)."""
+    m = ti.cloth(12, seed=21)
+    rng = np.random.default_rng(7)
+    e = O.mesh_edges(m.tri)
+    rest = rng.uniform(0.8, 1.2, len(e)) * np.linalg.norm(m.x[e[:, 0]] - m.x[e[:, 1]], axis=1)
+    anchors = np.array([3, 50, 100])
+    el = O.Elastic(e, rest, 0.5, anchors, m.x[anchors] + 0.02, 2.0)
+    prm = O.NewtonParams()
+    E, n, grad, _, _ = O.newton_direction_elastic(m.x, m.tri, None, prm, el)
+    assert n > 0
+    sum_T = O.energy(m.x, m.tri, None, prm)[0]
+    E_el = O.elastic_energy(m.x, el)
+    assert E_el > 1e-2 * sum_T
+    assert E == pytest.approx(sum_T + E_el, rel=1e-13)
+    assert O.total_energy(m.x, m.tri, None, prm, el)[0] == pytest.approx(sum_T + E_el, rel=1e-13)
+    ev = O.evaluate(m.x, m.tri, O.candidate_pairs(m.x, m.tri))
+    g_el = grad - O.assemble(m.tri, ev, m.V)[0]
+    h = 1e-6
+    for _ in range(4):
+        v = rng.standard_normal(m.x.shape)
+        fd = (O.elastic_energy(m.x + h * v, el) - O.elastic_energy(m.x - h * v, el)) / (2 * h)
+        assert fd == pytest.approx(float(np.sum(g_el * v)), rel=1e-6)
 
 
 def test_zero_length_spring():
