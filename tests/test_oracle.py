@@ -446,6 +446,44 @@ def test_newton_direction_solves_system():
     assert np.sum(grad * d) < 0   # descent direction
 
 
+def test_newton_rows_are_vertices_of_intersecting_pairs():
+    """The policy's system (H+ + mu I) d = -g lives on the vertices of intersecting pairs, and
+    mu is mu_rel times the mean diagonal there (reading 10): no vertex of a candidate that
+    does not intersect is a row."""
+    m = ti.triangle_soup(120, seed=5, size=0.45)
+    prm = O.NewtonParams()
+    pairs = O.candidate_pairs(m.x, m.tri)
+    act = O.exact.active_exact(m.x, m.tri, pairs)
+    assert 0 < act.sum() < len(pairs)
+    rows = sorted({int(v) for p in pairs[act] for t in p for v in m.tri[t]})
+    _, n, _, d, verts = O.newton_direction(m.x, m.tri, None, prm)
+    assert n == act.sum() and list(verts) == rows
+    others = np.setdiff1d(np.arange(m.V), rows)
+    assert np.all(d[others] == 0.0)
+
+
+def test_mesh_edges_counts():
+    """Unique undirected edges: 3F/2 on a closed mesh (every edge shared by two triangles),
+    V + F - 1 on a triangulated disk (Euler: V - E + F = 1)."""
+    s = ti.icosphere(2)
+    e = O.mesh_edges(s.tri)
+    assert len(e) == 3 * s.F // 2 and np.all(e[:, 0] < e[:, 1])
+    c = ti.cloth(9, seed=2, crossing=False)
+    assert len(O.mesh_edges(c.tri)) == c.V + c.F - 1
+    assert len({tuple(r) for r in O.mesh_edges(c.tri)}) == c.V + c.F - 1
+
+
+def test_side_filter_certifies_generic_signs():
+    """The FP64 side filter leaves a sign undecided only near a tie: on random triangles every
+    one of the six signs of almost every pair is certified."""
+    m = ti.triangle_soup(150, seed=11, size=0.5)
+    pairs = np.array([(i, j) for i in range(m.F) for j in range(i + 1, m.F)], np.int64)
+    f = O.filtered_sides(m.x, m.tri, pairs)
+    assert np.mean(f == 2) < 1e-3
+    for k in range(6):
+        assert np.mean(f[:, k] == 2) < 1e-3, k
+
+
 def test_line_search_rule():
     """The policy's line search on E(x) = |x|^2 (one intersecting pair throughout unless stated),
     decided by hand: trials 1.5, 1, 1/2, ...; Armijo E(x + a d) <= E + c a g.d, or no pair."""
