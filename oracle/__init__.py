@@ -27,6 +27,10 @@ Parity status of each function:
                              differences, projected-spectrum closed form,
                              invariances (the elastic model is a reading: the
                              paper does not state it)
+
+The pins are themselves checked: tests/test_oracle_mutations.py plants one
+plausible mistake at a time in a copy of this package and requires the pin
+that covers it to fail.
 """
 from .ttie_oracle import (build_oracle, candidate_pairs, partners_of, evaluate,  # noqa: F401
                           eval_pairs_f64, filtered_sides, gradient, hessian_parts,
