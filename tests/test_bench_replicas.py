@@ -44,3 +44,27 @@ def test_two_rank_aggregation():
     for rank, secs, pairs in out:
         assert secs == pytest.approx(0.2)       # max over ranks of 100 ms and 200 ms
         assert pairs == 3000                    # 1000 + 2000
+
+
+def test_reference_arm_line():
+    """bench.py --impl reference (the oracle on host cores) prints one JSON line with the
+    contract's keys: impl, the same metric and unit as the GPU arm, a positive value, a
+    cpu_baseline describing the run and an e2e with no transfers."""
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--steps", "2",
+                        "--warmup", "0"], cwd=root, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    sys.path.insert(0, root)
+    import bench
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == bench.UNIT
+    assert d["value"] > 0 and d["higher_is_better"] is True and d["steps"] == 2 and d["warmup"] == 0
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    assert d["config"]["workload"] and d["vs_baseline"] is None
