@@ -55,6 +55,8 @@ def test_appendix_half_scale():
     e2 = O.evaluate(m.x, m.tri, np.array([[0, 1]]), tc_scale=0.5)
     assert np.allclose(e2.tc, 0.5 * e1.tc)
     assert e2.T[0] == pytest.approx(e1.T[0] / 16)
+    # the scale is a constant factor of t_c, so their gradients scale with it
+    assert np.allclose(e2.dtc, 0.5 * e1.dtc) and np.abs(e1.dtc).max() > 0
 
 
 def test_vertex_on_plane_case():
@@ -398,6 +400,11 @@ def test_certify_respects_pair_mode():
     assert O.certify(x, tri, group, "self") == 3
     assert O.certify(x, tri, group, "instance") == 2
     assert O.certify(x, tri, group, "inter") == 1
+    # the energy of the line search counts the same pairs (three copies of one pair: T each)
+    T1 = O.energy(a.x, a.tri, None, O.NewtonParams())[0]
+    for mode, k in (("self", 3), ("instance", 2), ("inter", 1)):
+        E, n = O.energy(x, tri, group, O.NewtonParams(mode=mode))
+        assert n == k and E == pytest.approx(k * T1, rel=1e-12), mode
 
 
 def test_pair_modes():
