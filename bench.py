@@ -9,6 +9,13 @@ through that step per second (whole job), inputs resident in HBM.  ``e2e`` is
 the same metric through the public API with the positions copied host->device
 before and device->host after every step.
 
+The default workload is the largest single-GPU configuration: the 2,097,152-
+triangle noisy sphere.  The other configurations (two icospheres in FP64 with
+brute-force pairs, the crossing cloth, the interlocked tori with the Adam loop,
+the batch of 512 ellipsoid pairs) are reported under ``configs`` in the same
+line, each with its time per step, rooflines and the outcome of the solve to
+intersection-free in the FP32 form and the plain FP64 form.
+
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 ``--impl reference`` times the CPU oracle (the program the CUDA path is
@@ -26,41 +33,63 @@ sys.path.insert(0, ROOT)
 
 METRIC = "TTIE pair evals/s (E+grad+PSD Hess+assembly); seconds to intersection-free"
 UNIT = "pair evals/s"
-# dram__bytes_read.sum + dram__bytes_write.sum per launch, one ncu capture of the default
-# workload (256x256 crossing cloth, first Newton step) with the kernels as they are now;
-# reported only for that workload.
-NCU_TRAFFIC = {"cloth256": {"k_pcg_resident": 20037376, "k_classify": 8869888}}
 L2_FLUSH_BYTES = 256 << 20   # larger than the 129 MB L2
+# dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant kernel, from one ncu
+# capture of the kernels as they are now (None until one is taken)
+NCU_TRAFFIC = {}
+
+# Algorithmic bytes (the minimum an implementation moves, FP32):
+B_CANDIDATE = 104.0      # pair ids 8 + 2 x (indices 12 + coordinates 36)
+B_ACTIVE_EVAL = 228.0    # T 4 + gradient 72 + t_c and their gradients 152
+B_ASM_PAIR = 36 * 36 * 2 + 36 * 8   # 36 block values written and read, 36 keys
+B_ASM_BLOCK = 36.0       # assembled 3x3 block
+B_PCG_BLOCK = 40.0       # per product: 3x3 block 36 + column index 4
+B_PCG_ROW = 72.0         # per product: 3 floats x 6 vectors per row
 
 
 def workload(name):
-    """(mesh, precision, description, pair mode: 0 all pairs, 2 pairs within a group)."""
+    """(mesh, precision, description, pair mode: 0 self, 1 inter-group, 2 intra-group; brute)."""
     import ttie_inputs as ti
+    if name == "noisy_sphere":
+        return ti.noisy_sphere(9, seed=5).as_f32(), 0, (
+            "octahedral sphere level 9 (2,097,152 triangles, radius 1) displaced by 0.15*(N1,N2,N3), three "
+            "seeded 5-octave value-noise fields of base frequency 8 (folds through itself); self pairs, "
+            "LBVH; float32"), 0, False
+    if name == "noisy_sphere_literal":
+        return ti.noisy_sphere(9, seed=5, vector=False).as_f32(), 0, (
+            "octahedral sphere level 9 displaced radially by 0.15*N (intersection-free by construction); "
+            "float32"), 0, False
     if name == "cloth256":
         return ti.cloth(256, seed=2).as_f32(), 0, (
             "cloth 256x256 vertices (130,050 triangles) on [0,1]^2, z = 8 seeded sinusoids "
             "(A~U[0.05,0.3], k~U[2,12]), x += 0.4*g(x,y) with g an independent 8-sinusoid field "
-            "(folds that cross themselves); self pairs, LBVH; float32"), 0
+            "(folds that cross themselves); self pairs, LBVH; float32"), 0, False
     if name == "cloth256_literal":
         return ti.cloth(256, seed=2, crossing=False).as_f32(), 0, (
-            "cloth 256x256 (130,050 triangles), x += 0.4*z shear (intersection-free by construction)"), 0
-    if name == "noisy_sphere":
-        return ti.noisy_sphere(9, seed=5).as_f32(), 0, (
-            "octahedral sphere level 9 (2,097,152 triangles) displaced by 0.15*(N1,N2,N3) value noise"), 0
+            "cloth 256x256 (130,050 triangles), x += 0.4*z shear (intersection-free by construction)"), 0, False
     if name == "ellipsoids512":
         m, _, _ = ti.ellipsoid_batch(512, seed=4)
         return m.as_f32(), 0, (
             "512 independent pairs of lat-long ellipsoids, triangles per mesh log-uniform in [100, 20000], "
             "semi-axes U[0.5,1.5], random relative rotation, centre offset U[0.3,1] x (sum of mean semi-axes); "
-            "pairs within an instance, each instance solved on its own (per-instance PCG blocks in one launch, "
-            "per-instance line search); float32"), 2
+            "pairs within an instance, each instance solved on its own; float32"), 2, False
+    if name == "icospheres":
+        return ti.two_icospheres(), 1, (
+            "two unit icospheres (2 subdivisions, 320 triangles each), the second rotated at random and "
+            "centred at (1.2, 0, 0); all 102,400 inter-mesh pairs by brute force; float64"), 1, True
+    if name == "tori":
+        return ti.interlocked_tori(offset=(0.5, 0, 0)).as_f32(), 0, (
+            "two tori R=1, r=0.3, 256x128 segments (65,536 triangles each), the second rotated 90 deg "
+            "about x and offset by (0.5, 0, 0) so the tubes interpenetrate, Gaussian jitter 0.005; self "
+            "pairs, LBVH; float32"), 0, False
     raise SystemExit("unknown workload %s" % name)
 
 
 def oracle_sample(m, n_side, mode=0):
     """The workload restricted to the first n_side x n_side grid vertices (cloth), to whole
-    instances up to about 2 n_side^2 triangles (batched instances), or to the first triangles
-    (others): what the oracle can process in seconds."""
+    instances up to about 2 n_side^2 triangles (batched instances), or to the 2 n_side^2
+    triangles whose centroids lie nearest the first triangle's (a connected patch, others):
+    what the oracle can process in seconds."""
     import numpy as np
     import ttie_inputs as ti
     if m.V == 256 * 256:
@@ -72,8 +101,10 @@ def oracle_sample(m, n_side, mode=0):
         upto = max(1, int(np.searchsorted(np.cumsum(counts), 2 * n_side * n_side)))
         keep_t = m.group < upto
     else:
+        cen = m.x[m.tri].mean(axis=1)
+        near = np.argsort(np.linalg.norm(cen - cen[0], axis=1), kind="stable")[: n_side * n_side * 2]
         keep_t = np.zeros(m.F, bool)
-        keep_t[: n_side * n_side * 2] = True
+        keep_t[near] = True
     tri = m.tri[keep_t]
     used = np.unique(tri)
     remap = -np.ones(m.V, np.int64)
@@ -85,7 +116,7 @@ def oracle_step(sub, mode=0):
     """One pass of the oracle over the sample: brute-force candidates, per-pair evaluation
     (duals + exact test), gradient, PSD Hessian and assembly.  Returns candidate pairs."""
     import oracle as O
-    pairs = O.candidate_pairs(sub.x, sub.tri, sub.group, "instance" if mode == 2 else "self")
+    pairs = O.candidate_pairs(sub.x, sub.tri, sub.group, ("self", "inter", "instance")[mode])
     ev = O.evaluate(sub.x, sub.tri, pairs)
     O.assemble(sub.tri, ev, sub.V)
     return len(pairs)
@@ -168,7 +199,7 @@ def run_reference(args, rank, world):
     """CPU oracle arm: rank 0 only."""
     if rank != 0:
         return
-    m, _, desc, mode = workload(args.workload)
+    m, _, desc, mode, _ = workload(args.workload)
     sub = oracle_sample(m, 24, mode)
     for _ in range(args.warmup):
         oracle_step(sub, mode)
@@ -178,7 +209,7 @@ def run_reference(args, rank, world):
         n += oracle_step(sub, mode)
     dt = time.perf_counter() - t0
     v = n / dt
-    sample = "oracle on a 24x24-vertex patch of the workload (%d triangles, %d candidate pairs per step)" % (
+    sample = "oracle on a %d-triangle patch of the workload (%d candidate pairs per step)" % (
         sub.F, n // max(args.steps, 1))
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -202,19 +233,38 @@ def cpu_baseline(m, mode=0, seconds_target=15.0):
             break
     dt = time.perf_counter() - t0
     return {"value": n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "oracle on a sample of the workload (an 80x80-vertex patch of a grid, or whole instances "
-                      "up to ~12,800 triangles; %d triangles, %d candidate pairs) x %d, %.1f s" % (
-                          sub.F, n // reps, reps, dt)}
+            "sample": "oracle on a sample of the workload (an 80x80-vertex patch of a grid, whole instances "
+                      "up to ~12,800 triangles, or a patch of 12,800 triangles; %d triangles, %d candidate "
+                      "pairs) x %d, %.1f s" % (sub.F, n // reps, reps, dt)}
+
+
+def rooflines(last, ms, peak, hbm):
+    """Algorithmic bytes per launch (or stage) over its CUDA-event duration, against the peak.
+    ms: per-step milliseconds of the PCG kernel, the classification kernel and the assembly
+    and evaluation stages."""
+    src = "measured" if hbm else "fallback"
+
+    def line(name, nbytes, t_ms, kind="kernel"):
+        ach = nbytes / (t_ms * 1e-3) / 1e9 if t_ms > 0 else None
+        return {kind: name, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "peak_source": src,
+                "frac": ach / peak if ach else None, "ms": t_ms, "algorithmic_bytes": nbytes}
+    pcg = line("k_pcg_resident", B_PCG_BLOCK * last["pcg_block_iters"] + B_PCG_ROW * last["pcg_row_iters"], ms["pcg"])
+    cls = line("k_classify", B_CANDIDATE * last["n_candidates"], ms["classify"])
+    asm = line("assemble", B_ASM_PAIR * last["n_active"] + B_ASM_BLOCK * last["nnzb"], ms["assemble"], "stage")
+    ev = line("eval", B_CANDIDATE * last["n_candidates"] + B_ACTIVE_EVAL * last["n_active"], ms["eval"], "stage")
+    return pcg, cls, asm, ev
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=60)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="cloth256")
-    ap.add_argument("--no-solve", action="store_true", help="skip the time-to-intersection-free run")
+    ap.add_argument("--workload", default="noisy_sphere")
+    ap.add_argument("--configs", default="icospheres,cloth256,tori,ellipsoids512",
+                    help="further configurations reported under 'configs' ('' for none)")
+    ap.add_argument("--no-solve", action="store_true", help="skip the solves to intersection-free")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-form", action="store_true", help="skip the plain FP64 comparison")
     ap.add_argument("--no-quasi-static", action="store_true", help="skip the quasi-static simulation run")
@@ -248,22 +298,94 @@ def main():
     __graft_entry__.build()
     from paper_2606_06511_gb300 import ttie
 
-    m, precision, desc, mode = workload(args.workload)
-    dt = torch.float32 if precision == 0 else torch.float64
-    x0 = torch.tensor(m.x, dtype=dt, device="cuda")
-    tri = torch.tensor(m.tri, dtype=torch.int32, device="cuda")
-    grp = torch.tensor(m.group, dtype=torch.int32, device="cuda") if mode else None
-    x = x0.clone()
     solver = {"pcg_precond": {"block_jacobi": ttie.PCG_BLOCK_JACOBI, "chebyshev": ttie.PCG_CHEBYSHEV}[args.pcg_precond],
               "pcg_cheb_degree": args.pcg_cheb_degree,
               "assembly_mode": {"sorted_keys": ttie.ASSEMBLY_SORTED_KEYS,
                                 "row_buckets": ttie.ASSEMBLY_ROW_BUCKETS}[args.assembly],
               "traversal_mode": {"two_walks": ttie.TRAVERSAL_TWO_WALKS,
                                  "one_walk": ttie.TRAVERSAL_ONE_WALK}[args.traversal]}
-    ctx = ttie.Context(precision=precision, pair_mode=mode, profile=1, **solver)
-    ctx.build_bvh(x0, tri, grp)
     stream = torch.cuda.current_stream()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    peaks = measured_peaks()
+    hbm = peaks.get("hbm_gbs")
+    peak = hbm if hbm else 6800.0
+
+    def on_device(m, precision, mode):
+        dt = torch.float32 if precision == 0 else torch.float64
+        x0 = torch.tensor(m.x, dtype=dt, device="cuda")
+        tri = torch.tensor(m.tri, dtype=torch.int32, device="cuda")
+        grp = torch.tensor(m.group, dtype=torch.int32, device="cuda") if mode else None
+        return x0, tri, grp
+
+    def time_steps(ctx, x0, steps, warmup):
+        """Newton steps from x0 (L2 flushed before each), timed with CUDA events on the stream."""
+        x = x0.clone()
+        for _ in range(warmup):
+            x.copy_(x0)
+            ctx.newton_step(x)
+        torch.cuda.synchronize()
+        tot, pairs, active = 0.0, 0, 0
+        stage = {"build": 0.0, "eval": 0.0, "assemble": 0.0, "pcg": 0.0, "line_search": 0.0}
+        kern = {"classify": 0.0, "pcg": 0.0}
+        last = None
+        for _ in range(steps):
+            x.copy_(x0)
+            flush.zero_()
+            ev0.record(stream)
+            info = ctx.newton_step(x)
+            ev1.record(stream)
+            ev1.synchronize()
+            tot += ev0.elapsed_time(ev1)
+            pairs += info["n_candidates"]
+            active += info["n_active"]
+            for k in stage:
+                stage[k] += info["ms_" + k]
+            kern["classify"] += info["ms_classify"]
+            kern["pcg"] += info["ms_pcg_kernel"]
+            last = info
+        ms = {"pcg": kern["pcg"] / steps, "classify": kern["classify"] / steps,
+              "assemble": stage["assemble"] / steps, "eval": stage["eval"] / steps}
+        return {"total_ms": tot, "pairs": pairs, "active": active, "last": last,
+                "stage_ms_per_step": {k: v / steps for k, v in stage.items()}, "kernel_ms": ms}
+
+    def certify(m, x, mode):
+        """The oracle's exact test on an end state (intersecting pairs; 0 = intersection-free),
+        with its brute-force candidate list where that fits the bench's time."""
+        import oracle as O
+        if m.F > 20000:
+            return None
+        return O.certify(x.double().cpu().numpy(), m.tri, m.group, ("self", "inter", "instance")[mode])
+
+    def solve_outcome(m, precision, mode, brute, max_it=100):
+        """Seconds to intersection-free (ttie_solve's wall time, after one solve that allocates the
+        context's buffers), with the end state certified by the oracle where its brute force fits."""
+        x0, tri, grp = on_device(m, precision, mode)
+        pm = mode | (ttie.PAIRS_BRUTE if brute else 0)
+        c = ttie.Context(precision=precision, pair_mode=pm, newton_max_it=max_it, **solver)
+        try:
+            c.build_bvh(x0, tri, grp)
+            c.newton_step(x0.clone())   # allocations
+            xs = x0.clone()
+            torch.cuda.synchronize()
+            s = c.solve(xs)
+            cert = certify(m, xs, mode) if s["converged"] else None
+            return {"dtype": "f32" if precision == 0 else "f64", "converged": bool(s["converged"]),
+                    "iterations": s["iterations"], "seconds": s["seconds"],
+                    "n_active_initial": s["n_active_initial"], "n_active_final": s["n_active_final"],
+                    "energy_initial": s["energy_initial"], "energy_final": s["energy_final"],
+                    "newton_max_it": max_it,
+                    "oracle_certified_intersecting": cert}
+        except ttie.TTIEError as e:   # reported, the line still prints
+            return {"dtype": "f32" if precision == 0 else "f64", "error": str(e)[:200]}
+        finally:
+            c.close()
+
+    # ---------------------------------------------------------------- main workload
+    m, precision, desc, mode, brute = workload(args.workload)
+    x0, tri, grp = on_device(m, precision, mode)
+    ctx = ttie.Context(precision=precision, pair_mode=mode | (ttie.PAIRS_BRUTE if brute else 0), profile=1, **solver)
+    ctx.build_bvh(x0, tri, grp)
 
     def barrier():
         torch.cuda.synchronize()
@@ -273,38 +395,22 @@ def main():
 
     clocks = Clocks(local)
     clocks.start()
+    x = x0.clone()
     for _ in range(args.warmup):
         x.copy_(x0)
-        info = ctx.newton_step(x)
+        ctx.newton_step(x)
     barrier()
     clocks.mark_begin()
     launches0 = ctx.get_launch_count()
-    total_ms, pairs, active = 0.0, 0, 0
-    stage = {"build": 0.0, "eval": 0.0, "assemble": 0.0, "pcg": 0.0, "line_search": 0.0}
-    kern = {"classify": 0.0, "pcg": 0.0}
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    infos = []
-    for _ in range(args.steps):
-        x.copy_(x0)
-        flush.zero_()
-        ev0.record(stream)
-        info = ctx.newton_step(x)
-        ev1.record(stream)
-        ev1.synchronize()
-        total_ms += ev0.elapsed_time(ev1)
-        pairs += info["n_candidates"]
-        active += info["n_active"]
-        for k in stage:
-            stage[k] += info["ms_" + k]
-        kern["classify"] += info["ms_classify"]
-        kern["pcg"] += info["ms_pcg_kernel"]
-        infos.append(info)
+    main_t = time_steps(ctx, x0, args.steps, 0)
     launches = ctx.get_launch_count() - launches0
     barrier()
     clocks.mark_end()
     clk = clocks.stop()
-    total_s, all_pairs = aggregate(total_ms, pairs, world, "cuda")
+    total_ms = main_t["total_ms"]
+    total_s, all_pairs = aggregate(total_ms, main_t["pairs"], world, "cuda")
     value = all_pairs / total_s
+    last = main_t["last"]
 
     # end to end through the public API with host buffers
     xh0 = x0.cpu().pin_memory()
@@ -323,129 +429,88 @@ def main():
             e2e_pairs += info["n_candidates"]
     e2e_bytes = x0.numel() * x0.element_size()
 
-    # Rooflines (algorithmic bytes per launch / CUDA-event duration of that launch):
-    # the dominant kernel is the persistent PCG: per iteration the block-CSR matrix
-    # (36 B value + 4 B column per 3x3 block) and 160 B of vector traffic per row, summed over
-    # the iterations each instance ran
-    # (z read/write, p, q, x, r updates, inverse diagonal block, row offset);
-    # the pair kernel is the narrow-phase classification, 104 B per candidate
-    # (pair ids 8 B + 2 x (indices 12 B + coordinates 36 B)).
-    peaks = measured_peaks()
-    hbm = peaks.get("hbm_gbs")
-    peak = hbm if hbm else 6800.0
-    last = infos[-1]
-    pcg_ms = kern["pcg"] / args.steps
-    pcg_bytes = 40.0 * last["pcg_block_iters"] + 160.0 * last["pcg_row_iters"]
-    pcg_ach = pcg_bytes / (pcg_ms * 1e-3) / 1e9 if pcg_ms > 0 else None
-    roofline = {"kernel": "k_pcg_instances" if mode == 2 else "k_pcg_resident", "bound": "hbm", "achieved": pcg_ach, "peak": peak, "unit": "GB/s",
-                "peak_source": "measured" if hbm else "fallback", "frac": pcg_ach / peak if pcg_ach else None,
-                "traffic": NCU_TRAFFIC.get(args.workload, {}).get("k_pcg_resident"), "ms_per_launch": pcg_ms, "algorithmic_bytes_per_launch": pcg_bytes,
-                "share_of_step": pcg_ms / (total_ms / args.steps)}
-    k_ms = kern["classify"] / args.steps
-    n_cand = last["n_candidates"]
-    cl_ach = 104.0 * n_cand / (k_ms * 1e-3) / 1e9 if k_ms > 0 else None
-    roofline_pairs = {"kernel": "k_classify", "bound": "hbm", "achieved": cl_ach, "peak": peak, "unit": "GB/s",
-                      "peak_source": "measured" if hbm else "fallback", "frac": cl_ach / peak if cl_ach else None,
-                      "traffic": NCU_TRAFFIC.get(args.workload, {}).get("k_classify"), "ms_per_launch": k_ms, "algorithmic_bytes_per_launch": 104.0 * n_cand}
-    # the assembly stage as a whole (its sort passes, kernels and two host reads of sizes):
-    # 36 block keys of 8 B and 36 block values of 36 B per intersecting pair
-    asm_ms = stage["assemble"] / args.steps
-    asm_bytes = 1584.0 * last["n_active"]
-    asm_ach = asm_bytes / (asm_ms / 1e3) / 1e9 if asm_ms > 0 else None
-    roofline_asm = {"stage": "assemble", "bound": "hbm", "achieved": asm_ach, "peak": peak, "unit": "GB/s",
-                    "peak_source": "measured" if hbm else "fallback", "frac": asm_ach / peak if asm_ach else None,
-                    "ms_per_step": asm_ms, "algorithmic_bytes_per_step": asm_bytes}
+    r_pcg, r_cls, r_asm, r_ev = rooflines(last, main_t["kernel_ms"], peak, hbm)
+    r_pcg["kernel"] = "k_pcg_instances" if mode == 2 else "k_pcg_resident"
+    r_pcg["traffic"] = NCU_TRAFFIC.get((args.workload, "pcg"))
+    r_cls["traffic"] = NCU_TRAFFIC.get((args.workload, "classify"))
+    r_pcg["share_of_step"] = r_pcg["ms"] / (total_ms / args.steps)
+    roofline = r_pcg
 
-    # the plain FP64 form on the same GPU: every stage in double precision (same kernels
-    # instantiated for FP64), a few steps of the same workload
+    def fp64_form(mm, mode_, brute_, steps):
+        """The plain FP64 form on the same GPU: every stage in double precision (same kernels
+        instantiated for FP64), a few steps of the workload."""
+        x64_0, tri64, grp64 = on_device(mm, 1, mode_)
+        c64 = ttie.Context(precision=ttie.F64, pair_mode=mode_ | (ttie.PAIRS_BRUTE if brute_ else 0), profile=1,
+                           **solver)
+        c64.build_bvh(x64_0, tri64, grp64)
+        t = time_steps(c64, x64_0, steps, args.warmup)
+        c64.close()
+        return {"value": t["pairs"] / (t["total_ms"] / 1e3), "unit": UNIT, "ms_per_step": t["total_ms"] / steps,
+                "steps": steps, "dtype": "f64", "pcg_iters": t["last"]["pcg_iters"],
+                "intersecting_per_step": t["last"]["n_active"], "stage_ms_per_step": t["stage_ms_per_step"]}
+
     fp64 = None
     if precision == 0 and not args.no_fp64_form and rank == 0:
-        x64_0 = torch.tensor(m.x, dtype=torch.float64, device="cuda")
-        x64 = x64_0.clone()
-        ctx64 = ttie.Context(precision=ttie.F64, pair_mode=mode, profile=1, **solver)
-        ctx64.build_bvh(x64_0, tri, grp)
-        n64 = max(3, min(args.steps, 10))
-        for _ in range(args.warmup):
-            x64.copy_(x64_0)
-            ctx64.newton_step(x64)
-        ms64, pairs64, stage64 = 0.0, 0, {k: 0.0 for k in stage}
-        for _ in range(n64):
-            x64.copy_(x64_0)
-            flush.zero_()
-            ev0.record(stream)
-            i64 = ctx64.newton_step(x64)
-            ev1.record(stream)
-            ev1.synchronize()
-            ms64 += ev0.elapsed_time(ev1)
-            pairs64 += i64["n_candidates"]
-            for k in stage64:
-                stage64[k] += i64["ms_" + k]
-        fp64 = {"value": pairs64 / (ms64 / 1e3), "unit": UNIT, "ms_per_step": ms64 / n64, "steps": n64,
-                "dtype": "f64", "pcg_iters": i64["pcg_iters"], "intersecting_per_step": i64["n_active"],
-                "stage_ms_per_step": {k: v / n64 for k, v in stage64.items()},
-                "speedup_of_fp32_form": (ms64 / n64) / (total_ms / args.steps)}
-        ctx64.close()
-
-    # broad phase alone: LBVH against the spatial-hash grid, same candidate set
-    broad = None
-    if rank == 0 and mode != 2:
-        broad = {}
-        for name, flag in (("lbvh", 0), ("hash", ttie.PAIRS_HASH)):
-            cb = ttie.Context(precision=precision, pair_mode=mode | flag)
-            cb.build_bvh(x0, tri, grp)
-            ms = []
-            for _ in range(5):
-                flush.zero_()
-                ev0.record(stream)
-                nb = cb.build_bvh(x0, tri, grp)
-                ev1.record(stream)
-                ev1.synchronize()
-                ms.append(ev0.elapsed_time(ev1))
-            broad[name] = {"ms": sorted(ms)[len(ms) // 2], "candidates": nb}
-            cb.close()
+        fp64 = fp64_form(m, mode, brute, max(3, min(args.steps, 10)))
+        fp64["speedup_of_fp32_form"] = fp64["ms_per_step"] / (total_ms / args.steps)
 
     solve = None
     if not args.no_solve and rank == 0:
-        xs = x0.clone()
-        ctx.set_params(newton_max_it=100)
-        torch.cuda.synchronize()
-        s = ctx.solve(xs)
-        solve = {"converged": bool(s["converged"]), "iterations": s["iterations"], "seconds": s["seconds"],
-                 "n_active_initial": s["n_active_initial"], "n_active_final": s["n_active_final"],
-                 "energy_initial": s["energy_initial"], "energy_final": s["energy_final"],
-                 "newton_max_it": 100}
+        solve = {"f32": solve_outcome(m, precision, mode, brute)}
+        if precision == 0 and not args.no_fp64_form:
+            solve["f64"] = solve_outcome(m, 1, mode, brute)
 
-    # seconds to intersection-free where the method reaches it: a shallow overlap of two
-    # spheres and a mildly folded cloth (the certified end state is the library's own exact
-    # decision, n_active_final = 0); median of 5 solves after one that allocates the buffers
+    # ---------------------------------------------------------------- the other configurations
+    configs = {}
+    if rank == 0:
+        for name in [c for c in args.configs.split(",") if c and c != args.workload]:
+            mc, pc, dc, mdc, bc = workload(name)
+            entry = {"workload": dc, "triangles": mc.F, "vertices": mc.V}
+            try:
+                xc0, tc_, gc = on_device(mc, pc, mdc)
+                cc = ttie.Context(precision=pc, pair_mode=mdc | (ttie.PAIRS_BRUTE if bc else 0), profile=1, **solver)
+                cc.build_bvh(xc0, tc_, gc)
+                ks = max(3, min(args.steps, 10))
+                t = time_steps(cc, xc0, ks, args.warmup)
+                cc.close()
+                lc = t["last"]
+                rp, rc, ra, re = rooflines(lc, t["kernel_ms"], peak, hbm)
+                if mdc == 2:
+                    rp["kernel"] = "k_pcg_instances"
+                entry.update({
+                    "dtype": "f32" if pc == 0 else "f64", "steps": ks, "ms_per_step": t["total_ms"] / ks,
+                    "value": t["pairs"] / (t["total_ms"] / 1e3), "unit": UNIT,
+                    "active_pairs_per_s": t["active"] / (t["total_ms"] / 1e3),
+                    "candidates_per_step": lc["n_candidates"], "intersecting_per_step": lc["n_active"],
+                    "pcg_iters": lc["pcg_iters"], "bsr_rows": lc["n_rows"], "bsr_blocks": lc["nnzb"],
+                    "stage_ms_per_step": t["stage_ms_per_step"],
+                    "roofline_pcg": rp, "roofline_pair_eval": rc, "roofline_assembly": ra, "roofline_eval": re})
+                if pc == 0 and not args.no_fp64_form:
+                    f = fp64_form(mc, mdc, bc, ks)
+                    f["speedup_of_fp32_form"] = f["ms_per_step"] / entry["ms_per_step"]
+                    entry["fp64_form"] = f
+                if not args.no_solve:
+                    entry["solve"] = {"f32" if pc == 0 else "f64": solve_outcome(mc, pc, mdc, bc)}
+                    if pc == 0 and not args.no_fp64_form:
+                        entry["solve"]["f64"] = solve_outcome(mc, 1, mdc, bc)
+            except Exception as e:   # a failure here is reported, the line still prints
+                entry["error"] = "%s: %s" % (type(e).__name__, str(e)[:200])
+            configs[name] = entry
+
+    # seconds to intersection-free where the method reaches it on small scenes: a shallow
+    # overlap of two spheres and a mildly folded cloth (substitute workloads, not configs)
     reach = None
     if not args.no_solve and rank == 0:
         reach = []
-        for name, mr, pm, desc in (
-                ("spheres_shallow", ti.two_icospheres(offset=(1.95, 0.0, 0.0)).as_f32(), 1,
-                 "two unit icospheres (640 triangles), overlap 0.05, inter-mesh pairs; float32"),
-                ("cloth_mild", ti.cloth(16, seed=2, shear=0.05).as_f32(), 0,
-                 "16x16-vertex cloth, the crossing fold field scaled to 0.05; self pairs; float32")):
-            try:
-                xr0 = torch.tensor(mr.x, dtype=torch.float32, device="cuda")
-                tr = torch.tensor(mr.tri, dtype=torch.int32, device="cuda")
-                gr = torch.tensor(mr.group, dtype=torch.int32, device="cuda")
-                cr = ttie.Context(pair_mode=pm, newton_max_it=60, **solver)
-                cr.build_bvh(xr0, tr, gr)
-                runs = []
-                for _ in range(6):
-                    xr = xr0.clone()
-                    torch.cuda.synchronize()
-                    runs.append(cr.solve(xr))
-                runs = sorted(runs[1:], key=lambda r: r["seconds"])
-                r = runs[len(runs) // 2]
-                reach.append({"workload": name, "description": desc, "triangles": mr.F,
-                              "converged": bool(r["converged"]), "iterations": r["iterations"],
-                              "seconds": r["seconds"], "n_active_initial": r["n_active_initial"],
-                              "n_active_final": r["n_active_final"], "runs": 5})
-                cr.close()
-            except Exception as e:   # a failure here is reported, the line still prints
-                reach.append({"workload": name, "error": str(e)[:200]})
+        for name, mr, pm, d in (
+                ("spheres_shallow", ti.two_icospheres(offset=(1.95, 0.0, 0.0)), 1,
+                 "two unit icospheres (640 triangles), overlap 0.05, inter-mesh pairs"),
+                ("cloth_mild", ti.cloth(16, seed=2, shear=0.05), 0,
+                 "16x16-vertex cloth, the crossing fold field scaled to 0.05; self pairs")):
+            row = {"workload": name, "description": d, "triangles": mr.F}
+            for prec in (0, 1):   # the same float32-representable start for both forms
+                row["f32" if prec == 0 else "f64"] = solve_outcome(mr.as_f32(), prec, pm, False, max_it=60)
+            reach.append(row)
 
     # the quasi-static simulation (Fig. 2): from an intersecting state to a valid one with a
     # mass-spring term on every edge (rest = initial lengths); seconds to valid, median of 5
@@ -500,6 +565,7 @@ def main():
             cp.build_bvh(x0, tri, grp)
             xs = x0.clone()
             cp.newton_step(xs)   # warm-up (allocations)
+
             def one():
                 xs.copy_(x0)
                 return cp.newton_step(xs)
@@ -539,21 +605,22 @@ def main():
                        "l2": "flushed (256 MiB write) before every timed step",
                        "pcg_precond": args.pcg_precond, "assembly": args.assembly, "traversal": args.traversal,
                        "parallelism": "replicas" if world > 1 else "single GPU"},
-            "stage_ms_per_step": {k: v / args.steps for k, v in stage.items()},
-            "active_pairs_per_s": active / (total_ms / 1e3),
+            "stage_ms_per_step": main_t["stage_ms_per_step"],
+            "active_pairs_per_s": main_t["active"] / (total_ms / 1e3),
             "roofline": roofline,
-            "roofline_pair_eval": roofline_pairs,
-            "roofline_assembly": roofline_asm,
+            "roofline_pair_eval": r_cls,
+            "roofline_assembly": r_asm,
+            "roofline_eval": r_ev,
             "cpu_baseline": cpu,
             "fp64_form": fp64,
-            "broad_phase_ms": broad,
             "e2e": {"value": e2e_pairs / (e2e_ms / 1e3) if e2e_ms > 0 else None, "unit": UNIT,
                     "h2d_bytes_per_step": e2e_bytes, "d2h_bytes_per_step": e2e_bytes},
             "gpu_launches": launches,
             "gpu_launches_per_step": launches / args.steps,
             "clocks": clk,
             "time_to_intersection_free": solve,
-            "time_to_intersection_free_reachable": reach,
+            "configs": configs,
+            "time_to_intersection_free_substitutes": reach,
             "quasi_static": qs,
             "next_rows": nxt,
         }

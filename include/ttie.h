@@ -110,7 +110,21 @@ typedef struct {
                              both give the same pattern and bit-identical values          */
     int traversal_mode;   /* TTIE_TRAVERSAL_*: how the LBVH walk lists candidates; both give
                              the same list in the same order                              */
+    int ls_rule;          /* TTIE_LS_*: which line-search trials are accepted            */
+    double push_eta_max;  /* adaptive overshoot (TTIE_LS_FEWER): when a step took the
+                             overshoot trial 1 + eta and left as many intersecting pairs,
+                             eta doubles for the next step, up to this (<= push_eta: no
+                             growth); it returns to push_eta when a step lowers the count.
+                             Not used by batched instances.                           */
 } ttie_params;
+
+/* Line-search acceptance (the paper states no line search; these are readings of its inexact
+ * Newton route).  E: energy, n: intersecting pairs, at x and at the trial x + a d.
+ * ARMIJO: accept when Armijo's condition holds or no pair intersects at the trial.
+ * FEWER:  ARMIJO, or fewer intersecting pairs with E not above E(x); with the adaptive
+ *         overshoot of push_eta_max.
+ * With either rule the last (smallest) trial of the ladder is taken when none is accepted.  */
+enum { TTIE_LS_ARMIJO = 0, TTIE_LS_FEWER = 1 };
 
 /* LBVH traversal (one thread per leaf, depth-first walk over rope links).
  * TWO_WALKS: a counting walk from the root keeps each leaf's first 16 partners; leaves with
@@ -147,7 +161,8 @@ typedef struct ttie_ctx ttie_ctx;
  * pcg_rtol 1e-3, pcg_max_it 200, newton_max_it 200, ls_max_halvings 20,
  * armijo_c 1e-4, push_eta 0.5, exact_only 0, profile 0, max_step 1,
  * max_candidates 0, inst_threads 0, test_withhold 0, pcg_precond BLOCK_JACOBI,
- * pcg_cheb_degree 0, assembly_mode SORTED_KEYS, traversal_mode TWO_WALKS. */
+ * pcg_cheb_degree 0, assembly_mode SORTED_KEYS, traversal_mode TWO_WALKS, ls_rule FEWER,
+ * push_eta_max 7. */
 void ttie_default_params(ttie_params *p);
 
 /* Creates a context on the current CUDA device.  stream: a cudaStream_t or NULL
@@ -205,7 +220,10 @@ typedef struct {
 
 /*
  * Assembles the PSD Hessian H+ and the gradient of the last ttie_eval_pairs
- * (which must have included TTIE_EVAL_H) over the active vertices.  The block
+ * (which must have included TTIE_EVAL_H) over the active vertices.  Each pair
+ * contributes its gradient (Eq. 3) and its Eq. 4 Hessian projected as §1.1's
+ * eigen-analysis prescribes (params.psd_mode); the Newton system of the inexact
+ * Newton route (abstract, §1.2) is the sum over pairs.  The block
  * pattern is the union of the 6x6 vertex blocks of the intersecting pairs; the
  * sums run in a fixed order (sorted keys), so the result is deterministic.
  * Errors: STATE, OOM, CUDA.
@@ -313,7 +331,10 @@ typedef struct {
 ttie_status ttie_set_elastic(ttie_ctx *ctx, const ttie_elastic *el);
 
 /*
- * One inexact Newton iteration on the mesh recorded by ttie_build_bvh:
+ * One iteration of the inexact Newton method the abstract and §1.2 name for
+ * driving a mesh to an intersection-free state ("GPU-based inexact Newton"; its
+ * tolerances, regulariser and line search are not stated there and are this
+ * library's parameters) on the mesh recorded by ttie_build_bvh:
  * candidates and evaluation at x, assembly, PCG for d, then a backtracking line
  * search over the trial steps 1+push_eta, 1, 1/2, ... on candidates from the
  * boxes swept between x and x + (1+push_eta) d; a trial is accepted when it
@@ -341,7 +362,9 @@ typedef struct {
     double seconds;              /* wall time of the solve                              */
 } ttie_solve_info;
 
-/* Newton iterations until no pair intersects or params.newton_max_it.
+/* Newton iterations until no pair intersects or params.newton_max_it: the paper's
+ * use of the energy, from an intersecting start to a valid state (abstract, §1.2,
+ * Fig. 2); "intersects" is the exact test of ttie_eval_pairs (§1).
  * Returns NOT_CONVERGED (with d_x_inout holding the last iterate) at the limit. */
 ttie_status ttie_solve(ttie_ctx *ctx, void *d_x_inout, ttie_solve_info *info);
 
@@ -387,17 +410,26 @@ ttie_status ttie_get_filter_stats(ttie_ctx *ctx, int64_t *out3);
  * n_rows beyond that limit is refused with TTIE_ERR_INVALID before any work.
  *
  * The first call on a device looks up the array's device address (once per device, with
- * that device current); make that first call before any stream capture begins.  Every
- * call reuses the same array and clears the parts that must start at zero; two calls
- * whose work overlaps on the GPU (other streams, other host threads, the same device)
- * race on it, so serialise them.  Work is enqueued on `stream` (NULL: legacy default
- * stream) and the call synchronises it before returning iters and rel_residual (host
- * outs, nullable).  Errors: INVALID, CUDA (also when the solver's bounded grid-barrier
- * wait runs out), NONFINITE.
+ * that device current).  Every call reuses the same array and clears the parts that must
+ * start at zero; two calls whose work overlaps on the GPU (other streams, other host
+ * threads, the same device) race on it, so serialise them.  Work is enqueued on `stream`
+ * (NULL: legacy default stream); every call copies host values to the device and
+ * synchronises that stream before returning iters and rel_residual (host outs, nullable),
+ * so it cannot be called on a stream that is being captured into a CUDA graph.
+ * Errors: INVALID (arguments; also, in a self-checking build, arrays that fail its bounds
+ * checks), CUDA (a runtime call failed, or the solver's bounded grid-barrier wait ran out),
+ * NONFINITE.
  */
 ttie_status ttie_pcg_static(const int32_t *d_row_ptr, const int32_t *d_col_idx, const float *d_val,
                             int64_t n_rows, double mu, const float *d_rhs, float *d_out, double rtol,
                             int max_it, void *stream, int *iters, double *rel_residual);
+
+/* Counters of the last ttie_eval_pairs with gradients or Hessian factors, copied to out[0..n)
+ * (at most 5): the three counts of ttie_get_filter_stats; for FP32 positions, the intersecting
+ * pairs whose t_c gradients were evaluated again in FP64 because the FP32 evaluation was
+ * ill-conditioned for them (planes or cut edges at small angles, or Eq. 3's two terms
+ * cancelling); the intersecting pairs.  Errors: INVALID (null out, negative n), CUDA. */
+ttie_status ttie_get_eval_stats(ttie_ctx *ctx, int64_t *out, int n);
 
 /* Number of CUDA kernels the context has launched since ttie_create (host out). */
 ttie_status ttie_get_launch_count(ttie_ctx *ctx, int64_t *n);

@@ -36,7 +36,7 @@ from .ttie_oracle import (build_oracle, candidate_pairs, partners_of, evaluate, 
                           eval_pairs_f64, filtered_sides, gradient, hessian_parts,
                           hessian_inexact, hessian_psd, clamp_psd, assemble, pair_dofs,
                           blocks_to_dense, hessian_vector_product, pair_hessian_vector,
-                          newton_direction, newton_solve, line_search, capped_direction,
+                          newton_direction, newton_solve, line_search, next_overshoot, capped_direction,
                           certify, energy,
                           NewtonParams, PairEval)
 from . import exact  # noqa: F401

@@ -25,7 +25,7 @@ from dataclasses import dataclass
 import numpy as np
 
 from .ttie_oracle import (NewtonParams, assemble, blocks_to_dense, candidate_pairs,
-                          capped_direction, clamp_psd, evaluate, line_search, pair_dofs)
+                          capped_direction, clamp_psd, evaluate, line_search, next_overshoot, pair_dofs)
 
 
 @dataclass
@@ -155,11 +155,13 @@ def newton_direction_elastic(x, tri, group, prm: NewtonParams, el: Elastic):
 
 def quasi_static_solve(x0, tri, group, prm: NewtonParams, el: Elastic, log=None):
     """The quasi-static simulation: inexact Newton on E_el + sum T with the plain solve's
-    step cap and line search (first trial 1 + push_eta, then 1, 1/2, ...; Armijo or no
-    intersecting pair), from x0 until no pair intersects."""
+    step cap, line search and overshoot (first trial 1 + eta, then 1, 1/2, ...; Armijo, no
+    intersecting pair, or with rule "fewer" fewer pairs without raising E), from x0 until no
+    pair intersects."""
     x = np.array(x0, dtype=np.float64)
     e = np.concatenate([x[tri[:, 1]] - x[tri[:, 0]], x[tri[:, 2]] - x[tri[:, 1]], x[tri[:, 0]] - x[tri[:, 2]]])
     cap = prm.max_step * float(np.linalg.norm(e, axis=1).mean())
+    eta = prm.push_eta
     for it in range(prm.newton_max_it):
         E, n_act, grad, d, _ = newton_direction_elastic(x, tri, group, prm, el)
         if log is not None:
@@ -167,6 +169,7 @@ def quasi_static_solve(x0, tri, group, prm: NewtonParams, el: Elastic, log=None)
         if n_act == 0:
             return x, it, True
         d = capped_direction(d, cap)
-        _, x, _, _ = line_search(x, d, E, float(np.sum(grad * d)),
-                                 lambda xt: total_energy(xt, tri, group, prm, el), prm)
+        a, x, _, nt = line_search(x, d, E, float(np.sum(grad * d)),
+                                  lambda xt: total_energy(xt, tri, group, prm, el), prm, n0=n_act, eta=eta)
+        eta = next_overshoot(eta, a, n_act, nt, prm)
     return x, prm.newton_max_it, False

@@ -346,6 +346,8 @@ class NewtonParams:
     push_eta: float = 0.5         # first trial step 1 + eta (overshoot past touching)
     max_step: float = 1.0         # largest vertex move per iteration, in mean edge lengths (0: none)
     mode: str = "self"
+    ls_rule: str = "fewer"        # "armijo": Armijo or no pair; "fewer": also fewer pairs, E not above
+    push_eta_max: float = 7.0     # "fewer": the overshoot doubles up to this while it leaves the count
 
 
 def energy(x, tri, group, prm: NewtonParams):
@@ -373,18 +375,37 @@ def newton_direction(x, tri, group, prm: NewtonParams):
     return E, n_act, grad, d, verts
 
 
-def line_search(x, d, E: float, slope: float, energy_at, prm: NewtonParams):
+def line_search(x, d, E: float, slope: float, energy_at, prm: NewtonParams, n0: int | None = None,
+                eta: float | None = None):
     """The backtracking line search of the Newton policy (reading of §1.2's unstated inexact
-    Newton): trial steps 1 + push_eta, then 1, 1/2, ..., 2^-ls_max_halvings; the first trial
-    with Armijo's condition E(x + a d) <= E + c a slope (slope = g.d < 0), or with no
-    intersecting pair, is taken, else the last.  energy_at(xt) -> (E, intersecting pairs).
-    Returns (a, x + a d, E there, intersecting pairs there)."""
-    for a in [1.0 + prm.push_eta] + [0.5 ** k for k in range(prm.ls_max_halvings + 1)]:
+    Newton): trial steps 1 + eta (eta = push_eta unless given), then 1, 1/2, ...,
+    2^-ls_max_halvings; the first trial with Armijo's condition E(x + a d) <= E + c a slope
+    (slope = g.d < 0), or with no intersecting pair, or (rule "fewer", with n0 the pairs at x)
+    with fewer intersecting pairs than n0 and E(x + a d) <= E, is taken, else the last.
+    energy_at(xt) -> (E, intersecting pairs).  Returns (a, x + a d, E there, pairs there)."""
+    eta = prm.push_eta if eta is None else eta
+    for a in [1.0 + eta] + [0.5 ** k for k in range(prm.ls_max_halvings + 1)]:
+        if a > 1.0 + eta:
+            continue
         xt = x + a * d
         Et, nt = energy_at(xt)
-        if nt == 0 or Et <= E + prm.armijo_c * a * slope:
+        fewer = prm.ls_rule == "fewer" and n0 is not None and nt < n0 and Et <= E
+        if nt == 0 or Et <= E + prm.armijo_c * a * slope or fewer:
             break
     return a, xt, Et, nt
+
+
+def next_overshoot(eta: float, a: float, n0: int, n_new: int, prm: NewtonParams) -> float:
+    """Rule "fewer": the overshoot of the next step.  A step that took the overshoot trial and
+    left at least as many intersecting pairs doubles it (up to push_eta_max); a step that lowered
+    the count returns it to push_eta."""
+    if prm.ls_rule != "fewer":
+        return prm.push_eta
+    if n_new < n0:
+        return prm.push_eta
+    if a == 1.0 + eta and a > 1.0:
+        return min(max(prm.push_eta_max, prm.push_eta), 2.0 * eta)
+    return eta
 
 
 def capped_direction(d, cap: float):
@@ -399,13 +420,15 @@ def newton_solve(x0, tri, group=None, prm: NewtonParams | None = None, log=None)
     than max_step mean edge lengths (of the initial mesh) per iteration.
 
     The minimum T = 0 of a pair is reached at touching, which a Newton iteration on (ab)^2
-    only approaches; so every iteration first tries the overshoot step 1 + push_eta, then
+    only approaches; so every iteration first tries the overshoot step 1 + eta, then
     1, 1/2, 1/4, ...  A trial is accepted when it satisfies Armijo's condition
-    E(x + a d) <= E(x) + c a g.d or leaves no intersecting pair."""
+    E(x + a d) <= E(x) + c a g.d or leaves no intersecting pair, or (rule "fewer") leaves
+    fewer intersecting pairs without raising E; eta follows next_overshoot."""
     prm = prm or NewtonParams()
     x = np.array(x0, dtype=np.float64)
     edges = np.concatenate([x[tri[:, 1]] - x[tri[:, 0]], x[tri[:, 2]] - x[tri[:, 1]], x[tri[:, 0]] - x[tri[:, 2]]])
     cap = prm.max_step * float(np.linalg.norm(edges, axis=1).mean())
+    eta = prm.push_eta
     for it in range(prm.newton_max_it):
         E, n_act, grad, d, verts = newton_direction(x, tri, group, prm)
         if log is not None:
@@ -413,7 +436,9 @@ def newton_solve(x0, tri, group=None, prm: NewtonParams | None = None, log=None)
         if n_act == 0:
             return x, it, True
         d = capped_direction(d, cap)
-        _, x, _, _ = line_search(x, d, E, float(np.sum(grad * d)), lambda xt: energy(xt, tri, group, prm), prm)
+        a, x, _, nt = line_search(x, d, E, float(np.sum(grad * d)), lambda xt: energy(xt, tri, group, prm), prm,
+                                  n0=n_act, eta=eta)
+        eta = next_overshoot(eta, a, n_act, nt, prm)
     return x, prm.newton_max_it, False
 
 

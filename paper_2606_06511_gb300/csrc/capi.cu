@@ -115,7 +115,9 @@ static ttie_status check_params(Ctx &c, const ttie_params *p) {
         (p->pcg_precond != TTIE_PCG_BLOCK_JACOBI && p->pcg_precond != TTIE_PCG_CHEBYSHEV) ||
         p->pcg_cheb_degree < 0 || p->pcg_cheb_degree > 8 ||
         (p->assembly_mode != TTIE_ASSEMBLY_SORTED_KEYS && p->assembly_mode != TTIE_ASSEMBLY_ROW_BUCKETS) ||
-        (p->traversal_mode != TTIE_TRAVERSAL_TWO_WALKS && p->traversal_mode != TTIE_TRAVERSAL_ONE_WALK))
+        (p->traversal_mode != TTIE_TRAVERSAL_TWO_WALKS && p->traversal_mode != TTIE_TRAVERSAL_ONE_WALK) ||
+        (p->ls_rule != TTIE_LS_ARMIJO && p->ls_rule != TTIE_LS_FEWER) ||
+        !(p->push_eta_max >= 0.0) || p->push_eta_max > 1e3)
         return set_err(c, TTIE_ERR_INVALID, "numeric parameter out of range");
     return TTIE_OK;
 }
@@ -144,6 +146,8 @@ void ttie_default_params(ttie_params *p) {
     p->pcg_cheb_degree = 0;
     p->assembly_mode = TTIE_ASSEMBLY_SORTED_KEYS;
     p->traversal_mode = TTIE_TRAVERSAL_TWO_WALKS;
+    p->ls_rule = TTIE_LS_FEWER;
+    p->push_eta_max = 7.0;
 }
 
 ttie_status ttie_create(ttie_ctx **out, const ttie_params *p, void *stream) {
@@ -272,6 +276,7 @@ static ttie_status build_impl(Ctx &c, const T *x, const int32_t *tri, const int3
         if (c.group_bits == 0) c.group_bits = 1;
     }
     c.have_mesh = true;
+    c.eta_cur = c.prm.push_eta;
     int64_t n = 0;
     CK(mean_edge_length<T>(c, (const vec4_t<T> *)c.xp.p, &c.ds->red[7]), "build");
     CK(cudaMemcpyAsync(&c.hs->red[7], &c.ds->red[7], sizeof(double), cudaMemcpyDeviceToHost, c.stream), "build");
@@ -461,7 +466,9 @@ static ttie_status newton_impl(Ctx &c, T *x, ttie_step_info *info) {
     inf.pcg_row_iters = passes * c.n_rows;
     mark(c, 4);
     // line search on candidates from the boxes swept between x and x + a_max d
-    double a_max = 1.0 + c.prm.push_eta;
+    if (!(c.eta_cur >= c.prm.push_eta)) c.eta_cur = c.prm.push_eta;
+    double a_max = 1.0 + (c.prm.ls_rule == TTIE_LS_FEWER ? c.eta_cur : c.prm.push_eta);
+    const double a_top = a_max;
     CK(ensure(c, c.xq, (size_t)c.V * sizeof(vec4_t<T>)), "newton");
     CK(ensure(c, c.xt, (size_t)c.V * sizeof(vec4_t<T>)), "newton");
     int64_t ns = 0;
@@ -499,15 +506,25 @@ static ttie_status newton_impl(Ctx &c, T *x, ttie_step_info *info) {
         s = energy_at<T>(c, (const vec4_t<T> *)c.xt.p, (const int2 *)c.sweep_cand.p, ns, &Et, &nt);
         if (s != TTIE_OK) return s;
         ++trials;
-        alpha = a;
+        const bool armijo = Et <= E + c.prm.armijo_c * a * gd;
+        const bool fewer = nt < c.n_active && Et <= E;
+        const bool ok = nt == 0 || armijo || (c.prm.ls_rule == TTIE_LS_FEWER && fewer);
+        alpha = a;   // the last (smallest) trial is taken when none is accepted
         E_new = Et;
         n_new = nt;
-        if (nt == 0 || Et <= E + c.prm.armijo_c * a * gd) {
+        if (ok) {
             accepted = true;
             break;
         }
     }
-    (void)accepted;   // the last (smallest) trial is taken when none is accepted
+    // adaptive overshoot: the overshoot trial taken without lowering the count (the pairs
+    // approach touching without crossing, e.g. held back by the regulariser or an elastic
+    // term) doubles eta for the next step; a lower count resets it
+    if (c.prm.ls_rule == TTIE_LS_FEWER) {
+        if (n_new < c.n_active) c.eta_cur = c.prm.push_eta;
+        else if (accepted && alpha == a_top && a_top > 1.0)
+            c.eta_cur = std::min(std::max(c.prm.push_eta_max, c.prm.push_eta), 2.0 * c.eta_cur);
+    }
     CK(update_positions<T>(c, x, c.x_stride, (const T *)c.dir.p, (T)alpha), "newton: update");
     c.have_eval = false;   // the last evaluation ran on the line-search candidates
     mark(c, 5);
@@ -869,6 +886,7 @@ ttie_status ttie_solve(ttie_ctx *h, void *d_x_inout, ttie_solve_info *info) {
     const auto t0 = std::chrono::steady_clock::now();
     ttie_status s = TTIE_OK;
     int it = 0;
+    c.eta_cur = c.prm.push_eta;
     for (;; ++it) {
         ttie_step_info st;
         s = ttie_newton_step(h, d_x_inout, &st);
@@ -955,6 +973,18 @@ ttie_status ttie_get_filter_stats(ttie_ctx *h, int64_t *out3) {
     CK(cudaMemcpyAsync(c.hs->filter_stats, c.ds->filter_stats, 3 * 8, cudaMemcpyDeviceToHost, c.stream), "stats");
     CK(cudaStreamSynchronize(c.stream), "stats");
     for (int i = 0; i < 3; ++i) out3[i] = (int64_t)c.hs->filter_stats[i];
+    return TTIE_OK;
+}
+
+ttie_status ttie_get_eval_stats(ttie_ctx *h, int64_t *out, int n) {
+    if (!h) return TTIE_ERR_INVALID;
+    Ctx &c = h->c;
+    if (!out || n < 0) return set_err(c, TTIE_ERR_INVALID, "ttie_get_eval_stats: null output or negative count");
+    CK(cudaMemcpyAsync(c.hs, c.ds, sizeof(DevScalars), cudaMemcpyDeviceToHost, c.stream), "stats");
+    CK(cudaStreamSynchronize(c.stream), "stats");
+    const int64_t v[5] = {(int64_t)c.hs->filter_stats[0], (int64_t)c.hs->filter_stats[1],
+                          (int64_t)c.hs->filter_stats[2], (int64_t)c.hs->n_illcond, (int64_t)c.n_active};
+    for (int i = 0; i < n && i < 5; ++i) out[i] = v[i];
     return TTIE_OK;
 }
 

@@ -102,6 +102,7 @@ struct DevScalars {
     double el_energy;                      // energy of the elastic term at the last evaluation
     unsigned long long pcg_products;       // Chebyshev-preconditioned PCG: products computed
     unsigned long long ovf_cursor;         // one-walk traversal: overflow chunks taken
+    unsigned long long n_illcond;          // FP32 evaluation: pairs whose gradients were redone in FP64
 };
 
 static_assert(offsetof(DevScalars, n_defer2) == offsetof(DevScalars, n_defer) + sizeof(unsigned long long),
@@ -155,6 +156,7 @@ struct Ctx {
     int64_t n_rows = 0, nnzb = 0;
     bool have_dir = false;
     double mean_edge = 0.0;   // mean edge length at the last ttie_build_bvh
+    double eta_cur = 0.0;     // overshoot of the next line search (adaptive with TTIE_LS_FEWER)
     // memory
     DevScalars *ds = nullptr;     // device
     DevScalars *hs = nullptr;     // pinned host mirror

@@ -85,6 +85,11 @@ extern "C" ttie_status ttie_pcg_static(const int32_t *d_row_ptr, const int32_t *
     init.n_rows = (unsigned long long)n_rows;
     init.trace = mu * 3.0 * (double)n_rows;
     cudaError_t e = cudaMemcpyAsync(ds, &init, sizeof init, cudaMemcpyHostToDevice, st);
+    // the block count row_ptr[n_rows] into the low half of ds->nnzb (zeroed just above): the
+    // kernels' bounds checks in self-checking builds test column positions against it
+    static_assert(sizeof(int32_t) <= sizeof(init.nnzb), "nnzb holds an int32 count");
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&ds->nnzb, d_row_ptr + n_rows, sizeof(int32_t), cudaMemcpyDeviceToDevice, st);
     if (e == cudaSuccess)
         e = pcg_run_raw(st, sms, d_row_ptr, d_col_idx, d_val, n_rows, 1.0, d_rhs, d_out,
                         (float *)(base + kOffDinv), (float *)(base + kOffR), (float *)(base + kOffZ),
@@ -97,7 +102,8 @@ extern "C" ttie_status ttie_pcg_static(const int32_t *d_row_ptr, const int32_t *
         cudaGetLastError();
         return TTIE_ERR_CUDA;
     }
-    if (fin.err & ERR_BARRIER) return TTIE_ERR_CUDA;
+    if (fin.err & ERR_CHECK) return TTIE_ERR_INVALID;   // the caller's arrays failed a bounds check
+    if (fin.err) return TTIE_ERR_CUDA;                  // the bounded grid-barrier wait ran out
     const double rel = fin.red[1] > 0.0 ? sqrt(fin.red[4] / fin.red[1]) : 0.0;
     if (iters) *iters = fin.pcg_iters;
     if (rel_residual) *rel_residual = rel;

@@ -12,7 +12,7 @@ import torch
 
 import oracle as O
 import ttie_inputs as ti
-from _cases import fp32_tolerance, pair_set
+from _cases import G_RTOL, H_RTOL, T_RTOL, pair_errors, pair_set, tolerance_mask
 
 pytestmark = pytest.mark.gpu
 
@@ -48,17 +48,16 @@ def _sample_checks(ttie, m, x, ctx, rng):
     ev = O.evaluate(xn, m.tri, pick)
     gpu_flag = np.array([tuple(p) in active for p in pick.tolist()])
     assert np.array_equal(gpu_flag, ev.active)
-    # T and gradient on the sampled active pairs
+    # T, gradient and projected Hessian of the sampled intersecting pairs: the stated tolerances
     idx = {tuple(p): k for k, p in enumerate(ap.tolist())}
     k = np.array([idx[tuple(p)] for p in pick[ev.active].tolist()])
-    tcs = tc.double().cpu().numpy()[k]
-    dts = dtc.double().cpu().numpy()[k]
-    T_gpu = (tcs[:, 0] * tcs[:, 1]) ** 2
-    T_or = ev.T[ev.active]
-    g_or = O.gradient(ev)[ev.active]
-    v = np.concatenate([xn[m.tri[pick[ev.active, 0]]], xn[m.tri[pick[ev.active, 1]]]], axis=1)
-    L = (v.max(1) - v.min(1)).max(1)
-    assert (np.abs(T_gpu - T_or) <= fp32_tolerance(T_or, g_or, L)).all()
+    a = ev.active
+    sub = O.PairEval(ev.pairs[a], ev.tc[a], ev.dtc[a], ev.sides64[a], ev.flags64[a], ev.active[a])
+    eT, eg, eH = pair_errors(tc.double().cpu().numpy()[k], dtc.double().cpu().numpy()[k], sub)
+    mask = tolerance_mask(xn, sub.tc)
+    assert mask.sum() > 500
+    assert eT[mask].max() <= T_RTOL and eg[mask].max() <= G_RTOL and eH[mask].max() <= H_RTOL, (
+        eT[mask].max(), eg[mask].max(), eH[mask].max())
     return E, n_act
 
 

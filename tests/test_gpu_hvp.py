@@ -201,8 +201,8 @@ def test_adam_descends_on_linked_tori(ttie):
 @pytest.mark.parametrize("prec", ["f64", "f32"])
 def test_dual_gradients_match_analytic_chain_rule(ttie, name, prec):
     """Forward-mode duals in FP64 on the GPU (the appendix's route) against the analytic
-    gradients of t_c from the evaluation (FP64: 1e-9 relative on pairs away from degeneracy;
-    FP32 analytic values: the FP32 tolerance of the gradients) and against the oracle."""
+    gradients of t_c from the evaluation (FP64: 1e-7 of each pair's largest entry; FP32
+    positions: the stated 1e-4 for gradients, every pair) and against the oracle."""
     precision = ttie.F64 if prec == "f64" else ttie.F32
     m, mode, x, ctx, g, n_act = _setup(ttie, name, precision)
     dual = ctx.dual_gradients(x).cpu().numpy()
@@ -217,6 +217,6 @@ def test_dual_gradients_match_analytic_chain_rule(ttie, name, prec):
     scale = np.abs(od).max(axis=2, keepdims=True)
     # the dual evaluation reads the stored positions, so it matches the oracle to FP64 rounding
     assert (np.abs(dual - od) <= 1e-7 * scale).all()
-    tol = 1e-7 if prec == "f64" else 2e-2
-    ok = np.abs(dtc - dual) <= tol * scale
-    assert ok.mean() > 0.99 if prec == "f32" else ok.all()
+    tol = 1e-7 if prec == "f64" else 1e-4
+    err = (np.abs(dtc - dual) / scale).max()
+    assert err <= tol, err

@@ -1,11 +1,10 @@
 """Parity of the CUDA path (through the C ABI) with the CPU oracle.
 
 Integer results are compared bit-exactly: the candidate pair set (closed box
-overlap, non-adjacent), the intersecting pair set and the block pattern.  FP32
-values are compared with a tolerance derived from the arithmetic (see
-``_cases.fp32_tolerance``); the FP64 form with relative 1e-5 (T) and 1e-4
-(gradients, Hessian blocks) on pairs with min(|t_c^0|, |t_c^1|) > 1e-6 of the
-bounding-box diagonal.
+overlap, non-adjacent), the intersecting pair set and the block pattern.  Values
+meet the stated tolerances in both forms (FP32 positions and FP64): T relative
+1e-5, gradients and Hessian blocks relative 1e-4, on pairs with
+min(|t_c^0|, |t_c^1|) > 1e-6 of the bounding-box diagonal (``_cases``).
 """
 import numpy as np
 import pytest
@@ -13,7 +12,8 @@ import torch
 
 import oracle as O
 import ttie_inputs as ti
-from _cases import MODE, fp32_tolerance, pair_set, small_cases
+from _cases import (G_RTOL, H_RTOL, MODE, T_RTOL, block_errors, pair_errors, pair_set, small_cases,
+                    tolerance_mask)
 
 pytestmark = pytest.mark.gpu
 
@@ -100,33 +100,35 @@ def _pair_size(m, pairs):
     return (v.max(1) - v.min(1)).max(1)
 
 
-@pytest.mark.parametrize("name", ["cloth40", "spheres_inter", "soup", "tori", "ellipsoids_intra"])
-def test_energy_and_gradient_fp32(ttie, name):
+@pytest.mark.parametrize("name", ["cloth40", "spheres_inter", "soup", "tori", "ellipsoids_intra", "snapped_grid"])
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_pair_values_meet_stated_tolerances(ttie, name, prec):
+    """T, the Eq. 3 gradient and the projected Eq. 4 Hessian of every intersecting pair in the
+    tolerance mask, per pair, against the oracle.  On the snapped grid many pairs sit exactly at
+    a tie of the construction (an interval end point shared, a cut vertex on the plane), where
+    t_c is not differentiable and either one-sided gradient is correct: there only T and the
+    energy are compared."""
     m, mode = CASES[name]
-    x, tri, grp = _dev(m)
-    ctx = _ctx(ttie, mode)
+    precision = ttie.F64 if prec == "f64" else ttie.F32
+    x, tri, grp = _dev(m, torch.float64 if prec == "f64" else torch.float32)
+    ctx = _ctx(ttie, mode, precision=precision)
     ctx.build_bvh(x, tri, grp)
     E, n_act = ctx.eval_pairs(x, ttie.EVAL_E | ttie.EVAL_H)
     pairs, ev = _oracle(name)
     ap, tc, dtc, k = _match(ctx, pairs, ev)
-    T_or = ev.T[k]
-    g_or = O.gradient(ev)[k]
-    T_gpu = (tc[:, 0] * tc[:, 1]) ** 2
-    L = _pair_size(m, ap)
-    tol = fp32_tolerance(T_or, g_or, L)
-    bad = np.abs(T_gpu - T_or) > tol
-    assert not bad.any(), (np.abs(T_gpu - T_or)[bad][:5], T_or[bad][:5])
-    assert abs(E - ev.T.sum()) <= 1e-5 * ev.T.sum() + tol.sum()
-    # gradient of T per pair (Eq. 3) from the GPU's t_c and their gradients
-    a, b = tc[:, 0], tc[:, 1]
-    g_gpu = (2 * a * b * b)[:, None] * dtc[:, 0] + (2 * b * a * a)[:, None] * dtc[:, 1]
-    H_or = O.hessian_inexact(O.PairEval(ev.pairs[k], ev.tc[k], ev.dtc[k], ev.sides64[k], ev.flags64[k],
-                                        ev.active[k]))
-    gtol = 1e-4 * np.abs(g_or).max(1, keepdims=True) + 64 * 2.0 ** -24 * L[:, None] * np.abs(H_or).sum(2)
-    well = np.minimum(np.abs(ev.tc[k, 0]), np.abs(ev.tc[k, 1])) > 1e-2 * L
-    assert well.sum() > 0.5 * len(k)
-    bad = (np.abs(g_gpu - g_or) > gtol)[well]
-    assert not bad.any(), np.abs(g_gpu - g_or)[well][bad][:5]
+    sub = O.PairEval(ev.pairs[k], ev.tc[k], ev.dtc[k], ev.sides64[k], ev.flags64[k], ev.active[k])
+    mask = tolerance_mask(m.x, sub.tc)
+    assert mask.mean() > 0.9
+    eT, eg, eH = pair_errors(tc, dtc, sub)
+    assert eT[mask].max() <= T_RTOL, eT[mask].max()
+    assert abs(E - ev.T.sum()) <= T_RTOL * ev.T.sum()
+    if name == "snapped_grid":
+        return
+    assert eg[mask].max() <= G_RTOL, (eg[mask].max(), ap[mask][np.argmax(eg[mask])])
+    assert eH[mask].max() <= H_RTOL, (eH[mask].max(), ap[mask][np.argmax(eH[mask])])
+    if prec == "f32":
+        st = ctx.get_eval_stats()
+        assert st["active"] == n_act and 0 <= st["grad_fp64_pairs"] <= n_act
 
 
 @pytest.mark.parametrize("name", ["spheres_inter", "cloth40"])
@@ -141,15 +143,10 @@ def test_fp64_form_meets_relative_tolerances(ttie, name):
     pairs, ev = _oracle(name)
     assert n_act == int(ev.active.sum())
     ap, tc, dtc, k = _match(ctx, pairs, ev)
-    diag = np.linalg.norm(m.x.max(0) - m.x.min(0))
-    mask = np.minimum(np.abs(ev.tc[k, 0]), np.abs(ev.tc[k, 1])) > 1e-6 * diag
-    T_gpu = (tc[:, 0] * tc[:, 1]) ** 2
-    assert np.allclose(T_gpu[mask], ev.T[k][mask], rtol=1e-5, atol=0)
-    a, b = tc[:, 0], tc[:, 1]
-    g_gpu = (2 * a * b * b)[:, None] * dtc[:, 0] + (2 * b * a * a)[:, None] * dtc[:, 1]
-    g_or = O.gradient(ev)[k]
-    err = np.abs(g_gpu - g_or).max(1) / np.abs(g_or).max(1)
-    assert (err[mask] <= 1e-4).all(), err[mask].max()
+    sub = O.PairEval(ev.pairs[k], ev.tc[k], ev.dtc[k], ev.sides64[k], ev.flags64[k], ev.active[k])
+    mask = tolerance_mask(m.x, sub.tc)
+    eT, eg, eH = pair_errors(tc, dtc, sub)
+    assert eT[mask].max() <= T_RTOL and eg[mask].max() <= G_RTOL and eH[mask].max() <= H_RTOL
     assert E == pytest.approx(ev.T.sum(), rel=1e-9)
 
 
@@ -177,13 +174,19 @@ def test_assembly_pattern_and_values(ttie, name, precision):
     assert np.all(np.diff(rows) > 0)
     for r in range(len(rows)):                          # columns ascending within a row
         assert np.all(np.diff(ci[rp[r]:rp[r + 1]]) > 0)
-    scale = max(np.abs(b).max() for b in blocks.values())
-    tol = 1e-4 if precision else 2e-3
-    for key, b in blocks.items():
-        assert np.allclose(got[key], b, rtol=tol, atol=tol * scale), key
+    # blocks relative to sqrt(|H_rr| |H_cc|); gradient rows relative to the sum of the sizes
+    # of the pair gradients they add up (the stated 1e-4 in both forms)
+    eb = block_errors(got, blocks)
+    assert eb.max() <= H_RTOL, eb.max()
+    vid = O.pair_dofs(m.tri, ev.pairs[ev.active])
+    gp = np.abs(O.gradient(ev)[ev.active])
+    contrib = np.zeros((m.V, 3))
+    for r in range(6):
+        np.add.at(contrib, vid[:, r], gp[:, 3 * r:3 * r + 3])
+    scale = contrib.max(1, keepdims=True)
     g = grad_full.double().cpu().numpy()
-    assert np.allclose(g, grad_or, rtol=tol, atol=tol * np.abs(grad_or).max())
-    assert np.allclose(bsr.grad.double().cpu().numpy(), grad_or[rows], rtol=tol, atol=tol * np.abs(grad_or).max())
+    assert (np.abs(g - grad_or) <= G_RTOL * scale).all()
+    assert (np.abs(bsr.grad.double().cpu().numpy() - grad_or[rows]) <= G_RTOL * scale[rows]).all()
     # deterministic
     ctx.eval_pairs(x, ttie.EVAL_E | ttie.EVAL_H)
     bsr2 = ctx.assemble()
@@ -192,6 +195,10 @@ def test_assembly_pattern_and_values(ttie, name, precision):
 
 @pytest.mark.parametrize("precision", [0, 1])
 def test_pcg_matches_direct_solve(ttie, precision):
+    """The PCG's solution against a dense direct solve of the same system (the matrix the GPU
+    assembled, read back in FP64): the true residual is at the requested level and the
+    solution error is below a fixed bound (FP32 2e-3, FP64 1e-6).  The residual on the
+    oracle's own matrix adds the assembly's rounding."""
     name = "cloth40"
     m, mode = CASES[name]
     dt = torch.float64 if precision else torch.float32
@@ -201,23 +208,33 @@ def test_pcg_matches_direct_solve(ttie, precision):
     ctx.eval_pairs(x, ttie.EVAL_E | ttie.EVAL_H)
     bsr = ctx.assemble()
     rhs = -bsr.grad
-    rtol = 1e-7 if precision else 1e-4
+    rtol = 1e-9 if precision else 1e-5
     d, iters, rel = ctx.pcg(rhs.contiguous(), rtol=rtol, max_it=5000)
     assert rel <= rtol
-    pairs, ev = _oracle(name)
-    _, blocks = O.assemble(m.tri, ev, m.V)
     rows = bsr.vertex_of_row.cpu().numpy()
-    H = O.blocks_to_dense(blocks, rows)
-    A = H + 1e-3 * np.mean(np.diag(H)) * np.eye(len(H))
+    rp = bsr.row_ptr.cpu().numpy()
+    ci = bsr.col_idx.cpu().numpy()
+    val = bsr.val.double().cpu().numpy().reshape(-1, 3, 3)
+    n = len(rows)
+    Hg = np.zeros((3 * n, 3 * n))
+    for r in range(n):
+        for b in range(rp[r], rp[r + 1]):
+            Hg[3 * r:3 * r + 3, 3 * ci[b]:3 * ci[b] + 3] = val[b]
+    mu = 1e-3 * np.mean(np.diag(Hg))
+    A = Hg + mu * np.eye(3 * n)
     b = -bsr.grad.double().cpu().numpy().ravel()
     sol = np.linalg.solve(A, b)
     dd = d.double().cpu().numpy().ravel()
-    # the true residual of the GPU solution (oracle matrix, FP64) is at the requested level,
-    # up to the rounding of the FP32 product; the error is bounded by cond(A) times it
     res = np.linalg.norm(A @ dd - b) / np.linalg.norm(b)
-    assert res <= (10 * rtol if precision else 1e-2), (res, iters, rel)
+    assert res <= (2 * rtol if precision else 5 * rtol), (res, iters, rel)
     err = np.linalg.norm(dd - sol) / np.linalg.norm(sol)
-    assert err <= 2 * np.linalg.cond(A) * res, (err, res, iters)
+    assert err <= (1e-6 if precision else 2e-3), (err, res, iters)
+    pairs, ev = _oracle(name)
+    _, blocks = O.assemble(m.tri, ev, m.V)
+    Ho = O.blocks_to_dense(blocks, rows)
+    Ao = Ho + 1e-3 * np.mean(np.diag(Ho)) * np.eye(len(Ho))
+    res_o = np.linalg.norm(Ao @ dd - b) / np.linalg.norm(b)
+    assert res_o <= (1e-8 if precision else 1e-3), res_o
 
 
 def test_newton_step_descends(ttie):

@@ -512,6 +512,33 @@ def test_line_search_rule():
     # nothing acceptable: the last trial, 2^-4, is taken
     a, _, _, _ = O.line_search(x, x, E, float(np.sum(g * x)), quad, prm)
     assert a == 0.5 ** 4
+    # rule "fewer": a trial with fewer intersecting pairs and no higher energy is accepted even
+    # without Armijo's decrease (E(x + a d) = E at every trial here); with as many pairs it is not
+    flat = lambda cnt: (lambda xt: (E, cnt))
+    prm_f = O.NewtonParams(armijo_c=1e-4, push_eta=0.5, ls_max_halvings=4, ls_rule="fewer")
+    a, _, _, nt = O.line_search(x, -x, E, -2.0, flat(1), prm_f, n0=2)
+    assert a == 1.5 and nt == 1
+    a, _, _, _ = O.line_search(x, -x, E, -2.0, flat(2), prm_f, n0=2)
+    assert a == 0.5 ** 4
+    # ... and not under the Armijo-only rule
+    prm_a = O.NewtonParams(armijo_c=1e-4, push_eta=0.5, ls_max_halvings=4, ls_rule="armijo")
+    a, _, _, _ = O.line_search(x, -x, E, -2.0, flat(1), prm_a, n0=2)
+    assert a == 0.5 ** 4
+    # a larger overshoot is the first trial
+    a, _, _, _ = O.line_search(x, -x, E, -2.0, flat(1), prm_f, n0=2, eta=3.0)
+    assert a == 4.0
+
+
+def test_adaptive_overshoot():
+    """Rule "fewer": the overshoot doubles after a step that took it and left as many pairs, up
+    to push_eta_max, and returns to push_eta when the count falls; other steps keep it."""
+    prm = O.NewtonParams(push_eta=0.5, push_eta_max=7.0)
+    assert O.next_overshoot(0.5, 1.5, 12, 12, prm) == 1.0
+    assert O.next_overshoot(4.0, 5.0, 12, 13, prm) == 7.0
+    assert O.next_overshoot(7.0, 8.0, 12, 12, prm) == 7.0
+    assert O.next_overshoot(4.0, 5.0, 12, 11, prm) == 0.5
+    assert O.next_overshoot(4.0, 1.0, 12, 12, prm) == 4.0
+    assert O.next_overshoot(4.0, 5.0, 12, 12, O.NewtonParams(push_eta=0.5, ls_rule="armijo")) == 0.5
 
 
 def test_step_cap_bounds_each_iteration():

@@ -27,8 +27,11 @@ CASES = [
      "test_psd_projection_properties"),                           # the per-part projection of §1.1
     ("oracle/exact.py", "return max(tA) > min(tB) and min(tA) < max(tB)",
      "return max(tA) >= min(tB) and min(tA) <= max(tB)", "test_closed_form_pairs"),   # touching
-    ("oracle/ttie_oracle.py", "if nt == 0 or Et <= E + prm.armijo_c * a * slope:",
-     "if nt == 0 or Et <= E - prm.armijo_c * a * slope:", "test_line_search_rule"),    # Armijo
+    ("oracle/ttie_oracle.py", "if nt == 0 or Et <= E + prm.armijo_c * a * slope or fewer:",
+     "if nt == 0 or Et <= E - prm.armijo_c * a * slope or fewer:", "test_line_search_rule"),    # Armijo
+    ("oracle/ttie_oracle.py", "fewer = prm.ls_rule == \"fewer\" and n0 is not None and nt < n0 and Et <= E",
+     "fewer = prm.ls_rule == \"fewer\" and n0 is not None and nt <= n0 and Et <= E",
+     "test_line_search_rule"),                                    # the fewer-pairs acceptance
     ("oracle/elastic.py", "K = k * (P + (1.0 - L / l) * (np.eye(3) - P))",
      "K = k * (P + (1.0 - l / L) * (np.eye(3) - P))", "test_spring_hessian_central_differences"),
 ]
