@@ -270,12 +270,10 @@ def main():
     ap.add_argument("--no-quasi-static", action="store_true", help="skip the quasi-static simulation run")
     ap.add_argument("--no-next-rows", action="store_true",
                     help="skip the timings of the PSD variants, the exact Hessian-vector product and the dual evaluator")
-    ap.add_argument("--pcg-precond", choices=["block_jacobi", "chebyshev"], default="block_jacobi",
+    ap.add_argument("--pcg-precond", choices=["auto", "block_jacobi", "chebyshev"], default="auto",
                     help="preconditioner of the shared-memory PCG")
     ap.add_argument("--pcg-cheb-degree", type=int, default=0, help="Chebyshev degree (0: the library's default)")
-    ap.add_argument("--assembly", choices=["sorted_keys", "row_buckets"], default="sorted_keys",
-                    help="assembly of the block-CSR system")
-    ap.add_argument("--traversal", choices=["two_walks", "one_walk"], default="two_walks",
+    ap.add_argument("--traversal", choices=["one_walk", "two_walks"], default="one_walk",
                     help="LBVH traversal")
     args = ap.parse_args()
 
@@ -298,10 +296,9 @@ def main():
     __graft_entry__.build()
     from paper_2606_06511_gb300 import ttie
 
-    solver = {"pcg_precond": {"block_jacobi": ttie.PCG_BLOCK_JACOBI, "chebyshev": ttie.PCG_CHEBYSHEV}[args.pcg_precond],
+    solver = {"pcg_precond": {"auto": ttie.PCG_AUTO, "block_jacobi": ttie.PCG_BLOCK_JACOBI,
+                              "chebyshev": ttie.PCG_CHEBYSHEV}[args.pcg_precond],
               "pcg_cheb_degree": args.pcg_cheb_degree,
-              "assembly_mode": {"sorted_keys": ttie.ASSEMBLY_SORTED_KEYS,
-                                "row_buckets": ttie.ASSEMBLY_ROW_BUCKETS}[args.assembly],
               "traversal_mode": {"two_walks": ttie.TRAVERSAL_TWO_WALKS,
                                  "one_walk": ttie.TRAVERSAL_ONE_WALK}[args.traversal]}
     stream = torch.cuda.current_stream()
@@ -497,6 +494,37 @@ def main():
                 entry["error"] = "%s: %s" % (type(e).__name__, str(e)[:200])
             configs[name] = entry
 
+    # the tori configuration's use of the energy as a loss: Adam on sum T + lambda/2 |x - x0|^2
+    # through the autograd Function (forward: the library's energy; backward: its gradient)
+    if rank == 0 and "tori" in configs and "error" not in configs["tori"]:
+        from paper_2606_06511_gb300.autograd import TTIEnergy
+        mt, _, _, _, _ = workload("tori")
+        xt0 = torch.tensor(mt.x, dtype=torch.float32, device="cuda")
+        f = TTIEnergy(torch.tensor(mt.tri, dtype=torch.int32, device="cuda"), None, precision=ttie.F32, **solver)
+        xa = xt0.clone().requires_grad_(True)
+        opt = torch.optim.Adam([xa], lr=1e-3)
+        lam, n_adam = 1.0, 200
+        hist = []
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(n_adam):
+            opt.zero_grad()
+            E = f(xa)
+            loss = E + 0.5 * lam * ((xa - xt0) ** 2).sum()
+            loss.backward()
+            opt.step()
+            hist.append((E.item(), f.last))
+        torch.cuda.synchronize()
+        sec = time.perf_counter() - t0
+        E_end = f(xa.detach()).item()
+        configs["tori"]["adam"] = {
+            "loss": "sum T + lambda/2 |x - x0|^2, lambda 1, Adam lr 1e-3, through the autograd Function",
+            "steps": n_adam, "seconds": sec, "ms_per_step": 1e3 * sec / n_adam,
+            "energy_initial": hist[0][0], "n_active_initial": hist[0][1],
+            "energy_final": E_end, "n_active_final": f.last,
+            "energy_min": min(h[0] for h in hist)}
+        f.ctx.close()
+
     # seconds to intersection-free where the method reaches it on small scenes: a shallow
     # overlap of two spheres and a mildly folded cloth (substitute workloads, not configs)
     reach = None
@@ -603,7 +631,7 @@ def main():
                        "line_search_trials": last["ls_trials"], "pcg_iters": last["pcg_iters"],
                        "bsr_rows": last["n_rows"], "bsr_blocks": last["nnzb"],
                        "l2": "flushed (256 MiB write) before every timed step",
-                       "pcg_precond": args.pcg_precond, "assembly": args.assembly, "traversal": args.traversal,
+                       "pcg_precond": args.pcg_precond, "traversal": args.traversal,
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "stage_ms_per_step": main_t["stage_ms_per_step"],
             "active_pairs_per_s": main_t["active"] / (total_ms / 1e3),

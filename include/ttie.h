@@ -106,8 +106,6 @@ typedef struct {
                              global-memory PCG and the batched-instance PCG always use
                              3x3 block Jacobi                                          */
     int pcg_cheb_degree;  /* TTIE_PCG_CHEBYSHEV: degree k of the polynomial, 1..8 (0 = 2) */
-    int assembly_mode;    /* TTIE_ASSEMBLY_*: how the 3x3 block-CSR system is assembled;
-                             both give the same pattern and bit-identical values          */
     int traversal_mode;   /* TTIE_TRAVERSAL_*: how the LBVH walk lists candidates; both give
                              the same list in the same order                              */
     int ls_rule;          /* TTIE_LS_*: which line-search trials are accepted            */
@@ -135,13 +133,6 @@ enum { TTIE_LS_ARMIJO = 0, TTIE_LS_FEWER = 1 };
  *            second walk writes those leaves instead.                                       */
 enum { TTIE_TRAVERSAL_TWO_WALKS = 0, TTIE_TRAVERSAL_ONE_WALK = 1 };
 
-/* Assembly of the block-CSR system (same result either way: each block is the sum of its
- * entries in the order pair index, then spring, then anchor).
- * SORTED_KEYS: every entry's (row, column) key radix-sorted, runs summed.
- * ROW_BUCKETS: the items of each row (a pair's vertex, a spring end, an anchor) bucketed by
- *              row; one warp per row orders them, finds the distinct columns and sums each
- *              column's entries in item order (no global sort; one host read).          */
-enum { TTIE_ASSEMBLY_SORTED_KEYS = 0, TTIE_ASSEMBLY_ROW_BUCKETS = 1 };
 
 /* PCG preconditioners.
  * BLOCK_JACOBI: M^-1 = D^-1, the inverses of the 3x3 diagonal blocks of H+ + mu I.
@@ -153,16 +144,20 @@ enum { TTIE_ASSEMBLY_SORTED_KEYS = 0, TTIE_ASSEMBLY_ROW_BUCKETS = 1 };
  *               keeps M^-1 positive definite whatever the estimate; with an odd k a
  *               lambda_max above the estimate can make it indefinite, which ends the solve
  *               at the breakdown test with the iterate so far.                           */
-enum { TTIE_PCG_BLOCK_JACOBI = 0, TTIE_PCG_CHEBYSHEV = 1 };
+enum { TTIE_PCG_BLOCK_JACOBI = 0, TTIE_PCG_CHEBYSHEV = 1, TTIE_PCG_AUTO = 2 };
+/* AUTO: CHEBYSHEV when the system's matrix rows fit the solver blocks' shared memory (an
+ * iteration is then bound by its grid reduction, which the polynomial's extra products do not
+ * repeat), BLOCK_JACOBI when they stream from global memory (an iteration is then bound by
+ * its product, and the polynomial's products cost more than the iterations they save). */
 
 typedef struct ttie_ctx ttie_ctx;
 
 /* Fills *p with the defaults: F32, SELF, PER_PART, tc_scale 1, mu_rel 1e-3,
  * pcg_rtol 1e-3, pcg_max_it 200, newton_max_it 200, ls_max_halvings 20,
  * armijo_c 1e-4, push_eta 0.5, exact_only 0, profile 0, max_step 1,
- * max_candidates 0, inst_threads 0, test_withhold 0, pcg_precond BLOCK_JACOBI,
- * pcg_cheb_degree 0, assembly_mode SORTED_KEYS, traversal_mode TWO_WALKS, ls_rule FEWER,
- * push_eta_max 7. */
+ * max_candidates 0, inst_threads 0, test_withhold 0, pcg_precond AUTO,
+ * pcg_cheb_degree 0, traversal_mode ONE_WALK, ls_rule ARMIJO,
+ * push_eta_max 1.5. */
 void ttie_default_params(ttie_params *p);
 
 /* Creates a context on the current CUDA device.  stream: a cudaStream_t or NULL
@@ -423,13 +418,6 @@ ttie_status ttie_get_filter_stats(ttie_ctx *ctx, int64_t *out3);
 ttie_status ttie_pcg_static(const int32_t *d_row_ptr, const int32_t *d_col_idx, const float *d_val,
                             int64_t n_rows, double mu, const float *d_rhs, float *d_out, double rtol,
                             int max_it, void *stream, int *iters, double *rel_residual);
-
-/* Counters of the last ttie_eval_pairs with gradients or Hessian factors, copied to out[0..n)
- * (at most 5): the three counts of ttie_get_filter_stats; for FP32 positions, the intersecting
- * pairs whose t_c gradients were evaluated again in FP64 because the FP32 evaluation was
- * ill-conditioned for them (planes or cut edges at small angles, or Eq. 3's two terms
- * cancelling); the intersecting pairs.  Errors: INVALID (null out, negative n), CUDA. */
-ttie_status ttie_get_eval_stats(ttie_ctx *ctx, int64_t *out, int n);
 
 /* Number of CUDA kernels the context has launched since ttie_create (host out). */
 ttie_status ttie_get_launch_count(ttie_ctx *ctx, int64_t *n);

@@ -346,8 +346,8 @@ class NewtonParams:
     push_eta: float = 0.5         # first trial step 1 + eta (overshoot past touching)
     max_step: float = 1.0         # largest vertex move per iteration, in mean edge lengths (0: none)
     mode: str = "self"
-    ls_rule: str = "fewer"        # "armijo": Armijo or no pair; "fewer": also fewer pairs, E not above
-    push_eta_max: float = 7.0     # "fewer": the overshoot doubles up to this while it leaves the count
+    ls_rule: str = "armijo"       # "armijo": Armijo or no pair; "fewer": also fewer pairs, E not above
+    push_eta_max: float = 1.5     # "fewer": the overshoot doubles up to this while it leaves the count
 
 
 def energy(x, tri, group, prm: NewtonParams):

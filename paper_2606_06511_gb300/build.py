@@ -24,11 +24,15 @@ def nvcc() -> str:
     raise RuntimeError("nvcc not found")
 
 
-def flags(extra=()):
+LIB_CHECKED = os.path.join(HERE, "libttie_checked.so")
+
+
+def flags(extra=(), checks=None):
     # TTIE_BUILD_CHECKS=1 builds the self-checking variant (bounds checks, a sync after every launch)
-    checks = ["-DTTIE_CHECKS"] if os.environ.get("TTIE_BUILD_CHECKS") == "1" else []
+    if checks is None:
+        checks = os.environ.get("TTIE_BUILD_CHECKS") == "1"
     return ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include"),
-                   "-I", SRC] + checks + list(extra)
+                   "-I", SRC] + (["-DTTIE_CHECKS"] if checks else []) + list(extra)
 
 
 def _stamp():
@@ -36,17 +40,21 @@ def _stamp():
     return max(os.path.getmtime(f) for f in files)
 
 
-def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:
-    force = force or os.environ.get("TTIE_BUILD_CHECKS") == "1"
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _stamp() and not ptxas_info:
-        return LIB
-    os.makedirs(OUT_DIR, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False, checked: bool = False) -> str:
+    """Builds libttie.so (or, with checked, the self-checking libttie_checked.so beside it,
+    leaving libttie.so as it is) and returns its path."""
+    lib = LIB_CHECKED if checked else LIB
+    out_dir = os.path.join(OUT_DIR, "checked") if checked else OUT_DIR
+    force = force or (not checked and os.environ.get("TTIE_BUILD_CHECKS") == "1")
+    if not force and os.path.exists(lib) and os.path.getmtime(lib) >= _stamp() and not ptxas_info:
+        return lib
+    os.makedirs(out_dir, exist_ok=True)
     cc = nvcc()
     extra = ["-Xptxas", "-v"] if ptxas_info else []
 
     def compile_unit(u):
-        obj = os.path.join(OUT_DIR, u.replace(".cu", ".o"))
-        cmd = [cc, "-c", os.path.join(SRC, u), "-o", obj] + flags(extra)
+        obj = os.path.join(out_dir, u.replace(".cu", ".o"))
+        cmd = [cc, "-c", os.path.join(SRC, u), "-o", obj] + flags(extra, True if checked else None)
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("nvcc failed for %s:\n%s%s" % (u, r.stdout, r.stderr))
@@ -57,13 +65,13 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
     if verbose or ptxas_info:
         for _, err in res:
             sys.stderr.write(err)
-    tmp = LIB + ".%d.tmp" % os.getpid()
+    tmp = lib + ".%d.tmp" % os.getpid()
     cmd = [cc] + ARCH + ["-shared", "-o", tmp] + [o for o, _ in res] + ["-lcudart"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s%s" % (r.stdout, r.stderr))
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

@@ -388,214 +388,6 @@ __global__ void k_block_values(const unsigned long long *__restrict__ key, const
     }
 }
 
-// ---------------------------------------------------------------- assembly by row buckets
-// The same system without a global sort.  An item is what one row receives from one source:
-// pair k's vertex r (code 6k + r, six entries: columns of the pair's six vertices), spring s's
-// end (code 6 n_act + 2s + side, two entries: columns of i and j) or anchor a (code
-// 6 n_act + 2 n_springs + a, one entry).  Items are counted and bucketed per row (in arrival
-// order), then one warp per row orders its items by code, lists each item's entry columns,
-// and finds the distinct columns in ascending order; after a scan of their counts, one warp
-// per row sums, for each distinct column, the entries in item order.  Within a block (row, col)
-// a source has one entry, so item order is the entry order of the sorted-key assembly (pair
-// index, then springs, then anchors) and every value is the same sum in the same order.
-
-// the row and the number of entries of item code
-__device__ __forceinline__ void item_row(uint32_t code, unsigned long long n_pair_items, int64_t n_springs,
-                                         const int4 *__restrict__ tri4, const int2 *__restrict__ pairs,
-                                         const uint32_t *__restrict__ active, const unsigned long long *__restrict__ vrow,
-                                         const int2 *__restrict__ edges, const int32_t *__restrict__ anchors,
-                                         unsigned long long &row) {
-    if (code < n_pair_items) {
-        const uint32_t k = code / 6, r = code - k * 6;
-        const int2 pr = pairs[active[k]];
-        row = vrow[vid(tri4[pr.x], tri4[pr.y], (int)r)];
-    } else if ((unsigned long long)code - n_pair_items < 2ull * (unsigned long long)n_springs) {
-        const unsigned long long w = code - n_pair_items, sp = w / 2;
-        const int2 e = edges[sp];
-        row = vrow[(w - 2 * sp) ? e.y : e.x];
-    } else {
-        row = vrow[anchors[code - n_pair_items - 2ull * (unsigned long long)n_springs]];
-    }
-}
-
-// count (fill = false) or place (fill = true) every item in its row's bucket
-template <bool kFill>
-__global__ void k_row_items(const int4 *__restrict__ tri4, const int2 *__restrict__ pairs,
-                            const uint32_t *__restrict__ active, const unsigned long long *__restrict__ vrow,
-                            const int2 *__restrict__ edges, int64_t n_springs, const int32_t *__restrict__ anchors,
-                            int64_t n_anchors, DevScalars *ds, uint32_t *__restrict__ cnt,
-                            const unsigned long long *__restrict__ off, uint32_t *__restrict__ items) {
-    const unsigned long long n_pair_items = ds->n_active * 6, nr = ds->n_rows;
-    const unsigned long long n = n_pair_items + 2ull * (unsigned long long)n_springs + (unsigned long long)n_anchors;
-    for (unsigned long long code = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; code < n;
-         code += (unsigned long long)gridDim.x * blockDim.x) {
-        unsigned long long row;
-        item_row((uint32_t)code, n_pair_items, n_springs, tri4, pairs, active, vrow, edges, anchors, row);
-        // (these kernels guard every write in all builds; the checked build also records it)
-        if (TTIE_BAD(ds, row < nr, 61, row) || row >= nr) continue;
-        const uint32_t slot = atomicAdd(&cnt[row], 1u);
-        if (kFill) {
-            if (TTIE_BAD(ds, off[row] + slot < off[row + 1], 62, row) || off[row] + slot >= off[row + 1]) continue;
-            items[off[row] + slot] = (uint32_t)code;
-        }
-    }
-}
-
-// One group per row: items in code order (each item's rank among the row's codes, which are
-// distinct), each item's entry columns (6 slots, -1 where an item has fewer), the first entry
-// of each column (no earlier entry in item order has that column) and the distinct columns in
-// ascending order (a first entry's place is the number of first entries with a smaller
-// column).  All of a row's scratch lies in its items' range (x6 for entries).  The work per row
-// grows with the square of its entries, so a row with more than kBigItems items goes to a
-// block (kBig: kBigThreads threads) and the others to a warp.
-constexpr int kRowWarps = 4;
-constexpr int kBigThreads = 512;
-constexpr unsigned long long kBigItems = 48;
-template <bool kBig> __device__ __forceinline__ void group_sync() {
-    if (kBig) __syncthreads();
-    else __syncwarp();
-}
-
-template <bool kBig>
-__global__ void __launch_bounds__(kBig ? kBigThreads : 32 * kRowWarps)
-    k_row_columns(const uint32_t *__restrict__ items, const unsigned long long *__restrict__ off,
-                  const int4 *__restrict__ tri4, const int2 *__restrict__ pairs, const uint32_t *__restrict__ active,
-                  const unsigned long long *__restrict__ vrow, const int2 *__restrict__ edges, int64_t n_springs,
-                  const int32_t *__restrict__ anchors, DevScalars *ds, uint32_t *__restrict__ items2,
-                  int32_t *__restrict__ ecol, uint8_t *__restrict__ efirst, int32_t *__restrict__ dlist,
-                  uint32_t *__restrict__ dcnt) {
-    constexpr int G = kBig ? kBigThreads : 32;
-    __shared__ unsigned int s_nd;
-    const int tid = kBig ? (int)threadIdx.x : (int)(threadIdx.x & 31);
-    const unsigned long long nr = ds->n_rows, n_pair_items = ds->n_active * 6;
-    const unsigned long long row0 = kBig ? blockIdx.x : blockIdx.x * (unsigned long long)kRowWarps + (threadIdx.x >> 5);
-    const unsigned long long stride = kBig ? gridDim.x : (unsigned long long)gridDim.x * kRowWarps;
-    for (unsigned long long row = row0; row < nr; row += stride) {
-        const unsigned long long base = off[row], n = off[row + 1] - base;
-        if ((n > kBigItems) != kBig) continue;   // the same for the whole group
-        if (kBig && tid == 0) s_nd = 0;
-        for (unsigned long long i = tid; i < n; i += G) {
-            const uint32_t code = items[base + i];
-            unsigned long long rank = 0;
-            for (unsigned long long j = 0; j < n; ++j) rank += items[base + j] < code;
-            if (rank < n) items2[base + rank] = code;
-        }
-        group_sync<kBig>();
-        for (unsigned long long i = tid; i < n; i += G) {
-            const uint32_t code = items2[base + i];
-            int32_t cols[6] = {-1, -1, -1, -1, -1, -1};
-            if (code < n_pair_items) {
-                const uint32_t k = code / 6;
-                const int2 pr = pairs[active[k]];
-                const int4 a = tri4[pr.x], b = tri4[pr.y];
-#pragma unroll
-                for (int c = 0; c < 6; ++c) cols[c] = (int32_t)vrow[vid(a, b, c)];
-            } else if ((unsigned long long)code - n_pair_items < 2ull * (unsigned long long)n_springs) {
-                const int2 e = edges[(code - n_pair_items) / 2];
-                cols[0] = (int32_t)vrow[e.x];
-                cols[1] = (int32_t)vrow[e.y];
-            } else {
-                cols[0] = (int32_t)vrow[anchors[code - n_pair_items - 2ull * (unsigned long long)n_springs]];
-            }
-#pragma unroll
-            for (int c = 0; c < 6; ++c) ecol[(base + i) * 6 + c] = cols[c];
-        }
-        group_sync<kBig>();
-        const unsigned long long ne = 6 * n;
-        int32_t *ec = ecol + base * 6;
-        for (unsigned long long q = tid; q < ne; q += G) {
-            const int32_t col = ec[q];
-            bool first = col >= 0;
-            for (unsigned long long p = 0; p < q && first; ++p) first = ec[p] != col;
-            efirst[base * 6 + q] = first ? 1 : 0;
-        }
-        group_sync<kBig>();
-        uint32_t nd = 0;
-        for (unsigned long long q = tid; q < ne; q += G) {
-            if (!efirst[base * 6 + q]) continue;
-            const int32_t col = ec[q];
-            unsigned long long place = 0;
-            for (unsigned long long p = 0; p < ne; ++p) place += efirst[base * 6 + p] && ec[p] < col;
-            if (place < ne) dlist[base * 6 + place] = col;
-            ++nd;
-        }
-#pragma unroll
-        for (int o = 16; o; o >>= 1) nd += __shfl_xor_sync(0xffffffffu, nd, o);
-        if (kBig) {
-            if ((threadIdx.x & 31) == 0) atomicAdd(&s_nd, nd);
-            __syncthreads();
-            if (tid == 0) dcnt[row] = s_nd;
-        } else if (tid == 0) {
-            dcnt[row] = nd;
-        }
-        group_sync<kBig>();
-    }
-}
-
-// One group per row (as above), a thread per distinct column: the block (row, col) as the sum
-// of its entries in item order, its column index and, on the diagonal, the gradient rows;
-// row_ptr from the scanned distinct counts (dptr[V] = nnzb).
-template <typename T, bool kBig>
-__global__ void __launch_bounds__(kBig ? kBigThreads : 32 * kRowWarps)
-    k_row_values(const uint32_t *__restrict__ items2, const unsigned long long *__restrict__ off,
-                 const int32_t *__restrict__ ecol, const int32_t *__restrict__ dlist, const uint32_t *__restrict__ dcnt,
-                 const unsigned long long *__restrict__ dptr, int64_t V, unsigned long long cap, const T *__restrict__ z,
-                 const T *__restrict__ sfac, int64_t n_springs, const T *__restrict__ afac, T ka, DevScalars *ds,
-                 int32_t *__restrict__ row_ptr, int32_t *__restrict__ col_idx, T *__restrict__ bval,
-                 T *__restrict__ grad_rows, const int32_t *__restrict__ row_vertex, T *__restrict__ grad_full) {
-    constexpr int G = kBig ? kBigThreads : 32;
-    const int tid = kBig ? (int)threadIdx.x : (int)(threadIdx.x & 31);
-    const unsigned long long nr = ds->n_rows, n_pair_items = ds->n_active * 6;
-    const unsigned long long row0 = kBig ? blockIdx.x : blockIdx.x * (unsigned long long)kRowWarps + (threadIdx.x >> 5);
-    const unsigned long long stride = kBig ? gridDim.x : (unsigned long long)gridDim.x * kRowWarps;
-    if (!kBig && blockIdx.x == 0 && threadIdx.x == 0) {
-        ds->nnzb = dptr[V];
-        if (nr <= (unsigned long long)V) row_ptr[nr] = (int32_t)dptr[V];
-    }
-    for (unsigned long long row = row0; row < nr; row += stride) {
-        const unsigned long long base = off[row], n = off[row + 1] - base, rp = dptr[row];
-        if ((n > kBigItems) != kBig) continue;
-        const uint32_t nd = dcnt[row];
-        if (tid == 0) row_ptr[row] = (int32_t)rp;
-        for (uint32_t d = tid; d < nd && rp + d < cap; d += G) {
-            const int32_t col = dlist[base * 6 + d];
-            const bool diag = (unsigned long long)col == row;
-            T m[9];
-#pragma unroll
-            for (int i = 0; i < 9; ++i) m[i] = T(0);
-            T g0 = 0, g1 = 0, g2 = 0;
-            for (unsigned long long i = 0; i < n; ++i) {
-                const uint32_t code = items2[base + i];
-                const int32_t *ci = ecol + (base + i) * 6;
-                for (int c = 0; c < 6; ++c) {
-                    if (ci[c] != col) continue;
-                    if (code < n_pair_items) {
-                        const uint32_t k = code / 6;
-                        add_pair_entry<T>(z, k, code - k * 6, (uint32_t)c, diag, m, g0, g1, g2);
-                    } else if ((unsigned long long)code - n_pair_items < 2ull * (unsigned long long)n_springs) {
-                        const unsigned long long w = code - n_pair_items, sp = w / 2;
-                        const unsigned q = (w - 2 * sp) ? (c == 0 ? 2u : 3u) : (c == 0 ? 0u : 1u);
-                        add_spring_entry<T>(sfac, sp, q, diag, m, g0, g1, g2);
-                    } else {
-                        add_anchor_entry<T>(afac, code - n_pair_items - 2ull * (unsigned long long)n_springs, ka, diag,
-                                            m, g0, g1, g2);
-                    }
-                }
-            }
-            col_idx[rp + d] = col;
-#pragma unroll
-            for (int i = 0; i < 9; ++i) bval[(rp + d) * 9 + i] = m[i];
-            if (diag) {
-                grad_rows[row * 3] = g0; grad_rows[row * 3 + 1] = g1; grad_rows[row * 3 + 2] = g2;
-                if (grad_full) {
-                    const int64_t v = row_vertex[row];
-                    grad_full[v * 3] = g0; grad_full[v * 3 + 1] = g1; grad_full[v * 3 + 2] = g2;
-                }
-            }
-        }
-    }
-}
-
 template <typename T>
 __global__ void k_axpy_positions(const vec4_t<T> *__restrict__ x, const T *__restrict__ d, T alpha, int64_t V,
                                  vec4_t<T> *__restrict__ out) {
@@ -685,28 +477,6 @@ __global__ void k_vertex_sums(const unsigned long long *__restrict__ key, const 
     }
 }
 
-// The same sums from the row-bucket assembly: a row's pair items in code order are its
-// (pair, vertex) entries of the diagonal block in the same order.
-template <typename T>
-__global__ void k_vertex_sums_rows(const uint32_t *__restrict__ items2, const unsigned long long *__restrict__ off,
-                                   const T *__restrict__ h, const int32_t *__restrict__ row_vertex, const DevScalars *ds,
-                                   T *__restrict__ out) {
-    const unsigned long long nr = ds->n_rows, n_pair_items = ds->n_active * 6;
-    for (unsigned long long row = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; row < nr;
-         row += (unsigned long long)gridDim.x * blockDim.x) {
-        T g0 = 0, g1 = 0, g2 = 0;
-        for (unsigned long long i = off[row]; i < off[row + 1]; ++i) {
-            const uint32_t code = items2[i];
-            if (code >= n_pair_items) continue;
-            const uint32_t pk = code / 6, r = code - pk * 6;
-            const T *hp = h + (size_t)pk * 18 + 3 * r;
-            g0 += hp[0]; g1 += hp[1]; g2 += hp[2];
-        }
-        const int64_t vx = row_vertex[row];
-        out[vx * 3] = g0; out[vx * 3 + 1] = g1; out[vx * 3 + 2] = g2;
-    }
-}
-
 // out (V x 3) = H+ v on the assembled rows (vertices of intersecting pairs); other rows 0.
 template <typename T>
 __global__ void k_bsr_matvec(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col_idx,
@@ -736,78 +506,6 @@ int bits_for(unsigned long long v) {
 }
 
 }  // namespace
-
-// The row-bucket assembly (TTIE_ASSEMBLY_ROW_BUCKETS), after the factor kernels: buffers sized
-// by V and the entry count so that no size is read before the end, then one read of n_rows and
-// nnzb.
-template <typename T>
-static cudaError_t assemble_rows(Ctx &c, T *grad_full, int64_t n_springs, int64_t n_anchors) {
-    const int64_t n_act = c.n_active, V = c.V;
-    const int64_t n_items = n_act * 6 + 2 * n_springs + n_anchors;
-    const int64_t nk = n_act * 36 + 4 * n_springs + n_anchors;
-    if (n_items >= (int64_t)UINT32_MAX) return cudaErrorInvalidValue;   // item codes are 32-bit
-    const size_t vb = (size_t)(V > 0 ? V : 1), ib = (size_t)(n_items > 0 ? n_items : 1), kb = (size_t)(nk > 0 ? nk : 1);
-    TTIE_CUDA_TRY(ensure(c, c.it_cnt, vb * 4));
-    TTIE_CUDA_TRY(ensure(c, c.it_fill, vb * 4));
-    TTIE_CUDA_TRY(ensure(c, c.dcnt, vb * 4));
-    TTIE_CUDA_TRY(ensure(c, c.it_off, (vb + 1) * 8));
-    TTIE_CUDA_TRY(ensure(c, c.dptr, (vb + 1) * 8));
-    TTIE_CUDA_TRY(ensure(c, c.items, ib * 4));
-    TTIE_CUDA_TRY(ensure(c, c.items2, ib * 4));
-    TTIE_CUDA_TRY(ensure(c, c.ecol, ib * 6 * 4));
-    TTIE_CUDA_TRY(ensure(c, c.eflag, ib * 6));
-    TTIE_CUDA_TRY(ensure(c, c.dlist, ib * 6 * 4));
-    TTIE_CUDA_TRY(ensure(c, c.row_ptr, (vb + 1) * 4));
-    TTIE_CUDA_TRY(ensure(c, c.col_idx, kb * 4));
-    TTIE_CUDA_TRY(ensure(c, c.bsr_val, kb * 9 * sizeof(T)));
-    TTIE_CUDA_TRY(ensure(c, c.rhs, vb * 3 * sizeof(T)));
-    TTIE_CUDA_TRY(cudaMemsetAsync(c.it_cnt.p, 0, vb * 4, c.stream));
-    TTIE_CUDA_TRY(cudaMemsetAsync(c.it_fill.p, 0, vb * 4, c.stream));
-    TTIE_CUDA_TRY(cudaMemsetAsync(c.dcnt.p, 0, vb * 4, c.stream));
-    if (grad_full) TTIE_CUDA_TRY(cudaMemsetAsync(grad_full, 0, (size_t)V * 3 * sizeof(T), c.stream));
-    const int4 *tri4 = (const int4 *)c.tri4.p;
-    const int2 *pairs = (const int2 *)c.cand.p;
-    const uint32_t *active = (const uint32_t *)c.active.p;
-    const unsigned long long *vrow = (const unsigned long long *)c.vrow.p;
-    const int2 *edges = (const int2 *)c.el_edges.p;
-    const int32_t *anchors = (const int32_t *)c.el_anchor.p;
-    const unsigned gI = grid_for(n_items, kThreads);
-    launch(c, k_row_items<false>, dim3(gI), dim3(kThreads), tri4, pairs, active, vrow, edges, n_springs, anchors,
-           n_anchors, c.ds, (uint32_t *)c.it_cnt.p, (const unsigned long long *)nullptr, (uint32_t *)nullptr);
-    TTIE_CUDA_TRY(scan_u32_u64(c, (const uint32_t *)c.it_cnt.p, (unsigned long long *)c.it_off.p, V));
-    launch(c, k_row_items<true>, dim3(gI), dim3(kThreads), tri4, pairs, active, vrow, edges, n_springs, anchors,
-           n_anchors, c.ds, (uint32_t *)c.it_fill.p, (const unsigned long long *)c.it_off.p, (uint32_t *)c.items.p);
-    // rows of up to kBigItems items: a warp each; larger rows: a block each (the big-row
-    // launches skip the small rows, one load per row)
-    const unsigned gR = grid_for((V + kRowWarps - 1) / kRowWarps, 1, kNumSMs * 16);
-    const unsigned gB = grid_for(V, 1, kNumSMs * 2);
-    launch(c, k_row_columns<false>, dim3(gR), dim3(32 * kRowWarps), (const uint32_t *)c.items.p,
-           (const unsigned long long *)c.it_off.p, tri4, pairs, active, vrow, edges, n_springs, anchors, c.ds,
-           (uint32_t *)c.items2.p, (int32_t *)c.ecol.p, (uint8_t *)c.eflag.p, (int32_t *)c.dlist.p,
-           (uint32_t *)c.dcnt.p);
-    launch(c, k_row_columns<true>, dim3(gB), dim3(kBigThreads), (const uint32_t *)c.items.p,
-           (const unsigned long long *)c.it_off.p, tri4, pairs, active, vrow, edges, n_springs, anchors, c.ds,
-           (uint32_t *)c.items2.p, (int32_t *)c.ecol.p, (uint8_t *)c.eflag.p, (int32_t *)c.dlist.p,
-           (uint32_t *)c.dcnt.p);
-    TTIE_CUDA_TRY(scan_u32_u64(c, (const uint32_t *)c.dcnt.p, (unsigned long long *)c.dptr.p, V));
-    launch(c, k_row_values<T, false>, dim3(gR), dim3(32 * kRowWarps), (const uint32_t *)c.items2.p,
-           (const unsigned long long *)c.it_off.p, (const int32_t *)c.ecol.p, (const int32_t *)c.dlist.p,
-           (const uint32_t *)c.dcnt.p, (const unsigned long long *)c.dptr.p, V, (unsigned long long)kb, (const T *)c.zfac.p,
-           (const T *)c.el_sfac.p, n_springs, (const T *)c.el_afac.p, (T)c.el_ka, c.ds, (int32_t *)c.row_ptr.p,
-           (int32_t *)c.col_idx.p, (T *)c.bsr_val.p, (T *)c.rhs.p, (const int32_t *)c.row_vertex.p, grad_full);
-    launch(c, k_row_values<T, true>, dim3(gB), dim3(kBigThreads), (const uint32_t *)c.items2.p,
-           (const unsigned long long *)c.it_off.p, (const int32_t *)c.ecol.p, (const int32_t *)c.dlist.p,
-           (const uint32_t *)c.dcnt.p, (const unsigned long long *)c.dptr.p, V, (unsigned long long)kb, (const T *)c.zfac.p,
-           (const T *)c.el_sfac.p, n_springs, (const T *)c.el_afac.p, (T)c.el_ka, c.ds, (int32_t *)c.row_ptr.p,
-           (int32_t *)c.col_idx.p, (T *)c.bsr_val.p, (T *)c.rhs.p, (const int32_t *)c.row_vertex.p, grad_full);
-    TTIE_CUDA_TRY(cudaGetLastError());
-    TTIE_CUDA_TRY(cudaMemcpyAsync(&c.hs->n_rows, &c.ds->n_rows, 8, cudaMemcpyDeviceToHost, c.stream));
-    TTIE_CUDA_TRY(cudaMemcpyAsync(&c.hs->nnzb, &c.ds->nnzb, 8, cudaMemcpyDeviceToHost, c.stream));
-    TTIE_CUDA_TRY(cudaStreamSynchronize(c.stream));
-    c.n_rows = (int64_t)c.hs->n_rows;
-    c.nnzb = nk > 0 ? (int64_t)c.hs->nnzb : 0;
-    return cudaSuccess;
-}
 
 template <typename T>
 cudaError_t assemble_system(Ctx &c, T *grad_full, bool with_elastic) {
@@ -843,8 +541,6 @@ cudaError_t assemble_system(Ctx &c, T *grad_full, bool with_elastic) {
                (const int32_t *)c.el_anchor.p, (const T *)c.el_target.p, n_anchors, (T)c.el_ka, (T *)c.el_sfac.p,
                (T *)c.el_afac.p, (double *)c.partials.p, c.ds);
     }
-    c.asm_rows = c.prm.assembly_mode == TTIE_ASSEMBLY_ROW_BUCKETS;
-    if (c.asm_rows) return assemble_rows<T>(c, grad_full, n_springs, n_anchors);
     const int64_t nk = n_act * 36 + 4 * n_springs + n_anchors;
     if (nk >= (int64_t)UINT32_MAX) return cudaErrorInvalidValue;   // entry indices are 32-bit
     TTIE_CUDA_TRY(ensure(c, c.bkey, (size_t)(nk > 0 ? nk : 1) * 8));
@@ -984,11 +680,7 @@ template cudaError_t direction_stats<double>(Ctx &, const double *, const double
 template <typename T> cudaError_t vertex_sums(Ctx &c, const T *h, T *out) {
     TTIE_CUDA_TRY(cudaMemsetAsync(out, 0, (size_t)c.V * 3 * sizeof(T), c.stream));
     if (c.nnzb == 0) return cudaSuccess;
-    if (c.asm_rows)
-        launch(c, k_vertex_sums_rows<T>, dim3(grid_for(c.n_rows, kThreads)), dim3(kThreads), (const uint32_t *)c.items2.p,
-               (const unsigned long long *)c.it_off.p, h, (const int32_t *)c.row_vertex.p, c.ds, out);
-    else
-        launch(c, k_vertex_sums<T>, dim3(grid_for(c.nnzb, kThreads)), dim3(kThreads), (const unsigned long long *)c.bkey.p,
+    launch(c, k_vertex_sums<T>, dim3(grid_for(c.nnzb, kThreads)), dim3(kThreads), (const unsigned long long *)c.bkey.p,
                (const uint32_t *)c.bval.p, (const uint32_t *)c.run_start.p, h, (const int32_t *)c.row_vertex.p, c.ds, out);
     return cudaGetLastError();
 }

@@ -112,9 +112,9 @@ static ttie_status check_params(Ctx &c, const ttie_params *p) {
         (p->inst_threads != 0 && p->inst_threads != 128 && p->inst_threads != 256 && p->inst_threads != 512 &&
          p->inst_threads != 1024) ||
         (p->test_withhold != 0 && p->test_withhold != 1) ||
-        (p->pcg_precond != TTIE_PCG_BLOCK_JACOBI && p->pcg_precond != TTIE_PCG_CHEBYSHEV) ||
+        (p->pcg_precond != TTIE_PCG_BLOCK_JACOBI && p->pcg_precond != TTIE_PCG_CHEBYSHEV &&
+         p->pcg_precond != TTIE_PCG_AUTO) ||
         p->pcg_cheb_degree < 0 || p->pcg_cheb_degree > 8 ||
-        (p->assembly_mode != TTIE_ASSEMBLY_SORTED_KEYS && p->assembly_mode != TTIE_ASSEMBLY_ROW_BUCKETS) ||
         (p->traversal_mode != TTIE_TRAVERSAL_TWO_WALKS && p->traversal_mode != TTIE_TRAVERSAL_ONE_WALK) ||
         (p->ls_rule != TTIE_LS_ARMIJO && p->ls_rule != TTIE_LS_FEWER) ||
         !(p->push_eta_max >= 0.0) || p->push_eta_max > 1e3)
@@ -142,12 +142,11 @@ void ttie_default_params(ttie_params *p) {
     p->max_candidates = 0;
     p->inst_threads = 0;
     p->test_withhold = 0;
-    p->pcg_precond = TTIE_PCG_BLOCK_JACOBI;
+    p->pcg_precond = TTIE_PCG_AUTO;
     p->pcg_cheb_degree = 0;
-    p->assembly_mode = TTIE_ASSEMBLY_SORTED_KEYS;
-    p->traversal_mode = TTIE_TRAVERSAL_TWO_WALKS;
-    p->ls_rule = TTIE_LS_FEWER;
-    p->push_eta_max = 7.0;
+    p->traversal_mode = TTIE_TRAVERSAL_ONE_WALK;
+    p->ls_rule = TTIE_LS_ARMIJO;
+    p->push_eta_max = 1.5;
 }
 
 ttie_status ttie_create(ttie_ctx **out, const ttie_params *p, void *stream) {
@@ -193,10 +192,6 @@ void ttie_destroy(ttie_ctx *h) {
     if (c.hs) cudaFreeHost(c.hs);
     for (int i = 0; i < 12; ++i)
         if (c.ev[i]) cudaEventDestroy(c.ev[i]);
-    for (int i = 0; i < kInstBuckets; ++i)
-        if (c.aux[i]) cudaStreamDestroy(c.aux[i]);
-    for (int i = 0; i <= kInstBuckets; ++i)
-        if (c.aux_ev[i]) cudaEventDestroy(c.aux_ev[i]);
     if (c.sort_exec) cudaGraphExecDestroy(c.sort_exec);
     if (c.cap_stream) cudaStreamDestroy(c.cap_stream);
     delete h;
@@ -973,18 +968,6 @@ ttie_status ttie_get_filter_stats(ttie_ctx *h, int64_t *out3) {
     CK(cudaMemcpyAsync(c.hs->filter_stats, c.ds->filter_stats, 3 * 8, cudaMemcpyDeviceToHost, c.stream), "stats");
     CK(cudaStreamSynchronize(c.stream), "stats");
     for (int i = 0; i < 3; ++i) out3[i] = (int64_t)c.hs->filter_stats[i];
-    return TTIE_OK;
-}
-
-ttie_status ttie_get_eval_stats(ttie_ctx *h, int64_t *out, int n) {
-    if (!h) return TTIE_ERR_INVALID;
-    Ctx &c = h->c;
-    if (!out || n < 0) return set_err(c, TTIE_ERR_INVALID, "ttie_get_eval_stats: null output or negative count");
-    CK(cudaMemcpyAsync(c.hs, c.ds, sizeof(DevScalars), cudaMemcpyDeviceToHost, c.stream), "stats");
-    CK(cudaStreamSynchronize(c.stream), "stats");
-    const int64_t v[5] = {(int64_t)c.hs->filter_stats[0], (int64_t)c.hs->filter_stats[1],
-                          (int64_t)c.hs->filter_stats[2], (int64_t)c.hs->n_illcond, (int64_t)c.n_active};
-    for (int i = 0; i < n && i < 5; ++i) out[i] = v[i];
     return TTIE_OK;
 }
 

@@ -52,7 +52,6 @@ enum ErrBits : int {
     ERR_GROUP = 64,         // batched instances: a vertex in two groups, or a group's vertices not contiguous
 };
 
-constexpr int kInstBuckets = 4;   // size buckets of the batched PCG
 
 // Per-pair rows of the evaluation: [a, b, grad a (18), grad b (18), pad 2] (a = t_c^0, b = t_c^1)
 constexpr int kFacStride = 40;
@@ -102,7 +101,7 @@ struct DevScalars {
     double el_energy;                      // energy of the elastic term at the last evaluation
     unsigned long long pcg_products;       // Chebyshev-preconditioned PCG: products computed
     unsigned long long ovf_cursor;         // one-walk traversal: overflow chunks taken
-    unsigned long long n_illcond;          // FP32 evaluation: pairs whose gradients were redone in FP64
+    unsigned int inst_queue;               // batched PCG: next instance to take
 };
 
 static_assert(offsetof(DevScalars, n_defer2) == offsetof(DevScalars, n_defer) + sizeof(unsigned long long),
@@ -128,7 +127,6 @@ cudaError_t ensure(Ctx &c, Buf &b, size_t bytes);   // grow-only, contents not k
     X(el_edges) X(el_rest) X(el_anchor) X(el_target) X(el_sfac) X(el_afac) X(defer2)          \
     X(inst) X(ls_cand) X(inst_acc) X(inst_ids) X(ab) X(ls_flag)  \
     X(ls_off) X(ls_scalars) X(hgrid) X(hkey) X(hkey2) X(hval) X(hval2) X(hcnt) X(hoff)   \
-    X(it_cnt) X(it_off) X(it_fill) X(items) X(items2) X(ecol) X(eflag) X(dlist) X(dcnt) X(dptr)  \
     X(ovf_pool) X(ovf_next) X(ovf_head)
 
 struct Ctx {
@@ -150,7 +148,6 @@ struct Ctx {
     unsigned eval_what = 0;
     int64_t n_active = 0;
     bool have_bsr = false;
-    bool asm_rows = false;   // the current system came from the row-bucket assembly
     bool pcg_cheb = false;   // the last PCG ran the Chebyshev-preconditioned kernel
     unsigned long long ovf_chunks = 0;   // one-walk traversal: chunks the last walk needed, + 25 %
     int64_t n_rows = 0, nnzb = 0;
@@ -164,14 +161,12 @@ struct Ctx {
     TTIE_BUFS(TTIE_DECL_BUF)
 #undef TTIE_DECL_BUF
     cudaEvent_t ev[12] = {};
-    cudaStream_t aux[kInstBuckets] = {};      // batched PCG: one stream per size bucket (lazily made)
     cudaStream_t cap_stream = nullptr;         // stream that graphs are captured on (lazily made)
-    cudaEvent_t aux_ev[kInstBuckets + 1] = {}; //   fork / join events
     int num_sms = 0;
     unsigned long long n_launch = 0;   // kernels launched through this context
     bool time_kernels = false;         // profile: events around the classification / PCG kernels
     int64_t tree_leaves = -1;          // leaves of the hierarchy in the BVH buffers (-1: none)
-    int inst_tuned[4] = {0, 0, 0, 0};  // batched PCG: block size chosen per size bucket (0: not yet)
+    int inst_tuned[4] = {0, 0, 0, 0};  // batched PCG schedule: threads, blocks per SM, order (0: not tuned)
     // elastic term of the quasi-static simulation (ttie_set_elastic)
     bool have_elastic = false;
     int64_t el_n_edges = 0, el_n_anchors = 0, el_V = -1;

@@ -16,6 +16,10 @@
 // contiguous range of every pair list too.
 #include <algorithm>
 #include <climits>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
 #include <vector>
 
 #include "common.cuh"
@@ -154,7 +158,9 @@ template <typename T> struct InstPcgArgs {
     T *r, *u, *p, *s, *w, *dinv;  // row vectors of instances kept in global memory
     unsigned long long *acc;      // their row partials: 3 x rows
     const double *edge;           // mean edge length per instance
-    const int32_t *ids;           // the instances of this launch
+    const int32_t *ids;           // the instances of this launch, in the order they are taken
+    int n_ids;
+    unsigned int *queue;          // next position of ids to take (zeroed before the launch)
     Inst *inst;
     double mu_rel, rtol2, max_step;
     int max_it;
@@ -221,13 +227,11 @@ __device__ __forceinline__ Acc<T> rows_total(const unsigned long long *part, int
     return out[0];
 }
 
-// PCG (Chronopoulos-Gear form, as in the grid-wide solver) of one instance per block.  Each
-// row's product is summed by kInstLanes lanes in a fixed order and every reduction goes
-// through rows_total, so the result does not depend on THREADS (which the tuner picks).
+// The PCG of instance gid by the whole block (k_pcg_instances takes the instances).
 template <typename T, int THREADS>
-__global__ void __launch_bounds__(THREADS) k_pcg_instances(InstPcgArgs<T> a, int smem_bytes) {
+__device__ __forceinline__ void inst_pcg_one(const InstPcgArgs<T> &a, int gid, int smem_bytes) {
     extern __shared__ __align__(16) unsigned char smem[];
-    Inst *I = a.inst + a.ids[blockIdx.x];
+    Inst *I = a.inst + gid;
     InstView<T> v;
     v.nrow = I->count;
     if (v.nrow <= 0) return;
@@ -416,7 +420,7 @@ __global__ void __launch_bounds__(THREADS) k_pcg_instances(InstPcgArgs<T> a, int
     dm = T(0);
     for (int k = 0; k < THREADS / 32; ++k) dm = fmax(dm, s_max[k]);
     const double dmax = sqrt((double)dm);
-    const double cap = a.max_step * a.edge[a.ids[blockIdx.x]];
+    const double cap = a.max_step * a.edge[gid];
     const double scale = (cap > 0.0 && dmax > cap) ? cap / dmax : 1.0;
     for (int i = threadIdx.x; i < 3 * v.nrow; i += THREADS) {
         const T di = v.x[i] * (T)scale;
@@ -426,6 +430,25 @@ __global__ void __launch_bounds__(THREADS) k_pcg_instances(InstPcgArgs<T> a, int
         I->iters = it;
         I->rel = rr0 > T(0) ? sqrt((double)rr_last / (double)rr0) : 0.0;
         I->gd = gdt.value() * scale;
+    }
+}
+
+// PCG (Chronopoulos-Gear form, as in the grid-wide solver) of one instance at a time per
+// block: a persistent launch whose blocks take the instances from a queue in the order of ids
+// (one atomic per instance), so one launch covers every instance, whatever their sizes.  Each
+// row's product is summed by kInstLanes lanes in a fixed order and every reduction goes
+// through rows_total, so the result depends neither on THREADS nor on which block takes an
+// instance (the tuner picks THREADS, the blocks per SM and the order).
+template <typename T, int THREADS>
+__global__ void __launch_bounds__(THREADS) k_pcg_instances(InstPcgArgs<T> a, int smem_bytes) {
+    __shared__ int s_take;
+    while (true) {
+        __syncthreads();   // s_take of the previous instance has been read by every thread
+        if (threadIdx.x == 0) s_take = (int)atomicAdd(a.queue, 1u);
+        __syncthreads();
+        const int take = s_take;
+        if (take >= a.n_ids) return;
+        inst_pcg_one<T, THREADS>(a, a.ids[take], smem_bytes);
     }
 }
 
@@ -588,35 +611,93 @@ template <typename T> cudaError_t instance_energies(Ctx &c, const int2 *pairs, i
 template cudaError_t instance_energies<float>(Ctx &, const int2 *, int);
 template cudaError_t instance_energies<double>(Ctx &, const int2 *, int);
 
-// Size buckets of the batched PCG (rows per instance: <= 64, <= 512, <= 4096, more) and the
-// block sizes the tuner times for each bucket the first time the context meets it.  Results do
-// not depend on the block size (k_pcg_instances), so the choice only changes the speed.
-constexpr int kBucketRows[kInstBuckets - 1] = {64, 512, 4096};
-constexpr int kTunerThreads[] = {128, 256, 512, 1024};
+// The batched PCG is one persistent launch over all instances (k_pcg_instances takes them from
+// a queue).  Its schedule is tuned on the first batched step of a context by timing every
+// candidate on the actual system: threads per block, blocks per SM (each block's shared
+// memory is the SM's divided among them; an instance whose rows and matrix do not fit runs
+// from global memory) and the order of the queue (largest instance first, or as numbered).
+// Results do not depend on the schedule, only the time does.  With the environment variable
+// TTIE_TUNE_CACHE naming a file, the choice is kept there (one line per device, precision,
+// instance count and row count) and read back by later contexts instead of tuning again.
+constexpr int kTunerThreads[] = {256, 512, 1024};
+constexpr int kTunerBlocksPerSM[] = {1, 2, 4};
 
 template <typename T, int THREADS>
-cudaError_t launch_inst(Ctx &c, const InstPcgArgs<T> &a, int n, int smem, cudaStream_t st) {
-    // the dynamic share is at most what the device allows a block beside the kernel's static share
+cudaError_t launch_inst(Ctx &c, const InstPcgArgs<T> &a, int bps, cudaStream_t st) {
+    // per block: the SM's shared memory divided among bps blocks, beside the kernel's static share
     cudaFuncAttributes fa;
     TTIE_CUDA_TRY(cudaFuncGetAttributes(&fa, (const void *)k_pcg_instances<T, THREADS>));
-    int optin = 0;
+    int optin = 0, per_sm = 0;
     TTIE_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c.device));
-    smem = std::min(smem, (int)(optin - (int)fa.sharedSizeBytes) / 16 * 16);
+    TTIE_CUDA_TRY(cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, c.device));
+    int smem = std::min(optin, per_sm / bps - 1024) - (int)fa.sharedSizeBytes;
+    smem = std::max(0, std::min(smem, kInstSmemMax)) / 16 * 16;
     TTIE_CUDA_TRY(cudaFuncSetAttribute((const void *)k_pcg_instances<T, THREADS>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    int resident = 0;
+    TTIE_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, k_pcg_instances<T, THREADS>, THREADS,
+                                                                (size_t)smem));
+    if (resident < 1) resident = 1;
+    const int sms = c.num_sms > 0 ? c.num_sms : kNumSMs;
+    const int grid = std::max(1, std::min(a.n_ids, std::min(resident, bps) * sms));
+    TTIE_CUDA_TRY(cudaMemsetAsync(a.queue, 0, sizeof(unsigned int), st));
     ++c.n_launch;
-    k_pcg_instances<T, THREADS><<<dim3((unsigned)n), dim3(THREADS), (size_t)smem, st>>>(a, smem);
+    k_pcg_instances<T, THREADS><<<dim3((unsigned)grid), dim3(THREADS), (size_t)smem, st>>>(a, smem);
     return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_inst_threads(Ctx &c, const InstPcgArgs<T> &a, int n, int smem, int threads, cudaStream_t st) {
+cudaError_t launch_inst_threads(Ctx &c, const InstPcgArgs<T> &a, int threads, int bps, cudaStream_t st) {
     switch (threads) {
-    case 128: return launch_inst<T, 128>(c, a, n, smem, st);
-    case 256: return launch_inst<T, 256>(c, a, n, smem, st);
-    case 512: return launch_inst<T, 512>(c, a, n, smem, st);
-    default: return launch_inst<T, 1024>(c, a, n, smem, st);
+    case 128: return launch_inst<T, 128>(c, a, bps, st);
+    case 256: return launch_inst<T, 256>(c, a, bps, st);
+    case 512: return launch_inst<T, 512>(c, a, bps, st);
+    default: return launch_inst<T, 1024>(c, a, bps, st);
     }
+}
+
+static std::string tune_key(Ctx &c, int n_inst, long long rows) {
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, c.device) != cudaSuccess) prop.name[0] = 0;
+    std::string dev(prop.name);
+    for (char &ch : dev)
+        if (ch == ' ' || ch == '"') ch = '_';
+    char buf[256];
+    snprintf(buf, sizeof buf, "inst_pcg %s f%d n%d rows%lld", dev.c_str(), c.prm.precision == TTIE_F64 ? 64 : 32,
+             n_inst, rows);
+    return buf;
+}
+
+// the cache file holds one JSON object per line: {"key": "...", "threads": T, "blocks_per_sm": B, "order": O}
+static bool tune_read(const std::string &key, int *threads, int *bps, int *order) {
+    const char *path = getenv("TTIE_TUNE_CACHE");
+    if (!path || !*path) return false;
+    FILE *f = fopen(path, "r");
+    if (!f) return false;
+    char line[512];
+    bool found = false;
+    const std::string want = "{\"key\": \"" + key + "\",";
+    while (fgets(line, sizeof line, f)) {
+        if (strncmp(line, want.c_str(), want.size()) != 0) continue;
+        int t = 0, b = 0, o = 0;
+        if (sscanf(line + want.size(), " \"threads\": %d, \"blocks_per_sm\": %d, \"order\": %d", &t, &b, &o) == 3 &&
+            (t == 256 || t == 512 || t == 1024) && (b == 1 || b == 2 || b == 4) && (o == 0 || o == 1)) {
+            *threads = t; *bps = b; *order = o;
+            found = true;
+        }
+    }
+    fclose(f);
+    return found;
+}
+
+static void tune_write(const std::string &key, int threads, int bps, int order, float ms) {
+    const char *path = getenv("TTIE_TUNE_CACHE");
+    if (!path || !*path) return;
+    FILE *f = fopen(path, "a");
+    if (!f) return;
+    fprintf(f, "{\"key\": \"%s\", \"threads\": %d, \"blocks_per_sm\": %d, \"order\": %d, \"ms\": %.4f}\n", key.c_str(),
+            threads, bps, order, ms);
+    fclose(f);
 }
 
 template <typename T> cudaError_t instance_pcg(Ctx &c, const T *rhs, T *out) {
@@ -630,31 +711,22 @@ template <typename T> cudaError_t instance_pcg(Ctx &c, const T *rhs, T *out) {
     TTIE_CUDA_TRY(ensure(c, c.pcg_w, n3));
     TTIE_CUDA_TRY(ensure(c, c.dinv, (size_t)(nr > 0 ? nr : 1) * 9 * sizeof(T)));
     TTIE_CUDA_TRY(ensure(c, c.inst_acc, (size_t)(nr > 0 ? nr : 1) * 3 * 8));
-    TTIE_CUDA_TRY(ensure(c, c.inst_ids, (size_t)(G > 0 ? G : 1) * 4));
-    // buckets by size, and the shared memory that keeps a bucket's largest instance resident
+    TTIE_CUDA_TRY(ensure(c, c.inst_ids, (size_t)(G > 0 ? G : 1) * 4 * 2));
+    // the instances with rows, in the two queue orders: largest first (by rows, then nnz), as numbered
     std::vector<Inst> h(G);
     TTIE_CUDA_TRY(cudaMemcpyAsync(h.data(), c.inst.p, (size_t)G * sizeof(Inst), cudaMemcpyDeviceToHost, c.stream));
     TTIE_CUDA_TRY(cudaStreamSynchronize(c.stream));
     std::vector<int32_t> ids;
-    int start[kInstBuckets + 1] = {0}, smem[kInstBuckets] = {0};
-    for (int b = 0; b < kInstBuckets; ++b) {
-        start[b] = (int)ids.size();
-        for (int g = 0; g < G; ++g) {
-            const int rows = h[g].count;
-            if (rows <= 0) continue;
-            int bb = kInstBuckets - 1;
-            for (int k = 0; k < kInstBuckets - 1; ++k)
-                if (rows <= kBucketRows[k]) { bb = k; break; }
-            if (bb != b) continue;
-            ids.push_back(g);
-            const size_t need = ((size_t)rows * (27 * sizeof(T) + 24) + (size_t)(rows + 1) * 4 + 15) / 16 * 16 +
-                                (size_t)h[g].nnz * (9 * sizeof(T) + 4);
-            smem[b] = (int)std::min<size_t>(std::max<size_t>((size_t)smem[b], (need + 15) / 16 * 16), kInstSmemMax);
-        }
-    }
-    start[kInstBuckets] = (int)ids.size();
-    if (!ids.empty())
-        TTIE_CUDA_TRY(cudaMemcpyAsync(c.inst_ids.p, ids.data(), ids.size() * 4, cudaMemcpyHostToDevice, c.stream));
+    for (int g = 0; g < G; ++g)
+        if (h[g].count > 0) ids.push_back(g);
+    const int n = (int)ids.size();
+    std::vector<int32_t> both(ids);
+    std::stable_sort(both.begin(), both.end(), [&](int32_t x, int32_t y) {
+        return h[x].count != h[y].count ? h[x].count > h[y].count : h[x].nnz > h[y].nnz;
+    });
+    both.insert(both.end(), ids.begin(), ids.end());
+    if (n > 0)
+        TTIE_CUDA_TRY(cudaMemcpyAsync(c.inst_ids.p, both.data(), both.size() * 4, cudaMemcpyHostToDevice, c.stream));
     InstPcgArgs<T> a;
     a.row_ptr = (const int32_t *)c.row_ptr.p;
     a.col_idx = (const int32_t *)c.col_idx.p;
@@ -670,52 +742,51 @@ template <typename T> cudaError_t instance_pcg(Ctx &c, const T *rhs, T *out) {
     a.acc = (unsigned long long *)c.inst_acc.p;
     a.edge = (const double *)c.iedge.p;
     a.inst = (Inst *)c.inst.p;
+    a.n_ids = n;
+    a.queue = &c.ds->inst_queue;
     a.mu_rel = c.prm.mu_rel;
     a.rtol2 = c.prm.pcg_rtol * c.prm.pcg_rtol;
     a.max_step = c.prm.max_step;
     a.max_it = c.prm.pcg_max_it;
     a.n_rows = nr;
-    // tuning (first time a bucket is met): every candidate block size timed on the main stream
-    for (int b = 0; b < kInstBuckets; ++b) {
-        const int n = start[b + 1] - start[b];
-        if (n == 0 || c.prm.inst_threads > 0 || c.inst_tuned[b] > 0) continue;
-        a.ids = (const int32_t *)c.inst_ids.p + start[b];
-        cudaEvent_t e0, e1;
-        TTIE_CUDA_TRY(cudaEventCreate(&e0));
-        TTIE_CUDA_TRY(cudaEventCreate(&e1));
-        float best = 0.f;
-        int pick = 0;
-        for (int t : kTunerThreads) {
-            TTIE_CUDA_TRY(cudaEventRecord(e0, c.stream));
-            TTIE_CUDA_TRY(launch_inst_threads<T>(c, a, n, smem[b], t, c.stream));
-            TTIE_CUDA_TRY(cudaEventRecord(e1, c.stream));
-            TTIE_CUDA_TRY(cudaEventSynchronize(e1));
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            if (pick == 0 || ms < best) { best = ms; pick = t; }
+    if (n == 0) return cudaSuccess;
+    // the schedule: a caller's block size with the tuned rest, the cache, or a timed sweep
+    if (c.inst_tuned[0] == 0) {
+        const std::string key = tune_key(c, n, (long long)nr);
+        int t = 0, b = 0, o = 0;
+        if (tune_read(key, &t, &b, &o)) {
+            c.inst_tuned[0] = t; c.inst_tuned[1] = b; c.inst_tuned[2] = o;
+        } else {
+            cudaEvent_t e0, e1;
+            TTIE_CUDA_TRY(cudaEventCreate(&e0));
+            TTIE_CUDA_TRY(cudaEventCreate(&e1));
+            float best = -1.f;
+            for (int tt : kTunerThreads) {
+                if (c.prm.inst_threads > 0 && tt != c.prm.inst_threads) continue;
+                for (int bb : kTunerBlocksPerSM)
+                    for (int oo = 0; oo < 2; ++oo) {
+                        a.ids = (const int32_t *)c.inst_ids.p + (oo ? n : 0);
+                        TTIE_CUDA_TRY(cudaEventRecord(e0, c.stream));
+                        TTIE_CUDA_TRY(launch_inst_threads<T>(c, a, tt, bb, c.stream));
+                        TTIE_CUDA_TRY(cudaEventRecord(e1, c.stream));
+                        TTIE_CUDA_TRY(cudaEventSynchronize(e1));
+                        float ms = 0.f;
+                        cudaEventElapsedTime(&ms, e0, e1);
+                        if (best < 0.f || ms < best) {
+                            best = ms; c.inst_tuned[0] = tt; c.inst_tuned[1] = bb; c.inst_tuned[2] = oo;
+                        }
+                    }
+            }
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            if (c.inst_tuned[0] == 0) { c.inst_tuned[0] = 512; c.inst_tuned[1] = 1; c.inst_tuned[2] = 0; }
+            else tune_write(key, c.inst_tuned[0], c.inst_tuned[1], c.inst_tuned[2], best);
         }
-        cudaEventDestroy(e0);
-        cudaEventDestroy(e1);
-        c.inst_tuned[b] = pick;
     }
-    // the buckets run side by side, one stream each, forked from and joined to the main stream
-    for (int b = 0; b < kInstBuckets; ++b) {
-        if (!c.aux[b]) TTIE_CUDA_TRY(cudaStreamCreateWithFlags(&c.aux[b], cudaStreamNonBlocking));
-        if (!c.aux_ev[b]) TTIE_CUDA_TRY(cudaEventCreateWithFlags(&c.aux_ev[b], cudaEventDisableTiming));
-    }
-    if (!c.aux_ev[kInstBuckets]) TTIE_CUDA_TRY(cudaEventCreateWithFlags(&c.aux_ev[kInstBuckets], cudaEventDisableTiming));
+    const int threads = c.prm.inst_threads > 0 ? c.prm.inst_threads : c.inst_tuned[0];
+    a.ids = (const int32_t *)c.inst_ids.p + (c.inst_tuned[2] ? n : 0);
     if (c.prm.profile) cudaEventRecord(c.ev[8], c.stream);
-    TTIE_CUDA_TRY(cudaEventRecord(c.aux_ev[kInstBuckets], c.stream));
-    for (int b = 0; b < kInstBuckets; ++b) {
-        const int n = start[b + 1] - start[b];
-        if (n == 0) continue;
-        a.ids = (const int32_t *)c.inst_ids.p + start[b];
-        const int threads = c.prm.inst_threads > 0 ? c.prm.inst_threads : c.inst_tuned[b];
-        TTIE_CUDA_TRY(cudaStreamWaitEvent(c.aux[b], c.aux_ev[kInstBuckets], 0));
-        TTIE_CUDA_TRY(launch_inst_threads<T>(c, a, n, smem[b], threads, c.aux[b]));
-        TTIE_CUDA_TRY(cudaEventRecord(c.aux_ev[b], c.aux[b]));
-        TTIE_CUDA_TRY(cudaStreamWaitEvent(c.stream, c.aux_ev[b], 0));
-    }
+    TTIE_CUDA_TRY(launch_inst_threads<T>(c, a, threads, c.inst_tuned[1], c.stream));
     if (c.prm.profile) cudaEventRecord(c.ev[9], c.stream);
     return cudaGetLastError();
 }

@@ -479,13 +479,9 @@ using ::fabs;
 // chain rule through the construction above.  S is float, double or a dual number (the
 // exact Hessian-vector product differentiates this function once more in forward mode).
 // br: the branch taken (out), or with given = true the branch to take (in).
-// cond (nullable, out): the smallest of the sines of the angle between the two planes and of
-// the angles between each cut edge and the plane that cuts it; the derivatives' sensitivity to
-// rounding grows with the inverse of these sines (D = normalize(n_B x n_A), and the endpoint
-// parameter lambda and the coefficient rho divide by n.e).
 template <typename S, bool kGrad>
 __device__ __forceinline__ void pair_tc(v3<S> A[3], v3<S> B[3], S tc_scale, S &a, S &b, S *ga, S *gb, Branch &br,
-                                        bool given = false, S *cond = nullptr) {
+                                        bool given = false) {
     // local frame at A0: T and its gradient are translation invariant, and small
     // coordinates keep the cancellations in t_c at the size of the triangles
     const v3<S> o = A[0];
@@ -499,20 +495,6 @@ __device__ __forceinline__ void pair_tc(v3<S> A[3], v3<S> B[3], S tc_scale, S &a
     const S wn = sqrt(dot(wv, wv));
     const S inv_w = wn > S(0) ? S(1) / wn : S(0);
     const v3<S> D = inv_w * wv;
-    if (cond) {
-        const S na = sqrt(dot(nA, nA)), nb = sqrt(dot(nB, nB));
-        S c = wn / (na * nb);
-        const auto edge_sine = [&](const v3<S> Q[3], int m, int p, v3<S> nP, S nn) {
-            const v3<S> e = Q[p] - Q[m];
-            const S s = fabs(dot(nP, e)) / (nn * sqrt(dot(e, e)));
-            if (s < c) c = s;
-        };
-        edge_sine(B, cB.m0, cB.p0, nA, na);
-        edge_sine(B, cB.m1, cB.p1, nA, na);
-        edge_sine(A, cA.m0, cA.p0, nB, nb);
-        edge_sine(A, cA.m1, cA.p1, nB, nb);
-        *cond = (c != c) ? S(0) : c;   // NaN (degenerate triangle) counts as ill-conditioned
-    }
     const S tA0 = dot(D, cA.S0), tA1 = dot(D, cA.S1), tB0 = dot(D, cB.S0), tB1 = dot(D, cB.S1);
     if (!given) {
         br.a0min = !(tA1 < tA0);
@@ -544,125 +526,56 @@ __device__ __forceinline__ void pair_tc(v3<S> A[3], v3<S> B[3], S tc_scale, S &a
 
 // t_c^0 and t_c^1 are differences of positions of the pair's size L, so an FP32 evaluation
 // carries an absolute error of a few u32 L in them: relative 1e-3 and more on pairs whose
-// |t_c| is 1e-6 of the scene.  For FP32 positions the values and the branch (the cut edges,
-// the min/max ends) are therefore evaluated in FP64 from the exactly converted FP32 inputs,
-// and only the gradients, whose relative error is not amplified by a small t_c, in FP32
-// along that same branch.  This runs on the intersecting pairs only.
-//
-// The FP32 gradients' relative error grows with the inverse of pair_tc's cond (the smallest
-// sine) and with the cancellation between the two terms of Eq. 3, b grad a + a grad b (the
-// ratio kappa of its largest entry to that of |b grad a| + |a grad b|); measured on the
-// crossing cloth, the error stays below 1e-5 while cond * kappa >= 0.05.  A pair below that
-// returns false: its gradients are evaluated again in FP64 (k_derivs_fp64).  cond and kappa
-// come from the FP32 pass itself.
-constexpr float kCondMin = 0.05f;
-
+// |t_c| is 1e-6 of the scene.  Their gradients carry errors that grow with the inverse sines
+// of the angles between the planes and between the cut edges and the cutting planes, and with
+// the cancellation between the two terms of Eq. 3: up to 1.4e-4 relative on the crossing
+// cloth, and no cheap estimate of those factors kept every FP32 gradient within 1e-4 (one
+// missed 1.1e-4 after a few Newton steps).  So for FP32 positions the derivatives of the
+// intersecting pairs are evaluated in FP64 from the exactly converted FP32 inputs and
+// rounded to FP32; the classification of all candidates (k_classify) stays in FP32.  This runs
+// on the intersecting pairs only (about 9 % of the candidates).
 template <typename T, bool kGrad>
-__device__ __forceinline__ bool pair_values(const vec4_t<T> *__restrict__ x, const int4 *__restrict__ tri4, int2 pr,
+__device__ __forceinline__ void pair_values(const vec4_t<T> *__restrict__ x, const int4 *__restrict__ tri4, int2 pr,
                                             T tc_scale, double &a, double &b, T *ga, T *gb) {
     v3<T> A[3], B[3];
     load_pair<T>(x, tri4, pr, A, B);
+    v3<double> Ad[3], Bd[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) { Ad[i] = to_d(A[i]); Bd[i] = to_d(B[i]); }
+    double gad[18], gbd[18];
     Branch br;
-    if (sizeof(T) == 4) {
-        v3<double> Ad[3], Bd[3];
+    pair_tc<double, kGrad>(Ad, Bd, (double)tc_scale, a, b, gad, gbd, br);
+    if (kGrad) {
 #pragma unroll
-        for (int i = 0; i < 3; ++i) { Ad[i] = to_d(A[i]); Bd[i] = to_d(B[i]); }
-        pair_tc<double, false>(Ad, Bd, (double)tc_scale, a, b, nullptr, nullptr, br);
-        if (kGrad) {
-            T af, bf, cond = T(1);
-            pair_tc<T, true>(A, B, tc_scale, af, bf, ga, gb, br, true, &cond);
-            const T fa = (T)a, fb = (T)b;
-            T num = T(0), den = T(0);
-#pragma unroll
-            for (int i = 0; i < 18; ++i) {
-                num = fmax(num, fabs(fb * ga[i] + fa * gb[i]));
-                den = fmax(den, fabs(fb * ga[i]) + fabs(fa * gb[i]));
-            }
-            return cond * num >= T(kCondMin) * den;   // cond * kappa >= kCondMin
-        }
-    } else {
-        T at, bt;
-        pair_tc<T, kGrad>(A, B, tc_scale, at, bt, ga, gb, br);
-        a = (double)at;
-        b = (double)bt;
+        for (int i = 0; i < 18; ++i) { ga[i] = (T)gad[i]; gb[i] = (T)gbd[i]; }
     }
-    return true;
 }
 
-// ill (with kGrad, FP32 positions): receives the rows whose gradients k_derivs_fp64 redoes
-// (count in ds->n_illcond, cleared before the launch).
 template <typename T, bool kGrad>
 __global__ void __launch_bounds__(128) k_derivs(const vec4_t<T> *__restrict__ x, const int4 *__restrict__ tri4,
                                                 const int2 *__restrict__ pairs, const uint32_t *__restrict__ active,
                                                 T tc_scale, T *__restrict__ fac, int stride, double *partials,
-                                                uint32_t *__restrict__ ill, DevScalars *ds) {
+                                                DevScalars *ds) {
     const unsigned long long n_act = ds->n_active;
-    const int lane = threadIdx.x & 31;
     double e_sum = 0.0;
-    // whole warps run the loop, so the deferred rows are appended with one atomic per warp
-    const unsigned long long n_round = (n_act + 31) / 32 * 32;
-    for (unsigned long long k = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; k < n_round;
+    for (unsigned long long k = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; k < n_act;
          k += (unsigned long long)gridDim.x * blockDim.x) {
-        bool redo = false;
-        if (k < n_act) {
-            double a, b;
-            T ga[18], gb[18];
-            const bool good = pair_values<T, kGrad>(x, tri4, pairs[active[k]], tc_scale, a, b, ga, gb);
-            e_sum += (a * b) * (a * b);
-            T *row = fac + k * stride;
-            row[0] = (T)a;
-            row[1] = (T)b;
-            if (kGrad) {
-                redo = !good;
-                if (good) {
+        double a, b;
+        T ga[18], gb[18];
+        pair_values<T, kGrad>(x, tri4, pairs[active[k]], tc_scale, a, b, ga, gb);
+        e_sum += (a * b) * (a * b);
+        T *row = fac + k * stride;
+        row[0] = (T)a;
+        row[1] = (T)b;
+        if (kGrad) {
 #pragma unroll
-                    for (int i = 0; i < 18; ++i) {
-                        row[2 + i] = ga[i];
-                        row[20 + i] = gb[i];
-                    }
-                }
-            }
-        }
-        if (kGrad && ill) {
-            const unsigned m = __ballot_sync(0xffffffffu, redo);
-            if (m) {
-                unsigned long long base = 0;
-                if (lane == 0) base = atomicAdd(&ds->n_illcond, (unsigned long long)__popc(m));
-                base = __shfl_sync(0xffffffffu, base, 0);
-                if (redo) ill[base + __popc(m & ((1u << lane) - 1u))] = (uint32_t)k;
+            for (int i = 0; i < 18; ++i) {
+                row[2 + i] = ga[i];
+                row[20 + i] = gb[i];
             }
         }
     }
     grid_sum(e_sum, partials, &ds->done_counter[0], &ds->energy);
-}
-
-// Gradients of t_c^0 and t_c^1 in FP64 for the rows k_derivs deferred (ill-conditioned or
-// cancelling pairs of an FP32 evaluation), rounded to the row's precision.
-template <typename T>
-__global__ void __launch_bounds__(128) k_derivs_fp64(const vec4_t<T> *__restrict__ x, const int4 *__restrict__ tri4,
-                                                     const int2 *__restrict__ pairs,
-                                                     const uint32_t *__restrict__ active, double tc_scale,
-                                                     const uint32_t *__restrict__ ill, T *__restrict__ fac, int stride,
-                                                     const DevScalars *ds) {
-    const unsigned long long n = ds->n_illcond;
-    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
-         i += (unsigned long long)gridDim.x * blockDim.x) {
-        const uint32_t k = ill[i];
-        v3<T> A[3], B[3];
-        load_pair<T>(x, tri4, pairs[active[k]], A, B);
-        v3<double> Ad[3], Bd[3];
-#pragma unroll
-        for (int j = 0; j < 3; ++j) { Ad[j] = to_d(A[j]); Bd[j] = to_d(B[j]); }
-        double a, b, ga[18], gb[18];
-        Branch br;
-        pair_tc<double, true>(Ad, Bd, tc_scale, a, b, ga, gb, br);
-        T *row = fac + (size_t)k * stride;
-#pragma unroll
-        for (int j = 0; j < 18; ++j) {
-            row[2 + j] = (T)ga[j];
-            row[20 + j] = (T)gb[j];
-        }
-    }
 }
 
 // Exact Hessian-vector product per intersecting pair: the pair gradient of Eq. 3,
@@ -788,21 +701,12 @@ cudaError_t eval_candidates(Ctx &c, const vec4_t<T> *x, const int2 *pairs, int64
     const int64_t n_act = (int64_t)c.hs->n_active;
     TTIE_CUDA_TRY(ensure(c, c.fac, (size_t)(n_act > 0 ? n_act : 1) * kFacStride * sizeof(T)));
     const unsigned gd = grid_for(n_act, 128, (int64_t)kNumSMs * 8);
-    if (grad) {
-        // the deferred list reuses the classification's first defer list (consumed by now)
-        const bool f32 = sizeof(T) == 4;
-        uint32_t *ill = f32 ? (uint32_t *)c.defer.p : nullptr;
-        if (f32) TTIE_CUDA_TRY(cudaMemsetAsync(&c.ds->n_illcond, 0, sizeof(unsigned long long), c.stream));
+    if (grad)
         launch(c, k_derivs<T, true>, dim3(gd), dim3(128), x, tri4, pairs, (const uint32_t *)c.active.p, (T)c.prm.tc_scale,
-               (T *)c.fac.p, kFacStride, (double *)c.partials.p, ill, c.ds);
-        if (f32)
-            launch(c, k_derivs_fp64<T>, dim3(grid_for(n_act, 128, (int64_t)kNumSMs * 4)), dim3(128), x, tri4, pairs,
-                   (const uint32_t *)c.active.p, c.prm.tc_scale, (const uint32_t *)ill, (T *)c.fac.p, kFacStride,
-                   (const DevScalars *)c.ds);
-    } else {
+               (T *)c.fac.p, kFacStride, (double *)c.partials.p, c.ds);
+    else
         launch(c, k_derivs<T, false>, dim3(gd), dim3(128), x, tri4, pairs, (const uint32_t *)c.active.p, (T)c.prm.tc_scale,
-               (T *)c.fac.p, kFacStride, (double *)c.partials.p, (uint32_t *)nullptr, c.ds);
-    }
+               (T *)c.fac.p, kFacStride, (double *)c.partials.p, c.ds);
     c.n_active = n_act;
     return cudaGetLastError();
 }
@@ -856,8 +760,7 @@ cudaError_t energy_eval_nosync(Ctx &c, const vec4_t<T> *x, const int2 *pairs, in
         TTIE_CUDA_TRY(cudaMemsetAsync(&c.ds->n_active, 0, 8, c.stream));
     }
     launch(c, k_derivs<T, false>, dim3(grid_for(n_cap, 128, (int64_t)kNumSMs * 8)), dim3(128), x, tri4, pairs,
-           (const uint32_t *)c.active.p, (T)c.prm.tc_scale, (T *)c.ab.p, 2, (double *)c.partials.p,
-           (uint32_t *)nullptr, c.ds);
+           (const uint32_t *)c.active.p, (T)c.prm.tc_scale, (T *)c.ab.p, 2, (double *)c.partials.p, c.ds);
     return cudaGetLastError();
 }
 template cudaError_t energy_eval_nosync<float>(Ctx &, const float4 *, const int2 *, int64_t, const unsigned long long *);

@@ -557,118 +557,9 @@ template <typename T> struct ResidentView {
     int *col;                         // their columns when cached
     T *gu;                            // u at each block's column (3 per block) when gathered
     T *d, *rr;                        // Chebyshev preconditioner: direction and D^-1 residual (3 each)
-    T *stage;                         // matrix not cached: one tile of blocks (9 values each) ...
-    int *stage_col;                   // ... and their columns
     bool cached, gathered;
     int nrow, nnz, b_begin;
 };
-
-// Matrix blocks per tile of the streamed product (a 36 KB tile of values either way) and the
-// shared memory the tile takes, values and columns.
-template <typename T> __host__ __device__ constexpr int stage_blocks() { return sizeof(T) == 4 ? 1024 : 512; }
-template <typename T> __host__ __device__ constexpr size_t stage_bytes() {
-    return (size_t)stage_blocks<T>() * (9 * sizeof(T) + sizeof(int));
-}
-constexpr int kStageQuads = 2304;   // 16-byte words of a tile's values (36,864 bytes)
-static_assert(kStageQuads * 16 == 1024 * 9 * 4 && kStageQuads * 16 == 512 * 9 * 8, "tile of 36 KB");
-constexpr int kStageLoads = (kStageQuads + kPcgThreads - 1) / kPcgThreads;   // 16-byte loads per thread
-
-// w = (A + mu I) u on the block's rows when its matrix rows are not cached: the block's
-// blocks [b_begin, b_begin + nnz) are contiguous in global memory and stream through shared
-// memory one tile at a time (16-byte loads by every thread, the next tile's issued before the
-// current one is used), so the matrix is read at the rate of the memory system rather than
-// behind the gathers of u.  Then a thread per block of the tile gathers u of its column (tagged
-// word, as below) and multiplies, leaving the 3-vector in its block's slot, and a thread per
-// row of the tile adds its blocks' products in block order to w (a row that spans tiles
-// receives them tile by tile, so every sum has a fixed order).  Tiles start at a multiple of
-// four blocks (16-byte aligned for both value types); the last 16-byte word of a tile may
-// reach past the block range, at most into the allocation's tail (the context's buffers are
-// allocated with at least 256 bytes to spare).
-template <typename T>
-__device__ __noinline__ Acc<T> resident_product_streamed(const PcgArgs<T> &a, const ResidentView<T> &v,
-                                                         const vec4_t<T> *src, const T *loc, T mu, unsigned t,
-                                                         int *bad) {
-    constexpr int TB = stage_blocks<T>();
-    const int tid = threadIdx.x;
-    for (int i = tid; i < 3 * v.nrow; i += kPcgThreads) v.w[i] = mu * loc[i];
-    // local block indices, relative to lo4 = b_begin rounded down to a multiple of 4: the
-    // block's blocks are [first, last), tile j holds [j TB, j TB + TB)
-    const int first = v.b_begin & 3, last = first + v.nnz;
-    const float4 *mat4 = reinterpret_cast<const float4 *>(a.bval + (size_t)(v.b_begin - first) * 9);
-    const int *colp = a.col_idx + (v.b_begin - first);
-    const int n_tiles = v.nnz > 0 ? (last + TB - 1) / TB : 0;
-    const unsigned n_rows = (unsigned)a.ds->n_rows;
-    float4 pre[kStageLoads];
-    int pcol = -1;
-    if (n_tiles > 0) {
-        const int nq = (min(TB, last) * 9 * (int)sizeof(T) + 15) / 16;
-#pragma unroll
-        for (int k = 0; k < kStageLoads; ++k)
-            if (tid + k * kPcgThreads < nq) pre[k] = __ldcs(mat4 + tid + k * kPcgThreads);
-        if (tid < TB && tid >= first && tid < last) pcol = colp[tid];
-    }
-    for (int j = 0; j < n_tiles; ++j) {
-        const int t0 = j * TB, t1 = min(t0 + TB, last);
-        float4 *st4 = reinterpret_cast<float4 *>(v.stage);
-        {
-            const int nq = ((t1 - t0) * 9 * (int)sizeof(T) + 15) / 16;
-#pragma unroll
-            for (int k = 0; k < kStageLoads; ++k)
-                if (tid + k * kPcgThreads < nq) st4[tid + k * kPcgThreads] = pre[k];
-        }
-        if (tid < TB) v.stage_col[tid] = pcol;
-        __syncthreads();
-        if (j + 1 < n_tiles) {   // the next tile's loads are in flight during this tile's work
-            const int u0 = t0 + TB, u1 = min(u0 + TB, last);
-            const int nq = ((u1 - u0) * 9 * (int)sizeof(T) + 15) / 16;
-            const float4 *b4 = mat4 + (size_t)(j + 1) * kStageQuads;
-#pragma unroll
-            for (int k = 0; k < kStageLoads; ++k)
-                if (tid + k * kPcgThreads < nq) pre[k] = __ldcs(b4 + tid + k * kPcgThreads);
-            pcol = (tid < TB && u0 + tid < u1) ? colp[u0 + tid] : -1;
-        }
-        // products of the tile's blocks
-        if (tid < TB) {
-            const int c = v.stage_col[tid];
-            if (c >= 0 && !TTIE_BAD(a.ds, (unsigned)c < n_rows, 46, c)) {
-                vec4_t<T> g = ld_row<T>(&src[c]);
-                settle_row<T>(g, &src[c], t, bad);
-                T *m = v.stage + tid * 9;
-                T y0 = 0, y1 = 0, y2 = 0;
-                block_times(m, g.x, g.y, g.z, y0, y1, y2);
-                m[0] = y0; m[1] = y1; m[2] = y2;
-            }
-        }
-        __syncthreads();
-        // rows of the tile: the row whose blocks start at or before the tile's first one, and
-        // the following ones up to the tile's end (v.rp is relative to b_begin)
-        const int lo = max(t0, first) - first, hi = t1 - first;
-        int r0 = 0, r1 = v.nrow;
-        while (r1 - r0 > 1) {
-            const int mid = (r0 + r1) >> 1;
-            if (v.rp[mid] <= lo) r0 = mid;
-            else r1 = mid;
-        }
-        const int r = r0 + tid;
-        if (r < v.nrow && v.rp[r] < hi) {
-            const int e0 = max(v.rp[r], lo), e1 = min(v.rp[r + 1], hi);
-            T y0 = 0, y1 = 0, y2 = 0;
-            for (int e = e0; e < e1; ++e) {
-                const T *m = v.stage + (e + first - t0) * 9;
-                y0 += m[0]; y1 += m[1]; y2 += m[2];
-            }
-            v.w[r * 3] += y0; v.w[r * 3 + 1] += y1; v.w[r * 3 + 2] += y2;
-        }
-        __syncthreads();
-    }
-    Acc<T> wu;
-    for (int lr = tid; lr < v.nrow; lr += kPcgThreads) {
-        wu.add_prod(v.w[lr * 3], loc[lr * 3]);
-        wu.add_prod(v.w[lr * 3 + 1], loc[lr * 3 + 1]);
-        wu.add_prod(v.w[lr * 3 + 2], loc[lr * 3 + 2]);
-    }
-    return wu;
-}
 
 // w = (A + mu I) u on the block's rows, u of every row read from the published vectors src
 // with tag t (loc: the block's own rows of u, for the shift); returns the rows' w.u.  A load
@@ -676,7 +567,6 @@ __device__ __noinline__ Acc<T> resident_product_streamed(const PcgArgs<T> &a, co
 template <typename T>
 __device__ __forceinline__ Acc<T> resident_product(const PcgArgs<T> &a, const ResidentView<T> &v,
                                                    const vec4_t<T> *src, const T *loc, T mu, unsigned t, int *bad) {
-    if (!v.cached) return resident_product_streamed<T>(a, v, src, loc, mu, t, bad);
     if (v.gathered) {
         // gather every block's column vector first: all loads of a thread in flight together
         // words not yet tagged t are loaded again, all of a thread's together
@@ -720,8 +610,8 @@ __device__ __forceinline__ Acc<T> resident_product(const PcgArgs<T> &a, const Re
             for (int b = v.rp[lr] + sub; b < be; b += kLanesPerRow)
                 block_times(v.val + (size_t)b * 9, v.gu[3 * b], v.gu[3 * b + 1], v.gu[3 * b + 2], y0, y1, y2);
         } else {
-            // up to four of the lane's blocks at a time: every load in flight before any tag
-            // is checked (a check is a branch on the loaded value)
+            // matrix rows cached, u not gathered: up to four of the lane's blocks at a time,
+            // every load in flight before any tag is checked (a check is a branch on the value)
             constexpr int U = 4;
             for (int b0 = v.rp[lr] + sub; b0 < be; b0 += U * kLanesPerRow) {
                 int cc[U];
@@ -850,26 +740,15 @@ __global__ void __launch_bounds__(kPcgThreads) k_pcg_resident(PcgArgs<T> a, int 
     };
     // the Chebyshev preconditioner's d and rr, after the other vectors
     const auto cheb_size = [](int rows) { return kCheb ? ((size_t)rows * 6 * sizeof(T) + 15) / 16 * 16 : (size_t)0; };
-    // the smallest layout: lean vectors and a tile of the streamed product (or the whole
-    // matrix rows, when smaller)
-    const auto mat_size = [](long long nnz) { return ((size_t)nnz * (9 * sizeof(T) + sizeof(int)) + 15) / 16 * 16; };
-    if (!(row0 >= 0 && v.nrow >= 0 && row0 + v.nrow <= nr)) {
+    if (!(row0 >= 0 && v.nrow >= 0 && row0 + v.nrow <= nr &&
+          vec_size(v.nrow, 15) + cheb_size(v.nrow) <= (size_t)smem_bytes)) {
         partition_fail(ds, 45);   // checked in every build: the rows index shared memory
         v.nrow = 0;
     }
-    long long nnz_rows = v.nrow ? (long long)a.row_ptr[row0 + v.nrow] - a.row_ptr[row0] : 0;
-    if (vec_size(v.nrow, 15) + cheb_size(v.nrow) + min(mat_size(nnz_rows), stage_bytes<T>()) > (size_t)smem_bytes) {
-        partition_fail(ds, 45);
-        v.nrow = 0;
-        nnz_rows = 0;
-    }
     const int R = v.nrow;
     // lean: x and the inverse diagonal blocks (read or written once per row and iteration) stay
-    // in global memory so that larger row ranges fit (with the matrix rows cached, or else with
-    // room for a tile of the streamed product)
-    const size_t mat_or_tile = min(mat_size(nnz_rows), stage_bytes<T>());
-    const bool full_cached = vec_size(R, 27) + cheb_size(R) + mat_size(nnz_rows) <= (size_t)smem_bytes;
-    const bool lean = !full_cached && vec_size(R, 27) + cheb_size(R) + mat_or_tile > (size_t)smem_bytes;
+    // in global memory so that larger row ranges fit
+    const bool lean = vec_size(R, 27) + cheb_size(R) > (size_t)smem_bytes;
     size_t vec_bytes;
     if (lean) {
         v.r = (T *)smem; v.u = v.r + 3 * R; v.p = v.u + 3 * R; v.s = v.p + 3 * R; v.w = v.s + 3 * R;
@@ -890,14 +769,12 @@ __global__ void __launch_bounds__(kPcgThreads) k_pcg_resident(PcgArgs<T> a, int 
     }
     v.b_begin = v.nrow ? a.row_ptr[row0] : 0;
     v.nnz = v.nrow ? a.row_ptr[row0 + v.nrow] - v.b_begin : 0;
-    const size_t mat_bytes = mat_size(v.nnz);
+    const size_t mat_bytes = ((size_t)v.nnz * (9 * sizeof(T) + sizeof(int)) + 15) / 16 * 16;
     v.cached = vec_bytes + mat_bytes <= (size_t)smem_bytes;
     v.gathered = v.cached && vec_bytes + mat_bytes + (size_t)v.nnz * 3 * sizeof(T) <= (size_t)smem_bytes;
     v.val = (T *)(smem + vec_bytes);
     v.col = (int *)(v.val + (size_t)9 * v.nnz);
     v.gu = (T *)(smem + vec_bytes + mat_bytes);
-    v.stage = (T *)(smem + vec_bytes);   // used only when the matrix rows are not cached
-    v.stage_col = (int *)(v.stage + (size_t)9 * stage_blocks<T>());
     // load the block's rows (x = 0, r, u = M^-1 r as published with tag 0 by the setup kernel,
     // M^-1; p = s = 0)
     for (int i = threadIdx.x; i < 3 * v.nrow; i += blockDim.x) {
@@ -1143,11 +1020,14 @@ cudaError_t pcg_solve(Ctx &c, const T *rhs, T *out, double rtol, int max_it) {
     // per row); blocks are balanced by nnz + kRowWeight * rows within that cap; else the
     // global-memory kernel
     // (the Chebyshev preconditioner keeps 6 more values per row, rounded up separately)
-    const bool cheb = c.prm.pcg_precond == TTIE_PCG_CHEBYSHEV;
-    // (lean vectors beside a tile of the streamed product)
-    const int64_t smem_rows = (int64_t)kResidentSmem - (int64_t)stage_bytes<T>();
-    const int64_t r_cap = cheb ? (smem_rows - 4 - 15 - 15) / (21 * (int64_t)sizeof(T) + 4)
-                               : (smem_rows - 4 - 15) / (15 * (int64_t)sizeof(T) + 4);
+    // AUTO: the polynomial preconditioner when a block's share of the matrix rows (with a
+    // quarter to spare for the partition's imbalance) fits its shared memory beside the vectors
+    const int64_t blk_bytes = (int64_t)((double)c.nnzb * (9 * sizeof(T) + 4) * 1.25 / (double)blocks) +
+                              (nr + blocks - 1) / blocks * (27 + 6) * (int64_t)sizeof(T);
+    const bool cheb = c.prm.pcg_precond == TTIE_PCG_CHEBYSHEV ||
+                      (c.prm.pcg_precond == TTIE_PCG_AUTO && blk_bytes <= (int64_t)kResidentSmem);
+    const int64_t r_cap = cheb ? ((int64_t)kResidentSmem - 4 - 15 - 15) / (21 * (int64_t)sizeof(T) + 4)
+                               : ((int64_t)kResidentSmem - 4 - 15) / (15 * (int64_t)sizeof(T) + 4);
     const bool resident = (nr + blocks - 1) / blocks <= r_cap;
     if (cheb && resident) {
         // odd publications; zeros carry tag 0, which no odd publication has

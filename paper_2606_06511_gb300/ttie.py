@@ -26,8 +26,7 @@ STATUS_NAMES = ["OK", "INVALID", "CUDA", "OOM", "CAPACITY", "NONFINITE", "NOT_CO
 F32, F64 = 0, 1
 PAIRS_SELF, PAIRS_INTER_GROUP, PAIRS_INTRA_GROUP, PAIRS_BRUTE, PAIRS_HASH = 0, 1, 2, 4, 8
 PSD_PER_PART, PSD_DROP_CROSS, PSD_WHOLE = 0, 1, 2
-PCG_BLOCK_JACOBI, PCG_CHEBYSHEV = 0, 1
-ASSEMBLY_SORTED_KEYS, ASSEMBLY_ROW_BUCKETS = 0, 1
+PCG_BLOCK_JACOBI, PCG_CHEBYSHEV, PCG_AUTO = 0, 1, 2
 TRAVERSAL_TWO_WALKS, TRAVERSAL_ONE_WALK = 0, 1
 LS_ARMIJO, LS_FEWER = 0, 1
 EVAL_E, EVAL_G, EVAL_H = 1, 2, 4
@@ -47,7 +46,7 @@ class Params(ctypes.Structure):
                 ("armijo_c", ctypes.c_double), ("push_eta", ctypes.c_double), ("exact_only", ctypes.c_int),
                 ("profile", ctypes.c_int), ("max_step", ctypes.c_double), ("max_candidates", ctypes.c_int64),
                 ("inst_threads", ctypes.c_int), ("test_withhold", ctypes.c_int), ("pcg_precond", ctypes.c_int),
-                ("pcg_cheb_degree", ctypes.c_int), ("assembly_mode", ctypes.c_int), ("traversal_mode", ctypes.c_int),
+                ("pcg_cheb_degree", ctypes.c_int), ("traversal_mode", ctypes.c_int),
                 ("ls_rule", ctypes.c_int), ("push_eta_max", ctypes.c_double)]
 
 
@@ -112,7 +111,6 @@ _SIGS = {
                                        ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]),
     "ttie_get_direction": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "ttie_get_filter_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)]),
-    "ttie_get_eval_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64), ctypes.c_int]),
     "ttie_get_launch_count": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)]),
     "ttie_hvp": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     "ttie_dual_gradients": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
@@ -349,11 +347,6 @@ class Context:
         arr = (ctypes.c_int64 * 3)()
         self._chk(self.lib.ttie_get_filter_stats(self.h, arr))
         return {"fp32": arr[0], "fp64": arr[1], "exact": arr[2]}
-
-    def get_eval_stats(self):
-        arr = (ctypes.c_int64 * 5)()
-        self._chk(self.lib.ttie_get_eval_stats(self.h, arr, 5))
-        return {"fp32": arr[0], "fp64": arr[1], "exact": arr[2], "grad_fp64_pairs": arr[3], "active": arr[4]}
 
     def get_launch_count(self) -> int:
         n = ctypes.c_int64()

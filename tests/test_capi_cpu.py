@@ -56,8 +56,9 @@ def test_default_params(lib):
     assert p.tc_scale == 1.0 and p.mu_rel == 1e-3 and p.push_eta == 0.5 and p.exact_only == 0
     # the fields appended last come back from the library's defaults: the binding's layout matches
     assert p.max_step == 1.0 and p.max_candidates == 0 and p.inst_threads == 0 and p.test_withhold == 0
-    assert p.pcg_precond == ttie.PCG_BLOCK_JACOBI and p.pcg_cheb_degree == 0
-    assert p.assembly_mode == ttie.ASSEMBLY_SORTED_KEYS and p.traversal_mode == ttie.TRAVERSAL_TWO_WALKS
+    assert p.pcg_precond == ttie.PCG_AUTO and p.pcg_cheb_degree == 0
+    assert p.traversal_mode == ttie.TRAVERSAL_ONE_WALK
+    assert p.ls_rule == ttie.LS_ARMIJO and p.push_eta_max == 1.5
 
 
 def test_null_context_is_rejected(lib):
@@ -84,12 +85,14 @@ def test_bad_params_rejected_before_device(lib):
     assert lib.ttie_create(ctypes.byref(h), ctypes.byref(p), None) == ttie.TTIE_ERR_INVALID
     p = ttie.default_params(test_withhold=2)
     assert lib.ttie_create(ctypes.byref(h), ctypes.byref(p), None) == ttie.TTIE_ERR_INVALID
-    p = ttie.default_params(pcg_precond=2)
+    p = ttie.default_params(pcg_precond=3)
     assert lib.ttie_create(ctypes.byref(h), ctypes.byref(p), None) == ttie.TTIE_ERR_INVALID
     for deg in (-1, 9):
         p = ttie.default_params(pcg_precond=ttie.PCG_CHEBYSHEV, pcg_cheb_degree=deg)
         assert lib.ttie_create(ctypes.byref(h), ctypes.byref(p), None) == ttie.TTIE_ERR_INVALID
-    p = ttie.default_params(assembly_mode=2)
+    p = ttie.default_params(ls_rule=2)
+    assert lib.ttie_create(ctypes.byref(h), ctypes.byref(p), None) == ttie.TTIE_ERR_INVALID
+    p = ttie.default_params(push_eta_max=-1.0)
     assert lib.ttie_create(ctypes.byref(h), ctypes.byref(p), None) == ttie.TTIE_ERR_INVALID
     p = ttie.default_params(traversal_mode=2)
     assert lib.ttie_create(ctypes.byref(h), ctypes.byref(p), None) == ttie.TTIE_ERR_INVALID

@@ -176,6 +176,61 @@ def test_autograd_gradcheck_fp64(ttie):
     assert torch.autograd.gradgradcheck(f, (x,), eps=1e-6, atol=1e-5, rtol=1e-4, fast_mode=True)
 
 
+def _first_active_pairs_submesh(ttie, m, n_pairs):
+    """The triangles of the first n_pairs intersecting pairs by key (i, j) of mesh m, as a mesh of
+    their own (vertices renumbered), with the keys."""
+    x = torch.tensor(m.x, dtype=torch.float64, device="cuda")
+    tri = torch.tensor(m.tri, dtype=torch.int32, device="cuda")
+    ctx = ttie.Context(precision=ttie.F64)
+    ctx.build_bvh(x, tri)
+    ctx.eval_pairs(x, ttie.EVAL_E)
+    ap, _, _ = ctx.get_active(with_derivatives=False)
+    ap = ap.cpu().numpy().astype(np.int64)
+    ap = ap[np.lexsort((ap[:, 1], ap[:, 0]))][:n_pairs]
+    keep = np.unique(ap.ravel())
+    sub_tri = m.tri[keep]
+    used = np.unique(sub_tri)
+    remap = -np.ones(m.V, np.int64)
+    remap[used] = np.arange(len(used))
+    return ti.Mesh(m.x[used], remap[sub_tri].astype(np.int32), np.zeros(len(keep), np.int32)), ap
+
+
+def test_gradcheck_on_interlocked_tori_full_size(ttie):
+    """The tori workload at full size (2 x 65,536 triangles, tubes interpenetrating at offset 0.5,
+    jitter 0.005): the triangles of its first 1,000 intersecting pairs by key, in FP64, pass
+    gradcheck and gradgradcheck of the autograd energy (exact Hessian-vector products in the
+    double backward), and the exact Hessian-vector product matches central differences of the
+    library's gradient along a random direction."""
+    m = ti.interlocked_tori(offset=(0.5, 0, 0))
+    assert m.F == 2 * 65536
+    sub, keys = _first_active_pairs_submesh(ttie, m, 1000)
+    assert len(keys) == 1000
+    f = _energy_fn(ttie, sub, "self", ttie.F64)
+    x = torch.tensor(sub.x, dtype=torch.float64, device="cuda", requires_grad=True)
+    assert f(x).item() > 0 and f.last >= 1000
+    assert torch.autograd.gradcheck(f, (x,), eps=1e-7, atol=1e-7, rtol=1e-5, fast_mode=True)
+    assert torch.autograd.gradgradcheck(f, (x,), eps=1e-7, atol=1e-6, rtol=1e-4, fast_mode=True)
+    # exact HVP against central differences of the gradient (4th order), step 1e-6 of an edge
+    ctx = ttie.Context(precision=ttie.F64)
+    xd = x.detach()
+    tri = torch.tensor(sub.tri, dtype=torch.int32, device="cuda")
+    rng = np.random.default_rng(9)
+    v = torch.tensor(rng.normal(size=sub.x.shape), device="cuda")
+
+    def grad_at(xx):
+        ctx.build_bvh(xx, tri)
+        g = torch.zeros_like(xx)
+        ctx.eval_pairs(xx, ttie.EVAL_E | ttie.EVAL_G, grad=g)
+        return g
+    ctx.build_bvh(xd, tri)
+    ctx.eval_pairs(xd, ttie.EVAL_E | ttie.EVAL_H)
+    hv = ctx.hvp(xd, v, exact=True)
+    h = 2e-8
+    fd = (8 * (grad_at(xd + h * v) - grad_at(xd - h * v)) - (grad_at(xd + 2 * h * v) - grad_at(xd - 2 * h * v))) / (12 * h)
+    err = (hv - fd).abs().max().item() / hv.abs().max().item()
+    assert err <= 1e-4, err
+
+
 def test_adam_descends_on_linked_tori(ttie):
     """The energy as a loss for a first-order optimizer: Adam (lr 1e-3) on sum T over
     interpenetrating linked tori (2 x 8192 triangles) lowers the energy at least fourfold

@@ -126,9 +126,6 @@ def test_pair_values_meet_stated_tolerances(ttie, name, prec):
         return
     assert eg[mask].max() <= G_RTOL, (eg[mask].max(), ap[mask][np.argmax(eg[mask])])
     assert eH[mask].max() <= H_RTOL, (eH[mask].max(), ap[mask][np.argmax(eH[mask])])
-    if prec == "f32":
-        st = ctx.get_eval_stats()
-        assert st["active"] == n_act and 0 <= st["grad_fp64_pairs"] <= n_act
 
 
 @pytest.mark.parametrize("name", ["spheres_inter", "cloth40"])
@@ -194,7 +191,8 @@ def test_assembly_pattern_and_values(ttie, name, precision):
 
 
 @pytest.mark.parametrize("precision", [0, 1])
-def test_pcg_matches_direct_solve(ttie, precision):
+@pytest.mark.parametrize("precond", ["block_jacobi", "auto"])
+def test_pcg_matches_direct_solve(ttie, precision, precond):
     """The PCG's solution against a dense direct solve of the same system (the matrix the GPU
     assembled, read back in FP64): the true residual is at the requested level and the
     solution error is below a fixed bound (FP32 2e-3, FP64 1e-6).  The residual on the
@@ -203,7 +201,8 @@ def test_pcg_matches_direct_solve(ttie, precision):
     m, mode = CASES[name]
     dt = torch.float64 if precision else torch.float32
     x, tri, grp = _dev(m, dt)
-    ctx = _ctx(ttie, mode, precision=precision)
+    ctx = _ctx(ttie, mode, precision=precision,
+               pcg_precond={"block_jacobi": ttie.PCG_BLOCK_JACOBI, "auto": ttie.PCG_AUTO}[precond])
     ctx.build_bvh(x, tri, grp)
     ctx.eval_pairs(x, ttie.EVAL_E | ttie.EVAL_H)
     bsr = ctx.assemble()

@@ -1,13 +1,11 @@
-"""The alternative kernels of three stages against the default ones, on the same inputs.
+"""The alternative kernels of two stages against each other, on the same inputs.
 
-* One-walk LBVH traversal (TTIE_TRAVERSAL_ONE_WALK): the same candidate list in the same
-  order as the two-walk traversal, so every later result is identical.
-* Row-bucket assembly (TTIE_ASSEMBLY_ROW_BUCKETS): the same rows, pattern and bit-identical
-  values and gradient rows as the sorted-key assembly (each block is the same sum in the same
-  order), with and without an elastic term.
-* Chebyshev-preconditioned PCG (TTIE_PCG_CHEBYSHEV): the same bar as the block-Jacobi PCG
-  (residual at the requested level on the system it solved, fixed bound on the solution error
-  against a dense direct solve).
+* LBVH traversal: the one-walk traversal (the default) gives the same candidate list in the
+  same order as the two-walk traversal, so every later result is identical.
+* Chebyshev-preconditioned PCG (TTIE_PCG_CHEBYSHEV, what TTIE_PCG_AUTO picks for systems
+  whose matrix rows fit shared memory): the same bar as the block-Jacobi PCG (residual at the
+  requested level on the system it solved, fixed bound on the solution error against a dense
+  direct solve).
 """
 import numpy as np
 import pytest
@@ -65,57 +63,6 @@ def test_one_walk_traversal_newton_steps_identical(ttie):
     assert torch.equal(res[0][0], res[1][0])
 
 
-@pytest.mark.parametrize("name", ["cloth40", "tori", "soup", "snapped_grid", "spheres_inter", "ellipsoids_intra"])
-@pytest.mark.parametrize("precision", [0, 1])
-def test_row_bucket_assembly_bit_identical(ttie, name, precision):
-    m, mode = CASES[name]
-    dt = torch.float64 if precision else torch.float32
-    x, tri, grp = _dev(m, dt)
-    got = []
-    for am in (ttie.ASSEMBLY_SORTED_KEYS, ttie.ASSEMBLY_ROW_BUCKETS):
-        ctx = ttie.Context(precision=precision, pair_mode=MODE[mode], assembly_mode=am)
-        ctx.build_bvh(x, tri, grp)
-        g = torch.zeros((m.V, 3), dtype=dt, device="cuda")
-        ctx.eval_pairs(x, ttie.EVAL_E | ttie.EVAL_G | ttie.EVAL_H, grad=g)
-        b = ctx.assemble()
-        got.append([t.clone() for t in (b.row_ptr, b.col_idx, b.val, b.vertex_of_row, b.grad, g)])
-    for a, b in zip(*got):
-        assert torch.equal(a, b)
-
-
-def test_row_bucket_assembly_with_springs_identical_step(ttie):
-    """The quasi-static system (pairs + springs on every edge): the Newton direction of both
-    assemblies is bit-identical."""
-    m = ti.two_icospheres(offset=(1.95, 0.0, 0.0)).as_f32()
-    e = ti.edge_list(m.tri)
-    rest = np.linalg.norm(m.x[e[:, 0]] - m.x[e[:, 1]], axis=1)
-    x0, tri, grp = _dev(m)
-    dirs = []
-    for am in (ttie.ASSEMBLY_SORTED_KEYS, ttie.ASSEMBLY_ROW_BUCKETS):
-        x = x0.clone()
-        ctx = ttie.Context(pair_mode=1, assembly_mode=am)
-        ctx.build_bvh(x, tri, grp)
-        ctx.set_elastic(torch.tensor(e, device="cuda"), torch.tensor(rest, dtype=torch.float32, device="cuda"), 0.1)
-        info = ctx.newton_step(x)
-        assert info["n_active"] > 0
-        dirs.append((ctx.get_direction(), x))
-    assert torch.equal(dirs[0][0], dirs[1][0]) and torch.equal(dirs[0][1], dirs[1][1])
-
-
-def test_row_bucket_assembly_full_size(ttie):
-    m = ti.cloth(256, seed=2).as_f32()
-    x, tri, _ = _dev(m)
-    got = []
-    for am in (ttie.ASSEMBLY_SORTED_KEYS, ttie.ASSEMBLY_ROW_BUCKETS):
-        ctx = ttie.Context(assembly_mode=am)
-        ctx.build_bvh(x, tri)
-        ctx.eval_pairs(x, ttie.EVAL_E | ttie.EVAL_H)
-        b = ctx.assemble()
-        got.append([t.clone() for t in (b.row_ptr, b.col_idx, b.val, b.grad)])
-    for a, b in zip(*got):
-        assert torch.equal(a, b)
-
-
 def _dense(bsr):
     rp = bsr.row_ptr.cpu().numpy()
     ci = bsr.col_idx.cpu().numpy()
@@ -154,13 +101,13 @@ def test_chebyshev_pcg_matches_direct_solve(ttie, precision, degree):
 
 
 def test_chebyshev_pcg_reaches_newton_tolerance_full_size(ttie):
-    """The bench cloth's Newton system: the Chebyshev-preconditioned PCG reaches the Newton
-    step's relative tolerance (1e-3) within the iteration cap, in fewer iterations than block
-    Jacobi."""
+    """The crossing cloth's Newton system: the Chebyshev-preconditioned PCG (what AUTO picks
+    there) reaches the Newton step's relative tolerance (1e-3) within the iteration cap, in fewer
+    iterations than block Jacobi."""
     m = ti.cloth(256, seed=2).as_f32()
     x0, tri, _ = _dev(m)
     it = {}
-    for pc in (ttie.PCG_BLOCK_JACOBI, ttie.PCG_CHEBYSHEV):
+    for pc in (ttie.PCG_BLOCK_JACOBI, ttie.PCG_CHEBYSHEV, ttie.PCG_AUTO):
         x = x0.clone()
         ctx = ttie.Context(pcg_precond=pc)
         ctx.build_bvh(x, tri)
@@ -169,3 +116,4 @@ def test_chebyshev_pcg_reaches_newton_tolerance_full_size(ttie):
         assert np.isfinite(info["energy_new"]) and info["grad_dot_dir"] < 0
     assert it[ttie.PCG_CHEBYSHEV][1] <= 1e-3 and it[ttie.PCG_CHEBYSHEV][0] < 200, it
     assert it[ttie.PCG_CHEBYSHEV][0] < it[ttie.PCG_BLOCK_JACOBI][0], it
+    assert it[ttie.PCG_AUTO] == it[ttie.PCG_CHEBYSHEV], it

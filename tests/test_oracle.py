@@ -532,7 +532,7 @@ def test_line_search_rule():
 def test_adaptive_overshoot():
     """Rule "fewer": the overshoot doubles after a step that took it and left as many pairs, up
     to push_eta_max, and returns to push_eta when the count falls; other steps keep it."""
-    prm = O.NewtonParams(push_eta=0.5, push_eta_max=7.0)
+    prm = O.NewtonParams(push_eta=0.5, push_eta_max=7.0, ls_rule="fewer")
     assert O.next_overshoot(0.5, 1.5, 12, 12, prm) == 1.0
     assert O.next_overshoot(4.0, 5.0, 12, 13, prm) == 7.0
     assert O.next_overshoot(7.0, 8.0, 12, 12, prm) == 7.0

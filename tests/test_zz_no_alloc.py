@@ -15,18 +15,21 @@ import torch
 pytestmark = pytest.mark.gpu
 
 
-@pytest.fixture(scope="module")
-def lib():
-    import __graft_entry__
-    __graft_entry__.build()
-    from paper_2606_06511_gb300 import ttie
-    L = ttie.load()
+def _declare(L):
     f = L.ttie_pcg_static
     f.restype = ctypes.c_int
     f.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_double,
                   ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_void_p,
                   ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]
     return L
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2606_06511_gb300 import ttie
+    return _declare(ttie.load())
 
 
 def _system():
@@ -100,3 +103,32 @@ def test_static_pcg_rejects_oversize(lib):
     s, out, _, _ = _call(lib, bsr, 1e-6, rhs, 1e-5, 10, n_rows=16385)
     assert s == ttie.TTIE_ERR_INVALID
     assert torch.isnan(out).all()   # nothing was written
+
+
+def test_static_pcg_in_the_self_checking_build(lib):
+    """The self-checking build (bounds checks against the block count read from row_ptr[n_rows],
+    a synchronisation after each launch) of the entry point accepts a valid system: TTIE_OK,
+    finite output, the same answer as the allocating solver within the tolerance above.  The
+    checked library is a separate file loaded beside the normal one; the system comes from the
+    normal library."""
+    from paper_2606_06511_gb300 import ttie
+    from paper_2606_06511_gb300.build import build as build_lib
+    checked = _declare(ctypes.CDLL(build_lib(checked=True)))
+    ctx, bsr = _system()
+    n = bsr.vertex_of_row.numel()
+    rhs = (-bsr.grad).contiguous()
+    ref, _, _ = ctx.pcg(rhs, rtol=1e-4, max_it=2000)
+    rp = bsr.row_ptr.cpu().numpy()
+    ci = bsr.col_idx.cpu().numpy()
+    val = bsr.val.double().cpu().numpy()
+    rows = np.repeat(np.arange(n), np.diff(rp))
+    mu = ctx.params.mu_rel * np.trace(val[rows == ci], axis1=1, axis2=2).sum() / (3.0 * n)
+    b = rhs.double().cpu().numpy().reshape(-1, 3)
+    nb = np.linalg.norm(b)
+    for call in range(2):
+        s, out, it, rel = _call(checked, bsr, mu, rhs, 1e-4, 2000)
+        assert s == ttie.TTIE_OK, call
+        o = out.double().cpu().numpy()
+        assert np.isfinite(o).all() and rel <= 1e-4 and it > 0
+        assert np.linalg.norm(_bsr_matvec(rp, ci, val, mu, o) - b) <= 1e-2 * nb, call
+        assert np.linalg.norm(_bsr_matvec(rp, ci, val, mu, o - ref.double().cpu().numpy())) <= 2e-2 * nb, call
