@@ -114,7 +114,18 @@ typedef struct {
                              eta doubles for the next step, up to this (<= push_eta: no
                              growth); it returns to push_eta when a step lowers the count.
                              Not used by batched instances.                           */
+    int pcg_kernel;       /* TTIE_PCG_KERNEL_*: which kernels run the PCG                */
 } ttie_params;
+
+/* PCG kernels (same recurrence, same stopping test; results agree to rounding).
+ * AUTO:     RESIDENT when a solver block's share of the matrix rows fits its shared memory,
+ *           else STREAMED.
+ * RESIDENT: one cooperative launch, each block's rows (and, when they fit, matrix rows) held in
+ *           shared memory for the whole solve, blocks exchanging through tagged words.
+ * STREAMED: two kernels per iteration replayed from a CUDA graph, the matrix streamed from
+ *           global memory and u read through the read-only path; block Jacobi only (with
+ *           pcg_precond CHEBYSHEV the resident kernel runs).                                 */
+enum { TTIE_PCG_KERNEL_AUTO = 0, TTIE_PCG_KERNEL_RESIDENT = 1, TTIE_PCG_KERNEL_STREAMED = 2 };
 
 /* Line-search acceptance (the paper states no line search; these are readings of its inexact
  * Newton route).  E: energy, n: intersecting pairs, at x and at the trial x + a d.
@@ -157,7 +168,7 @@ typedef struct ttie_ctx ttie_ctx;
  * armijo_c 1e-4, push_eta 0.5, exact_only 0, profile 0, max_step 1,
  * max_candidates 0, inst_threads 0, test_withhold 0, pcg_precond AUTO,
  * pcg_cheb_degree 0, traversal_mode ONE_WALK, ls_rule ARMIJO,
- * push_eta_max 1.5. */
+ * push_eta_max 1.5, pcg_kernel AUTO. */
 void ttie_default_params(ttie_params *p);
 
 /* Creates a context on the current CUDA device.  stream: a cudaStream_t or NULL

@@ -117,7 +117,9 @@ static ttie_status check_params(Ctx &c, const ttie_params *p) {
         p->pcg_cheb_degree < 0 || p->pcg_cheb_degree > 8 ||
         (p->traversal_mode != TTIE_TRAVERSAL_TWO_WALKS && p->traversal_mode != TTIE_TRAVERSAL_ONE_WALK) ||
         (p->ls_rule != TTIE_LS_ARMIJO && p->ls_rule != TTIE_LS_FEWER) ||
-        !(p->push_eta_max >= 0.0) || p->push_eta_max > 1e3)
+        !(p->push_eta_max >= 0.0) || p->push_eta_max > 1e3 ||
+        (p->pcg_kernel != TTIE_PCG_KERNEL_AUTO && p->pcg_kernel != TTIE_PCG_KERNEL_RESIDENT &&
+         p->pcg_kernel != TTIE_PCG_KERNEL_STREAMED))
         return set_err(c, TTIE_ERR_INVALID, "numeric parameter out of range");
     return TTIE_OK;
 }
@@ -147,6 +149,7 @@ void ttie_default_params(ttie_params *p) {
     p->traversal_mode = TTIE_TRAVERSAL_ONE_WALK;
     p->ls_rule = TTIE_LS_ARMIJO;
     p->push_eta_max = 1.5;
+    p->pcg_kernel = TTIE_PCG_KERNEL_AUTO;
 }
 
 ttie_status ttie_create(ttie_ctx **out, const ttie_params *p, void *stream) {

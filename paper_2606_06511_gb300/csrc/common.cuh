@@ -102,6 +102,9 @@ struct DevScalars {
     unsigned long long pcg_products;       // Chebyshev-preconditioned PCG: products computed
     unsigned long long ovf_cursor;         // one-walk traversal: overflow chunks taken
     unsigned int inst_queue;               // batched PCG: next instance to take
+    double cg_alpha, cg_beta;              // streamed PCG: the step's coefficients (decided on the device)
+    double cg_gamma_prev, cg_alpha_prev;   //   the previous iteration's r.u and alpha
+    int cg_stop_next;                      //   breakdown at the first iteration: stop after its update
 };
 
 static_assert(offsetof(DevScalars, n_defer2) == offsetof(DevScalars, n_defer) + sizeof(unsigned long long),

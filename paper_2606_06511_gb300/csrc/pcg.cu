@@ -996,7 +996,208 @@ __global__ void __launch_bounds__(kPcgThreads) k_pcg_resident(PcgArgs<T> a, int 
     }
 }
 
+// ---------------------------------------------------------------- PCG, streamed
+// Systems whose matrix rows do not fit the solver blocks' shared memory (the matrix streams
+// from HBM every product anyway): Chronopoulos and Gear's recurrence as two kernels per
+// iteration, replayed from a CUDA graph.  k_cg_spmv forms w = (A + mu I) u with 8 lanes per
+// row and the read-only path for u (u does not change during that kernel, so its gathers can
+// hit L1 and the neighbouring rows' shared columns), sums delta = w.u, and its last block
+// decides the step from gamma = r.u, delta and r.r (the same decisions as the block-resident
+// kernel); k_cg_update updates p, s, x, r, u = M^-1 r and sums the next gamma and r.r.  All
+// sums are block partials added in block order by the last block, so the result does not
+// depend on timing.  A kernel of an iteration after the stop returns at once.
+constexpr int kCgThreads = 256;
+
+template <typename T>
+__device__ __forceinline__ void cg_decide(DevScalars *ds, double gamma, double delta, double rr, double rtol2,
+                                          int max_it) {
+    const int it = ds->pcg_iters;
+    if (it == 0) ds->red[1] = rr;
+    const double rr0 = ds->red[1];
+    bool stop = ds->cg_stop_next || it >= max_it || rr <= rtol2 * rr0 || !isfinite(rr);
+    double alpha = 0.0, beta = 0.0;
+    if (!stop) {
+        bool ok;
+        if (it == 0) {
+            alpha = gamma / delta;
+            ok = delta > 0.0 && isfinite(alpha);
+        } else {
+            beta = gamma / ds->cg_gamma_prev;
+            const double den = delta - beta * gamma / ds->cg_alpha_prev;
+            alpha = gamma / den;
+            ok = den > 0.0 && isfinite(alpha);
+        }
+        if (!ok) {
+            if (it > 0) stop = true;
+            alpha = 1.0;   // breakdown at the first step keeps x = M^-1 r0 (preconditioned gradient)
+            beta = 0.0;
+            ds->cg_stop_next = 1;
+        }
+    }
+    ds->cg_gamma_prev = gamma;
+    ds->cg_alpha_prev = alpha;
+    ds->cg_alpha = alpha;
+    ds->cg_beta = beta;
+    ds->red[0] = gamma;
+    ds->red[4] = rr;
+    if (stop) ds->pcg_done = 1;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kCgThreads) k_cg_spmv(const int32_t *__restrict__ row_ptr,
+                                                        const int32_t *__restrict__ col_idx,
+                                                        const T *__restrict__ bval, const T *__restrict__ u,
+                                                        T *__restrict__ w, double *partials, double rtol2, int max_it,
+                                                        DevScalars *ds) {
+    if (*(volatile int *)&ds->pcg_done) return;
+    const unsigned long long nr = ds->n_rows;
+    const T mu = (T)ds->mu;
+    const int lane = threadIdx.x & 31, sub = lane & (kLanesPerRow - 1);
+    const unsigned gmask = 0xffu << (lane & ~(kLanesPerRow - 1));
+    const unsigned long long group = (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x) / kLanesPerRow;
+    const unsigned long long n_groups = (unsigned long long)gridDim.x * blockDim.x / kLanesPerRow;
+    Acc<T> wu;
+    for (unsigned long long row = group; row < nr; row += n_groups) {
+        T y0 = 0, y1 = 0, y2 = 0;
+        const int be = row_ptr[row + 1];
+        for (int b = row_ptr[row] + sub; b < be; b += kLanesPerRow) {
+            if (TTIE_BAD(ds, b >= 0 && (unsigned long long)b < ds->nnzb, 51, b)) break;
+            const int c = __ldg(col_idx + b);
+            if (TTIE_BAD(ds, c >= 0 && (unsigned long long)c < nr, 52, c)) break;
+            const T *m = bval + (size_t)b * 9;
+            const T c0 = __ldg(u + 3 * (size_t)c), c1 = __ldg(u + 3 * (size_t)c + 1), c2 = __ldg(u + 3 * (size_t)c + 2);
+            y0 += m[0] * c0 + m[1] * c1 + m[2] * c2;
+            y1 += m[3] * c0 + m[4] * c1 + m[5] * c2;
+            y2 += m[6] * c0 + m[7] * c1 + m[8] * c2;
+        }
+#pragma unroll
+        for (int o = kLanesPerRow / 2; o; o >>= 1) {
+            y0 += __shfl_xor_sync(gmask, y0, o, kLanesPerRow);
+            y1 += __shfl_xor_sync(gmask, y1, o, kLanesPerRow);
+            y2 += __shfl_xor_sync(gmask, y2, o, kLanesPerRow);
+        }
+        if (sub == 0) {
+            const T u0 = u[row * 3], u1 = u[row * 3 + 1], u2 = u[row * 3 + 2];
+            const T w0 = y0 + mu * u0, w1 = y1 + mu * u1, w2 = y2 + mu * u2;
+            w[row * 3] = w0; w[row * 3 + 1] = w1; w[row * 3 + 2] = w2;
+            wu.add_prod(w0, u0);
+            wu.add_prod(w1, u1);
+            wu.add_prod(w2, u2);
+        }
+    }
+    double v[1] = {wu.value()};
+    grid_sums<1>(v, partials, &ds->done_counter[3], [&](const double *t) {
+        cg_decide<T>(ds, ds->red[0], t[0], ds->red[4], rtol2, max_it);
+    });
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kCgThreads) k_cg_update(const T *__restrict__ dinv, T *__restrict__ x,
+                                                          T *__restrict__ r, T *__restrict__ u, T *__restrict__ p,
+                                                          T *__restrict__ s, const T *__restrict__ w,
+                                                          double *partials, DevScalars *ds) {
+    if (*(volatile int *)&ds->pcg_done) return;
+    const unsigned long long nr = ds->n_rows;
+    const T al = (T)ds->cg_alpha, be = (T)ds->cg_beta;
+    Acc<T> g, q;
+    for (unsigned long long row = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; row < nr;
+         row += (unsigned long long)gridDim.x * blockDim.x) {
+        T rv[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            const size_t k = row * 3 + i;
+            const T pi = u[k] + be * p[k];
+            const T si = w[k] + be * s[k];
+            p[k] = pi;
+            s[k] = si;
+            x[k] += al * pi;
+            rv[i] = r[k] - al * si;
+            r[k] = rv[i];
+        }
+        const T *di = dinv + row * 9;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            const T zi = di[3 * i] * rv[0] + di[3 * i + 1] * rv[1] + di[3 * i + 2] * rv[2];
+            u[row * 3 + i] = zi;
+            g.add_prod(rv[i], zi);
+            q.add_prod(rv[i], rv[i]);
+        }
+    }
+    double v[2] = {g.value(), q.value()};
+    grid_sums<2>(v, partials, &ds->done_counter[4], [&](const double *t) {
+        ds->red[0] = t[0];
+        ds->red[4] = t[1];
+        ds->pcg_iters += 1;
+    });
+}
+
 }  // namespace
+
+// The streamed PCG (kernels above): setup, then iterations of (k_cg_spmv, k_cg_update) from a
+// graph of kCgGraphIters iterations captured once per call and replayed until max_it is
+// covered; iterations after the stop return at once, so nothing is read back in between.
+constexpr int kCgGraphIters = 10;
+
+template <typename T>
+cudaError_t pcg_streamed(Ctx &c, const T *rhs, T *out, double rtol, int max_it) {
+    const int64_t nr = c.n_rows;
+    TTIE_CUDA_TRY(ensure(c, c.pcg_w, (size_t)(nr > 0 ? nr : 1) * 3 * sizeof(T)));
+    const int sms = c.num_sms > 0 ? c.num_sms : kNumSMs;
+    const unsigned gs = grid_for(nr * kLanesPerRow, kCgThreads, (int64_t)sms * 8);
+    const unsigned gu = grid_for(nr, kCgThreads, (int64_t)sms * 8);
+    TTIE_CUDA_TRY(ensure(c, c.partials, (size_t)kNumSMs * 16 * 4 * sizeof(double)));
+    double *part = (double *)c.partials.p;
+    // tickets of the two kernels' grid sums, the decision state and the iteration count
+    TTIE_CUDA_TRY(cudaMemsetAsync(&c.ds->done_counter[3], 0, 2 * sizeof(unsigned int), c.stream));
+    TTIE_CUDA_TRY(cudaMemsetAsync(&c.ds->cg_stop_next, 0, sizeof(int), c.stream));
+    TTIE_CUDA_TRY(cudaMemsetAsync(c.pcg_q.p, 0, (size_t)(nr > 0 ? nr : 1) * 3 * sizeof(T), c.stream));   // s
+    const unsigned g = grid_for(nr, kThreads, kNumSMs * 4);
+    launch(c, k_pcg_setup<T>, dim3(g), dim3(kThreads), (const int32_t *)c.row_ptr.p, (const int32_t *)c.col_idx.p,
+           (const T *)c.bsr_val.p, c.prm.mu_rel, (T *)c.dinv.p, rhs, out, (T *)c.pcg_r.p, (T *)c.pcg_z.p,
+           (T *)c.pcg_p.p, part, (vec4_t<T> *)nullptr, (unsigned long long *)nullptr, 0, (int *)nullptr, 0, 0, 0,
+           c.ds);
+    TTIE_CUDA_TRY(cudaGetLastError());
+    if (c.prm.profile) cudaEventRecord(c.ev[8], c.stream);
+    const double rtol2 = rtol * rtol;
+    const auto one_iteration = [&](cudaStream_t st) {
+        ++c.n_launch;
+        k_cg_spmv<T><<<gs, kCgThreads, 0, st>>>((const int32_t *)c.row_ptr.p, (const int32_t *)c.col_idx.p,
+                                               (const T *)c.bsr_val.p, (const T *)c.pcg_z.p, (T *)c.pcg_w.p, part,
+                                               rtol2, max_it, c.ds);
+        ++c.n_launch;
+        k_cg_update<T><<<gu, kCgThreads, 0, st>>>((const T *)c.dinv.p, out, (T *)c.pcg_r.p, (T *)c.pcg_z.p,
+                                                 (T *)c.pcg_p.p, (T *)c.pcg_q.p, (const T *)c.pcg_w.p,
+                                                 part + 2 * (size_t)kNumSMs * 16, c.ds);
+    };
+    // max_it + 1 products: the last decides the stop at max_it
+    const int iters = max_it + 1;
+#ifndef TTIE_CHECKS
+    if (!c.cap_stream) TTIE_CUDA_TRY(cudaStreamCreateWithFlags(&c.cap_stream, cudaStreamNonBlocking));
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    TTIE_CUDA_TRY(cudaStreamBeginCapture(c.cap_stream, cudaStreamCaptureModeThreadLocal));
+    const unsigned long long n0 = c.n_launch;
+    for (int i = 0; i < kCgGraphIters; ++i) one_iteration(c.cap_stream);
+    const unsigned long long per_graph = c.n_launch - n0;
+    c.n_launch = n0;
+    cudaError_t e = cudaGetLastError();
+    const cudaError_t ec = cudaStreamEndCapture(c.cap_stream, &graph);
+    if (e == cudaSuccess) e = ec;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    for (int done = 0; e == cudaSuccess && done < iters; done += kCgGraphIters) {
+        e = cudaGraphLaunch(exec, c.stream);
+        c.n_launch += per_graph;
+    }
+    if (exec) cudaGraphExecDestroy(exec);
+    TTIE_CUDA_TRY(e);
+#else
+    for (int i = 0; i < iters; ++i) one_iteration(c.stream);
+#endif
+    if (c.prm.profile) cudaEventRecord(c.ev[9], c.stream);
+    c.pcg_cheb = false;
+    return cudaGetLastError();
+}
 
 template <typename T>
 cudaError_t pcg_solve(Ctx &c, const T *rhs, T *out, double rtol, int max_it) {
@@ -1029,6 +1230,12 @@ cudaError_t pcg_solve(Ctx &c, const T *rhs, T *out, double rtol, int max_it) {
     const int64_t r_cap = cheb ? ((int64_t)kResidentSmem - 4 - 15 - 15) / (21 * (int64_t)sizeof(T) + 4)
                                : ((int64_t)kResidentSmem - 4 - 15) / (15 * (int64_t)sizeof(T) + 4);
     const bool resident = (nr + blocks - 1) / blocks <= r_cap;
+    // systems whose matrix rows do not fit the blocks' shared memory: the streamed kernels
+    // (the block-resident kernel would read them from global memory on every product too)
+    const bool streamed = !cheb && c.prm.test_withhold == 0 &&
+                          (c.prm.pcg_kernel == TTIE_PCG_KERNEL_STREAMED ||
+                           (c.prm.pcg_kernel == TTIE_PCG_KERNEL_AUTO && blk_bytes > (int64_t)kResidentSmem));
+    if (streamed) return pcg_streamed<T>(c, rhs, out, rtol, max_it);
     if (cheb && resident) {
         // odd publications; zeros carry tag 0, which no odd publication has
         TTIE_CUDA_TRY(ensure(c, c.pcg_z4b, (size_t)(nr > 0 ? nr : 1) * sizeof(vec4_t<T>)));

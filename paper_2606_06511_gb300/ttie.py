@@ -29,6 +29,7 @@ PSD_PER_PART, PSD_DROP_CROSS, PSD_WHOLE = 0, 1, 2
 PCG_BLOCK_JACOBI, PCG_CHEBYSHEV, PCG_AUTO = 0, 1, 2
 TRAVERSAL_TWO_WALKS, TRAVERSAL_ONE_WALK = 0, 1
 LS_ARMIJO, LS_FEWER = 0, 1
+PCG_KERNEL_AUTO, PCG_KERNEL_RESIDENT, PCG_KERNEL_STREAMED = 0, 1, 2
 EVAL_E, EVAL_G, EVAL_H = 1, 2, 4
 
 
@@ -47,7 +48,7 @@ class Params(ctypes.Structure):
                 ("profile", ctypes.c_int), ("max_step", ctypes.c_double), ("max_candidates", ctypes.c_int64),
                 ("inst_threads", ctypes.c_int), ("test_withhold", ctypes.c_int), ("pcg_precond", ctypes.c_int),
                 ("pcg_cheb_degree", ctypes.c_int), ("traversal_mode", ctypes.c_int),
-                ("ls_rule", ctypes.c_int), ("push_eta_max", ctypes.c_double)]
+                ("ls_rule", ctypes.c_int), ("push_eta_max", ctypes.c_double), ("pcg_kernel", ctypes.c_int)]
 
 
 class BsrView(ctypes.Structure):

@@ -58,7 +58,7 @@ def test_default_params(lib):
     assert p.max_step == 1.0 and p.max_candidates == 0 and p.inst_threads == 0 and p.test_withhold == 0
     assert p.pcg_precond == ttie.PCG_AUTO and p.pcg_cheb_degree == 0
     assert p.traversal_mode == ttie.TRAVERSAL_ONE_WALK
-    assert p.ls_rule == ttie.LS_ARMIJO and p.push_eta_max == 1.5
+    assert p.ls_rule == ttie.LS_ARMIJO and p.push_eta_max == 1.5 and p.pcg_kernel == ttie.PCG_KERNEL_AUTO
 
 
 def test_null_context_is_rejected(lib):
@@ -93,6 +93,8 @@ def test_bad_params_rejected_before_device(lib):
     p = ttie.default_params(ls_rule=2)
     assert lib.ttie_create(ctypes.byref(h), ctypes.byref(p), None) == ttie.TTIE_ERR_INVALID
     p = ttie.default_params(push_eta_max=-1.0)
+    assert lib.ttie_create(ctypes.byref(h), ctypes.byref(p), None) == ttie.TTIE_ERR_INVALID
+    p = ttie.default_params(pcg_kernel=3)
     assert lib.ttie_create(ctypes.byref(h), ctypes.byref(p), None) == ttie.TTIE_ERR_INVALID
     p = ttie.default_params(traversal_mode=2)
     assert lib.ttie_create(ctypes.byref(h), ctypes.byref(p), None) == ttie.TTIE_ERR_INVALID

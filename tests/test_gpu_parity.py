@@ -191,7 +191,7 @@ def test_assembly_pattern_and_values(ttie, name, precision):
 
 
 @pytest.mark.parametrize("precision", [0, 1])
-@pytest.mark.parametrize("precond", ["block_jacobi", "auto"])
+@pytest.mark.parametrize("precond", ["block_jacobi", "auto", "streamed"])
 def test_pcg_matches_direct_solve(ttie, precision, precond):
     """The PCG's solution against a dense direct solve of the same system (the matrix the GPU
     assembled, read back in FP64): the true residual is at the requested level and the
@@ -202,7 +202,9 @@ def test_pcg_matches_direct_solve(ttie, precision, precond):
     dt = torch.float64 if precision else torch.float32
     x, tri, grp = _dev(m, dt)
     ctx = _ctx(ttie, mode, precision=precision,
-               pcg_precond={"block_jacobi": ttie.PCG_BLOCK_JACOBI, "auto": ttie.PCG_AUTO}[precond])
+               pcg_precond={"block_jacobi": ttie.PCG_BLOCK_JACOBI, "auto": ttie.PCG_AUTO,
+                            "streamed": ttie.PCG_BLOCK_JACOBI}[precond],
+               pcg_kernel=ttie.PCG_KERNEL_STREAMED if precond == "streamed" else ttie.PCG_KERNEL_RESIDENT)
     ctx.build_bvh(x, tri, grp)
     ctx.eval_pairs(x, ttie.EVAL_E | ttie.EVAL_H)
     bsr = ctx.assemble()
