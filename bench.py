@@ -275,6 +275,8 @@ def main():
     ap.add_argument("--pcg-cheb-degree", type=int, default=0, help="Chebyshev degree (0: the library's default)")
     ap.add_argument("--traversal", choices=["one_walk", "two_walks"], default="one_walk",
                     help="LBVH traversal")
+    ap.add_argument("--pcg-kernel", choices=["auto", "resident", "streamed"], default="auto",
+                    help="PCG kernel: block-resident (one launch) or streamed (two kernels per iteration)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -300,7 +302,9 @@ def main():
                               "chebyshev": ttie.PCG_CHEBYSHEV}[args.pcg_precond],
               "pcg_cheb_degree": args.pcg_cheb_degree,
               "traversal_mode": {"two_walks": ttie.TRAVERSAL_TWO_WALKS,
-                                 "one_walk": ttie.TRAVERSAL_ONE_WALK}[args.traversal]}
+                                 "one_walk": ttie.TRAVERSAL_ONE_WALK}[args.traversal],
+              "pcg_kernel": {"auto": ttie.PCG_KERNEL_AUTO, "resident": ttie.PCG_KERNEL_RESIDENT,
+                             "streamed": ttie.PCG_KERNEL_STREAMED}[args.pcg_kernel]}
     stream = torch.cuda.current_stream()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -354,6 +358,14 @@ def main():
             return None
         return O.certify(x.double().cpu().numpy(), m.tri, m.group, ("self", "inter", "instance")[mode])
 
+    def c_active_tris(c, x, tri, grp):
+        """First triangles of the intersecting pairs of the last evaluation (x given: evaluate at x)."""
+        if x is not None:
+            c.build_bvh(x, tri, grp)
+            c.eval_pairs(x, ttie.EVAL_E)
+        ap, _, _ = c.get_active(with_derivatives=False)
+        return ap[:, 0].long().cpu().numpy()
+
     def solve_outcome(m, precision, mode, brute, max_it=100):
         """Seconds to intersection-free (ttie_solve's wall time, after one solve that allocates the
         context's buffers), with the end state certified by the oracle where its brute force fits."""
@@ -367,12 +379,21 @@ def main():
             torch.cuda.synchronize()
             s = c.solve(xs)
             cert = certify(m, xs, mode) if s["converged"] else None
-            return {"dtype": "f32" if precision == 0 else "f64", "converged": bool(s["converged"]),
-                    "iterations": s["iterations"], "seconds": s["seconds"],
-                    "n_active_initial": s["n_active_initial"], "n_active_final": s["n_active_final"],
-                    "energy_initial": s["energy_initial"], "energy_final": s["energy_final"],
-                    "newton_max_it": max_it,
-                    "oracle_certified_intersecting": cert}
+            out = {"dtype": "f32" if precision == 0 else "f64", "converged": bool(s["converged"]),
+                   "iterations": s["iterations"], "seconds": s["seconds"],
+                   "n_active_initial": s["n_active_initial"], "n_active_final": s["n_active_final"],
+                   "energy_initial": s["energy_initial"], "energy_final": s["energy_final"],
+                   "newton_max_it": max_it,
+                   "oracle_certified_intersecting": cert}
+            if mode == 2:   # independent instances: how many end without an intersecting pair
+                n_inst = int(m.group.max()) + 1
+                open0 = np.unique(m.group[c_active_tris(c, x0, tri, grp)])
+                c.build_bvh(xs, tri, grp)
+                c.eval_pairs(xs, ttie.EVAL_E)
+                open1 = np.unique(m.group[c_active_tris(c, None, None, None)])
+                out.update({"instances": n_inst, "instances_intersecting_initial": int(len(open0)),
+                            "instances_intersecting_final": int(len(open1))})
+            return out
         except ttie.TTIEError as e:   # reported, the line still prints
             return {"dtype": "f32" if precision == 0 else "f64", "error": str(e)[:200]}
         finally:
@@ -427,7 +448,9 @@ def main():
     e2e_bytes = x0.numel() * x0.element_size()
 
     r_pcg, r_cls, r_asm, r_ev = rooflines(last, main_t["kernel_ms"], peak, hbm)
-    r_pcg["kernel"] = "k_pcg_instances" if mode == 2 else "k_pcg_resident"
+    r_pcg["kernel"] = ("k_pcg_instances" if mode == 2 else
+                       "k_cg_spmv + k_cg_update" if last.get("pcg_kernel") == ttie.PCG_KERNEL_STREAMED else
+                       "k_pcg_resident")
     r_pcg["traffic"] = NCU_TRAFFIC.get((args.workload, "pcg"))
     r_cls["traffic"] = NCU_TRAFFIC.get((args.workload, "classify"))
     r_pcg["share_of_step"] = r_pcg["ms"] / (total_ms / args.steps)
@@ -472,8 +495,9 @@ def main():
                 cc.close()
                 lc = t["last"]
                 rp, rc, ra, re = rooflines(lc, t["kernel_ms"], peak, hbm)
-                if mdc == 2:
-                    rp["kernel"] = "k_pcg_instances"
+                rp["kernel"] = ("k_pcg_instances" if mdc == 2 else
+                                "k_cg_spmv + k_cg_update" if lc.get("pcg_kernel") == ttie.PCG_KERNEL_STREAMED else
+                                "k_pcg_resident")
                 entry.update({
                     "dtype": "f32" if pc == 0 else "f64", "steps": ks, "ms_per_step": t["total_ms"] / ks,
                     "value": t["pairs"] / (t["total_ms"] / 1e3), "unit": UNIT,
@@ -631,7 +655,7 @@ def main():
                        "line_search_trials": last["ls_trials"], "pcg_iters": last["pcg_iters"],
                        "bsr_rows": last["n_rows"], "bsr_blocks": last["nnzb"],
                        "l2": "flushed (256 MiB write) before every timed step",
-                       "pcg_precond": args.pcg_precond, "traversal": args.traversal,
+                       "pcg_precond": args.pcg_precond, "pcg_kernel": args.pcg_kernel, "traversal": args.traversal,
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "stage_ms_per_step": main_t["stage_ms_per_step"],
             "active_pairs_per_s": main_t["active"] / (total_ms / 1e3),

@@ -118,8 +118,9 @@ typedef struct {
 } ttie_params;
 
 /* PCG kernels (same recurrence, same stopping test; results agree to rounding).
- * AUTO:     RESIDENT when a solver block's share of the matrix rows fits its shared memory,
- *           else STREAMED.
+ * AUTO:     RESIDENT when every solver block's rows fit its shared memory (with the matrix
+ *           rows too when they fit, else in the lean layout that reads them from global
+ *           memory), else STREAMED.
  * RESIDENT: one cooperative launch, each block's rows (and, when they fit, matrix rows) held in
  *           shared memory for the whole solve, blocks exchanging through tagged words.
  * STREAMED: two kernels per iteration replayed from a CUDA graph, the matrix streamed from
@@ -299,6 +300,9 @@ typedef struct {
                                     preconditioner after its restart)                      */
     int64_t pcg_row_iters;       /* sum over the PCG's products of the rows updated           */
     double energy_elastic;       /* elastic term's part of energy (0 without one)             */
+    int pcg_kernel;              /* the PCG kernels that ran: TTIE_PCG_KERNEL_RESIDENT or
+                                    TTIE_PCG_KERNEL_STREAMED; 0 when no PCG ran or with batched
+                                    instances (their own solver)                              */
 } ttie_step_info;
 
 /*

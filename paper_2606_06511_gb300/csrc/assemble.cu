@@ -87,47 +87,66 @@ __device__ __forceinline__ void whole_projection(T a, T b, T uu, T uv, T vv, T &
     }
 }
 
-// PSD factors z1, z2, z3 and the gradient of each intersecting pair; trace of H+.
+// PSD factors z1, z2, z3 and the gradient of each intersecting pair; trace of H+.  A block of
+// fac_threads threads handles as many pairs: their rows of t_c values and gradients are read
+// into shared memory and their factor rows written out of it, each by the whole block in
+// consecutive words (a thread's own row is kFacStride or kZStride values long, so direct
+// per-thread row accesses would touch a separate sector per thread and word).
+// (32 pairs per block for FP64 rows, so the staging stays at 29 KB of static shared memory)
+template <typename T> __host__ __device__ constexpr int fac_threads() { return sizeof(T) == 4 ? 64 : 32; }
+
 template <typename T>
-__global__ void k_factors(const T *__restrict__ fac, int psd_mode, T *__restrict__ z, double *partials, DevScalars *ds) {
+__global__ void __launch_bounds__(fac_threads<T>()) k_factors(const T *__restrict__ fac, int psd_mode, T *__restrict__ z,
+                                                              double *partials, DevScalars *ds) {
+    constexpr int kFacThreads = fac_threads<T>();
+    __shared__ T s_in[kFacThreads * kFacStride];
+    __shared__ T s_out[kFacThreads * kZStride];
     const unsigned long long n = ds->n_active;
     double tr = 0.0;
-    for (unsigned long long k = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; k < n;
-         k += (unsigned long long)gridDim.x * blockDim.x) {
-        const T *r = fac + k * kFacStride;
-        const T a = r[0], b = r[1];
-        T uu = 0, vv = 0, uv = 0;
+    for (unsigned long long k0 = (unsigned long long)blockIdx.x * kFacThreads; k0 < n;
+         k0 += (unsigned long long)gridDim.x * kFacThreads) {
+        const int rows = (int)min((unsigned long long)kFacThreads, n - k0);
+        for (int i = threadIdx.x; i < rows * kFacStride; i += kFacThreads) s_in[i] = fac[k0 * kFacStride + i];
+        __syncthreads();
+        if (threadIdx.x < rows) {
+            const T *r = s_in + threadIdx.x * kFacStride;
+            const T a = r[0], b = r[1];
+            T uu = 0, vv = 0, uv = 0;
 #pragma unroll
-        for (int i = 0; i < 18; ++i) {
-            uu += r[2 + i] * r[2 + i];
-            vv += r[20 + i] * r[20 + i];
-            uv += r[2 + i] * r[20 + i];
-        }
-        const T nu = sqrt(uu), nv = sqrt(vv);
-        T c1 = sqrt(T(2)) * fabs(b), c2 = sqrt(T(2)) * fabs(a);
-        T c3 = T(0), iu = T(0), iv = T(0), wa = T(0), wb = T(0);
-        if (psd_mode == TTIE_PSD_PER_PART && nu > T(0) && nv > T(0)) {
-            c3 = sqrt(T(2) * fabs(a * b) * nu * nv);
-            iu = T(1) / nu;
-            iv = T(1) / nv;
-        } else if (psd_mode == TTIE_PSD_WHOLE) {
-            whole_projection(a, b, uu, uv, vv, wa, wb);
-            c1 = c2 = T(0);
-        }
-        T *o = z + k * kZStride;
-        double t = 0.0;
+            for (int i = 0; i < 18; ++i) {
+                uu += r[2 + i] * r[2 + i];
+                vv += r[20 + i] * r[20 + i];
+                uv += r[2 + i] * r[20 + i];
+            }
+            const T nu = sqrt(uu), nv = sqrt(vv);
+            T c1 = sqrt(T(2)) * fabs(b), c2 = sqrt(T(2)) * fabs(a);
+            T c3 = T(0), iu = T(0), iv = T(0), wa = T(0), wb = T(0);
+            if (psd_mode == TTIE_PSD_PER_PART && nu > T(0) && nv > T(0)) {
+                c3 = sqrt(T(2) * fabs(a * b) * nu * nv);
+                iu = T(1) / nu;
+                iv = T(1) / nv;
+            } else if (psd_mode == TTIE_PSD_WHOLE) {
+                whole_projection(a, b, uu, uv, vv, wa, wb);
+                c1 = c2 = T(0);
+            }
+            T *o = s_out + threadIdx.x * kZStride;
+            double t = 0.0;
 #pragma unroll
-        for (int i = 0; i < 18; ++i) {
-            const T u = r[2 + i], v = r[20 + i];
-            const T z1 = c1 * u + (wa * u + wb * v), z2 = c2 * v, z3 = c3 * (u * iu - v * iv);
-            T *ov = o + (i / 3) * kZVertex + i % 3;
-            ov[0] = z1;
-            ov[3] = z2;
-            ov[6] = z3;
-            ov[9] = T(2) * a * b * (b * u + a * v);
-            t += (double)z1 * z1 + (double)z2 * z2 + (double)z3 * z3;
+            for (int i = 0; i < 18; ++i) {
+                const T u = r[2 + i], v = r[20 + i];
+                const T z1 = c1 * u + (wa * u + wb * v), z2 = c2 * v, z3 = c3 * (u * iu - v * iv);
+                T *ov = o + (i / 3) * kZVertex + i % 3;
+                ov[0] = z1;
+                ov[3] = z2;
+                ov[6] = z3;
+                ov[9] = T(2) * a * b * (b * u + a * v);
+                t += (double)z1 * z1 + (double)z2 * z2 + (double)z3 * z3;
+            }
+            tr += t;
         }
-        tr += t;
+        __syncthreads();
+        for (int i = threadIdx.x; i < rows * kZStride; i += kFacThreads) z[k0 * kZStride + i] = s_out[i];
+        __syncthreads();
     }
     double v[1] = {tr};
     grid_sums<1>(v, partials, &ds->done_counter[1], [&](const double *tot) { ds->trace = tot[0]; });
@@ -303,10 +322,33 @@ __global__ void k_run_starts(const uint32_t *__restrict__ flag, const unsigned l
 // the three PSD factors t, and on the diagonal the gradient rows of r.  Spring entry q (0: (i, i),
 // 1: (i, j), 2: (j, i), 3: (j, j)): +-K+, and on the diagonal +-the gradient on i.  Anchor: k_a I
 // and its gradient.
+// The 12 values of one vertex's factors, [z1 (3), z2 (3), z3 (3), g (3)], 16-byte aligned (a
+// pair's row is 72 values): three 16-byte loads for FP32, six for FP64.
+template <typename T> __device__ __forceinline__ void load_vertex_factors(const T *__restrict__ p, T (&o)[12]);
+template <> __device__ __forceinline__ void load_vertex_factors<float>(const float *__restrict__ p, float (&o)[12]) {
+    const float4 *q = reinterpret_cast<const float4 *>(p);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const float4 v = __ldg(q + i);
+        o[4 * i] = v.x; o[4 * i + 1] = v.y; o[4 * i + 2] = v.z; o[4 * i + 3] = v.w;
+    }
+}
+template <> __device__ __forceinline__ void load_vertex_factors<double>(const double *__restrict__ p, double (&o)[12]) {
+    const double2 *q = reinterpret_cast<const double2 *>(p);
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        const double2 v = __ldg(q + i);
+        o[2 * i] = v.x; o[2 * i + 1] = v.y;
+    }
+}
+static_assert(kZStride % 4 == 0 && kZVertex % 4 == 0, "factor rows and vertices start on 16 bytes");
+
 template <typename T>
 __device__ __forceinline__ void add_pair_entry(const T *__restrict__ z, uint32_t pk, uint32_t r, uint32_t c, bool diag,
                                                T (&m)[9], T &g0, T &g1, T &g2) {
-    const T *zr = z + (size_t)pk * kZStride + r * kZVertex, *zc = z + (size_t)pk * kZStride + c * kZVertex;
+    T zr[12], zc[12];
+    load_vertex_factors<T>(z + (size_t)pk * kZStride + r * kZVertex, zr);
+    load_vertex_factors<T>(z + (size_t)pk * kZStride + c * kZVertex, zc);
 #pragma unroll
     for (int t = 0; t < 3; ++t) {
         const T x0 = zr[3 * t], x1 = zr[3 * t + 1], x2 = zr[3 * t + 2];
@@ -531,8 +573,8 @@ cudaError_t assemble_system(Ctx &c, T *grad_full, bool with_elastic) {
                                                                   (int32_t *)c.row_vertex.p, c.ds);
     TTIE_CUDA_TRY(ensure(c, c.zfac, (size_t)(n_act > 0 ? n_act : 1) * kZStride * sizeof(T)));
     TTIE_CUDA_TRY(ensure(c, c.partials, (size_t)kNumSMs * 16 * 4 * sizeof(double)));
-    launch(c, k_factors<T>, dim3(grid_for(n_act, 128, kNumSMs * 8)), dim3(128), (const T *)c.fac.p, c.prm.psd_mode,
-           (T *)c.zfac.p, (double *)c.partials.p, c.ds);
+    launch(c, k_factors<T>, dim3(grid_for(n_act, fac_threads<T>(), kNumSMs * 16)), dim3(fac_threads<T>()),
+           (const T *)c.fac.p, c.prm.psd_mode, (T *)c.zfac.p, (double *)c.partials.p, c.ds);
     if (el) {   // after k_factors: adds the term's trace to the pairs'
         TTIE_CUDA_TRY(ensure(c, c.el_sfac, (size_t)(n_springs > 0 ? n_springs : 1) * kElStride * sizeof(T)));
         TTIE_CUDA_TRY(ensure(c, c.el_afac, (size_t)(n_anchors > 0 ? n_anchors : 1) * 3 * sizeof(T)));

@@ -460,6 +460,7 @@ static ttie_status newton_impl(Ctx &c, T *x, ttie_step_info *info) {
     inf.pcg_rel_residual = c.hs->red[1] > 0.0 ? std::sqrt(c.hs->red[4] / c.hs->red[1]) : 0.0;
     // the Chebyshev-preconditioned kernel multiplies k + 1 times per iteration after its restart
     const int64_t passes = c.pcg_cheb ? (int64_t)c.hs->pcg_products : (int64_t)inf.pcg_iters;
+    inf.pcg_kernel = c.pcg_streamed ? TTIE_PCG_KERNEL_STREAMED : TTIE_PCG_KERNEL_RESIDENT;
     inf.pcg_block_iters = passes * c.nnzb;
     inf.pcg_row_iters = passes * c.n_rows;
     mark(c, 4);

@@ -66,7 +66,7 @@ class StepInfo(ctypes.Structure):
                 ("ms_assemble", ctypes.c_float), ("ms_pcg", ctypes.c_float), ("ms_line_search", ctypes.c_float),
                 ("ms_classify", ctypes.c_float), ("ms_pcg_kernel", ctypes.c_float),
                 ("pcg_block_iters", ctypes.c_int64), ("pcg_row_iters", ctypes.c_int64),
-                ("energy_elastic", ctypes.c_double)]
+                ("energy_elastic", ctypes.c_double), ("pcg_kernel", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

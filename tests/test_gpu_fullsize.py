@@ -105,11 +105,11 @@ def test_fullsize_after_newton_steps(setup):
     assert torch.equal(bsr2.row_ptr, bsr.row_ptr)
 
 
-@pytest.mark.parametrize("kernel", ["auto", "resident"])
+@pytest.mark.parametrize("kernel", ["streamed", "resident"])
 def test_pcg_large_system(kernel):
-    """A system too large for the shared-memory layouts of the PCG (386k rows, 5M blocks): the
-    streamed kernels (what AUTO picks) and the block-resident kernel in its lean layout (x and
-    the inverse diagonal blocks in global memory): the true residual |rhs - (H+ + mu I) d| / |rhs|,
+    """A system too large to keep its matrix rows in shared memory (386k rows, 5M blocks): the
+    block-resident kernel in its lean layout (x and the inverse diagonal blocks in global memory;
+    what AUTO picks here) and the streamed kernels: the true residual |rhs - (H+ + mu I) d| / |rhs|,
     with H+ d from the library's own block product, matches the residual the PCG reports."""
     import __graft_entry__
     __graft_entry__.build()
@@ -117,7 +117,7 @@ def test_pcg_large_system(kernel):
     m = ti.noisy_sphere(level=9, seed=5).as_f32()
     x = torch.tensor(m.x, dtype=torch.float32, device="cuda")
     tri = torch.tensor(m.tri, dtype=torch.int32, device="cuda")
-    ctx = ttie.Context(pcg_kernel={"auto": ttie.PCG_KERNEL_AUTO, "resident": ttie.PCG_KERNEL_RESIDENT}[kernel])
+    ctx = ttie.Context(pcg_kernel={"streamed": ttie.PCG_KERNEL_STREAMED, "resident": ttie.PCG_KERNEL_RESIDENT}[kernel])
     ctx.build_bvh(x, tri)
     ctx.eval_pairs(x, ttie.EVAL_E | ttie.EVAL_H)
     bsr = ctx.assemble()
