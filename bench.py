@@ -275,8 +275,9 @@ def main():
     ap.add_argument("--pcg-cheb-degree", type=int, default=0, help="Chebyshev degree (0: the library's default)")
     ap.add_argument("--traversal", choices=["one_walk", "two_walks"], default="one_walk",
                     help="LBVH traversal")
-    ap.add_argument("--pcg-kernel", choices=["auto", "resident", "streamed"], default="auto",
-                    help="PCG kernel: block-resident (one launch) or streamed (two kernels per iteration)")
+    ap.add_argument("--pcg-kernel", choices=["auto", "resident", "streamed", "resident_uncached"], default="auto",
+                    help="PCG kernel: block-resident (one launch; uncached: matrix rows from global memory on "
+                         "every product) or streamed (two kernels per iteration)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -304,7 +305,8 @@ def main():
               "traversal_mode": {"two_walks": ttie.TRAVERSAL_TWO_WALKS,
                                  "one_walk": ttie.TRAVERSAL_ONE_WALK}[args.traversal],
               "pcg_kernel": {"auto": ttie.PCG_KERNEL_AUTO, "resident": ttie.PCG_KERNEL_RESIDENT,
-                             "streamed": ttie.PCG_KERNEL_STREAMED}[args.pcg_kernel]}
+                             "streamed": ttie.PCG_KERNEL_STREAMED,
+                             "resident_uncached": ttie.PCG_KERNEL_RESIDENT_UNCACHED}[args.pcg_kernel]}
     stream = torch.cuda.current_stream()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

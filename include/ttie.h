@@ -89,7 +89,9 @@ typedef struct {
     int ls_max_halvings;  /* line search tries 1+push_eta, 1, 1/2, ... 2^-this      */
     double armijo_c;
     double push_eta;      /* first trial step 1 + push_eta (overshoot past touching) */
-    int exact_only;       /* test switch: decide every sign with exact arithmetic  */
+    int exact_only;       /* test switch: 1 decides every sign with exact arithmetic
+                             (float32 points in 256-bit integers where their span fits,
+                             else expansions), 2 with expansion arithmetic only         */
     int profile;          /* record per-stage GPU times in ttie_step_info          */
     double max_step;      /* Newton step cap: largest vertex move per iteration, in
                              mean edge lengths of the mesh (0 = no cap)            */
@@ -125,8 +127,16 @@ typedef struct {
  *           shared memory for the whole solve, blocks exchanging through tagged words.
  * STREAMED: two kernels per iteration replayed from a CUDA graph, the matrix streamed from
  *           global memory and u read through the read-only path; block Jacobi only (with
- *           pcg_precond CHEBYSHEV the resident kernel runs).                                 */
-enum { TTIE_PCG_KERNEL_AUTO = 0, TTIE_PCG_KERNEL_RESIDENT = 1, TTIE_PCG_KERNEL_STREAMED = 2 };
+ *           pcg_precond CHEBYSHEV the resident kernel runs).
+ * RESIDENT_UNCACHED: RESIDENT with the matrix rows read from global memory on every product
+ *           even where they would fit shared memory (the product that systems too large for
+ *           shared memory get, on any system).                                           */
+enum {
+    TTIE_PCG_KERNEL_AUTO = 0,
+    TTIE_PCG_KERNEL_RESIDENT = 1,
+    TTIE_PCG_KERNEL_STREAMED = 2,
+    TTIE_PCG_KERNEL_RESIDENT_UNCACHED = 3
+};
 
 /* Line-search acceptance (the paper states no line search; these are readings of its inexact
  * Newton route).  E: energy, n: intersecting pairs, at x and at the trial x + a d.
@@ -300,9 +310,9 @@ typedef struct {
                                     preconditioner after its restart)                      */
     int64_t pcg_row_iters;       /* sum over the PCG's products of the rows updated           */
     double energy_elastic;       /* elastic term's part of energy (0 without one)             */
-    int pcg_kernel;              /* the PCG kernels that ran: TTIE_PCG_KERNEL_RESIDENT or
-                                    TTIE_PCG_KERNEL_STREAMED; 0 when no PCG ran or with batched
-                                    instances (their own solver)                              */
+    int pcg_kernel;              /* the PCG kernels that ran: TTIE_PCG_KERNEL_RESIDENT,
+                                    _STREAMED or _RESIDENT_UNCACHED; 0 when no PCG ran or with
+                                    batched instances (their own solver)                      */
 } ttie_step_info;
 
 /*

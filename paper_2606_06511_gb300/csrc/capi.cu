@@ -118,8 +118,8 @@ static ttie_status check_params(Ctx &c, const ttie_params *p) {
         (p->traversal_mode != TTIE_TRAVERSAL_TWO_WALKS && p->traversal_mode != TTIE_TRAVERSAL_ONE_WALK) ||
         (p->ls_rule != TTIE_LS_ARMIJO && p->ls_rule != TTIE_LS_FEWER) ||
         !(p->push_eta_max >= 0.0) || p->push_eta_max > 1e3 ||
-        (p->pcg_kernel != TTIE_PCG_KERNEL_AUTO && p->pcg_kernel != TTIE_PCG_KERNEL_RESIDENT &&
-         p->pcg_kernel != TTIE_PCG_KERNEL_STREAMED))
+        p->pcg_kernel < TTIE_PCG_KERNEL_AUTO || p->pcg_kernel > TTIE_PCG_KERNEL_RESIDENT_UNCACHED ||
+        p->exact_only < 0 || p->exact_only > 2)
         return set_err(c, TTIE_ERR_INVALID, "numeric parameter out of range");
     return TTIE_OK;
 }
@@ -460,7 +460,9 @@ static ttie_status newton_impl(Ctx &c, T *x, ttie_step_info *info) {
     inf.pcg_rel_residual = c.hs->red[1] > 0.0 ? std::sqrt(c.hs->red[4] / c.hs->red[1]) : 0.0;
     // the Chebyshev-preconditioned kernel multiplies k + 1 times per iteration after its restart
     const int64_t passes = c.pcg_cheb ? (int64_t)c.hs->pcg_products : (int64_t)inf.pcg_iters;
-    inf.pcg_kernel = c.pcg_streamed ? TTIE_PCG_KERNEL_STREAMED : TTIE_PCG_KERNEL_RESIDENT;
+    inf.pcg_kernel = c.pcg_streamed ? TTIE_PCG_KERNEL_STREAMED
+                     : c.prm.pcg_kernel == TTIE_PCG_KERNEL_RESIDENT_UNCACHED ? TTIE_PCG_KERNEL_RESIDENT_UNCACHED
+                                                                             : TTIE_PCG_KERNEL_RESIDENT;
     inf.pcg_block_iters = passes * c.nnzb;
     inf.pcg_row_iters = passes * c.n_rows;
     mark(c, 4);

@@ -107,6 +107,155 @@ __device__ __noinline__ int det3_exact(const double *e1, const double *e2, const
     return expansion_sign(24, s24);
 }
 
+// Sign of det[e1, e2, f] for exactly known entries in integer arithmetic.  Scaled by 2^-lo,
+// lo the exponent of the lowest set significand bit among the nine entries, every entry is
+// an integer (exactly); when every scaled entry is below 2^40 in magnitude, the 2x2 minors
+// (below 2^81) and the determinant (below 2^123) are exact in signed 128-bit integers.
+// Entries of coordinate differences of float32 positions of similar magnitude have about 24
+// to 30 significant bits and fit.  False (sign not set) for a subnormal, infinite or NaN
+// entry, or entries whose bits span more than 40 places.
+__device__ __forceinline__ bool det3_int_sign(const double *e1, const double *e2, const double *f, int &sign) {
+    const double *rows[3] = {e1, e2, f};
+    int lo = 1 << 20, hi = -(1 << 20);
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const double v = rows[r][k];
+            if (v == 0.0) continue;
+            const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+            const int E = (int)((b >> 52) & 0x7ff);
+            if (E == 0 || E == 0x7ff) return false;
+            const unsigned long long m = (b & ((1ull << 52) - 1)) | (1ull << 52);
+            lo = min(lo, E - 1075 + __ffsll((long long)m) - 1);   // lowest set bit: 2^lo
+            hi = max(hi, E - 1023);                               // |v| < 2^(hi + 1)
+        }
+    if (hi < lo) { sign = 0; return true; }   // every entry zero
+    if (hi - lo > 39) return false;
+    long long I[3][3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) I[r][k] = __double2ll_rn(ldexp(rows[r][k], -lo));
+    const __int128 mx = (__int128)I[1][1] * I[2][2] - (__int128)I[1][2] * I[2][1];
+    const __int128 my = (__int128)I[1][2] * I[2][0] - (__int128)I[1][0] * I[2][2];
+    const __int128 mz = (__int128)I[1][0] * I[2][1] - (__int128)I[1][1] * I[2][0];
+    const __int128 d = (__int128)I[0][0] * mx + (__int128)I[0][1] * my + (__int128)I[0][2] * mz;
+    sign = (d > 0) - (d < 0);
+    return true;
+}
+
+// ---- 256-bit two's-complement integers (arithmetic modulo 2^256; exact while the true
+// values stay below 2^255 in magnitude)
+struct I256 {
+    unsigned long long w[4];
+};
+__device__ __forceinline__ I256 i256_from(__int128 v) {
+    const unsigned long long ext = v < 0 ? ~0ull : 0ull;
+    return {{(unsigned long long)v, (unsigned long long)(v >> 64), ext, ext}};
+}
+__device__ __forceinline__ I256 i256_add(const I256 &a, const I256 &b) {
+    I256 r;
+    unsigned long long c = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const unsigned __int128 t = (unsigned __int128)a.w[k] + b.w[k] + c;
+        r.w[k] = (unsigned long long)t;
+        c = (unsigned long long)(t >> 64);
+    }
+    return r;
+}
+__device__ __forceinline__ I256 i256_neg(const I256 &a) {
+    I256 r;
+    unsigned long long c = 1;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const unsigned __int128 t = (unsigned __int128)(~a.w[k]) + c;
+        r.w[k] = (unsigned long long)t;
+        c = (unsigned long long)(t >> 64);
+    }
+    return r;
+}
+__device__ __forceinline__ I256 i256_mul(const I256 &a, const I256 &b) {
+    I256 r = {{0ull, 0ull, 0ull, 0ull}};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        unsigned long long c = 0;
+#pragma unroll
+        for (int j = 0; i + j < 4; ++j) {
+            const unsigned __int128 t = (unsigned __int128)a.w[i] * b.w[j] + r.w[i + j] + c;
+            r.w[i + j] = (unsigned long long)t;
+            c = (unsigned long long)(t >> 64);
+        }
+    }
+    return r;
+}
+__device__ __forceinline__ int i256_sign(const I256 &a) {
+    if ((long long)a.w[3] < 0) return -1;
+    return (a.w[0] | a.w[1] | a.w[2] | a.w[3]) ? 1 : 0;
+}
+
+// Sign of det[b - a, c - a, d - a] for float32 points, in integer arithmetic.  Each coordinate
+// is +-s 2^e with s < 2^24; scaled by 2^-lo (lo: the smallest exponent of a lowest set bit
+// among the twelve) all are integers, below 2^(hi - lo + 1) with hi the largest exponent of a
+// top bit.  When that bound is at most 2^79 the differences are below 2^80, the 2x2 minors
+// below 2^161 and the determinant below 2^243: exact in 256-bit integers.  Coordinates of a
+// mesh spanning 1e-17 to 10 fit.  False (sign not set) for infinite or NaN coordinates or a
+// wider span.
+__device__ __noinline__ bool orient3d_f32_int(const float *a, const float *b, const float *c, const float *d,
+                                              int &sign) {
+    const float *P[4] = {a, b, c, d};
+    unsigned s[4][3];
+    int ex[4][3];
+    int lo = 1 << 20, hi = -(1 << 20);
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const unsigned bits = __float_as_uint(P[p][k]);
+            const int E = (int)((bits >> 23) & 0xffu);
+            if (E == 255) return false;
+            unsigned m = bits & 0x7fffffu;
+            int e = -149;
+            if (E != 0) {
+                m |= 0x800000u;
+                e = E - 150;
+            }
+            s[p][k] = m;
+            ex[p][k] = e;
+            if (m == 0) continue;
+            lo = min(lo, e + __ffs((int)m) - 1);
+            hi = max(hi, e + 31 - __clz((int)m));
+        }
+    if (hi < lo) { sign = 0; return true; }   // every coordinate zero
+    if (hi - lo > 78) return false;
+    __int128 X[4][3];
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            // a right shift drops only zero bits: lo is at most e + (trailing zeros of s)
+            const int sh = ex[p][k] - lo;
+            __int128 v = sh >= 0 ? ((__int128)s[p][k] << sh) : (__int128)(s[p][k] >> (-sh));
+            if (__float_as_uint(P[p][k]) >> 31) v = -v;
+            X[p][k] = v;
+        }
+    I256 e1[3], e2[3], f[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        e1[k] = i256_from(X[1][k] - X[0][k]);
+        e2[k] = i256_from(X[2][k] - X[0][k]);
+        f[k] = i256_from(X[3][k] - X[0][k]);
+    }
+    // det = e1 . (e2 x f)
+    const I256 mx = i256_add(i256_mul(e2[1], f[2]), i256_neg(i256_mul(e2[2], f[1])));
+    const I256 my = i256_add(i256_mul(e2[2], f[0]), i256_neg(i256_mul(e2[0], f[2])));
+    const I256 mz = i256_add(i256_mul(e2[0], f[1]), i256_neg(i256_mul(e2[1], f[0])));
+    const I256 det = i256_add(i256_add(i256_mul(e1[0], mx), i256_mul(e1[1], my)), i256_mul(e1[2], mz));
+    sign = i256_sign(det);
+    return true;
+}
+
 // Sign of det[b - a, c - a, d - a] (positive when d lies on the side of the plane
 // (a, b, c) that the normal (b - a) x (c - a) points to).  When the nine coordinate
 // differences are exact doubles (always the case for float32 inputs of similar

@@ -535,15 +535,17 @@ __global__ void k_update_grouped(T *__restrict__ x, int stride, const T *__restr
 // Totals of a batched step in fixed order: energy and pairs after the step, largest PCG
 // iteration count and relative residual, sum of g.d, smallest accepted step, instances
 // solved, and the PCG work (iterations x 3x3 blocks, iterations x rows) summed over them.
-__global__ void k_inst_totals(const Inst *inst, int G, const int32_t *row_ptr, double *out) {
-    if (blockIdx.x != 0 || threadIdx.x != 0) return;
-    double e = 0.0, gd = 0.0, rel = 0.0, amin = 1e300, wb = 0.0, wr = 0.0;
-    long long n = 0;
+constexpr int kTotThreads = 512;
+__global__ void __launch_bounds__(kTotThreads) k_inst_totals(const Inst *inst, int G, const int32_t *row_ptr,
+                                                             double *out) {
+    // per thread over instances g = tid, tid + kTotThreads, ..., then a tree over the threads:
+    // a fixed order, so the sums do not depend on timing
+    double e = 0.0, gd = 0.0, rel = 0.0, amin = 1e300, wb = 0.0, wr = 0.0, n = 0.0;
     int it = 0, solved = 0;
-    for (int g = 0; g < G; ++g) {
+    for (int g = threadIdx.x; g < G; g += kTotThreads) {
         const Inst &I = inst[g];
         e += I.e_new;
-        n += I.n_new;
+        n += (double)I.n_new;
         if (I.n0 > 0) {
             gd += I.gd;
             rel = fmax(rel, I.rel);
@@ -556,15 +558,37 @@ __global__ void k_inst_totals(const Inst *inst, int G, const int32_t *row_ptr, d
             wr += (double)I.iters * I.count;
         }
     }
-    out[7] = wb;
-    out[8] = wr;
-    out[0] = e;
-    out[1] = (double)n;
-    out[2] = (double)it;
-    out[3] = rel;
-    out[4] = gd;
-    out[5] = solved ? amin : 0.0;
-    out[6] = (double)solved;
+    __shared__ double s_d[7][kTotThreads];
+    __shared__ int s_i[2][kTotThreads];
+    const int t = threadIdx.x;
+    s_d[0][t] = e; s_d[1][t] = gd; s_d[2][t] = rel; s_d[3][t] = amin; s_d[4][t] = wb; s_d[5][t] = wr; s_d[6][t] = n;
+    s_i[0][t] = it; s_i[1][t] = solved;
+    __syncthreads();
+    for (int h = kTotThreads / 2; h; h >>= 1) {
+        if (t < h) {
+            s_d[0][t] += s_d[0][t + h];
+            s_d[1][t] += s_d[1][t + h];
+            s_d[2][t] = fmax(s_d[2][t], s_d[2][t + h]);
+            s_d[3][t] = fmin(s_d[3][t], s_d[3][t + h]);
+            s_d[4][t] += s_d[4][t + h];
+            s_d[5][t] += s_d[5][t + h];
+            s_d[6][t] += s_d[6][t + h];
+            s_i[0][t] = max(s_i[0][t], s_i[0][t + h]);
+            s_i[1][t] += s_i[1][t + h];
+        }
+        __syncthreads();
+    }
+    if (t == 0) {
+        out[7] = s_d[4][0];
+        out[8] = s_d[5][0];
+        out[0] = s_d[0][0];
+        out[1] = s_d[6][0];
+        out[2] = (double)s_i[0][0];
+        out[3] = s_d[2][0];
+        out[4] = s_d[1][0];
+        out[5] = s_i[1][0] ? s_d[3][0] : 0.0;
+        out[6] = (double)s_i[1][0];
+    }
 }
 
 }  // namespace
@@ -902,7 +926,7 @@ template cudaError_t instance_update<float>(Ctx &, float *, int, const float *);
 template cudaError_t instance_update<double>(Ctx &, double *, int, const double *);
 
 cudaError_t instance_totals(Ctx &c, double *d_out) {
-    launch(c, k_inst_totals, dim3(1), dim3(32), (const Inst *)c.inst.p, c.n_groups, (const int32_t *)c.row_ptr.p,
+    launch(c, k_inst_totals, dim3(1), dim3(kTotThreads), (const Inst *)c.inst.p, c.n_groups, (const int32_t *)c.row_ptr.p,
            d_out);
     return cudaGetLastError();
 }

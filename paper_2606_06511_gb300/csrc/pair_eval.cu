@@ -62,11 +62,51 @@ __device__ __forceinline__ bool structural_zero(v3<double> a, v3<double> b, v3<d
            (az || by || fx);
 }
 
-// FP64 stage: filter, then the structural-zero certificate.
-__device__ __noinline__ int det_sign_f64(v3<double> e1, v3<double> e2, v3<double> f) {
+// a * b == c * d exactly: the rounded products and their errors (fma) both equal.  Only
+// where the errors are exact (no product near underflow) and a zero product has a zero factor.
+__device__ __forceinline__ bool prod_eq(double a, double b, double c, double d) {
+    const double p = a * b, q = c * d;
+    if (p != q) return false;
+    if (p == 0.0) return (a == 0.0 || b == 0.0) && (c == 0.0 || d == 0.0);
+    if (!(fabs(p) > 0x1p-960) || !(fabs(p) < 0x1p+1000)) return false;
+    return fma(a, b, -p) == fma(c, d, -q);
+}
+
+// det[e1, e2, f] (entries exact) is exactly zero when, expanded along one of its rows w with
+// the other two rows u, v in cyclic order, every term w_i (u x v)_i vanishes: w_i = 0, or the
+// minor u_j v_k - u_k v_j has two exactly equal products.  Meshes with mirror symmetry
+// (a vertex quadruple symmetric about a coordinate plane: an isosceles trapezoid, coplanar)
+// give such determinants, which neither filter can certify.
+__device__ __forceinline__ bool terms_vanish(v3<double> u, v3<double> v, v3<double> w) {
+    return (w.x == 0.0 || prod_eq(u.y, v.z, u.z, v.y)) && (w.y == 0.0 || prod_eq(u.z, v.x, u.x, v.z)) &&
+           (w.z == 0.0 || prod_eq(u.x, v.y, u.y, v.x));
+}
+__device__ __forceinline__ bool minor_zero(v3<double> e1, v3<double> e2, v3<double> f) {
+    return terms_vanish(e1, e2, f) || terms_vanish(e2, f, e1) || terms_vanish(f, e1, e2);
+}
+
+// b - a, and whether it is exact (Knuth's two-sum error of b + (-a) is zero).
+__device__ __forceinline__ double sub_exact(double b, double a, bool &exact) {
+    const double s = b - a, bp = s + a, ap = s - bp;
+    exact &= ((b - bp) + (-a - ap)) == 0.0;
+    return s;
+}
+__device__ __forceinline__ v3<double> sub_exact(v3<double> b, v3<double> a, bool &exact) {
+    return {sub_exact(b.x, a.x, exact), sub_exact(b.y, a.y, exact), sub_exact(b.z, a.z, exact)};
+}
+
+// FP64 stage: filter, then the structural-zero certificate, then (differences exact) the
+// exact sign in 128-bit integers where the entries fit, else the vanishing-terms certificate.
+// Only what none of these settles goes to the expansion arithmetic.
+__device__ __noinline__ int det_sign_f64(v3<double> e1, v3<double> e2, v3<double> f, bool exact) {
     const int s = filt_f64(cross(e1, e2), abs_cross(e1, e2), f);
     if (s != kUndec) return s;
-    return structural_zero(e1, e2, f) ? 0 : kUndec;
+    if (structural_zero(e1, e2, f)) return 0;
+    if (!exact) return kUndec;
+    const double a[3] = {e1.x, e1.y, e1.z}, b[3] = {e2.x, e2.y, e2.z}, c[3] = {f.x, f.y, f.z};
+    int si;
+    if (exact::det3_int_sign(a, b, c, si)) return si;
+    return minor_zero(e1, e2, f) ? 0 : kUndec;
 }
 
 __device__ __forceinline__ int orient_exact(v3<double> a, v3<double> b, v3<double> c, v3<double> d) {
@@ -97,7 +137,10 @@ template <typename T, bool kF32Only = false> struct Filtered {
             if (kF32Only) return kUndec;
         }
         const v3<double> a = to_d(P0);
-        s = det_sign_f64(to_d(P1) - a, to_d(P2) - a, to_d(q) - a);
+        bool exact = true;
+        const v3<double> e1 = sub_exact(to_d(P1), a, exact), e2 = sub_exact(to_d(P2), a, exact),
+                         f = sub_exact(to_d(q), a, exact);
+        s = det_sign_f64(e1, e2, f, exact);
         if (s != kUndec) ++st.f64;
         return s;
     }
@@ -110,7 +153,10 @@ template <typename T, bool kF32Only = false> struct Filtered {
             if (s != kUndec) { ++st.f32; return s; }
             if (kF32Only) return kUndec;
         }
-        s = det_sign_f64(to_d(pu) - to_d(p1), to_d(qv) - to_d(q1), to_d(q1) - to_d(p1));
+        bool exact = true;
+        const v3<double> e1 = sub_exact(to_d(pu), to_d(p1), exact), e2 = sub_exact(to_d(qv), to_d(q1), exact),
+                         f = sub_exact(to_d(q1), to_d(p1), exact);
+        s = det_sign_f64(e1, e2, f, exact);
         if (s != kUndec) ++st.f64;
         return s;
     }
@@ -121,31 +167,44 @@ template <typename T, bool kF32Only = false> struct Filtered {
 // so the same decisions), and only the signs neither certifies through exact expansions.
 // Counts the signs decided by FP64 and by exact arithmetic (the FP32 ones were counted by the
 // first pass).  With exact_only every sign is exact.
+// Exact signs for what the filters leave: float32 points in 256-bit integers where their span
+// allows, else (and for FP64 points) expansion arithmetic.  exact_mode 1: no filters; 2: no
+// filters and expansions only (test switches).
 template <typename T> struct Cascade {
-    bool exact_only;
+    int exact_mode;
     Stats &st;
+    __device__ int exact_sign(v3<T> a, v3<T> b, v3<T> c, v3<T> d) {
+        ++st.ex;
+        if constexpr (sizeof(T) == 4) {
+            if (exact_mode != 2) {
+                const float A[3] = {(float)a.x, (float)a.y, (float)a.z}, B[3] = {(float)b.x, (float)b.y, (float)b.z},
+                            C[3] = {(float)c.x, (float)c.y, (float)c.z}, D[3] = {(float)d.x, (float)d.y, (float)d.z};
+                int s;
+                if (exact::orient3d_f32_int(A, B, C, D, s)) return s;
+            }
+        }
+        return orient_exact(to_d(a), to_d(b), to_d(c), to_d(d));
+    }
     __device__ int side(v3<T> P0, v3<T> P1, v3<T> P2, v3<T> q) {
-        if (!exact_only) {
+        if (!exact_mode) {
             Stats inner;
             Filtered<T> f{false, inner};
             const int s = f.side(P0, P1, P2, q);
             st.f64 += inner.f64;
             if (s != kUndec) return s;
         }
-        ++st.ex;
-        return orient_exact(to_d(P0), to_d(P1), to_d(P2), to_d(q));
+        return exact_sign(P0, P1, P2, q);
     }
     // det[pu - p1, qv - q1, q1 - p1] = det[pu - p1, qv - p1, q1 - p1]
     __device__ int over(v3<T> p1, v3<T> pu, v3<T> q1, v3<T> qv) {
-        if (!exact_only) {
+        if (!exact_mode) {
             Stats inner;
             Filtered<T> f{false, inner};
             const int s = f.over(p1, pu, q1, qv);
             st.f64 += inner.f64;
             if (s != kUndec) return s;
         }
-        ++st.ex;
-        return orient_exact(to_d(p1), to_d(pu), to_d(qv), to_d(q1));
+        return exact_sign(p1, pu, qv, q1);
     }
 };
 
@@ -278,7 +337,7 @@ __global__ void k_resolve(const vec4_t<T> *__restrict__ x, const int4 *__restric
                           DevScalars *ds) {
     const unsigned long long m = ds->n_defer2;
     Stats st;
-    Cascade<T> sg{exact_only != 0, st};
+    Cascade<T> sg{exact_only, st};
     for (unsigned long long k = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; k < m;
          k += (unsigned long long)gridDim.x * blockDim.x) {
         const uint32_t p = defer2[k];

@@ -215,6 +215,7 @@ template <typename T> struct PcgArgs {
     RedSlot *slots;          // resident kernel: 2 x kMaxGridPcg tagged reduction slots, then 2 total slots
     const int *part;         // resident kernel: rows of block b are part[b] .. part[b + 1]
     int withhold;            // test switch: block 0 never publishes its partial sums
+    int no_cache;            // resident kernel: matrix rows read from global memory even where they fit
     double rtol2;
     int max_it;
     DevScalars *ds;
@@ -561,22 +562,35 @@ template <typename T> struct ResidentView {
     int nrow, nnz, b_begin;
 };
 
-// w = (A + mu I) u on the block's rows, u of every row read from the published vectors src
-// with tag t (loc: the block's own rows of u, for the shift); returns the rows' w.u.  A load
-// that never sees tag t sets *bad.
-template <typename T>
+// Hint: bring [b, e) of global memory into L2 (one bulk prefetch; the 16-byte-aligned part
+// inside the range, so no byte outside [b, e) rounded down to 16 bytes is touched).
+__device__ __forceinline__ void prefetch_l2(const void *b, const void *e) {
+    const size_t lo = __cvta_generic_to_global(b) & ~(size_t)15, hi = __cvta_generic_to_global(e) & ~(size_t)15;
+    if (hi > lo) asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(lo), "r"((unsigned)(hi - lo)) : "memory");
+}
+// waves of rows ahead that a warp prefetches its matrix rows when they are not cached
+constexpr int kPrefetchWaves = 2;
+
+// w = (A + mu I) u on the block's rows (THREADS threads), u of every row read from the
+// published vectors src with tag t (loc: the block's own rows of u, for the shift); returns the
+// rows' w.u.  A load that never sees tag t sets *bad.  rev: the rows in reverse order.
+// Successive products alternate the order, so that a matrix streamed from global memory
+// (larger than L2) starts each pass on the part the previous pass left in L2 (noisy sphere,
+// 201 MB of blocks: 20.8 -> 19.2 ms for 200 iterations).
+template <typename T, int THREADS>
 __device__ __forceinline__ Acc<T> resident_product(const PcgArgs<T> &a, const ResidentView<T> &v,
-                                                   const vec4_t<T> *src, const T *loc, T mu, unsigned t, int *bad) {
+                                                   const vec4_t<T> *src, const T *loc, T mu, unsigned t, int *bad,
+                                                   bool rev) {
     if (v.gathered) {
         // gather every block's column vector first: all loads of a thread in flight together
         // words not yet tagged t are loaded again, all of a thread's together
         constexpr int U = 4;
-        for (int j0 = threadIdx.x; j0 < v.nnz; j0 += U * kPcgThreads) {
+        for (int j0 = threadIdx.x; j0 < v.nnz; j0 += U * THREADS) {
             vec4_t<T> g[U];
             unsigned pend = 0;
 #pragma unroll
             for (int k = 0; k < U; ++k) {
-                const int j = j0 + k * kPcgThreads;
+                const int j = j0 + k * THREADS;
                 if (j < v.nnz) {
                     g[k] = ld_row<T>(&src[v.col[j]]);
                     pend |= 1u << k;
@@ -587,7 +601,7 @@ __device__ __forceinline__ Acc<T> resident_product(const PcgArgs<T> &a, const Re
 #pragma unroll
                 for (int k = 0; k < U; ++k)
                     if ((pend >> k & 1u) && row_tagged<T>(g[k], t)) {
-                        const int j = j0 + k * kPcgThreads;
+                        const int j = j0 + k * THREADS;
                         v.gu[3 * j] = g[k].x; v.gu[3 * j + 1] = g[k].y; v.gu[3 * j + 2] = g[k].z;
                         pend &= ~(1u << k);
                     }
@@ -595,7 +609,7 @@ __device__ __forceinline__ Acc<T> resident_product(const PcgArgs<T> &a, const Re
                 if (wc.out() || *(volatile int *)bad) { *bad = 1; break; }
 #pragma unroll
                 for (int k = 0; k < U; ++k)
-                    if (pend >> k & 1u) g[k] = ld_row<T>(&src[v.col[j0 + k * kPcgThreads]]);
+                    if (pend >> k & 1u) g[k] = ld_row<T>(&src[v.col[j0 + k * THREADS]]);
             }
         }
         __syncthreads();
@@ -603,7 +617,18 @@ __device__ __forceinline__ Acc<T> resident_product(const PcgArgs<T> &a, const Re
     const int lane = threadIdx.x & 31, sub = lane & (kLanesPerRow - 1);
     const unsigned gmask = 0xffu << (lane & ~(kLanesPerRow - 1));
     Acc<T> wu;
-    for (int lr = threadIdx.x / kLanesPerRow; lr < v.nrow; lr += kPcgThreads / kLanesPerRow) {
+    for (int lr0 = threadIdx.x / kLanesPerRow; lr0 < v.nrow; lr0 += THREADS / kLanesPerRow) {
+        const int lr = rev ? v.nrow - 1 - lr0 : lr0;
+        if (!v.cached && lane == 0) {
+            // the warp's rows kPrefetchWaves waves on, [w0, w1) in loop order, [ra, rb) local
+            const int w0 = lr0 + kPrefetchWaves * (THREADS / kLanesPerRow);
+            if (w0 < v.nrow) {
+                const int w1 = min(w0 + 32 / kLanesPerRow, v.nrow);
+                const int ra = rev ? v.nrow - w1 : w0, rb = rev ? v.nrow - w0 : w1;
+                prefetch_l2(a.bval + (size_t)(v.b_begin + v.rp[ra]) * 9, a.bval + (size_t)(v.b_begin + v.rp[rb]) * 9);
+                prefetch_l2(a.col_idx + v.b_begin + v.rp[ra], a.col_idx + v.b_begin + v.rp[rb]);
+            }
+        }
         T y0 = 0, y1 = 0, y2 = 0;
         const int be = v.rp[lr + 1];
         if (v.gathered) {
@@ -724,8 +749,12 @@ __device__ __noinline__ bool cheb_coefficients(const double *al, const double *b
     return true;
 }
 
-template <typename T, bool kCheb>
-__global__ void __launch_bounds__(kPcgThreads) k_pcg_resident(PcgArgs<T> a, int smem_bytes) {
+// THREADS: 512 when the matrix rows are cached in shared memory (the product and its
+// exchanges are latency-bound and fewer warps meet sooner: cloth 2.02 -> 1.78 ms for 85
+// iterations), 1024 when they stream from global memory (more loads in flight: noisy sphere
+// 19.2 against 29.0 ms with 512).
+template <typename T, bool kCheb, int THREADS>
+__global__ void __launch_bounds__(THREADS) k_pcg_resident(PcgArgs<T> a, int smem_bytes) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ T s_alpha, s_beta;
     __shared__ int s_stop, s_bad;
@@ -770,7 +799,7 @@ __global__ void __launch_bounds__(kPcgThreads) k_pcg_resident(PcgArgs<T> a, int 
     v.b_begin = v.nrow ? a.row_ptr[row0] : 0;
     v.nnz = v.nrow ? a.row_ptr[row0 + v.nrow] - v.b_begin : 0;
     const size_t mat_bytes = ((size_t)v.nnz * (9 * sizeof(T) + sizeof(int)) + 15) / 16 * 16;
-    v.cached = vec_bytes + mat_bytes <= (size_t)smem_bytes;
+    v.cached = !a.no_cache && vec_bytes + mat_bytes <= (size_t)smem_bytes;
     v.gathered = v.cached && vec_bytes + mat_bytes + (size_t)v.nnz * 3 * sizeof(T) <= (size_t)smem_bytes;
     v.val = (T *)(smem + vec_bytes);
     v.col = (int *)(v.val + (size_t)9 * v.nnz);
@@ -875,11 +904,12 @@ __global__ void __launch_bounds__(kPcgThreads) k_pcg_resident(PcgArgs<T> a, int 
     // the product of the polynomial's j-th direction
     int jstep = 0;
     unsigned long long n_prod = 0;
+    unsigned n_calls = 0;   // products so far (their parity sets the order of the next)
     while (true) {
         const bool inner = kCheb && jstep > 0;
         const vec4_t<T> *src = (kCheb && (pub & 1u)) ? a.z4b : a.z4;
         const unsigned tu = kCheb ? (pub & 3u) : ((unsigned)it & 3u);
-        const Acc<T> wu = resident_product(a, v, src, inner ? v.d : v.u, mu, tu, &s_bad);
+        const Acc<T> wu = resident_product<T, THREADS>(a, v, src, inner ? v.d : v.u, mu, tu, &s_bad, (n_calls++ & 1u) != 0);
         if constexpr (kCheb) ++n_prod;
         if (inner) {
             // the polynomial's next step: rr -= D^-1 (A + mu I) d, d = c1 d + c2 rr, y += d;
@@ -1214,7 +1244,7 @@ cudaError_t pcg_solve(Ctx &c, const T *rhs, T *out, double rtol, int max_it) {
     TTIE_CUDA_TRY(ensure(c, c.pcg_sync, (2 * (size_t)kMaxGridPcg + 2) * sizeof(RedSlot) + (kMaxGridPcg + 1) * sizeof(int)));
     const int sms = c.num_sms > 0 ? c.num_sms : kNumSMs;
     // one block per SM at most: fewer participants in every reduction
-    int64_t blocks = (nr * kLanesPerRow + kPcgThreads - 1) / kPcgThreads;
+    int64_t blocks = (nr * kLanesPerRow + 1023) / 1024;
     if (blocks > (int64_t)sms) blocks = sms;
     if (blocks > kMaxGridPcg) blocks = kMaxGridPcg;
     if (blocks < 1) blocks = 1;
@@ -1231,13 +1261,10 @@ cudaError_t pcg_solve(Ctx &c, const T *rhs, T *out, double rtol, int max_it) {
     const int64_t r_cap = cheb ? ((int64_t)kResidentSmem - 4 - 15 - 15) / (21 * (int64_t)sizeof(T) + 4)
                                : ((int64_t)kResidentSmem - 4 - 15) / (15 * (int64_t)sizeof(T) + 4);
     const bool resident = (nr + blocks - 1) / blocks <= r_cap;
-    // systems whose matrix rows do not fit the blocks' shared memory: the streamed kernels
-    // (the block-resident kernel would read them from global memory on every product too)
     // the streamed kernels for systems whose rows do not fit the block-resident kernel's lean
-    // layout (in place of the global-memory persistent kernel), or when asked for; measured on
-    // the noisy sphere's FP32 system (386k rows) the resident kernel in its lean layout is
-    // slightly faster (20.9 against 21.8 ms for 200 iterations), on its FP64 system only the
-    // streamed kernels fit
+    // layout (in place of the global-memory persistent kernel), or when asked for: the noisy
+    // sphere's FP32 system (386k rows) fits the lean layout, its FP64 system only the streamed
+    // kernels
     const bool streamed = !(cheb && resident) && c.prm.test_withhold == 0 &&
                           (c.prm.pcg_kernel == TTIE_PCG_KERNEL_STREAMED ||
                            (c.prm.pcg_kernel == TTIE_PCG_KERNEL_AUTO && !resident));
@@ -1283,14 +1310,18 @@ cudaError_t pcg_solve(Ctx &c, const T *rhs, T *out, double rtol, int max_it) {
     args.slots = slots;
     args.part = rpart;
     args.withhold = c.prm.test_withhold;
+    args.no_cache = c.prm.pcg_kernel == TTIE_PCG_KERNEL_RESIDENT_UNCACHED ? 1 : 0;
     ++c.n_launch;
     if (c.prm.profile) cudaEventRecord(c.ev[8], c.stream);
     if (resident) {
-        const void *kern = cheb ? (const void *)k_pcg_resident<T, true> : (const void *)k_pcg_resident<T, false>;
+        // 512 threads when the blocks' matrix rows are expected in shared memory, else 1024
+        const bool narrow = blk_bytes <= (int64_t)kResidentSmem && !args.no_cache;
+        const void *kern = cheb ? (narrow ? (const void *)k_pcg_resident<T, true, 512> : (const void *)k_pcg_resident<T, true, 1024>)
+                                : (narrow ? (const void *)k_pcg_resident<T, false, 512> : (const void *)k_pcg_resident<T, false, 1024>);
         TTIE_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kResidentSmem));
         int smem = kResidentSmem;
         void *kargs[] = {&args, &smem};
-        TTIE_CUDA_TRY(cudaLaunchCooperativeKernel(kern, dim3((unsigned)blocks), dim3(kPcgThreads), kargs,
+        TTIE_CUDA_TRY(cudaLaunchCooperativeKernel(kern, dim3((unsigned)blocks), dim3(narrow ? 512 : 1024), kargs,
                                                   (size_t)kResidentSmem, c.stream));
     } else {
         void *kargs[] = {&args};
@@ -1330,6 +1361,7 @@ cudaError_t pcg_run_raw(cudaStream_t stream, int num_sms, const int32_t *row_ptr
     args.slots = nullptr;
     args.part = nullptr;
     args.withhold = 0;
+    args.no_cache = 0;
     args.partA = partials;
     args.partB = partials + 2 * kNumSMs * 8;
     args.rtol2 = rtol * rtol;

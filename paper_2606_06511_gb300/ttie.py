@@ -29,7 +29,7 @@ PSD_PER_PART, PSD_DROP_CROSS, PSD_WHOLE = 0, 1, 2
 PCG_BLOCK_JACOBI, PCG_CHEBYSHEV, PCG_AUTO = 0, 1, 2
 TRAVERSAL_TWO_WALKS, TRAVERSAL_ONE_WALK = 0, 1
 LS_ARMIJO, LS_FEWER = 0, 1
-PCG_KERNEL_AUTO, PCG_KERNEL_RESIDENT, PCG_KERNEL_STREAMED = 0, 1, 2
+PCG_KERNEL_AUTO, PCG_KERNEL_RESIDENT, PCG_KERNEL_STREAMED, PCG_KERNEL_RESIDENT_UNCACHED = 0, 1, 2, 3
 EVAL_E, EVAL_G, EVAL_H = 1, 2, 4
 
 

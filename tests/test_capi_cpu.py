@@ -94,7 +94,9 @@ def test_bad_params_rejected_before_device(lib):
     assert lib.ttie_create(ctypes.byref(h), ctypes.byref(p), None) == ttie.TTIE_ERR_INVALID
     p = ttie.default_params(push_eta_max=-1.0)
     assert lib.ttie_create(ctypes.byref(h), ctypes.byref(p), None) == ttie.TTIE_ERR_INVALID
-    p = ttie.default_params(pcg_kernel=3)
+    p = ttie.default_params(pcg_kernel=4)
+    assert lib.ttie_create(ctypes.byref(h), ctypes.byref(p), None) == ttie.TTIE_ERR_INVALID
+    p = ttie.default_params(exact_only=3)
     assert lib.ttie_create(ctypes.byref(h), ctypes.byref(p), None) == ttie.TTIE_ERR_INVALID
     p = ttie.default_params(traversal_mode=2)
     assert lib.ttie_create(ctypes.byref(h), ctypes.byref(p), None) == ttie.TTIE_ERR_INVALID

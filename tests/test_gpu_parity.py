@@ -69,8 +69,11 @@ def test_candidates_bit_exact(ttie, name):
 
 
 @pytest.mark.parametrize("name", list(CASES))
-@pytest.mark.parametrize("exact_only", [0, 1])
+@pytest.mark.parametrize("exact_only", [0, 1, 2])
 def test_active_set_bit_exact(ttie, name, exact_only):
+    """Intersecting pairs bit-exact against the oracle's exact test: with the filters (0), every
+    sign exact (1: float32 points in 256-bit integers where their span fits, else expansions),
+    every sign by expansion arithmetic (2)."""
     m, mode = CASES[name]
     x, tri, grp = _dev(m)
     ctx = _ctx(ttie, mode, exact_only=exact_only)
@@ -83,6 +86,30 @@ def test_active_set_bit_exact(ttie, name, exact_only):
     st = ctx.get_filter_stats()
     if exact_only:
         assert st["fp32"] == 0 and st["fp64"] == 0
+
+
+def test_exact_zeros_settled_before_expansions(ttie):
+    """Mirror-symmetric lat-long ellipsoids (the second with equal x and y semi-axes, so vertex
+    quadruples symmetric about x = 0, y = 0 and x = y are exactly coplanar; coordinates below
+    1e-6 set to 0): every orientation sign neither filter certifies is an exact zero or a
+    determinant whose entries fit the 128-bit integer evaluation, so none reaches the expansion
+    arithmetic, and the intersecting set equals the exact oracle's."""
+    from ttie_inputs.meshes import Mesh, concat
+    m1 = ti.ellipsoid(14, (1.0, 0.8, 0.6))
+    m2 = ti.ellipsoid(10, (0.7, 0.7, 0.9))
+    m = concat([m1, Mesh(m2.x + np.array([0.0, 0.0, 0.5]), m2.tri, m2.group)]).as_f32()
+    m.x[np.abs(m.x) < 1e-6] = 0.0
+    x, tri, grp = _dev(m)
+    ctx = _ctx(ttie, "self")
+    ctx.build_bvh(x, tri, grp)
+    E, n_act = ctx.eval_pairs(x, ttie.EVAL_E)
+    pairs = O.candidate_pairs(m.x, m.tri, m.group, "self")
+    ev = O.evaluate(m.x, m.tri, pairs)
+    act_pairs, _, _ = ctx.get_active(with_derivatives=False)
+    assert n_act == int(ev.active.sum()) > 0
+    assert pair_set(act_pairs.cpu().numpy()) == pair_set(pairs[ev.active])
+    st = ctx.get_filter_stats()
+    assert st["fp64"] > 0 and st["exact"] == 0, st
 
 
 def _match(ctx, pairs, ev):
@@ -191,20 +218,24 @@ def test_assembly_pattern_and_values(ttie, name, precision):
 
 
 @pytest.mark.parametrize("precision", [0, 1])
-@pytest.mark.parametrize("precond", ["block_jacobi", "auto", "streamed"])
+@pytest.mark.parametrize("precond", ["block_jacobi", "auto", "streamed", "uncached", "uncached_auto"])
 def test_pcg_matches_direct_solve(ttie, precision, precond):
     """The PCG's solution against a dense direct solve of the same system (the matrix the GPU
     assembled, read back in FP64): the true residual is at the requested level and the
     solution error is below a fixed bound (FP32 2e-3, FP64 1e-6).  The residual on the
-    oracle's own matrix adds the assembly's rounding."""
+    oracle's own matrix adds the assembly's rounding.  Kernels: the block-resident one with
+    its matrix rows in shared memory (block Jacobi; AUTO, which picks Chebyshev here) or read
+    from global memory on every product (the product of systems too large for shared memory:
+    "uncached", both preconditioners), and the streamed kernels."""
     name = "cloth40"
     m, mode = CASES[name]
     dt = torch.float64 if precision else torch.float32
     x, tri, grp = _dev(m, dt)
+    kernel = {"streamed": ttie.PCG_KERNEL_STREAMED, "uncached": ttie.PCG_KERNEL_RESIDENT_UNCACHED,
+              "uncached_auto": ttie.PCG_KERNEL_RESIDENT_UNCACHED}.get(precond, ttie.PCG_KERNEL_RESIDENT)
     ctx = _ctx(ttie, mode, precision=precision,
-               pcg_precond={"block_jacobi": ttie.PCG_BLOCK_JACOBI, "auto": ttie.PCG_AUTO,
-                            "streamed": ttie.PCG_BLOCK_JACOBI}[precond],
-               pcg_kernel=ttie.PCG_KERNEL_STREAMED if precond == "streamed" else ttie.PCG_KERNEL_RESIDENT)
+               pcg_precond=ttie.PCG_AUTO if precond in ("auto", "uncached_auto") else ttie.PCG_BLOCK_JACOBI,
+               pcg_kernel=kernel)
     ctx.build_bvh(x, tri, grp)
     ctx.eval_pairs(x, ttie.EVAL_E | ttie.EVAL_H)
     bsr = ctx.assemble()
