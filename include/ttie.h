@@ -405,8 +405,10 @@ ttie_status ttie_get_active(ttie_ctx *ctx, int32_t *d_pairs, void *d_tc, void *d
 ttie_status ttie_get_direction(ttie_ctx *ctx, void *d_out);
 
 /* Counters of the last ttie_eval_pairs (host out array of 3): signs decided by the FP32
- * filter in the pass over all candidates (FP32 positions), then, in the pass over the pairs
- * that left a sign undecided, signs decided by the FP64 filter and by exact arithmetic. */
+ * filter in the pass over all candidates (FP32 positions); then, in the pass over the pairs
+ * that left a sign undecided, signs decided by the second stage (FP32 positions: the exact
+ * sign in 128/256-bit integers where the coordinates' span fits; otherwise the FP64 filter
+ * and its zero certificates); then signs decided by the last pass's exact arithmetic. */
 ttie_status ttie_get_filter_stats(ttie_ctx *ctx, int64_t *out3);
 
 /* ---- solve without allocating -------------------------------------------------- */

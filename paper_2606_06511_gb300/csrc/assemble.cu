@@ -604,8 +604,13 @@ cudaError_t assemble_system(Ctx &c, T *grad_full, bool with_elastic) {
                (unsigned long long)n_act * 36, (unsigned long long *)c.bkey.p, (uint32_t *)c.bval.p);
     TTIE_CUDA_TRY(cudaGetLastError());
     const int kbits = bits_for((unsigned long long)nr * (unsigned long long)nr);
+    bool in_second = false;
     TTIE_CUDA_TRY(radix_sort(c, (unsigned long long *)c.bkey.p, (uint32_t *)c.bval.p, (unsigned long long *)c.bkey2.p,
-                             (uint32_t *)c.bval2.p, nk, kbits));
+                             (uint32_t *)c.bval2.p, nk, kbits, &in_second));
+    if (in_second) {   // the sorted entries are in the scratch buffers: they become bkey / bval
+        std::swap(c.bkey, c.bkey2);
+        std::swap(c.bval, c.bval2);
+    }
 #ifdef TTIE_CHECKS
     launch(c, k_check_sorted, dim3(grid_for(nk, kThreads)), dim3(kThreads), (const unsigned long long *)c.bkey.p, nk, c.ds);
 #endif

@@ -223,10 +223,11 @@ inline unsigned grid_for(int64_t n, int threads, int64_t cap = 152 * 16) {
 // ------------------------------------------------------------------ primitives (sort_scan.cu)
 // Exclusive scan of n uint32 counts into uint64 offsets; out[n] = total.
 cudaError_t scan_u32_u64(Ctx &c, const uint32_t *in, unsigned long long *out, int64_t n);
-// Stable LSD radix sort of (key, value) by the low `bits` bits of key.  The result is
-// left in keys/vals; keys2/vals2 are scratch of the same size.
+// Stable LSD radix sort of (key, value) by the low `bits` bits of key; keys2/vals2 are scratch
+// of the same size.  The result is left in keys/vals, or, with in_second, wherever the last
+// pass wrote it: *in_second tells whether that is keys2/vals2 (no copy back).
 cudaError_t radix_sort(Ctx &c, unsigned long long *keys, uint32_t *vals, unsigned long long *keys2,
-                       uint32_t *vals2, int64_t n, int bits);
+                       uint32_t *vals2, int64_t n, int bits, bool *in_second = nullptr);
 // The same sort replayed from a graph captured on the first call with these arguments.
 cudaError_t radix_sort_graph(Ctx &c, unsigned long long *keys, uint32_t *vals, unsigned long long *keys2,
                              uint32_t *vals2, int64_t n, int bits);

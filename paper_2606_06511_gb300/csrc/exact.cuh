@@ -198,10 +198,11 @@ __device__ __forceinline__ int i256_sign(const I256 &a) {
 // Sign of det[b - a, c - a, d - a] for float32 points, in integer arithmetic.  Each coordinate
 // is +-s 2^e with s < 2^24; scaled by 2^-lo (lo: the smallest exponent of a lowest set bit
 // among the twelve) all are integers, below 2^(hi - lo + 1) with hi the largest exponent of a
-// top bit.  When that bound is at most 2^79 the differences are below 2^80, the 2x2 minors
-// below 2^161 and the determinant below 2^243: exact in 256-bit integers.  Coordinates of a
-// mesh spanning 1e-17 to 10 fit.  False (sign not set) for infinite or NaN coordinates or a
-// wider span.
+// top bit.  When that bound is at most 2^39 the differences are below 2^40, the 2x2 minors
+// below 2^81 and the determinant below 2^123: exact in 128-bit integers (coordinates of
+// similar magnitude).  Up to 2^79: differences below 2^80, minors below 2^161, determinant
+// below 2^243, exact in 256-bit integers (a mesh spanning 1e-17 to 10).  False (sign not set)
+// for infinite or NaN coordinates or a wider span.
 __device__ __noinline__ bool orient3d_f32_int(const float *a, const float *b, const float *c, const float *d,
                                               int &sign) {
     const float *P[4] = {a, b, c, d};
@@ -229,12 +230,36 @@ __device__ __noinline__ bool orient3d_f32_int(const float *a, const float *b, co
         }
     if (hi < lo) { sign = 0; return true; }   // every coordinate zero
     if (hi - lo > 78) return false;
+    // a right shift below drops only zero bits: lo is at most e + (trailing zeros of s)
+    if (hi - lo <= 38) {
+        long long X[4][3];
+#pragma unroll
+        for (int p = 0; p < 4; ++p)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const int sh = ex[p][k] - lo;
+                long long v = sh >= 0 ? ((long long)s[p][k] << sh) : (long long)(s[p][k] >> (-sh));
+                X[p][k] = (__float_as_uint(P[p][k]) >> 31) ? -v : v;
+            }
+        long long e1[3], e2[3], f[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            e1[k] = X[1][k] - X[0][k];
+            e2[k] = X[2][k] - X[0][k];
+            f[k] = X[3][k] - X[0][k];
+        }
+        const __int128 mx = (__int128)e2[1] * f[2] - (__int128)e2[2] * f[1];
+        const __int128 my = (__int128)e2[2] * f[0] - (__int128)e2[0] * f[2];
+        const __int128 mz = (__int128)e2[0] * f[1] - (__int128)e2[1] * f[0];
+        const __int128 det = (__int128)e1[0] * mx + (__int128)e1[1] * my + (__int128)e1[2] * mz;
+        sign = (det > 0) - (det < 0);
+        return true;
+    }
     __int128 X[4][3];
 #pragma unroll
     for (int p = 0; p < 4; ++p)
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            // a right shift drops only zero bits: lo is at most e + (trailing zeros of s)
             const int sh = ex[p][k] - lo;
             __int128 v = sh >= 0 ? ((__int128)s[p][k] << sh) : (__int128)(s[p][k] >> (-sh));
             if (__float_as_uint(P[p][k]) >> 31) v = -v;

@@ -135,6 +135,7 @@ template <typename T, bool kF32Only = false> struct Filtered {
             s = filt_f32(to_f(cross(e1, e2)), to_f(abs_cross(e1, e2)), to_f(f));
             if (s != kUndec) { ++st.f32; return s; }
             if (kF32Only) return kUndec;
+            if (int_sign(P0, P1, P2, q, s)) { ++st.f64; return s; }
         }
         const v3<double> a = to_d(P0);
         bool exact = true;
@@ -152,6 +153,7 @@ template <typename T, bool kF32Only = false> struct Filtered {
             s = filt_f32(to_f(cross(e1, e2)), to_f(abs_cross(e1, e2)), to_f(q1 - p1));
             if (s != kUndec) { ++st.f32; return s; }
             if (kF32Only) return kUndec;
+            if (int_sign(p1, pu, qv, q1, s)) { ++st.f64; return s; }   // det[pu - p1, qv - p1, q1 - p1]
         }
         bool exact = true;
         const v3<double> e1 = sub_exact(to_d(pu), to_d(p1), exact), e2 = sub_exact(to_d(qv), to_d(q1), exact),
@@ -161,6 +163,13 @@ template <typename T, bool kF32Only = false> struct Filtered {
         return s;
     }
     __device__ __forceinline__ static v3<float> to_f(v3<T> a) { return {(float)a.x, (float)a.y, (float)a.z}; }
+    // float32 points: the exact sign in integers, cheaper than the FP64 filter on a part whose
+    // FP64 rate is a small fraction of its integer rate (false where the span does not fit)
+    __device__ __forceinline__ static bool int_sign(v3<T> a, v3<T> b, v3<T> c, v3<T> d, int &s) {
+        const float A[3] = {(float)a.x, (float)a.y, (float)a.z}, B[3] = {(float)b.x, (float)b.y, (float)b.z},
+                    C[3] = {(float)c.x, (float)c.y, (float)c.z}, D[3] = {(float)d.x, (float)d.y, (float)d.z};
+        return exact::orient3d_f32_int(A, B, C, D, s);
+    }
 };
 
 // The undecided pairs' signs: each one through the FP32 and FP64 filters again (certified,
@@ -310,7 +319,7 @@ __global__ void __launch_bounds__(kThreads) k_classify(const vec4_t<T> *__restri
 // registers of the exact expansions (and their low occupancy) off the many pairs that FP64
 // decides.
 template <typename T>
-__global__ void k_resolve_f64(const vec4_t<T> *__restrict__ x, const int4 *__restrict__ tri4,
+__global__ void __launch_bounds__(128, 4) k_resolve_f64(const vec4_t<T> *__restrict__ x, const int4 *__restrict__ tri4,
                               const int2 *__restrict__ pairs, const uint32_t *__restrict__ defer, int exact_only,
                               uint32_t *__restrict__ bits, uint32_t *__restrict__ defer2, DevScalars *ds) {
     const unsigned long long m = ds->n_defer;

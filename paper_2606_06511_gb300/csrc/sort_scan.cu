@@ -201,7 +201,8 @@ cudaError_t scan_u32_u64(Ctx &c, const uint32_t *in, unsigned long long *out, in
 }
 
 cudaError_t radix_sort(Ctx &c, unsigned long long *keys, uint32_t *vals, unsigned long long *keys2, uint32_t *vals2,
-                       int64_t n, int bits) {
+                       int64_t n, int bits, bool *in_second) {
+    if (in_second) *in_second = false;
     if (n <= 1 || bits <= 0) return cudaSuccess;
     const int64_t n_tiles = (n + kTile - 1) / kTile;
     const int64_t n_cnt = n_tiles * kRadix;
@@ -219,7 +220,9 @@ cudaError_t radix_sort(Ctx &c, unsigned long long *keys, uint32_t *vals, unsigne
         unsigned long long *tk = ka; ka = kb; kb = tk;
         uint32_t *tv = va; va = vb; vb = tv;
     }
-    if (passes & 1) {
+    if ((passes & 1) && in_second) {
+        *in_second = true;   // the caller takes the result from keys2 / vals2
+    } else if (passes & 1) {
         TTIE_CUDA_TRY(cudaMemcpyAsync(keys, ka, n * sizeof(unsigned long long), cudaMemcpyDeviceToDevice, c.stream));
         TTIE_CUDA_TRY(cudaMemcpyAsync(vals, va, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, c.stream));
     }
