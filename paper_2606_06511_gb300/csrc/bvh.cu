@@ -78,12 +78,15 @@ template <typename T> __device__ __forceinline__ T tmin(T a, T b) { return a < b
 template <typename T> __device__ __forceinline__ T tmax(T a, T b) { return a > b ? a : b; }
 
 // Box of each triangle (over the vertices at x0 and, when x1 is given, also at x1:
-// the box swept by a straight-line motion) and the scene bounds of the box centres.
+// the box swept by a straight-line motion) and the scene bounds of the box centres.  The
+// centres and their bounds only place the Morton codes, so they are taken in the positions'
+// own precision (FP32 for FP32 positions, not the slow FP64 pipe).
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_tri_boxes(const vec4_t<T> *__restrict__ x0, const vec4_t<T> *__restrict__ x1,
                                                         const int4 *__restrict__ tri4, int64_t F, Box<T> *__restrict__ box,
                                                         DevScalars *ds) {
-    double clo[3] = {1e300, 1e300, 1e300}, chi[3] = {-1e300, -1e300, -1e300};
+    constexpr T kBig = sizeof(T) == 4 ? T(3e38) : T(1e300);
+    T clo[3] = {kBig, kBig, kBig}, chi[3] = {-kBig, -kBig, -kBig};
     for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < F; f += (int64_t)gridDim.x * blockDim.x) {
         int4 t = tri4[f];
         vec4_t<T> a = x0[t.x], b = x0[t.y], c = x0[t.z];
@@ -102,23 +105,22 @@ __global__ void __launch_bounds__(kThreads) k_tri_boxes(const vec4_t<T> *__restr
         bx.lo.w = T(0);
         bx.hi.w = T(0);
         box[f] = bx;
-        double cx = 0.5 * ((double)bx.lo.x + (double)bx.hi.x), cy = 0.5 * ((double)bx.lo.y + (double)bx.hi.y),
-               cz = 0.5 * ((double)bx.lo.z + (double)bx.hi.z);
-        clo[0] = fmin(clo[0], cx); clo[1] = fmin(clo[1], cy); clo[2] = fmin(clo[2], cz);
-        chi[0] = fmax(chi[0], cx); chi[1] = fmax(chi[1], cy); chi[2] = fmax(chi[2], cz);
+        const T cx = T(0.5) * (bx.lo.x + bx.hi.x), cy = T(0.5) * (bx.lo.y + bx.hi.y), cz = T(0.5) * (bx.lo.z + bx.hi.z);
+        clo[0] = tmin(clo[0], cx); clo[1] = tmin(clo[1], cy); clo[2] = tmin(clo[2], cz);
+        chi[0] = tmax(chi[0], cx); chi[1] = tmax(chi[1], cy); chi[2] = tmax(chi[2], cz);
     }
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         for (int o = 16; o; o >>= 1) {
-            clo[k] = fmin(clo[k], __shfl_xor_sync(0xffffffffu, clo[k], o));
-            chi[k] = fmax(chi[k], __shfl_xor_sync(0xffffffffu, chi[k], o));
+            clo[k] = tmin(clo[k], __shfl_xor_sync(0xffffffffu, clo[k], o));
+            chi[k] = tmax(chi[k], __shfl_xor_sync(0xffffffffu, chi[k], o));
         }
     }
     if ((threadIdx.x & 31) == 0 && clo[0] <= chi[0]) {
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            atomicMin(&ds->bounds_lo[k], ordered_bits(clo[k]));
-            atomicMax(&ds->bounds_hi[k], ordered_bits(chi[k]));
+            atomicMin(&ds->bounds_lo[k], ordered_bits((double)clo[k]));
+            atomicMax(&ds->bounds_hi[k], ordered_bits((double)chi[k]));
         }
     }
 }
@@ -137,24 +139,25 @@ __device__ __forceinline__ unsigned long long spread3(unsigned long long v) {
 template <typename T>
 __global__ void k_morton(const Box<T> *__restrict__ box, int64_t F, const int32_t *__restrict__ grp, int group_bits,
                          const DevScalars *ds, unsigned long long *__restrict__ key, uint32_t *__restrict__ perm) {
+    // quantised in FP32 (the codes only order the leaves; any deterministic rounding does)
     const int b = (63 - group_bits) / 3;
-    const double scale = (double)((1ull << b) - 1);
-    double lo[3], ext[3];
+    const float scale = (float)((1u << b) - 1u);
+    float lo[3], inv[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        lo[k] = from_ordered(ds->bounds_lo[k]);
-        double hi = from_ordered(ds->bounds_hi[k]);
-        ext[k] = hi > lo[k] ? hi - lo[k] : 1.0;
+        const double l = from_ordered(ds->bounds_lo[k]), h = from_ordered(ds->bounds_hi[k]);
+        lo[k] = (float)l;
+        const float e = (float)(h - l);
+        inv[k] = e > 0.0f ? 1.0f / e : 1.0f;
     }
     for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < F; f += (int64_t)gridDim.x * blockDim.x) {
         Box<T> bx = box[f];
-        double c[3] = {0.5 * ((double)bx.lo.x + (double)bx.hi.x), 0.5 * ((double)bx.lo.y + (double)bx.hi.y),
-                       0.5 * ((double)bx.lo.z + (double)bx.hi.z)};
+        const float c[3] = {(float)(T(0.5) * (bx.lo.x + bx.hi.x)), (float)(T(0.5) * (bx.lo.y + bx.hi.y)),
+                            (float)(T(0.5) * (bx.lo.z + bx.hi.z))};
         unsigned long long q[3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            double u = (c[k] - lo[k]) / ext[k];
-            u = fmin(fmax(u, 0.0), 1.0);
+            const float u = fminf(fmaxf((c[k] - lo[k]) * inv[k], 0.0f), 1.0f);
             q[k] = (unsigned long long)(u * scale);
         }
         unsigned long long m = (spread3(q[0]) << 2) | (spread3(q[1]) << 1) | spread3(q[2]);
@@ -251,7 +254,8 @@ __global__ void k_refit(int n, const int *__restrict__ parent, const int2 *__res
                 atomicOr(&ds->err, ERR_STACK);
                 break;
             }
-            __threadfence();
+            // the first child to arrive stops; the second sees both boxes: leaf boxes come from
+            // an earlier launch, an inner node's box was written and fenced before its counter
             if (atomicAdd(&visit[node], 1u) == 0u) break;
             int2 ch = child[node];
             vec4_t<T> alo = ld_cg<T>(&node_box[ch.x].lo), ahi = ld_cg<T>(&node_box[ch.x].hi);
@@ -260,6 +264,7 @@ __global__ void k_refit(int n, const int *__restrict__ parent, const int2 *__res
             u.lo.x = tmin(alo.x, blo.x); u.lo.y = tmin(alo.y, blo.y); u.lo.z = tmin(alo.z, blo.z); u.lo.w = T(0);
             u.hi.x = tmax(ahi.x, bhi.x); u.hi.y = tmax(ahi.y, bhi.y); u.hi.z = tmax(ahi.z, bhi.z); u.hi.w = T(0);
             node_box[node] = u;
+            __threadfence();   // this box before the parent's counter
             node = parent[node];
         }
     }
@@ -269,6 +274,17 @@ template <typename T>
 __device__ __forceinline__ bool overlap(const vec4_t<T> &alo, const vec4_t<T> &ahi, const vec4_t<T> &blo,
                                         const vec4_t<T> &bhi) {
     return alo.x <= bhi.x && blo.x <= ahi.x && alo.y <= bhi.y && blo.y <= ahi.y && alo.z <= bhi.z && blo.z <= ahi.z;
+}
+
+// Each leaf's triangle in leaf order: its vertex indices and, in w, the triangle's index.
+__global__ void k_leaf_tri(const uint32_t *__restrict__ perm, const int4 *__restrict__ tri4, int64_t n,
+                           int4 *__restrict__ leaf_tri) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t t = perm[i];
+        int4 v = tri4[t];
+        v.w = (int)t;
+        leaf_tri[i] = v;
+    }
 }
 
 __device__ __forceinline__ bool share_vertex(int4 a, int4 b) {
@@ -317,7 +333,7 @@ constexpr int kChunk = 32;
 template <typename T, int kPass, bool kOneWalk = false>
 __global__ void __launch_bounds__(kThreads) k_traverse(int n, const int2 *__restrict__ range,
                                                        const Box<T> *__restrict__ node_box,
-                                                       const uint32_t *__restrict__ perm, const int4 *__restrict__ tri4,
+                                                       const int4 *__restrict__ leaf_tri,
                                                        const int32_t *__restrict__ leaf_group,
                                                        const int2 *__restrict__ group_range, int mode,
                                                        uint32_t *__restrict__ count,
@@ -340,8 +356,8 @@ __global__ void __launch_bounds__(kThreads) k_traverse(int n, const int2 *__rest
         int chunk = -1;
         const unsigned long long out = kPass == 1 ? offset[s] : 0ull;
         if (lo <= hi) {
-            const uint32_t qi = perm[s];
-            const int4 tq = tri4[qi];
+            const int4 tq = leaf_tri[s];
+            const uint32_t qi = (uint32_t)tq.w;
             const Box<T> qb = node_box[n - 1 + s];
             int node = kOneWalk ? get_link<T>(node_box[n - 1 + lo - 1].hi.w) : 0;
             for (int steps = 0; node >= 0; ++steps) {
@@ -349,6 +365,10 @@ __global__ void __launch_bounds__(kThreads) k_traverse(int n, const int2 *__rest
                     atomicOr(&ds->err, ERR_STACK);
                     break;
                 }
+                // a leaf's triangle is loaded with its box (leaves are the nodes from n - 1 on), so
+                // the shared-vertex test waits for no further load
+                int4 lt = make_int4(-1, -1, -1, -1);
+                if (node >= n - 1) lt = leaf_tri[node - (n - 1)];
                 const Box<T> nb = node_box[node];
                 const int2 r = range[node];
                 if (kOneWalk && r.x > hi) break;
@@ -358,8 +378,8 @@ __global__ void __launch_bounds__(kThreads) k_traverse(int n, const int2 *__rest
                     if (left >= 0) {
                         next = left;
                     } else {
-                        const uint32_t tj = perm[node - (n - 1)];
-                        if (!share_vertex(tq, tri4[tj])) {
+                        const uint32_t tj = (uint32_t)lt.w;
+                        if (!share_vertex(tq, lt)) {
                             const int2 pr = make_int2((int)min(qi, tj), (int)max(qi, tj));
                             if (kPass == 0) {
                                 if (cnt < (uint32_t)kSpill) {
@@ -517,6 +537,9 @@ cudaError_t build_candidates(Ctx &c, const vec4_t<T> *x0, const vec4_t<T> *x1, B
                    (int2 *)c.group_range.p);
         }
         launch(c, k_karras, dim3(grid_for(n - 1, kThreads)), dim3(kThreads), key, n, child, parent, range);
+        TTIE_CUDA_TRY(ensure(c, c.leaf_tri, (size_t)n * sizeof(int4)));
+        launch(c, k_leaf_tri, dim3(g), dim3(kThreads), (const uint32_t *)perm, (const int4 *)c.tri4.p, n,
+               (int4 *)c.leaf_tri.p);
         c.tree_leaves = n;
     }
     // a refit-only build keeps the hierarchy (and leaf order) of the last full build: any
@@ -539,12 +562,12 @@ cudaError_t build_candidates(Ctx &c, const vec4_t<T> *x0, const vec4_t<T> *x1, B
         TTIE_CUDA_TRY(ensure(c, c.ovf_head, (size_t)n * sizeof(int)));
         TTIE_CUDA_TRY(cudaMemsetAsync(&c.ds->ovf_cursor, 0, sizeof(unsigned long long), c.stream));
         launch(c, k_traverse<T, 0, true>, dim3(g), dim3(kThreads), n, (const int2 *)range, (const Box<T> *)nbox,
-               (const uint32_t *)perm, (const int4 *)c.tri4.p, (const int32_t *)c.leaf_group.p,
+               (const int4 *)c.leaf_tri.p, (const int32_t *)c.leaf_group.p,
                (const int2 *)c.group_range.p, mode, cnt, (const unsigned long long *)nullptr, (int2 *)c.spill.p,
                (int2 *)nullptr, c.ds, (int2 *)c.ovf_pool.p, (int *)c.ovf_next.p, (int *)c.ovf_head.p, pool_chunks);
     } else {
         launch(c, k_traverse<T, 0>, dim3(g), dim3(kThreads), n, (const int2 *)range, (const Box<T> *)nbox,
-               (const uint32_t *)perm, (const int4 *)c.tri4.p, (const int32_t *)c.leaf_group.p,
+               (const int4 *)c.leaf_tri.p, (const int32_t *)c.leaf_group.p,
                (const int2 *)c.group_range.p, mode, cnt, (const unsigned long long *)nullptr, (int2 *)c.spill.p,
                (int2 *)nullptr, c.ds, (int2 *)nullptr, (int *)nullptr, (int *)nullptr, 0ull);
     }
@@ -571,7 +594,7 @@ cudaError_t build_candidates(Ctx &c, const vec4_t<T> *x0, const vec4_t<T> *x1, B
                    (int2 *)out_pairs.p);
         else
             launch(c, k_traverse<T, 1>, dim3(g), dim3(kThreads), n, (const int2 *)range, (const Box<T> *)nbox,
-                   (const uint32_t *)perm, (const int4 *)c.tri4.p, (const int32_t *)c.leaf_group.p,
+                   (const int4 *)c.leaf_tri.p, (const int32_t *)c.leaf_group.p,
                    (const int2 *)c.group_range.p, mode, cnt, (const unsigned long long *)off, (int2 *)nullptr,
                    (int2 *)out_pairs.p, c.ds, (int2 *)nullptr, (int *)nullptr, (int *)nullptr, 0ull);
     }

@@ -130,7 +130,7 @@ cudaError_t ensure(Ctx &c, Buf &b, size_t bytes);   // grow-only, contents not k
     X(el_edges) X(el_rest) X(el_anchor) X(el_target) X(el_sfac) X(el_afac) X(defer2)          \
     X(inst) X(ls_cand) X(inst_acc) X(inst_ids) X(ab) X(ls_flag)  \
     X(ls_off) X(ls_scalars) X(hgrid) X(hkey) X(hkey2) X(hval) X(hval2) X(hcnt) X(hoff)   \
-    X(ovf_pool) X(ovf_next) X(ovf_head)
+    X(ovf_pool) X(ovf_next) X(ovf_head) X(leaf_tri)
 
 struct Ctx {
     ttie_params prm;
