@@ -36,7 +36,11 @@ UNIT = "pair evals/s"
 L2_FLUSH_BYTES = 256 << 20   # larger than the 129 MB L2
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant kernel, from one ncu
 # capture of the kernels as they are now (None until one is taken)
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    # k_pcg_resident<float, no Chebyshev, 1024 threads>, first Newton step of the noisy sphere,
+    # one launch (200 iterations): dram__bytes_read.sum + dram__bytes_write.sum
+    ("noisy_sphere", "pcg"): 36139574000,
+}
 
 # Algorithmic bytes (the minimum an implementation moves, FP32):
 B_CANDIDATE = 104.0      # pair ids 8 + 2 x (indices 12 + coordinates 36)
@@ -352,6 +356,15 @@ def main():
         return {"total_ms": tot, "pairs": pairs, "active": active, "last": last,
                 "stage_ms_per_step": {k: v / steps for k, v in stage.items()}, "kernel_ms": ms}
 
+    def step_launches(info):
+        """Kernels the step launched per stage; for batched instances also the PCG schedule."""
+        out = {"launches_per_stage": dict(zip(["build", "eval", "assemble", "pcg", "line_search"],
+                                              info["stage_launches"]))}
+        if info.get("inst_threads"):
+            out["pcg_schedule"] = {"threads": info["inst_threads"], "blocks_per_sm": info["inst_blocks_per_sm"],
+                                   "order": "largest first" if info["inst_order"] == 0 else "as numbered"}
+        return out
+
     def certify(m, x, mode):
         """The oracle's exact test on an end state (intersecting pairs; 0 = intersection-free),
         with its brute-force candidate list where that fits the bench's time."""
@@ -508,6 +521,7 @@ def main():
                     "pcg_iters": lc["pcg_iters"], "bsr_rows": lc["n_rows"], "bsr_blocks": lc["nnzb"],
                     "stage_ms_per_step": t["stage_ms_per_step"],
                     "roofline_pcg": rp, "roofline_pair_eval": rc, "roofline_assembly": ra, "roofline_eval": re})
+                entry.update(step_launches(lc))
                 if pc == 0 and not args.no_fp64_form:
                     f = fp64_form(mc, mdc, bc, ks)
                     f["speedup_of_fp32_form"] = f["ms_per_step"] / entry["ms_per_step"]
@@ -660,6 +674,7 @@ def main():
                        "pcg_precond": args.pcg_precond, "pcg_kernel": args.pcg_kernel, "traversal": args.traversal,
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "stage_ms_per_step": main_t["stage_ms_per_step"],
+            **step_launches(last),
             "active_pairs_per_s": main_t["active"] / (total_ms / 1e3),
             "roofline": roofline,
             "roofline_pair_eval": r_cls,

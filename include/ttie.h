@@ -313,6 +313,14 @@ typedef struct {
     int pcg_kernel;              /* the PCG kernels that ran: TTIE_PCG_KERNEL_RESIDENT,
                                     _STREAMED or _RESIDENT_UNCACHED; 0 when no PCG ran or with
                                     batched instances (their own solver)                      */
+    int64_t stage_launches[5];   /* kernels launched by the step per stage: build, evaluation,
+                                    assembly, PCG, line search (graph replays count each of
+                                    their kernels)                                            */
+    int inst_threads;            /* batched instances: the PCG schedule that ran (threads per
+                                    block, blocks per SM requested, instance order 0 largest
+                                    first / 1 as numbered); 0 otherwise                        */
+    int inst_blocks_per_sm;
+    int inst_order;
 } ttie_step_info;
 
 /*
@@ -410,6 +418,11 @@ ttie_status ttie_get_direction(ttie_ctx *ctx, void *d_out);
  * sign in 128/256-bit integers where the coordinates' span fits; otherwise the FP64 filter
  * and its zero certificates); then signs decided by the last pass's exact arithmetic. */
 ttie_status ttie_get_filter_stats(ttie_ctx *ctx, int64_t *out3);
+
+/* sizeof of the public structs, so that a binding can check its layouts against this build:
+ * out5 (host, 5 entries) = ttie_params, ttie_bsr_view, ttie_step_info, ttie_elastic,
+ * ttie_solve_info.  Needs no GPU and no context. */
+void ttie_struct_sizes(int64_t *out5);
 
 /* ---- solve without allocating -------------------------------------------------- */
 

@@ -357,6 +357,17 @@ static float ms_between(Ctx &c, int a, int b) {
 
 static void mark(Ctx &c, int i) {
     if (c.prm.profile) cudaEventRecord(c.ev[i], c.stream);
+    if (i < 6) c.mark_launch[i] = c.n_launch;
+}
+
+// per-stage launch counts (and, batched, the PCG schedule) into a step's info
+static void stage_info(const Ctx &c, ttie_step_info &inf, bool batched_step) {
+    for (int k = 0; k < 5; ++k) inf.stage_launches[k] = (int64_t)(c.mark_launch[k + 1] - c.mark_launch[k]);
+    if (batched_step) {
+        inf.inst_threads = c.prm.inst_threads > 0 ? c.prm.inst_threads : c.inst_tuned[0];
+        inf.inst_blocks_per_sm = c.inst_tuned[1];
+        inf.inst_order = c.inst_tuned[2];
+    }
 }
 
 template <typename T> static cudaError_t negate_copy(Ctx &c, const T *a, T *b, int64_t n) {
@@ -424,6 +435,7 @@ static ttie_status newton_impl(Ctx &c, T *x, ttie_step_info *info) {
         inf.ms_build = ms_between(c, 0, 1);
         inf.ms_eval = ms_between(c, 1, 2);
         inf.ms_classify = c.n_cand > 0 ? ms_between(c, 6, 7) : 0.f;
+        stage_info(c, inf, false);
         if (info) *info = inf;
         return TTIE_OK;
     }
@@ -541,6 +553,7 @@ static ttie_status newton_impl(Ctx &c, T *x, ttie_step_info *info) {
     inf.ms_line_search = ms_between(c, 4, 5);
     inf.ms_classify = c.n_cand > 0 ? ms_between(c, 6, 7) : 0.f;
     inf.ms_pcg_kernel = ms_between(c, 8, 9);
+    stage_info(c, inf, false);
     if (info) *info = inf;
     return TTIE_OK;
 }
@@ -587,6 +600,7 @@ static ttie_status newton_batched(Ctx &c, T *x, ttie_step_info *info) {
         inf.ms_build = ms_between(c, 0, 1);
         inf.ms_eval = ms_between(c, 1, 2);
         inf.ms_classify = c.n_cand > 0 ? ms_between(c, 6, 7) : 0.f;
+        stage_info(c, inf, true);
         if (info) *info = inf;
         return TTIE_OK;
     }
@@ -694,6 +708,7 @@ static ttie_status newton_batched(Ctx &c, T *x, ttie_step_info *info) {
     inf.ms_line_search = ms_between(c, 4, 5);
     inf.ms_classify = c.n_cand > 0 ? ms_between(c, 6, 7) : 0.f;
     inf.ms_pcg_kernel = ms_between(c, 8, 9);
+    stage_info(c, inf, true);
     if (info) *info = inf;
     return TTIE_OK;
 }
@@ -965,6 +980,15 @@ ttie_status ttie_get_direction(ttie_ctx *h, void *d_out) {
     CK(cudaMemcpyAsync(d_out, c.dir.p, (size_t)c.V * 3 * es, cudaMemcpyDeviceToDevice, c.stream), "ttie_get_direction");
     CK(cudaStreamSynchronize(c.stream), "ttie_get_direction");
     return TTIE_OK;
+}
+
+void ttie_struct_sizes(int64_t *out5) {
+    if (!out5) return;
+    out5[0] = (int64_t)sizeof(ttie_params);
+    out5[1] = (int64_t)sizeof(ttie_bsr_view);
+    out5[2] = (int64_t)sizeof(ttie_step_info);
+    out5[3] = (int64_t)sizeof(ttie_elastic);
+    out5[4] = (int64_t)sizeof(ttie_solve_info);
 }
 
 ttie_status ttie_get_filter_stats(ttie_ctx *h, int64_t *out3) {

@@ -171,6 +171,7 @@ struct Ctx {
     bool time_kernels = false;         // profile: events around the classification / PCG kernels
     int64_t tree_leaves = -1;          // leaves of the hierarchy in the BVH buffers (-1: none)
     int inst_tuned[4] = {0, 0, 0, 0};  // batched PCG schedule: threads, blocks per SM, order (0: not tuned)
+    unsigned long long mark_launch[6] = {};   // n_launch at the step's stage marks
     // elastic term of the quasi-static simulation (ttie_set_elastic)
     bool have_elastic = false;
     int64_t el_n_edges = 0, el_n_anchors = 0, el_V = -1;

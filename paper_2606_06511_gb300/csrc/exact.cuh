@@ -195,6 +195,35 @@ __device__ __forceinline__ int i256_sign(const I256 &a) {
     return (a.w[0] | a.w[1] | a.w[2] | a.w[3]) ? 1 : 0;
 }
 
+// The 256-bit evaluation of orient3d_f32_int (coordinates spanning 40 to 79 bits), out of
+// line so that the common 128-bit path stays small.
+__device__ __noinline__ int orient3d_i256(const unsigned (&s)[4][3], const int (&ex)[4][3], const float *const (&P)[4],
+                                          int lo) {
+    __int128 X[4][3];
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const int sh = ex[p][k] - lo;
+            __int128 v = sh >= 0 ? ((__int128)s[p][k] << sh) : (__int128)(s[p][k] >> (-sh));
+            if (__float_as_uint(P[p][k]) >> 31) v = -v;
+            X[p][k] = v;
+        }
+    I256 e1[3], e2[3], f[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        e1[k] = i256_from(X[1][k] - X[0][k]);
+        e2[k] = i256_from(X[2][k] - X[0][k]);
+        f[k] = i256_from(X[3][k] - X[0][k]);
+    }
+    // det = e1 . (e2 x f)
+    const I256 mx = i256_add(i256_mul(e2[1], f[2]), i256_neg(i256_mul(e2[2], f[1])));
+    const I256 my = i256_add(i256_mul(e2[2], f[0]), i256_neg(i256_mul(e2[0], f[2])));
+    const I256 mz = i256_add(i256_mul(e2[0], f[1]), i256_neg(i256_mul(e2[1], f[0])));
+    const I256 det = i256_add(i256_add(i256_mul(e1[0], mx), i256_mul(e1[1], my)), i256_mul(e1[2], mz));
+    return i256_sign(det);
+}
+
 // Sign of det[b - a, c - a, d - a] for float32 points, in integer arithmetic.  Each coordinate
 // is +-s 2^e with s < 2^24; scaled by 2^-lo (lo: the smallest exponent of a lowest set bit
 // among the twelve) all are integers, below 2^(hi - lo + 1) with hi the largest exponent of a
@@ -255,29 +284,7 @@ __device__ __noinline__ bool orient3d_f32_int(const float *a, const float *b, co
         sign = (det > 0) - (det < 0);
         return true;
     }
-    __int128 X[4][3];
-#pragma unroll
-    for (int p = 0; p < 4; ++p)
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            const int sh = ex[p][k] - lo;
-            __int128 v = sh >= 0 ? ((__int128)s[p][k] << sh) : (__int128)(s[p][k] >> (-sh));
-            if (__float_as_uint(P[p][k]) >> 31) v = -v;
-            X[p][k] = v;
-        }
-    I256 e1[3], e2[3], f[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        e1[k] = i256_from(X[1][k] - X[0][k]);
-        e2[k] = i256_from(X[2][k] - X[0][k]);
-        f[k] = i256_from(X[3][k] - X[0][k]);
-    }
-    // det = e1 . (e2 x f)
-    const I256 mx = i256_add(i256_mul(e2[1], f[2]), i256_neg(i256_mul(e2[2], f[1])));
-    const I256 my = i256_add(i256_mul(e2[2], f[0]), i256_neg(i256_mul(e2[0], f[2])));
-    const I256 mz = i256_add(i256_mul(e2[0], f[1]), i256_neg(i256_mul(e2[1], f[0])));
-    const I256 det = i256_add(i256_add(i256_mul(e1[0], mx), i256_mul(e1[1], my)), i256_mul(e1[2], mz));
-    sign = i256_sign(det);
+    sign = orient3d_i256(s, ex, P, lo);
     return true;
 }
 

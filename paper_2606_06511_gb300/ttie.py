@@ -66,10 +66,14 @@ class StepInfo(ctypes.Structure):
                 ("ms_assemble", ctypes.c_float), ("ms_pcg", ctypes.c_float), ("ms_line_search", ctypes.c_float),
                 ("ms_classify", ctypes.c_float), ("ms_pcg_kernel", ctypes.c_float),
                 ("pcg_block_iters", ctypes.c_int64), ("pcg_row_iters", ctypes.c_int64),
-                ("energy_elastic", ctypes.c_double), ("pcg_kernel", ctypes.c_int)]
+                ("energy_elastic", ctypes.c_double), ("pcg_kernel", ctypes.c_int),
+                ("stage_launches", ctypes.c_int64 * 5), ("inst_threads", ctypes.c_int),
+                ("inst_blocks_per_sm", ctypes.c_int), ("inst_order", ctypes.c_int)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d["stage_launches"] = list(self.stage_launches)
+        return d
 
 
 class Elastic(ctypes.Structure):
@@ -112,6 +116,7 @@ _SIGS = {
                                        ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]),
     "ttie_get_direction": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "ttie_get_filter_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)]),
+    "ttie_struct_sizes": (None, [ctypes.POINTER(ctypes.c_int64)]),
     "ttie_get_launch_count": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)]),
     "ttie_hvp": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     "ttie_dual_gradients": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),

@@ -110,3 +110,13 @@ def test_no_device_reports_cuda_error(lib):
     h = ctypes.c_void_p()
     p = ttie.default_params()
     assert lib.ttie_create(ctypes.byref(h), ctypes.byref(p), None) == ttie.TTIE_ERR_CUDA
+
+
+def test_struct_layouts_match_the_library(lib):
+    """The binding's ctypes structs have the sizes of the C structs of this build (a field
+    missing, added or reordered in one of them changes a size or an offset)."""
+    from paper_2606_06511_gb300 import ttie
+    out = (ctypes.c_int64 * 5)()
+    lib.ttie_struct_sizes(out)
+    assert list(out) == [ctypes.sizeof(ttie.Params), ctypes.sizeof(ttie.BsrView), ctypes.sizeof(ttie.StepInfo),
+                         ctypes.sizeof(ttie.Elastic), ctypes.sizeof(ttie.SolveInfo)]
