@@ -104,9 +104,10 @@ typedef struct {
                              publishes its partial sums, so every block's bounded wait for
                              them runs out (about a second) and the call returns
                              TTIE_ERR_CUDA with the context still usable               */
-    int pcg_precond;      /* preconditioner of the shared-memory PCG (TTIE_PCG_*); the
-                             global-memory PCG and the batched-instance PCG always use
-                             3x3 block Jacobi                                          */
+    int pcg_precond;      /* preconditioner (TTIE_PCG_*) of the shared-memory PCG and of
+                             the batched-instance PCG (AUTO there: Chebyshev for the
+                             instances whose rows fit a block's shared memory); the
+                             global-memory and streamed PCGs use 3x3 block Jacobi      */
     int pcg_cheb_degree;  /* TTIE_PCG_CHEBYSHEV: degree k of the polynomial, 1..8 (0 = 2) */
     int traversal_mode;   /* TTIE_TRAVERSAL_*: how the LBVH walk lists candidates; both give
                              the same list in the same order                              */

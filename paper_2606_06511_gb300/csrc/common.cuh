@@ -62,6 +62,7 @@ struct Inst {
     int first, last, count;   // rows [first, last] of the system (contiguous), count of them
     int nnz;                  // 3x3 blocks of its rows
     int iters;                // PCG iterations
+    int prods;                // products with the matrix (iterations, plus the polynomial's with Chebyshev)
     double rel;               // PCG relative residual
     double gd;                // g . d after the step cap
     double e0, et, e_new;     // energy at x, at the current trial, at the accepted step
@@ -130,7 +131,7 @@ cudaError_t ensure(Ctx &c, Buf &b, size_t bytes);   // grow-only, contents not k
     X(el_edges) X(el_rest) X(el_anchor) X(el_target) X(el_sfac) X(el_afac) X(defer2)          \
     X(inst) X(ls_cand) X(inst_acc) X(inst_ids) X(ab) X(ls_flag)  \
     X(ls_off) X(ls_scalars) X(hgrid) X(hkey) X(hkey2) X(hval) X(hval2) X(hcnt) X(hoff)   \
-    X(ovf_pool) X(ovf_next) X(ovf_head) X(leaf_tri)
+    X(ovf_pool) X(ovf_next) X(ovf_head) X(leaf_tri) X(inst_cd) X(inst_crr)
 
 struct Ctx {
     ttie_params prm;

@@ -156,6 +156,7 @@ template <typename T> struct InstPcgArgs {
     const T *bval, *rhs;          // rhs = -g on the rows
     T *x;                         // the direction d on the rows (output)
     T *r, *u, *p, *s, *w, *dinv;  // row vectors of instances kept in global memory
+    T *cd, *crr;                  // the Chebyshev preconditioner's d and D^-1 residual (global layout)
     unsigned long long *acc;      // their row partials: 3 x rows
     const double *edge;           // mean edge length per instance
     const int32_t *ids;           // the instances of this launch, in the order they are taken
@@ -165,10 +166,13 @@ template <typename T> struct InstPcgArgs {
     double mu_rel, rtol2, max_step;
     int max_it;
     long long n_rows;
+    int cheb;                     // Chebyshev preconditioner: 0 never, 1 instances in shared memory, 2 all
+    int cheb_degree;
 };
 
 template <typename T> struct InstView {
     T *x, *r, *u, *p, *s, *w, *di;
+    T *d, *rr;                    // Chebyshev: the polynomial's direction and D^-1 residual
     unsigned long long *pg, *pd, *pr;   // per-row partials of r.u, w.u, r.r (accumulator bits)
     const T *val;
     bool resident;
@@ -227,10 +231,19 @@ __device__ __forceinline__ Acc<T> rows_total(const unsigned long long *part, int
     return out[0];
 }
 
-// The PCG of instance gid by the whole block (k_pcg_instances takes the instances).
+// The PCG of instance gid by the whole block (k_pcg_instances takes the instances).  With the
+// Chebyshev preconditioner (a.cheb: every instance, or the ones whose rows sit in shared
+// memory) the first kChebWarm iterations use 3x3 block Jacobi; their CG coefficients give the
+// Lanczos estimate of lambda_max(D^-1 A), and CG restarts with M^-1 = p_k(D^-1 A) D^-1, the
+// degree-k Chebyshev polynomial on [lambda_max / kChebRatio, lambda_max] (cheb_coefficients),
+// applied by k more products per iteration.  In one block the polynomial's products need
+// only block barriers, while each iteration's reductions and barriers are what an instance's
+// solve waits on, so fewer iterations pay.
 template <typename T, int THREADS>
 __device__ __forceinline__ void inst_pcg_one(const InstPcgArgs<T> &a, int gid, int smem_bytes) {
     extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ T s_c1[kChebMaxDeg], s_c2[kChebMaxDeg], s_thi;
+    __shared__ int s_restart;
     Inst *I = a.inst + gid;
     InstView<T> v;
     v.nrow = I->count;
@@ -238,14 +251,19 @@ __device__ __forceinline__ void inst_pcg_one(const InstPcgArgs<T> &a, int gid, i
     v.r0 = I->first;
     v.b0 = a.row_ptr[v.r0];
     v.nnz = a.row_ptr[v.r0 + v.nrow] - v.b0;
-    const size_t vec_bytes = ((size_t)v.nrow * (27 * sizeof(T) + 24) + (size_t)(v.nrow + 1) * 4 + 15) / 16 * 16;
+    // resident layout: 3 accumulator words, 27 values (x r u p s w, 9 of M^-1) per row, 6 more
+    // (d, rr) when the Chebyshev preconditioner may run, the local row offsets, then the matrix
+    const int per_row = 27 + (a.cheb ? 6 : 0);
+    const size_t vec_bytes = ((size_t)v.nrow * (per_row * sizeof(T) + 24) + (size_t)(v.nrow + 1) * 4 + 15) / 16 * 16;
     const size_t mat_bytes = (size_t)v.nnz * (9 * sizeof(T) + 4);
     v.resident = vec_bytes + mat_bytes <= (size_t)smem_bytes;
+    const bool cheb = a.cheb == 2 || (a.cheb == 1 && v.resident);
     if (v.resident) {
         v.pg = (unsigned long long *)smem; v.pd = v.pg + v.nrow; v.pr = v.pd + v.nrow;
         v.x = (T *)(v.pr + v.nrow); v.r = v.x + 3 * v.nrow; v.u = v.r + 3 * v.nrow; v.p = v.u + 3 * v.nrow;
         v.s = v.p + 3 * v.nrow; v.w = v.s + 3 * v.nrow; v.di = v.w + 3 * v.nrow;
-        v.rp = (int *)(v.di + 9 * v.nrow);
+        v.d = v.di + 9 * v.nrow; v.rr = v.d + 3 * v.nrow;   // inside the layout only when a.cheb
+        v.rp = (int *)(v.di + (size_t)(per_row - 18) * v.nrow);
         T *val = (T *)(smem + vec_bytes);
         v.col = (int *)(val + (size_t)9 * v.nnz);
         for (int i = threadIdx.x; i < 9 * v.nnz; i += THREADS) val[i] = a.bval[(size_t)v.b0 * 9 + i];
@@ -255,6 +273,7 @@ __device__ __forceinline__ void inst_pcg_one(const InstPcgArgs<T> &a, int gid, i
     } else {
         const size_t o = (size_t)v.r0 * 3;
         v.x = a.x + o; v.r = a.r + o; v.u = a.u + o; v.p = a.p + o; v.s = a.s + o; v.w = a.w + o;
+        v.d = a.cd + o; v.rr = a.crr + o;
         v.di = a.dinv + (size_t)v.r0 * 9;
         v.pg = a.acc + v.r0; v.pd = a.acc + a.n_rows + v.r0; v.pr = a.acc + 2 * a.n_rows + v.r0;
         v.rp = nullptr;
@@ -306,19 +325,16 @@ __device__ __forceinline__ void inst_pcg_one(const InstPcgArgs<T> &a, int gid, i
     __syncthreads();
     const int lane = threadIdx.x & 31, sub = lane & (kInstLanes - 1);
     const unsigned gmask = ((1u << kInstLanes) - 1u) << (lane & ~(kInstLanes - 1));
-    const T rtol2 = (T)a.rtol2;
-    T rr0 = T(0), gamma_prev = T(1), alpha_prev = T(1), rr_last = T(0);
-    bool stop_next = false;
-    int it = 0;
-    while (true) {
-        // w = (A + mu I) u and the rows' w.u
+    // dst = (A + mu I) src on the instance's rows, kInstLanes lanes per row summed in a fixed
+    // order; with pd, each row's dst.src too
+    const auto product = [&](const T *src, T *dst, unsigned long long *pd) {
         for (int lr = threadIdx.x / kInstLanes; lr < v.nrow; lr += THREADS / kInstLanes) {
             T y0 = 0, y1 = 0, y2 = 0;
             const int be = inst_rowp(a, v, lr + 1);
             for (int b = inst_rowp(a, v, lr) + sub; b < be; b += kInstLanes) {
                 const int c = inst_col(a, v, b);
                 const T *m = v.val + (size_t)b * 9;
-                const T c0 = v.u[c * 3], c1 = v.u[c * 3 + 1], c2 = v.u[c * 3 + 2];
+                const T c0 = src[c * 3], c1 = src[c * 3 + 1], c2 = src[c * 3 + 2];
                 y0 += m[0] * c0 + m[1] * c1 + m[2] * c2;
                 y1 += m[3] * c0 + m[4] * c1 + m[5] * c2;
                 y2 += m[6] * c0 + m[7] * c1 + m[8] * c2;
@@ -330,15 +346,30 @@ __device__ __forceinline__ void inst_pcg_one(const InstPcgArgs<T> &a, int gid, i
                 y2 += __shfl_xor_sync(gmask, y2, o, kInstLanes);
             }
             if (sub == 0) {
-                const T w0 = y0 + mu * v.u[lr * 3], w1 = y1 + mu * v.u[lr * 3 + 1], w2 = y2 + mu * v.u[lr * 3 + 2];
-                v.w[lr * 3] = w0; v.w[lr * 3 + 1] = w1; v.w[lr * 3 + 2] = w2;
-                Acc<T> wu;
-                wu.add_prod(w0, v.u[lr * 3]);
-                wu.add_prod(w1, v.u[lr * 3 + 1]);
-                wu.add_prod(w2, v.u[lr * 3 + 2]);
-                v.pd[lr] = wu.bits();
+                const T w0 = y0 + mu * src[lr * 3], w1 = y1 + mu * src[lr * 3 + 1], w2 = y2 + mu * src[lr * 3 + 2];
+                dst[lr * 3] = w0; dst[lr * 3 + 1] = w1; dst[lr * 3 + 2] = w2;
+                if (pd) {
+                    Acc<T> wu;
+                    wu.add_prod(w0, src[lr * 3]);
+                    wu.add_prod(w1, src[lr * 3 + 1]);
+                    wu.add_prod(w2, src[lr * 3 + 2]);
+                    pd[lr] = wu.bits();
+                }
             }
         }
+    };
+    const T rtol2 = (T)a.rtol2;
+    T rr0 = T(0), gamma_prev = T(1), alpha_prev = T(1), rr_last = T(0);
+    bool stop_next = false;
+    int it = 0, prods = 0;
+    // Chebyshev: kit counts the iterations since CG (re)started; al, be the block-Jacobi ones'
+    int kit = 0;
+    bool cheb_on = false, cheb_tried = false;
+    double al[kChebWarm], be[kChebWarm];
+    while (true) {
+        // w = (A + mu I) u and the rows' w.u
+        product(v.u, v.w, v.pd);
+        ++prods;
         __syncthreads();
         Acc<T> tot[3];
         {
@@ -352,7 +383,7 @@ __device__ __forceinline__ void inst_pcg_one(const InstPcgArgs<T> &a, int gid, i
         if (stop_next || it >= a.max_it || r2 <= rtol2 * rr0 || !isfinite(r2)) break;
         T alpha, beta = T(0);
         bool ok;
-        if (it == 0) {
+        if ((cheb ? kit : it) == 0) {
             alpha = g / d;
             ok = d > T(0) && isfinite(alpha);
         } else {
@@ -369,6 +400,22 @@ __device__ __forceinline__ void inst_pcg_one(const InstPcgArgs<T> &a, int gid, i
         }
         gamma_prev = g;
         alpha_prev = alpha;
+        // the block-Jacobi iterations' coefficients; after the last of them the polynomial's
+        // (thread 0, from the same values every thread holds), and CG restarts with it
+        bool restart = false;
+        if (cheb && !cheb_tried && !stop_next && kit < kChebWarm) {
+            al[kit] = (double)alpha;
+            be[kit] = (double)beta;
+            if (kit == kChebWarm - 1 && it + 1 < a.max_it) {
+                cheb_tried = true;
+                if (threadIdx.x == 0)
+                    s_restart = cheb_coefficients<T>(al, be, a.cheb_degree, s_c1, s_c2, &s_thi) ? 1 : 0;
+                __syncthreads();
+                restart = s_restart != 0;
+            }
+        }
+        const bool cheb_now = cheb_on || restart;
+        const T thi = cheb_now ? s_thi : T(0);
         for (int lr = threadIdx.x; lr < v.nrow; lr += THREADS) {
             T rv[3];
 #pragma unroll
@@ -387,14 +434,53 @@ __device__ __forceinline__ void inst_pcg_one(const InstPcgArgs<T> &a, int gid, i
 #pragma unroll
             for (int i = 0; i < 3; ++i) {
                 const T zi = di[3 * i] * rv[0] + di[3 * i + 1] * rv[1] + di[3 * i + 2] * rv[2];
-                v.u[lr * 3 + i] = zi;
-                gp.add_prod(rv[i], zi);
+                if (cheb_now) {
+                    v.rr[lr * 3 + i] = zi;   // D^-1 r; the polynomial's first direction and y
+                    v.d[lr * 3 + i] = zi * thi;
+                    v.u[lr * 3 + i] = zi * thi;
+                } else {
+                    v.u[lr * 3 + i] = zi;
+                    gp.add_prod(rv[i], zi);
+                }
                 qp.add_prod(rv[i], rv[i]);
             }
-            v.pg[lr] = gp.bits();
+            if (!cheb_now) v.pg[lr] = gp.bits();
             v.pr[lr] = qp.bits();
         }
         ++it;
+        if (cheb_now) {
+            // u = p_k(D^-1 A) D^-1 r: rr -= D^-1 (A + mu I) d, d = c1 d + c2 rr, u += d
+            for (int j = 0; j < a.cheb_degree; ++j) {
+                __syncthreads();
+                product(v.d, v.w, nullptr);   // w is free until the next iteration's product
+                ++prods;
+                __syncthreads();
+                const T c1 = s_c1[j], c2 = s_c2[j];
+                for (int lr = threadIdx.x; lr < v.nrow; lr += THREADS) {
+                    const T *di = v.di + lr * 9;
+                    const T w0 = v.w[lr * 3], w1 = v.w[lr * 3 + 1], w2 = v.w[lr * 3 + 2];
+#pragma unroll
+                    for (int i = 0; i < 3; ++i) {
+                        const int k = lr * 3 + i;
+                        const T rri = v.rr[k] - (di[3 * i] * w0 + di[3 * i + 1] * w1 + di[3 * i + 2] * w2);
+                        v.rr[k] = rri;
+                        const T dn = c1 * v.d[k] + c2 * rri;
+                        v.d[k] = dn;
+                        v.u[k] += dn;
+                    }
+                }
+            }
+            for (int lr = threadIdx.x; lr < v.nrow; lr += THREADS) {
+                Acc<T> gp;
+#pragma unroll
+                for (int i = 0; i < 3; ++i) gp.add_prod(v.r[lr * 3 + i], v.u[lr * 3 + i]);
+                v.pg[lr] = gp.bits();
+            }
+            kit = cheb_on ? kit + 1 : 0;   // CG restarts with the polynomial
+            cheb_on = true;
+        } else {
+            ++kit;
+        }
         __syncthreads();
     }
     // g.d and max |d_r| of the instance's direction; the step cap; the direction out
@@ -428,6 +514,7 @@ __device__ __forceinline__ void inst_pcg_one(const InstPcgArgs<T> &a, int gid, i
     }
     if (threadIdx.x == 0) {
         I->iters = it;
+        I->prods = prods;
         I->rel = rr0 > T(0) ? sqrt((double)rr_last / (double)rr0) : 0.0;
         I->gd = gdt.value() * scale;
     }
@@ -554,8 +641,8 @@ __global__ void __launch_bounds__(kTotThreads) k_inst_totals(const Inst *inst, i
             ++solved;
         }
         if (I.count > 0) {
-            wb += (double)I.iters * (row_ptr[I.first + I.count] - row_ptr[I.first]);
-            wr += (double)I.iters * I.count;
+            wb += (double)I.prods * (row_ptr[I.first + I.count] - row_ptr[I.first]);
+            wr += (double)I.prods * I.count;
         }
     }
     __shared__ double s_d[7][kTotThreads];
@@ -687,8 +774,8 @@ static std::string tune_key(Ctx &c, int n_inst, long long rows) {
     for (char &ch : dev)
         if (ch == ' ' || ch == '"') ch = '_';
     char buf[256];
-    snprintf(buf, sizeof buf, "inst_pcg %s f%d n%d rows%lld", dev.c_str(), c.prm.precision == TTIE_F64 ? 64 : 32,
-             n_inst, rows);
+    snprintf(buf, sizeof buf, "inst_pcg %s f%d pc%d n%d rows%lld", dev.c_str(), c.prm.precision == TTIE_F64 ? 64 : 32,
+             c.prm.pcg_precond, n_inst, rows);
     return buf;
 }
 
@@ -735,6 +822,11 @@ template <typename T> cudaError_t instance_pcg(Ctx &c, const T *rhs, T *out) {
     TTIE_CUDA_TRY(ensure(c, c.pcg_w, n3));
     TTIE_CUDA_TRY(ensure(c, c.dinv, (size_t)(nr > 0 ? nr : 1) * 9 * sizeof(T)));
     TTIE_CUDA_TRY(ensure(c, c.inst_acc, (size_t)(nr > 0 ? nr : 1) * 3 * 8));
+    const int cheb = c.prm.pcg_precond == TTIE_PCG_CHEBYSHEV ? 2 : c.prm.pcg_precond == TTIE_PCG_AUTO ? 1 : 0;
+    if (cheb == 2) {   // instances outside shared memory keep d and rr in global memory
+        TTIE_CUDA_TRY(ensure(c, c.inst_cd, n3));
+        TTIE_CUDA_TRY(ensure(c, c.inst_crr, n3));
+    }
     TTIE_CUDA_TRY(ensure(c, c.inst_ids, (size_t)(G > 0 ? G : 1) * 4 * 2));
     // the instances with rows, in the two queue orders: largest first (by rows, then nnz), as numbered
     std::vector<Inst> h(G);
@@ -772,6 +864,10 @@ template <typename T> cudaError_t instance_pcg(Ctx &c, const T *rhs, T *out) {
     a.rtol2 = c.prm.pcg_rtol * c.prm.pcg_rtol;
     a.max_step = c.prm.max_step;
     a.max_it = c.prm.pcg_max_it;
+    a.cheb = cheb;
+    a.cheb_degree = c.prm.pcg_cheb_degree > 0 ? c.prm.pcg_cheb_degree : 2;
+    a.cd = (T *)c.inst_cd.p;
+    a.crr = (T *)c.inst_crr.p;
     a.n_rows = nr;
     if (n == 0) return cudaSuccess;
     // the schedule: a caller's block size with the tuned rest, the cache, or a timed sweep

@@ -100,4 +100,68 @@ __device__ __forceinline__ void inv3(const T *m, T mu, T *o) {
     o[6] = (T)(C * id); o[7] = (T)(-(a * h - b * g) * id); o[8] = (T)((a * e - b * d) * id);
 }
 
+// Chebyshev preconditioner (TTIE_PCG_CHEBYSHEV): block-Jacobi iterations before the estimate
+// of lambda_max(D^-1 A), the margin on that estimate, lambda_max / lambda_min of the interval
+// and the largest degree.
+constexpr int kChebWarm = 6;
+constexpr double kChebSafety = 1.1;
+constexpr double kChebRatio = 10.0;
+constexpr int kChebMaxDeg = 8;
+
+// Eigenvalues below x of the symmetric tridiagonal (diagonal dg, squared off-diagonal e2):
+// the number of negative pivots of its LDL^T factorisation shifted by x (Sturm sequence).
+__device__ __forceinline__ int sturm_below(const double *dg, const double *e2, int m, double x) {
+    int below = 0;
+    double q = 1.0;
+    for (int i = 0; i < m; ++i) {
+        q = dg[i] - x - (i ? e2[i - 1] / q : 0.0);
+        if (q == 0.0) q = 1e-300;
+        below += q < 0.0;
+    }
+    return below;
+}
+
+// From the first kChebWarm CG coefficients (al[j], be[j]: alpha and beta of iteration j; be[0]
+// unused), the Lanczos tridiagonal of D^-1 A: diagonal 1/al[j] + be[j]/al[j-1], off-diagonal
+// sqrt(be[j+1])/al[j].  Its largest eigenvalue (a lower bound of lambda_max, by bisection on
+// the Sturm count from its Gershgorin bound) times kChebSafety is the interval's top; the
+// Chebyshev iteration y = p_k(D^-1 A) D^-1 v on [top / kChebRatio, top] then runs
+//   rr = D^-1 v,  d = rr / theta,  y = d;  for j < k: rr -= D^-1 A d,
+//   d = c1[j] d + c2[j] rr,  y += d
+// with theta, delta the interval's centre and half-width, sigma = theta / delta,
+// rho_0 = 1 / sigma, rho_{j+1} = 1 / (2 sigma - rho_j), c1[j] = rho_{j+1} rho_j and
+// c2[j] = 2 rho_{j+1} / delta.  Same inputs in every block, same coefficients.  False (keep
+// block Jacobi) when a coefficient is not positive and finite.
+template <typename T>
+__device__ __noinline__ bool cheb_coefficients(const double *al, const double *be, int deg, T *c1, T *c2, T *theta_inv) {
+    double dg[kChebWarm], e2[kChebWarm];
+    for (int j = 0; j < kChebWarm; ++j) {
+        if (!(al[j] > 0.0) || !isfinite(al[j]) || (j > 0 && (!(be[j] > 0.0) || !isfinite(be[j])))) return false;
+        dg[j] = 1.0 / al[j] + (j ? be[j] / al[j - 1] : 0.0);
+        if (j > 0) e2[j - 1] = be[j] / (al[j - 1] * al[j - 1]);
+    }
+    double hi = 0.0;
+    for (int i = 0; i < kChebWarm; ++i)
+        hi = fmax(hi, dg[i] + (i ? sqrt(e2[i - 1]) : 0.0) + (i + 1 < kChebWarm ? sqrt(e2[i]) : 0.0));
+    if (!(hi > 0.0) || !isfinite(hi)) return false;
+    double lo = 0.0;
+    for (int s = 0; s < 60; ++s) {
+        const double mid = 0.5 * (lo + hi);
+        if (sturm_below(dg, e2, kChebWarm, mid) < kChebWarm) lo = mid;
+        else hi = mid;
+    }
+    const double top = hi * kChebSafety, bot = top / kChebRatio;
+    const double th = 0.5 * (top + bot), de = 0.5 * (top - bot), sig = th / de;
+    double rho = 1.0 / sig;
+    for (int j = 0; j < deg; ++j) {
+        const double rn = 1.0 / (2.0 * sig - rho);
+        c1[j] = (T)(rn * rho);
+        c2[j] = (T)(2.0 * rn / de);
+        rho = rn;
+    }
+    *theta_inv = (T)(1.0 / th);
+    return true;
+}
+
+
 }  // namespace ttie

@@ -39,10 +39,15 @@ def _instance(m, vo, to, k):
     return ti.Mesh(x.copy(), tri.astype(np.int32), np.zeros(len(tri), np.int32))
 
 
-def test_batched_direction_is_each_instance_solution(ttie, batch):
+@pytest.mark.parametrize("precond", ["auto", "block_jacobi", "chebyshev"])
+def test_batched_direction_is_each_instance_solution(ttie, batch, precond):
+    """Each instance's direction against a dense solve of its own oracle system, with each
+    preconditioner of the batched PCG (AUTO: Chebyshev for instances in shared memory)."""
     m, vo, to = batch
     x, tri, grp = _dev(m, torch.float64)
-    prm = dict(precision=ttie.F64, pair_mode=MODE_INTRA, pcg_rtol=1e-9, pcg_max_it=4000, max_step=1.0)
+    pc = {"auto": ttie.PCG_AUTO, "block_jacobi": ttie.PCG_BLOCK_JACOBI, "chebyshev": ttie.PCG_CHEBYSHEV}[precond]
+    prm = dict(precision=ttie.F64, pair_mode=MODE_INTRA, pcg_rtol=1e-9, pcg_max_it=4000, max_step=1.0,
+               pcg_precond=pc)
     ctx = ttie.Context(**prm)
     ctx.build_bvh(x, tri, grp)
     info = ctx.newton_step(x.clone())
@@ -150,13 +155,16 @@ def test_batched_block_size_does_not_change_results(ttie, batch):
         assert torch.equal(o, outs[0])
 
 
-def test_batched_large_instances_in_global_memory(ttie):
+@pytest.mark.parametrize("precond", ["auto", "chebyshev"])
+def test_batched_large_instances_in_global_memory(ttie, precond):
     """Instances too large for one block's shared memory keep their PCG vectors and matrix rows
-    in global memory; the step still equals stepping each instance alone."""
+    in global memory (block Jacobi under AUTO; the Chebyshev polynomial's vectors in global
+    memory too when asked for); the step still equals stepping each instance alone."""
     m, vo, to = ti.ellipsoid_batch(2, seed=7, f_min=12000, f_max=16000)
     x, tri, grp = _dev(m, torch.float64)
     prm = dict(precision=ttie.F64, pcg_rtol=1e-9, pcg_max_it=4000)
-    ctx = ttie.Context(pair_mode=MODE_INTRA, **prm)
+    ctx = ttie.Context(pair_mode=MODE_INTRA, pcg_precond=ttie.PCG_AUTO if precond == "auto" else ttie.PCG_CHEBYSHEV,
+                       **prm)
     ctx.build_bvh(x, tri, grp)
     info = ctx.newton_step(x)
     # FP64: 244 B per row and 76 B per 3x3 block; an instance needs more than a block's 220 KB

@@ -112,6 +112,30 @@ def test_exact_zeros_settled_before_expansions(ttie):
     assert st["fp64"] > 0 and st["exact"] == 0, st
 
 
+@pytest.mark.parametrize("exact_only", [0, 1, 2])
+def test_wide_coordinate_span_bit_exact(ttie, exact_only):
+    """Triangles whose coordinates span about 60 binary orders (1e-17 next to 1: the lat-long
+    vertices at cos(pi/2) and sin(pi), not snapped), coplanar and crossing by construction:
+    signs whose integer evaluation needs the 256-bit path, and exact zeros among them.  The
+    intersecting set equals the exact oracle's with the filters, with every sign exact, and with
+    expansion arithmetic only."""
+    from ttie_inputs.meshes import Mesh, concat
+    m1 = ti.ellipsoid(12, (1.0, 0.8, 0.6))
+    m2 = ti.ellipsoid(8, (0.7, 0.7, 0.9))
+    m = concat([m1, Mesh(m2.x + np.array([0.0, 0.0, 0.5]), m2.tri, m2.group)]).as_f32()
+    tiny = np.abs(m.x[m.x != 0]).min()
+    assert tiny < 1e-15   # the span the 128-bit evaluation cannot hold
+    x, tri, grp = _dev(m)
+    ctx = _ctx(ttie, "self", exact_only=exact_only)
+    ctx.build_bvh(x, tri, grp)
+    E, n_act = ctx.eval_pairs(x, ttie.EVAL_E)
+    pairs = O.candidate_pairs(m.x, m.tri, m.group, "self")
+    ev = O.evaluate(m.x, m.tri, pairs)
+    act_pairs, _, _ = ctx.get_active(with_derivatives=False)
+    assert n_act == int(ev.active.sum()) > 0
+    assert pair_set(act_pairs.cpu().numpy()) == pair_set(pairs[ev.active])
+
+
 def _match(ctx, pairs, ev):
     ap, tc, dtc = ctx.get_active()
     ap = ap.cpu().numpy().astype(np.int64)
