@@ -2,6 +2,8 @@
 // (inverse diagonal blocks, first residual and preconditioned vector, the block-resident
 // kernel's row partition), the persistent global-memory kernel and the block-resident kernel
 // (block-Jacobi or Chebyshev preconditioner), and their host entry points.
+#include <algorithm>
+
 #include "common.cuh"
 #include "pcg_common.cuh"
 #include "reduce.cuh"
@@ -550,7 +552,6 @@ __device__ __forceinline__ void block_times(const T *m, T v0, T v1, T v2, T &y0,
     y1 += m[3] * v0 + m[4] * v1 + m[5] * v2;
     y2 += m[6] * v0 + m[7] * v1 + m[8] * v2;
 }
-
 template <typename T> struct ResidentView {
     T *x, *r, *u, *p, *s, *w, *di;   // 3 (9 for di) values per local row
     int *rp;                          // local row offsets (nrow + 1)
@@ -614,73 +615,101 @@ __device__ __forceinline__ Acc<T> resident_product(const PcgArgs<T> &a, const Re
         }
         __syncthreads();
     }
-    const int lane = threadIdx.x & 31, sub = lane & (kLanesPerRow - 1);
-    const unsigned gmask = 0xffu << (lane & ~(kLanesPerRow - 1));
+    // lanes per row: 2, 4, 16 and 32 measured slower (noisy sphere, 200 iterations: 40.7, 33.1,
+    // 37.5 and 51.0 ms against 18.4 ms with fixed turns)
+    constexpr int LPR = kLanesPerRow;
+    const int lane = threadIdx.x & 31, sub = lane & (LPR - 1);
+    const unsigned gmask = ((1u << LPR) - 1u) << (lane & ~(LPR - 1));
     Acc<T> wu;
-    for (int lr0 = threadIdx.x / kLanesPerRow; lr0 < v.nrow; lr0 += THREADS / kLanesPerRow) {
-        const int lr = rev ? v.nrow - 1 - lr0 : lr0;
-        if (!v.cached && lane == 0) {
-            // the warp's rows kPrefetchWaves waves on, [w0, w1) in loop order, [ra, rb) local
-            const int w0 = lr0 + kPrefetchWaves * (THREADS / kLanesPerRow);
-            if (w0 < v.nrow) {
-                const int w1 = min(w0 + 32 / kLanesPerRow, v.nrow);
-                const int ra = rev ? v.nrow - w1 : w0, rb = rev ? v.nrow - w0 : w1;
-                prefetch_l2(a.bval + (size_t)(v.b_begin + v.rp[ra]) * 9, a.bval + (size_t)(v.b_begin + v.rp[rb]) * 9);
-                prefetch_l2(a.col_idx + v.b_begin + v.rp[ra], a.col_idx + v.b_begin + v.rp[rb]);
-            }
-        }
-        T y0 = 0, y1 = 0, y2 = 0;
-        const int be = v.rp[lr + 1];
-        if (v.gathered) {
-            for (int b = v.rp[lr] + sub; b < be; b += kLanesPerRow)
-                block_times(v.val + (size_t)b * 9, v.gu[3 * b], v.gu[3 * b + 1], v.gu[3 * b + 2], y0, y1, y2);
+    // Streamed rows (1024 threads) are handed out to warps as they finish, 32 / LPR
+    // consecutive rows at a time in loop order, not dealt in fixed turns: the rows' costs
+    // differ, and every warp waits for the slowest one at the reduction that follows (noisy
+    // sphere, 200 iterations: 18.1 -> 15.1 ms).  Rows in shared memory (512 threads) keep the
+    // fixed turns, whose products are too short to repay the counter's two barriers (cloth:
+    // 1.90 against 2.04 ms for 85 iterations).
+    constexpr bool kHandOut = THREADS >= 1024;
+    __shared__ int s_next_row;
+    if (kHandOut) {
+        __syncthreads();   // the previous product's last reads of the counter are done
+        if (threadIdx.x == 0) s_next_row = 0;
+        __syncthreads();
+    }
+    for (int turn = 0;; ++turn) {
+        int wbase;
+        if (kHandOut) {
+            wbase = 0;
+            if (lane == 0) wbase = atomicAdd(&s_next_row, 32 / LPR);
+            wbase = __shfl_sync(0xffffffffu, wbase, 0);
         } else {
-            // matrix rows cached, u not gathered: up to four of the lane's blocks at a time,
-            // every load in flight before any tag is checked (a check is a branch on the value)
-            constexpr int U = 4;
-            for (int b0 = v.rp[lr] + sub; b0 < be; b0 += U * kLanesPerRow) {
-                int cc[U];
+            wbase = turn * (THREADS / LPR) + (threadIdx.x >> 5) * (32 / LPR);
+        }
+        if (wbase >= v.nrow) break;
+        const int lr0 = wbase + lane / LPR;
+        if (lr0 < v.nrow) {
+            const int lr = rev ? v.nrow - 1 - lr0 : lr0;
+            if (!v.cached && lane == 0) {
+                // the warp's rows kPrefetchWaves waves on, [w0, w1) in loop order, [ra, rb) local
+                const int w0 = lr0 + kPrefetchWaves * (THREADS / LPR);
+                if (w0 < v.nrow) {
+                    const int w1 = min(w0 + 32 / LPR, v.nrow);
+                    const int ra = rev ? v.nrow - w1 : w0, rb = rev ? v.nrow - w0 : w1;
+                    prefetch_l2(a.bval + (size_t)(v.b_begin + v.rp[ra]) * 9, a.bval + (size_t)(v.b_begin + v.rp[rb]) * 9);
+                    prefetch_l2(a.col_idx + v.b_begin + v.rp[ra], a.col_idx + v.b_begin + v.rp[rb]);
+                }
+            }
+            T y0 = 0, y1 = 0, y2 = 0;
+            const int be = v.rp[lr + 1];
+            if (v.gathered) {
+                for (int b = v.rp[lr] + sub; b < be; b += LPR)
+                    block_times(v.val + (size_t)b * 9, v.gu[3 * b], v.gu[3 * b + 1], v.gu[3 * b + 2], y0, y1, y2);
+            } else {
+                // matrix rows cached, u not gathered: up to four of the lane's blocks at a time,
+                // every load in flight before any tag is checked (a check is a branch on the value)
+                constexpr int U = 4;
+                for (int b0 = v.rp[lr] + sub; b0 < be; b0 += U * LPR) {
+                    int cc[U];
 #pragma unroll
-                for (int k = 0; k < U; ++k) {
-                    const int b = b0 + k * kLanesPerRow;
-                    cc[k] = -1;
-                    if (b < be) {
-                        if (v.cached) {
-                            cc[k] = v.col[b];
-                        } else {
-                            if (TTIE_BAD(a.ds, (unsigned long long)(v.b_begin + b) < a.ds->nnzb, 41, b)) continue;
-                            const int c = a.col_idx[v.b_begin + b];
-                            if (TTIE_BAD(a.ds, c >= 0 && (unsigned long long)c < a.ds->n_rows, 42, c)) continue;
-                            cc[k] = c;
+                    for (int k = 0; k < U; ++k) {
+                        const int b = b0 + k * LPR;
+                        cc[k] = -1;
+                        if (b < be) {
+                            if (v.cached) {
+                                cc[k] = v.col[b];
+                            } else {
+                                if (TTIE_BAD(a.ds, (unsigned long long)(v.b_begin + b) < a.ds->nnzb, 41, b)) continue;
+                                const int c = a.col_idx[v.b_begin + b];
+                                if (TTIE_BAD(a.ds, c >= 0 && (unsigned long long)c < a.ds->n_rows, 42, c)) continue;
+                                cc[k] = c;
+                            }
                         }
                     }
+                    vec4_t<T> g[U];
+#pragma unroll
+                    for (int k = 0; k < U; ++k)
+                        if (cc[k] >= 0) g[k] = ld_row<T>(&src[cc[k]]);
+#pragma unroll
+                    for (int k = 0; k < U; ++k)
+                        if (cc[k] >= 0) {
+                            settle_row<T>(g[k], &src[cc[k]], t, bad);
+                            const int b = b0 + k * LPR;
+                            const T *m = v.cached ? v.val + (size_t)b * 9 : a.bval + (size_t)(v.b_begin + b) * 9;
+                            block_times(m, g[k].x, g[k].y, g[k].z, y0, y1, y2);
+                        }
                 }
-                vec4_t<T> g[U];
-#pragma unroll
-                for (int k = 0; k < U; ++k)
-                    if (cc[k] >= 0) g[k] = ld_row<T>(&src[cc[k]]);
-#pragma unroll
-                for (int k = 0; k < U; ++k)
-                    if (cc[k] >= 0) {
-                        settle_row<T>(g[k], &src[cc[k]], t, bad);
-                        const int b = b0 + k * kLanesPerRow;
-                        const T *m = v.cached ? v.val + (size_t)b * 9 : a.bval + (size_t)(v.b_begin + b) * 9;
-                        block_times(m, g[k].x, g[k].y, g[k].z, y0, y1, y2);
-                    }
             }
-        }
 #pragma unroll
-        for (int o = kLanesPerRow / 2; o; o >>= 1) {
-            y0 += __shfl_xor_sync(gmask, y0, o, kLanesPerRow);
-            y1 += __shfl_xor_sync(gmask, y1, o, kLanesPerRow);
-            y2 += __shfl_xor_sync(gmask, y2, o, kLanesPerRow);
-        }
-        if (sub == 0) {
-            const T w0 = y0 + mu * loc[lr * 3], w1 = y1 + mu * loc[lr * 3 + 1], w2 = y2 + mu * loc[lr * 3 + 2];
-            v.w[lr * 3] = w0; v.w[lr * 3 + 1] = w1; v.w[lr * 3 + 2] = w2;
-            wu.add_prod(w0, loc[lr * 3]);
-            wu.add_prod(w1, loc[lr * 3 + 1]);
-            wu.add_prod(w2, loc[lr * 3 + 2]);
+            for (int o = LPR / 2; o; o >>= 1) {
+                y0 += __shfl_xor_sync(gmask, y0, o, LPR);
+                y1 += __shfl_xor_sync(gmask, y1, o, LPR);
+                y2 += __shfl_xor_sync(gmask, y2, o, LPR);
+            }
+            if (sub == 0) {
+                const T w0 = y0 + mu * loc[lr * 3], w1 = y1 + mu * loc[lr * 3 + 1], w2 = y2 + mu * loc[lr * 3 + 2];
+                v.w[lr * 3] = w0; v.w[lr * 3 + 1] = w1; v.w[lr * 3 + 2] = w2;
+                wu.add_prod(w0, loc[lr * 3]);
+                wu.add_prod(w1, loc[lr * 3 + 1]);
+                wu.add_prod(w2, loc[lr * 3 + 2]);
+            }
         }
     }
     return wu;
@@ -1206,6 +1235,19 @@ cudaError_t pcg_solve(Ctx &c, const T *rhs, T *out, double rtol, int max_it) {
                           (c.prm.pcg_kernel == TTIE_PCG_KERNEL_STREAMED ||
                            (c.prm.pcg_kernel == TTIE_PCG_KERNEL_AUTO && !resident));
     if (streamed) return pcg_streamed<T>(c, rhs, out, rtol, max_it);
+    // 512 threads when the blocks' matrix rows are expected in shared memory, else 1024 with
+    // the rows streamed from global memory; then the launch asks for just the shared memory of
+    // the lean layout (the partition's rows capped at 1/8 above the mean) and leaves the rest
+    // of the SM's 256 KB of L1 and shared memory to L1, which holds the streamed rows' loads
+    // (L1 28 -> about 60 KB on the noisy sphere: 18.8 -> 18.5 ms for 200 iterations)
+    const bool no_cache = c.prm.pcg_kernel == TTIE_PCG_KERNEL_RESIDENT_UNCACHED;
+    const bool narrow = blk_bytes <= (int64_t)kResidentSmem && !no_cache;
+    int64_t r_cap_run = r_cap, smem_run = kResidentSmem;
+    if (resident && !narrow) {
+        const int64_t per_row = (cheb ? 21 : 15) * (int64_t)sizeof(T) + 4;
+        r_cap_run = std::min<int64_t>(r_cap, (nr + blocks - 1) / blocks * 9 / 8 + 32);
+        smem_run = std::min<int64_t>(kResidentSmem, (r_cap_run * per_row + 64 + 1023) / 1024 * 1024);
+    }
     if (cheb && resident) {
         // odd publications; zeros carry tag 0, which no odd publication has
         TTIE_CUDA_TRY(ensure(c, c.pcg_z4b, (size_t)(nr > 0 ? nr : 1) * sizeof(vec4_t<T>)));
@@ -1222,7 +1264,7 @@ cudaError_t pcg_solve(Ctx &c, const T *rhs, T *out, double rtol, int max_it) {
                                                  (T *)c.pcg_r.p, (T *)c.pcg_z.p, (T *)c.pcg_p.p, part,
                                                  (vec4_t<T> *)c.pcg_z4.p, (unsigned long long *)slots,
                                                  (int)((2 * kMaxGridPcg + 2) * sizeof(RedSlot) / sizeof(unsigned long long)),
-                                                 resident ? rpart : nullptr, (int)blocks, (int)r_cap, kRowWeight, c.ds);
+                                                 resident ? rpart : nullptr, (int)blocks, (int)r_cap_run, kRowWeight, c.ds);
     TTIE_CUDA_TRY(cudaGetLastError());
     PcgArgs<T> args;
     args.row_ptr = (const int32_t *)c.row_ptr.p;
@@ -1247,19 +1289,20 @@ cudaError_t pcg_solve(Ctx &c, const T *rhs, T *out, double rtol, int max_it) {
     args.slots = slots;
     args.part = rpart;
     args.withhold = c.prm.test_withhold;
-    args.no_cache = c.prm.pcg_kernel == TTIE_PCG_KERNEL_RESIDENT_UNCACHED ? 1 : 0;
+    args.no_cache = no_cache ? 1 : 0;
     ++c.n_launch;
     if (c.prm.profile) cudaEventRecord(c.ev[8], c.stream);
     if (resident) {
-        // 512 threads when the blocks' matrix rows are expected in shared memory, else 1024
-        const bool narrow = blk_bytes <= (int64_t)kResidentSmem && !args.no_cache;
         const void *kern = cheb ? (narrow ? (const void *)k_pcg_resident<T, true, 512> : (const void *)k_pcg_resident<T, true, 1024>)
                                 : (narrow ? (const void *)k_pcg_resident<T, false, 512> : (const void *)k_pcg_resident<T, false, 1024>);
         TTIE_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kResidentSmem));
-        int smem = kResidentSmem;
+        // the carve-out: the launch's shared memory with the static part, the rest L1
+        const int carve = (int)std::min<int64_t>(100, (smem_run + 8192) * 100 / (228 * 1024) + 1);
+        TTIE_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, carve));
+        int smem = (int)smem_run;
         void *kargs[] = {&args, &smem};
         TTIE_CUDA_TRY(cudaLaunchCooperativeKernel(kern, dim3((unsigned)blocks), dim3(narrow ? 512 : 1024), kargs,
-                                                  (size_t)kResidentSmem, c.stream));
+                                                  (size_t)smem_run, c.stream));
     } else {
         void *kargs[] = {&args};
         TTIE_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)k_pcg_persistent<T>, dim3((unsigned)blocks),
