@@ -36,7 +36,11 @@ UNIT = "pair evals/s"
 L2_FLUSH_BYTES = 256 << 20   # larger than the 129 MB L2
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant kernel, from one ncu
 # capture of the kernels as they are now (None until one is taken)
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    # k_pcg_resident<float, no Chebyshev, 1024 threads>, first Newton step of the noisy sphere,
+    # one launch (200 iterations): dram__bytes_read.sum + dram__bytes_write.sum
+    ("noisy_sphere", "pcg"): 35391303000,
+}
 
 # Algorithmic bytes (the minimum an implementation moves, FP32):
 B_CANDIDATE = 104.0      # pair ids 8 + 2 x (indices 12 + coordinates 36)
