@@ -37,9 +37,9 @@ L2_FLUSH_BYTES = 256 << 20   # larger than the 129 MB L2
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant kernel, from one ncu
 # capture of the kernels as they are now (None until one is taken)
 NCU_TRAFFIC = {
-    # k_pcg_resident<float, no Chebyshev, 1024 threads>, first Newton step of the noisy sphere,
-    # one launch (200 iterations): dram__bytes_read.sum + dram__bytes_write.sum
-    ("noisy_sphere", "pcg"): 35391303000,
+    # k_pcg_resident<float, Chebyshev, 1024 threads>, first Newton step of the noisy sphere,
+    # one launch (68 iterations, 204 products): dram__bytes_read.sum + dram__bytes_write.sum
+    ("noisy_sphere", "pcg"): 35991111000,
 }
 
 # Algorithmic bytes (the minimum an implementation moves, FP32):
@@ -641,6 +641,25 @@ def main():
             nxt["psd_modes"][name] = {"ms_per_step": ms, "pcg_iters": inf["pcg_iters"],
                                       "energy_ratio": inf["energy_new"] / inf["energy"] if inf["energy"] else None,
                                       "alpha": inf["alpha"]}
+            cp.close()
+        # the PCG to its tolerance: one step with each preconditioner, iterations and the
+        # relative residual reached (block Jacobi may stop at its iteration cap first)
+        nxt["pcg_preconditioners"] = {}
+        for name, pc in (("block_jacobi", ttie.PCG_BLOCK_JACOBI), ("chebyshev", ttie.PCG_CHEBYSHEV)):
+            cp = ttie.Context(precision=precision, pair_mode=mode, pcg_precond=pc, profile=1)
+            cp.build_bvh(x0, tri, grp)
+            xs = x0.clone()
+            cp.newton_step(xs)
+
+            def one():
+                xs.copy_(x0)
+                return cp.newton_step(xs)
+            ms, inf = med(one)
+            nxt["pcg_preconditioners"][name] = {
+                "ms_per_step": ms, "pcg_ms": inf["ms_pcg"], "pcg_iters": inf["pcg_iters"],
+                "pcg_rel_residual": inf["pcg_rel_residual"], "rtol": cp.params.pcg_rtol,
+                "max_it": cp.params.pcg_max_it,
+                "energy_ratio": inf["energy_new"] / inf["energy"] if inf["energy"] else None}
             cp.close()
         cx = ttie.Context(precision=precision, pair_mode=mode)
         cx.build_bvh(x0, tri, grp)
