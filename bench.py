@@ -89,24 +89,29 @@ def workload(name):
     raise SystemExit("unknown workload %s" % name)
 
 
-def oracle_sample(m, n_side, mode=0):
-    """The workload restricted to the first n_side x n_side grid vertices (cloth), to whole
-    instances up to about 2 n_side^2 triangles (batched instances), or to the 2 n_side^2
-    triangles whose centroids lie nearest the first triangle's (a connected patch, others):
-    what the oracle can process in seconds."""
+def oracle_sample(m, n_side, mode=0, part=0, parts=1):
+    """The workload restricted to n_side x n_side grid vertices (cloth), to whole instances up to
+    about 2 n_side^2 triangles (batched instances), or to the 2 n_side^2 triangles whose
+    centroids lie nearest one triangle's (a connected patch, others): what the oracle can
+    process in seconds.  part of parts: one of parts disjoint-start samples spread over the
+    workload (part 0: the grid's corner, the first instances, the first triangle)."""
     import numpy as np
     import ttie_inputs as ti
     if m.V == 256 * 256:
         ij = np.arange(m.V)
-        keep_v = ((ij % 256) < n_side) & ((ij // 256) < n_side)
+        i0 = (part * (256 - n_side)) // max(parts - 1, 1) if parts > 1 else 0
+        keep_v = ((ij % 256) >= i0) & ((ij % 256) < i0 + n_side) & ((ij // 256) < n_side)
         keep_t = keep_v[m.tri].all(axis=1)
     elif mode == 2:
         counts = np.bincount(m.group)
-        upto = max(1, int(np.searchsorted(np.cumsum(counts), 2 * n_side * n_side)))
-        keep_t = m.group < upto
+        cum = np.cumsum(counts)
+        g0 = int(np.searchsorted(cum, cum[-1] * part // parts, side="right")) if parts > 1 else 0
+        upto = max(g0 + 1, int(np.searchsorted(cum, (cum[g0 - 1] if g0 else 0) + 2 * n_side * n_side)))
+        keep_t = (m.group >= g0) & (m.group < upto)
     else:
         cen = m.x[m.tri].mean(axis=1)
-        near = np.argsort(np.linalg.norm(cen - cen[0], axis=1), kind="stable")[: n_side * n_side * 2]
+        a = (part * m.F) // parts
+        near = np.argsort(np.linalg.norm(cen - cen[a], axis=1), kind="stable")[: n_side * n_side * 2]
         keep_t = np.zeros(m.F, bool)
         keep_t[near] = True
     tri = m.tri[keep_t]
@@ -240,6 +245,37 @@ def cpu_baseline(m, mode=0, seconds_target=15.0):
             "sample": "oracle on a sample of the workload (an 80x80-vertex patch of a grid, whole instances "
                       "up to ~12,800 triangles, or a patch of 12,800 triangles; %d triangles, %d candidate "
                       "pairs) x %d, %.1f s" % (sub.F, n // reps, reps, dt)}
+
+
+def _oracle_worker(sub, mode, seconds_target):
+    """One process of the all-cores baseline: the oracle over its sample until the target time."""
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        n += oracle_step(sub, mode)
+        if time.perf_counter() - t0 > seconds_target:
+            break
+    return n, time.perf_counter() - t0
+
+
+def cpu_baseline_all_cores(m, mode=0, seconds_target=10.0):
+    """The oracle on every host core: one process per core (started by spawn, as the GPU is in
+    use), each running the oracle as it stands over its own sample of the workload; throughput
+    is all processes' candidate pairs over the wall time."""
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    subs = [oracle_sample(m, 80, mode, part=i, parts=cores) for i in range(cores)]
+    t0 = time.perf_counter()
+    with mp.get_context("spawn").Pool(cores) as pool:
+        res = pool.starmap(_oracle_worker, [(sub, mode, seconds_target) for sub in subs])
+    wall = time.perf_counter() - t0
+    n = sum(r[0] for r in res)
+    busy = max(r[1] for r in res)   # the processes run side by side; the longest one's compute time
+    return {"value": n / busy, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "oracle, one process per host core, each on its own sample of the workload (an 80x80-vertex "
+                      "patch of a grid, whole instances up to ~12,800 triangles, or a patch of 12,800 triangles "
+                      "around a different triangle) for about %.0f s; %d candidate pairs over the longest "
+                      "process's %.1f s (%.1f s of wall time with process start)" % (seconds_target, n, busy, wall)}
 
 
 def rooflines(last, ms, peak, hbm):
@@ -674,9 +710,10 @@ def main():
         nxt["dual_gradients"] = {"ms": ms_du, "pairs": n_act0, "pairs_per_s": n_act0 / (ms_du / 1e3)}
         cx.close()
 
-    cpu = None
+    cpu = cpu_all = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline(m, mode)
+        cpu_all = cpu_baseline_all_cores(m, mode)
 
     if rank == 0:
         line = {
@@ -700,6 +737,7 @@ def main():
             "roofline_assembly": r_asm,
             "roofline_eval": r_ev,
             "cpu_baseline": cpu,
+            "cpu_baseline_all_cores": cpu_all,
             "fp64_form": fp64,
             "e2e": {"value": e2e_pairs / (e2e_ms / 1e3) if e2e_ms > 0 else None, "unit": UNIT,
                     "h2d_bytes_per_step": e2e_bytes, "d2h_bytes_per_step": e2e_bytes},
