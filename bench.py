@@ -263,7 +263,7 @@ def cpu_baseline_all_cores(m, mode=0, seconds_target=10.0):
     use), each running the oracle as it stands over its own sample of the workload; throughput
     is all processes' candidate pairs over the wall time."""
     import multiprocessing as mp
-    cores = os.cpu_count() or 1
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
     subs = [oracle_sample(m, 80, mode, part=i, parts=cores) for i in range(cores)]
     t0 = time.perf_counter()
     with mp.get_context("spawn").Pool(cores) as pool:
